@@ -1,0 +1,162 @@
+"""Plain CPU oracle for the Faugere-Lachartre reduction over GF(p).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA product path never imports, links or executes it, and it
+shares no code with that path: the only module both sides use is the seeded
+input generator ``paper_1602_06097_gb300.synth``, which holds none of the
+method's arithmetic.
+
+``oracle.c`` holds the arithmetic (exact uint64 with ``%``); this module only
+compiles it with gcc and marshals numpy arrays through ctypes.  Passages
+followed (GBLA paper, arXiv 1602.06097):
+
+* :func:`rref`     -- textbook Gauss-Jordan on the whole matrix: FL steps 4-5
+  and the reduced-echelon pass (Sec. 4.1), Alg. 3's normalise/reduce rule.
+* :func:`echelon`  -- the new order of operations (Alg. 2, Sec. 4.2) in plain
+  row form, then Gauss-Jordan of the Schur complement.
+* :func:`pivots`   -- the FL step-1 pivot choice (Sec. 3.1, Sec. 4.1 step 1).
+* :func:`multiline` -- the 2-multiline vector of Definition 1 (Sec. 4.2).
+
+Every function is pinned by ``tests/test_oracle.py`` against results fixed by
+the mathematics (brute-force row spaces, determinant ranks, closed forms,
+invariants) and, for :func:`multiline`, by the paper's Example 1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LOCK = threading.Lock()
+_LIBS: dict = {}
+
+
+def lib_path(mutant: int = 0) -> str:
+    name = "liboracle.so" if mutant == 0 else f"liboracle_mutant{mutant}.so"
+    return os.path.join(_HERE, name)
+
+
+def build(mutant: int = 0, force: bool = False) -> str:
+    """Compile oracle.c with gcc (OpenMP for the row-parallel forward pass)."""
+    out = lib_path(mutant)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           f"-DORACLE_MUTANT={int(mutant)}", _SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def _lib(mutant: int = 0):
+    with _LOCK:
+        if mutant in _LIBS:
+            return _LIBS[mutant]
+        lib = ctypes.CDLL(build(mutant))
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        u16p = ctypes.POINTER(ctypes.c_uint16)
+        vp = ctypes.c_void_p
+        lib.oracle_rref.restype = ctypes.c_int
+        lib.oracle_rref.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, vp, vp, vp,
+                                    i64p, ctypes.POINTER(i64p), ctypes.POINTER(i32p),
+                                    ctypes.POINTER(u16p)]
+        lib.oracle_echelon.restype = ctypes.c_int
+        lib.oracle_echelon.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, vp, vp, vp,
+                                       i64p, ctypes.POINTER(i64p), ctypes.POINTER(i32p),
+                                       ctypes.POINTER(u16p), i64p]
+        lib.oracle_pivots.restype = ctypes.c_int64
+        lib.oracle_pivots.argtypes = [ctypes.c_int64, ctypes.c_int64, vp, vp, vp]
+        lib.oracle_free.restype = None
+        lib.oracle_free.argtypes = [vp]
+        _LIBS[mutant] = lib
+        return lib
+
+
+def _csr_args(row_ptr, col, val):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.uint16)
+    return row_ptr, col, val
+
+
+def _take(lib, rank, rp, cl, vl):
+    r = int(rank.value)
+    row_ptr = np.ctypeslib.as_array(rp, shape=(r + 1,)).copy()
+    nnz = int(row_ptr[-1])
+    col = np.ctypeslib.as_array(cl, shape=(max(nnz, 1),))[:nnz].copy()
+    val = np.ctypeslib.as_array(vl, shape=(max(nnz, 1),))[:nnz].copy()
+    for ptr in (rp, cl, vl):
+        lib.oracle_free(ctypes.cast(ptr, ctypes.c_void_p))
+    return r, row_ptr, col, val
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def rref(m, n, p, row_ptr, col, val, mutant: int = 0):
+    """RREF(M) over GF(p): returns (rank, row_ptr, col, val), rows by pivot column."""
+    lib = _lib(mutant)
+    row_ptr, col, val = _csr_args(row_ptr, col, val)
+    rank = ctypes.c_int64(0)
+    rp = ctypes.POINTER(ctypes.c_int64)()
+    cl = ctypes.POINTER(ctypes.c_int32)()
+    vl = ctypes.POINTER(ctypes.c_uint16)()
+    rc = lib.oracle_rref(m, n, p, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
+                         ctypes.byref(rank), ctypes.byref(rp), ctypes.byref(cl), ctypes.byref(vl))
+    if rc != 0:
+        raise OracleError(f"oracle_rref failed with code {rc}")
+    return _take(lib, rank, rp, cl, vl)
+
+
+def echelon(m, n, p, row_ptr, col, val, mutant: int = 0):
+    """Canonical echelon form (normalised pivot rows + RREF of the Schur
+    complement): returns (rank, row_ptr, col, val, npiv)."""
+    lib = _lib(mutant)
+    row_ptr, col, val = _csr_args(row_ptr, col, val)
+    rank = ctypes.c_int64(0)
+    npiv = ctypes.c_int64(0)
+    rp = ctypes.POINTER(ctypes.c_int64)()
+    cl = ctypes.POINTER(ctypes.c_int32)()
+    vl = ctypes.POINTER(ctypes.c_uint16)()
+    rc = lib.oracle_echelon(m, n, p, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
+                            ctypes.byref(rank), ctypes.byref(rp), ctypes.byref(cl),
+                            ctypes.byref(vl), ctypes.byref(npiv))
+    if rc != 0:
+        raise OracleError(f"oracle_echelon failed with code {rc}")
+    return _take(lib, rank, rp, cl, vl) + (int(npiv.value),)
+
+
+def pivots(m, n, row_ptr, col, mutant: int = 0):
+    """FL step-1 pivot choice: array piv_row[c] (-1 where no row leads at c)."""
+    lib = _lib(mutant)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    out = np.empty(max(n, 1), dtype=np.int64)
+    lib.oracle_pivots(m, n, row_ptr.ctypes.data, col.ctypes.data, out.ctypes.data)
+    return out[:n]
+
+
+def multiline(cols1, vals1, cols2, vals2):
+    """2-multiline vector of two sparse rows (Definition 1, Sec. 4.2).
+
+    ``pos`` lists, ascending, every column where at least one of the two rows
+    is nonzero; ``val`` stores the two rows' entries at ``pos[i]`` next to each
+    other (row 1 first), with explicit zeros where only one row is nonzero.
+    """
+    a = dict(zip((int(c) for c in cols1), (int(v) for v in vals1)))
+    b = dict(zip((int(c) for c in cols2), (int(v) for v in vals2)))
+    pos = sorted(set(a) | set(b))
+    val = []
+    for c in pos:
+        val.append(a.get(c, 0))
+        val.append(b.get(c, 0))
+    return np.array(pos, dtype=np.int64), np.array(val, dtype=np.int64)

@@ -1,0 +1,431 @@
+/*
+ * oracle.c -- plain, slow, obviously-correct CPU reference for the
+ * Faugere-Lachartre (FL) reduction over GF(p), p < 2^16.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the tests, the package smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code, header, table or
+ * helper with the CUDA library.
+ *
+ * Arithmetic: exact integers.  Residues are kept in [0,p); working rows are
+ * uint64 accumulators that are only reduced with the C `%` operator when a
+ * value is read as a multiplier or stored (delayed reduction; every term
+ * added is < p^2 < 2^32, and no entry receives more than 2^31 additions, so
+ * no accumulator can overflow 2^64).
+ *
+ * Functions and the passages they follow (GBLA paper, arXiv 1602.06097):
+ *   oracle_rref     -- textbook Gauss-Jordan on the WHOLE matrix, rows taken
+ *                      in input order: FL steps 4-5 plus the reduced-echelon
+ *                      pass (Sec. 4.1, the RREF remark after step 5), and
+ *                      the "normalize, reduce by matching head" rule of
+ *                      Alg. 3 (Sec. 4.3).  Output: the unique reduced row
+ *                      echelon form of M, rows sorted by pivot column.
+ *   oracle_pivots   -- FL step 1 pivot choice (Sec. 3.1, Sec. 4.1 step 1):
+ *                      the leading (leftmost) nonzero of a row is its pivot
+ *                      candidate; among rows with the same candidate column
+ *                      the one keeping A sparsest is chosen.  The paper does
+ *                      not fix the tie-break; this oracle reads it as
+ *                      (fewest nonzeros, then smallest input row index).
+ *   oracle_echelon  -- the "new order of operations" (Alg. 2, Sec. 4.2) in
+ *                      plain row form: every non-pivot row is reduced by the
+ *                      normalised pivot rows in ascending pivot column order
+ *                      (this is C <- C*A^-1 with D <- D - C*A^-1*B applied on
+ *                      the fly), then the leftover rows (the Schur complement
+ *                      D') are brought to reduced echelon form by the same
+ *                      textbook Gauss-Jordan (Sec. 4.1 step 4).  Output: the
+ *                      normalised pivot rows plus RREF(D'), merged in pivot
+ *                      column order (the canonical non-reduced echelon form).
+ *
+ * Parity pins live in tests/test_oracle.py (brute-force row spaces over
+ * GF(7), Leibniz-determinant ranks, closed-form special cases, invariants).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORA_OK 0
+#define ORA_E_INVAL 1
+#define ORA_E_NOMEM 2
+
+/* Compile-time planted mistakes, used only by the mutation test that shows
+ * the pins are sensitive.  0 = the real oracle. */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+
+/* Modular inverse by the extended Euclidean algorithm (a != 0 mod p). */
+static uint64_t ora_inv(uint64_t a, uint64_t p)
+{
+    int64_t t = 0, newt = 1;
+    int64_t r = (int64_t)p, newr = (int64_t)(a % p);
+    while (newr != 0) {
+        int64_t q = r / newr, tmp;
+        tmp = t - q * newt; t = newt; newt = tmp;
+        tmp = r - q * newr; r = newr; newr = tmp;
+    }
+    if (t < 0) t += (int64_t)p;
+    return (uint64_t)t;
+}
+
+/* Validate a CSR matrix: row_ptr monotone from 0, columns strictly increasing
+ * inside a row and in [0,n), values in [1,p).  p must be a prime < 2^16
+ * (primality checked by trial division). */
+static int ora_validate(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
+                        const int32_t *col, const uint16_t *val)
+{
+    if (m < 0 || n < 0 || p < 2 || p >= 65536u) return ORA_E_INVAL;
+    for (uint32_t d = 2; d * d <= p; ++d)
+        if (p % d == 0) return ORA_E_INVAL;
+    if (m > 0 && !row_ptr) return ORA_E_INVAL;
+    if (m > 0 && row_ptr[0] != 0) return ORA_E_INVAL;
+    for (int64_t i = 0; i < m; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return ORA_E_INVAL;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (col[e] < 0 || col[e] >= n) return ORA_E_INVAL;
+            if (e > row_ptr[i] && col[e] <= col[e - 1]) return ORA_E_INVAL;
+            if (val[e] == 0 || val[e] >= p) return ORA_E_INVAL;
+        }
+    }
+    return ORA_OK;
+}
+
+/* A growing list of reduced dense rows (entries in [0,p)), each with the
+ * column of its pivot (leading 1). */
+typedef struct {
+    int64_t n, count, cap;
+    uint32_t *rows;   /* count x n */
+    int64_t *pcol;    /* pivot column of each row */
+} ora_rows;
+
+static int ora_rows_push(ora_rows *R, const uint64_t *w, int64_t pc)
+{
+    if (R->count == R->cap) {
+        int64_t nc = R->cap ? 2 * R->cap : 16;
+        uint32_t *nr = (uint32_t *)realloc(R->rows, (size_t)nc * (size_t)(R->n ? R->n : 1) * sizeof(uint32_t));
+        if (!nr) return ORA_E_NOMEM;
+        R->rows = nr;
+        int64_t *np = (int64_t *)realloc(R->pcol, (size_t)nc * sizeof(int64_t));
+        if (!np) return ORA_E_NOMEM;
+        R->pcol = np;
+        R->cap = nc;
+    }
+    uint32_t *dst = R->rows + (size_t)R->count * (size_t)R->n;
+    for (int64_t k = 0; k < R->n; ++k) dst[k] = (uint32_t)w[k];
+    R->pcol[R->count] = pc;
+    R->count++;
+    return ORA_OK;
+}
+
+/*
+ * Textbook Gauss-Jordan over GF(p) on dense rows.
+ *
+ * Forward pass (Sec. 4.1 step 4, Alg. 3): each row in turn is scattered into
+ * a dense accumulator; scanning its columns left to right, every nonzero
+ * entry whose column already owns a pivot row is cancelled by subtracting
+ * that multiple of the pivot row; the first nonzero entry whose column owns
+ * no pivot makes the row (normalised to a leading 1) the pivot of that
+ * column.  Rows that cancel completely are zero reductions and are dropped.
+ *
+ * Backward pass (the RREF remark after FL step 5): pivot rows are taken in
+ * descending pivot column order; each one subtracts from itself the final
+ * rows of all larger pivot columns, which clears every pivot column except
+ * its own.
+ *
+ * `in` holds `m_in` dense input rows of width n with entries in [0,p).
+ * Result rows (sorted by pivot column, entries in [0,p)) go to *out.
+ */
+static int ora_gauss_jordan(int64_t n, uint32_t p, int64_t m_in,
+                            const uint32_t *in, ora_rows *out)
+{
+    int rc = ORA_OK;
+    int64_t *pivot_of = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    uint64_t *w = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    ora_rows E = {n, 0, 0, NULL, NULL};
+    if (!pivot_of || !w) { rc = ORA_E_NOMEM; goto done; }
+    for (int64_t j = 0; j < n; ++j) pivot_of[j] = -1;
+
+    for (int64_t i = 0; i < m_in; ++i) {
+        const uint32_t *src = in + (size_t)i * (size_t)n;
+        for (int64_t k = 0; k < n; ++k) w[k] = src[k];
+        for (int64_t j = 0; j < n; ++j) {
+            uint64_t f = w[j] % p;
+            if (f == 0) continue;
+            if (pivot_of[j] >= 0) {
+                const uint32_t *P = E.rows + (size_t)pivot_of[j] * (size_t)n;
+                uint64_t g = p - f;            /* subtract f * P */
+#if ORACLE_MUTANT == 1
+                g = f;                          /* planted: wrong sign */
+#endif
+                for (int64_t k = j; k < n; ++k) w[k] += g * P[k];
+            } else {
+                uint64_t inv = ora_inv(f, p);
+                for (int64_t k = 0; k < j; ++k) w[k] = 0;
+                for (int64_t k = j; k < n; ++k) w[k] = (w[k] % p) * inv % p;
+                pivot_of[j] = E.count;
+                if ((rc = ora_rows_push(&E, w, j)) != ORA_OK) goto done;
+                break;
+            }
+        }
+    }
+
+    /* Backward pass, descending pivot columns. */
+    {
+        int64_t r = E.count;
+        int64_t *order = (int64_t *)malloc((size_t)(r ? r : 1) * sizeof(int64_t));
+        if (!order) { rc = ORA_E_NOMEM; goto done; }
+        int64_t t = 0;
+        for (int64_t j = 0; j < n; ++j)
+            if (pivot_of[j] >= 0) order[t++] = pivot_of[j]; /* ascending columns */
+        for (int64_t a = r - 1; a >= 0; --a) {
+            uint32_t *Q = E.rows + (size_t)order[a] * (size_t)n;
+            int64_t qc = E.pcol[order[a]];
+            for (int64_t k = 0; k < n; ++k) w[k] = Q[k];
+            for (int64_t b = a + 1; b < r; ++b) {
+                int64_t c = E.pcol[order[b]];
+                uint64_t f = w[c] % p;
+                if (f == 0) continue;
+                const uint32_t *P = E.rows + (size_t)order[b] * (size_t)n;
+                uint64_t g = p - f;
+#if ORACLE_MUTANT == 2
+                if (b == a + 1) continue;       /* planted: dropped term */
+#endif
+                for (int64_t k = c; k < n; ++k) w[k] += g * P[k];
+            }
+            for (int64_t k = qc; k < n; ++k) Q[k] = (uint32_t)(w[k] % p);
+        }
+        /* Emit in ascending pivot column order. */
+        for (int64_t a = 0; a < r; ++a) {
+            const uint32_t *Q = E.rows + (size_t)order[a] * (size_t)n;
+            for (int64_t k = 0; k < n; ++k) w[k] = Q[k];
+            if ((rc = ora_rows_push(out, w, E.pcol[order[a]])) != ORA_OK) { free(order); goto done; }
+        }
+        free(order);
+    }
+done:
+    free(pivot_of);
+    free(w);
+    free(E.rows);
+    free(E.pcol);
+    return rc;
+}
+
+/* Convert reduced dense rows to a freshly malloc'ed CSR (zeros dropped). */
+static int ora_rows_to_csr(const ora_rows *R, int64_t **rp, int32_t **cl, uint16_t **vl)
+{
+    int64_t nnz = 0;
+    for (int64_t a = 0; a < R->count; ++a)
+        for (int64_t k = 0; k < R->n; ++k)
+            if (R->rows[(size_t)a * (size_t)R->n + (size_t)k]) nnz++;
+    int64_t *row_ptr = (int64_t *)malloc((size_t)(R->count + 1) * sizeof(int64_t));
+    int32_t *col = (int32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t));
+    uint16_t *val = (uint16_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint16_t));
+    if (!row_ptr || !col || !val) { free(row_ptr); free(col); free(val); return ORA_E_NOMEM; }
+    int64_t e = 0;
+    row_ptr[0] = 0;
+    for (int64_t a = 0; a < R->count; ++a) {
+        const uint32_t *Q = R->rows + (size_t)a * (size_t)R->n;
+        for (int64_t k = 0; k < R->n; ++k)
+            if (Q[k]) { col[e] = (int32_t)k; val[e] = (uint16_t)Q[k]; ++e; }
+        row_ptr[a + 1] = e;
+    }
+    *rp = row_ptr; *cl = col; *vl = val;
+    return ORA_OK;
+}
+
+void oracle_free(void *ptr) { free(ptr); }
+
+/*
+ * RREF(M) over GF(p), M given as CSR (m x n).  On success *rank is the number
+ * of rows of the result and *out_* are malloc'ed (release with oracle_free).
+ */
+int oracle_rref(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
+                const int32_t *col, const uint16_t *val, int64_t *rank,
+                int64_t **out_row_ptr, int32_t **out_col, uint16_t **out_val)
+{
+    int rc = ora_validate(m, n, p, row_ptr, col, val);
+    if (rc) return rc;
+    uint32_t *dense = (uint32_t *)calloc((size_t)(m ? m : 1) * (size_t)(n ? n : 1), sizeof(uint32_t));
+    if (!dense) return ORA_E_NOMEM;
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            dense[(size_t)i * (size_t)n + (size_t)col[e]] = val[e];
+    ora_rows R = {n, 0, 0, NULL, NULL};
+    rc = ora_gauss_jordan(n, p, m, dense, &R);
+    free(dense);
+    if (rc == ORA_OK) rc = ora_rows_to_csr(&R, out_row_ptr, out_col, out_val);
+    if (rc == ORA_OK) *rank = R.count;
+    free(R.rows);
+    free(R.pcol);
+    return rc;
+}
+
+/*
+ * FL step 1 pivot choice.  piv_row[c] = input row chosen as pivot for column
+ * c, or -1 if no row leads at c.  Rows lead at their leftmost nonzero; among
+ * rows sharing a leading column the one with the fewest nonzeros wins, ties
+ * going to the smaller row index.  Returns the number of pivots.
+ */
+int64_t oracle_pivots(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                      int64_t *piv_row)
+{
+    int64_t npiv = 0;
+    for (int64_t c = 0; c < n; ++c) piv_row[c] = -1;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t w = row_ptr[i + 1] - row_ptr[i];
+        if (w == 0) continue;
+        int64_t c = col[row_ptr[i]];
+        int64_t cur = piv_row[c];
+        if (cur < 0) { piv_row[c] = i; npiv++; continue; }
+        int64_t wc = row_ptr[cur + 1] - row_ptr[cur];
+#if ORACLE_MUTANT == 3
+        if (w > wc) piv_row[c] = i;              /* planted: densest row wins */
+#else
+        if (w < wc) piv_row[c] = i;              /* strictly fewer: earlier index keeps ties */
+#endif
+    }
+    return npiv;
+}
+
+/*
+ * Canonical echelon form by the new order of operations (Alg. 2), plain row
+ * form.  Output rows: the chosen pivot rows normalised to a leading 1, plus
+ * RREF of the Schur complement, merged by pivot column.
+ */
+int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
+                   const int32_t *col, const uint16_t *val, int64_t *rank,
+                   int64_t **out_row_ptr, int32_t **out_col, uint16_t **out_val,
+                   int64_t *npiv_out)
+{
+    int rc = ora_validate(m, n, p, row_ptr, col, val);
+    if (rc) return rc;
+    int64_t *piv_row = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    uint64_t *inv_lead = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    char *is_piv_row = (char *)calloc((size_t)(m ? m : 1), 1);
+    if (!piv_row || !inv_lead || !is_piv_row) { rc = ORA_E_NOMEM; goto fail0; }
+    int64_t npiv = oracle_pivots(m, n, row_ptr, col, piv_row);
+    for (int64_t c = 0; c < n; ++c)
+        if (piv_row[c] >= 0) {
+            is_piv_row[piv_row[c]] = 1;
+            inv_lead[c] = ora_inv(val[row_ptr[piv_row[c]]], p);
+        }
+
+    /* Non-pivot, non-empty rows in input order. */
+    int64_t mcd = 0;
+    for (int64_t i = 0; i < m; ++i)
+        if (!is_piv_row[i] && row_ptr[i + 1] > row_ptr[i]) mcd++;
+    int64_t *cd_rows = (int64_t *)malloc((size_t)(mcd ? mcd : 1) * sizeof(int64_t));
+    uint32_t *left = (uint32_t *)calloc((size_t)(mcd ? mcd : 1) * (size_t)(n ? n : 1), sizeof(uint32_t));
+    if (!cd_rows || !left) { free(cd_rows); free(left); rc = ORA_E_NOMEM; goto fail0; }
+    mcd = 0;
+    for (int64_t i = 0; i < m; ++i)
+        if (!is_piv_row[i] && row_ptr[i + 1] > row_ptr[i]) cd_rows[mcd++] = i;
+
+    /* Reduce every non-pivot row by the pivot rows, pivot columns ascending
+     * (Alg. 2: the multiplier dense_C[j] is final once all smaller pivot
+     * columns are cleared, since the pivot rows are zero left of their
+     * leading column).  Rows are independent of one another. */
+    int fail = 0;
+#pragma omp parallel
+    {
+        uint64_t *w = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+        if (!w) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < mcd; ++t) {
+            if (!w) continue;
+            int64_t i = cd_rows[t];
+            memset(w, 0, (size_t)n * sizeof(uint64_t));
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) w[col[e]] = val[e];
+            for (int64_t j = 0; j < n; ++j) {
+                if (piv_row[j] < 0) continue;
+                uint64_t f = w[j] % p;
+                if (f == 0) { w[j] = 0; continue; }
+                /* multiplier of the normalised pivot row = f; the pivot row
+                 * holds val * inv_lead, so subtract (f * inv_lead) * val. */
+                int64_t r = piv_row[j];
+                uint64_t g = (p - f) * inv_lead[j] % p;
+                for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+                    w[col[e]] += g * val[e];
+            }
+            uint32_t *dst = left + (size_t)t * (size_t)n;
+            for (int64_t k = 0; k < n; ++k) dst[k] = (uint32_t)(w[k] % p);
+        }
+        free(w);
+    }
+    if (fail) { free(cd_rows); free(left); rc = ORA_E_NOMEM; goto fail0; }
+
+    ora_rows B = {n, 0, 0, NULL, NULL};
+    rc = ora_gauss_jordan(n, p, mcd, left, &B);
+    free(left);
+    free(cd_rows);
+    if (rc) { free(B.rows); free(B.pcol); goto fail0; }
+
+    /* Merge: top rows (pivot columns of A) and bottom rows (pivots of D'). */
+    {
+        int64_t r = npiv + B.count, nnz = 0;
+        for (int64_t c = 0; c < n; ++c)
+            if (piv_row[c] >= 0) nnz += row_ptr[piv_row[c] + 1] - row_ptr[piv_row[c]];
+        for (int64_t a = 0; a < B.count; ++a)
+            for (int64_t k = 0; k < n; ++k)
+                if (B.rows[(size_t)a * (size_t)n + (size_t)k]) nnz++;
+        int64_t *rp = (int64_t *)malloc((size_t)(r + 1) * sizeof(int64_t));
+        int32_t *cl = (int32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t));
+        uint16_t *vl = (uint16_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint16_t));
+        int64_t *bottom_of = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+        if (!rp || !cl || !vl || !bottom_of) {
+            free(rp); free(cl); free(vl); free(bottom_of); free(B.rows); free(B.pcol);
+            rc = ORA_E_NOMEM; goto fail0;
+        }
+        for (int64_t c = 0; c < n; ++c) bottom_of[c] = -1;
+        for (int64_t a = 0; a < B.count; ++a) bottom_of[B.pcol[a]] = a;
+        int64_t e = 0, a_out = 0;
+        rp[0] = 0;
+        for (int64_t c = 0; c < n; ++c) {
+            if (piv_row[c] >= 0) {
+                int64_t i = piv_row[c];
+                for (int64_t s = row_ptr[i]; s < row_ptr[i + 1]; ++s) {
+                    cl[e] = col[s];
+                    vl[e] = (uint16_t)((uint64_t)val[s] * inv_lead[c] % p);
+                    ++e;
+                }
+                rp[++a_out] = e;
+            } else if (bottom_of[c] >= 0) {
+                const uint32_t *Q = B.rows + (size_t)bottom_of[c] * (size_t)n;
+                for (int64_t k = 0; k < n; ++k)
+                    if (Q[k]) { cl[e] = (int32_t)k; vl[e] = (uint16_t)Q[k]; ++e; }
+                rp[++a_out] = e;
+            }
+        }
+        free(bottom_of);
+        free(B.rows);
+        free(B.pcol);
+        *out_row_ptr = rp; *out_col = cl; *out_val = vl;
+        *rank = r;
+        if (npiv_out) *npiv_out = npiv;
+    }
+fail0:
+    free(piv_row);
+    free(inv_lead);
+    free(is_piv_row);
+    return rc;
+}
+
+/*
+ * Reference split of a matrix into the FL blocks (Sec. 4.1 step 1, Table 2),
+ * used only to pin the shapes of the split.  Outputs the pivot count and the
+ * number of non-pivot non-empty rows.
+ */
+int oracle_split_shape(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                       int64_t *npiv, int64_t *m_cd)
+{
+    int64_t *piv_row = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    if (!piv_row) return ORA_E_NOMEM;
+    *npiv = oracle_pivots(m, n, row_ptr, col, piv_row);
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < m; ++i) if (row_ptr[i + 1] > row_ptr[i]) cnt++;
+    *m_cd = cnt - *npiv;
+    free(piv_row);
+    return ORA_OK;
+}

@@ -1,0 +1,258 @@
+"""Seeded synthetic F4-shaped matrices over GF(p).
+
+This module only draws random matrices; it holds none of the reduction's
+arithmetic.  Both the CUDA path's tests/benchmarks and the CPU oracle's tests
+read their inputs from here.
+
+The shapes follow the statistics the GBLA paper gives for matrices out of F4
+and F5 symbolic preprocessing (Sec. 3.1, Sec. 4.2 and Tables 2 and 6): rows are
+polynomials, columns monomials in decreasing order; a row's leftmost nonzero
+is its pivoting candidate; many rows share a leading column; nonzeros come in
+horizontal runs of consecutive columns, and neighbouring rows repeat one
+another's pattern (the "vertical pattern").  The paper's own matrices are not
+reproduced: only their shape statistics are.
+
+Recipe (all draws from ``numpy.random.Generator(PCG64(seed))``):
+
+1. ``npiv`` distinct leading columns are drawn uniformly in ``[0, n)``.  Each
+   designated pivot row has value 1 at its lead.
+2. Every row gets ``k = round(density * n * U[1-spread, 1+spread])`` nonzeros
+   (clipped to the columns right of its lead) laid out in runs whose lengths
+   are uniform in ``run_len``; the runs are spread uniformly over the columns
+   right of the lead.
+3. With ``group=(gmin, gmax)``, consecutive designated leads form groups whose
+   members copy the group's run pattern shifted by the difference of leads
+   (a monomial shift), with a fraction ``1 - share`` of runs redrawn.
+4. A non-pivot row leads, with probability ``lead_from_pivot``, at the lead of
+   a random designated pivot row (an S-pair-like reducible row, copying that
+   row's group pattern when groups are on) and otherwise at a random other
+   column; its leading value is uniform in ``[1, p-1]``.
+5. All other values are uniform in ``[1, p-1]``; rows are shuffled.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class FLSpec:
+    m: int
+    n: int
+    npiv: int
+    p: int = 65521
+    density: float = 0.04
+    run_len: tuple = (4, 32)
+    spread: float = 0.5
+    lead_from_pivot: float = 0.9
+    group: tuple | None = None
+    share: float = 0.8
+    seed: int = 20160219
+
+
+def _runs(rng, lead, k, n, run_len):
+    """Column indices of runs totalling k[i] entries right of lead[i].
+
+    Returns (row_of_entry, col_of_entry) sorted by row then column.
+    """
+    k = k.astype(np.int64)
+    total = int(k.sum())
+    if total == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    K = np.cumsum(k)
+    mean = 0.5 * (run_len[0] + run_len[1])
+    lens = rng.integers(run_len[0], run_len[1] + 1, size=int(total / mean * 1.25) + 16)
+    C = np.cumsum(lens)
+    while C[-1] < total:
+        more = rng.integers(run_len[0], run_len[1] + 1, size=len(lens))
+        lens = np.concatenate([lens, more])
+        C = np.cumsum(lens)
+    # Piece boundaries: run boundaries of one global stream cut at row ends.
+    bounds = _sorted_unique(np.concatenate([C[C < total], K[:-1]]))
+    bounds = bounds[bounds > 0]
+    bounds = np.concatenate([[0], bounds, [total]]).astype(np.int64)
+    pstart = bounds[:-1]
+    plen = np.diff(bounds)
+    prow = np.searchsorted(K, pstart, side="right")
+    row_first_slot = K - k
+    span = n - lead - 1
+    free = span - k
+    o = (rng.random(len(pstart)) * (free[prow] + 1)).astype(np.int64)
+    o = np.minimum(o, free[prow])
+    order = np.lexsort((o, prow))
+    o = o[order]
+    start_col = lead[prow] + 1 + o + (pstart - row_first_slot[prow])
+    within = np.arange(total, dtype=np.int64) - np.repeat(pstart, plen)
+    cols = np.repeat(start_col, plen) + within
+    rows = np.repeat(prow, plen)
+    return rows, cols
+
+
+def _sorted_unique(a):
+    a = np.sort(a, kind="stable")
+    if len(a) == 0:
+        return a
+    keep = np.empty(len(a), bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
+def _row_counts(rng, nrows, density, n, spread):
+    base = density * n
+    f = 1.0 + spread * (2.0 * rng.random(nrows) - 1.0)
+    return np.maximum(1, np.rint(base * f)).astype(np.int64)
+
+
+def fl_matrix(spec: FLSpec):
+    """Draw one matrix.  Returns (row_ptr int64[m+1], col int32[nnz], val uint16[nnz])."""
+    rng = np.random.Generator(np.random.PCG64(spec.seed))
+    m, n, npiv, p = spec.m, spec.n, spec.npiv, spec.p
+    if not (0 <= npiv <= min(m, n)):
+        raise ValueError("need 0 <= npiv <= min(m, n)")
+    piv_leads = np.sort(rng.choice(n, size=npiv, replace=False)).astype(np.int64)
+    mnp = m - npiv
+    # Leads of the non-pivot rows.
+    from_piv = rng.random(mnp) < spec.lead_from_pivot if npiv > 0 else np.zeros(mnp, bool)
+    which = rng.integers(0, max(npiv, 1), size=mnp)
+    lead_np = np.where(from_piv, piv_leads[np.minimum(which, max(npiv - 1, 0))] if npiv else 0,
+                       rng.integers(0, n, size=mnp))
+    lead = np.concatenate([piv_leads, lead_np]).astype(np.int64)
+    k = _row_counts(rng, m, spec.density, n, spec.spread) - 1
+    k = np.minimum(k, n - lead - 1)
+
+    if spec.group is None:
+        rows, cols = _runs(rng, lead, k, n, spec.run_len)
+    else:
+        rows, cols = _grouped(rng, spec, lead, k, piv_leads, from_piv, which)
+
+    # Assemble: lead entry first, then the run entries (already sorted).
+    counts = np.bincount(rows, minlength=m).astype(np.int64) + 1
+    row_ptr = np.zeros(m + 1, np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    nnz = int(row_ptr[-1])
+    col = np.empty(nnz, np.int64)
+    col[row_ptr[:-1]] = lead
+    # run entries go after the lead of their row
+    rank_in_row = np.arange(len(rows), dtype=np.int64) - np.repeat(
+        np.concatenate([[0], np.cumsum(counts - 1)[:-1]]), counts - 1)
+    col[row_ptr[rows] + 1 + rank_in_row] = cols
+    val = rng.integers(1, p, size=nnz).astype(np.int64)
+    val[row_ptr[:npiv]] = 1                       # designated pivot rows are monic
+    # Shuffle rows.
+    perm = rng.permutation(m)
+    cnt = counts[perm]
+    new_ptr = np.zeros(m + 1, np.int64)
+    np.cumsum(cnt, out=new_ptr[1:])
+    src = np.repeat(row_ptr[perm], cnt) + (np.arange(nnz, dtype=np.int64) - np.repeat(new_ptr[:-1], cnt))
+    return new_ptr, col[src].astype(np.int32), val[src].astype(np.uint16)
+
+
+def _grouped(rng, spec, lead, k, piv_leads, from_piv, which):
+    """Run patterns shared inside groups of consecutive designated leads."""
+    n = spec.n
+    npiv = len(piv_leads)
+    m = len(lead)
+    gmin, gmax = spec.group
+    # Group ids over designated pivots (consecutive leads).
+    sizes = []
+    tot = 0
+    while tot < npiv:
+        s = int(rng.integers(gmin, gmax + 1))
+        sizes.append(s)
+        tot += s
+    gid_piv = np.repeat(np.arange(len(sizes)), sizes)[:npiv]
+    gfirst = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    ngroups = len(sizes)
+    # Non-pivot rows copying a pivot's pattern join its group; others get own patterns.
+    gid_np = np.where(from_piv, gid_piv[np.minimum(which, max(npiv - 1, 0))] if npiv else -1, -1)
+    gid = np.concatenate([gid_piv, gid_np]).astype(np.int64)
+    # Base pattern per group: drawn right of the group's first lead.
+    base_lead = piv_leads[gfirst] if npiv else np.zeros(0, np.int64)
+    base_k = np.minimum(_row_counts(rng, ngroups, spec.density, n, spec.spread) - 1, n - base_lead - 1)
+    b_rows, b_cols = _runs(rng, base_lead, base_k, n, spec.run_len)
+    b_ptr = np.zeros(ngroups + 1, np.int64)
+    np.cumsum(np.bincount(b_rows, minlength=ngroups), out=b_ptr[1:])
+    # Members: shifted base entries; keep each with probability `share`
+    # (run-granular keep via a per-entry draw on the run id), then top up with
+    # fresh runs to the member's own count.
+    member = np.nonzero(gid >= 0)[0]
+    g = gid[member]
+    shift = lead[member] - base_lead[g]
+    cnt = b_ptr[g + 1] - b_ptr[g]
+    e_row = np.repeat(member, cnt)
+    e_src = np.repeat(b_ptr[g], cnt) + (np.arange(int(cnt.sum()), dtype=np.int64) - np.repeat(
+        np.concatenate([[0], np.cumsum(cnt)[:-1]]), cnt))
+    e_col = b_cols[e_src] + np.repeat(shift, cnt)
+    # run id of each base entry: a new run starts where columns are not consecutive
+    brk = np.ones(len(b_cols), bool)
+    brk[1:] = (b_cols[1:] != b_cols[:-1] + 1) | (b_rows[1:] != b_rows[:-1])
+    run_id = np.cumsum(brk) - 1
+    keep_run = rng.random(int(run_id[-1]) + 1 if len(run_id) else 0) < spec.share
+    keep = (e_col > np.repeat(lead[member], cnt)) & (e_col < n) & keep_run[run_id[e_src]] if len(e_src) else np.zeros(0, bool)
+    e_row, e_col = e_row[keep], e_col[keep]
+    have = np.bincount(e_row, minlength=m)
+    # Fresh runs: rows outside groups get their whole count; members top up.
+    need = np.maximum(k - have, 0)
+    f_rows, f_cols = _runs(rng, lead, need, n, spec.run_len)
+    rows = np.concatenate([e_row, f_rows])
+    cols = np.concatenate([e_col, f_cols])
+    # Deduplicate and sort per row.
+    key = _sorted_unique(rows * (n + 1) + cols)
+    rows = key // (n + 1)
+    cols = key % (n + 1)
+    return rows.astype(np.int64), cols.astype(np.int64)
+
+
+# Named workloads (sizes from the F4 shape statistics quoted above).
+WORKLOADS = {
+    # 2,000 x 3,000, 1,200 pivots, 4% density, runs of 4-32: the small case.
+    "fl_2000x3000": FLSpec(m=2000, n=3000, npiv=1200, density=0.04, run_len=(4, 32), seed=20160219),
+    # 40,000 x 60,000, 30,000 pivots, 1.5% density, 2-8 runs per row,
+    # groups of 2-16 rows sharing ~80% of their pattern.
+    "fl_40000x60000": FLSpec(m=40000, n=60000, npiv=30000, density=0.015, run_len=(112, 450),
+                             group=(2, 16), share=0.8, seed=20160220),
+}
+
+
+def workload(name: str, **overrides):
+    spec = WORKLOADS[name]
+    if overrides:
+        spec = dataclasses.replace(spec, **overrides)
+    return spec
+
+
+def scaled(name: str, scale: float, seed: int | None = None) -> FLSpec:
+    """The named workload with rows, columns and pivots scaled by ``scale``."""
+    s = WORKLOADS[name]
+    m = max(2, int(round(s.m * scale)))
+    n = max(2, int(round(s.n * scale)))
+    npiv = max(1, min(m, n, int(round(s.npiv * scale))))
+    rl = (max(1, int(round(s.run_len[0] * min(1.0, scale * 4)))), max(1, int(round(s.run_len[1] * min(1.0, scale * 4)))))
+    return dataclasses.replace(s, m=m, n=n, npiv=npiv, run_len=(min(rl), max(rl)),
+                               seed=s.seed if seed is None else seed)
+
+
+def random_csr(rng, m, n, p, density):
+    """Unstructured random sparse matrix (for edge-case tests)."""
+    mask = rng.random((m, n)) < density
+    vals = rng.integers(1, p, size=(m, n))
+    dense = np.where(mask, vals, 0)
+    return dense_to_csr(dense)
+
+
+def dense_to_csr(dense):
+    dense = np.asarray(dense)
+    m, n = dense.shape
+    nzr, nzc = np.nonzero(dense)
+    row_ptr = np.zeros(m + 1, np.int64)
+    np.cumsum(np.bincount(nzr, minlength=m), out=row_ptr[1:])
+    return row_ptr, nzc.astype(np.int32), dense[nzr, nzc].astype(np.uint16)
+
+
+def csr_to_dense(m, n, row_ptr, col, val):
+    out = np.zeros((m, n), np.int64)
+    rows = np.repeat(np.arange(m), np.diff(row_ptr))
+    out[rows, np.asarray(col, np.int64)] = np.asarray(val, np.int64)
+    return out
