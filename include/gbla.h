@@ -1,0 +1,145 @@
+/*
+ * gbla.h -- C ABI of the GB300 (sm_103a) Faugere-Lachartre reduction.
+ *
+ * Problem (GBLA paper, arXiv 1602.06097, Sec. 3.1 and Sec. 4.1): M is an
+ * m x n matrix over GF(p), p a prime < 2^16, stored as CSR with uint16
+ * coefficients and int32 column indices, rows = polynomials, columns =
+ * monomials in decreasing monomial order (the layout of the paper's binary
+ * Format 1, Table 3).  The library returns either
+ *   - want_reduced = 1: the reduced row echelon form RREF(M) (FL steps 1-5 and
+ *     the second FL pass on the right block, Sec. 4.1), or
+ *   - want_reduced = 0: the echelon form of the new order of operations
+ *     (Alg. 2, Sec. 4.2): the chosen pivot rows of M normalised to a leading
+ *     1, plus the reduced echelon form of the Schur complement D - C A^-1 B.
+ * In both cases rows are sorted by pivot column (leftmost nonzero, always 1),
+ * zero rows are dropped, and columns are back in the input (monomial) order
+ * (FL step 5).  rank(M) = number of rows returned.  Pivot rows are chosen per
+ * leading column as the row with the fewest nonzeros, ties to the smaller row
+ * index (the paper's "keep A as sparse as possible", Sec. 3.1).
+ *
+ * All arithmetic is exact modular integer arithmetic.
+ *
+ * Threading: calls are independent; a call may run concurrently with others
+ * on different streams.  Errors are returned as codes, never thrown.
+ */
+#ifndef GBLA_H
+#define GBLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------- */
+#define GBLA_OK 0
+#define GBLA_E_INVAL 1       /* bad argument or malformed matrix (see gbla_csr_in) */
+#define GBLA_E_NOMEM 2       /* device or host allocation failed */
+#define GBLA_E_CUDA 3        /* a CUDA runtime/driver call failed */
+#define GBLA_E_TIMEOUT 4     /* a bounded device-side wait expired; the context stays usable */
+#define GBLA_E_INTERNAL 5    /* internal consistency check failed */
+#define GBLA_E_UNSUPPORTED 6 /* no sm_103a device, or an option this build cannot honour */
+
+/* ---- matrix types ---------------------------------------------------- */
+/* Input matrix, borrowed (never modified, never freed by the library).
+ * row_ptr[nrows+1] with row_ptr[0] = 0 and row_ptr[nrows] = nnz, monotone;
+ * col[nnz] strictly increasing inside each row, 0 <= col < ncols;
+ * val[nnz] in [1, p) (no explicit zeros).  Violations give GBLA_E_INVAL.
+ * The pointers are host pointers, or device pointers when
+ * gbla_options.device_ptrs = 1. */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const uint16_t *val;
+} gbla_csr_in;
+
+/* Result matrix, owned by the library; release with gbla_free().  nrows is
+ * the rank.  on_device = 1 when the arrays are device memory (requested with
+ * gbla_options.device_ptrs = 1), else host memory. */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    int64_t *row_ptr;
+    int32_t *col;
+    uint16_t *val;
+    int on_device;
+} gbla_csr_out;
+
+#define GBLA_GEMM_AUTO 0     /* tensor-core path where it applies */
+#define GBLA_GEMM_TCGEN05 1  /* bf16 8-bit digits on tcgen05.mma, fp32 TMEM accumulators */
+#define GBLA_GEMM_SIMT 2     /* exact int64 CUDA-core kernel (reference variant) */
+
+typedef struct {
+    int want_reduced;  /* 1: RREF(M); 0: echelon form of the new order */
+    int gemm_variant;  /* GBLA_GEMM_* for every dense modular product */
+    int device_ptrs;   /* 1: input and output arrays live on the device */
+    int panel_width;   /* column panel of the D echelonisation, 0 = default (128) */
+} gbla_options;
+
+/* Per-call statistics (optional out-parameter). */
+typedef struct {
+    int64_t npiv;      /* pivots known from the input (rows of A) */
+    int64_t m_cd;      /* non-pivot, non-empty rows (rows of C and D) */
+    int64_t n_d;       /* non-pivot columns (columns of B and D) */
+    int64_t rank_d;    /* rank of the Schur complement D' */
+    double ms_split, ms_trsm, ms_schur, ms_echelon, ms_backsub, ms_output, ms_total;
+    double mod_ops;    /* dense-equivalent modular multiply-adds executed */
+} gbla_stats;
+
+/* ---- whole reduction -------------------------------------------------- */
+/* Synchronous: host input, host output.  *rank receives the rank.  On error
+ * *out is zeroed. */
+int gbla_reduce(const gbla_csr_in *in, uint32_t p, int want_reduced,
+                gbla_csr_out *out, int64_t *rank);
+
+/* Extended form.  `stream` is a cudaStream_t (NULL = default stream).  The
+ * call enqueues its work on `stream` and synchronises it a few times to read
+ * sizes (pivot count, rank of D'); it returns once the result is complete.
+ * opt may be NULL (defaults).  stats may be NULL. */
+int gbla_reduce_ex(const gbla_csr_in *in, uint32_t p, const gbla_options *opt,
+                   void *stream, gbla_csr_out *out, int64_t *rank, gbla_stats *stats);
+
+/* Release a result (host or device arrays); zeroes *out.  NULL-safe. */
+void gbla_free(gbla_csr_out *out);
+
+/* Human-readable error text for a GBLA_* code (static storage). */
+const char *gbla_strerror(int code);
+
+/* ABI version (major*100 + minor). */
+int gbla_version(void);
+
+/* ---- building blocks, exposed for testing ----------------------------- */
+/* Modular matrix product on device memory (FL steps 2-3, the dense Schur
+ * update D <- D - C*A^-1*B of Sec. 4.1, done as an exact GEMM):
+ *     C <- (C + sign * A * B) mod p
+ * A: M x K, B: K x N, C: M x N, all row-major uint16 device arrays with
+ * leading dimensions lda, ldb, ldc (in elements), entries in [0, p).
+ * sign is +1 or -1.  variant is GBLA_GEMM_*.  Scratch is allocated on
+ * `stream` and released before return; the call synchronises `stream`. */
+int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t lda,
+                   const uint16_t *B, int64_t ldb, uint16_t *C, int64_t ldc,
+                   uint32_t p, int sign, int variant, void *stream);
+
+/* FL step 1 pivot analysis on device memory (Sec. 3.1, Sec. 4.1 step 1):
+ * validates the CSR (device pointers), and writes for every column c
+ * piv_row[c] = the input row chosen as pivot for c (-1 if no row leads at c).
+ * *npiv receives the number of pivots.  piv_row is a device array of ncols
+ * int64.  Synchronises `stream`. */
+int gbla_pivots(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev,
+                int64_t *npiv, void *stream);
+
+/* 2-multiline vector of pairs of pivot rows (Definition 1, Sec. 4.2), the
+ * layout the sparse reduction C <- C*A^-1 reads.  For a device CSR of 2*q
+ * rows (host pointers here, small inputs), fills for each pair of rows
+ * (2i, 2i+1): pos = union of their columns, ascending; val[2e], val[2e+1] =
+ * the two rows' values at pos[e] (0 where a row has none).  Output arrays are
+ * host arrays sized by the caller: ml_ptr[q+1], ml_pos[total], ml_val[2*total]
+ * where total <= nnz.  Returns GBLA_OK or an error. */
+int gbla_multiline(const gbla_csr_in *pairs_host, int64_t *ml_ptr, int32_t *ml_pos,
+                   uint16_t *ml_val, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBLA_H */

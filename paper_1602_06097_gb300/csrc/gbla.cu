@@ -1,0 +1,692 @@
+// gbla.cu -- C ABI entry points and the host orchestration of one reduction.
+//
+// One call runs the whole Faugere-Lachartre reduction (GBLA paper Sec. 4.1,
+// new order of Sec. 4.2) on the caller's stream:
+//   step 1  pivot analysis and split (split.cu)
+//   step 2' X = C * A^-1 by the blocked multiline solve (solve.cu)
+//   step 3' D <- D - X * B, exact tensor-core product (modgemm.cu)
+//   step 4  reduced echelon form of D' (solve.cu)
+//   (RREF)  Y = A^-1 * B, Y <- Y - Y[:, P_D] * RREF(D')   (second FL pass)
+//   step 5  output in the input column order, rows by pivot column.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "solve.cuh"
+#include "split.cuh"
+
+namespace gbla {
+
+static thread_local char g_last_err[512];
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what, file, line,
+             cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------- memory
+static std::once_flag g_pool_once;
+
+static void setup_pool() {
+    std::call_once(g_pool_once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;   // keep freed blocks for reuse by later calls
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+int dalloc(void **ptr, size_t bytes, cudaStream_t s) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(ptr, bytes, s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+        cudaGetLastError();
+        *ptr = nullptr;
+        return GBLA_E_NOMEM;
+    }
+    return GBLA_OK;
+}
+
+void dfree(void *ptr, cudaStream_t s) {
+    if (ptr) cudaFreeAsync(ptr, s);
+}
+
+int planes_alloc(Planes *pl, int64_t rows, int64_t k, int nplanes, cudaStream_t s) {
+    pl->rows = round_up(rows > 0 ? rows : 1, 128);
+    pl->kp = round_up(k > 0 ? k : 1, 128);
+    pl->nplanes = nplanes;
+    pl->ptr = nullptr;
+    return dalloc(reinterpret_cast<void **>(&pl->ptr), pl->plane_elems() * (size_t)nplanes * sizeof(__nv_bfloat16), s);
+}
+
+void planes_free(Planes *pl, cudaStream_t s) {
+    dfree(pl->ptr, s);
+    pl->ptr = nullptr;
+}
+
+static int planes_zero(const Planes &pl, cudaStream_t s) {
+    if (!pl.ptr) return GBLA_OK;
+    GBLA_CUDA_TRY(cudaMemsetAsync(pl.ptr, 0, pl.plane_elems() * (size_t)pl.nplanes * sizeof(__nv_bfloat16), s));
+    return GBLA_OK;
+}
+
+static bool is_prime(uint32_t p) {
+    if (p < 2) return false;
+    for (uint32_t d = 2; d * d <= p; ++d)
+        if (p % d == 0) return false;
+    return true;
+}
+
+static int check_device() {
+    int dev = 0, major = 0, minor = 0, n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return GBLA_E_UNSUPPORTED;
+    }
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return GBLA_E_UNSUPPORTED;   // built for sm_103a only
+    setup_pool();
+    return GBLA_OK;
+}
+
+static int map_dev_err(uint32_t e) {
+    if (e & DEV_ERR_TIMEOUT) return GBLA_E_TIMEOUT;
+    if (e & DEV_ERR_INVAL) return GBLA_E_INVAL;
+    if (e & DEV_ERR_INTERNAL) return GBLA_E_INTERNAL;
+    return GBLA_OK;
+}
+
+// ------------------------------------------------------- output assembly
+__global__ void mark_pivot_cols_kernel(int64_t npiv, const int32_t *__restrict__ pivcol_orig, int64_t *outflag) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < npiv) outflag[pivcol_orig[k]] = 1;
+}
+
+__global__ void mark_bottom_cols_kernel(int64_t rank_d, const int32_t *__restrict__ pcol,
+                                        const int32_t *__restrict__ npcol_orig, int64_t *outflag) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < rank_d) outflag[npcol_orig[pcol[k]]] = 1;
+}
+
+__device__ __forceinline__ int64_t warp_count_nz(const uint16_t *row, int64_t n, int lane) {
+    int64_t c = 0;
+    for (int64_t i = lane; i < n; i += 32) c += row[i] != 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    return c;
+}
+
+// counts of the top rows: echelon form = input row length; RREF = 1 + nnz(Y row)
+__global__ void top_counts_kernel(int64_t npiv, const int32_t *__restrict__ piv_row, const int32_t *__restrict__ pivcol_orig,
+                                  const int64_t *__restrict__ row_ptr, const uint16_t *__restrict__ Y, int64_t ldy,
+                                  int64_t n_d, const int64_t *__restrict__ outpos, int64_t *cnt) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= npiv) return;
+    int64_t c;
+    if (Y) c = 1 + warp_count_nz(Y + k * ldy, n_d, lane);
+    else c = row_ptr[piv_row[k] + 1] - row_ptr[piv_row[k]];
+    if (lane == 0) cnt[outpos[pivcol_orig[k]]] = c;
+}
+
+__global__ void bottom_counts_kernel(int64_t rank_d, const int32_t *__restrict__ prow, const int32_t *__restrict__ pcol,
+                                     const int32_t *__restrict__ npcol_orig, const uint16_t *__restrict__ D, int64_t ldd,
+                                     int64_t n_d, const int64_t *__restrict__ outpos, int64_t *cnt) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= rank_d) return;
+    const int64_t c = warp_count_nz(D + (int64_t)prow[k] * ldd, n_d, lane);
+    if (lane == 0) cnt[outpos[npcol_orig[pcol[k]]]] = c;
+}
+
+// Compact the nonzeros of a dense row (columns = permuted non-pivot indices,
+// increasing input columns) into (col, val) at out_off.
+__device__ __forceinline__ void warp_compact(const uint16_t *row, int64_t n, const int32_t *__restrict__ npcol_orig,
+                                             int32_t *ocol, uint16_t *oval, int64_t out_off, int lane) {
+    int64_t off = out_off;
+    for (int64_t base = 0; base < n; base += 32) {
+        const int64_t i = base + lane;
+        const uint16_t v = (i < n) ? row[i] : 0;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, v != 0);
+        if (v) {
+            const int64_t pos = off + __popc(bal & ((1u << lane) - 1u));
+            ocol[pos] = npcol_orig[i];
+            oval[pos] = v;
+        }
+        off += __popc(bal);
+    }
+}
+
+__global__ void top_fill_kernel(int64_t npiv, const int32_t *__restrict__ piv_row, const int32_t *__restrict__ pivcol_orig,
+                                const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                const uint16_t *__restrict__ val, const uint32_t *__restrict__ inv_lead,
+                                const uint16_t *__restrict__ Y, int64_t ldy, int64_t n_d,
+                                const int32_t *__restrict__ npcol_orig, const int64_t *__restrict__ outpos,
+                                const int64_t *__restrict__ orp, int32_t *ocol, uint16_t *oval, ModP mp) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= npiv) return;
+    const int64_t off = orp[outpos[pivcol_orig[k]]];
+    if (Y) {
+        if (lane == 0) {
+            ocol[off] = pivcol_orig[k];
+            oval[off] = 1;
+        }
+        warp_compact(Y + k * ldy, n_d, npcol_orig, ocol, oval, off + 1, lane);
+    } else {
+        const int64_t r = piv_row[k];
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        const uint32_t inv = inv_lead[k];
+        for (int64_t i = b + lane; i < e; i += 32) {
+            ocol[off + (i - b)] = col[i];
+            oval[off + (i - b)] = (uint16_t)mulmod(val[i], inv, mp);
+        }
+    }
+}
+
+__global__ void bottom_fill_kernel(int64_t rank_d, const int32_t *__restrict__ prow, const int32_t *__restrict__ pcol,
+                                   const int32_t *__restrict__ npcol_orig, const uint16_t *__restrict__ D, int64_t ldd,
+                                   int64_t n_d, const int64_t *__restrict__ outpos, const int64_t *__restrict__ orp,
+                                   int32_t *ocol, uint16_t *oval) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= rank_d) return;
+    const int64_t off = orp[outpos[npcol_orig[pcol[k]]]];
+    warp_compact(D + (int64_t)prow[k] * ldd, n_d, npcol_orig, ocol, oval, off, lane);
+}
+
+__global__ void transpose_u16_kernel(const uint16_t *__restrict__ src, int64_t lds, int64_t rows, int64_t cols,
+                                     uint16_t *__restrict__ dst, int64_t ldd) {
+    __shared__ uint16_t t[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) dst[c * ldd + r] = t[threadIdx.x][i];
+    }
+}
+
+// ------------------------------------------------------------ one call
+struct Timer {
+    cudaEvent_t ev[8];
+    int n = 0;
+    bool on = false;
+    void init(bool enable) {
+        on = enable;
+        if (on)
+            for (auto &e : ev) cudaEventCreate(&e);
+    }
+    void mark(cudaStream_t s) {
+        if (on && n < 8) cudaEventRecord(ev[n++], s);
+    }
+    double ms(int a, int b) {
+        float t = 0;
+        if (!on || b >= n) return 0;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+    ~Timer() {
+        if (on)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
+                       int64_t *rank_out, gbla_stats *stats) {
+    const int want_reduced = opt ? opt->want_reduced : 0;
+    const int variant = opt ? opt->gemm_variant : GBLA_GEMM_AUTO;
+    const int device_ptrs = opt ? opt->device_ptrs : 0;
+    if (variant < 0 || variant > GBLA_GEMM_SIMT) return GBLA_E_INVAL;
+    const int64_t m = in->nrows, n = in->ncols, nnz = in->nnz;
+    if (m < 0 || n < 0 || nnz < 0 || m >= (1ll << 31) || n >= (1ll << 31)) return GBLA_E_INVAL;
+    if (m > 0 && !in->row_ptr) return GBLA_E_INVAL;
+    if (nnz > 0 && (!in->col || !in->val)) return GBLA_E_INVAL;
+    GBLA_TRY(check_device());
+    const ModP mp = make_modp(p);
+    GemmCounters ctr;
+    Timer tm;
+    tm.init(stats != nullptr);
+    tm.mark(s);
+
+    // Everything below allocates from the stream-ordered pool; `cleanup`
+    // releases it on every path.
+    int rc = GBLA_OK;
+    uint32_t *err = nullptr;
+    int64_t *d_rp = nullptr;
+    int32_t *d_col = nullptr;
+    uint16_t *d_val = nullptr;
+    PivotInfo pi;
+    Multiline ml;
+    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{};
+    uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr;
+    int32_t *is_piv_row = nullptr, *prow = nullptr, *pcol = nullptr;
+    int64_t *outflag = nullptr, *outpos = nullptr, *cnt = nullptr, *orp = nullptr;
+    int32_t *ocol = nullptr;
+    uint16_t *oval = nullptr;
+    int64_t rank_d = 0, npiv = 0, m_cd = 0, n_d = 0, rank = 0, onnz = 0;
+    int64_t ldc = 0, ldd = 0, ldbt = 0;
+    DevCSR dc;
+
+#define STEP(expr)                 \
+    do {                           \
+        rc = (expr);               \
+        if (rc != GBLA_OK) goto cleanup; \
+    } while (0)
+#define CSTEP(expr)                                               \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) {                                  \
+            set_last_cuda_error(_e, #expr, __FILE__, __LINE__);   \
+            rc = GBLA_E_CUDA;                                     \
+            goto cleanup;                                         \
+        }                                                         \
+    } while (0)
+
+    STEP(dalloc_t(&err, 4, s));
+    CSTEP(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    if (device_ptrs) {
+        dc.row_ptr = in->row_ptr;
+        dc.col = in->col;
+        dc.val = in->val;
+    } else {
+        STEP(dalloc_t(&d_rp, (size_t)m + 1, s));
+        STEP(dalloc_t(&d_col, (size_t)nnz + 1, s));
+        STEP(dalloc_t(&d_val, (size_t)nnz + 1, s));
+        if (m > 0) CSTEP(cudaMemcpyAsync(d_rp, in->row_ptr, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyHostToDevice, s));
+        if (nnz > 0) {
+            CSTEP(cudaMemcpyAsync(d_col, in->col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+            CSTEP(cudaMemcpyAsync(d_val, in->val, sizeof(uint16_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+        }
+        dc.row_ptr = d_rp;
+        dc.col = d_col;
+        dc.val = d_val;
+    }
+    dc.m = m;
+    dc.n = n;
+    dc.nnz = nnz;
+
+    // ---- step 1: pivots and split
+    STEP(pivot_analysis(dc, mp, &pi, err, s));
+    npiv = pi.npiv;
+    m_cd = pi.m_cd;
+    n_d = pi.n_d;
+    ldc = round_up(npiv > 0 ? npiv : 1, 64);
+    ldd = round_up(n_d > 0 ? n_d : 1, 64);
+    ldbt = ldc;
+    if (m_cd > 0 && npiv > 0) {
+        STEP(planes_alloc(&At, npiv, npiv, 4, s));
+        STEP(planes_zero(At, s));
+    }
+    if (want_reduced && npiv > 0 && n_d > 0) {
+        STEP(planes_alloc(&Arow, npiv, npiv, 4, s));
+        STEP(planes_zero(Arow, s));
+        STEP(dalloc_t(&Bt16, (size_t)n_d * (size_t)ldbt, s));
+        CSTEP(cudaMemsetAsync(Bt16, 0, sizeof(uint16_t) * (size_t)n_d * (size_t)ldbt, s));
+    }
+    if (m_cd > 0 && n_d > 0 && npiv > 0) {
+        STEP(planes_alloc(&Bt, n_d, npiv, 4, s));
+        STEP(planes_zero(Bt, s));
+    }
+    STEP(dalloc_t(&C16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldc, s));
+    STEP(dalloc_t(&D16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldd, s));
+    if (m_cd > 0) {
+        CSTEP(cudaMemsetAsync(C16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldc, s));
+        CSTEP(cudaMemsetAsync(D16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldd, s));
+    }
+    STEP(split_scatter(dc, pi, At, Arow, Bt, Bt16, ldbt, C16, ldc, D16, ldd, mp, s));
+    STEP(multiline_build(dc, pi, &ml, mp, s));
+    tm.mark(s);  // 1
+
+    // ---- new order: X = C A^-1, then D <- D - X B
+    if (m_cd > 0 && npiv > 0) {
+        STEP(planes_alloc(&Xp, m_cd, npiv, 2, s));
+        STEP(planes_zero(Xp, s));
+        TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr};
+        STEP(trsm_upper(T));
+    }
+    tm.mark(s);  // 2
+    if (m_cd > 0 && npiv > 0 && n_d > 0)
+        STEP(modgemm(Xp, 0, 0, Bt, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr));
+    tm.mark(s);  // 3
+
+    // ---- step 4: RREF of D'
+    STEP(dalloc_t(&is_piv_row, (size_t)m_cd + 1, s));
+    STEP(dalloc_t(&prow, (size_t)m_cd + 1, s));
+    STEP(dalloc_t(&pcol, (size_t)m_cd + 1, s));
+    {
+        EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &mp, variant, err, s, &ctr};
+        STEP(echelon_d(E, &rank_d));
+    }
+    tm.mark(s);  // 4
+
+    // ---- second FL pass: Y = A^-1 B, then clear the columns P_D of Y
+    if (want_reduced && npiv > 0 && n_d > 0) {
+        STEP(planes_alloc(&Xq, n_d, npiv, 2, s));
+        STEP(planes_zero(Xq, s));
+        TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, variant, err, s, &ctr};
+        STEP(trsm_lower(T));
+        if (rank_d > 0) {
+            // Y^T[c][j] -= sum_k RREF(D')[k][c] * Y^T[P_D[k]][j]
+            STEP(planes_alloc(&RdT, n_d, rank_d, 2, s));
+            STEP(planes_alloc(&XpdT, npiv, rank_d, 4, s));
+            STEP(to_planes(RdT, n_d, rank_d, D16, ldd, 0, true, prow, nullptr, mp, s));
+            STEP(to_planes(XpdT, npiv, rank_d, Bt16, ldbt, 0, true, pcol, nullptr, mp, s));
+            STEP(modgemm(RdT, 0, 0, XpdT, 0, 0, Bt16, ldbt, n_d, npiv, rank_d, -1, mp, variant, err, s, &ctr));
+        }
+        STEP(dalloc_t(&Y16, (size_t)npiv * (size_t)ldd, s));
+        dim3 grid((unsigned)((npiv + 31) / 32), (unsigned)((n_d + 31) / 32));
+        transpose_u16_kernel<<<grid, dim3(32, 8), 0, s>>>(Bt16, ldbt, n_d, npiv, Y16, ldd);
+        CSTEP(cudaGetLastError());
+    } else if (want_reduced && npiv > 0) {
+        // no B block: the top rows are unit vectors
+        STEP(dalloc_t(&Y16, (size_t)npiv * (size_t)ldd, s));
+        CSTEP(cudaMemsetAsync(Y16, 0, sizeof(uint16_t) * (size_t)npiv * (size_t)ldd, s));
+    }
+    tm.mark(s);  // 5
+
+    // ---- step 5: output in input column order, rows sorted by pivot column
+    rank = npiv + rank_d;
+    STEP(dalloc_t(&outflag, (size_t)n + 1, s));
+    STEP(dalloc_t(&outpos, (size_t)n + 1, s));
+    STEP(dalloc_t(&cnt, (size_t)rank + 1, s));
+    STEP(dalloc_t(&orp, (size_t)rank + 2, s));
+    CSTEP(cudaMemsetAsync(outflag, 0, sizeof(int64_t) * (size_t)(n + 1), s));
+    if (npiv > 0) {
+        mark_pivot_cols_kernel<<<(unsigned)((npiv + 255) / 256), 256, 0, s>>>(npiv, pi.pivcol_orig, outflag);
+        CSTEP(cudaGetLastError());
+    }
+    if (rank_d > 0) {
+        mark_bottom_cols_kernel<<<(unsigned)((rank_d + 255) / 256), 256, 0, s>>>(rank_d, pcol, pi.npcol_orig, outflag);
+        CSTEP(cudaGetLastError());
+    }
+    STEP(scan_i64(outflag, outpos, n, nullptr, s));
+    if (npiv > 0) {
+        top_counts_kernel<<<(unsigned)((npiv * 32 + 255) / 256), 256, 0, s>>>(npiv, pi.piv_row, pi.pivcol_orig,
+                                                                            dc.row_ptr, Y16, ldd, n_d, outpos, cnt);
+        CSTEP(cudaGetLastError());
+    }
+    if (rank_d > 0) {
+        bottom_counts_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(rank_d, prow, pcol, pi.npcol_orig,
+                                                                                  D16, ldd, n_d, outpos, cnt);
+        CSTEP(cudaGetLastError());
+    }
+    STEP(scan_i64(cnt, orp, rank, orp + rank, s));
+    CSTEP(cudaMemcpyAsync(&onnz, orp + rank, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CSTEP(cudaStreamSynchronize(s));
+    STEP(dalloc_t(&ocol, (size_t)onnz + 1, s));
+    STEP(dalloc_t(&oval, (size_t)onnz + 1, s));
+    if (npiv > 0) {
+        top_fill_kernel<<<(unsigned)((npiv * 32 + 255) / 256), 256, 0, s>>>(
+            npiv, pi.piv_row, pi.pivcol_orig, dc.row_ptr, dc.col, dc.val, pi.inv_lead, Y16, ldd, n_d, pi.npcol_orig,
+            outpos, orp, ocol, oval, mp);
+        CSTEP(cudaGetLastError());
+    }
+    if (rank_d > 0) {
+        bottom_fill_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(
+            rank_d, prow, pcol, pi.npcol_orig, D16, ldd, n_d, outpos, orp, ocol, oval);
+        CSTEP(cudaGetLastError());
+    }
+    {
+        // results leave the pool: device results in plain device memory,
+        // host results in malloc'ed memory
+        out->nrows = rank;
+        out->ncols = n;
+        out->nnz = onnz;
+        if (device_ptrs) {
+            out->on_device = 1;
+            CSTEP(cudaMalloc(&out->row_ptr, sizeof(int64_t) * (size_t)(rank + 1)));
+            CSTEP(cudaMalloc(&out->col, sizeof(int32_t) * (size_t)(onnz + 1)));
+            CSTEP(cudaMalloc(&out->val, sizeof(uint16_t) * (size_t)(onnz + 1)));
+            CSTEP(cudaMemcpyAsync(out->row_ptr, orp, sizeof(int64_t) * (size_t)(rank + 1), cudaMemcpyDeviceToDevice, s));
+            if (onnz > 0) {
+                CSTEP(cudaMemcpyAsync(out->col, ocol, sizeof(int32_t) * (size_t)onnz, cudaMemcpyDeviceToDevice, s));
+                CSTEP(cudaMemcpyAsync(out->val, oval, sizeof(uint16_t) * (size_t)onnz, cudaMemcpyDeviceToDevice, s));
+            }
+        } else {
+            out->on_device = 0;
+            out->row_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(rank + 1));
+            out->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(onnz + 1));
+            out->val = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(onnz + 1));
+            if (!out->row_ptr || !out->col || !out->val) { rc = GBLA_E_NOMEM; goto cleanup; }
+            CSTEP(cudaMemcpyAsync(out->row_ptr, orp, sizeof(int64_t) * (size_t)(rank + 1), cudaMemcpyDeviceToHost, s));
+            if (onnz > 0) {
+                CSTEP(cudaMemcpyAsync(out->col, ocol, sizeof(int32_t) * (size_t)onnz, cudaMemcpyDeviceToHost, s));
+                CSTEP(cudaMemcpyAsync(out->val, oval, sizeof(uint16_t) * (size_t)onnz, cudaMemcpyDeviceToHost, s));
+            }
+        }
+    }
+    tm.mark(s);  // 6
+    CSTEP(cudaStreamSynchronize(s));
+    {
+        uint32_t herr = 0;
+        CSTEP(cudaMemcpy(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost));
+        rc = map_dev_err(herr);
+    }
+    if (rc == GBLA_OK) {
+        *rank_out = rank;
+        if (stats) {
+            stats->npiv = npiv;
+            stats->m_cd = m_cd;
+            stats->n_d = n_d;
+            stats->rank_d = rank_d;
+            stats->ms_split = tm.ms(0, 1);
+            stats->ms_trsm = tm.ms(1, 2);
+            stats->ms_schur = tm.ms(2, 3);
+            stats->ms_echelon = tm.ms(3, 4);
+            stats->ms_backsub = tm.ms(4, 5);
+            stats->ms_output = tm.ms(5, 6);
+            stats->ms_total = tm.ms(0, 6);
+            stats->mod_ops = ctr.mod_ops;
+        }
+    }
+
+cleanup:
+    dfree(err, s);
+    dfree(d_rp, s);
+    dfree(d_col, s);
+    dfree(d_val, s);
+    pivot_free(&pi, s);
+    multiline_free(&ml, s);
+    planes_free(&At, s);
+    planes_free(&Arow, s);
+    planes_free(&Bt, s);
+    planes_free(&Xp, s);
+    planes_free(&Xq, s);
+    planes_free(&RdT, s);
+    planes_free(&XpdT, s);
+    dfree(C16, s);
+    dfree(D16, s);
+    dfree(Bt16, s);
+    dfree(Y16, s);
+    dfree(is_piv_row, s);
+    dfree(prow, s);
+    dfree(pcol, s);
+    dfree(outflag, s);
+    dfree(outpos, s);
+    dfree(cnt, s);
+    dfree(orp, s);
+    dfree(ocol, s);
+    dfree(oval, s);
+    if (rc != GBLA_OK) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        gbla_free(out);
+    }
+#undef STEP
+#undef CSTEP
+    return rc;
+}
+
+__global__ void piv_row_out_kernel(int64_t n, const unsigned long long *__restrict__ best, int64_t *out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) out[c] = best[c] == ~0ull ? -1 : (int64_t)(best[c] & 0xFFFFFFFFull);
+}
+
+}  // namespace gbla
+
+// ==================================================================== ABI
+using namespace gbla;
+
+extern "C" {
+
+int gbla_version(void) { return 100; }
+
+const char *gbla_strerror(int code) {
+    switch (code) {
+        case GBLA_OK: return "ok";
+        case GBLA_E_INVAL: return "invalid argument or malformed matrix";
+        case GBLA_E_NOMEM: return "out of memory";
+        case GBLA_E_CUDA: return "CUDA error";
+        case GBLA_E_TIMEOUT: return "a bounded device wait expired";
+        case GBLA_E_INTERNAL: return "internal error";
+        case GBLA_E_UNSUPPORTED: return "unsupported device or option";
+        default: return "unknown error";
+    }
+}
+
+void gbla_free(gbla_csr_out *out) {
+    if (!out) return;
+    if (out->on_device) {
+        if (out->row_ptr) cudaFree(out->row_ptr);
+        if (out->col) cudaFree(out->col);
+        if (out->val) cudaFree(out->val);
+    } else {
+        free(out->row_ptr);
+        free(out->col);
+        free(out->val);
+    }
+    memset(out, 0, sizeof(*out));
+}
+
+int gbla_reduce_ex(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, void *stream, gbla_csr_out *out,
+                   int64_t *rank, gbla_stats *stats) {
+    if (!in || !out || !rank || p >= 65536u || !is_prime(p)) {
+        if (out) memset(out, 0, sizeof(*out));
+        return GBLA_E_INVAL;
+    }
+    memset(out, 0, sizeof(*out));
+    if (stats) memset(stats, 0, sizeof(*stats));
+    return reduce_impl(in, p, opt, (cudaStream_t)stream, out, rank, stats);
+}
+
+int gbla_reduce(const gbla_csr_in *in, uint32_t p, int want_reduced, gbla_csr_out *out, int64_t *rank) {
+    gbla_options o;
+    memset(&o, 0, sizeof(o));
+    o.want_reduced = want_reduced;
+    return gbla_reduce_ex(in, p, &o, nullptr, out, rank, nullptr);
+}
+
+int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb,
+                   uint16_t *C, int64_t ldc, uint32_t p, int sign, int variant, void *stream) {
+    if (M < 0 || N < 0 || K < 0 || p >= 65536u || !is_prime(p) || (sign != 1 && sign != -1)) return GBLA_E_INVAL;
+    if (variant < 0 || variant > GBLA_GEMM_SIMT) return GBLA_E_INVAL;
+    if (M == 0 || N == 0 || K == 0) return GBLA_OK;
+    if (!A || !B || !C || lda < K || ldb < N || ldc < N) return GBLA_E_INVAL;
+    GBLA_TRY(check_device());
+    cudaStream_t s = (cudaStream_t)stream;
+    const ModP mp = make_modp(p);
+    Planes Ap{}, Bp{};
+    uint32_t *err = nullptr;
+    int rc = GBLA_OK;
+    if ((rc = dalloc_t(&err, 4, s)) == GBLA_OK && (rc = planes_alloc(&Ap, M, K, 2, s)) == GBLA_OK &&
+        (rc = planes_alloc(&Bp, N, K, 4, s)) == GBLA_OK) {
+        cudaMemsetAsync(err, 0, 4, s);
+        rc = to_planes(Ap, M, K, A, lda, 0, false, nullptr, nullptr, mp, s);
+        if (rc == GBLA_OK) rc = to_planes(Bp, N, K, B, ldb, 0, true, nullptr, nullptr, mp, s);
+        if (rc == GBLA_OK) rc = modgemm(Ap, 0, 0, Bp, 0, 0, C, ldc, M, N, K, sign, mp, variant, err, s, nullptr);
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
+        uint32_t herr = 0;
+        if (rc == GBLA_OK && cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost) == cudaSuccess) rc = map_dev_err(herr);
+    }
+    planes_free(&Ap, s);
+    planes_free(&Bp, s);
+    dfree(err, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+int gbla_pivots(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev, int64_t *npiv, void *stream) {
+    if (!in_dev || !piv_row_dev || !npiv || p >= 65536u || !is_prime(p)) return GBLA_E_INVAL;
+    if (in_dev->nrows < 0 || in_dev->ncols < 0 || in_dev->nnz < 0) return GBLA_E_INVAL;
+    GBLA_TRY(check_device());
+    cudaStream_t s = (cudaStream_t)stream;
+    const ModP mp = make_modp(p);
+    DevCSR dc;
+    dc.m = in_dev->nrows;
+    dc.n = in_dev->ncols;
+    dc.nnz = in_dev->nnz;
+    dc.row_ptr = in_dev->row_ptr;
+    dc.col = in_dev->col;
+    dc.val = in_dev->val;
+    PivotInfo pi;
+    uint32_t *err = nullptr;
+    int rc = dalloc_t(&err, 4, s);
+    if (rc == GBLA_OK && cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK) rc = pivot_analysis(dc, mp, &pi, err, s);
+    if (rc == GBLA_OK && dc.n > 0) {
+        piv_row_out_kernel<<<(unsigned)((dc.n + 255) / 256), 256, 0, s>>>(dc.n, pi.best, piv_row_dev);
+        if (cudaGetLastError() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    if (rc == GBLA_OK) *npiv = pi.npiv;
+    pivot_free(&pi, s);
+    dfree(err, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == GBLA_OK) rc = GBLA_E_CUDA;
+    return rc;
+}
+
+int gbla_multiline(const gbla_csr_in *pairs_host, int64_t *ml_ptr, int32_t *ml_pos, uint16_t *ml_val, void *stream) {
+    if (!pairs_host || !ml_ptr || pairs_host->nrows < 0 || pairs_host->nnz < 0) return GBLA_E_INVAL;
+    GBLA_TRY(check_device());
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t m = pairs_host->nrows, nnz = pairs_host->nnz;
+    const int64_t npairs = (m + 1) / 2;
+    int64_t *rp = nullptr, *mp_ = nullptr;
+    int32_t *col = nullptr, *pos = nullptr;
+    uint16_t *val = nullptr, *mv = nullptr;
+    int64_t total = 0;
+    int rc = GBLA_OK;
+    if ((rc = dalloc_t(&rp, (size_t)m + 1, s)) || (rc = dalloc_t(&col, (size_t)nnz + 1, s)) ||
+        (rc = dalloc_t(&val, (size_t)nnz + 1, s)) || (rc = dalloc_t(&mp_, (size_t)npairs + 2, s)) ||
+        (rc = dalloc_t(&pos, (size_t)nnz + 1, s)) || (rc = dalloc_t(&mv, (size_t)2 * nnz + 2, s))) {
+    } else {
+        cudaMemcpyAsync(rp, pairs_host->row_ptr, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyHostToDevice, s);
+        if (nnz) {
+            cudaMemcpyAsync(col, pairs_host->col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(val, pairs_host->val, sizeof(uint16_t) * (size_t)nnz, cudaMemcpyHostToDevice, s);
+        }
+        rc = multiline_pairs(m, rp, col, val, mp_, pos, mv, &total, s);
+        if (rc == GBLA_OK) {
+            cudaMemcpyAsync(ml_ptr, mp_, sizeof(int64_t) * (size_t)(npairs + 1), cudaMemcpyDeviceToHost, s);
+            if (total) {
+                cudaMemcpyAsync(ml_pos, pos, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, s);
+                cudaMemcpyAsync(ml_val, mv, sizeof(uint16_t) * (size_t)(2 * total), cudaMemcpyDeviceToHost, s);
+            }
+            if (cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
+        }
+    }
+    dfree(rp, s);
+    dfree(col, s);
+    dfree(val, s);
+    dfree(mp_, s);
+    dfree(pos, s);
+    dfree(mv, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+}  // extern "C"

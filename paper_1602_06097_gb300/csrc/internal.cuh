@@ -1,0 +1,44 @@
+// internal.cuh -- host-side interfaces between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace gbla {
+
+struct GemmCounters {
+    double mod_ops = 0;      // dense modular multiply-adds issued (M*N*K summed)
+    long launches = 0;
+    long tc_launches = 0;
+};
+
+int device_sm_count();
+
+// C <- (C + sign * A * B^T) mod p, A an A-operand plane set (2 planes,
+// rows a_row0.., K from a_k0), B a B-operand plane set (4 planes, rows
+// b_row0.., K from b_k0).  K beyond the logical range must read zeros
+// (zero padding) when K is not a multiple of 64.
+int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
+            uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
+            uint32_t *err, cudaStream_t s, GemmCounters *ctr);
+
+// u16 -> digit planes (see modgemm.cu).
+int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds, int64_t col_off,
+              bool transposed, const int32_t *rgather, const int32_t *cgather, const ModP &mp, cudaStream_t s);
+
+// Stream-ordered device allocation helpers (memory pool of the device).
+int dalloc(void **ptr, size_t bytes, cudaStream_t s);
+void dfree(void *ptr, cudaStream_t s);
+
+template <typename T>
+inline int dalloc_t(T **ptr, size_t count, cudaStream_t s) {
+    return dalloc(reinterpret_cast<void **>(ptr), count * sizeof(T) + 16, s);
+}
+
+int planes_alloc(Planes *pl, int64_t rows, int64_t k, int nplanes, cudaStream_t s);
+void planes_free(Planes *pl, cudaStream_t s);
+
+// Exclusive prefix sum of n int64 values (in may equal out); *total_dev (a
+// device pointer, may be null) receives the sum.
+int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, cudaStream_t s);
+
+}  // namespace gbla

@@ -1,0 +1,686 @@
+// modgemm.cu -- exact modular matrix product C <- (C + sign * A * B) mod p.
+//
+// This is the dense Schur update of the FL reduction, D <- D - C*A^-1*B
+// (GBLA paper Sec. 4.1 steps 2-3; Sec. 4.2 step 4 of the new order), and the
+// block updates of the triangular solves and of the echelonisation of D.
+//
+// Tensor-core path (sm_103a).  Residues are written in balanced form and
+// split into two 8-bit digits that are exact in bf16 (common.cuh).  With
+// b' = 256*b mod p,
+//     a*b = (256*ah + al)*b == ah*b' + al*b
+//         == 256*(ah*b'h + al*bh) + (ah*b'l + al*bl)      (mod p),
+// so two fp32 accumulators P = sum(ah*b'h + al*bh) and Q = sum(ah*b'l + al*bl)
+// suffice.  Every digit product is at most 2^14 in magnitude and each k adds
+// two of them, so over a k-block of 512 every partial sum stays below 2^24 and
+// fp32 accumulation is exact whatever the order of additions.  After each
+// k-block the accumulators are drained from TMEM, reduced mod p and added to
+// a running residue kept in registers.  The kernel is a persistent,
+// warp-specialised tcgen05 pipeline: one thread issues TMA loads into a
+// 2-stage shared-memory ring, one thread issues tcgen05.mma into a
+// double-buffered TMEM accumulator pair, four warps drain TMEM.
+//
+// SIMT path: exact int64 dot products on CUDA cores, used as the reference
+// variant in tests and for p < 8.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdio.h>
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace gbla {
+
+// ===================================================================
+// u16 matrix -> digit planes
+// ===================================================================
+// dst(r, k), r < dst.rows, k < dst.kp:
+//   transposed == false : src[g(r) * lds + col_off + h(k)]
+//   transposed == true  : src[g(k) * lds + col_off + r]
+// with g = row gather (or identity), h = column gather (or identity); values
+// outside r < R, k < Kc are written as 0.
+template <bool TRANSPOSED>
+__global__ void to_planes_kernel(Planes dst, int64_t R, int64_t Kc, const uint16_t *__restrict__ src,
+                                 int64_t lds, int64_t col_off, const int32_t *__restrict__ rgather,
+                                 const int32_t *__restrict__ cgather, uint32_t p, uint32_t r256)
+{
+    __shared__ uint16_t tile[32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    if (TRANSPOSED) {
+        // read src rows g(k) for k in [k0, k0+32), columns col_off + r for r in [r0, r0+32)
+        for (int i = ty; i < 32; i += 8) {
+            int64_t k = k0 + i, r = r0 + tx;
+            uint16_t v = 0;
+            if (k < Kc && r < R) {
+                int64_t sr = rgather ? (int64_t)rgather[k] : k;
+                v = src[sr * lds + col_off + r];
+            }
+            tile[i][tx] = v;
+        }
+        __syncthreads();
+        for (int i = ty; i < 32; i += 8) {
+            int64_t r = r0 + i, k = k0 + tx;
+            uint32_t a = tile[tx][i];
+            int hi, lo;
+            digits(a, p, hi, lo);
+            size_t off = (size_t)r * (size_t)dst.kp + (size_t)k;
+            dst.plane(0)[off] = i2bf(hi);
+            dst.plane(1)[off] = i2bf(lo);
+            if (dst.nplanes == 4) {
+                uint32_t b2 = (a * r256) % p;
+                digits(b2, p, hi, lo);
+                dst.plane(2)[off] = i2bf(hi);
+                dst.plane(3)[off] = i2bf(lo);
+            }
+        }
+    } else {
+        for (int i = ty; i < 32; i += 8) {
+            int64_t r = r0 + i, k = k0 + tx;
+            uint32_t a = 0;
+            if (r < R && k < Kc) {
+                int64_t sr = rgather ? (int64_t)rgather[r] : r;
+                int64_t sc = cgather ? (int64_t)cgather[k] : k;
+                a = src[sr * lds + col_off + sc];
+            }
+            int hi, lo;
+            digits(a, p, hi, lo);
+            size_t off = (size_t)r * (size_t)dst.kp + (size_t)k;
+            dst.plane(0)[off] = i2bf(hi);
+            dst.plane(1)[off] = i2bf(lo);
+            if (dst.nplanes == 4) {
+                uint32_t b2 = (a * r256) % p;
+                digits(b2, p, hi, lo);
+                dst.plane(2)[off] = i2bf(hi);
+                dst.plane(3)[off] = i2bf(lo);
+            }
+        }
+    }
+}
+
+int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds,
+              int64_t col_off, bool transposed, const int32_t *rgather, const int32_t *cgather,
+              const ModP &mp, cudaStream_t s)
+{
+    if (dst.rows <= 0 || dst.kp <= 0) return GBLA_OK;
+    dim3 block(32, 8);
+    dim3 grid((unsigned)(dst.kp / 32), (unsigned)(dst.rows / 32));
+    if (transposed)
+        to_planes_kernel<true><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, mp.p, mp.r256);
+    else
+        to_planes_kernel<false><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, mp.p, mp.r256);
+    GBLA_CUDA_TRY(cudaGetLastError());
+    return GBLA_OK;
+}
+
+// ===================================================================
+// SIMT reference GEMM (exact int64)
+// ===================================================================
+__device__ __forceinline__ int bf2i(__nv_bfloat16 v) { return (int)__bfloat162float(v); }
+
+__global__ void __launch_bounds__(256) modgemm_simt_kernel(Planes A, int64_t a_row0, int64_t a_k0, Planes B,
+                                                           int64_t b_row0, int64_t b_k0, uint16_t *C, int64_t ldc,
+                                                           int64_t M, int64_t N, int64_t K, int sign, ModP mp)
+{
+    __shared__ int sa[64][33];
+    __shared__ int sb[64][33];
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;   // 16 x 16 threads, 4 x 4 outputs each
+    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    long long acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int64_t kk = 0; kk < K; kk += 32) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            int r = e / 32, k = e % 32;
+            int va = 0, vb = 0;
+            if (kk + k < K) {
+                if (m0 + r < M) {
+                    size_t off = (size_t)(a_row0 + m0 + r) * A.kp + (size_t)(a_k0 + kk + k);
+                    va = 256 * bf2i(A.plane(0)[off]) + bf2i(A.plane(1)[off]);
+                }
+                if (n0 + r < N) {
+                    size_t off = (size_t)(b_row0 + n0 + r) * B.kp + (size_t)(b_k0 + kk + k);
+                    vb = 256 * bf2i(B.plane(0)[off]) + bf2i(B.plane(1)[off]);
+                }
+            }
+            sa[r][k] = va;
+            sb[r][k] = vb;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            int a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sa[tr * 4 + i][k];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = sb[tc * 4 + j][k];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += (long long)a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    const long long P = mp.p;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t r = m0 + tr * 4 + i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t c = n0 + tc * 4 + j;
+            if (c >= N) continue;
+            long long v = acc[i][j] % P;
+            if (v < 0) v += P;
+            long long cur = C[r * ldc + c];
+            long long o = sign > 0 ? (cur + v) % P : (cur - v + P) % P;
+            C[r * ldc + c] = (uint16_t)o;
+        }
+    }
+}
+
+// ===================================================================
+// tcgen05 / TMA GEMM
+// ===================================================================
+namespace tc {
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int STAGES = 2;
+constexpr int KSTEPS_PER_BLOCK = 8;                 // k-block of 512: exact fp32 sums
+constexpr int TILE_BYTES = BM * BK * 2;             // 16 KiB (A and B tiles are 128 rows)
+constexpr int STAGE_BYTES = 6 * TILE_BYTES;         // Ah Al | Bh Bl B'h B'l
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr uint32_t TMEM_COLS = 512;                 // 2 buffers x (P 128 + Q 128)
+constexpr float MAGIC = 12582912.0f;                // 1.5 * 2^23
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000ll;  // ~1 s
+
+struct Args {
+    int64_t M, N, K;
+    int32_t a_row0, a_k0, a_rows;   // a_rows = padded rows per A plane
+    int32_t b_row0, b_k0, b_rows;
+    uint16_t *C;
+    int64_t ldc;
+    int sign;
+    uint32_t p;
+    float pf, pinv;
+    uint32_t *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: returns false (and raises the abort flag and the timeout
+// bit) if the phase does not complete within WAIT_LIMIT_CYCLES, or if
+// another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, uint32_t *err) {
+    const uint32_t addr = smem_u32(bar);
+    long long start = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(addr, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag) return false;
+            long long now = clock64();
+            if (start == 0) start = now;
+            else if (now - start > WAIT_LIMIT_CYCLES) {
+                *abort_flag = 1;
+                dev_fail(err, DEV_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tcgen05_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tcgen05_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tcgen05_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile of 128 rows x 64 bf16
+// (128-byte rows) loaded by TMA with 128-byte swizzle.  8-row swizzle atoms
+// are 1024 bytes apart (stride byte offset); the leading byte offset is unused
+// for swizzled K-major tiles.  Layout type 2 = 128-byte swizzle; bit 46 is the
+// fixed descriptor version of sm_100-family tcgen05.
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (16 B, unused)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = f32, A = B = bf16, both K-major,
+// N = 128, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// x an exact integer in fp32 with |x| <= 2^24 and p >= 8: returns an exact
+// integer r == x (mod p) with |r| <= 5p/8.  q = round(x * (1/p)) is formed by
+// one fused multiply-add into the 2^23 rounding window; the error of the
+// rounded reciprocal moves x/p by at most 1/8.
+__device__ __forceinline__ float fred(float x, float pf, float pinv) {
+    float q = fmaf(x, pinv, MAGIC) - MAGIC;
+    return fmaf(-q, pf, x);
+}
+
+__device__ __forceinline__ int f2i_small(float r) {  // exact integer |r| < 2^22
+    return __float_as_int(r + MAGIC) - 0x4B400000;
+}
+
+__device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t num_n, int64_t &mt, int64_t &nt) {
+    const int64_t GM = 8;
+    int64_t group = t / (GM * num_n);
+    int64_t first_m = group * GM;
+    int64_t gm = num_m - first_m < GM ? num_m - first_m : GM;
+    int64_t in = t % (GM * num_n);
+    mt = first_m + in % gm;
+    nt = in / gm;
+}
+
+__global__ void __launch_bounds__(192, 1)
+    modgemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + STAGES * STAGE_BYTES);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + STAGES;
+    uint64_t *accf = bars + 2 * STAGES;
+    uint64_t *acce = accf + 2;
+    uint64_t *done = acce + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    }
+    tcgen05_fence_before();
+    __syncthreads();
+    tcgen05_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
+    const int64_t num_tiles = num_m * num_n;
+    const int ksteps = (int)((g.K + BK - 1) / BK);
+    const int kblocks = (ksteps + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[STAGES];
+            uint32_t issued_parity[STAGES];
+            for (int s = 0; s < STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                int64_t mt, nt;
+                tile_coords(t, num_m, num_n, mt, nt);
+                const int ay = g.a_row0 + (int)(mt * BM), by = g.b_row0 + (int)(nt * BN);
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                    uint8_t *st = tiles + stage * STAGE_BYTES;
+                    mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    const int ax = g.a_k0 + ks * BK, bx = g.b_k0 + ks * BK;
+                    tma_load_2d(st + 0 * TILE_BYTES, &tmA, &full[stage], ax, ay);
+                    tma_load_2d(st + 1 * TILE_BYTES, &tmA, &full[stage], ax, ay + g.a_rows);
+                    tma_load_2d(st + 2 * TILE_BYTES, &tmB, &full[stage], bx, by);
+                    tma_load_2d(st + 3 * TILE_BYTES, &tmB, &full[stage], bx, by + g.b_rows);
+                    tma_load_2d(st + 4 * TILE_BYTES, &tmB, &full[stage], bx, by + 2 * g.b_rows);
+                    tma_load_2d(st + 5 * TILE_BYTES, &tmB, &full[stage], bx, by + 3 * g.b_rows);
+                    issued[stage] = 1;
+                    issued_parity[stage] = phase;
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+            }
+            // Never leave with copies in flight: wait (bounded) for the last
+            // load issued into every stage.
+            for (int s = 0; s < STAGES; ++s) {
+                if (!issued[s]) continue;
+                const uint32_t addr = smem_u32(&full[s]);
+                long long start = clock64();
+                while (!mbar_try_wait(addr, issued_parity[s])) {
+                    if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                        dev_fail(g.err, DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t kbc = 0;
+            bool ok = true;
+            const uint32_t tiles_base = smem_u32(tiles);
+            for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                for (int kb = 0; kb < kblocks && ok; ++kb, ++kbc) {
+                    const uint32_t buf = kbc & 1u, use = kbc >> 1;
+                    if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                    tcgen05_fence_after();
+                    const uint32_t dP = tmem + buf * 256u, dQ = dP + 128u;
+                    const int ks_end = min(ksteps, (kb + 1) * KSTEPS_PER_BLOCK);
+                    for (int ks = kb * KSTEPS_PER_BLOCK; ks < ks_end; ++ks) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, g.err)) { ok = false; break; }
+                        tcgen05_fence_after();
+                        const uint32_t sb = tiles_base + stage * STAGE_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint32_t ko = kk * 32;  // 16 bf16 = 32 bytes along K
+                            const uint64_t ah = make_sdesc(sb + 0 * TILE_BYTES + ko);
+                            const uint64_t al = make_sdesc(sb + 1 * TILE_BYTES + ko);
+                            const uint64_t bh = make_sdesc(sb + 2 * TILE_BYTES + ko);
+                            const uint64_t bl = make_sdesc(sb + 3 * TILE_BYTES + ko);
+                            const uint64_t b2h = make_sdesc(sb + 4 * TILE_BYTES + ko);
+                            const uint64_t b2l = make_sdesc(sb + 5 * TILE_BYTES + ko);
+                            const uint32_t acc0 = (ks > kb * KSTEPS_PER_BLOCK || kk > 0) ? 1u : 0u;
+                            mma_bf16(dP, ah, b2h, acc0);
+                            mma_bf16(dP, al, bh, 1u);
+                            mma_bf16(dQ, ah, b2l, acc0);
+                            mma_bf16(dQ, al, bl, 1u);
+                        }
+                        tcgen05_commit(&empty[stage]);
+                        if (++stage == STAGES) stage = 0, phase ^= 1u;
+                    }
+                    tcgen05_commit(&accf[buf]);
+                }
+            }
+            // Wait (bounded) until every issued MMA has completed before the
+            // accumulators are released.
+            tcgen05_commit(done);
+            const uint32_t addr = smem_u32(done);
+            long long start = clock64();
+            while (!mbar_try_wait(addr, 0)) {
+                if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                    dev_fail(g.err, DEV_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+        const int quarter = warp & 3;
+        const int row_in_tile = quarter * 32 + lane;
+        const float pf = g.pf, pinv = g.pinv;
+        const int P = (int)g.p;
+        uint32_t kbc = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            int64_t mt, nt;
+            tile_coords(t, num_m, num_n, mt, nt);
+            uint32_t run[BN / 2];
+#pragma unroll
+            for (int i = 0; i < BN / 2; ++i) run[i] = 0;
+            for (int kb = 0; kb < kblocks; ++kb, ++kbc) {
+                const uint32_t buf = kbc & 1u, use = kbc >> 1;
+                if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
+                tcgen05_fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * 256u;
+#pragma unroll
+                for (int c = 0; c < BN / 16; ++c) {
+                    float pv[16], qv[16];
+                    tmem_ld16(tbase + c * 16, pv);
+                    tmem_ld16(tbase + 128 + c * 16, qv);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        uint32_t pair = run[c * 8 + j / 2];
+                        int lo16 = (int)(pair & 0xFFFFu), hi16 = (int)(pair >> 16);
+                        {
+                            float v = fmaf(256.0f, fred(pv[j], pf, pinv), fred(qv[j], pf, pinv));
+                            int s = lo16 + f2i_small(fred(v, pf, pinv));
+                            s += (s < 0) ? P : 0;
+                            s -= (s >= P) ? P : 0;
+                            lo16 = s;
+                        }
+                        {
+                            float v = fmaf(256.0f, fred(pv[j + 1], pf, pinv), fred(qv[j + 1], pf, pinv));
+                            int s = hi16 + f2i_small(fred(v, pf, pinv));
+                            s += (s < 0) ? P : 0;
+                            s -= (s >= P) ? P : 0;
+                            hi16 = s;
+                        }
+                        run[c * 8 + j / 2] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
+                    }
+                }
+                tcgen05_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[buf]);
+            }
+            if (!ok) break;
+            // C <- (C + sign * run) mod p for this thread's row.
+            const int64_t row = mt * BM + row_in_tile;
+            const int64_t col0 = nt * BN;
+            if (row < g.M) {
+                uint16_t *crow = g.C + row * g.ldc + col0;
+                const bool vec = (col0 + BN <= g.N) && ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
+                if (vec) {
+#pragma unroll
+                    for (int v = 0; v < BN / 8; ++v) {
+                        uint4 cur = reinterpret_cast<const uint4 *>(crow)[v];
+                        uint32_t w[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            uint32_t rr = run[v * 4 + e];
+                            int c0 = (int)(w[e] & 0xFFFFu), c1 = (int)(w[e] >> 16);
+                            int r0 = (int)(rr & 0xFFFFu), r1 = (int)(rr >> 16);
+                            int o0 = g.sign > 0 ? c0 + r0 : c0 - r0;
+                            int o1 = g.sign > 0 ? c1 + r1 : c1 - r1;
+                            o0 += (o0 < 0) ? P : 0; o0 -= (o0 >= P) ? P : 0;
+                            o1 += (o1 < 0) ? P : 0; o1 -= (o1 >= P) ? P : 0;
+                            w[e] = (uint32_t)o0 | ((uint32_t)o1 << 16);
+                        }
+                        reinterpret_cast<uint4 *>(crow)[v] = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < BN; ++j) {
+                        if (col0 + j < g.N) {
+                            int r = (int)((run[j / 2] >> ((j & 1) * 16)) & 0xFFFFu);
+                            int cc = (int)crow[j];
+                            int o = g.sign > 0 ? cc + r : cc - r;
+                            o += (o < 0) ? P : 0;
+                            o -= (o >= P) ? P : 0;
+                            crow[j] = (uint16_t)o;
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    tcgen05_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tcgen05_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+}  // namespace tc
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static int get_encode() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode ? GBLA_OK : GBLA_E_UNSUPPORTED;
+}
+
+static int make_map(CUtensorMap *map, const Planes &pl) {
+    GBLA_TRY(get_encode());
+    cuuint64_t dims[2] = {(cuuint64_t)pl.kp, (cuuint64_t)pl.rows * (cuuint64_t)pl.nplanes};
+    cuuint64_t strides[1] = {(cuuint64_t)pl.kp * 2};
+    cuuint32_t box[2] = {tc::BK, tc::BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)pl.ptr, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GBLA_OK : GBLA_E_CUDA;
+}
+
+int device_sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+static bool tc_supported() {
+    static int ok = -1;
+    if (ok < 0) {
+        int dev = 0, major = 0, minor = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        ok = (major == 10 && minor == 3) ? 1 : 0;
+    }
+    return ok == 1;
+}
+
+int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
+            uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
+            uint32_t *err, cudaStream_t s, GemmCounters *ctr)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return GBLA_OK;
+    if (variant == GBLA_GEMM_AUTO) variant = (mp.p >= 8 && tc_supported()) ? GBLA_GEMM_TCGEN05 : GBLA_GEMM_SIMT;
+    if (ctr) {
+        ctr->launches += 1;
+        ctr->mod_ops += (double)M * (double)N * (double)K;
+    }
+    if (variant == GBLA_GEMM_SIMT) {
+        dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+        modgemm_simt_kernel<<<grid, 256, 0, s>>>(A, a_row0, a_k0, B, b_row0, b_k0, C, ldc, M, N, K, sign, mp);
+        GBLA_CUDA_TRY(cudaGetLastError());
+        return GBLA_OK;
+    }
+    if (variant != GBLA_GEMM_TCGEN05) return GBLA_E_INVAL;
+    if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
+    if (A.nplanes != 2 || B.nplanes != 4) return GBLA_E_INTERNAL;
+    if ((a_k0 % tc::BK) || (b_k0 % tc::BK)) return GBLA_E_INTERNAL;
+    CUtensorMap ma, mb;
+    GBLA_TRY(make_map(&ma, A));
+    GBLA_TRY(make_map(&mb, B));
+    static bool attr = false;
+    if (!attr) {
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           tc::SMEM_BYTES));
+        attr = true;
+    }
+    tc::Args g;
+    g.M = M; g.N = N; g.K = K;
+    g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0; g.a_rows = (int32_t)A.rows;
+    g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0; g.b_rows = (int32_t)B.rows;
+    g.C = C; g.ldc = ldc; g.sign = sign;
+    g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+    g.err = err;
+    const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
+    const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+    tc::modgemm_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    GBLA_CUDA_TRY(cudaGetLastError());
+    if (ctr) ctr->tc_launches += 1;
+    return GBLA_OK;
+}
+
+}  // namespace gbla

@@ -1,0 +1,59 @@
+// solve.cuh -- triangular solves and the echelonisation of D.
+#pragma once
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "split.cuh"
+
+namespace gbla {
+
+// X * A = C (A unit upper triangular, npiv x npiv), X overwrites C.
+struct TrsmUpper {
+    int64_t mrows, npiv;
+    uint16_t *C16;
+    int64_t ldc;
+    const Multiline *ml;   // A rows, 2-multiline
+    const Planes *Xp;      // A-operand planes of X (mrows x npiv), written here
+    const Planes *At;      // B-operand planes of A^T (npiv x npiv)
+    const ModP *mp;
+    int variant;
+    uint32_t *err;
+    cudaStream_t s;
+    GemmCounters *ctr;
+};
+int trsm_upper(const TrsmUpper &T);
+
+// X' * A^T = C' (A^T unit lower triangular), X' overwrites C'.
+struct TrsmLower {
+    int64_t mrows, npiv;
+    uint16_t *C16;
+    int64_t ldc;
+    const Multiline *ml;
+    const Planes *Xp;      // A-operand planes of X' (mrows x npiv), written here
+    const Planes *Arow;    // B-operand planes of A (npiv x npiv, row-major A)
+    const ModP *mp;
+    int variant;
+    uint32_t *err;
+    cudaStream_t s;
+    GemmCounters *ctr;
+};
+int trsm_lower(const TrsmLower &T);
+
+// Reduced echelon form of D (m x n, uint16, in place).  On return rows
+// prow[0..rank) of D are the RREF rows, with pivot columns pcol[0..rank)
+// ascending; every other row of D is zero.
+struct EchelonD {
+    int64_t m, n;
+    uint16_t *D16;
+    int64_t ldd;
+    int32_t *is_piv_row;   // [m] scratch
+    int32_t *prow, *pcol;  // [m] outputs
+    const ModP *mp;
+    int variant;
+    uint32_t *err;
+    cudaStream_t s;
+    GemmCounters *ctr;
+};
+int echelon_d(const EchelonD &E, int64_t *rank_out);
+
+}  // namespace gbla

@@ -1,0 +1,56 @@
+// split.cuh -- device data of FL step 1 (pivot analysis and splicing).
+#pragma once
+
+#include "common.cuh"
+
+namespace gbla {
+
+// A CSR matrix in device memory.
+struct DevCSR {
+    int64_t m = 0, n = 0, nnz = 0;
+    const int64_t *row_ptr = nullptr;
+    const int32_t *col = nullptr;
+    const uint16_t *val = nullptr;
+};
+
+// Result of the pivot analysis.  Permuted column order: the npiv pivot
+// columns ascending, then the n_d other columns ascending.  Row k of A/B is
+// input row piv_row[k]; row i of C/D is input row cd_rows[i].
+struct PivotInfo {
+    int64_t m = 0, n = 0, npiv = 0, m_cd = 0, n_d = 0;
+    int32_t *lead = nullptr;                 // [m] leading column or -1
+    unsigned long long *best = nullptr;      // [n] (weight << 32 | row) of the chosen pivot, or ~0
+    int64_t *dev_counts = nullptr;           // [2] npiv, m_cd on the device
+    int32_t *colmap = nullptr;               // [n] input column -> permuted index
+    int32_t *pivcol_orig = nullptr;          // [npiv] permuted pivot column -> input column
+    int32_t *npcol_orig = nullptr;           // [n_d] permuted other column -> input column
+    int32_t *piv_row = nullptr;              // [npiv] row of A -> input row
+    int32_t *cd_rows = nullptr;              // [m_cd] row of C/D -> input row
+    int32_t *cd_index = nullptr;             // [m] input row -> row of C/D or -1
+    uint32_t *inv_lead = nullptr;            // [npiv] inverse of the pivot row's leading coefficient
+};
+
+// 2-multiline storage of A (Definition 1): pair q = A rows 2q, 2q+1, entries
+// at permuted pivot columns excluding each row's unit diagonal.  val packs
+// row 2q's value in the low 16 bits and row 2q+1's in the high 16 bits.
+struct Multiline {
+    int64_t npairs = 0, total = 0;
+    int64_t *ptr = nullptr;    // [npairs + 1]
+    int32_t *pos = nullptr;    // [total]
+    uint32_t *val = nullptr;   // [total]
+};
+
+int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *err, cudaStream_t s);
+void pivot_free(PivotInfo *pi, cudaStream_t s);
+
+int split_scatter(const DevCSR &in, const PivotInfo &pi, const Planes &At, const Planes &Arow, const Planes &Bt,
+                  uint16_t *Bt16, int64_t ldbt16, uint16_t *C16, int64_t ldc, uint16_t *D16, int64_t ldd,
+                  const ModP &mp, cudaStream_t s);
+
+int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const ModP &mp, cudaStream_t s);
+void multiline_free(Multiline *ml, cudaStream_t s);
+
+int multiline_pairs(int64_t m, const int64_t *row_ptr, const int32_t *col, const uint16_t *val, int64_t *ml_ptr_dev,
+                    int32_t *ml_pos_dev, uint16_t *ml_val_dev, int64_t *total, cudaStream_t s);
+
+}  // namespace gbla

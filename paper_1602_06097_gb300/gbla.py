@@ -1,0 +1,245 @@
+"""Thin ctypes binding over the C ABI in ``include/gbla.h``.
+
+Argument marshalling only: every step of the reduction runs in the CUDA
+library ``libgbla.so``.  The library is loaded on first use and there is no
+fallback: if it is missing or fails to load, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbla.so")
+
+GBLA_OK = 0
+GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT = 0, 1, 2
+
+EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
+           "gbla_modmatmul", "gbla_pivots", "gbla_multiline"]
+
+
+class CsrIn(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class CsrOut(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("on_device", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("want_reduced", ctypes.c_int), ("gemm_variant", ctypes.c_int),
+                ("device_ptrs", ctypes.c_int), ("panel_width", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("npiv", ctypes.c_int64), ("m_cd", ctypes.c_int64), ("n_d", ctypes.c_int64),
+                ("rank_d", ctypes.c_int64), ("ms_split", ctypes.c_double), ("ms_trsm", ctypes.c_double),
+                ("ms_schur", ctypes.c_double), ("ms_echelon", ctypes.c_double),
+                ("ms_backsub", ctypes.c_double), ("ms_output", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("mod_ops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class GblaError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Open libgbla.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgbla.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, u32, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int
+        lib.gbla_reduce.argtypes = [ctypes.POINTER(CsrIn), u32, i32, ctypes.POINTER(CsrOut), ctypes.POINTER(i64)]
+        lib.gbla_reduce.restype = i32
+        lib.gbla_reduce_ex.argtypes = [ctypes.POINTER(CsrIn), u32, ctypes.POINTER(Options), vp,
+                                       ctypes.POINTER(CsrOut), ctypes.POINTER(i64), ctypes.POINTER(Stats)]
+        lib.gbla_reduce_ex.restype = i32
+        lib.gbla_free.argtypes = [ctypes.POINTER(CsrOut)]
+        lib.gbla_free.restype = None
+        lib.gbla_strerror.argtypes = [i32]
+        lib.gbla_strerror.restype = ctypes.c_char_p
+        lib.gbla_version.argtypes = []
+        lib.gbla_version.restype = i32
+        lib.gbla_modmatmul.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, u32, i32, i32, vp]
+        lib.gbla_modmatmul.restype = i32
+        lib.gbla_pivots.argtypes = [ctypes.POINTER(CsrIn), u32, vp, ctypes.POINTER(i64), vp]
+        lib.gbla_pivots.restype = i32
+        lib.gbla_multiline.argtypes = [ctypes.POINTER(CsrIn), vp, vp, vp, vp]
+        lib.gbla_multiline.restype = i32
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().gbla_strerror(code).decode()
+    except Exception:  # library missing: still give a message
+        return "error"
+
+
+def _check(rc, what):
+    if rc != GBLA_OK:
+        raise GblaError(rc, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None):
+    """Reduce a host CSR matrix.  Returns (rank, row_ptr, col, val) as numpy
+    arrays (and a stats dict when ``stats``)."""
+    lib = load()
+    m, n = int(shape[0]), int(shape[1])
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.uint16)
+    cin = CsrIn(m, n, int(len(col)), row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data)
+    opt = Options(1 if want_reduced else 0, int(variant), 0, 0)
+    out = CsrOut()
+    rank = ctypes.c_int64(0)
+    st = Stats()
+    rc = lib.gbla_reduce_ex(ctypes.byref(cin), int(p), ctypes.byref(opt), _stream_ptr(stream),
+                            ctypes.byref(out), ctypes.byref(rank), ctypes.byref(st))
+    _check(rc, "gbla_reduce_ex")
+    try:
+        r = int(out.nrows)
+        onnz = int(out.nnz)
+        orp = np.ctypeslib.as_array(ctypes.cast(out.row_ptr, ctypes.POINTER(ctypes.c_int64)), shape=(r + 1,)).copy()
+        if onnz:
+            oc = np.ctypeslib.as_array(ctypes.cast(out.col, ctypes.POINTER(ctypes.c_int32)), shape=(onnz,)).copy()
+            ov = np.ctypeslib.as_array(ctypes.cast(out.val, ctypes.POINTER(ctypes.c_uint16)), shape=(onnz,)).copy()
+        else:
+            oc = np.zeros(0, np.int32)
+            ov = np.zeros(0, np.uint16)
+    finally:
+        lib.gbla_free(ctypes.byref(out))
+    res = (int(rank.value), orp, oc, ov)
+    return res + (st.as_dict(),) if stats else res
+
+
+class DeviceResult:
+    """A result left in device memory (owned by the library until free())."""
+
+    def __init__(self, out: CsrOut, rank: int, stats: dict):
+        self._out = out
+        self.rank = rank
+        self.nnz = int(out.nnz)
+        self.stats = stats
+
+    def tensors(self):
+        """Zero-copy torch views (row_ptr, col, val) of the device arrays;
+        valid until free()."""
+        import torch
+        r, nnz = self.rank, self.nnz
+        rp = torch.as_tensor(_CudaArray(self._out.row_ptr, (r + 1,), "<i8"), device="cuda")
+        oc = torch.as_tensor(_CudaArray(self._out.col, (nnz,), "<i4"), device="cuda")
+        ov = torch.as_tensor(_CudaArray(self._out.val, (nnz,), "<i2"), device="cuda")
+        return rp, oc, ov
+
+    def to_host(self):
+        rp, oc, ov = self.tensors()
+        return (self.rank, rp.cpu().numpy(), oc.cpu().numpy(),
+                ov.cpu().numpy().view(np.uint16))
+
+    def free(self):
+        if self._out is not None:
+            load().gbla_free(ctypes.byref(self._out))
+            self._out = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ over a raw device pointer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None):
+    """Reduce a CSR matrix already on the device (torch CUDA tensors: int64
+    row_ptr, int32 col, int16/uint16 val).  Returns a DeviceResult whose
+    arrays stay in device memory."""
+    lib = load()
+    m, n = int(shape[0]), int(shape[1])
+    cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    opt = Options(1 if want_reduced else 0, int(variant), 1, 0)
+    out = CsrOut()
+    rank = ctypes.c_int64(0)
+    st = Stats()
+    rc = lib.gbla_reduce_ex(ctypes.byref(cin), int(p), ctypes.byref(opt), _stream_ptr(stream),
+                            ctypes.byref(out), ctypes.byref(rank), ctypes.byref(st))
+    _check(rc, "gbla_reduce_ex")
+    return DeviceResult(out, int(rank.value), st.as_dict())
+
+
+def modmatmul(A, B, C, p, sign=-1, variant=GEMM_AUTO, stream=None):
+    """C <- (C + sign*A*B) mod p in place; A, B, C are 2-D row-major CUDA
+    tensors of 16-bit values (int16 views of uint16 residues)."""
+    lib = load()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K2 == K and tuple(C.shape) == (M, N)
+    rc = lib.gbla_modmatmul(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                            C.data_ptr(), C.stride(0), int(p), int(sign), int(variant), _stream_ptr(stream))
+    _check(rc, "gbla_modmatmul")
+
+
+def pivots(row_ptr, col, val, shape, p, stream=None):
+    """FL step-1 pivot choice on device tensors; returns (piv_row tensor, npiv)."""
+    import torch
+    lib = load()
+    m, n = int(shape[0]), int(shape[1])
+    cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    out = torch.empty(max(n, 1), dtype=torch.int64, device=row_ptr.device)
+    npiv = ctypes.c_int64(0)
+    rc = lib.gbla_pivots(ctypes.byref(cin), int(p), out.data_ptr(), ctypes.byref(npiv), _stream_ptr(stream))
+    _check(rc, "gbla_pivots")
+    return out[:n], int(npiv.value)
+
+
+def multiline(row_ptr, col, val, m):
+    """2-multiline vectors of consecutive row pairs of a host CSR (computed on
+    the device).  Returns (ml_ptr, ml_pos, ml_val) numpy arrays."""
+    lib = load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.uint16)
+    nnz = len(col)
+    cin = CsrIn(m, 0, nnz, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data)
+    npairs = (m + 1) // 2
+    ptr = np.zeros(npairs + 1, np.int64)
+    pos = np.zeros(max(nnz, 1), np.int32)
+    mv = np.zeros(max(2 * nnz, 2), np.uint16)
+    rc = lib.gbla_multiline(ctypes.byref(cin), ptr.ctypes.data, pos.ctypes.data, mv.ctypes.data, None)
+    _check(rc, "gbla_multiline")
+    total = int(ptr[-1])
+    return ptr, pos[:total], mv[:2 * total]

@@ -70,7 +70,7 @@ def _runs(rng, lead, k, n, run_len):
         C = np.cumsum(lens)
     # Piece boundaries: run boundaries of one global stream cut at row ends.
     bounds = _sorted_unique(np.concatenate([C[C < total], K[:-1]]))
-    bounds = bounds[bounds > 0]
+    bounds = bounds[(bounds > 0) & (bounds < total)]
     bounds = np.concatenate([[0], bounds, [total]]).astype(np.int64)
     pstart = bounds[:-1]
     plen = np.diff(bounds)
