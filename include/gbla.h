@@ -85,6 +85,7 @@ typedef struct {
     int64_t rank_d;    /* rank of the Schur complement D' */
     double ms_split, ms_trsm, ms_schur, ms_echelon, ms_backsub, ms_output, ms_total;
     double mod_ops;    /* dense-equivalent modular multiply-adds executed */
+    int64_t launches;  /* CUDA kernels launched by the call */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */

@@ -42,6 +42,14 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+
+static double ora_now(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 #define ORA_OK 0
 #define ORA_E_INVAL 1
@@ -294,8 +302,11 @@ int64_t oracle_pivots(int64_t m, int64_t n, const int64_t *row_ptr, const int32_
 int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
                    const int32_t *col, const uint16_t *val, int64_t *rank,
                    int64_t **out_row_ptr, int32_t **out_col, uint16_t **out_val,
-                   int64_t *npiv_out)
+                   int64_t *npiv_out, double *seconds)
 {
+    /* seconds (optional, 2 entries): wall time of the row reduction by the
+     * pivot rows, and of the Gauss-Jordan pass on the Schur complement. */
+    double t0 = ora_now(), t1 = t0;
     int rc = ora_validate(m, n, p, row_ptr, col, val);
     if (rc) return rc;
     int64_t *piv_row = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
@@ -356,8 +367,10 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
     }
     if (fail) { free(cd_rows); free(left); rc = ORA_E_NOMEM; goto fail0; }
 
+    t1 = ora_now();
     ora_rows B = {n, 0, 0, NULL, NULL};
     rc = ora_gauss_jordan(n, p, mcd, left, &B);
+    if (seconds) { seconds[0] = t1 - t0; seconds[1] = ora_now() - t1; }
     free(left);
     free(cd_rows);
     if (rc) { free(B.rows); free(B.pcol); goto fail0; }

@@ -129,4 +129,11 @@ __device__ __forceinline__ void dev_fail(uint32_t *err, uint32_t bit) {
 
 namespace gbla {
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+// Kernel launches made by this thread (reported in gbla_stats.launches).
+extern thread_local long long g_launches;
+// Call right after a kernel launch: counts it and returns the launch status.
+inline cudaError_t launch_check() {
+    ++g_launches;
+    return cudaGetLastError();
+}
 }

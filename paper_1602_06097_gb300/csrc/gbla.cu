@@ -22,6 +22,7 @@
 namespace gbla {
 
 static thread_local char g_last_err[512];
+thread_local long long g_launches = 0;
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
     snprintf(g_last_err, sizeof(g_last_err), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what, file, line,
@@ -146,7 +147,7 @@ __global__ void bottom_counts_kernel(int64_t rank_d, const int32_t *__restrict__
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= rank_d) return;
-    const int64_t c = warp_count_nz(D + (int64_t)prow[k] * ldd, n_d, lane);
+    const int64_t c = warp_count_nz(D + (prow ? (int64_t)prow[k] : k) * ldd, n_d, lane);
     if (lane == 0) cnt[outpos[npcol_orig[pcol[k]]]] = c;
 }
 
@@ -203,7 +204,7 @@ __global__ void bottom_fill_kernel(int64_t rank_d, const int32_t *__restrict__ p
     const int lane = threadIdx.x & 31;
     if (k >= rank_d) return;
     const int64_t off = orp[outpos[npcol_orig[pcol[k]]]];
-    warp_compact(D + (int64_t)prow[k] * ldd, n_d, npcol_orig, ocol, oval, off, lane);
+    warp_compact(D + (prow ? (int64_t)prow[k] : k) * ldd, n_d, npcol_orig, ocol, oval, off, lane);
 }
 
 __global__ void transpose_u16_kernel(const uint16_t *__restrict__ src, int64_t lds, int64_t rows, int64_t cols,
@@ -259,6 +260,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     GBLA_TRY(check_device());
     const ModP mp = make_modp(p);
     GemmCounters ctr;
+    const long long launches0 = g_launches;
     Timer tm;
     tm.init(stats != nullptr);
     tm.mark(s);
@@ -273,7 +275,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     PivotInfo pi;
     Multiline ml;
     Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{};
-    uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr;
+    uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
     int32_t *is_piv_row = nullptr, *prow = nullptr, *pcol = nullptr;
     int64_t *outflag = nullptr, *outpos = nullptr, *cnt = nullptr, *orp = nullptr;
     int32_t *ocol = nullptr;
@@ -369,7 +371,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     STEP(dalloc_t(&prow, (size_t)m_cd + 1, s));
     STEP(dalloc_t(&pcol, (size_t)m_cd + 1, s));
     {
-        EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &mp, variant, err, s, &ctr};
+        EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, variant, err, s, &ctr};
         STEP(echelon_d(E, &rank_d));
     }
     tm.mark(s);  // 4
@@ -384,14 +386,14 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
             // Y^T[c][j] -= sum_k RREF(D')[k][c] * Y^T[P_D[k]][j]
             STEP(planes_alloc(&RdT, n_d, rank_d, 2, s));
             STEP(planes_alloc(&XpdT, npiv, rank_d, 4, s));
-            STEP(to_planes(RdT, n_d, rank_d, D16, ldd, 0, true, prow, nullptr, mp, s));
+            STEP(to_planes(RdT, n_d, rank_d, R16, ldd, 0, true, nullptr, nullptr, mp, s));
             STEP(to_planes(XpdT, npiv, rank_d, Bt16, ldbt, 0, true, pcol, nullptr, mp, s));
             STEP(modgemm(RdT, 0, 0, XpdT, 0, 0, Bt16, ldbt, n_d, npiv, rank_d, -1, mp, variant, err, s, &ctr));
         }
         STEP(dalloc_t(&Y16, (size_t)npiv * (size_t)ldd, s));
         dim3 grid((unsigned)((npiv + 31) / 32), (unsigned)((n_d + 31) / 32));
         transpose_u16_kernel<<<grid, dim3(32, 8), 0, s>>>(Bt16, ldbt, n_d, npiv, Y16, ldd);
-        CSTEP(cudaGetLastError());
+        CSTEP(launch_check());
     } else if (want_reduced && npiv > 0) {
         // no B block: the top rows are unit vectors
         STEP(dalloc_t(&Y16, (size_t)npiv * (size_t)ldd, s));
@@ -408,22 +410,22 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     CSTEP(cudaMemsetAsync(outflag, 0, sizeof(int64_t) * (size_t)(n + 1), s));
     if (npiv > 0) {
         mark_pivot_cols_kernel<<<(unsigned)((npiv + 255) / 256), 256, 0, s>>>(npiv, pi.pivcol_orig, outflag);
-        CSTEP(cudaGetLastError());
+        CSTEP(launch_check());
     }
     if (rank_d > 0) {
         mark_bottom_cols_kernel<<<(unsigned)((rank_d + 255) / 256), 256, 0, s>>>(rank_d, pcol, pi.npcol_orig, outflag);
-        CSTEP(cudaGetLastError());
+        CSTEP(launch_check());
     }
     STEP(scan_i64(outflag, outpos, n, nullptr, s));
     if (npiv > 0) {
         top_counts_kernel<<<(unsigned)((npiv * 32 + 255) / 256), 256, 0, s>>>(npiv, pi.piv_row, pi.pivcol_orig,
                                                                             dc.row_ptr, Y16, ldd, n_d, outpos, cnt);
-        CSTEP(cudaGetLastError());
+        CSTEP(launch_check());
     }
     if (rank_d > 0) {
-        bottom_counts_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(rank_d, prow, pcol, pi.npcol_orig,
-                                                                                  D16, ldd, n_d, outpos, cnt);
-        CSTEP(cudaGetLastError());
+        bottom_counts_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(rank_d, nullptr, pcol, pi.npcol_orig,
+                                                                                  R16, ldd, n_d, outpos, cnt);
+        CSTEP(launch_check());
     }
     STEP(scan_i64(cnt, orp, rank, orp + rank, s));
     CSTEP(cudaMemcpyAsync(&onnz, orp + rank, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -434,12 +436,12 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
         top_fill_kernel<<<(unsigned)((npiv * 32 + 255) / 256), 256, 0, s>>>(
             npiv, pi.piv_row, pi.pivcol_orig, dc.row_ptr, dc.col, dc.val, pi.inv_lead, Y16, ldd, n_d, pi.npcol_orig,
             outpos, orp, ocol, oval, mp);
-        CSTEP(cudaGetLastError());
+        CSTEP(launch_check());
     }
     if (rank_d > 0) {
         bottom_fill_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(
-            rank_d, prow, pcol, pi.npcol_orig, D16, ldd, n_d, outpos, orp, ocol, oval);
-        CSTEP(cudaGetLastError());
+            rank_d, nullptr, pcol, pi.npcol_orig, R16, ldd, n_d, outpos, orp, ocol, oval);
+        CSTEP(launch_check());
     }
     {
         // results leave the pool: device results in plain device memory,
@@ -492,6 +494,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
             stats->ms_output = tm.ms(5, 6);
             stats->ms_total = tm.ms(0, 6);
             stats->mod_ops = ctr.mod_ops;
+            stats->launches = g_launches - launches0;
         }
     }
 
@@ -513,6 +516,7 @@ cleanup:
     dfree(D16, s);
     dfree(Bt16, s);
     dfree(Y16, s);
+    dfree(R16, s);
     dfree(is_piv_row, s);
     dfree(prow, s);
     dfree(pcol, s);
@@ -640,7 +644,7 @@ int gbla_pivots(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev, int
     if (rc == GBLA_OK) rc = pivot_analysis(dc, mp, &pi, err, s);
     if (rc == GBLA_OK && dc.n > 0) {
         piv_row_out_kernel<<<(unsigned)((dc.n + 255) / 256), 256, 0, s>>>(dc.n, pi.best, piv_row_dev);
-        if (cudaGetLastError() != cudaSuccess) rc = GBLA_E_CUDA;
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
     if (rc == GBLA_OK) *npiv = pi.npiv;
     pivot_free(&pi, s);

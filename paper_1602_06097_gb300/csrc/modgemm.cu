@@ -17,7 +17,7 @@
 // a running residue kept in registers.  The kernel is a persistent,
 // warp-specialised tcgen05 pipeline: one thread issues TMA loads into a
 // 2-stage shared-memory ring, one thread issues tcgen05.mma into a
-// double-buffered TMEM accumulator pair, four warps drain TMEM.
+// double-buffered TMEM accumulator pair, eight warps drain TMEM.
 //
 // SIMT path: exact int64 dot products on CUDA cores, used as the reference
 // variant in tests and for p < 8.
@@ -34,7 +34,7 @@ namespace gbla {
 // ===================================================================
 // u16 matrix -> digit planes
 // ===================================================================
-// dst(r, k), r < dst.rows, k < dst.kp:
+// dst(r, k) for r < round_up(R, 128), k < round_up(Kc, 128) (within the buffer):
 //   transposed == false : src[g(r) * lds + col_off + h(k)]
 //   transposed == true  : src[g(k) * lds + col_off + r]
 // with g = row gather (or identity), h = column gather (or identity); values
@@ -103,13 +103,17 @@ int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int
               const ModP &mp, cudaStream_t s)
 {
     if (dst.rows <= 0 || dst.kp <= 0) return GBLA_OK;
+    // Cover the logical rectangle rounded up to whole 128 x 128 tiles (the
+    // product reads nothing else); the rest of the buffer is left as is.
+    const int64_t rows = round_up(R > 0 ? R : 1, 128) < dst.rows ? round_up(R > 0 ? R : 1, 128) : dst.rows;
+    const int64_t ks = round_up(Kc > 0 ? Kc : 1, 128) < dst.kp ? round_up(Kc > 0 ? Kc : 1, 128) : dst.kp;
     dim3 block(32, 8);
-    dim3 grid((unsigned)(dst.kp / 32), (unsigned)(dst.rows / 32));
+    dim3 grid((unsigned)(ks / 32), (unsigned)(rows / 32));
     if (transposed)
         to_planes_kernel<true><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, mp.p, mp.r256);
     else
         to_planes_kernel<false><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, mp.p, mp.r256);
-    GBLA_CUDA_TRY(cudaGetLastError());
+    GBLA_CUDA_TRY(launch_check());
     return GBLA_OK;
 }
 
@@ -120,7 +124,8 @@ __device__ __forceinline__ int bf2i(__nv_bfloat16 v) { return (int)__bfloat162fl
 
 __global__ void __launch_bounds__(256) modgemm_simt_kernel(Planes A, int64_t a_row0, int64_t a_k0, Planes B,
                                                            int64_t b_row0, int64_t b_k0, uint16_t *C, int64_t ldc,
-                                                           int64_t M, int64_t N, int64_t K, int sign, ModP mp)
+                                                           const int32_t *__restrict__ c_rows, int64_t M, int64_t N,
+                                                           int64_t K, int sign, ModP mp)
 {
     __shared__ int sa[64][33];
     __shared__ int sb[64][33];
@@ -175,9 +180,10 @@ __global__ void __launch_bounds__(256) modgemm_simt_kernel(Planes A, int64_t a_r
             if (c >= N) continue;
             long long v = acc[i][j] % P;
             if (v < 0) v += P;
-            long long cur = C[r * ldc + c];
+            const int64_t pr = c_rows ? (int64_t)c_rows[r] : r;
+            long long cur = C[pr * ldc + c];
             long long o = sign > 0 ? (cur + v) % P : (cur - v + P) % P;
-            C[r * ldc + c] = (uint16_t)o;
+            C[pr * ldc + c] = (uint16_t)o;
         }
     }
 }
@@ -192,6 +198,8 @@ constexpr int KSTEPS_PER_BLOCK = 8;                 // k-block of 512: exact fp3
 constexpr int TILE_BYTES = BM * BK * 2;             // 16 KiB (A and B tiles are 128 rows)
 constexpr int STAGE_BYTES = 6 * TILE_BYTES;         // Ah Al | Bh Bl B'h B'l
 constexpr int BAR_BYTES = 256;
+constexpr int EPI_WARPS = 8;                        // two drain warps per TMEM lane quarter
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;                 // 2 buffers x (P 128 + Q 128)
 constexpr float MAGIC = 12582912.0f;                // 1.5 * 2^23
@@ -203,6 +211,7 @@ struct Args {
     int32_t b_row0, b_k0, b_rows;
     uint16_t *C;
     int64_t ldc;
+    const int32_t *c_rows;   // optional: row r of the product goes to C row c_rows[r]
     int sign;
     uint32_t p;
     float pf, pinv;
@@ -343,7 +352,7 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t nu
     nt = in / gm;
 }
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(tc::THREADS, 1)
     modgemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args g)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -365,7 +374,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 4);
+            mbar_init(&acce[b], EPI_WARPS);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
@@ -488,26 +497,29 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else {
-        // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+        // ---------------- epilogue: warps 2..9.  A warp may only read the TMEM
+        // lane quarter warp % 4; the two warps of a quarter split the columns.
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
         const float pf = g.pf, pinv = g.pinv;
         const int P = (int)g.p;
+        constexpr int HC = BN / 2;    // columns per drain warp
         uint32_t kbc = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
             int64_t mt, nt;
             tile_coords(t, num_m, num_n, mt, nt);
-            uint32_t run[BN / 2];
+            uint32_t run[HC / 2];
 #pragma unroll
-            for (int i = 0; i < BN / 2; ++i) run[i] = 0;
+            for (int i = 0; i < HC / 2; ++i) run[i] = 0;
             for (int kb = 0; kb < kblocks; ++kb, ++kbc) {
                 const uint32_t buf = kbc & 1u, use = kbc >> 1;
                 if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
                 tcgen05_fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * 256u;
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * 256u + half * HC;
 #pragma unroll
-                for (int c = 0; c < BN / 16; ++c) {
+                for (int c = 0; c < HC / 16; ++c) {
                     float pv[16], qv[16];
                     tmem_ld16(tbase + c * 16, pv);
                     tmem_ld16(tbase + 128 + c * 16, qv);
@@ -538,17 +550,21 @@ __global__ void __launch_bounds__(192, 1)
                 if (lane == 0) mbar_arrive(&acce[buf]);
             }
             if (!ok) break;
-            // C <- (C + sign * run) mod p for this thread's row.
+            // C <- (C + sign * run) mod p for this thread's row segment.
             const int64_t row = mt * BM + row_in_tile;
-            const int64_t col0 = nt * BN;
-            if (row < g.M) {
-                uint16_t *crow = g.C + row * g.ldc + col0;
-                const bool vec = (col0 + BN <= g.N) && ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
+            const int64_t col0 = nt * BN + half * HC;
+            if (row < g.M && col0 < g.N) {
+                const int64_t prow = g.c_rows ? (int64_t)g.c_rows[row] : row;
+                uint16_t *crow = g.C + prow * g.ldc + col0;
+                const bool vec = (col0 + HC <= g.N) && ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
                 if (vec) {
+                    // issue every load of the segment before the first store
+                    uint4 cv[HC / 8];
 #pragma unroll
-                    for (int v = 0; v < BN / 8; ++v) {
-                        uint4 cur = reinterpret_cast<const uint4 *>(crow)[v];
-                        uint32_t w[4] = {cur.x, cur.y, cur.z, cur.w};
+                    for (int v = 0; v < HC / 8; ++v) cv[v] = reinterpret_cast<const uint4 *>(crow)[v];
+#pragma unroll
+                    for (int v = 0; v < HC / 8; ++v) {
+                        uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             uint32_t rr = run[v * 4 + e];
@@ -560,11 +576,13 @@ __global__ void __launch_bounds__(192, 1)
                             o1 += (o1 < 0) ? P : 0; o1 -= (o1 >= P) ? P : 0;
                             w[e] = (uint32_t)o0 | ((uint32_t)o1 << 16);
                         }
-                        reinterpret_cast<uint4 *>(crow)[v] = make_uint4(w[0], w[1], w[2], w[3]);
+                        cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
                     }
+#pragma unroll
+                    for (int v = 0; v < HC / 8; ++v) reinterpret_cast<uint4 *>(crow)[v] = cv[v];
                 } else {
 #pragma unroll
-                    for (int j = 0; j < BN; ++j) {
+                    for (int j = 0; j < HC; ++j) {
                         if (col0 + j < g.N) {
                             int r = (int)((run[j / 2] >> ((j & 1) * 16)) & 0xFFFFu);
                             int cc = (int)crow[j];
@@ -641,7 +659,7 @@ static bool tc_supported() {
 
 int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
             uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
-            uint32_t *err, cudaStream_t s, GemmCounters *ctr)
+            uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows)
 {
     if (M <= 0 || N <= 0 || K <= 0) return GBLA_OK;
     if (variant == GBLA_GEMM_AUTO) variant = (mp.p >= 8 && tc_supported()) ? GBLA_GEMM_TCGEN05 : GBLA_GEMM_SIMT;
@@ -651,8 +669,8 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     }
     if (variant == GBLA_GEMM_SIMT) {
         dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
-        modgemm_simt_kernel<<<grid, 256, 0, s>>>(A, a_row0, a_k0, B, b_row0, b_k0, C, ldc, M, N, K, sign, mp);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        modgemm_simt_kernel<<<grid, 256, 0, s>>>(A, a_row0, a_k0, B, b_row0, b_k0, C, ldc, c_rows, M, N, K, sign, mp);
+        GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
     if (variant != GBLA_GEMM_TCGEN05) return GBLA_E_INVAL;
@@ -672,13 +690,13 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     g.M = M; g.N = N; g.K = K;
     g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0; g.a_rows = (int32_t)A.rows;
     g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0; g.b_rows = (int32_t)B.rows;
-    g.C = C; g.ldc = ldc; g.sign = sign;
+    g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.sign = sign;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
-    tc::modgemm_tc_kernel<<<grid, 192, tc::SMEM_BYTES, s>>>(ma, mb, g);
-    GBLA_CUDA_TRY(cudaGetLastError());
+    tc::modgemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
 }

@@ -18,6 +18,8 @@
 #include "internal.cuh"
 #include "solve.cuh"
 
+#include <vector>
+
 namespace gbla {
 
 constexpr int LEAF = 128;
@@ -112,7 +114,7 @@ static int trsm_upper_rec(const TrsmUpper &T, int64_t lo, int64_t hi)
         const int64_t pairs = (T.mrows + 1) / 2;
         trsm_upper_leaf_kernel<<<(unsigned)((pairs + 7) / 8), 256, 0, T.s>>>(
             T.mrows, T.npiv, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val, T.C16, T.ldc, *T.Xp, *T.mp);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
     const int64_t mid = lo + round_up((hi - lo) / 2, LEAF);
@@ -226,7 +228,7 @@ static int trsm_lower_rec(const TrsmLower &T, int64_t lo, int64_t hi)
         const int64_t pairs = (T.mrows + 1) / 2;
         trsm_lower_leaf_kernel<<<(unsigned)((pairs + 7) / 8), 256, 0, T.s>>>(
             T.mrows, T.npiv, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val, T.C16, T.ldc, *T.Xp, *T.mp);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
     const int64_t mid = lo + round_up((hi - lo) / 2, LEAF);
@@ -244,60 +246,151 @@ int trsm_lower(const TrsmLower &T)
 }
 
 // ================================================================ echelon
-// Blocked Gauss-Jordan of D over column panels of width <= 128.
+// Reduced echelon form of D' (Sec. 4.1 step 4; Alg. 3 and its parallel form
+// in Sec. 5.1), in two passes.
 //
-// Panel step (one CTA): the rows that are not yet pivots are taken in order;
-// each is reduced by the panel basis found so far (kept in reduced echelon
-// form over the panel's columns) and, if something is left, becomes a new
-// basis row (normalised at its leftmost nonzero, the other basis rows cleared
-// at that column).  This is Alg. 3's "normalise, reduce by matching heads",
-// restricted to the panel.  Each candidate carries the coefficients that
-// express it in the chosen rows S, so at the end G satisfies
-// G * D[S, panel] = U, U in reduced echelon form with pivot columns pc.
-// The trailing update then applies, to every row outside S (earlier pivot
-// rows included, which is what makes the result reduced):
-//   row[c0:] <- row[c0:] - row[pc] * W,   W = G * D[S, c0:],
-// and the rows S receive W.  Both products run on the tensor cores.
+// Forward pass, column panels of width <= 128.  Rows of D' are kept with
+// their current leading column.  The panel starts at the smallest leading
+// column among the rows that are not pivots yet; its candidates are the
+// non-pivot rows whose leading column falls inside it (the others are zero
+// there and are not touched).  One CTA takes the candidates in order; each is
+// reduced by the panel basis found so far (reduced echelon form over the
+// panel's columns) and, if something is left, becomes a new basis row,
+// normalised at its leftmost nonzero (Alg. 3's "normalise, reduce by matching
+// heads", restricted to the panel).  Each candidate carries the coefficients
+// expressing it in the chosen rows S, so G * D[S, panel] = U with U in
+// reduced echelon form at pivot columns pc.  Then, on the tensor cores,
+//     D[S, c0:]    <- G * D[S, c0:]
+//     D[cand, c0:] <- D[cand, c0:] - D[cand, pc] * D[S, c0:]   (cand outside S)
+// and the candidates that did not become pivots get their new leading column.
+// The pivot rows end in echelon form with unit pivots and identity blocks
+// on each panel's pivot columns.
+//
+// Backward pass: with R = the pivot rows in pivot-column order and
+// T = R[:, P_D] (unit upper triangular), RREF(D') = T^-1 R.  This is a
+// left-sided triangular solve done by recursive halving: the off-diagonal
+// updates R_top -= R_top[:, P_D(bottom)] * R_bottom are tensor-core
+// products, and each diagonal block of <= 128 rows is applied as
+// R_J <- R_J - (I - T_JJ^-1) R_J.
 constexpr int PANEL = 128;
 
-__global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t m, int64_t c0,
-                                                    int bw, const int32_t *__restrict__ is_piv_row,
-                                                    int32_t *__restrict__ t_out, int32_t *__restrict__ S_out,
-                                                    int32_t *__restrict__ pc_out, uint16_t *__restrict__ G_out,
-                                                    ModP mp)
+// First nonzero column >= from of each listed row (or every row), -1 if none.
+__global__ void row_leads_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t n, int64_t m,
+                                 const int32_t *__restrict__ rows, const int32_t *__restrict__ count_dev,
+                                 int64_t from, const int32_t *__restrict__ skip, int32_t *__restrict__ lead)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t cnt = count_dev ? *count_dev : m;
+    if (w >= cnt) return;
+    const int64_t r = rows ? rows[w] : w;
+    if (skip && skip[r]) return;
+    const uint16_t *row = D + r * ldd;
+    int64_t found = -1;
+    for (int64_t base = from; base < n && found < 0; base += 32 * 8) {
+        int64_t best = INT64_MAX;
+        for (int e = 0; e < 8; ++e) {
+            const int64_t c = base + (int64_t)e * 32 + lane;
+            if (c < n && row[c] != 0) { best = c; break; }
+        }
+        // minimum over the warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t t = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+            best = t < best ? t : best;
+        }
+        if (best != INT64_MAX) found = best;
+    }
+    if (lane == 0) lead[r] = (int32_t)found;
+}
+
+// One CTA: c0 = smallest leading column of a non-pivot row; candidates =
+// non-pivot rows with leading column in [c0, c0 + PANEL), in row order.
+__global__ void __launch_bounds__(1024) candidates_kernel(int64_t m, const int32_t *__restrict__ lead,
+                                                          const int32_t *__restrict__ is_piv_row,
+                                                          int32_t *__restrict__ cand, int32_t *__restrict__ info)
+{
+    __shared__ int smin;
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) { smin = INT32_MAX; base = 0; }
+    __syncthreads();
+    int lmin = INT32_MAX;
+    for (int64_t r = tid; r < m; r += blockDim.x) {
+        const int l = lead[r];
+        if (!is_piv_row[r] && l >= 0 && l < lmin) lmin = l;
+    }
+    atomicMin(&smin, lmin);
+    __syncthreads();
+    const int c0 = smin;
+    for (int64_t r0 = 0; r0 < m; r0 += blockDim.x) {
+        const int64_t r = r0 + tid;
+        int f = 0;
+        if (r < m && c0 != INT32_MAX) {
+            const int l = lead[r];
+            f = (!is_piv_row[r] && l >= 0 && l < c0 + PANEL) ? 1 : 0;
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int off = base;
+        for (int k = 0; k < wid; ++k) off += wsum[k];
+        if (f) cand[off + __popc(bal & ((1u << lane) - 1u))] = (int32_t)r;
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += wsum[k];
+            base += tot;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        info[0] = (c0 == INT32_MAX) ? -1 : c0;
+        info[1] = base;
+    }
+}
+
+__global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t c0, int bw,
+                                                    const int32_t *__restrict__ cand, int ncand,
+                                                    int32_t *__restrict__ is_piv_row, int32_t *__restrict__ t_out,
+                                                    int32_t *__restrict__ S_out, int32_t *__restrict__ Spos_out,
+                                                    int32_t *__restrict__ pc_out, uint16_t *__restrict__ Gm_out,
+                                                    int32_t *__restrict__ prow, int32_t *__restrict__ pcol,
+                                                    int64_t rank0, ModP mp)
 {
     extern __shared__ uint32_t smem_u32[];
     uint32_t(*aug)[2 * PANEL] = reinterpret_cast<uint32_t(*)[2 * PANEL]>(smem_u32);  // [PANEL][256]
-    __shared__ uint32_t cand[2 * PANEL];
+    __shared__ uint32_t cand_v[2 * PANEL];
     __shared__ uint32_t fk[PANEL];
-    __shared__ int bcol[PANEL], S[PANEL], rnk[PANEL];
+    __shared__ int bcol[PANEL], S[PANEL], Spos[PANEL], rnk[PANEL];
     __shared__ int cstar;
     __shared__ uint32_t inv_s;
     const int c = threadIdx.x;  // column of the augmented row: [panel | coefficients]
     const uint64_t P = mp.p;
     int t = 0;
-    for (int64_t i = 0; i < m && t < bw; ++i) {
-        if (is_piv_row[i]) continue;
+    for (int ci = 0; ci < ncand && t < bw; ++ci) {
+        const int64_t i = cand[ci];
         const uint32_t v = (c < bw) ? D[i * ldd + c0 + c] : ((c >= PANEL && c - PANEL == t) ? 1u : 0u);
         if (!__syncthreads_or(c < bw && v != 0)) continue;
-        cand[c] = v;
+        cand_v[c] = v;
         __syncthreads();
         // reduce by the basis (reduced echelon: coefficient = entry at its pivot)
         unsigned long long a = v;
         for (int k = 0; k < t; ++k) {
-            const uint64_t coef = cand[bcol[k]];
+            const uint64_t coef = cand_v[bcol[k]];
             a += (P - coef) * aug[k][c];
         }
         const uint32_t nv = mod64(a, mp);
         __syncthreads();
-        cand[c] = nv;
+        cand_v[c] = nv;
         if (c == 0) cstar = 1 << 30;
         __syncthreads();
         if (c < bw && nv != 0) atomicMin(&cstar, c);
         __syncthreads();
         const int cs = cstar;
         if (cs >= bw) continue;           // dependent on the rows taken so far
-        if (c == 0) inv_s = invmod(cand[cs], mp);
+        if (c == 0) inv_s = invmod(cand_v[cs], mp);
         if (c < t) fk[c] = aug[c][cs];
         __syncthreads();
         const uint32_t nrm = mulmod(nv, inv_s, mp);
@@ -309,6 +402,7 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
         if (c == 0) {
             bcol[t] = cs;
             S[t] = (int)i;
+            Spos[t] = ci;
         }
         ++t;
         __syncthreads();
@@ -324,11 +418,23 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
     if (c == 0) *t_out = t;
     if (c < t) {
         S_out[c] = S[c];
+        Spos_out[c] = Spos[c];
         pc_out[rnk[c]] = bcol[c];
+        is_piv_row[S[c]] = 1;
+        // the pivot with the c-th smallest column lands in physical row S[c]
+    }
+    __syncthreads();
+    if (c < t) {
+        prow[rank0 + c] = S[c];
+        pcol[rank0 + c] = (int32_t)(c0 + pc_out[c]);
     }
     for (int k = 0; k < t; ++k) {
-        // G row rnk[k] = coefficient part of basis row k (columns = S order)
-        if (c < PANEL) G_out[rnk[k] * PANEL + c] = (uint16_t)((c < t) ? aug[k][PANEL + c] : 0u);
+        // Gm row rnk[k] = coefficient part of basis row k minus the identity
+        if (c < PANEL) {
+            uint32_t g = (c < t) ? aug[k][PANEL + c] : 0u;
+            if (c == rnk[k]) g = (g + mp.p - 1) % mp.p;
+            Gm_out[rnk[k] * PANEL + c] = (uint16_t)g;
+        }
     }
 }
 
@@ -344,23 +450,81 @@ __global__ void zero_plane_rows_kernel(Planes H, const int32_t *__restrict__ row
     }
 }
 
-// D[S[k]][c0 + i] = W^T[i][k]; mark the rows as pivots; record pivots.
-__global__ void write_pivots_kernel(uint16_t *D, int64_t ldd, int64_t c0, int64_t ncols, const uint16_t *__restrict__ WT,
-                                    int64_t ldw, const int32_t *__restrict__ S, const int32_t *__restrict__ pc,
-                                    const int32_t *__restrict__ t_dev, int32_t *__restrict__ is_piv_row,
-                                    int32_t *__restrict__ prow, int32_t *__restrict__ pcol, int64_t rank0)
+__global__ void gather_rows_kernel(const uint16_t *__restrict__ D, int64_t ldd, const int32_t *__restrict__ rows,
+                                   int64_t nrows, int64_t n, uint16_t *__restrict__ R, int64_t ldr)
 {
-    const int t = *t_dev;
-    const int k = blockIdx.y;
-    if (k >= t) return;
-    const int64_t r = S[k];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncols; i += (int64_t)gridDim.x * blockDim.x)
-        D[r * ldd + c0 + i] = WT[i * ldw + k];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        is_piv_row[r] = 1;
-        prow[rank0 + k] = (int32_t)r;
-        pcol[rank0 + k] = (int32_t)(c0 + pc[k]);
+    for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
+        const uint16_t *src = D + (int64_t)rows[k] * ldd;
+        uint16_t *dst = R + k * ldr;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = src[i];
     }
+}
+
+// Nm = I - T^-1 for T = R[lo + i][pcol[lo + j]] (w x w, unit upper triangular).
+__global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__restrict__ R, int64_t ldr, int64_t lo,
+                                                           int w, const int32_t *__restrict__ pcol,
+                                                           uint16_t *__restrict__ Nm, ModP mp)
+{
+    extern __shared__ uint16_t leaf_smem[];
+    uint16_t(*T)[129] = reinterpret_cast<uint16_t(*)[129]>(leaf_smem);             // [128][129]
+    uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(leaf_smem + 128 * 129);  // [128][129]
+    const int j = threadIdx.x;
+    for (int i = 0; i < w; ++i)
+        T[i][j] = (j < w) ? R[(lo + i) * ldr + pcol[lo + j]] : 0;
+    __syncthreads();
+    const uint64_t P = mp.p;
+    // column j of Z = T^-1, rows from the bottom: Z[i][j] = d_ij - sum_{i<k<=j} T[i][k] Z[k][j]
+    for (int i = w - 1; i >= 0; --i) {
+        if (j < w) {
+            uint64_t acc = (i == j) ? 1 : 0;
+            uint64_t sub = 0;
+            for (int k = i + 1; k <= j; ++k) sub += (uint64_t)T[i][k] * Z[k][j];
+            Z[i][j] = (uint16_t)((j < i) ? 0u : mod64(acc + P * P - mod64(sub, mp), mp));
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < w; ++i)
+        if (j < PANEL) {
+            uint32_t z = (j < w) ? Z[i][j] : 0u;
+            uint32_t v = ((i == j) ? 1u : 0u) + mp.p - z;
+            Nm[i * PANEL + j] = (uint16_t)(v % mp.p);
+        }
+}
+
+constexpr int LEAF_INV_SMEM = 2 * 128 * 129 * (int)sizeof(uint16_t);
+
+struct EchScratch {
+    int32_t *info, *cand, *t_dev, *S, *Spos, *pc, *lead;
+    uint16_t *Gm;
+    Planes Gp, Bs, H;
+};
+
+static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_t *pcol_dev,
+                       const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &Bp, uint16_t *Nm)
+{
+    const ModP &mp = *E.mp;
+    cudaStream_t s = E.s;
+    const int64_t n = E.n;
+    if (hi - lo <= PANEL) {
+        const int w = (int)(hi - lo);
+        const int64_t cs = pcol[lo];
+        leaf_inverse_kernel<<<1, 128, LEAF_INV_SMEM, s>>>(R, ldr, lo, w, pcol_dev, Nm, mp);
+        GBLA_CUDA_TRY(launch_check());
+        GBLA_TRY(to_planes(Ap, w, w, Nm, PANEL, 0, false, nullptr, nullptr, mp, s));
+        GBLA_TRY(to_planes(Bp, n - cs, w, R + lo * ldr, ldr, cs, true, nullptr, nullptr, mp, s));
+        return modgemm(Ap, 0, 0, Bp, 0, 0, R + lo * ldr + cs, ldr, w, n - cs, w, -1, mp, E.variant, E.err, s,
+                       E.ctr);
+    }
+    const int64_t mid = lo + round_up((hi - lo) / 2, PANEL);
+    GBLA_TRY(backsub_rec(E, R, ldr, pcol_dev, pcol, mid, hi, Ap, Bp, Nm));
+    // R[lo:mid] -= R[lo:mid, P_D[mid:hi]] * R[mid:hi]   (rows mid.. are zero left of P_D[mid])
+    const int64_t cs = pcol[mid];
+    GBLA_TRY(to_planes(Ap, mid - lo, hi - mid, R + lo * ldr, ldr, 0, false, nullptr, pcol_dev + mid, mp, s));
+    GBLA_TRY(to_planes(Bp, n - cs, hi - mid, R + mid * ldr, ldr, cs, true, nullptr, nullptr, mp, s));
+    GBLA_TRY(modgemm(Ap, 0, 0, Bp, 0, 0, R + lo * ldr + cs, ldr, mid - lo, n - cs, hi - mid, -1, mp, E.variant,
+                     E.err, s, E.ctr));
+    return backsub_rec(E, R, ldr, pcol_dev, pcol, lo, mid, Ap, Bp, Nm);
 }
 
 int echelon_d(const EchelonD &E, int64_t *rank_out)
@@ -370,67 +534,105 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     if (m <= 0 || n <= 0) return GBLA_OK;
     cudaStream_t s = E.s;
     const ModP &mp = *E.mp;
-    int32_t *t_dev = nullptr, *S = nullptr, *pc = nullptr;
-    uint16_t *G = nullptr, *WT = nullptr;
-    Planes Gp{}, DsT{}, Wp{}, H{};
+    EchScratch X{};
     int rc = GBLA_OK;
     int64_t rank = 0;
-    const int64_t ldw = PANEL;
     const size_t panel_smem = (size_t)PANEL * 2 * PANEL * sizeof(uint32_t);
+    int32_t info_h[2];
     GBLA_CUDA_TRY(cudaMemsetAsync(E.is_piv_row, 0, sizeof(int32_t) * (size_t)m, s));
-    GBLA_TRY(dalloc_t(&t_dev, 4, s));
-    GBLA_TRY(dalloc_t(&S, PANEL, s));
-    GBLA_TRY(dalloc_t(&pc, PANEL, s));
-    GBLA_TRY(dalloc_t(&G, (size_t)PANEL * PANEL, s));
-    GBLA_TRY(dalloc_t(&WT, (size_t)round_up(n, 128) * PANEL, s));
-    GBLA_TRY(planes_alloc(&Gp, PANEL, PANEL, 4, s));
-    GBLA_TRY(planes_alloc(&DsT, n, PANEL, 2, s));
-    GBLA_TRY(planes_alloc(&Wp, n, PANEL, 4, s));
-    GBLA_TRY(planes_alloc(&H, m, PANEL, 2, s));
+    GBLA_TRY(dalloc_t(&X.info, 4, s));
+    GBLA_TRY(dalloc_t(&X.cand, (size_t)m + 1, s));
+    GBLA_TRY(dalloc_t(&X.t_dev, 4, s));
+    GBLA_TRY(dalloc_t(&X.S, PANEL, s));
+    GBLA_TRY(dalloc_t(&X.Spos, PANEL, s));
+    GBLA_TRY(dalloc_t(&X.pc, PANEL, s));
+    GBLA_TRY(dalloc_t(&X.lead, (size_t)m + 1, s));
+    GBLA_TRY(dalloc_t(&X.Gm, (size_t)PANEL * PANEL, s));
+    GBLA_TRY(planes_alloc(&X.Gp, PANEL, PANEL, 2, s));
+    GBLA_TRY(planes_alloc(&X.Bs, n, PANEL, 4, s));
+    GBLA_TRY(planes_alloc(&X.H, m, PANEL, 2, s));
     static bool attr = false;
     if (!attr) {
         GBLA_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(leaf_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           LEAF_INV_SMEM));
         attr = true;
     }
-    for (int64_t c0 = 0; c0 < n && rank < m; c0 += PANEL) {
-        const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
-        const int64_t nc = n - c0;   // trailing columns incl. the panel
-        panel_kernel<<<1, 2 * PANEL, panel_smem, s>>>(E.D16, E.ldd, m, c0, bw, E.is_piv_row, t_dev, S, pc, G, mp);
-        if (cudaGetLastError() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        int32_t t = 0;
-        if (cudaMemcpyAsync(&t, t_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    row_leads_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(E.D16, E.ldd, n, m, nullptr, nullptr, 0,
+                                                                     nullptr, X.lead);
+    GBLA_CUDA_TRY(launch_check());
+    // ---- forward pass
+    while (rank < m) {
+        candidates_kernel<<<1, 1024, 0, s>>>(m, X.lead, E.is_piv_row, X.cand, X.info);
+        if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
+        if (cudaMemcpyAsync(info_h, X.info, sizeof(info_h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        if (t == 0) continue;
-        // G (rows: pivots in column order, cols: S order) as a B-operand: Bop[k][j] = G[k][j]
-        if ((rc = to_planes(Gp, t, t, G, PANEL, 0, false, nullptr, nullptr, mp, s))) break;
-        // D[S, c0:]^T as an A-operand: Aop[i][j] = D[S[j]][c0 + i]
-        if ((rc = to_planes(DsT, nc, t, E.D16, E.ldd, c0, true, S, nullptr, mp, s))) break;
-        // W^T = D[S, c0:]^T * G^T
-        if (cudaMemsetAsync(WT, 0, sizeof(uint16_t) * (size_t)nc * ldw, s) != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        if ((rc = modgemm(DsT, 0, 0, Gp, 0, 0, WT, ldw, nc, t, t, +1, mp, E.variant, E.err, s, E.ctr))) break;
-        // W as a B-operand: Bop[i][k] = W^T[i][k]
-        if ((rc = to_planes(Wp, nc, t, WT, ldw, 0, false, nullptr, nullptr, mp, s))) break;
-        // H = D[:, c0 + pc] with the rows S zeroed
-        if ((rc = to_planes(H, m, t, E.D16, E.ldd, c0, false, nullptr, pc, mp, s))) break;
-        zero_plane_rows_kernel<<<t, 128, 0, s>>>(H, S, t_dev);
-        if (cudaGetLastError() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        // every other row: row[c0:] -= row[pc] * W
-        if ((rc = modgemm(H, 0, 0, Wp, 0, 0, E.D16 + c0, E.ldd, m, nc, t, -1, mp, E.variant, E.err, s, E.ctr))) break;
-        dim3 grid((unsigned)((nc + 255) / 256 < 64 ? (nc + 255) / 256 : 64), (unsigned)t);
-        write_pivots_kernel<<<grid, 256, 0, s>>>(E.D16, E.ldd, c0, nc, WT, ldw, S, pc, t_dev, E.is_piv_row, E.prow,
-                                                 E.pcol, rank);
-        if (cudaGetLastError() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
+        const int64_t c0 = info_h[0];
+        const int ncand = info_h[1];
+        if (c0 < 0 || ncand == 0) break;
+        const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
+        const int64_t nc = n - c0;
+        panel_kernel<<<1, 2 * PANEL, panel_smem, s>>>(E.D16, E.ldd, c0, bw, X.cand, ncand, E.is_piv_row, X.t_dev, X.S,
+                                                      X.Spos, X.pc, X.Gm, E.prow, E.pcol, rank, mp);
+        if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
+        int32_t t = 0;
+        if (cudaMemcpyAsync(&t, X.t_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = GBLA_E_CUDA; break; }
+        if (t == 0) { rc = GBLA_E_INTERNAL; break; }   // a candidate always has a nonzero in the panel
+        // D[S, c0:] <- G * D[S, c0:]  as  D[S] += (G - I) * D[S]
+        if ((rc = to_planes(X.Gp, t, t, X.Gm, PANEL, 0, false, nullptr, nullptr, mp, s))) break;
+        if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0, true, X.S, nullptr, mp, s))) break;
+        if ((rc = modgemm(X.Gp, 0, 0, X.Bs, 0, 0, E.D16 + c0, E.ldd, t, nc, t, +1, mp, E.variant, E.err, s, E.ctr,
+                          X.S))) break;
+        if (ncand > t) {
+            // D[cand, c0:] -= D[cand, c0 + pc] * D[S, c0:]   (rows of S have a zero multiplier row)
+            if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0, true, X.S, nullptr, mp, s))) break;
+            Planes Hc = X.H;
+            if ((rc = to_planes(Hc, ncand, t, E.D16, E.ldd, c0, false, X.cand, X.pc, mp, s))) break;
+            zero_plane_rows_kernel<<<t, 128, 0, s>>>(Hc, X.Spos, X.t_dev);
+            if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
+            if ((rc = modgemm(Hc, 0, 0, X.Bs, 0, 0, E.D16 + c0, E.ldd, ncand, nc, t, -1, mp, E.variant, E.err, s,
+                              E.ctr, X.cand))) break;
+            row_leads_kernel<<<(unsigned)(((int64_t)ncand * 32 + 255) / 256), 256, 0, s>>>(
+                E.D16, E.ldd, n, m, X.cand, X.info + 1, c0 + bw, E.is_piv_row, X.lead);
+            if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
+        }
         rank += t;
     }
-    dfree(t_dev, s);
-    dfree(S, s);
-    dfree(pc, s);
-    dfree(G, s);
-    dfree(WT, s);
-    planes_free(&Gp, s);
-    planes_free(&DsT, s);
-    planes_free(&Wp, s);
-    planes_free(&H, s);
+    // ---- backward pass: RREF rows into R (pivot column order)
+    if (rc == GBLA_OK && rank > 0) {
+        const int64_t ldr = E.ldd;
+        std::vector<int32_t> pcol_h((size_t)rank);
+        uint16_t *Nm = nullptr;
+        Planes Ap{}, Bp{};
+        rc = dalloc_t(&E.R[0], (size_t)rank * (size_t)ldr, s);
+        if (rc == GBLA_OK && cudaMemcpyAsync(pcol_h.data(), E.pcol, sizeof(int32_t) * (size_t)rank,
+                                             cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = GBLA_E_CUDA;
+        if (rc == GBLA_OK) {
+            dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64), (unsigned)(rank < 65535 ? rank : 65535));
+            gather_rows_kernel<<<grid, 256, 0, s>>>(E.D16, E.ldd, E.prow, rank, n, E.R[0], ldr);
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+        }
+        if (rc == GBLA_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
+        if (rc == GBLA_OK) rc = dalloc_t(&Nm, (size_t)PANEL * PANEL, s);
+        if (rc == GBLA_OK) rc = planes_alloc(&Ap, rank, rank < 2 * PANEL ? PANEL : rank, 2, s);
+        if (rc == GBLA_OK) rc = planes_alloc(&Bp, n, rank < 2 * PANEL ? PANEL : rank, 4, s);
+        if (rc == GBLA_OK) rc = backsub_rec(E, E.R[0], ldr, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm);
+        dfree(Nm, s);
+        planes_free(&Ap, s);
+        planes_free(&Bp, s);
+    }
+    dfree(X.info, s);
+    dfree(X.cand, s);
+    dfree(X.t_dev, s);
+    dfree(X.S, s);
+    dfree(X.Spos, s);
+    dfree(X.pc, s);
+    dfree(X.lead, s);
+    dfree(X.Gm, s);
+    planes_free(&X.Gp, s);
+    planes_free(&X.Bs, s);
+    planes_free(&X.H, s);
     *rank_out = rank;
     return rc;
 }

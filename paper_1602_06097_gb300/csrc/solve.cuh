@@ -39,15 +39,16 @@ struct TrsmLower {
 };
 int trsm_lower(const TrsmLower &T);
 
-// Reduced echelon form of D (m x n, uint16, in place).  On return rows
-// prow[0..rank) of D are the RREF rows, with pivot columns pcol[0..rank)
-// ascending; every other row of D is zero.
+// Reduced echelon form of D (m x n, uint16, modified in place).  On return
+// *R (allocated here, rank x ldd, release with dfree) holds the RREF rows in
+// pivot-column order, with pivot columns pcol[0..rank) ascending.
 struct EchelonD {
     int64_t m, n;
     uint16_t *D16;
     int64_t ldd;
     int32_t *is_piv_row;   // [m] scratch
-    int32_t *prow, *pcol;  // [m] outputs
+    int32_t *prow, *pcol;  // [m] outputs (prow: row of D each pivot came from)
+    uint16_t **R;          // out: RREF rows, rank x ldd
     const ModP *mp;
     int variant;
     uint32_t *err;

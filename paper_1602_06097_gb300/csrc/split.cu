@@ -77,24 +77,24 @@ int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, cud
     int64_t *sums = nullptr;
     GBLA_TRY(dalloc_t(&sums, (size_t)nb + 1, s));
     scan_block_kernel<<<(unsigned)nb, 256, 0, s>>>(in, out, n, sums);
-    GBLA_CUDA_TRY(cudaGetLastError());
+    GBLA_CUDA_TRY(launch_check());
     int rc = GBLA_OK;
     if (nb == 1) {
         // one block: its sum is the total
         if (total_dev) {
             copy_i64_kernel<<<1, 1, 0, s>>>(total_dev, sums);
-            if (cudaGetLastError() != cudaSuccess) rc = GBLA_E_CUDA;
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
     } else {
         // scan the block sums (sums[nb] receives the grand total), add them back
         rc = scan_i64(sums, sums, nb, sums + nb, s);
         if (rc == GBLA_OK) {
             scan_add_kernel<<<(unsigned)nb, 256, 0, s>>>(out, n, sums);
-            if (cudaGetLastError() != cudaSuccess) rc = GBLA_E_CUDA;
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
         if (rc == GBLA_OK && total_dev) {
             copy_i64_kernel<<<1, 1, 0, s>>>(total_dev, sums + nb);
-            if (cudaGetLastError() != cudaSuccess) rc = GBLA_E_CUDA;
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
     }
     dfree(sums, s);
@@ -210,7 +210,7 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
         const int64_t threads = m * 32;
         scan_rows_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m, n, in.nnz, in.row_ptr, in.col, in.val,
                                                                            mp.p, pi->lead, pi->best, err);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
     }
     int64_t *cflag = nullptr, *rflag = nullptr, *rpos = nullptr;
     GBLA_TRY(dalloc_t(&cflag, (size_t)n + 1, s));
@@ -219,12 +219,12 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
     GBLA_TRY(dalloc_t(&pi->dev_counts, 2, s));
     if (n > 0) {
         col_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pi->best, cflag);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
     }
     GBLA_TRY(scan_i64(cflag, cflag, n, pi->dev_counts + 0, s));
     if (m > 0) {
         row_flags_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, pi->lead, pi->best, rflag);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
     }
     GBLA_TRY(scan_i64(rflag, rpos, m, pi->dev_counts + 1, s));
     int64_t host_counts[2] = {0, 0};
@@ -252,16 +252,16 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
     if (n > 0) {
         colmap_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pi->best, cflag, pi->dev_counts, pi->colmap,
                                                                   pi->pivcol_orig, pi->npcol_orig, pi->piv_row);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
     }
     if (m > 0) {
         cd_rows_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, rflag, rpos, pi->cd_rows, pi->cd_index);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
     }
     if (pi->npiv > 0) {
         inv_lead_kernel<<<(unsigned)((pi->npiv + 255) / 256), 256, 0, s>>>(pi->npiv, pi->piv_row, in.row_ptr, in.val,
                                                                           pi->inv_lead, mp);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
     }
     dfree(cflag, s);
     dfree(rflag, s);
@@ -349,7 +349,7 @@ int split_scatter(const DevCSR &in, const PivotInfo &pi, const Planes &At, const
     split_scatter_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
         in.m, in.row_ptr, in.col, in.val, pi.lead, pi.best, pi.colmap, pi.cd_index, pi.inv_lead, pi.npiv, At, Arow,
         Bt, Bt16, ldbt16, C16, ldc, D16, ldd, mp);
-    GBLA_CUDA_TRY(cudaGetLastError());
+    GBLA_CUDA_TRY(launch_check());
     return GBLA_OK;
 }
 
@@ -422,7 +422,7 @@ int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const 
     const unsigned nb = (unsigned)((npairs + 127) / 128);
     multiline_kernel<false><<<nb, 128, 0, s>>>(npairs, pi.npiv, pi.piv_row, in.row_ptr, in.col, in.val, pi.colmap,
                                                pi.inv_lead, ml->ptr, nullptr, nullptr, mp);
-    GBLA_CUDA_TRY(cudaGetLastError());
+    GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(scan_i64(ml->ptr, ml->ptr, npairs, ml->ptr + npairs, s));
     int64_t total = 0;
     GBLA_CUDA_TRY(cudaMemcpyAsync(&total, ml->ptr + npairs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -432,7 +432,7 @@ int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const 
     GBLA_TRY(dalloc_t(&ml->val, (size_t)total + 1, s));
     multiline_kernel<true><<<nb, 128, 0, s>>>(npairs, pi.npiv, pi.piv_row, in.row_ptr, in.col, in.val, pi.colmap,
                                               pi.inv_lead, ml->ptr, ml->pos, ml->val, mp);
-    GBLA_CUDA_TRY(cudaGetLastError());
+    GBLA_CUDA_TRY(launch_check());
     return GBLA_OK;
 }
 
@@ -482,13 +482,13 @@ int multiline_pairs(int64_t m, const int64_t *row_ptr, const int32_t *col, const
     }
     const unsigned nb = (unsigned)((npairs + 127) / 128);
     multiline_pairs_kernel<<<nb, 128, 0, s>>>(npairs, m, row_ptr, col, val, ml_ptr_dev, nullptr, nullptr, 0);
-    GBLA_CUDA_TRY(cudaGetLastError());
+    GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(scan_i64(ml_ptr_dev, ml_ptr_dev, npairs, ml_ptr_dev + npairs, s));
     GBLA_CUDA_TRY(cudaMemcpyAsync(total, ml_ptr_dev + npairs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GBLA_CUDA_TRY(cudaStreamSynchronize(s));
     if (ml_pos_dev) {
         multiline_pairs_kernel<<<nb, 128, 0, s>>>(npairs, m, row_ptr, col, val, ml_ptr_dev, ml_pos_dev, ml_val_dev, 1);
-        GBLA_CUDA_TRY(cudaGetLastError());
+        GBLA_CUDA_TRY(launch_check());
     }
     return GBLA_OK;
 }
