@@ -140,6 +140,21 @@ int gbla_pivots(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev,
 int gbla_multiline(const gbla_csr_in *pairs_host, int64_t *ml_ptr, int32_t *ml_pos,
                    uint16_t *ml_val, void *stream);
 
+/* Pivot analysis that allocates no memory.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * during a call -- an application that reserves all device memory up front
+ * for its own pool, or a latency-sensitive loop where an allocation may
+ * synchronise the device.  Same arguments and result as gbla_pivots (device
+ * CSR in, device piv_row[ncols] out, *npiv on the host), but its only scratch
+ * is a fixed 8 MiB device array inside the library, held by every GPU that
+ * loads the library until the process exits.  ncols above 1,048,576 (2^20)
+ * is rejected with GBLA_E_INVAL.  The first call on a device looks up that
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array (each clears what it uses), so calls that
+ * overlap on the GPU race: serialise them.  Synchronises `stream`. */
+int gbla_pivots_noalloc(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev,
+                        int64_t *npiv, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

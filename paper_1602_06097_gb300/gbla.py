@@ -19,7 +19,7 @@ GBLA_OK = 0
 GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT = 0, 1, 2
 
 EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
-           "gbla_modmatmul", "gbla_pivots", "gbla_multiline"]
+           "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc"]
 
 
 class CsrIn(ctypes.Structure):
@@ -86,6 +86,8 @@ def load():
         lib.gbla_pivots.restype = i32
         lib.gbla_multiline.argtypes = [ctypes.POINTER(CsrIn), vp, vp, vp, vp]
         lib.gbla_multiline.restype = i32
+        lib.gbla_pivots_noalloc.argtypes = [ctypes.POINTER(CsrIn), u32, vp, ctypes.POINTER(i64), vp]
+        lib.gbla_pivots_noalloc.restype = i32
         _lib = lib
         return lib
 
@@ -224,6 +226,21 @@ def pivots(row_ptr, col, val, shape, p, stream=None):
     rc = lib.gbla_pivots(ctypes.byref(cin), int(p), out.data_ptr(), ctypes.byref(npiv), _stream_ptr(stream))
     _check(rc, "gbla_pivots")
     return out[:n], int(npiv.value)
+
+
+def pivots_noalloc(row_ptr, col, val, shape, p, out, stream=None):
+    """Pivot choice without any allocation in the library: writes piv_row into
+    the caller's int64 CUDA tensor ``out`` (at least ncols long) and returns
+    npiv.  For callers that must not allocate device memory during a call;
+    at most 2^20 columns; calls that overlap on the GPU race."""
+    lib = load()
+    m, n = int(shape[0]), int(shape[1])
+    cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    npiv = ctypes.c_int64(0)
+    rc = lib.gbla_pivots_noalloc(ctypes.byref(cin), int(p), out.data_ptr(), ctypes.byref(npiv),
+                                 _stream_ptr(stream))
+    _check(rc, "gbla_pivots_noalloc")
+    return int(npiv.value)
 
 
 def multiline(row_ptr, col, val, m):
