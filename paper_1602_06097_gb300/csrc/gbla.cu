@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.cuh"
@@ -283,6 +284,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     int64_t rank_d = 0, npiv = 0, m_cd = 0, n_d = 0, rank = 0, onnz = 0;
     int64_t ldc = 0, ldd = 0, ldbt = 0;
     DevCSR dc;
+    std::vector<int32_t> lead_h;
 
 #define STEP(expr)                 \
     do {                           \
@@ -358,12 +360,16 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     if (m_cd > 0 && npiv > 0) {
         STEP(planes_alloc(&Xp, m_cd, npiv, 2, s));
         STEP(planes_zero(Xp, s));
-        TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr};
+        lead_h.resize((size_t)m_cd);
+        CSTEP(cudaMemcpyAsync(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, cudaMemcpyDeviceToHost, s));
+        CSTEP(cudaStreamSynchronize(s));
+        TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr, pi.cd_lead, &lead_h};
         STEP(trsm_upper(T));
     }
     tm.mark(s);  // 2
     if (m_cd > 0 && npiv > 0 && n_d > 0)
-        STEP(modgemm(Xp, 0, 0, Bt, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr));
+        STEP(modgemm(Xp, 0, 0, Bt, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr, nullptr,
+                     pi.cd_lead));
     tm.mark(s);  // 3
 
     // ---- step 4: RREF of D'

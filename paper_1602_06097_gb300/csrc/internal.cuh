@@ -15,11 +15,15 @@ int device_sm_count();
 
 // C <- (C + sign * A * B^T) mod p, A an A-operand plane set (2 planes,
 // rows a_row0.., K from a_k0), B a B-operand plane set (4 planes, rows
-// b_row0.., K from b_k0).  With c_rows, product row r updates C row c_rows[r].  K beyond the logical range must read zeros
-// (zero padding) when K is not a multiple of 64.
+// b_row0.., K from b_k0).  With c_rows, product row r updates C row c_rows[r].
+// With row_lead (ascending, absolute K index of each A row's first nonzero;
+// a_row0 must be 0), each 128-row tile starts at its first row's lead.  K
+// beyond the logical range must read zeros (zero padding) when K is not a
+// multiple of 64.
 int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
             uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
-            uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows = nullptr);
+            uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows = nullptr,
+            const int32_t *row_lead = nullptr);
 
 // u16 -> digit planes (see modgemm.cu).
 int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds, int64_t col_off,

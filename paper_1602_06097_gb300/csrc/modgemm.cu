@@ -212,6 +212,7 @@ struct Args {
     uint16_t *C;
     int64_t ldc;
     const int32_t *c_rows;   // optional: row r of the product goes to C row c_rows[r]
+    const int32_t *row_lead; // optional: ascending first nonzero K index of each A row
     int sign;
     uint32_t p;
     float pf, pinv;
@@ -352,6 +353,14 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t nu
     nt = in / gm;
 }
 
+// First k-step of tile row mt: A rows are zero left of their lead, and with
+// leads ascending the tile's first row has the smallest one.
+__device__ __forceinline__ int tile_kstep0(const Args &g, int64_t mt) {
+    if (!g.row_lead) return 0;
+    const int64_t k = (int64_t)g.row_lead[mt * BM] - g.a_k0;
+    return k > 0 ? (int)(k / BK) : 0;
+}
+
 __global__ void __launch_bounds__(tc::THREADS, 1)
     modgemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args g)
 {
@@ -399,7 +408,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     const int64_t num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
     const int64_t num_tiles = num_m * num_n;
     const int ksteps = (int)((g.K + BK - 1) / BK);
-    const int kblocks = (ksteps + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 int64_t mt, nt;
                 tile_coords(t, num_m, num_n, mt, nt);
                 const int ay = g.a_row0 + (int)(mt * BM), by = g.b_row0 + (int)(nt * BN);
-                for (int ks = 0; ks < ksteps; ++ks) {
+                for (int ks = tile_kstep0(g, mt); ks < ksteps; ++ks) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
                     uint8_t *st = tiles + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], STAGE_BYTES);
@@ -453,13 +461,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             bool ok = true;
             const uint32_t tiles_base = smem_u32(tiles);
             for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                for (int kb = 0; kb < kblocks && ok; ++kb, ++kbc) {
+                int64_t mt, nt;
+                tile_coords(t, num_m, num_n, mt, nt);
+                const int ks0 = tile_kstep0(g, mt);
+                const int kbt = (ksteps - ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+                for (int kb = 0; kb < kbt && ok; ++kb, ++kbc) {
                     const uint32_t buf = kbc & 1u, use = kbc >> 1;
                     if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
                     tcgen05_fence_after();
                     const uint32_t dP = tmem + buf * 256u, dQ = dP + 128u;
-                    const int ks_end = min(ksteps, (kb + 1) * KSTEPS_PER_BLOCK);
-                    for (int ks = kb * KSTEPS_PER_BLOCK; ks < ks_end; ++ks) {
+                    const int ks_beg = ks0 + kb * KSTEPS_PER_BLOCK;
+                    const int ks_end = min(ksteps, ks_beg + KSTEPS_PER_BLOCK);
+                    for (int ks = ks_beg; ks < ks_end; ++ks) {
                         if (!mbar_wait(&full[stage], phase, abort_flag, g.err)) { ok = false; break; }
                         tcgen05_fence_after();
                         const uint32_t sb = tiles_base + stage * STAGE_BYTES;
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             const uint64_t bl = make_sdesc(sb + 3 * TILE_BYTES + ko);
                             const uint64_t b2h = make_sdesc(sb + 4 * TILE_BYTES + ko);
                             const uint64_t b2l = make_sdesc(sb + 5 * TILE_BYTES + ko);
-                            const uint32_t acc0 = (ks > kb * KSTEPS_PER_BLOCK || kk > 0) ? 1u : 0u;
+                            const uint32_t acc0 = (ks > ks_beg || kk > 0) ? 1u : 0u;
                             mma_bf16(dP, ah, b2h, acc0);
                             mma_bf16(dP, al, bh, 1u);
                             mma_bf16(dQ, ah, b2l, acc0);
@@ -510,10 +523,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
             int64_t mt, nt;
             tile_coords(t, num_m, num_n, mt, nt);
+            const int kbt = (ksteps - tile_kstep0(g, mt) + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+            if (kbt <= 0) continue;   // the product is zero on this tile: C stays as it is
             uint32_t run[HC / 2];
 #pragma unroll
             for (int i = 0; i < HC / 2; ++i) run[i] = 0;
-            for (int kb = 0; kb < kblocks; ++kb, ++kbc) {
+            for (int kb = 0; kb < kbt; ++kb, ++kbc) {
                 const uint32_t buf = kbc & 1u, use = kbc >> 1;
                 if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
                 tcgen05_fence_after();
@@ -556,41 +571,50 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             if (row < g.M && col0 < g.N) {
                 const int64_t prow = g.c_rows ? (int64_t)g.c_rows[row] : row;
                 uint16_t *crow = g.C + prow * g.ldc + col0;
-                const bool vec = (col0 + HC <= g.N) && ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
-                if (vec) {
-                    // issue every load of the segment before the first store
-                    uint4 cv[HC / 8];
+                const bool aligned = (reinterpret_cast<uintptr_t>(crow) & 15u) == 0;
+                // Chunks of 8 columns: whole in-range chunks move as 16-byte
+                // vectors, a ragged or unaligned chunk element by element.
+                // Every load is issued before the first store.
+                uint4 cv[HC / 8];
 #pragma unroll
-                    for (int v = 0; v < HC / 8; ++v) cv[v] = reinterpret_cast<const uint4 *>(crow)[v];
+                for (int v = 0; v < HC / 8; ++v) {
+                    const int64_t cbase = col0 + v * 8;
+                    if (aligned && cbase + 8 <= g.N) {
+                        cv[v] = reinterpret_cast<const uint4 *>(crow)[v];
+                    } else {
+                        uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
-                    for (int v = 0; v < HC / 8; ++v) {
-                        uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            uint32_t rr = run[v * 4 + e];
-                            int c0 = (int)(w[e] & 0xFFFFu), c1 = (int)(w[e] >> 16);
-                            int r0 = (int)(rr & 0xFFFFu), r1 = (int)(rr >> 16);
-                            int o0 = g.sign > 0 ? c0 + r0 : c0 - r0;
-                            int o1 = g.sign > 0 ? c1 + r1 : c1 - r1;
-                            o0 += (o0 < 0) ? P : 0; o0 -= (o0 >= P) ? P : 0;
-                            o1 += (o1 < 0) ? P : 0; o1 -= (o1 >= P) ? P : 0;
-                            w[e] = (uint32_t)o0 | ((uint32_t)o1 << 16);
-                        }
+                        for (int e = 0; e < 8; ++e)
+                            if (cbase + e < g.N) w[e >> 1] |= (uint32_t)crow[v * 8 + e] << ((e & 1) * 16);
                         cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
                     }
+                }
 #pragma unroll
-                    for (int v = 0; v < HC / 8; ++v) reinterpret_cast<uint4 *>(crow)[v] = cv[v];
-                } else {
+                for (int v = 0; v < HC / 8; ++v) {
+                    uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
 #pragma unroll
-                    for (int j = 0; j < HC; ++j) {
-                        if (col0 + j < g.N) {
-                            int r = (int)((run[j / 2] >> ((j & 1) * 16)) & 0xFFFFu);
-                            int cc = (int)crow[j];
-                            int o = g.sign > 0 ? cc + r : cc - r;
-                            o += (o < 0) ? P : 0;
-                            o -= (o >= P) ? P : 0;
-                            crow[j] = (uint16_t)o;
-                        }
+                    for (int e = 0; e < 4; ++e) {
+                        uint32_t rr = run[v * 4 + e];
+                        int c0 = (int)(w[e] & 0xFFFFu), c1 = (int)(w[e] >> 16);
+                        int r0 = (int)(rr & 0xFFFFu), r1 = (int)(rr >> 16);
+                        int o0 = g.sign > 0 ? c0 + r0 : c0 - r0;
+                        int o1 = g.sign > 0 ? c1 + r1 : c1 - r1;
+                        o0 += (o0 < 0) ? P : 0; o0 -= (o0 >= P) ? P : 0;
+                        o1 += (o1 < 0) ? P : 0; o1 -= (o1 >= P) ? P : 0;
+                        w[e] = (uint32_t)o0 | ((uint32_t)o1 << 16);
+                    }
+                    cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+#pragma unroll
+                for (int v = 0; v < HC / 8; ++v) {
+                    const int64_t cbase = col0 + v * 8;
+                    if (aligned && cbase + 8 <= g.N) {
+                        reinterpret_cast<uint4 *>(crow)[v] = cv[v];
+                    } else {
+                        const uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (cbase + e < g.N) crow[v * 8 + e] = (uint16_t)(w[e >> 1] >> ((e & 1) * 16));
                     }
                 }
             }
@@ -659,7 +683,7 @@ static bool tc_supported() {
 
 int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
             uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
-            uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows)
+            uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows, const int32_t *row_lead)
 {
     if (M <= 0 || N <= 0 || K <= 0) return GBLA_OK;
     if (variant == GBLA_GEMM_AUTO) variant = (mp.p >= 8 && tc_supported()) ? GBLA_GEMM_TCGEN05 : GBLA_GEMM_SIMT;
@@ -690,7 +714,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     g.M = M; g.N = N; g.K = K;
     g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0; g.a_rows = (int32_t)A.rows;
     g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0; g.b_rows = (int32_t)B.rows;
-    g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.sign = sign;
+    g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.row_lead = row_lead; g.sign = sign;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);

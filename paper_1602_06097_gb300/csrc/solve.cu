@@ -18,6 +18,7 @@
 #include "internal.cuh"
 #include "solve.cuh"
 
+#include <algorithm>
 #include <vector>
 
 namespace gbla {
@@ -108,20 +109,34 @@ __global__ void __launch_bounds__(256) trsm_upper_leaf_kernel(int64_t mrows, int
     }
 }
 
+// Rows whose lead is >= bound (a prefix count, leads ascending).
+static int64_t rows_before(const TrsmUpper &T, int64_t bound)
+{
+    if (!T.lead_host) return T.mrows;
+    const auto &L = *T.lead_host;
+    return std::lower_bound(L.begin(), L.end(), (int32_t)bound) - L.begin();
+}
+
 static int trsm_upper_rec(const TrsmUpper &T, int64_t lo, int64_t hi)
 {
     if (hi - lo <= LEAF) {
-        const int64_t pairs = (T.mrows + 1) / 2;
+        // rows leading at or after hi have a zero block here (C and X alike)
+        const int64_t rows = rows_before(T, hi);
+        const int64_t pairs = (rows + 1) / 2;
+        if (pairs == 0) return GBLA_OK;
         trsm_upper_leaf_kernel<<<(unsigned)((pairs + 7) / 8), 256, 0, T.s>>>(
-            T.mrows, T.npiv, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val, T.C16, T.ldc, *T.Xp, *T.mp);
+            rows, T.npiv, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val, T.C16, T.ldc, *T.Xp, *T.mp);
         GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
     const int64_t mid = lo + round_up((hi - lo) / 2, LEAF);
     GBLA_TRY(trsm_upper_rec(T, lo, mid));
-    // C[:, mid:hi] -= X[:, lo:mid] * A[lo:mid, mid:hi]   (A^T planes: row = column of A)
-    GBLA_TRY(modgemm(*T.Xp, 0, lo, *T.At, mid, lo, T.C16 + mid, T.ldc, T.mrows, hi - mid, mid - lo, -1, *T.mp,
-                     T.variant, T.err, T.s, T.ctr));
+    // C[:, mid:hi] -= X[:, lo:mid] * A[lo:mid, mid:hi]   (A^T planes: row = column of A);
+    // only rows leading before mid have X[:, lo:mid] != 0.
+    const int64_t rows = rows_before(T, mid);
+    if (rows > 0)
+        GBLA_TRY(modgemm(*T.Xp, 0, lo, *T.At, mid, lo, T.C16 + mid, T.ldc, rows, hi - mid, mid - lo, -1, *T.mp,
+                         T.variant, T.err, T.s, T.ctr, nullptr, T.lead_dev));
     return trsm_upper_rec(T, mid, hi);
 }
 
@@ -508,7 +523,7 @@ static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_
     const int64_t n = E.n;
     if (hi - lo <= PANEL) {
         const int w = (int)(hi - lo);
-        const int64_t cs = pcol[lo];
+        const int64_t cs = pcol[lo] & ~int64_t(63);   // rows lo.. are zero left of pcol[lo]
         leaf_inverse_kernel<<<1, 128, LEAF_INV_SMEM, s>>>(R, ldr, lo, w, pcol_dev, Nm, mp);
         GBLA_CUDA_TRY(launch_check());
         GBLA_TRY(to_planes(Ap, w, w, Nm, PANEL, 0, false, nullptr, nullptr, mp, s));
@@ -519,7 +534,7 @@ static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_
     const int64_t mid = lo + round_up((hi - lo) / 2, PANEL);
     GBLA_TRY(backsub_rec(E, R, ldr, pcol_dev, pcol, mid, hi, Ap, Bp, Nm));
     // R[lo:mid] -= R[lo:mid, P_D[mid:hi]] * R[mid:hi]   (rows mid.. are zero left of P_D[mid])
-    const int64_t cs = pcol[mid];
+    const int64_t cs = pcol[mid] & ~int64_t(63);
     GBLA_TRY(to_planes(Ap, mid - lo, hi - mid, R + lo * ldr, ldr, 0, false, nullptr, pcol_dev + mid, mp, s));
     GBLA_TRY(to_planes(Bp, n - cs, hi - mid, R + mid * ldr, ldr, cs, true, nullptr, nullptr, mp, s));
     GBLA_TRY(modgemm(Ap, 0, 0, Bp, 0, 0, R + lo * ldr + cs, ldr, mid - lo, n - cs, hi - mid, -1, mp, E.variant,
@@ -571,7 +586,11 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         const int ncand = info_h[1];
         if (c0 < 0 || ncand == 0) break;
         const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
-        const int64_t nc = n - c0;
+        // Rows of S and the candidates are zero left of c0, so the products may
+        // start at the 64-aligned column c0a (they add zeros there); this keeps
+        // the C rows 16-byte aligned for the vectorised epilogue.
+        const int64_t c0a = c0 & ~int64_t(63);
+        const int64_t nc = n - c0a;
         panel_kernel<<<1, 2 * PANEL, panel_smem, s>>>(E.D16, E.ldd, c0, bw, X.cand, ncand, E.is_piv_row, X.t_dev, X.S,
                                                       X.Spos, X.pc, X.Gm, E.prow, E.pcol, rank, mp);
         if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
@@ -581,17 +600,17 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         if (t == 0) { rc = GBLA_E_INTERNAL; break; }   // a candidate always has a nonzero in the panel
         // D[S, c0:] <- G * D[S, c0:]  as  D[S] += (G - I) * D[S]
         if ((rc = to_planes(X.Gp, t, t, X.Gm, PANEL, 0, false, nullptr, nullptr, mp, s))) break;
-        if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0, true, X.S, nullptr, mp, s))) break;
-        if ((rc = modgemm(X.Gp, 0, 0, X.Bs, 0, 0, E.D16 + c0, E.ldd, t, nc, t, +1, mp, E.variant, E.err, s, E.ctr,
+        if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
+        if ((rc = modgemm(X.Gp, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, t, nc, t, +1, mp, E.variant, E.err, s, E.ctr,
                           X.S))) break;
         if (ncand > t) {
             // D[cand, c0:] -= D[cand, c0 + pc] * D[S, c0:]   (rows of S have a zero multiplier row)
-            if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0, true, X.S, nullptr, mp, s))) break;
+            if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
             Planes Hc = X.H;
             if ((rc = to_planes(Hc, ncand, t, E.D16, E.ldd, c0, false, X.cand, X.pc, mp, s))) break;
             zero_plane_rows_kernel<<<t, 128, 0, s>>>(Hc, X.Spos, X.t_dev);
             if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-            if ((rc = modgemm(Hc, 0, 0, X.Bs, 0, 0, E.D16 + c0, E.ldd, ncand, nc, t, -1, mp, E.variant, E.err, s,
+            if ((rc = modgemm(Hc, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, ncand, nc, t, -1, mp, E.variant, E.err, s,
                               E.ctr, X.cand))) break;
             row_leads_kernel<<<(unsigned)(((int64_t)ncand * 32 + 255) / 256), 256, 0, s>>>(
                 E.D16, E.ldd, n, m, X.cand, X.info + 1, c0 + bw, E.is_piv_row, X.lead);

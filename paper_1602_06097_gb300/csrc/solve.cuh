@@ -5,6 +5,8 @@
 #include "internal.cuh"
 #include "split.cuh"
 
+#include <vector>
+
 namespace gbla {
 
 // X * A = C (A unit upper triangular, npiv x npiv), X overwrites C.
@@ -20,6 +22,8 @@ struct TrsmUpper {
     uint32_t *err;
     cudaStream_t s;
     GemmCounters *ctr;
+    const int32_t *lead_dev;                 // optional: ascending lead of each row (device)
+    const std::vector<int32_t> *lead_host;   // the same on the host
 };
 int trsm_upper(const TrsmUpper &T);
 

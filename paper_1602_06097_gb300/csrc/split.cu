@@ -177,16 +177,49 @@ __global__ void row_flags_kernel(int64_t m, const int32_t *__restrict__ lead,
     flag[r] = (l >= 0 && (int64_t)(best[l] & 0xFFFFFFFFull) != r) ? 1 : 0;
 }
 
-__global__ void cd_rows_kernel(int64_t m, const int64_t *__restrict__ flag, const int64_t *__restrict__ pos,
-                               int32_t *__restrict__ cd_rows, int32_t *__restrict__ cd_index)
+// C/D rows are ordered by the permuted index of their leading column (a
+// counting sort; rows with the same lead stay in input order).  X = C*A^-1 is
+// zero left of a row's lead, so in this order the nonzeros of X, and of the
+// Schur complement, form a staircase that the products and solves skip.
+__global__ void cd_count_kernel(int64_t m, const int64_t *__restrict__ flag, const int32_t *__restrict__ lead,
+                                const int32_t *__restrict__ colmap, int64_t *__restrict__ cnt)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= m) return;
-    if (flag[r]) {
-        cd_rows[pos[r]] = (int32_t)r;
-        cd_index[r] = (int32_t)pos[r];
-    } else {
-        cd_index[r] = -1;
+    if (r < m && flag[r]) atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[colmap[lead[r]]]), 1ull);
+}
+
+__global__ void cd_scatter_kernel(int64_t m, const int64_t *__restrict__ flag, const int32_t *__restrict__ lead,
+                                  const int32_t *__restrict__ colmap, const int64_t *__restrict__ off,
+                                  int32_t *__restrict__ fill, int32_t *__restrict__ cd_rows)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m || !flag[r]) return;
+    const int64_t k = colmap[lead[r]];
+    cd_rows[off[k] + atomicAdd(&fill[k], 1)] = (int32_t)r;
+}
+
+// Sort each bucket by input row index, then index.  Buckets are small in
+// F4 matrices (a few rows share a lead); a bucket of more than 2048 rows keeps
+// the arrival order, which changes which rows become pivots of D' but not
+// the result, the reduced echelon form being unique.
+__global__ void cd_finish_kernel(int64_t npiv, const int64_t *__restrict__ off, int32_t *__restrict__ cd_rows,
+                                 int32_t *__restrict__ cd_index, int32_t *__restrict__ cd_lead)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npiv) return;
+    const int64_t b = off[k], e = off[k + 1];
+    for (int64_t i = b + 1; i < e && e - b <= 2048; ++i) {
+        const int32_t v = cd_rows[i];
+        int64_t j = i - 1;
+        while (j >= b && cd_rows[j] > v) {
+            cd_rows[j + 1] = cd_rows[j];
+            --j;
+        }
+        cd_rows[j + 1] = v;
+    }
+    for (int64_t i = b; i < e; ++i) {
+        cd_index[cd_rows[i]] = (int32_t)i;
+        cd_lead[i] = (int32_t)k;
     }
 }
 
@@ -215,7 +248,7 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
     int64_t *cflag = nullptr, *rflag = nullptr, *rpos = nullptr;
     GBLA_TRY(dalloc_t(&cflag, (size_t)n + 1, s));
     GBLA_TRY(dalloc_t(&rflag, (size_t)m + 1, s));
-    GBLA_TRY(dalloc_t(&rpos, (size_t)m + 1, s));
+    GBLA_TRY(dalloc_t(&rpos, (size_t)(m > n ? m : n) + 2, s));
     GBLA_TRY(dalloc_t(&pi->dev_counts, 2, s));
     if (n > 0) {
         col_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pi->best, cflag);
@@ -248,6 +281,7 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
     GBLA_TRY(dalloc_t(&pi->piv_row, (size_t)pi->npiv + 1, s));
     GBLA_TRY(dalloc_t(&pi->cd_rows, (size_t)pi->m_cd + 1, s));
     GBLA_TRY(dalloc_t(&pi->cd_index, (size_t)m + 1, s));
+    GBLA_TRY(dalloc_t(&pi->cd_lead, (size_t)pi->m_cd + 1, s));
     GBLA_TRY(dalloc_t(&pi->inv_lead, (size_t)pi->npiv + 1, s));
     if (n > 0) {
         colmap_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pi->best, cflag, pi->dev_counts, pi->colmap,
@@ -255,8 +289,25 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
         GBLA_CUDA_TRY(launch_check());
     }
     if (m > 0) {
-        cd_rows_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, rflag, rpos, pi->cd_rows, pi->cd_index);
+        // counting sort of the C/D rows by leading pivot column (rpos reused as counts/offsets)
+        int32_t *fill = nullptr;
+        const int64_t nk = pi->npiv + 1;
+        GBLA_TRY(dalloc_t(&fill, (size_t)nk, s));
+        GBLA_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)nk, s));
+        GBLA_CUDA_TRY(cudaMemsetAsync(rpos, 0, sizeof(int64_t) * (size_t)(nk < m + 1 ? m + 1 : nk), s));
+        GBLA_CUDA_TRY(cudaMemsetAsync(pi->cd_index, 0xFF, sizeof(int32_t) * (size_t)m, s));
+        cd_count_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, rflag, pi->lead, pi->colmap, rpos);
         GBLA_CUDA_TRY(launch_check());
+        GBLA_TRY(scan_i64(rpos, rpos, nk, nullptr, s));
+        cd_scatter_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, rflag, pi->lead, pi->colmap, rpos, fill,
+                                                                      pi->cd_rows);
+        GBLA_CUDA_TRY(launch_check());
+        if (pi->npiv > 0) {
+            cd_finish_kernel<<<(unsigned)((pi->npiv + 255) / 256), 256, 0, s>>>(pi->npiv, rpos, pi->cd_rows,
+                                                                                pi->cd_index, pi->cd_lead);
+            GBLA_CUDA_TRY(launch_check());
+        }
+        dfree(fill, s);
     }
     if (pi->npiv > 0) {
         inv_lead_kernel<<<(unsigned)((pi->npiv + 255) / 256), 256, 0, s>>>(pi->npiv, pi->piv_row, in.row_ptr, in.val,
@@ -280,6 +331,7 @@ void pivot_free(PivotInfo *pi, cudaStream_t s)
     dfree(pi->piv_row, s);
     dfree(pi->cd_rows, s);
     dfree(pi->cd_index, s);
+    dfree(pi->cd_lead, s);
     dfree(pi->inv_lead, s);
     *pi = PivotInfo();
 }

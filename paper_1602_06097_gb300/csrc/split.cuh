@@ -15,7 +15,8 @@ struct DevCSR {
 
 // Result of the pivot analysis.  Permuted column order: the npiv pivot
 // columns ascending, then the n_d other columns ascending.  Row k of A/B is
-// input row piv_row[k]; row i of C/D is input row cd_rows[i].
+// input row piv_row[k]; row i of C/D is input row cd_rows[i], C/D rows
+// ordered by leading column (cd_lead ascending), ties in input order.
 struct PivotInfo {
     int64_t m = 0, n = 0, npiv = 0, m_cd = 0, n_d = 0;
     int32_t *lead = nullptr;                 // [m] leading column or -1
@@ -27,6 +28,7 @@ struct PivotInfo {
     int32_t *piv_row = nullptr;              // [npiv] row of A -> input row
     int32_t *cd_rows = nullptr;              // [m_cd] row of C/D -> input row
     int32_t *cd_index = nullptr;             // [m] input row -> row of C/D or -1
+    int32_t *cd_lead = nullptr;              // [m_cd] permuted leading column of each C/D row (ascending)
     uint32_t *inv_lead = nullptr;            // [npiv] inverse of the pivot row's leading coefficient
 };
 
