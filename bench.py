@@ -16,6 +16,7 @@ ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -42,6 +43,8 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbla", choices=["gbla", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink rows, columns and pivots (small cases for profiling)")
     ap.add_argument("--want-reduced", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -177,7 +180,7 @@ def run_reference(a, world, rank):
 
 
 def config_of(spec, a):
-    return {"workload": a.workload, "rows": spec.m, "cols": spec.n, "designated_pivots": spec.npiv,
+    return {"workload": a.workload + ("" if a.scale == 1.0 else f"@scale{a.scale}"), "rows": spec.m, "cols": spec.n, "designated_pivots": spec.npiv,
             "p": spec.p, "density": spec.density, "run_len": list(spec.run_len),
             "groups": list(spec.group) if spec.group else None, "want_reduced": a.want_reduced,
             "l2": "inputs larger than L2 (231 MB CSR; >10 GB working set per step)",
@@ -199,8 +202,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     gbla.load()
-    spec = synth.workload(a.workload)
-    spec = synth.workload(a.workload, seed=spec.seed + 1000 * rank)
+    spec = synth.workload(a.workload) if a.scale == 1.0 else synth.scaled(a.workload, a.scale)
+    spec = dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
     rp, c, v = synth.fl_matrix(spec)
     m, n, p = spec.m, spec.n, spec.p
     d_rp = torch.from_numpy(rp).cuda()
@@ -245,7 +248,9 @@ def main():
     st0 = stats[0]
     m_cd, n_d, npiv = st0["m_cd"], st0["n_d"], st0["npiv"]
     schur_ms = float(np.mean([s["ms_schur"] for s in stats]))
-    flops = 2.0 * 4.0 * m_cd * n_d * npiv          # four bf16 digit products per modular multiply-add
+    # algorithmic flops of the Schur launch: its modular multiply-adds over the
+    # nonzero staircase of X, times four bf16 digit products of 2 flops each
+    flops = 8.0 * float(np.mean([s["schur_mod_ops"] for s in stats]))
     peaks, kind = measured_peaks()
     achieved = flops / (schur_ms / 1e3) / 1e12 if schur_ms > 0 else None
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))

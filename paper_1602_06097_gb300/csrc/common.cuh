@@ -22,6 +22,7 @@ struct ModP {
     float pf;        // (float)p
     float pinv;      // 1/p rounded to float
     uint32_t r256;   // 256 mod p
+    uint32_t r32;    // 2^32 mod p
 };
 
 inline ModP make_modp(uint32_t p) {
@@ -32,6 +33,7 @@ inline ModP make_modp(uint32_t p) {
     m.pf = (float)p;
     m.pinv = 1.0f / (float)p;
     m.r256 = 256u % p;
+    m.r32 = (uint32_t)((1ull << 32) % p);
     return m;
 }
 
@@ -51,6 +53,13 @@ __device__ __forceinline__ uint32_t mod64(uint64_t x, const ModP &m) {
     uint64_t r = x - q * (uint64_t)m.p;
     while (r >= m.p) r -= m.p;
     return (uint32_t)r;
+}
+
+// x mod p for x < 2^40 (sums of at most 256 products of residues): the high
+// byte times 2^32 mod p stays below 2^24.
+__device__ __forceinline__ uint32_t mod40(uint64_t x, const ModP &m) {
+    const uint32_t hi = (uint32_t)(x >> 32);
+    return mod32(mod32((uint32_t)x, m) + hi * m.r32, m);
 }
 
 __device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, const ModP &m) {

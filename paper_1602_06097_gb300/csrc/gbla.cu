@@ -15,6 +15,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "internal.cuh"
 #include "solve.cuh"
@@ -224,6 +226,13 @@ __global__ void transpose_u16_kernel(const uint16_t *__restrict__ src, int64_t l
 }
 
 // ------------------------------------------------------------ one call
+// Phase markers for profilers (NVTX ranges "gbla.<phase>"; no cost without
+// an attached tool).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 struct Timer {
     cudaEvent_t ev[8];
     int n = 0;
@@ -285,6 +294,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     int64_t ldc = 0, ldd = 0, ldbt = 0;
     DevCSR dc;
     std::vector<int32_t> lead_h;
+    double schur_ops = 0;
 
 #define STEP(expr)                 \
     do {                           \
@@ -325,7 +335,10 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     dc.nnz = nnz;
 
     // ---- step 1: pivots and split
-    STEP(pivot_analysis(dc, mp, &pi, err, s));
+    nvtxRangePushA("gbla.split");
+    rc = pivot_analysis(dc, mp, &pi, err, s);
+    nvtxRangePop();
+    if (rc != GBLA_OK) goto cleanup;
     npiv = pi.npiv;
     m_cd = pi.m_cd;
     n_d = pi.n_d;
@@ -364,12 +377,16 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
         CSTEP(cudaMemcpyAsync(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, cudaMemcpyDeviceToHost, s));
         CSTEP(cudaStreamSynchronize(s));
         TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr, pi.cd_lead, &lead_h};
+        NvtxRange r("gbla.trsm");
         STEP(trsm_upper(T));
     }
     tm.mark(s);  // 2
-    if (m_cd > 0 && npiv > 0 && n_d > 0)
+    if (m_cd > 0 && npiv > 0 && n_d > 0) {
+        NvtxRange r("gbla.schur");
         STEP(modgemm(Xp, 0, 0, Bt, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr, nullptr,
-                     pi.cd_lead));
+                     pi.cd_lead, lead_h.data()));
+    }
+    schur_ops = ctr.last_ops;
     tm.mark(s);  // 3
 
     // ---- step 4: RREF of D'
@@ -378,6 +395,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     STEP(dalloc_t(&pcol, (size_t)m_cd + 1, s));
     {
         EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, variant, err, s, &ctr};
+        NvtxRange r("gbla.echelon");
         STEP(echelon_d(E, &rank_d));
     }
     tm.mark(s);  // 4
@@ -501,6 +519,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
             stats->ms_total = tm.ms(0, 6);
             stats->mod_ops = ctr.mod_ops;
             stats->launches = g_launches - launches0;
+            stats->schur_mod_ops = schur_ops;
         }
     }
 

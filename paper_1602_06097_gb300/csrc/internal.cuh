@@ -6,7 +6,8 @@
 namespace gbla {
 
 struct GemmCounters {
-    double mod_ops = 0;      // dense modular multiply-adds issued (M*N*K summed)
+    double mod_ops = 0;      // algorithmic modular multiply-adds of the products
+    double last_ops = 0;     // the same for the last product
     long launches = 0;
     long tc_launches = 0;
 };
@@ -15,7 +16,8 @@ int device_sm_count();
 
 // C <- (C + sign * A * B^T) mod p, A an A-operand plane set (2 planes,
 // rows a_row0.., K from a_k0), B a B-operand plane set (4 planes, rows
-// b_row0.., K from b_k0).  With c_rows, product row r updates C row c_rows[r].
+// b_row0.., K from b_k0).  With c_rows, product row r updates C row
+// c_rows[r] (a negative entry skips the row).
 // With row_lead (ascending, absolute K index of each A row's first nonzero;
 // a_row0 must be 0), each 128-row tile starts at its first row's lead.  K
 // beyond the logical range must read zeros (zero padding) when K is not a
@@ -23,11 +25,12 @@ int device_sm_count();
 int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
             uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
             uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows = nullptr,
-            const int32_t *row_lead = nullptr);
+            const int32_t *row_lead = nullptr, const int32_t *row_lead_host = nullptr);
 
 // u16 -> digit planes (see modgemm.cu).
 int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds, int64_t col_off,
-              bool transposed, const int32_t *rgather, const int32_t *cgather, const ModP &mp, cudaStream_t s);
+              bool transposed, const int32_t *rgather, const int32_t *cgather, const ModP &mp, cudaStream_t s,
+              const int32_t *zero_if = nullptr);
 
 // Stream-ordered device allocation helpers (memory pool of the device).
 int dalloc(void **ptr, size_t bytes, cudaStream_t s);

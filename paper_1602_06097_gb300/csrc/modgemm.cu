@@ -38,11 +38,13 @@ namespace gbla {
 //   transposed == false : src[g(r) * lds + col_off + h(k)]
 //   transposed == true  : src[g(k) * lds + col_off + r]
 // with g = row gather (or identity), h = column gather (or identity); values
-// outside r < R, k < Kc are written as 0.
+// outside r < R, k < Kc, or at a negative gather index, are written as 0, and
+// (not transposed) so are source rows sr with zero_if[sr] != 0.
 template <bool TRANSPOSED>
 __global__ void to_planes_kernel(Planes dst, int64_t R, int64_t Kc, const uint16_t *__restrict__ src,
                                  int64_t lds, int64_t col_off, const int32_t *__restrict__ rgather,
-                                 const int32_t *__restrict__ cgather, uint32_t p, uint32_t r256)
+                                 const int32_t *__restrict__ cgather, const int32_t *__restrict__ zero_if,
+                                 uint32_t p, uint32_t r256)
 {
     __shared__ uint16_t tile[32][33];
     const int64_t k0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
@@ -53,8 +55,8 @@ __global__ void to_planes_kernel(Planes dst, int64_t R, int64_t Kc, const uint16
             int64_t k = k0 + i, r = r0 + tx;
             uint16_t v = 0;
             if (k < Kc && r < R) {
-                int64_t sr = rgather ? (int64_t)rgather[k] : k;
-                v = src[sr * lds + col_off + r];
+                const int64_t sr = rgather ? (int64_t)rgather[k] : k;
+                if (sr >= 0) v = src[sr * lds + col_off + r];
             }
             tile[i][tx] = v;
         }
@@ -79,9 +81,9 @@ __global__ void to_planes_kernel(Planes dst, int64_t R, int64_t Kc, const uint16
             int64_t r = r0 + i, k = k0 + tx;
             uint32_t a = 0;
             if (r < R && k < Kc) {
-                int64_t sr = rgather ? (int64_t)rgather[r] : r;
-                int64_t sc = cgather ? (int64_t)cgather[k] : k;
-                a = src[sr * lds + col_off + sc];
+                const int64_t sr = rgather ? (int64_t)rgather[r] : r;
+                const int64_t sc = cgather ? (int64_t)cgather[k] : k;
+                if (sr >= 0 && sc >= 0 && !(zero_if && zero_if[sr])) a = src[sr * lds + col_off + sc];
             }
             int hi, lo;
             digits(a, p, hi, lo);
@@ -100,7 +102,7 @@ __global__ void to_planes_kernel(Planes dst, int64_t R, int64_t Kc, const uint16
 
 int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds,
               int64_t col_off, bool transposed, const int32_t *rgather, const int32_t *cgather,
-              const ModP &mp, cudaStream_t s)
+              const ModP &mp, cudaStream_t s, const int32_t *zero_if)
 {
     if (dst.rows <= 0 || dst.kp <= 0) return GBLA_OK;
     // Cover the logical rectangle rounded up to whole 128 x 128 tiles (the
@@ -110,9 +112,11 @@ int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int
     dim3 block(32, 8);
     dim3 grid((unsigned)(ks / 32), (unsigned)(rows / 32));
     if (transposed)
-        to_planes_kernel<true><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, mp.p, mp.r256);
+        to_planes_kernel<true><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, nullptr, mp.p,
+                                                       mp.r256);
     else
-        to_planes_kernel<false><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, mp.p, mp.r256);
+        to_planes_kernel<false><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, zero_if, mp.p,
+                                                        mp.r256);
     GBLA_CUDA_TRY(launch_check());
     return GBLA_OK;
 }
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(256) modgemm_simt_kernel(Planes A, int64_t a_r
             long long v = acc[i][j] % P;
             if (v < 0) v += P;
             const int64_t pr = c_rows ? (int64_t)c_rows[r] : r;
+            if (pr < 0) continue;
             long long cur = C[pr * ldc + c];
             long long o = sign > 0 ? (cur + v) % P : (cur - v + P) % P;
             C[pr * ldc + c] = (uint16_t)o;
@@ -198,6 +203,7 @@ constexpr int KSTEPS_PER_BLOCK = 8;                 // k-block of 512: exact fp3
 constexpr int TILE_BYTES = BM * BK * 2;             // 16 KiB (A and B tiles are 128 rows)
 constexpr int STAGE_BYTES = 6 * TILE_BYTES;         // Ah Al | Bh Bl B'h B'l
 constexpr int BAR_BYTES = 256;
+constexpr int64_t GROUP_M = 8;                      // row tiles per raster group (see tile_coords)
 constexpr int EPI_WARPS = 8;                        // two drain warps per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
@@ -344,7 +350,7 @@ __device__ __forceinline__ int f2i_small(float r) {  // exact integer |r| < 2^22
 }
 
 __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t num_n, int64_t &mt, int64_t &nt) {
-    const int64_t GM = 8;
+    const int64_t GM = GROUP_M;
     int64_t group = t / (GM * num_n);
     int64_t first_m = group * GM;
     int64_t gm = num_m - first_m < GM ? num_m - first_m : GM;
@@ -354,10 +360,12 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t nu
 }
 
 // First k-step of tile row mt: A rows are zero left of their lead, and with
-// leads ascending the tile's first row has the smallest one.
+// leads ascending the first row of the tile's raster group has the smallest
+// one.  All tiles of a group start there, so the CTAs working on the group at
+// the same time walk K in step and share operand tiles in L2.
 __device__ __forceinline__ int tile_kstep0(const Args &g, int64_t mt) {
     if (!g.row_lead) return 0;
-    const int64_t k = (int64_t)g.row_lead[mt * BM] - g.a_k0;
+    const int64_t k = (int64_t)g.row_lead[(mt / GROUP_M) * GROUP_M * BM] - g.a_k0;
     return k > 0 ? (int)(k / BK) : 0;
 }
 
@@ -568,8 +576,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             // C <- (C + sign * run) mod p for this thread's row segment.
             const int64_t row = mt * BM + row_in_tile;
             const int64_t col0 = nt * BN + half * HC;
-            if (row < g.M && col0 < g.N) {
-                const int64_t prow = g.c_rows ? (int64_t)g.c_rows[row] : row;
+            const int64_t prow = (row < g.M && g.c_rows) ? (int64_t)g.c_rows[row] : row;
+            if (row < g.M && col0 < g.N && prow >= 0) {
                 uint16_t *crow = g.C + prow * g.ldc + col0;
                 const bool aligned = (reinterpret_cast<uintptr_t>(crow) & 15u) == 0;
                 // Chunks of 8 columns: whole in-range chunks move as 16-byte
@@ -683,13 +691,26 @@ static bool tc_supported() {
 
 int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
             uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
-            uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows, const int32_t *row_lead)
+            uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows, const int32_t *row_lead,
+            const int32_t *row_lead_host)
 {
     if (M <= 0 || N <= 0 || K <= 0) return GBLA_OK;
     if (variant == GBLA_GEMM_AUTO) variant = (mp.p >= 8 && tc_supported()) ? GBLA_GEMM_TCGEN05 : GBLA_GEMM_SIMT;
     if (ctr) {
         ctr->launches += 1;
-        ctr->mod_ops += (double)M * (double)N * (double)K;
+        // algorithmic multiply-adds: with known row leads, only the nonzero
+        // part of each A row counts
+        double ops = (double)M * (double)N * (double)K;
+        if (row_lead_host) {
+            double kk = 0;
+            for (int64_t i = 0; i < M; ++i) {
+                const int64_t z = (int64_t)row_lead_host[i] - a_k0;
+                kk += (double)(K - (z > 0 ? (z < K ? z : K) : 0));
+            }
+            ops = kk * (double)N;
+        }
+        ctr->mod_ops += ops;
+        ctr->last_ops = ops;
     }
     if (variant == GBLA_GEMM_SIMT) {
         dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));

@@ -23,21 +23,81 @@
 
 namespace gbla {
 
-constexpr int LEAF = 128;
+constexpr int LEAF = LEAF_COLS;
+constexpr int LEAF_WARPS = 8;
+// Shared memory of a leaf CTA: the block's multiline entries (at most 127 per
+// pair inside a block of 128 columns) as (column - j0, value) plus per-pair
+// offsets, then the warps' accumulator rows.
+constexpr int LEAF_CAP = (LEAF / 2) * (LEAF - 1);
+constexpr int LEAF_SMEM_TAB = LEAF_CAP * 5 + (LEAF / 2 + 1) * 4;
+constexpr int LEAF_SMEM_UPPER = ((LEAF_SMEM_TAB + 15) & ~15) + LEAF_WARPS * 2 * LEAF * 8;
+constexpr int LEAF_SMEM_LOWER = ((LEAF_SMEM_TAB + 15) & ~15) + LEAF_WARPS * 2 * LEAF * 4;
+
+struct LeafTab {
+    uint32_t *val;   // [LEAF_CAP]
+    uint8_t *pos;    // [LEAF_CAP] column - j0
+    int *off;        // [LEAF/2 + 1]
+};
+
+// Copy the multiline entries of the block's pivot pairs that fall inside the
+// block into shared memory (all warps of the CTA read them many times).
+__device__ __forceinline__ LeafTab load_leaf_tab(uint8_t *smem, int64_t j0, int W, const int64_t *__restrict__ mlptr,
+                                                 const int32_t *__restrict__ mlpos,
+                                                 const uint32_t *__restrict__ mlval,
+                                                 const int32_t *__restrict__ inblk)
+{
+    LeafTab T;
+    T.val = reinterpret_cast<uint32_t *>(smem);
+    T.pos = smem + LEAF_CAP * 4;
+    T.off = reinterpret_cast<int *>(smem + LEAF_CAP * 5);
+    const int npairs = (W + 1) / 2;
+    const int64_t q0 = j0 / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        // exclusive prefix of the in-block counts, two pairs per lane
+        const int a = (2 * lane < npairs) ? inblk[q0 + 2 * lane] : 0;
+        const int b = (2 * lane + 1 < npairs) ? inblk[q0 + 2 * lane + 1] : 0;
+        int incl = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int excl = incl - a - b;
+        if (2 * lane < npairs) T.off[2 * lane] = excl;
+        if (2 * lane + 1 < npairs) T.off[2 * lane + 1] = excl + a;
+        if (lane == 31) T.off[npairs] = incl;
+    }
+    __syncthreads();
+    for (int q = warp; q < npairs; q += LEAF_WARPS) {
+        const int64_t e0 = mlptr[q0 + q];
+        const int cnt = T.off[q + 1] - T.off[q];
+        for (int i = lane; i < cnt; i += 32) {
+            T.val[T.off[q] + i] = mlval[e0 + i];
+            T.pos[T.off[q] + i] = (uint8_t)(mlpos[e0 + i] - j0);
+        }
+    }
+    __syncthreads();
+    return T;
+}
 
 // ------------------------------------------------------------ upper leaf
-// X_J * A_JJ = C_J for the column block J = [j0, j0 + W), all rows, where C_J
-// already holds C_J - X_{<J} * A_{<J,J}.  X_J overwrites C_J (uint16) and is
-// written to the A-operand digit planes Xp.
-__global__ void __launch_bounds__(256) trsm_upper_leaf_kernel(int64_t mrows, int64_t npiv, int64_t j0, int W,
+// X_J * A_JJ = C_J for the column block J = [j0, j0 + W), rows [0, mrows),
+// where C_J already holds C_J - X_{<J} * A_{<J,J}.  X_J overwrites C_J
+// (uint16) and is written to the A-operand digit planes Xp.
+__global__ void __launch_bounds__(256) trsm_upper_leaf_kernel(int64_t mrows, int64_t j0, int W,
                                                               const int64_t *__restrict__ mlptr,
                                                               const int32_t *__restrict__ mlpos,
-                                                              const uint32_t *__restrict__ mlval, uint16_t *C16,
+                                                              const uint32_t *__restrict__ mlval,
+                                                              const int32_t *__restrict__ inblk, uint16_t *C16,
                                                               int64_t ldc, Planes Xp, ModP mp)
 {
-    __shared__ unsigned long long acc_s[8][2][LEAF];
+    extern __shared__ __align__(16) uint8_t leaf_smem[];
+    const LeafTab T = load_leaf_tab(leaf_smem, j0, W, mlptr, mlpos, mlval, inblk);
+    unsigned long long(*acc_s)[2][LEAF] =
+        reinterpret_cast<unsigned long long(*)[2][LEAF]>(leaf_smem + ((LEAF_SMEM_TAB + 15) & ~15));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t pair = (int64_t)blockIdx.x * 8 + warp;
+    const int64_t pair = (int64_t)blockIdx.x * LEAF_WARPS + warp;
     const int64_t r1 = 2 * pair, r2 = 2 * pair + 1;
     if (r1 >= mrows) return;
     const bool has2 = r2 < mrows;
@@ -49,21 +109,16 @@ __global__ void __launch_bounds__(256) trsm_upper_leaf_kernel(int64_t mrows, int
     __syncwarp();
     const uint64_t P = mp.p;
     for (int jl = 0; jl < W; jl += 2) {
-        const int64_t q = (j0 + jl) >> 1;
-        const int64_t e0 = mlptr[q], e1 = mlptr[q + 1];
+        const int e0 = T.off[jl >> 1], e1 = T.off[(jl >> 1) + 1];
         const bool has_b = jl + 1 < W;
-        uint32_t a01 = 0;
-        bool first_is_coupling = false;
-        if (e0 < e1 && mlpos[e0] == j0 + jl + 1) {
-            a01 = mlval[e0] & 0xFFFFu;
-            first_is_coupling = true;
-        }
-        // multipliers: lambda for row j (x?a) and row j+1 (x?b), both C rows
-        const uint32_t x1a = mod64(acc[0][jl], mp), x2a = mod64(acc[1][jl], mp);
+        const bool coupling = e0 < e1 && T.pos[e0] == jl + 1;
+        const uint32_t a01 = coupling ? (T.val[e0] & 0xFFFFu) : 0u;
+        // multipliers: lambda for pivot j (x?a) and pivot j+1 (x?b), both C rows
+        const uint32_t x1a = mod40(acc[0][jl], mp), x2a = mod40(acc[1][jl], mp);
         uint32_t x1b = 0, x2b = 0;
         if (has_b) {
-            x1b = mod64(acc[0][jl + 1] + (P - x1a) * a01, mp);
-            x2b = mod64(acc[1][jl + 1] + (P - x2a) * a01, mp);
+            x1b = mod40(acc[0][jl + 1] + (P - x1a) * a01, mp);
+            x2b = mod40(acc[1][jl + 1] + (P - x2a) * a01, mp);
         }
         __syncwarp();
         if (lane == 0) {
@@ -76,13 +131,10 @@ __global__ void __launch_bounds__(256) trsm_upper_leaf_kernel(int64_t mrows, int
         }
         // Alg. 1: both accumulator rows minus the multiline of A rows (j, j+1)
         const uint64_t n1a = P - x1a, n1b = P - x1b, n2a = P - x2a, n2b = P - x2b;
-        const int64_t lim = j0 + W;
-        for (int64_t e = e0 + (first_is_coupling ? 1 : 0) + lane; e < e1; e += 32) {
-            const int64_t k = mlpos[e];
-            if (k >= lim) break;
-            const uint32_t v = mlval[e];
+        for (int e = e0 + (coupling ? 1 : 0) + lane; e < e1; e += 32) {
+            const int kl = T.pos[e];
+            const uint32_t v = T.val[e];
             const uint64_t v1 = v & 0xFFFFu, v2 = v >> 16;
-            const int kl = (int)(k - j0);
             acc[0][kl] += n1a * v1 + n1b * v2;
             acc[1][kl] += n2a * v1 + n2b * v2;
         }
@@ -124,8 +176,9 @@ static int trsm_upper_rec(const TrsmUpper &T, int64_t lo, int64_t hi)
         const int64_t rows = rows_before(T, hi);
         const int64_t pairs = (rows + 1) / 2;
         if (pairs == 0) return GBLA_OK;
-        trsm_upper_leaf_kernel<<<(unsigned)((pairs + 7) / 8), 256, 0, T.s>>>(
-            rows, T.npiv, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val, T.C16, T.ldc, *T.Xp, *T.mp);
+        trsm_upper_leaf_kernel<<<(unsigned)((pairs + LEAF_WARPS - 1) / LEAF_WARPS), 32 * LEAF_WARPS,
+                                 LEAF_SMEM_UPPER, T.s>>>(rows, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val,
+                                                         T.ml->inblk, T.C16, T.ldc, *T.Xp, *T.mp);
         GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
@@ -136,29 +189,27 @@ static int trsm_upper_rec(const TrsmUpper &T, int64_t lo, int64_t hi)
     const int64_t rows = rows_before(T, mid);
     if (rows > 0)
         GBLA_TRY(modgemm(*T.Xp, 0, lo, *T.At, mid, lo, T.C16 + mid, T.ldc, rows, hi - mid, mid - lo, -1, *T.mp,
-                         T.variant, T.err, T.s, T.ctr, nullptr, T.lead_dev));
+                         T.variant, T.err, T.s, T.ctr, nullptr, T.lead_dev,
+                         T.lead_host ? T.lead_host->data() : nullptr));
     return trsm_upper_rec(T, mid, hi);
-}
-
-int trsm_upper(const TrsmUpper &T)
-{
-    if (T.mrows <= 0 || T.npiv <= 0) return GBLA_OK;
-    return trsm_upper_rec(T, 0, T.npiv);
 }
 
 // ------------------------------------------------------------ lower leaf
 // X'_J * A'_JJ = C'_J with A' = A^T (lower unit triangular): for j descending,
 // x'_j = c'_j - sum_{k > j} A[j][k] x'_k.  One warp per pair of C' rows; each
 // pivot pair (j, j+1) contributes two dot products with its multiline.
-__global__ void __launch_bounds__(256) trsm_lower_leaf_kernel(int64_t mrows, int64_t npiv, int64_t j0, int W,
+__global__ void __launch_bounds__(256) trsm_lower_leaf_kernel(int64_t mrows, int64_t j0, int W,
                                                               const int64_t *__restrict__ mlptr,
                                                               const int32_t *__restrict__ mlpos,
-                                                              const uint32_t *__restrict__ mlval, uint16_t *C16,
+                                                              const uint32_t *__restrict__ mlval,
+                                                              const int32_t *__restrict__ inblk, uint16_t *C16,
                                                               int64_t ldc, Planes Xp, ModP mp)
 {
-    __shared__ uint32_t xs_s[8][2][LEAF];
+    extern __shared__ __align__(16) uint8_t leaf_smem[];
+    const LeafTab T = load_leaf_tab(leaf_smem, j0, W, mlptr, mlpos, mlval, inblk);
+    uint32_t(*xs_s)[2][LEAF] = reinterpret_cast<uint32_t(*)[2][LEAF]>(leaf_smem + ((LEAF_SMEM_TAB + 15) & ~15));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t pair = (int64_t)blockIdx.x * 8 + warp;
+    const int64_t pair = (int64_t)blockIdx.x * LEAF_WARPS + warp;
     const int64_t r1 = 2 * pair, r2 = 2 * pair + 1;
     if (r1 >= mrows) return;
     const bool has2 = r2 < mrows;
@@ -169,25 +220,17 @@ __global__ void __launch_bounds__(256) trsm_lower_leaf_kernel(int64_t mrows, int
     }
     __syncwarp();
     const uint64_t P = mp.p;
-    const int64_t lim = j0 + W;
     const int start = ((W - 1) & ~1);   // local index of the last pair's first column
     for (int jl = start; jl >= 0; jl -= 2) {
-        const int64_t q = (j0 + jl) >> 1;
-        const int64_t e0 = mlptr[q], e1 = mlptr[q + 1];
+        const int e0 = T.off[jl >> 1], e1 = T.off[(jl >> 1) + 1];
         const bool has_b = jl + 1 < W;
-        uint32_t a01 = 0;
-        bool first_is_coupling = false;
-        if (e0 < e1 && mlpos[e0] == j0 + jl + 1) {
-            a01 = mlval[e0] & 0xFFFFu;
-            first_is_coupling = true;
-        }
+        const bool coupling = e0 < e1 && T.pos[e0] == jl + 1;
+        const uint32_t a01 = coupling ? (T.val[e0] & 0xFFFFu) : 0u;
         unsigned long long d1r1 = 0, d2r1 = 0, d1r2 = 0, d2r2 = 0;  // d1: A row j, d2: A row j+1
-        for (int64_t e = e0 + (first_is_coupling ? 1 : 0) + lane; e < e1; e += 32) {
-            const int64_t k = mlpos[e];
-            if (k >= lim) break;
-            const uint32_t v = mlval[e];
+        for (int e = e0 + (coupling ? 1 : 0) + lane; e < e1; e += 32) {
+            const int kl = T.pos[e];
+            const uint32_t v = T.val[e];
             const uint64_t v1 = v & 0xFFFFu, v2 = v >> 16;
-            const int kl = (int)(k - j0);
             const uint64_t y1 = xs[0][kl], y2 = xs[1][kl];
             d1r1 += v1 * y1;
             d2r1 += v2 * y1;
@@ -202,18 +245,18 @@ __global__ void __launch_bounds__(256) trsm_lower_leaf_kernel(int64_t mrows, int
             d2r2 += __shfl_xor_sync(0xFFFFFFFFu, d2r2, o);
         }
         if (lane == 0) {
-            const uint32_t s2r1 = mod64(d2r1, mp), s2r2 = mod64(d2r2, mp);
+            const uint32_t s2r1 = mod40(d2r1, mp), s2r2 = mod40(d2r2, mp);
             uint32_t xb1 = 0, xb2 = 0;
             if (has_b) {
-                xb1 = mod64((uint64_t)xs[0][jl + 1] + P - s2r1, mp);
-                xb2 = mod64((uint64_t)xs[1][jl + 1] + P - s2r2, mp);
+                xb1 = mod40((uint64_t)xs[0][jl + 1] + P - s2r1, mp);
+                xb2 = mod40((uint64_t)xs[1][jl + 1] + P - s2r2, mp);
                 xs[0][jl + 1] = xb1;
                 xs[1][jl + 1] = xb2;
             }
-            const uint64_t t1 = (uint64_t)mod64(d1r1, mp) + (uint64_t)a01 * xb1;
-            const uint64_t t2 = (uint64_t)mod64(d1r2, mp) + (uint64_t)a01 * xb2;
-            xs[0][jl] = mod64((uint64_t)xs[0][jl] + P * P - mod64(t1, mp), mp);
-            xs[1][jl] = mod64((uint64_t)xs[1][jl] + P * P - mod64(t2, mp), mp);
+            const uint64_t t1 = (uint64_t)mod40(d1r1, mp) + (uint64_t)a01 * xb1;
+            const uint64_t t2 = (uint64_t)mod40(d1r2, mp) + (uint64_t)a01 * xb2;
+            xs[0][jl] = mod40((uint64_t)xs[0][jl] + P * P - mod40(t1, mp), mp);
+            xs[1][jl] = mod40((uint64_t)xs[1][jl] + P * P - mod40(t2, mp), mp);
         }
         __syncwarp();
     }
@@ -237,12 +280,33 @@ __global__ void __launch_bounds__(256) trsm_lower_leaf_kernel(int64_t mrows, int
     }
 }
 
+static int leaf_attrs()
+{
+    static bool done = false;
+    if (!done) {
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(trsm_upper_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           LEAF_SMEM_UPPER));
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(trsm_lower_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           LEAF_SMEM_LOWER));
+        done = true;
+    }
+    return GBLA_OK;
+}
+
+int trsm_upper(const TrsmUpper &T)
+{
+    if (T.mrows <= 0 || T.npiv <= 0) return GBLA_OK;
+    GBLA_TRY(leaf_attrs());
+    return trsm_upper_rec(T, 0, T.npiv);
+}
+
 static int trsm_lower_rec(const TrsmLower &T, int64_t lo, int64_t hi)
 {
     if (hi - lo <= LEAF) {
         const int64_t pairs = (T.mrows + 1) / 2;
-        trsm_lower_leaf_kernel<<<(unsigned)((pairs + 7) / 8), 256, 0, T.s>>>(
-            T.mrows, T.npiv, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val, T.C16, T.ldc, *T.Xp, *T.mp);
+        trsm_lower_leaf_kernel<<<(unsigned)((pairs + LEAF_WARPS - 1) / LEAF_WARPS), 32 * LEAF_WARPS,
+                                 LEAF_SMEM_LOWER, T.s>>>(T.mrows, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val,
+                                                         T.ml->inblk, T.C16, T.ldc, *T.Xp, *T.mp);
         GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
@@ -257,6 +321,7 @@ static int trsm_lower_rec(const TrsmLower &T, int64_t lo, int64_t hi)
 int trsm_lower(const TrsmLower &T)
 {
     if (T.mrows <= 0 || T.npiv <= 0) return GBLA_OK;
+    GBLA_TRY(leaf_attrs());
     return trsm_lower_rec(T, 0, T.npiv);
 }
 
@@ -366,57 +431,98 @@ __global__ void __launch_bounds__(1024) candidates_kernel(int64_t m, const int32
     }
 }
 
-__global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t c0, int bw,
-                                                    const int32_t *__restrict__ cand, int ncand,
+// Inverses of all residues (0 -> 0), for the panel kernel's table.
+__global__ void inverse_table_kernel(uint16_t *__restrict__ tab, ModP mp)
+{
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < mp.p) tab[a] = (uint16_t)(a ? invmod(a, mp) : 0u);
+}
+
+constexpr size_t PANEL_SMEM = (size_t)PANEL * 2 * PANEL * sizeof(uint16_t) + 65536 * sizeof(uint16_t);
+
+__global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__ D, int64_t ldd,
+                                                    const int32_t *__restrict__ info, int64_t n,
+                                                    const int32_t *__restrict__ cand,
+                                                    const uint16_t *__restrict__ inv_tab,
                                                     int32_t *__restrict__ is_piv_row, int32_t *__restrict__ t_out,
                                                     int32_t *__restrict__ S_out, int32_t *__restrict__ Spos_out,
                                                     int32_t *__restrict__ pc_out, uint16_t *__restrict__ Gm_out,
                                                     int32_t *__restrict__ prow, int32_t *__restrict__ pcol,
-                                                    int64_t rank0, ModP mp)
+                                                    int32_t *__restrict__ rank_dev, ModP mp)
 {
-    extern __shared__ uint32_t smem_u32[];
-    uint32_t(*aug)[2 * PANEL] = reinterpret_cast<uint32_t(*)[2 * PANEL]>(smem_u32);  // [PANEL][256]
+    extern __shared__ __align__(16) uint16_t panel_smem[];
+    uint16_t(*aug)[2 * PANEL] = reinterpret_cast<uint16_t(*)[2 * PANEL]>(panel_smem);  // [PANEL][256]
+    uint16_t *inv_s = panel_smem + PANEL * 2 * PANEL;                                  // [p]
     __shared__ uint32_t cand_v[2 * PANEL];
     __shared__ uint32_t fk[PANEL];
     __shared__ int bcol[PANEL], S[PANEL], Spos[PANEL], rnk[PANEL];
-    __shared__ int cstar;
-    __shared__ uint32_t inv_s;
+    __shared__ int wmin[8];
     const int c = threadIdx.x;  // column of the augmented row: [panel | coefficients]
-    const uint64_t P = mp.p;
+    const int lane = c & 31, warp = c >> 5;
+    const int64_t c0 = info[0];
+    const int ncand = info[1];
+    const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
+    const int64_t rank0 = *rank_dev;
+    const uint32_t p = mp.p;
+    const uint64_t P = p;
+    // inverse table into shared memory (16-byte copies; p <= 65536 entries)
+    {
+        const int nvec = (int)((p + 7) / 8);
+        const uint4 *src = reinterpret_cast<const uint4 *>(inv_tab);
+        uint4 *dst = reinterpret_cast<uint4 *>(inv_s);
+        for (int i = c; i < nvec; i += 2 * PANEL) dst[i] = src[i];
+    }
     int t = 0;
+    // software pipeline: the next candidate's panel entry is loaded while the
+    // current one is processed
+    uint32_t vnext = 0;
+    if (ncand > 0 && c < bw) vnext = D[(int64_t)cand[0] * ldd + c0 + c];
     for (int ci = 0; ci < ncand && t < bw; ++ci) {
-        const int64_t i = cand[ci];
-        const uint32_t v = (c < bw) ? D[i * ldd + c0 + c] : ((c >= PANEL && c - PANEL == t) ? 1u : 0u);
+        uint32_t v = vnext;
+        if (ci + 1 < ncand && c < bw) vnext = D[(int64_t)cand[ci + 1] * ldd + c0 + c];
+        if (c >= PANEL) v = (c - PANEL == t) ? 1u : 0u;
         if (!__syncthreads_or(c < bw && v != 0)) continue;
         cand_v[c] = v;
         __syncthreads();
-        // reduce by the basis (reduced echelon: coefficient = entry at its pivot)
-        unsigned long long a = v;
-        for (int k = 0; k < t; ++k) {
-            const uint64_t coef = cand_v[bcol[k]];
-            a += (P - coef) * aug[k][c];
+        // reduce by the basis (reduced echelon: coefficient = entry at its pivot);
+        // four partial sums shorten the dependency chain
+        unsigned long long a0 = v, a1 = 0, a2 = 0, a3 = 0;
+        int k = 0;
+        for (; k + 4 <= t; k += 4) {
+            a0 += (P - cand_v[bcol[k]]) * aug[k][c];
+            a1 += (P - cand_v[bcol[k + 1]]) * aug[k + 1][c];
+            a2 += (P - cand_v[bcol[k + 2]]) * aug[k + 2][c];
+            a3 += (P - cand_v[bcol[k + 3]]) * aug[k + 3][c];
         }
-        const uint32_t nv = mod64(a, mp);
+        for (; k < t; ++k) a0 += (P - cand_v[bcol[k]]) * aug[k][c];
+        const uint32_t nv = mod40(a0 + a1 + a2 + a3, mp);
+        // leftmost nonzero of the reduced panel part
+        int mine = (c < bw && nv != 0) ? c : (1 << 30);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_xor_sync(0xFFFFFFFFu, mine, o));
+        if (lane == 0) wmin[warp] = mine;
+        cand_v[c] = nv;   // every thread has read the coefficients it needed above
         __syncthreads();
-        cand_v[c] = nv;
-        if (c == 0) cstar = 1 << 30;
-        __syncthreads();
-        if (c < bw && nv != 0) atomicMin(&cstar, c);
-        __syncthreads();
-        const int cs = cstar;
+        int cs = wmin[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) cs = min(cs, wmin[w]);
         if (cs >= bw) continue;           // dependent on the rows taken so far
-        if (c == 0) inv_s = invmod(cand_v[cs], mp);
+        const uint32_t inv = inv_s[cand_v[cs]];
         if (c < t) fk[c] = aug[c][cs];
         __syncthreads();
-        const uint32_t nrm = mulmod(nv, inv_s, mp);
-        for (int k = 0; k < t; ++k) {
-            const uint32_t f = fk[k];
-            if (f) aug[k][c] = mod64((uint64_t)aug[k][c] + (P - f) * nrm, mp);
+        const uint32_t nrm = mulmod(nv, inv, mp);
+        for (int kk = 0; kk < t; ++kk) {
+            const uint32_t f = fk[kk];
+            if (f) {
+                const uint32_t sub = mulmod(f, nrm, mp);
+                const uint32_t x = aug[kk][c];
+                aug[kk][c] = (uint16_t)(x >= sub ? x - sub : x + p - sub);
+            }
         }
-        aug[t][c] = nrm;
+        aug[t][c] = (uint16_t)nrm;
         if (c == 0) {
             bcol[t] = cs;
-            S[t] = (int)i;
+            S[t] = (int)cand[ci];
             Spos[t] = ci;
         }
         ++t;
@@ -426,42 +532,43 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
     // order the basis rows by pivot column
     if (c < t) {
         int r = 0;
-        for (int k = 0; k < t; ++k) r += (bcol[k] < bcol[c]) ? 1 : 0;
+        for (int kk = 0; kk < t; ++kk) r += (bcol[kk] < bcol[c]) ? 1 : 0;
         rnk[c] = r;
     }
     __syncthreads();
-    if (c == 0) *t_out = t;
-    if (c < t) {
-        S_out[c] = S[c];
-        Spos_out[c] = Spos[c];
-        pc_out[rnk[c]] = bcol[c];
-        is_piv_row[S[c]] = 1;
-        // the pivot with the c-th smallest column lands in physical row S[c]
+    if (c == 0) {
+        *t_out = t;
+        *rank_dev = (int32_t)(rank0 + t);
+    }
+    if (c < PANEL) {
+        // rows beyond t are sentinels (-1): the products skip them
+        S_out[c] = (c < t) ? S[c] : -1;
+        Spos_out[c] = (c < t) ? Spos[c] : -1;
+        if (c < t) {
+            pc_out[rnk[c]] = bcol[c];
+            is_piv_row[S[c]] = 1;
+        } else {
+            pc_out[c] = -1;
+        }
     }
     __syncthreads();
+    // the pivot with the c-th smallest column lands in physical row S[c]
     if (c < t) {
         prow[rank0 + c] = S[c];
         pcol[rank0 + c] = (int32_t)(c0 + pc_out[c]);
     }
-    for (int k = 0; k < t; ++k) {
-        // Gm row rnk[k] = coefficient part of basis row k minus the identity
+    for (int kk = 0; kk < PANEL; ++kk) {
+        // Gm row rnk[kk] = coefficient part of basis row kk minus the identity;
+        // rows and columns beyond t are zero
         if (c < PANEL) {
-            uint32_t g = (c < t) ? aug[k][PANEL + c] : 0u;
-            if (c == rnk[k]) g = (g + mp.p - 1) % mp.p;
-            Gm_out[rnk[k] * PANEL + c] = (uint16_t)g;
+            if (kk < t) {
+                uint32_t g = (c < t) ? aug[kk][PANEL + c] : 0u;
+                if (c == rnk[kk]) g = (g + p - 1) % p;
+                Gm_out[rnk[kk] * PANEL + c] = (uint16_t)g;
+            } else {
+                Gm_out[kk * PANEL + c] = 0;
+            }
         }
-    }
-}
-
-__global__ void zero_plane_rows_kernel(Planes H, const int32_t *__restrict__ rows, const int32_t *__restrict__ t_dev)
-{
-    const int t = *t_dev;
-    const int j = blockIdx.x;
-    if (j >= t) return;
-    const size_t off = (size_t)rows[j] * H.kp;
-    for (int k = threadIdx.x; k < H.kp; k += blockDim.x) {
-        H.plane(0)[off + k] = __float2bfloat16_rn(0.f);
-        H.plane(1)[off + k] = __float2bfloat16_rn(0.f);
     }
 }
 
@@ -481,9 +588,9 @@ __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__res
                                                            int w, const int32_t *__restrict__ pcol,
                                                            uint16_t *__restrict__ Nm, ModP mp)
 {
-    extern __shared__ uint16_t leaf_smem[];
-    uint16_t(*T)[129] = reinterpret_cast<uint16_t(*)[129]>(leaf_smem);             // [128][129]
-    uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(leaf_smem + 128 * 129);  // [128][129]
+    extern __shared__ uint16_t inv_smem[];
+    uint16_t(*T)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem);             // [128][129]
+    uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem + 128 * 129);  // [128][129]
     const int j = threadIdx.x;
     for (int i = 0; i < w; ++i)
         T[i][j] = (j < w) ? R[(lo + i) * ldr + pcol[lo + j]] : 0;
@@ -495,7 +602,7 @@ __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__res
             uint64_t acc = (i == j) ? 1 : 0;
             uint64_t sub = 0;
             for (int k = i + 1; k <= j; ++k) sub += (uint64_t)T[i][k] * Z[k][j];
-            Z[i][j] = (uint16_t)((j < i) ? 0u : mod64(acc + P * P - mod64(sub, mp), mp));
+            Z[i][j] = (uint16_t)((j < i) ? 0u : mod40(acc + P * P - mod40(sub, mp), mp));
         }
         __syncthreads();
     }
@@ -511,7 +618,7 @@ constexpr int LEAF_INV_SMEM = 2 * 128 * 129 * (int)sizeof(uint16_t);
 
 struct EchScratch {
     int32_t *info, *cand, *t_dev, *S, *Spos, *pc, *lead;
-    uint16_t *Gm;
+    uint16_t *Gm, *inv_tab;
     Planes Gp, Bs, H;
 };
 
@@ -552,7 +659,6 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     EchScratch X{};
     int rc = GBLA_OK;
     int64_t rank = 0;
-    const size_t panel_smem = (size_t)PANEL * 2 * PANEL * sizeof(uint32_t);
     int32_t info_h[2];
     GBLA_CUDA_TRY(cudaMemsetAsync(E.is_piv_row, 0, sizeof(int32_t) * (size_t)m, s));
     GBLA_TRY(dalloc_t(&X.info, 4, s));
@@ -563,12 +669,15 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     GBLA_TRY(dalloc_t(&X.pc, PANEL, s));
     GBLA_TRY(dalloc_t(&X.lead, (size_t)m + 1, s));
     GBLA_TRY(dalloc_t(&X.Gm, (size_t)PANEL * PANEL, s));
+    GBLA_TRY(dalloc_t(&X.inv_tab, 65536, s));
+    inverse_table_kernel<<<(mp.p + 255) / 256, 256, 0, s>>>(X.inv_tab, mp);
+    GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(planes_alloc(&X.Gp, PANEL, PANEL, 2, s));
     GBLA_TRY(planes_alloc(&X.Bs, n, PANEL, 4, s));
     GBLA_TRY(planes_alloc(&X.H, m, PANEL, 2, s));
     static bool attr = false;
     if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM));
         GBLA_CUDA_TRY(cudaFuncSetAttribute(leaf_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            LEAF_INV_SMEM));
         attr = true;
@@ -576,8 +685,13 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     row_leads_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(E.D16, E.ldd, n, m, nullptr, nullptr, 0,
                                                                      nullptr, X.lead);
     GBLA_CUDA_TRY(launch_check());
-    // ---- forward pass
-    while (rank < m) {
+    // ---- forward pass (one host synchronisation per panel, to size the launches)
+    int32_t *rank_dev = nullptr;
+    GBLA_TRY(dalloc_t(&rank_dev, 1, s));
+    GBLA_CUDA_TRY(cudaMemsetAsync(rank_dev, 0, sizeof(int32_t), s));
+    for (int64_t iter = 0;; ++iter) {
+        // every panel turns at least its first candidate into a pivot
+        if (iter > m) { rc = GBLA_E_INTERNAL; break; }
         candidates_kernel<<<1, 1024, 0, s>>>(m, X.lead, E.is_piv_row, X.cand, X.info);
         if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
         if (cudaMemcpyAsync(info_h, X.info, sizeof(info_h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -586,38 +700,42 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         const int ncand = info_h[1];
         if (c0 < 0 || ncand == 0) break;
         const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
+        // at most min(ncand, bw) pivots; the launches below are sized by that
+        // bound and the sentinel rows of S make the surplus a no-op
+        const int tb = ncand < bw ? ncand : bw;
         // Rows of S and the candidates are zero left of c0, so the products may
         // start at the 64-aligned column c0a (they add zeros there); this keeps
         // the C rows 16-byte aligned for the vectorised epilogue.
         const int64_t c0a = c0 & ~int64_t(63);
         const int64_t nc = n - c0a;
-        panel_kernel<<<1, 2 * PANEL, panel_smem, s>>>(E.D16, E.ldd, c0, bw, X.cand, ncand, E.is_piv_row, X.t_dev, X.S,
-                                                      X.Spos, X.pc, X.Gm, E.prow, E.pcol, rank, mp);
+        panel_kernel<<<1, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, X.info, n, X.cand, X.inv_tab, E.is_piv_row,
+                                                      X.t_dev, X.S, X.Spos, X.pc, X.Gm, E.prow, E.pcol, rank_dev, mp);
         if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        int32_t t = 0;
-        if (cudaMemcpyAsync(&t, X.t_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        if (t == 0) { rc = GBLA_E_INTERNAL; break; }   // a candidate always has a nonzero in the panel
         // D[S, c0:] <- G * D[S, c0:]  as  D[S] += (G - I) * D[S]
-        if ((rc = to_planes(X.Gp, t, t, X.Gm, PANEL, 0, false, nullptr, nullptr, mp, s))) break;
-        if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
-        if ((rc = modgemm(X.Gp, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, t, nc, t, +1, mp, E.variant, E.err, s, E.ctr,
+        if ((rc = to_planes(X.Gp, tb, tb, X.Gm, PANEL, 0, false, nullptr, nullptr, mp, s))) break;
+        if ((rc = to_planes(X.Bs, nc, tb, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
+        if ((rc = modgemm(X.Gp, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, tb, nc, tb, +1, mp, E.variant, E.err, s, E.ctr,
                           X.S))) break;
-        if (ncand > t) {
+        if (ncand > 1) {
             // D[cand, c0:] -= D[cand, c0 + pc] * D[S, c0:]   (rows of S have a zero multiplier row)
-            if ((rc = to_planes(X.Bs, nc, t, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
+            if ((rc = to_planes(X.Bs, nc, tb, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
             Planes Hc = X.H;
-            if ((rc = to_planes(Hc, ncand, t, E.D16, E.ldd, c0, false, X.cand, X.pc, mp, s))) break;
-            zero_plane_rows_kernel<<<t, 128, 0, s>>>(Hc, X.Spos, X.t_dev);
-            if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-            if ((rc = modgemm(Hc, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, ncand, nc, t, -1, mp, E.variant, E.err, s,
+            // (rows that just became pivots read as zero rows)
+            if ((rc = to_planes(Hc, ncand, tb, E.D16, E.ldd, c0, false, X.cand, X.pc, mp, s, E.is_piv_row))) break;
+            if ((rc = modgemm(Hc, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, ncand, nc, tb, -1, mp, E.variant, E.err, s,
                               E.ctr, X.cand))) break;
             row_leads_kernel<<<(unsigned)(((int64_t)ncand * 32 + 255) / 256), 256, 0, s>>>(
                 E.D16, E.ldd, n, m, X.cand, X.info + 1, c0 + bw, E.is_piv_row, X.lead);
             if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
         }
-        rank += t;
     }
+    {
+        int32_t r32 = 0;
+        if (cudaMemcpyAsync(&r32, rank_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
+        rank = r32;
+    }
+    dfree(rank_dev, s);
     // ---- backward pass: RREF rows into R (pivot column order)
     if (rc == GBLA_OK && rank > 0) {
         const int64_t ldr = E.ldd;
@@ -649,6 +767,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     dfree(X.pc, s);
     dfree(X.lead, s);
     dfree(X.Gm, s);
+    dfree(X.inv_tab, s);
     planes_free(&X.Gp, s);
     planes_free(&X.Bs, s);
     planes_free(&X.H, s);

@@ -423,7 +423,8 @@ __global__ void multiline_kernel(int64_t npairs, int64_t npiv, const int32_t *__
                                  const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                  const uint16_t *__restrict__ val, const int32_t *__restrict__ colmap,
                                  const uint32_t *__restrict__ inv_lead, int64_t *__restrict__ cnt_or_ptr,
-                                 int32_t *__restrict__ ml_pos, uint32_t *__restrict__ ml_val, ModP mp)
+                                 int32_t *__restrict__ ml_pos, uint32_t *__restrict__ ml_val,
+                                 int32_t *__restrict__ inblk, ModP mp)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= npairs) return;
@@ -433,6 +434,8 @@ __global__ void multiline_kernel(int64_t npairs, int64_t npiv, const int32_t *__
     const uint32_t inv1 = inv_lead[2 * q];
     const uint32_t inv2 = (2 * q + 1 < npiv) ? inv_lead[2 * q + 1] : 0;
     int64_t i1 = b1, i2 = b2, out = FILL ? cnt_or_ptr[q] : 0;
+    const int64_t blk_end = (2 * q / LEAF_COLS + 1) * LEAF_COLS;
+    int32_t n_in = 0;
     // only entries in pivot columns (A part); both rows are sorted by column
     while (true) {
         int64_t c1 = INT64_MAX, c2 = INT64_MAX;
@@ -455,9 +458,11 @@ __global__ void multiline_kernel(int64_t npairs, int64_t npiv, const int32_t *__
             ml_pos[out] = (int32_t)c;
             ml_val[out] = v1 | (v2 << 16);
         }
+        n_in += (c < blk_end) ? 1 : 0;
         ++out;
     }
     if (!FILL) cnt_or_ptr[q] = out;
+    else inblk[q] = n_in;
 }
 
 int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const ModP &mp, cudaStream_t s)
@@ -473,7 +478,7 @@ int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const 
     }
     const unsigned nb = (unsigned)((npairs + 127) / 128);
     multiline_kernel<false><<<nb, 128, 0, s>>>(npairs, pi.npiv, pi.piv_row, in.row_ptr, in.col, in.val, pi.colmap,
-                                               pi.inv_lead, ml->ptr, nullptr, nullptr, mp);
+                                               pi.inv_lead, ml->ptr, nullptr, nullptr, nullptr, mp);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(scan_i64(ml->ptr, ml->ptr, npairs, ml->ptr + npairs, s));
     int64_t total = 0;
@@ -482,8 +487,9 @@ int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const 
     ml->total = total;
     GBLA_TRY(dalloc_t(&ml->pos, (size_t)total + 1, s));
     GBLA_TRY(dalloc_t(&ml->val, (size_t)total + 1, s));
+    GBLA_TRY(dalloc_t(&ml->inblk, (size_t)npairs + 1, s));
     multiline_kernel<true><<<nb, 128, 0, s>>>(npairs, pi.npiv, pi.piv_row, in.row_ptr, in.col, in.val, pi.colmap,
-                                              pi.inv_lead, ml->ptr, ml->pos, ml->val, mp);
+                                              pi.inv_lead, ml->ptr, ml->pos, ml->val, ml->inblk, mp);
     GBLA_CUDA_TRY(launch_check());
     return GBLA_OK;
 }
@@ -493,6 +499,7 @@ void multiline_free(Multiline *ml, cudaStream_t s)
     dfree(ml->ptr, s);
     dfree(ml->pos, s);
     dfree(ml->val, s);
+    dfree(ml->inblk, s);
     *ml = Multiline();
 }
 

@@ -35,11 +35,15 @@ struct PivotInfo {
 // 2-multiline storage of A (Definition 1): pair q = A rows 2q, 2q+1, entries
 // at permuted pivot columns excluding each row's unit diagonal.  val packs
 // row 2q's value in the low 16 bits and row 2q+1's in the high 16 bits.
+// Column blocks of the blocked triangular solves.
+constexpr int LEAF_COLS = 128;
+
 struct Multiline {
     int64_t npairs = 0, total = 0;
     int64_t *ptr = nullptr;    // [npairs + 1]
     int32_t *pos = nullptr;    // [total]
     uint32_t *val = nullptr;   // [total]
+    int32_t *inblk = nullptr;  // [npairs] entries of pair q inside its own column block of LEAF_COLS
 };
 
 int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *err, cudaStream_t s);

@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
                 ("rank_d", ctypes.c_int64), ("ms_split", ctypes.c_double), ("ms_trsm", ctypes.c_double),
                 ("ms_schur", ctypes.c_double), ("ms_echelon", ctypes.c_double),
                 ("ms_backsub", ctypes.c_double), ("ms_output", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("mod_ops", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("ms_total", ctypes.c_double), ("mod_ops", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("schur_mod_ops", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
