@@ -16,7 +16,7 @@
 // k-block the accumulators are drained from TMEM, reduced mod p and added to
 // a running residue kept in registers.  The kernel is a persistent,
 // warp-specialised tcgen05 pipeline: one thread issues TMA loads into a
-// 2-stage shared-memory ring, one thread issues tcgen05.mma into a
+// 4-stage shared-memory ring, one thread issues tcgen05.mma into a
 // double-buffered TMEM accumulator pair, eight warps drain TMEM.
 //
 // SIMT path: exact int64 dot products on CUDA cores, used as the reference
@@ -197,10 +197,10 @@ __global__ void __launch_bounds__(256) modgemm_simt_kernel(Planes A, int64_t a_r
 // tcgen05 / TMA GEMM
 // ===================================================================
 namespace tc {
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 2;
-constexpr int KSTEPS_PER_BLOCK = 8;                 // k-block of 512: exact fp32 sums
-constexpr int TILE_BYTES = BM * BK * 2;             // 16 KiB (A and B tiles are 128 rows)
+constexpr int BM = 128, BN = 128, BK = 32;         // K step of 32 bf16 = 64-byte rows
+constexpr int STAGES = 4;
+constexpr int KSTEPS_PER_BLOCK = 512 / BK;          // k-block of 512: exact fp32 sums
+constexpr int TILE_BYTES = BM * BK * 2;             // 8 KiB (A and B tiles are 128 rows)
 constexpr int STAGE_BYTES = 6 * TILE_BYTES;         // Ah Al | Bh Bl B'h B'l
 constexpr int BAR_BYTES = 256;
 constexpr int64_t GROUP_M = 8;                      // row tiles per raster group (see tile_coords)
@@ -294,18 +294,18 @@ __device__ __forceinline__ void tcgen05_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand tile of 128 rows x 64 bf16
-// (128-byte rows) loaded by TMA with 128-byte swizzle.  8-row swizzle atoms
-// are 1024 bytes apart (stride byte offset); the leading byte offset is unused
-// for swizzled K-major tiles.  Layout type 2 = 128-byte swizzle; bit 46 is the
+// Shared-memory matrix descriptor: K-major operand tile of 128 rows x 32 bf16
+// (64-byte rows) loaded by TMA with 64-byte swizzle.  8-row swizzle atoms
+// are 512 bytes apart (stride byte offset); the leading byte offset is unused
+// for swizzled K-major tiles.  Layout type 4 = 64-byte swizzle; bit 46 is the
 // fixed descriptor version of sm_100-family tcgen05.
 __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;                 // leading byte offset (16 B, unused)
-    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)((8 * BK * 2) >> 4) << 32;   // stride byte offset: 8 rows
     d |= (uint64_t)1 << 46;                 // descriptor version
-    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    d |= (uint64_t)4 << 61;                 // 64-byte swizzle
     return d;
 }
 
@@ -661,7 +661,7 @@ static int make_map(CUtensorMap *map, const Planes &pl) {
     cuuint32_t box[2] = {tc::BK, tc::BM};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)pl.ptr, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? GBLA_OK : GBLA_E_CUDA;
 }

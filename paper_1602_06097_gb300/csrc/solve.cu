@@ -583,11 +583,18 @@ __global__ void gather_rows_kernel(const uint16_t *__restrict__ D, int64_t ldd, 
     }
 }
 
-// Nm = I - T^-1 for T = R[lo + i][pcol[lo + j]] (w x w, unit upper triangular).
-__global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__restrict__ R, int64_t ldr, int64_t lo,
-                                                           int w, const int32_t *__restrict__ pcol,
-                                                           uint16_t *__restrict__ Nm, ModP mp)
+// For every diagonal block b of 128 rows: Nm_b = I - T^-1 with
+// T = R[lo + i][pcol[lo + j]], lo = 128 b (w x w, unit upper triangular).
+// The off-diagonal updates of the back-substitution only touch columns at or
+// right of the next block's pivots, so these blocks are final from the start
+// and all inverses are formed in one launch.
+__global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__restrict__ R, int64_t ldr, int64_t rank,
+                                                           const int32_t *__restrict__ pcol,
+                                                           uint16_t *__restrict__ Nm_all, ModP mp)
 {
+    const int64_t lo = (int64_t)blockIdx.x * 128;
+    const int w = (int)((rank - lo) < 128 ? (rank - lo) : 128);
+    uint16_t *Nm = Nm_all + (size_t)blockIdx.x * PANEL * PANEL;
     extern __shared__ uint16_t inv_smem[];
     uint16_t(*T)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem);             // [128][129]
     uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem + 128 * 129);  // [128][129]
@@ -623,30 +630,31 @@ struct EchScratch {
 };
 
 static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_t *pcol_dev,
-                       const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &Bp, uint16_t *Nm)
+                       const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &Bp,
+                       const uint16_t *Nm_all)
 {
     const ModP &mp = *E.mp;
     cudaStream_t s = E.s;
     const int64_t n = E.n;
     if (hi - lo <= PANEL) {
+        // leaves are the 128-row blocks (splits fall on multiples of 128)
         const int w = (int)(hi - lo);
         const int64_t cs = pcol[lo] & ~int64_t(63);   // rows lo.. are zero left of pcol[lo]
-        leaf_inverse_kernel<<<1, 128, LEAF_INV_SMEM, s>>>(R, ldr, lo, w, pcol_dev, Nm, mp);
-        GBLA_CUDA_TRY(launch_check());
+        const uint16_t *Nm = Nm_all + (size_t)(lo / PANEL) * PANEL * PANEL;
         GBLA_TRY(to_planes(Ap, w, w, Nm, PANEL, 0, false, nullptr, nullptr, mp, s));
         GBLA_TRY(to_planes(Bp, n - cs, w, R + lo * ldr, ldr, cs, true, nullptr, nullptr, mp, s));
         return modgemm(Ap, 0, 0, Bp, 0, 0, R + lo * ldr + cs, ldr, w, n - cs, w, -1, mp, E.variant, E.err, s,
                        E.ctr);
     }
     const int64_t mid = lo + round_up((hi - lo) / 2, PANEL);
-    GBLA_TRY(backsub_rec(E, R, ldr, pcol_dev, pcol, mid, hi, Ap, Bp, Nm));
+    GBLA_TRY(backsub_rec(E, R, ldr, pcol_dev, pcol, mid, hi, Ap, Bp, Nm_all));
     // R[lo:mid] -= R[lo:mid, P_D[mid:hi]] * R[mid:hi]   (rows mid.. are zero left of P_D[mid])
     const int64_t cs = pcol[mid] & ~int64_t(63);
     GBLA_TRY(to_planes(Ap, mid - lo, hi - mid, R + lo * ldr, ldr, 0, false, nullptr, pcol_dev + mid, mp, s));
     GBLA_TRY(to_planes(Bp, n - cs, hi - mid, R + mid * ldr, ldr, cs, true, nullptr, nullptr, mp, s));
     GBLA_TRY(modgemm(Ap, 0, 0, Bp, 0, 0, R + lo * ldr + cs, ldr, mid - lo, n - cs, hi - mid, -1, mp, E.variant,
                      E.err, s, E.ctr));
-    return backsub_rec(E, R, ldr, pcol_dev, pcol, lo, mid, Ap, Bp, Nm);
+    return backsub_rec(E, R, ldr, pcol_dev, pcol, lo, mid, Ap, Bp, Nm_all);
 }
 
 int echelon_d(const EchelonD &E, int64_t *rank_out)
@@ -751,7 +759,12 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
         if (rc == GBLA_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
-        if (rc == GBLA_OK) rc = dalloc_t(&Nm, (size_t)PANEL * PANEL, s);
+        const int64_t nleaves = (rank + PANEL - 1) / PANEL;
+        if (rc == GBLA_OK) rc = dalloc_t(&Nm, (size_t)nleaves * PANEL * PANEL, s);
+        if (rc == GBLA_OK) {
+            leaf_inverse_kernel<<<(unsigned)nleaves, 128, LEAF_INV_SMEM, s>>>(E.R[0], ldr, rank, E.pcol, Nm, mp);
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+        }
         if (rc == GBLA_OK) rc = planes_alloc(&Ap, rank, rank < 2 * PANEL ? PANEL : rank, 2, s);
         if (rc == GBLA_OK) rc = planes_alloc(&Bp, n, rank < 2 * PANEL ? PANEL : rank, 4, s);
         if (rc == GBLA_OK) rc = backsub_rec(E, E.R[0], ldr, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm);
