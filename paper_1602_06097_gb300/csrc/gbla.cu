@@ -286,6 +286,7 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     Multiline ml;
     Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{};
     uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
+    uint16_t *A16 = nullptr, *B16 = nullptr;
     int32_t *is_piv_row = nullptr, *prow = nullptr, *pcol = nullptr;
     int64_t *outflag = nullptr, *outpos = nullptr, *cnt = nullptr, *orp = nullptr;
     int32_t *ocol = nullptr;
@@ -345,27 +346,40 @@ static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *op
     ldc = round_up(npiv > 0 ? npiv : 1, 64);
     ldd = round_up(n_d > 0 ? n_d : 1, 64);
     ldbt = ldc;
-    if (m_cd > 0 && npiv > 0) {
-        STEP(planes_alloc(&At, npiv, npiv, 4, s));
-        STEP(planes_zero(At, s));
-    }
-    if (want_reduced && npiv > 0 && n_d > 0) {
-        STEP(planes_alloc(&Arow, npiv, npiv, 4, s));
-        STEP(planes_zero(Arow, s));
-        STEP(dalloc_t(&Bt16, (size_t)n_d * (size_t)ldbt, s));
-        CSTEP(cudaMemsetAsync(Bt16, 0, sizeof(uint16_t) * (size_t)n_d * (size_t)ldbt, s));
-    }
-    if (m_cd > 0 && n_d > 0 && npiv > 0) {
-        STEP(planes_alloc(&Bt, n_d, npiv, 4, s));
-        STEP(planes_zero(Bt, s));
-    }
+    // dense uint16 blocks: A, B (pivot rows, normalised), C, D (other rows)
+    STEP(dalloc_t(&A16, (size_t)(npiv > 0 ? npiv : 1) * (size_t)ldc, s));
+    STEP(dalloc_t(&B16, (size_t)(npiv > 0 ? npiv : 1) * (size_t)ldd, s));
     STEP(dalloc_t(&C16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldc, s));
     STEP(dalloc_t(&D16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldd, s));
+    if (npiv > 0) {
+        CSTEP(cudaMemsetAsync(A16, 0, sizeof(uint16_t) * (size_t)npiv * (size_t)ldc, s));
+        CSTEP(cudaMemsetAsync(B16, 0, sizeof(uint16_t) * (size_t)npiv * (size_t)ldd, s));
+    }
     if (m_cd > 0) {
         CSTEP(cudaMemsetAsync(C16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldc, s));
         CSTEP(cudaMemsetAsync(D16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldd, s));
     }
-    STEP(split_scatter(dc, pi, At, Arow, Bt, Bt16, ldbt, C16, ldc, D16, ldd, mp, s));
+    STEP(split_scatter(dc, pi, A16, ldc, B16, ldd, C16, ldc, D16, ldd, mp, s));
+    // digit planes of the operands the products read
+    if (m_cd > 0 && npiv > 0) {
+        STEP(planes_alloc(&At, npiv, npiv, 4, s));   // A^T: B-operand of C <- C - X*A
+        STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s));
+    }
+    if (m_cd > 0 && n_d > 0 && npiv > 0) {
+        STEP(planes_alloc(&Bt, n_d, npiv, 4, s));    // B^T: B-operand of D <- D - X*B
+        STEP(to_planes(Bt, n_d, npiv, B16, ldd, 0, true, nullptr, nullptr, mp, s));
+    }
+    if (want_reduced && npiv > 0 && n_d > 0) {
+        STEP(planes_alloc(&Arow, npiv, npiv, 4, s)); // A: B-operand of the second pass
+        STEP(to_planes(Arow, npiv, npiv, A16, ldc, 0, false, nullptr, nullptr, mp, s));
+        STEP(dalloc_t(&Bt16, (size_t)n_d * (size_t)ldbt, s));
+        dim3 grid((unsigned)((n_d + 31) / 32), (unsigned)((npiv + 31) / 32));
+        transpose_u16_kernel<<<grid, dim3(32, 8), 0, s>>>(B16, ldd, npiv, n_d, Bt16, ldbt);
+        CSTEP(launch_check());
+    }
+    dfree(A16, s);
+    dfree(B16, s);
+    A16 = B16 = nullptr;
     STEP(multiline_build(dc, pi, &ml, mp, s));
     tm.mark(s);  // 1
 
@@ -537,6 +551,8 @@ cleanup:
     planes_free(&Xq, s);
     planes_free(&RdT, s);
     planes_free(&XpdT, s);
+    dfree(A16, s);
+    dfree(B16, s);
     dfree(C16, s);
     dfree(D16, s);
     dfree(Bt16, s);

@@ -454,8 +454,8 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
     uint16_t(*aug)[2 * PANEL] = reinterpret_cast<uint16_t(*)[2 * PANEL]>(panel_smem);  // [PANEL][256]
     uint16_t *inv_s = panel_smem + PANEL * 2 * PANEL;                                  // [p]
     __shared__ uint32_t cand_v[2 * PANEL];
-    __shared__ uint32_t fk[PANEL];
-    __shared__ int bcol[PANEL], S[PANEL], Spos[PANEL], rnk[PANEL];
+    __shared__ uint32_t fk[PANEL], coef[PANEL];
+    __shared__ int bcol[PANEL], brow[PANEL], S[PANEL], Spos[PANEL], rnk[PANEL];
     __shared__ int wmin[8];
     const int c = threadIdx.x;  // column of the augmented row: [panel | coefficients]
     const int lane = c & 31, warp = c >> 5;
@@ -464,7 +464,6 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
     const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
     const int64_t rank0 = *rank_dev;
     const uint32_t p = mp.p;
-    const uint64_t P = p;
     // inverse table into shared memory (16-byte copies; p <= 65536 entries)
     {
         const int nvec = (int)((p + 7) / 8);
@@ -472,6 +471,8 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
         uint4 *dst = reinterpret_cast<uint4 *>(inv_s);
         for (int i = c; i < nvec; i += 2 * PANEL) dst[i] = src[i];
     }
+    if (c < PANEL) brow[c] = -1;     // basis row whose pivot is panel column c
+    __syncthreads();
     int t = 0;
     // software pipeline: the next candidate's panel entry is loaded while the
     // current one is processed
@@ -481,27 +482,26 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
         uint32_t v = vnext;
         if (ci + 1 < ncand && c < bw) vnext = D[(int64_t)cand[ci + 1] * ldd + c0 + c];
         if (c >= PANEL) v = (c - PANEL == t) ? 1u : 0u;
+        // the basis is in reduced echelon form, so the multiplier of basis
+        // row k is this candidate's entry at that row's pivot column
+        if (c < bw && brow[c] >= 0) coef[brow[c]] = p - v;
         if (!__syncthreads_or(c < bw && v != 0)) continue;
-        cand_v[c] = v;
-        __syncthreads();
-        // reduce by the basis (reduced echelon: coefficient = entry at its pivot);
-        // four partial sums shorten the dependency chain
-        unsigned long long a0 = v, a1 = 0, a2 = 0, a3 = 0;
+        unsigned long long a0 = v, a1 = 0, a2 = 0, a3 = 0;   // four chains
         int k = 0;
         for (; k + 4 <= t; k += 4) {
-            a0 += (P - cand_v[bcol[k]]) * aug[k][c];
-            a1 += (P - cand_v[bcol[k + 1]]) * aug[k + 1][c];
-            a2 += (P - cand_v[bcol[k + 2]]) * aug[k + 2][c];
-            a3 += (P - cand_v[bcol[k + 3]]) * aug[k + 3][c];
+            a0 += (uint64_t)coef[k] * aug[k][c];
+            a1 += (uint64_t)coef[k + 1] * aug[k + 1][c];
+            a2 += (uint64_t)coef[k + 2] * aug[k + 2][c];
+            a3 += (uint64_t)coef[k + 3] * aug[k + 3][c];
         }
-        for (; k < t; ++k) a0 += (P - cand_v[bcol[k]]) * aug[k][c];
+        for (; k < t; ++k) a0 += (uint64_t)coef[k] * aug[k][c];
         const uint32_t nv = mod40(a0 + a1 + a2 + a3, mp);
         // leftmost nonzero of the reduced panel part
         int mine = (c < bw && nv != 0) ? c : (1 << 30);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_xor_sync(0xFFFFFFFFu, mine, o));
         if (lane == 0) wmin[warp] = mine;
-        cand_v[c] = nv;   // every thread has read the coefficients it needed above
+        cand_v[c] = nv;
         __syncthreads();
         int cs = wmin[0];
 #pragma unroll
@@ -520,6 +520,7 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
             }
         }
         aug[t][c] = (uint16_t)nrm;
+        if (c == cs) brow[c] = t;
         if (c == 0) {
             bcol[t] = cs;
             S[t] = (int)cand[ci];

@@ -337,28 +337,17 @@ void pivot_free(PivotInfo *pi, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------- (a3)
-__device__ __forceinline__ void put4(const Planes &pl, int64_t row, int64_t k, uint32_t v, const ModP &mp)
-{
-    int hi, lo;
-    const size_t off = (size_t)row * (size_t)pl.kp + (size_t)k;
-    digits(v, mp.p, hi, lo);
-    pl.plane(0)[off] = i2bf(hi);
-    pl.plane(1)[off] = i2bf(lo);
-    digits(mulmod(v, mp.r256, mp), mp.p, hi, lo);
-    pl.plane(2)[off] = i2bf(hi);
-    pl.plane(3)[off] = i2bf(lo);
-}
-
 // One warp per input row.  Pivot rows are normalised by the inverse of their
-// leading coefficient and go to A (A^T planes, and A row-major planes when
-// the reduced form is requested) and B (B^T planes, and B^T as uint16 when the
-// reduced form is requested); other rows go to C and D (uint16 row-major).
+// leading coefficient and go to A (pivot columns) and B (other columns);
+// other rows go to C and D.  All four blocks are dense uint16 row-major here;
+// the digit planes the tensor-core product reads are made from A and B by a
+// tiled transposing conversion (coalesced on both sides).
 __global__ void split_scatter_kernel(int64_t m, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                      const uint16_t *__restrict__ val, const int32_t *__restrict__ lead,
                                      const unsigned long long *__restrict__ best, const int32_t *__restrict__ colmap,
                                      const int32_t *__restrict__ cd_index, const uint32_t *__restrict__ inv_lead,
-                                     int64_t npiv, Planes At, Planes Arow, Planes Bt, uint16_t *__restrict__ Bt16,
-                                     int64_t ldbt16, uint16_t *__restrict__ C16, int64_t ldc, uint16_t *__restrict__ D16,
+                                     int64_t npiv, uint16_t *__restrict__ A16, int64_t lda, uint16_t *__restrict__ B16,
+                                     int64_t ldb, uint16_t *__restrict__ C16, int64_t ldc, uint16_t *__restrict__ D16,
                                      int64_t ldd, ModP mp)
 {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -373,14 +362,9 @@ __global__ void split_scatter_kernel(int64_t m, const int64_t *__restrict__ row_
         const uint32_t inv = inv_lead[k];
         for (int64_t i = b + lane; i < e; i += 32) {
             const int64_t c = colmap[col[i]];
-            const uint32_t v = mulmod(val[i], inv, mp);
-            if (c < npiv) {
-                if (At.ptr) put4(At, c, k, v, mp);
-                if (Arow.ptr) put4(Arow, k, c, v, mp);
-            } else {
-                if (Bt.ptr) put4(Bt, c - npiv, k, v, mp);
-                if (Bt16) Bt16[(c - npiv) * ldbt16 + k] = (uint16_t)v;
-            }
+            const uint16_t v = (uint16_t)mulmod(val[i], inv, mp);
+            if (c < npiv) A16[k * lda + c] = v;
+            else B16[k * ldb + (c - npiv)] = v;
         }
     } else {
         const int64_t i_cd = cd_index[r];
@@ -392,15 +376,14 @@ __global__ void split_scatter_kernel(int64_t m, const int64_t *__restrict__ row_
     }
 }
 
-int split_scatter(const DevCSR &in, const PivotInfo &pi, const Planes &At, const Planes &Arow, const Planes &Bt,
-                  uint16_t *Bt16, int64_t ldbt16, uint16_t *C16, int64_t ldc, uint16_t *D16, int64_t ldd,
-                  const ModP &mp, cudaStream_t s)
+int split_scatter(const DevCSR &in, const PivotInfo &pi, uint16_t *A16, int64_t lda, uint16_t *B16, int64_t ldb,
+                  uint16_t *C16, int64_t ldc, uint16_t *D16, int64_t ldd, const ModP &mp, cudaStream_t s)
 {
     if (in.m <= 0) return GBLA_OK;
     const int64_t threads = in.m * 32;
     split_scatter_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        in.m, in.row_ptr, in.col, in.val, pi.lead, pi.best, pi.colmap, pi.cd_index, pi.inv_lead, pi.npiv, At, Arow,
-        Bt, Bt16, ldbt16, C16, ldc, D16, ldd, mp);
+        in.m, in.row_ptr, in.col, in.val, pi.lead, pi.best, pi.colmap, pi.cd_index, pi.inv_lead, pi.npiv, A16, lda,
+        B16, ldb, C16, ldc, D16, ldd, mp);
     GBLA_CUDA_TRY(launch_check());
     return GBLA_OK;
 }
@@ -436,7 +419,10 @@ __global__ void multiline_kernel(int64_t npairs, int64_t npiv, const int32_t *__
     int64_t i1 = b1, i2 = b2, out = FILL ? cnt_or_ptr[q] : 0;
     const int64_t blk_end = (2 * q / LEAF_COLS + 1) * LEAF_COLS;
     int32_t n_in = 0;
-    // only entries in pivot columns (A part); both rows are sorted by column
+    // Only entries in pivot columns inside the pair's own diagonal block of
+    // A: the sparse solves apply exactly these; everything right of the block
+    // goes through the dense products.  Both rows are sorted by column, and
+    // the permuted pivot columns keep the input order.
     while (true) {
         int64_t c1 = INT64_MAX, c2 = INT64_MAX;
         while (i1 < e1) {
@@ -449,6 +435,8 @@ __global__ void multiline_kernel(int64_t npairs, int64_t npiv, const int32_t *__
             if (c < npiv) { c2 = c; break; }
             ++i2;
         }
+        if (c1 >= blk_end) c1 = INT64_MAX;
+        if (c2 >= blk_end) c2 = INT64_MAX;
         if (c1 == INT64_MAX && c2 == INT64_MAX) break;
         const int64_t c = c1 < c2 ? c1 : c2;
         uint32_t v1 = 0, v2 = 0;

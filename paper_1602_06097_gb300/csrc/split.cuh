@@ -32,8 +32,9 @@ struct PivotInfo {
     uint32_t *inv_lead = nullptr;            // [npiv] inverse of the pivot row's leading coefficient
 };
 
-// 2-multiline storage of A (Definition 1): pair q = A rows 2q, 2q+1, entries
-// at permuted pivot columns excluding each row's unit diagonal.  val packs
+// 2-multiline storage of the diagonal blocks of A (Definition 1): pair q =
+// A rows 2q, 2q+1, entries at permuted pivot columns inside the pair's own
+// block of LEAF_COLS columns, excluding each row's unit diagonal.  val packs
 // row 2q's value in the low 16 bits and row 2q+1's in the high 16 bits.
 // Column blocks of the blocked triangular solves.
 constexpr int LEAF_COLS = 128;
@@ -49,9 +50,8 @@ struct Multiline {
 int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *err, cudaStream_t s);
 void pivot_free(PivotInfo *pi, cudaStream_t s);
 
-int split_scatter(const DevCSR &in, const PivotInfo &pi, const Planes &At, const Planes &Arow, const Planes &Bt,
-                  uint16_t *Bt16, int64_t ldbt16, uint16_t *C16, int64_t ldc, uint16_t *D16, int64_t ldd,
-                  const ModP &mp, cudaStream_t s);
+int split_scatter(const DevCSR &in, const PivotInfo &pi, uint16_t *A16, int64_t lda, uint16_t *B16, int64_t ldb,
+                  uint16_t *C16, int64_t ldc, uint16_t *D16, int64_t ldd, const ModP &mp, cudaStream_t s);
 
 int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const ModP &mp, cudaStream_t s);
 void multiline_free(Multiline *ml, cudaStream_t s);
