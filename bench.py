@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "F4 matrices reduced/sec and modular GOPS vs roofline, batched vs plain, bit-exact"
 UNIT = "matrices/s"
 WORKLOAD = "fl_40000x60000"
-CPU_SAMPLE_ROWS = 600
+CPU_SAMPLE_ROWS = 1500
 
 
 def args_parse():
@@ -111,6 +111,23 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profiled_traffic():
+    """DRAM bytes per Schur launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "modgemm_tc_schur_traffic_fl_40000x60000.md")).read()
+        src = open(os.path.join(ROOT, "paper_1602_06097_gb300", "csrc", "modgemm.cu"), "rb").read()
+    except OSError:
+        return None
+    m1 = re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt)
+    m2 = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
+    if not (m1 and m2) or hashlib.sha256(src).hexdigest() != m2.group(1):
+        return None
+    return int(m1.group(1))
 
 
 def measured_peaks():
@@ -302,7 +319,8 @@ def main():
         "wall_ms_per_step": wall * 1e3 / a.steps,
         "roofline": {"kernel": "modgemm_tc_kernel (Schur update launch)", "bound": "tensor",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": profiled_traffic() if a.workload == WORKLOAD and a.scale == 1.0 else None,
                      "peak_kind": f"bf16 dense sustained, {kind}"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
     }

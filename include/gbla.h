@@ -40,6 +40,7 @@ extern "C" {
 #define GBLA_E_TIMEOUT 4     /* a bounded device-side wait expired; the context stays usable */
 #define GBLA_E_INTERNAL 5    /* internal consistency check failed */
 #define GBLA_E_UNSUPPORTED 6 /* no sm_103a device, or an option this build cannot honour */
+#define GBLA_E_CANCELLED 7   /* a server request was cancelled before it ran */
 
 /* ---- matrix types ---------------------------------------------------- */
 /* Input matrix, borrowed (never modified, never freed by the library).
@@ -84,8 +85,9 @@ typedef struct {
     int64_t n_d;       /* non-pivot columns (columns of B and D) */
     int64_t rank_d;    /* rank of the Schur complement D' */
     double ms_split, ms_trsm, ms_schur, ms_echelon, ms_backsub, ms_output, ms_total;
-    double mod_ops;    /* dense-equivalent modular multiply-adds executed */
+    double mod_ops;    /* modular multiply-adds of the dense products (zero staircase excluded) */
     int64_t launches;  /* CUDA kernels launched by the call */
+    double schur_mod_ops; /* the same for the Schur update D <- D - X*B alone */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */
@@ -100,6 +102,48 @@ int gbla_reduce(const gbla_csr_in *in, uint32_t p, int want_reduced,
  * opt may be NULL (defaults).  stats may be NULL. */
 int gbla_reduce_ex(const gbla_csr_in *in, uint32_t p, const gbla_options *opt,
                    void *stream, gbla_csr_out *out, int64_t *rank, gbla_stats *stats);
+
+/* ---- many matrices ----------------------------------------------------- */
+/* Batch: reduce n independent matrices (in[i] over GF(p[i]), options opt for
+ * all, NULL = defaults).  `workers` host threads (0 = 8), each with its own
+ * CUDA stream on the current device, run whole reductions concurrently,
+ * largest matrices first, so that the latency-bound phases of one matrix
+ * overlap with the work of others.  outs[i], ranks[i], codes[i] receive each
+ * result (release outs with gbla_free).  Returns GBLA_OK, or the first
+ * failing code (the other results are still valid where codes[i] == 0). */
+int gbla_reduce_batch(int n, const gbla_csr_in *in, const uint32_t *p, const gbla_options *opt,
+                      int workers, gbla_csr_out *outs, int64_t *ranks, int *codes);
+
+/* Server: a request queue with continuous batching.  Requests (host CSR,
+ * copied at submit) are admitted in arrival order whenever a worker is free
+ * and the request's estimated device footprint fits in mem_budget next to
+ * the requests already running; a request larger than the budget runs alone.
+ * Admitted requests run concurrently on the workers' streams.  Latency is
+ * measured from submit to result ready. */
+typedef struct gbla_server gbla_server;
+typedef struct {
+    int64_t submitted, completed, failed, cancelled, queued, running;
+    double p50_ms, p99_ms, mean_ms;   /* submit-to-ready latency of completed requests */
+    size_t mem_budget, mem_in_use;    /* bytes, estimated footprints of running requests */
+} gbla_server_stats;
+
+/* mem_budget 0 = 80% of the device memory free now; workers 0 = 8. */
+int gbla_server_create(size_t mem_budget, int workers, gbla_server **srv);
+/* opt->device_ptrs must be 0.  *ticket identifies the request. */
+int gbla_server_submit(gbla_server *srv, const gbla_csr_in *in_host, uint32_t p,
+                       const gbla_options *opt, int64_t *ticket);
+/* Wait up to timeout_s seconds (< 0: forever).  Returns the request's code
+ * and fills *out (host arrays, release with gbla_free) and *rank; the ticket
+ * is consumed.  GBLA_E_TIMEOUT if not done in time (the ticket stays valid),
+ * GBLA_E_CANCELLED if it was cancelled. */
+int gbla_server_wait(gbla_server *srv, int64_t ticket, double timeout_s,
+                     gbla_csr_out *out, int64_t *rank, double *latency_ms);
+/* Cancel a request that is still queued (GBLA_E_INVAL if running or done). */
+int gbla_server_cancel(gbla_server *srv, int64_t ticket);
+int gbla_server_get_stats(gbla_server *srv, gbla_server_stats *st);
+/* Drop queued requests, wait for running ones, release everything.  Call it
+ * after all waits have returned. */
+void gbla_server_destroy(gbla_server *srv);
 
 /* Release a result (host or device arrays); zeroes *out.  NULL-safe. */
 void gbla_free(gbla_csr_out *out);
@@ -139,6 +183,15 @@ int gbla_pivots(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev,
  * where total <= nnz.  Returns GBLA_OK or an error. */
 int gbla_multiline(const gbla_csr_in *pairs_host, int64_t *ml_ptr, int32_t *ml_pos,
                    uint16_t *ml_val, void *stream);
+
+/* Failure-path self test (the paper has no counterpart).  Every wait of the
+ * library's kernels on an mbarrier is bounded (about one second of device
+ * clock); when one expires the kernel stops its other roles, waits for its own
+ * copies, frees tensor memory, records the timeout and returns, so the CUDA
+ * context stays usable.  This runs one product tile whose loads are withheld
+ * and returns the resulting code: GBLA_E_TIMEOUT after about a second.
+ * Synchronises `stream`. */
+int gbla_selftest_wait_timeout(void *stream);
 
 /* Pivot analysis that allocates no memory.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory

@@ -83,7 +83,7 @@ static int planes_zero(const Planes &pl, cudaStream_t s) {
     return GBLA_OK;
 }
 
-static bool is_prime(uint32_t p) {
+bool is_prime(uint32_t p) {
     if (p < 2) return false;
     for (uint32_t d = 2; d * d <= p; ++d)
         if (p % d == 0) return false;
@@ -257,8 +257,8 @@ struct Timer {
     }
 };
 
-static int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
-                       int64_t *rank_out, gbla_stats *stats) {
+int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
+                int64_t *rank_out, gbla_stats *stats) {
     const int want_reduced = opt ? opt->want_reduced : 0;
     const int variant = opt ? opt->gemm_variant : GBLA_GEMM_AUTO;
     const int device_ptrs = opt ? opt->device_ptrs : 0;
@@ -600,6 +600,7 @@ const char *gbla_strerror(int code) {
         case GBLA_E_TIMEOUT: return "a bounded device wait expired";
         case GBLA_E_INTERNAL: return "internal error";
         case GBLA_E_UNSUPPORTED: return "unsupported device or option";
+        case GBLA_E_CANCELLED: return "request cancelled";
         default: return "unknown error";
     }
 }
@@ -663,6 +664,22 @@ int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t l
     dfree(err, s);
     cudaStreamSynchronize(s);
     return rc;
+}
+
+int gbla_selftest_wait_timeout(void *stream) {
+    GBLA_TRY(check_device());
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *err = nullptr;
+    int rc = dalloc_t(&err, 4, s);
+    if (rc == GBLA_OK && cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK) rc = modgemm_withheld_loads(err, s);
+    uint32_t herr = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK && cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = GBLA_E_CUDA;
+    dfree(err, s);
+    cudaStreamSynchronize(s);
+    if (rc != GBLA_OK) return rc;
+    return map_dev_err(herr);
 }
 
 int gbla_pivots(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev, int64_t *npiv, void *stream) {

@@ -14,6 +14,13 @@ struct GemmCounters {
 
 int device_sm_count();
 
+// One whole reduction on stream s (the body of gbla_reduce_ex; arguments
+// already checked for null pointers and p).  Thread-safe: calls from
+// different host threads on different streams run concurrently.
+int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
+                int64_t *rank_out, gbla_stats *stats);
+bool is_prime(uint32_t p);
+
 // C <- (C + sign * A * B^T) mod p, A an A-operand plane set (2 planes,
 // rows a_row0.., K from a_k0), B a B-operand plane set (4 planes, rows
 // b_row0.., K from b_k0).  With c_rows, product row r updates C row
@@ -26,6 +33,10 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
             uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
             uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows = nullptr,
             const int32_t *row_lead = nullptr, const int32_t *row_lead_host = nullptr);
+
+// Test hook: a product whose loads are withheld, so that its bounded waits
+// expire; sets DEV_ERR_TIMEOUT in *err (see modgemm.cu).
+int modgemm_withheld_loads(uint32_t *err, cudaStream_t s);
 
 // u16 -> digit planes (see modgemm.cu).
 int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds, int64_t col_off,

@@ -223,6 +223,7 @@ struct Args {
     uint32_t p;
     float pf, pinv;
     uint32_t *err;
+    int withhold_loads;      // test hook: issue no TMA loads, so the waits expire
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             int issued[STAGES];
             uint32_t issued_parity[STAGES];
             for (int s = 0; s < STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
-            bool ok = true;
+            bool ok = !g.withhold_loads;
             for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
                 int64_t mt, nt;
                 tile_coords(t, num_m, num_n, mt, nt);
@@ -738,12 +739,54 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.row_lead = row_lead; g.sign = sign;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
+    g.withhold_loads = 0;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
     tc::modgemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
+}
+
+// Test hook for the failure path of the bounded waits: one 128 x 128 x 64
+// tile whose loads are withheld.  The MMA issuer's wait for the first stage
+// expires after WAIT_LIMIT_CYCLES, the other roles see the abort flag, and the
+// kernel frees TMEM and returns with DEV_ERR_TIMEOUT set.
+int modgemm_withheld_loads(uint32_t *err, cudaStream_t s)
+{
+    if (!tc_supported()) return GBLA_E_UNSUPPORTED;
+    Planes A{}, B{};
+    int rc = planes_alloc(&A, 128, 64, 2, s);
+    if (rc == GBLA_OK) rc = planes_alloc(&B, 128, 64, 4, s);
+    CUtensorMap ma, mb;
+    if (rc == GBLA_OK) rc = make_map(&ma, A);
+    if (rc == GBLA_OK) rc = make_map(&mb, B);
+    if (rc == GBLA_OK) {
+        static bool attr = false;
+        if (!attr) {
+            if (cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::SMEM_BYTES) != cudaSuccess) rc = GBLA_E_CUDA;
+            attr = true;
+        }
+    }
+    uint16_t *C = nullptr;
+    if (rc == GBLA_OK) rc = dalloc_t(&C, 128 * 128, s);
+    if (rc == GBLA_OK) {
+        tc::Args g{};
+        g.M = 128; g.N = 128; g.K = 64;
+        g.a_rows = (int32_t)A.rows; g.b_rows = (int32_t)B.rows;
+        g.C = C; g.ldc = 128; g.sign = 1;
+        const ModP mp = make_modp(65521);
+        g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+        g.err = err;
+        g.withhold_loads = 1;
+        tc::modgemm_tc_kernel<<<1, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    dfree(C, s);
+    planes_free(&A, s);
+    planes_free(&B, s);
+    return rc;
 }
 
 }  // namespace gbla

@@ -1,0 +1,332 @@
+// runtime.cu -- many reductions at once: the batch entry point and the
+// request server.
+//
+// Both run whole reductions (gbla.cu) concurrently: a pool of host worker
+// threads, each owning a non-blocking CUDA stream on the caller's device,
+// takes reductions from a shared queue.  The latency-bound parts of one
+// reduction (the sparse leaf solves, the single-CTA echelon panels, the host
+// reads of sizes) leave most of the GPU idle; other workers' reductions fill
+// it, and large products of different matrices share the SMs.
+//
+// Batch: every matrix is known up front; workers take them largest first
+// (longest-processing-time order) so the tail of the batch is short.
+//
+// Server: requests arrive over time.  Each is admitted when a worker is free
+// and its estimated device footprint fits the memory budget next to the
+// requests already running (continuous batching); the queue is served in
+// arrival order, and a request that alone exceeds the budget runs when
+// nothing else does.  Latency is measured from submit to result ready.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace gbla {
+namespace {
+
+struct StreamGuard {
+    cudaStream_t s = nullptr;
+    int create(int dev) {
+        if (cudaSetDevice(dev) != cudaSuccess) return GBLA_E_CUDA;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return GBLA_E_CUDA;
+        return GBLA_OK;
+    }
+    ~StreamGuard() {
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+int default_workers(int w) { return w > 0 ? (w > 64 ? 64 : w) : 8; }
+
+}  // namespace
+}  // namespace gbla
+
+using namespace gbla;
+
+// ------------------------------------------------------------------ batch
+extern "C" int gbla_reduce_batch(int n, const gbla_csr_in *in, const uint32_t *p, const gbla_options *opt,
+                                 int workers, gbla_csr_out *outs, int64_t *ranks, int *codes) {
+    if (n < 0 || (n > 0 && (!in || !p || !outs || !ranks || !codes))) return GBLA_E_INVAL;
+    for (int i = 0; i < n; ++i) {
+        memset(&outs[i], 0, sizeof(outs[i]));
+        ranks[i] = 0;
+        codes[i] = GBLA_E_INTERNAL;
+    }
+    if (n == 0) return GBLA_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GBLA_E_CUDA;
+    // largest first
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)in[a].nrows * (double)in[a].ncols > (double)in[b].nrows * (double)in[b].ncols;
+    });
+    std::atomic<int> next{0};
+    const int nw = std::min(default_workers(workers), n);
+    std::vector<std::thread> pool;
+    pool.reserve(nw);
+    for (int w = 0; w < nw; ++w) {
+        pool.emplace_back([&] {
+            StreamGuard sg;
+            const int rc0 = sg.create(dev);
+            for (;;) {
+                const int k = next.fetch_add(1);
+                if (k >= n) break;
+                const int i = order[k];
+                if (rc0 != GBLA_OK) { codes[i] = rc0; continue; }
+                if (p[i] >= 65536u || !is_prime(p[i])) { codes[i] = GBLA_E_INVAL; continue; }
+                codes[i] = reduce_impl(&in[i], p[i], opt, sg.s, &outs[i], &ranks[i], nullptr);
+            }
+        });
+    }
+    for (auto &t : pool) t.join();
+    for (int i = 0; i < n; ++i)
+        if (codes[i] != GBLA_OK) return codes[i];
+    return GBLA_OK;
+}
+
+// ----------------------------------------------------------------- server
+struct gbla_server {
+    struct Request {
+        int64_t ticket = 0;
+        std::vector<int64_t> row_ptr;
+        std::vector<int32_t> col;
+        std::vector<uint16_t> val;
+        gbla_csr_in in{};
+        uint32_t p = 0;
+        gbla_options opt{};
+        size_t est_bytes = 0;
+        enum State { QUEUED, RUNNING, DONE, CANCELLED } state = QUEUED;
+        gbla_csr_out out{};
+        int64_t rank = 0;
+        int code = GBLA_OK;
+        std::chrono::steady_clock::time_point t_submit, t_done;
+    };
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::map<int64_t, Request *> reqs;
+    std::vector<std::thread> workers;
+    std::vector<double> latencies_ms;
+    size_t budget = 0, in_use = 0;
+    int running = 0;
+    int64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0, cancelled = 0;
+    bool stop = false;
+    int dev = 0;
+
+    // Device bytes a reduction of an m x n matrix can need: input, the digit
+    // planes of A^T, B^T and X (at most 12 bytes per entry of an m x n dense
+    // matrix when pivots fill the smaller side) and the uint16 blocks.
+    static size_t estimate(const gbla_csr_in &in) {
+        const double m = (double)in.nrows, n = (double)in.ncols;
+        const double k = std::min(m, n);
+        const double b = 8.0 * (m + 1) + 6.0 * (double)in.nnz + 12.0 * k * n + 6.0 * m * n + (64 << 20);
+        return (size_t)b;
+    }
+
+    bool admissible(const Request *r) const {
+        return running == 0 || in_use + r->est_bytes <= budget;
+    }
+
+    void worker_main() {
+        StreamGuard sg;
+        const int rc0 = sg.create(dev);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv_work.wait(lk, [&] { return stop || (!queue.empty() && admissible(queue.front())); });
+            if (stop && queue.empty()) return;
+            if (queue.empty() || !admissible(queue.front())) continue;
+            Request *r = queue.front();
+            queue.pop_front();
+            r->state = Request::RUNNING;
+            in_use += r->est_bytes;
+            ++running;
+            lk.unlock();
+            int64_t rank = 0;
+            gbla_csr_out out{};
+            const int code = rc0 != GBLA_OK ? rc0 : reduce_impl(&r->in, r->p, &r->opt, sg.s, &out, &rank, nullptr);
+            lk.lock();
+            r->out = out;
+            r->rank = rank;
+            r->code = code;
+            r->t_done = std::chrono::steady_clock::now();
+            r->state = Request::DONE;
+            in_use -= r->est_bytes;
+            --running;
+            ++completed;
+            if (code != GBLA_OK) ++failed;
+            latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+            r->row_ptr.clear(); r->row_ptr.shrink_to_fit();
+            r->col.clear(); r->col.shrink_to_fit();
+            r->val.clear(); r->val.shrink_to_fit();
+            cv_done.notify_all();
+            cv_work.notify_all();   // memory was released: queued requests may fit now
+        }
+    }
+};
+
+extern "C" {
+
+int gbla_server_create(size_t mem_budget, int workers, gbla_server **out) {
+    if (!out) return GBLA_E_INVAL;
+    *out = nullptr;
+    auto *s = new (std::nothrow) gbla_server();
+    if (!s) return GBLA_E_NOMEM;
+    if (cudaGetDevice(&s->dev) != cudaSuccess) {
+        delete s;
+        return GBLA_E_CUDA;
+    }
+    if (mem_budget == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return GBLA_E_UNSUPPORTED;
+        }
+        mem_budget = free_b / 10 * 8;
+    }
+    s->budget = mem_budget;
+    const int nw = default_workers(workers);
+    for (int w = 0; w < nw; ++w) s->workers.emplace_back([s] { s->worker_main(); });
+    *out = s;
+    return GBLA_OK;
+}
+
+int gbla_server_submit(gbla_server *s, const gbla_csr_in *in, uint32_t p, const gbla_options *opt, int64_t *ticket) {
+    if (!s || !in || !ticket) return GBLA_E_INVAL;
+    if (opt && opt->device_ptrs) return GBLA_E_INVAL;   // the server copies host inputs
+    if (p >= 65536u || !is_prime(p)) return GBLA_E_INVAL;
+    const int64_t m = in->nrows, nnz = in->nnz;
+    if (m < 0 || in->ncols < 0 || nnz < 0 || (m > 0 && !in->row_ptr) || (nnz > 0 && (!in->col || !in->val)))
+        return GBLA_E_INVAL;
+    auto *r = new (std::nothrow) gbla_server::Request();
+    if (!r) return GBLA_E_NOMEM;
+    try {
+        r->row_ptr.assign(in->row_ptr, in->row_ptr + (m > 0 ? m + 1 : 0));
+        r->col.assign(in->col, in->col + nnz);
+        r->val.assign(in->val, in->val + nnz);
+    } catch (...) {
+        delete r;
+        return GBLA_E_NOMEM;
+    }
+    r->in = *in;
+    r->in.row_ptr = r->row_ptr.empty() ? nullptr : r->row_ptr.data();
+    r->in.col = r->col.empty() ? nullptr : r->col.data();
+    r->in.val = r->val.empty() ? nullptr : r->val.data();
+    r->p = p;
+    if (opt) r->opt = *opt;
+    r->opt.device_ptrs = 0;
+    r->est_bytes = gbla_server::estimate(*in);
+    r->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->ticket = s->next_ticket++;
+    s->reqs[r->ticket] = r;
+    s->queue.push_back(r);
+    ++s->submitted;
+    *ticket = r->ticket;
+    s->cv_work.notify_one();
+    return GBLA_OK;
+}
+
+int gbla_server_wait(gbla_server *s, int64_t ticket, double timeout_s, gbla_csr_out *out, int64_t *rank,
+                     double *latency_ms) {
+    if (!s || !out || !rank) return GBLA_E_INVAL;
+    memset(out, 0, sizeof(*out));
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return GBLA_E_INVAL;
+    gbla_server::Request *r = it->second;
+    auto done = [&] {
+        return r->state == gbla_server::Request::DONE || r->state == gbla_server::Request::CANCELLED;
+    };
+    if (timeout_s < 0) {
+        s->cv_done.wait(lk, done);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done)) {
+        return GBLA_E_TIMEOUT;   // still queued or running; the ticket stays valid
+    }
+    int code = r->code;
+    if (r->state == gbla_server::Request::CANCELLED) code = GBLA_E_CANCELLED;
+    *out = r->out;
+    *rank = r->rank;
+    if (latency_ms)
+        *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    s->reqs.erase(it);
+    delete r;
+    return code;
+}
+
+int gbla_server_cancel(gbla_server *s, int64_t ticket) {
+    if (!s) return GBLA_E_INVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return GBLA_E_INVAL;
+    gbla_server::Request *r = it->second;
+    if (r->state != gbla_server::Request::QUEUED) return GBLA_E_INVAL;   // running or done
+    s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+    r->state = gbla_server::Request::CANCELLED;
+    r->t_done = std::chrono::steady_clock::now();
+    ++s->cancelled;
+    s->cv_done.notify_all();
+    return GBLA_OK;
+}
+
+int gbla_server_get_stats(gbla_server *s, gbla_server_stats *st) {
+    if (!s || !st) return GBLA_E_INVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(st, 0, sizeof(*st));
+    st->submitted = s->submitted;
+    st->completed = s->completed;
+    st->failed = s->failed;
+    st->cancelled = s->cancelled;
+    st->queued = (int64_t)s->queue.size();
+    st->running = s->running;
+    st->mem_budget = s->budget;
+    st->mem_in_use = s->in_use;
+    if (!s->latencies_ms.empty()) {
+        std::vector<double> v = s->latencies_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const size_t i = (size_t)std::min<double>((double)v.size() - 1, q * (double)(v.size() - 1) + 0.5);
+            return v[i];
+        };
+        st->p50_ms = pct(0.50);
+        st->p99_ms = pct(0.99);
+        double sum = 0;
+        for (double x : v) sum += x;
+        st->mean_ms = sum / (double)v.size();
+    }
+    return GBLA_OK;
+}
+
+void gbla_server_destroy(gbla_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        // queued requests are dropped; running ones finish
+        for (auto *r : s->queue) {
+            r->state = gbla_server::Request::CANCELLED;
+            ++s->cancelled;
+        }
+        s->queue.clear();
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->cv_done.notify_all();
+    for (auto &t : s->workers) t.join();
+    for (auto &kv : s->reqs) {
+        gbla_free(&kv.second->out);
+        delete kv.second;
+    }
+    delete s;
+}
+
+}  // extern "C"

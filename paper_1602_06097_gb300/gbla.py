@@ -19,7 +19,9 @@ GBLA_OK = 0
 GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT = 0, 1, 2
 
 EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
-           "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc"]
+           "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc",
+           "gbla_selftest_wait_timeout", "gbla_reduce_batch", "gbla_server_create", "gbla_server_submit",
+           "gbla_server_wait", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy"]
 
 
 class CsrIn(ctypes.Structure):
@@ -48,6 +50,19 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("mem_budget", ctypes.c_size_t), ("mem_in_use", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+GBLA_E_TIMEOUT, GBLA_E_CANCELLED = 4, 7
 
 
 class GblaError(RuntimeError):
@@ -89,6 +104,25 @@ def load():
         lib.gbla_multiline.restype = i32
         lib.gbla_pivots_noalloc.argtypes = [ctypes.POINTER(CsrIn), u32, vp, ctypes.POINTER(i64), vp]
         lib.gbla_pivots_noalloc.restype = i32
+        lib.gbla_selftest_wait_timeout.argtypes = [vp]
+        lib.gbla_selftest_wait_timeout.restype = i32
+        lib.gbla_reduce_batch.argtypes = [i32, ctypes.POINTER(CsrIn), ctypes.POINTER(u32), ctypes.POINTER(Options),
+                                          i32, ctypes.POINTER(CsrOut), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        lib.gbla_reduce_batch.restype = i32
+        lib.gbla_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+        lib.gbla_server_create.restype = i32
+        lib.gbla_server_submit.argtypes = [vp, ctypes.POINTER(CsrIn), u32, ctypes.POINTER(Options),
+                                           ctypes.POINTER(i64)]
+        lib.gbla_server_submit.restype = i32
+        lib.gbla_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(CsrOut), ctypes.POINTER(i64),
+                                         ctypes.POINTER(ctypes.c_double)]
+        lib.gbla_server_wait.restype = i32
+        lib.gbla_server_cancel.argtypes = [vp, i64]
+        lib.gbla_server_cancel.restype = i32
+        lib.gbla_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.gbla_server_get_stats.restype = i32
+        lib.gbla_server_destroy.argtypes = [vp]
+        lib.gbla_server_destroy.restype = None
         _lib = lib
         return lib
 
@@ -204,6 +238,117 @@ def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_
     return DeviceResult(out, int(rank.value), st.as_dict())
 
 
+def _host_result(lib, out):
+    """Copy a host gbla_csr_out into numpy arrays and release it."""
+    try:
+        r = int(out.nrows)
+        onnz = int(out.nnz)
+        orp = np.ctypeslib.as_array(ctypes.cast(out.row_ptr, ctypes.POINTER(ctypes.c_int64)), shape=(r + 1,)).copy()
+        if onnz:
+            oc = np.ctypeslib.as_array(ctypes.cast(out.col, ctypes.POINTER(ctypes.c_int32)), shape=(onnz,)).copy()
+            ov = np.ctypeslib.as_array(ctypes.cast(out.val, ctypes.POINTER(ctypes.c_uint16)), shape=(onnz,)).copy()
+        else:
+            oc = np.zeros(0, np.int32)
+            ov = np.zeros(0, np.uint16)
+    finally:
+        lib.gbla_free(ctypes.byref(out))
+    return orp, oc, ov
+
+
+def _csr_in(row_ptr, col, val, shape):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.uint16)
+    cin = CsrIn(int(shape[0]), int(shape[1]), int(len(col)), row_ptr.ctypes.data, col.ctypes.data,
+                val.ctypes.data)
+    return cin, (row_ptr, col, val)
+
+
+def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0):
+    """Reduce many host CSR matrices concurrently.  ``mats`` is a list of
+    (row_ptr, col, val, shape, p).  Returns a list of (rank, row_ptr, col, val)
+    (raises on the first failure)."""
+    lib = load()
+    n = len(mats)
+    keep = []
+    ins = (CsrIn * max(n, 1))()
+    ps = (ctypes.c_uint32 * max(n, 1))()
+    for i, (rp, c, v, shape, p) in enumerate(mats):
+        cin, arrs = _csr_in(rp, c, v, shape)
+        keep.append(arrs)
+        ins[i] = cin
+        ps[i] = int(p)
+    opt = Options(1 if want_reduced else 0, int(variant), 0, 0)
+    outs = (CsrOut * max(n, 1))()
+    ranks = (ctypes.c_int64 * max(n, 1))()
+    codes = (ctypes.c_int * max(n, 1))()
+    rc = lib.gbla_reduce_batch(n, ins, ps, ctypes.byref(opt), int(workers), outs, ranks, codes)
+    res = []
+    for i in range(n):
+        if codes[i] == GBLA_OK:
+            res.append((int(ranks[i]),) + _host_result(lib, outs[i]))
+        else:
+            lib.gbla_free(ctypes.byref(outs[i]))
+            res.append(None)
+    _check(rc, "gbla_reduce_batch")
+    return res
+
+
+class Server:
+    """Request server with continuous batching (see gbla_server_* in gbla.h)."""
+
+    def __init__(self, mem_budget=0, workers=0):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        _check(self._lib.gbla_server_create(int(mem_budget), int(workers), ctypes.byref(self._h)),
+               "gbla_server_create")
+
+    def submit(self, row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO):
+        cin, _arrs = _csr_in(row_ptr, col, val, shape)   # copied by the server at submit
+        opt = Options(1 if want_reduced else 0, int(variant), 0, 0)
+        t = ctypes.c_int64(0)
+        _check(self._lib.gbla_server_submit(self._h, ctypes.byref(cin), int(p), ctypes.byref(opt), ctypes.byref(t)),
+               "gbla_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket, timeout=-1.0):
+        """Returns (code, result or None, latency_ms)."""
+        out = CsrOut()
+        rank = ctypes.c_int64(0)
+        lat = ctypes.c_double(0)
+        rc = self._lib.gbla_server_wait(self._h, int(ticket), float(timeout), ctypes.byref(out),
+                                        ctypes.byref(rank), ctypes.byref(lat))
+        if rc == GBLA_OK:
+            return rc, (int(rank.value),) + _host_result(self._lib, out), float(lat.value)
+        self._lib.gbla_free(ctypes.byref(out))
+        return rc, None, float(lat.value)
+
+    def cancel(self, ticket):
+        return int(self._lib.gbla_server_cancel(self._h, int(ticket)))
+
+    def stats(self):
+        st = ServerStats()
+        _check(self._lib.gbla_server_get_stats(self._h, ctypes.byref(st)), "gbla_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            self._lib.gbla_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def modmatmul(A, B, C, p, sign=-1, variant=GEMM_AUTO, stream=None):
     """C <- (C + sign*A*B) mod p in place; A, B, C are 2-D row-major CUDA
     tensors of 16-bit values (int16 views of uint16 residues)."""
@@ -242,6 +387,13 @@ def pivots_noalloc(row_ptr, col, val, shape, p, out, stream=None):
                                  _stream_ptr(stream))
     _check(rc, "gbla_pivots_noalloc")
     return int(npiv.value)
+
+
+def selftest_wait_timeout(stream=None) -> int:
+    """Run one product tile whose loads are withheld; returns the status code
+    (GBLA_E_TIMEOUT = 4 expected: the bounded waits expired and the kernel
+    returned cleanly)."""
+    return int(load().gbla_selftest_wait_timeout(_stream_ptr(stream)))
 
 
 def multiline(row_ptr, col, val, m):

@@ -273,3 +273,21 @@ def test_scaled_grouped_workload_matches_oracle():
     rp, c, v = synth.fl_matrix(spec)
     res = gbla.reduce(rp, c, v, (spec.m, spec.n), spec.p, want_reduced=False)
     same(res, oracle.echelon(spec.m, spec.n, spec.p, rp, c, v)[:4])
+
+
+def test_bounded_wait_expires_cleanly_and_context_survives():
+    """A product whose loads are withheld: the MMA issuer's bounded wait
+    expires (about a second), the kernel reports a timeout instead of hanging,
+    and later products on the same context are still exact."""
+    import time
+    t0 = time.time()
+    assert gbla.selftest_wait_timeout() == 4          # GBLA_E_TIMEOUT
+    assert time.time() - t0 < 30
+    p = 65521
+    rng = np.random.default_rng(3)
+    A = rng.integers(0, p, size=(130, 200))
+    B = rng.integers(0, p, size=(200, 70))
+    C = rng.integers(0, p, size=(130, 70))
+    tc = t16(C)
+    gbla.modmatmul(t16(A), t16(B), tc, p, sign=-1, variant=gbla.GEMM_TCGEN05)
+    assert np.array_equal(from_t16(tc), ref_gemm(A, B, C, p, -1))
