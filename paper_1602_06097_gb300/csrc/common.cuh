@@ -104,7 +104,7 @@ struct Planes {
     __host__ __device__ __nv_bfloat16 *plane(int h) const { return ptr + (size_t)h * plane_elems(); }
 };
 
-inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 // ------------------------------------------------------- error reporting
 // Device-side status word: kernels atomicOr one of these bits; the host maps

@@ -14,6 +14,24 @@ struct GemmCounters {
 
 int device_sm_count();
 
+// One problem of a grouped product: rows a_row0.. of the A plane set times
+// rows b_row0.. of the B plane set (the same K for all problems), into C
+// rows c_rows[0..M) at columns c_col0 .. c_col0 + N.  tile_off = exclusive
+// prefix of the problems' tile counts (ceil(M/128) * ceil(N/128)); entry
+// [nprob] holds the total.
+struct GroupProb {
+    int32_t a_row0, b_row0, M, N;
+    int64_t c_col0;
+    const int32_t *c_rows;
+    int64_t tile_off;
+};
+
+// Grouped product C[c_rows, c_col0:] += sign * A_p * B_p^T for every problem
+// p, one launch (see GroupProb).
+int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K, uint16_t *C,
+                    int64_t ldc, int sign, const ModP &mp, int variant, uint32_t *err, cudaStream_t s,
+                    GemmCounters *ctr);
+
 // One whole reduction on stream s (the body of gbla_reduce_ex; arguments
 // already checked for null pointers and p).  Thread-safe: calls from
 // different host threads on different streams run concurrently.

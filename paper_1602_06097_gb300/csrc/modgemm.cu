@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 #include <stdio.h>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.cuh"
@@ -213,6 +214,8 @@ constexpr long long WAIT_LIMIT_CYCLES = 2000000000ll;  // ~1 s
 
 struct Args {
     int64_t M, N, K;
+    const GroupProb *probs;  // grouped mode: nprob problems (device), else null
+    int nprob;
     int32_t a_row0, a_k0, a_rows;   // a_rows = padded rows per A plane
     int32_t b_row0, b_k0, b_rows;
     uint16_t *C;
@@ -370,6 +373,46 @@ __device__ __forceinline__ int tile_kstep0(const Args &g, int64_t mt) {
     return k > 0 ? (int)(k / BK) : 0;
 }
 
+struct TileInfo {
+    int64_t mt, nt, M, N, c_col0;
+    int a_row, b_row, ks0;
+    const int32_t *c_rows;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const Args &g, int64_t t, int64_t num_m, int64_t num_n) {
+    TileInfo ti;
+    if (g.probs) {
+        int lo = 0, hi = g.nprob - 1;   // last problem with tile_off <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.probs[mid].tile_off <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupProb &P = g.probs[lo];
+        const int64_t local = t - P.tile_off;
+        const int64_t nm = (P.M + BM - 1) / BM;
+        ti.mt = local % nm;
+        ti.nt = local / nm;
+        ti.M = P.M;
+        ti.N = P.N;
+        ti.c_col0 = P.c_col0;
+        ti.c_rows = P.c_rows;
+        ti.a_row = P.a_row0 + (int)(ti.mt * BM);
+        ti.b_row = P.b_row0 + (int)(ti.nt * BN);
+        ti.ks0 = 0;
+    } else {
+        tile_coords(t, num_m, num_n, ti.mt, ti.nt);
+        ti.M = g.M;
+        ti.N = g.N;
+        ti.c_col0 = 0;
+        ti.c_rows = g.c_rows;
+        ti.a_row = g.a_row0 + (int)(ti.mt * BM);
+        ti.b_row = g.b_row0 + (int)(ti.nt * BN);
+        ti.ks0 = tile_kstep0(g, ti.mt);
+    }
+    return ti;
+}
+
 __global__ void __launch_bounds__(tc::THREADS, 1)
     modgemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args g)
 {
@@ -415,7 +458,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     const int64_t num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
-    const int64_t num_tiles = num_m * num_n;
+    const int64_t num_tiles = g.probs ? g.probs[g.nprob].tile_off : num_m * num_n;
     const int ksteps = (int)((g.K + BK - 1) / BK);
 
     if (warp == 0) {
@@ -428,10 +471,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             for (int s = 0; s < STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
             bool ok = !g.withhold_loads;
             for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                int64_t mt, nt;
-                tile_coords(t, num_m, num_n, mt, nt);
-                const int ay = g.a_row0 + (int)(mt * BM), by = g.b_row0 + (int)(nt * BN);
-                for (int ks = tile_kstep0(g, mt); ks < ksteps; ++ks) {
+                const TileInfo ti = tile_info(g, t, num_m, num_n);
+                const int ay = ti.a_row, by = ti.b_row;
+                for (int ks = ti.ks0; ks < ksteps; ++ks) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
                     uint8_t *st = tiles + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], STAGE_BYTES);
@@ -470,9 +512,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             bool ok = true;
             const uint32_t tiles_base = smem_u32(tiles);
             for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                int64_t mt, nt;
-                tile_coords(t, num_m, num_n, mt, nt);
-                const int ks0 = tile_kstep0(g, mt);
+                const int ks0 = tile_info(g, t, num_m, num_n).ks0;
                 const int kbt = (ksteps - ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
                 for (int kb = 0; kb < kbt && ok; ++kb, ++kbc) {
                     const uint32_t buf = kbc & 1u, use = kbc >> 1;
@@ -530,9 +570,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         uint32_t kbc = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-            int64_t mt, nt;
-            tile_coords(t, num_m, num_n, mt, nt);
-            const int kbt = (ksteps - tile_kstep0(g, mt) + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+            const TileInfo ti = tile_info(g, t, num_m, num_n);
+            const int kbt = (ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
             if (kbt <= 0) continue;   // the product is zero on this tile: C stays as it is
             uint32_t run[HC / 2];
 #pragma unroll
@@ -575,10 +614,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             }
             if (!ok) break;
             // C <- (C + sign * run) mod p for this thread's row segment.
-            const int64_t row = mt * BM + row_in_tile;
-            const int64_t col0 = nt * BN + half * HC;
-            const int64_t prow = (row < g.M && g.c_rows) ? (int64_t)g.c_rows[row] : row;
-            if (row < g.M && col0 < g.N && prow >= 0) {
+            const int64_t row = ti.mt * BM + row_in_tile;
+            const int64_t col0 = ti.c_col0 + ti.nt * BN + half * HC;   // column of C
+            const int64_t ncol = ti.c_col0 + ti.N;                        // column limit
+            const int64_t prow = (row < ti.M && ti.c_rows) ? (int64_t)ti.c_rows[row] : row;
+            if (row < ti.M && col0 < ncol && prow >= 0) {
                 uint16_t *crow = g.C + prow * g.ldc + col0;
                 const bool aligned = (reinterpret_cast<uintptr_t>(crow) & 15u) == 0;
                 // Chunks of 8 columns: whole in-range chunks move as 16-byte
@@ -588,13 +628,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                 for (int v = 0; v < HC / 8; ++v) {
                     const int64_t cbase = col0 + v * 8;
-                    if (aligned && cbase + 8 <= g.N) {
+                    if (aligned && cbase + 8 <= ncol) {
                         cv[v] = reinterpret_cast<const uint4 *>(crow)[v];
                     } else {
                         uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
-                            if (cbase + e < g.N) w[e >> 1] |= (uint32_t)crow[v * 8 + e] << ((e & 1) * 16);
+                            if (cbase + e < ncol) w[e >> 1] |= (uint32_t)crow[v * 8 + e] << ((e & 1) * 16);
                         cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
@@ -617,13 +657,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                 for (int v = 0; v < HC / 8; ++v) {
                     const int64_t cbase = col0 + v * 8;
-                    if (aligned && cbase + 8 <= g.N) {
+                    if (aligned && cbase + 8 <= ncol) {
                         reinterpret_cast<uint4 *>(crow)[v] = cv[v];
                     } else {
                         const uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
-                            if (cbase + e < g.N) crow[v * 8 + e] = (uint16_t)(w[e >> 1] >> ((e & 1) * 16));
+                            if (cbase + e < ncol) crow[v * 8 + e] = (uint16_t)(w[e >> 1] >> ((e & 1) * 16));
                     }
                 }
             }
@@ -734,6 +774,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     }
     tc::Args g;
     g.M = M; g.N = N; g.K = K;
+    g.probs = nullptr; g.nprob = 0;
     g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0; g.a_rows = (int32_t)A.rows;
     g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0; g.b_rows = (int32_t)B.rows;
     g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.row_lead = row_lead; g.sign = sign;
@@ -743,6 +784,59 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
     tc::modgemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    GBLA_CUDA_TRY(launch_check());
+    if (ctr) ctr->tc_launches += 1;
+    return GBLA_OK;
+}
+
+// Grouped product, SIMT variant: one launch of the reference kernel per
+// problem (the problem table is read back; used in tests and for p < 8).
+static int modgemm_grouped_simt(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K,
+                                uint16_t *C, int64_t ldc, int sign, const ModP &mp, cudaStream_t s)
+{
+    std::vector<GroupProb> h((size_t)nprob + 1);
+    GBLA_CUDA_TRY(cudaMemcpyAsync(h.data(), probs, sizeof(GroupProb) * h.size(), cudaMemcpyDeviceToHost, s));
+    GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < nprob; ++i) {
+        const GroupProb &P = h[(size_t)i];
+        if (P.M <= 0 || P.N <= 0) continue;
+        dim3 grid((unsigned)((P.N + 63) / 64), (unsigned)((P.M + 63) / 64));
+        modgemm_simt_kernel<<<grid, 256, 0, s>>>(A, P.a_row0, 0, B, P.b_row0, 0, C + P.c_col0, ldc, P.c_rows, P.M, P.N,
+                                                 K, sign, mp);
+        GBLA_CUDA_TRY(launch_check());
+    }
+    return GBLA_OK;
+}
+
+// Grouped product: the problems (device array of nprob + 1 entries, tile
+// offsets filled, entry [nprob].tile_off = total tiles) share the A and B
+// plane sets and K; C is one matrix with leading dimension ldc.
+int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K, uint16_t *C,
+                    int64_t ldc, int sign, const ModP &mp, int variant, uint32_t *err, cudaStream_t s,
+                    GemmCounters *ctr)
+{
+    if (nprob <= 0 || K <= 0) return GBLA_OK;
+    if (variant == GBLA_GEMM_AUTO) variant = (mp.p >= 8 && tc_supported()) ? GBLA_GEMM_TCGEN05 : GBLA_GEMM_SIMT;
+    if (ctr) ctr->launches += 1;
+    if (variant == GBLA_GEMM_SIMT) return modgemm_grouped_simt(A, B, probs, nprob, K, C, ldc, sign, mp, s);
+    if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
+    CUtensorMap ma, mb;
+    GBLA_TRY(make_map(&ma, A));
+    GBLA_TRY(make_map(&mb, B));
+    static bool attr = false;
+    if (!attr) {
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           tc::SMEM_BYTES));
+        attr = true;
+    }
+    tc::Args g{};
+    g.M = 0; g.N = 0; g.K = K;
+    g.probs = probs; g.nprob = nprob;
+    g.a_rows = (int32_t)A.rows; g.b_rows = (int32_t)B.rows;
+    g.C = C; g.ldc = ldc; g.sign = sign;
+    g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+    g.err = err;
+    tc::modgemm_tc_kernel<<<device_sm_count(), tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;

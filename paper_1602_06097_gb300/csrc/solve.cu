@@ -354,26 +354,30 @@ int trsm_lower(const TrsmLower &T)
 // R_J <- R_J - (I - T_JJ^-1) R_J.
 constexpr int PANEL = 128;
 
-// First nonzero column >= from of each listed row (or every row), -1 if none.
-__global__ void row_leads_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t n, int64_t m,
-                                 const int32_t *__restrict__ rows, const int32_t *__restrict__ count_dev,
+// First nonzero column of each listed row (or every row), -1 if none.  The
+// search starts at `from`, or, with from < 0, at the panel boundary after
+// the row's current lead (the row was just cleared on its lead's panel).
+// Rows: rows[seg[0] .. seg[1]) with seg on the device, else rows[0 .. count)
+// (or rows 0 .. count when rows is null).
+__global__ void row_leads_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t n, int64_t count,
+                                 const int32_t *__restrict__ rows, const int64_t *__restrict__ seg,
                                  int64_t from, const int32_t *__restrict__ skip, int32_t *__restrict__ lead)
 {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t cnt = count_dev ? *count_dev : m;
+    const int64_t b = seg ? seg[0] : 0, cnt = seg ? seg[1] - seg[0] : count;
     if (w >= cnt) return;
-    const int64_t r = rows ? rows[w] : w;
+    const int64_t r = rows ? rows[b + w] : w;
     if (skip && skip[r]) return;
     const uint16_t *row = D + r * ldd;
+    const int64_t start = from >= 0 ? from : ((int64_t)lead[r] / PANEL + 1) * PANEL;
     int64_t found = -1;
-    for (int64_t base = from; base < n && found < 0; base += 32 * 8) {
+    for (int64_t base = start; base < n && found < 0; base += 32 * 8) {
         int64_t best = INT64_MAX;
         for (int e = 0; e < 8; ++e) {
             const int64_t c = base + (int64_t)e * 32 + lane;
             if (c < n && row[c] != 0) { best = c; break; }
         }
-        // minimum over the warp
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const int64_t t = __shfl_xor_sync(0xFFFFFFFFu, best, o);
@@ -384,17 +388,57 @@ __global__ void row_leads_kernel(const uint16_t *__restrict__ D, int64_t ldd, in
     if (lane == 0) lead[r] = (int32_t)found;
 }
 
-// One CTA: c0 = smallest leading column of a non-pivot row; candidates =
-// non-pivot rows with leading column in [c0, c0 + PANEL), in row order.
-__global__ void __launch_bounds__(1024) candidates_kernel(int64_t m, const int32_t *__restrict__ lead,
-                                                          const int32_t *__restrict__ is_piv_row,
-                                                          int32_t *__restrict__ cand, int32_t *__restrict__ info)
+// Candidate lists of the fixed panels (panel k = columns [128k, 128k + 128)):
+// the non-pivot rows whose lead falls in the panel, in row order.
+__global__ void panel_count_kernel(int64_t m, const int32_t *__restrict__ lead, const int32_t *__restrict__ is_piv_row,
+                                   int64_t *__restrict__ cnt)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < m && !is_piv_row[r] && lead[r] >= 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[lead[r] / PANEL]), 1ull);
+}
+
+__global__ void panel_scatter_kernel(int64_t m, const int32_t *__restrict__ lead, const int32_t *__restrict__ is_piv_row,
+                                     const int64_t *__restrict__ off, int32_t *__restrict__ fill,
+                                     int32_t *__restrict__ cand)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m || is_piv_row[r] || lead[r] < 0) return;
+    const int k = lead[r] / PANEL;
+    cand[off[k] + atomicAdd(&fill[k], 1)] = (int32_t)r;
+}
+
+__global__ void panel_sort_kernel(int64_t npan, const int64_t *__restrict__ off, int32_t *__restrict__ cand)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npan) return;
+    const int64_t b = off[k], e = off[k + 1];
+    for (int64_t i = b + 1; i < e && e - b <= 2048; ++i) {
+        const int32_t v = cand[i];
+        int64_t j = i - 1;
+        while (j >= b && cand[j] > v) {
+            cand[j + 1] = cand[j];
+            --j;
+        }
+        cand[j + 1] = v;
+    }
+}
+
+// The panel revisited for rows whose lead moved: the panel of the smallest
+// lead among non-pivot rows; its list = the panel's current pivot rows (they
+// re-enter the basis first, unchanged) then those rows, in row order.
+// info = {slot or -1}, seg = {0, list length}.
+__global__ void __launch_bounds__(1024) revisit_kernel(int64_t m, const int32_t *__restrict__ lead,
+                                                       const int32_t *__restrict__ is_piv_row,
+                                                       const int32_t *__restrict__ t_slot,
+                                                       const int32_t *__restrict__ S_slot, int32_t *__restrict__ cand,
+                                                       int32_t *__restrict__ info, int64_t *__restrict__ seg)
 {
     __shared__ int smin;
     __shared__ int wsum[32];
     __shared__ int base;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) { smin = INT32_MAX; base = 0; }
+    if (tid == 0) smin = INT32_MAX;
     __syncthreads();
     int lmin = INT32_MAX;
     for (int64_t r = tid; r < m; r += blockDim.x) {
@@ -403,31 +447,43 @@ __global__ void __launch_bounds__(1024) candidates_kernel(int64_t m, const int32
     }
     atomicMin(&smin, lmin);
     __syncthreads();
-    const int c0 = smin;
+    if (smin == INT32_MAX) {
+        if (tid == 0) {
+            info[0] = -1;
+            seg[0] = seg[1] = 0;
+        }
+        return;
+    }
+    const int k = smin / PANEL;
+    const int tk = t_slot[k];
+    if (tid < tk) cand[tid] = S_slot[k * PANEL + tid];
+    if (tid == 0) base = tk;
+    __syncthreads();
     for (int64_t r0 = 0; r0 < m; r0 += blockDim.x) {
         const int64_t r = r0 + tid;
         int f = 0;
-        if (r < m && c0 != INT32_MAX) {
+        if (r < m) {
             const int l = lead[r];
-            f = (!is_piv_row[r] && l >= 0 && l < c0 + PANEL) ? 1 : 0;
+            f = (!is_piv_row[r] && l >= 0 && l / PANEL == k) ? 1 : 0;
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
         if (lane == 0) wsum[wid] = __popc(bal);
         __syncthreads();
-        int off = base;
-        for (int k = 0; k < wid; ++k) off += wsum[k];
-        if (f) cand[off + __popc(bal & ((1u << lane) - 1u))] = (int32_t)r;
+        int offs = base;
+        for (int q = 0; q < wid; ++q) offs += wsum[q];
+        if (f) cand[offs + __popc(bal & ((1u << lane) - 1u))] = (int32_t)r;
         __syncthreads();
         if (tid == 0) {
             int tot = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += wsum[k];
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += wsum[q];
             base += tot;
         }
         __syncthreads();
     }
     if (tid == 0) {
-        info[0] = (c0 == INT32_MAX) ? -1 : c0;
-        info[1] = base;
+        info[0] = k;
+        seg[0] = 0;
+        seg[1] = base;
     }
 }
 
@@ -440,32 +496,41 @@ __global__ void inverse_table_kernel(uint16_t *__restrict__ tab, ModP mp)
 
 constexpr size_t PANEL_SMEM = (size_t)PANEL * 2 * PANEL * sizeof(uint16_t) + 65536 * sizeof(uint16_t);
 
-__global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__ D, int64_t ldd,
-                                                    const int32_t *__restrict__ info, int64_t n,
-                                                    const int32_t *__restrict__ cand,
+// One CTA per job.  Job j works on panel slot = job_slot[j] (or j), columns
+// [128 slot, 128 slot + 128), with candidate rows cand[seg[j] .. seg[j+1]).
+// Outputs of the slot: t, S (physical row of the pivot with the i-th
+// smallest column, -1 beyond t), pc (pivot columns in the panel, ascending,
+// -1 beyond t), Gm = G - I (128 x 128, zero beyond t).
+__global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t n,
+                                                    const int64_t *__restrict__ seg, const int32_t *__restrict__ cand,
+                                                    const int32_t *__restrict__ job_slot,
                                                     const uint16_t *__restrict__ inv_tab,
-                                                    int32_t *__restrict__ is_piv_row, int32_t *__restrict__ t_out,
-                                                    int32_t *__restrict__ S_out, int32_t *__restrict__ Spos_out,
-                                                    int32_t *__restrict__ pc_out, uint16_t *__restrict__ Gm_out,
-                                                    int32_t *__restrict__ prow, int32_t *__restrict__ pcol,
-                                                    int32_t *__restrict__ rank_dev, ModP mp)
+                                                    int32_t *__restrict__ is_piv_row, int32_t *__restrict__ t_slot,
+                                                    int32_t *__restrict__ S_slot, int32_t *__restrict__ pc_slot,
+                                                    uint16_t *__restrict__ Gm_all, ModP mp)
 {
     extern __shared__ __align__(16) uint16_t panel_smem[];
     uint16_t(*aug)[2 * PANEL] = reinterpret_cast<uint16_t(*)[2 * PANEL]>(panel_smem);  // [PANEL][256]
     uint16_t *inv_s = panel_smem + PANEL * 2 * PANEL;                                  // [p]
     __shared__ uint32_t cand_v[2 * PANEL];
     __shared__ uint32_t fk[PANEL], coef[PANEL];
-    __shared__ int bcol[PANEL], brow[PANEL], S[PANEL], Spos[PANEL], rnk[PANEL];
+    __shared__ int bcol[PANEL], brow[PANEL], S[PANEL], rnk[PANEL];
     __shared__ int wmin[8];
     const int c = threadIdx.x;  // column of the augmented row: [panel | coefficients]
     const int lane = c & 31, warp = c >> 5;
-    const int64_t c0 = info[0];
-    const int ncand = info[1];
+    const int job = blockIdx.x;
+    const int slot = job_slot ? job_slot[job] : job;
+    if (slot < 0) return;
+    const int64_t c0 = (int64_t)slot * PANEL;
+    const int32_t *cl = cand + seg[job];
+    const int ncand = (int)(seg[job + 1] - seg[job]);
     const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
-    const int64_t rank0 = *rank_dev;
     const uint32_t p = mp.p;
-    // inverse table into shared memory (16-byte copies; p <= 65536 entries)
-    {
+    int32_t *S_out = S_slot + (int64_t)slot * PANEL;
+    int32_t *pc_out = pc_slot + (int64_t)slot * PANEL;
+    uint16_t *Gm_out = Gm_all + (int64_t)slot * PANEL * PANEL;
+    if (ncand > 0) {
+        // inverse table into shared memory (16-byte copies; p <= 65536 entries)
         const int nvec = (int)((p + 7) / 8);
         const uint4 *src = reinterpret_cast<const uint4 *>(inv_tab);
         uint4 *dst = reinterpret_cast<uint4 *>(inv_s);
@@ -477,10 +542,10 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
     // software pipeline: the next candidate's panel entry is loaded while the
     // current one is processed
     uint32_t vnext = 0;
-    if (ncand > 0 && c < bw) vnext = D[(int64_t)cand[0] * ldd + c0 + c];
+    if (ncand > 0 && c < bw) vnext = D[(int64_t)cl[0] * ldd + c0 + c];
     for (int ci = 0; ci < ncand && t < bw; ++ci) {
         uint32_t v = vnext;
-        if (ci + 1 < ncand && c < bw) vnext = D[(int64_t)cand[ci + 1] * ldd + c0 + c];
+        if (ci + 1 < ncand && c < bw) vnext = D[(int64_t)cl[ci + 1] * ldd + c0 + c];
         if (c >= PANEL) v = (c - PANEL == t) ? 1u : 0u;
         // the basis is in reduced echelon form, so the multiplier of basis
         // row k is this candidate's entry at that row's pivot column
@@ -523,8 +588,7 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
         if (c == cs) brow[c] = t;
         if (c == 0) {
             bcol[t] = cs;
-            S[t] = (int)cand[ci];
-            Spos[t] = ci;
+            S[t] = (int)cl[ci];
         }
         ++t;
         __syncthreads();
@@ -537,26 +601,17 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
         rnk[c] = r;
     }
     __syncthreads();
-    if (c == 0) {
-        *t_out = t;
-        *rank_dev = (int32_t)(rank0 + t);
-    }
+    if (c == 0) t_slot[slot] = t;
     if (c < PANEL) {
-        // rows beyond t are sentinels (-1): the products skip them
+        // the pivot with the c-th smallest column lands in physical row S[c];
+        // entries beyond t are sentinels (-1): the products skip them
         S_out[c] = (c < t) ? S[c] : -1;
-        Spos_out[c] = (c < t) ? Spos[c] : -1;
         if (c < t) {
             pc_out[rnk[c]] = bcol[c];
             is_piv_row[S[c]] = 1;
         } else {
             pc_out[c] = -1;
         }
-    }
-    __syncthreads();
-    // the pivot with the c-th smallest column lands in physical row S[c]
-    if (c < t) {
-        prow[rank0 + c] = S[c];
-        pcol[rank0 + c] = (int32_t)(c0 + pc_out[c]);
     }
     for (int kk = 0; kk < PANEL; ++kk) {
         // Gm row rnk[kk] = coefficient part of basis row kk minus the identity;
@@ -571,6 +626,128 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
             }
         }
     }
+}
+
+// Per panel of a chunk: where its rows of the D[S]^T plane set start, its
+// slot and its column count n - 128 slot.
+struct PanelPlan {
+    int64_t boff;
+    int32_t slot, nc;
+};
+
+// B-operand planes of D[S]^T for every panel of a chunk (blockIdx.z):
+// dst[boff + i][j] = D[S_j][128 slot + i] for j < t, else 0.
+__global__ void gather_t_planes_kernel(Planes dst, const uint16_t *__restrict__ D, int64_t ldd,
+                                       const PanelPlan *__restrict__ plan, const int32_t *__restrict__ S_slot,
+                                       const int32_t *__restrict__ t_slot, uint32_t p, uint32_t r256)
+{
+    __shared__ uint16_t tile[32][33];
+    const PanelPlan pl = plan[blockIdx.z];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int64_t nrows = round_up(pl.nc, 128);
+    if (i0 >= nrows) return;
+    const int t = t_slot[pl.slot];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int q = ty; q < 32; q += 8) {
+        const int64_t j = j0 + q, i = i0 + tx;
+        uint16_t v = 0;
+        if (j < t && i < pl.nc) {
+            const int64_t sr = S_slot[(int64_t)pl.slot * PANEL + j];
+            v = D[sr * ldd + (int64_t)pl.slot * PANEL + i];
+        }
+        tile[q][tx] = v;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+        const int64_t i = i0 + q, j = j0 + tx;
+        const uint32_t a = tile[tx][q];
+        int hi, lo;
+        const size_t off = (size_t)(pl.boff + i) * (size_t)dst.kp + (size_t)j;
+        digits(a, p, hi, lo);
+        dst.plane(0)[off] = i2bf(hi);
+        dst.plane(1)[off] = i2bf(lo);
+        digits((a * r256) % p, p, hi, lo);
+        dst.plane(2)[off] = i2bf(hi);
+        dst.plane(3)[off] = i2bf(lo);
+    }
+}
+
+// A-operand planes of the candidates' entries at their panel's pivot columns:
+// row r - row_base of dst = D[cand[r]][128 slot + pc_j] for j < t (zero for
+// rows that are pivots now).  blockIdx.y = job of the chunk.
+__global__ void gather_h_planes_kernel(Planes dst, const uint16_t *__restrict__ D, int64_t ldd,
+                                       const int64_t *__restrict__ seg, const int32_t *__restrict__ cand,
+                                       const int32_t *__restrict__ job_slot, int job0, int64_t row_base,
+                                       const int32_t *__restrict__ pc_slot, const int32_t *__restrict__ t_slot,
+                                       const int32_t *__restrict__ is_piv_row, uint32_t p)
+{
+    const int job = job0 + blockIdx.y;
+    const int slot = job_slot ? job_slot[job] : job;
+    if (slot < 0) return;
+    const int t = t_slot[slot];
+    const int j = threadIdx.x;   // 128 threads: K column
+    const int pcj = (j < t) ? pc_slot[(int64_t)slot * PANEL + j] : -1;
+    for (int64_t r = seg[job] + blockIdx.x; r < seg[job + 1]; r += gridDim.x) {
+        const int64_t row = cand[r];
+        uint32_t a = 0;
+        if (pcj >= 0 && !is_piv_row[row]) a = D[row * ldd + (int64_t)slot * PANEL + pcj];
+        int hi, lo;
+        digits(a, p, hi, lo);
+        const size_t off = (size_t)(r - row_base) * (size_t)dst.kp + (size_t)j;
+        dst.plane(0)[off] = i2bf(hi);
+        dst.plane(1)[off] = i2bf(lo);
+    }
+}
+
+// Problem tables of the two grouped products of a chunk (one thread).
+// mode 1: D[S] += (G - I) * D[S];  mode 2: D[cand] -= H * D[S].
+__global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const PanelPlan *__restrict__ plan,
+                                  const int32_t *__restrict__ t_slot, const int32_t *__restrict__ S_slot,
+                                  const int64_t *__restrict__ seg, const int32_t *__restrict__ cand, int job0,
+                                  int64_t row_base)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t off = 0;
+    for (int q = 0; q < nprob; ++q) {
+        const PanelPlan pl = plan[q];
+        const int t = t_slot[pl.slot];
+        GroupProb P;
+        P.b_row0 = (int32_t)pl.boff;
+        P.N = pl.nc;
+        P.c_col0 = (int64_t)pl.slot * PANEL;
+        if (mode == 1) {
+            P.a_row0 = q * PANEL;
+            P.M = t;
+            P.c_rows = S_slot + (int64_t)pl.slot * PANEL;
+        } else {
+            const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
+            P.a_row0 = (int32_t)(b - row_base);
+            P.M = (e - b > t) ? (int32_t)(e - b) : 0;   // nothing to clear when every candidate is a pivot
+            P.c_rows = cand + b;
+        }
+        if (t == 0) P.M = 0;
+        P.tile_off = off;
+        probs[q] = P;
+        off += (P.M > 0 && P.N > 0) ? ((int64_t)(P.M + 127) / 128) * ((int64_t)(P.N + 127) / 128) : 0;
+    }
+    probs[nprob].tile_off = off;
+}
+
+// Pivot records in pivot-column order (slots ascending, columns ascending
+// inside a slot); *rank receives their number.  One thread.
+__global__ void compact_slots_kernel(int64_t npan, const int32_t *__restrict__ t_slot,
+                                     const int32_t *__restrict__ S_slot, const int32_t *__restrict__ pc_slot,
+                                     int32_t *__restrict__ prow, int32_t *__restrict__ pcol, int64_t *rank)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t r = 0;
+    for (int64_t k = 0; k < npan; ++k)
+        for (int i = 0; i < t_slot[k]; ++i) {
+            prow[r] = S_slot[k * PANEL + i];
+            pcol[r] = (int32_t)(k * PANEL + pc_slot[k * PANEL + i]);
+            ++r;
+        }
+    *rank = r;
 }
 
 __global__ void gather_rows_kernel(const uint16_t *__restrict__ D, int64_t ldd, const int32_t *__restrict__ rows,
@@ -624,11 +801,7 @@ __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__res
 
 constexpr int LEAF_INV_SMEM = 2 * 128 * 129 * (int)sizeof(uint16_t);
 
-struct EchScratch {
-    int32_t *info, *cand, *t_dev, *S, *Spos, *pc, *lead;
-    uint16_t *Gm, *inv_tab;
-    Planes Gp, Bs, H;
-};
+
 
 static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_t *pcol_dev,
                        const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &Bp,
@@ -658,6 +831,52 @@ static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_
     return backsub_rec(E, R, ldr, pcol_dev, pcol, lo, mid, Ap, Bp, Nm_all);
 }
 
+// Apply the panel bases of jobs [job0, job0 + njobs) (slots given by
+// job_slot or equal to the job index): D[S] <- G * D[S], then clear the other
+// candidates on their panel and find their new leads.
+struct PanelWork {
+    int32_t *t_slot, *S_slot, *pc_slot;
+    uint16_t *Gm_all;
+    int32_t *lead;
+    PanelPlan *plan_dev;
+    GroupProb *probs;
+    Planes Gp, Bs, H;
+};
+
+static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<PanelPlan> &plan, const int64_t *seg,
+                        const int32_t *cand, const int32_t *job_slot, int job0, int64_t row_base, int64_t rows_max,
+                        const uint16_t *Gm_first)
+{
+    const ModP &mp = *E.mp;
+    cudaStream_t s = E.s;
+    const int nj = (int)plan.size();
+    if (nj == 0) return GBLA_OK;
+    int64_t ncmax = 0;
+    for (const auto &pl : plan) ncmax = pl.nc > ncmax ? pl.nc : ncmax;
+    GBLA_CUDA_TRY(cudaMemcpyAsync(W.plan_dev, plan.data(), sizeof(PanelPlan) * (size_t)nj, cudaMemcpyHostToDevice, s));
+    // G - I of the jobs' slots as the A operand (rows q * 128 ..)
+    GBLA_TRY(to_planes(W.Gp, (int64_t)nj * PANEL, PANEL, Gm_first, PANEL, 0, false, nullptr, nullptr, mp, s));
+    dim3 gt((unsigned)(round_up(ncmax, 128) / 32), PANEL / 32, (unsigned)nj);
+    gather_t_planes_kernel<<<gt, dim3(32, 8), 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp.p,
+                                                      mp.r256);
+    GBLA_CUDA_TRY(launch_check());
+    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, seg, cand, job0, row_base);
+    GBLA_CUDA_TRY(launch_check());
+    GBLA_TRY(modgemm_grouped(W.Gp, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, +1, mp, E.variant, E.err, s, E.ctr));
+    // D[cand] -= D[cand, pc] * D[S]   (the pivot rows have zero multipliers)
+    gather_t_planes_kernel<<<gt, dim3(32, 8), 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp.p,
+                                                      mp.r256);
+    GBLA_CUDA_TRY(launch_check());
+    const unsigned rows_blocks = (unsigned)(rows_max < 64 ? (rows_max > 0 ? rows_max : 1) : 64);
+    gather_h_planes_kernel<<<dim3(rows_blocks, (unsigned)nj), PANEL, 0, s>>>(
+        W.H, E.D16, E.ldd, seg, cand, job_slot, job0, row_base, W.pc_slot, W.t_slot, E.is_piv_row, mp.p);
+    GBLA_CUDA_TRY(launch_check());
+    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 2, W.plan_dev, W.t_slot, W.S_slot, seg, cand, job0, row_base);
+    GBLA_CUDA_TRY(launch_check());
+    GBLA_TRY(modgemm_grouped(W.H, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, -1, mp, E.variant, E.err, s, E.ctr));
+    return GBLA_OK;
+}
+
 int echelon_d(const EchelonD &E, int64_t *rank_out)
 {
     *rank_out = 0;
@@ -665,25 +884,15 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     if (m <= 0 || n <= 0) return GBLA_OK;
     cudaStream_t s = E.s;
     const ModP &mp = *E.mp;
-    EchScratch X{};
+    const int64_t npan = (n + PANEL - 1) / PANEL;
     int rc = GBLA_OK;
     int64_t rank = 0;
-    int32_t info_h[2];
-    GBLA_CUDA_TRY(cudaMemsetAsync(E.is_piv_row, 0, sizeof(int32_t) * (size_t)m, s));
-    GBLA_TRY(dalloc_t(&X.info, 4, s));
-    GBLA_TRY(dalloc_t(&X.cand, (size_t)m + 1, s));
-    GBLA_TRY(dalloc_t(&X.t_dev, 4, s));
-    GBLA_TRY(dalloc_t(&X.S, PANEL, s));
-    GBLA_TRY(dalloc_t(&X.Spos, PANEL, s));
-    GBLA_TRY(dalloc_t(&X.pc, PANEL, s));
-    GBLA_TRY(dalloc_t(&X.lead, (size_t)m + 1, s));
-    GBLA_TRY(dalloc_t(&X.Gm, (size_t)PANEL * PANEL, s));
-    GBLA_TRY(dalloc_t(&X.inv_tab, 65536, s));
-    inverse_table_kernel<<<(mp.p + 255) / 256, 256, 0, s>>>(X.inv_tab, mp);
-    GBLA_CUDA_TRY(launch_check());
-    GBLA_TRY(planes_alloc(&X.Gp, PANEL, PANEL, 2, s));
-    GBLA_TRY(planes_alloc(&X.Bs, n, PANEL, 4, s));
-    GBLA_TRY(planes_alloc(&X.H, m, PANEL, 2, s));
+    PanelWork W{};
+    int32_t *cand = nullptr, *fill = nullptr, *info = nullptr;
+    int64_t *off = nullptr, *seg2 = nullptr, *rank_dev = nullptr;
+    uint16_t *inv_tab = nullptr;
+    // Phase B works on chunks of panels whose D[S]^T planes fit this many rows.
+    const int64_t BS_ROWS = int64_t(1) << 20;
     static bool attr = false;
     if (!attr) {
         GBLA_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM));
@@ -691,62 +900,106 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
                                            LEAF_INV_SMEM));
         attr = true;
     }
-    row_leads_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(E.D16, E.ldd, n, m, nullptr, nullptr, 0,
-                                                                     nullptr, X.lead);
-    GBLA_CUDA_TRY(launch_check());
-    // ---- forward pass (one host synchronisation per panel, to size the launches)
-    int32_t *rank_dev = nullptr;
-    GBLA_TRY(dalloc_t(&rank_dev, 1, s));
-    GBLA_CUDA_TRY(cudaMemsetAsync(rank_dev, 0, sizeof(int32_t), s));
-    for (int64_t iter = 0;; ++iter) {
-        // every panel turns at least its first candidate into a pivot
-        if (iter > m) { rc = GBLA_E_INTERNAL; break; }
-        candidates_kernel<<<1, 1024, 0, s>>>(m, X.lead, E.is_piv_row, X.cand, X.info);
-        if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        if (cudaMemcpyAsync(info_h, X.info, sizeof(info_h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        const int64_t c0 = info_h[0];
-        const int ncand = info_h[1];
-        if (c0 < 0 || ncand == 0) break;
-        const int bw = (int)((n - c0) < PANEL ? (n - c0) : PANEL);
-        // at most min(ncand, bw) pivots; the launches below are sized by that
-        // bound and the sentinel rows of S make the surplus a no-op
-        const int tb = ncand < bw ? ncand : bw;
-        // Rows of S and the candidates are zero left of c0, so the products may
-        // start at the 64-aligned column c0a (they add zeros there); this keeps
-        // the C rows 16-byte aligned for the vectorised epilogue.
-        const int64_t c0a = c0 & ~int64_t(63);
-        const int64_t nc = n - c0a;
-        panel_kernel<<<1, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, X.info, n, X.cand, X.inv_tab, E.is_piv_row,
-                                                      X.t_dev, X.S, X.Spos, X.pc, X.Gm, E.prow, E.pcol, rank_dev, mp);
-        if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        // D[S, c0:] <- G * D[S, c0:]  as  D[S] += (G - I) * D[S]
-        if ((rc = to_planes(X.Gp, tb, tb, X.Gm, PANEL, 0, false, nullptr, nullptr, mp, s))) break;
-        if ((rc = to_planes(X.Bs, nc, tb, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
-        if ((rc = modgemm(X.Gp, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, tb, nc, tb, +1, mp, E.variant, E.err, s, E.ctr,
-                          X.S))) break;
-        if (ncand > 1) {
-            // D[cand, c0:] -= D[cand, c0 + pc] * D[S, c0:]   (rows of S have a zero multiplier row)
-            if ((rc = to_planes(X.Bs, nc, tb, E.D16, E.ldd, c0a, true, X.S, nullptr, mp, s))) break;
-            Planes Hc = X.H;
-            // (rows that just became pivots read as zero rows)
-            if ((rc = to_planes(Hc, ncand, tb, E.D16, E.ldd, c0, false, X.cand, X.pc, mp, s, E.is_piv_row))) break;
-            if ((rc = modgemm(Hc, 0, 0, X.Bs, 0, 0, E.D16 + c0a, E.ldd, ncand, nc, tb, -1, mp, E.variant, E.err, s,
-                              E.ctr, X.cand))) break;
-            row_leads_kernel<<<(unsigned)(((int64_t)ncand * 32 + 255) / 256), 256, 0, s>>>(
-                E.D16, E.ldd, n, m, X.cand, X.info + 1, c0 + bw, E.is_piv_row, X.lead);
-            if (launch_check() != cudaSuccess) { rc = GBLA_E_CUDA; break; }
-        }
-    }
+#define ESTEP(expr)                         \
+    do {                                    \
+        if ((rc = (expr)) != GBLA_OK) goto done; \
+    } while (0)
+#define ECUDA(expr)                                   \
+    do {                                              \
+        if ((expr) != cudaSuccess) { rc = GBLA_E_CUDA; goto done; } \
+    } while (0)
     {
-        int32_t r32 = 0;
-        if (cudaMemcpyAsync(&r32, rank_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
-        rank = r32;
+        ESTEP(dalloc_t(&W.lead, (size_t)m + 1, s));
+        ESTEP(dalloc_t(&cand, (size_t)m + PANEL + 1, s));
+        ESTEP(dalloc_t(&fill, (size_t)npan + 1, s));
+        ESTEP(dalloc_t(&off, (size_t)npan + 2, s));
+        ESTEP(dalloc_t(&info, 4, s));
+        ESTEP(dalloc_t(&seg2, 4, s));
+        ESTEP(dalloc_t(&rank_dev, 2, s));
+        ESTEP(dalloc_t(&W.t_slot, (size_t)npan + 1, s));
+        ESTEP(dalloc_t(&W.S_slot, (size_t)npan * PANEL, s));
+        ESTEP(dalloc_t(&W.pc_slot, (size_t)npan * PANEL, s));
+        ESTEP(dalloc_t(&W.Gm_all, (size_t)npan * PANEL * PANEL, s));
+        ESTEP(dalloc_t(&W.plan_dev, (size_t)npan + 1, s));
+        ESTEP(dalloc_t(&W.probs, (size_t)npan + 2, s));
+        ESTEP(dalloc_t(&inv_tab, 65536, s));
+        ESTEP(planes_alloc(&W.Bs, BS_ROWS + n, PANEL, 4, s));
+        ESTEP(planes_alloc(&W.Gp, npan * PANEL, PANEL, 2, s));
+        ESTEP(planes_alloc(&W.H, m + PANEL, PANEL, 2, s));
+        ECUDA(cudaMemsetAsync(E.is_piv_row, 0, sizeof(int32_t) * (size_t)m, s));
+        ECUDA(cudaMemsetAsync(W.t_slot, 0, sizeof(int32_t) * (size_t)(npan + 1), s));
+        ECUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)(npan + 1), s));
+        ECUDA(cudaMemsetAsync(off, 0, sizeof(int64_t) * (size_t)(npan + 2), s));
+        inverse_table_kernel<<<(mp.p + 255) / 256, 256, 0, s>>>(inv_tab, mp);
+        ECUDA(launch_check());
+        // ---- leads, and each panel's fresh candidates (rows leading in it)
+        row_leads_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(E.D16, E.ldd, n, m, nullptr, nullptr, 0,
+                                                                         nullptr, W.lead);
+        ECUDA(launch_check());
+        panel_count_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, W.lead, E.is_piv_row, off);
+        ECUDA(launch_check());
+        ESTEP(scan_i64(off, off, npan + 1, nullptr, s));
+        panel_scatter_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, W.lead, E.is_piv_row, off, fill, cand);
+        ECUDA(launch_check());
+        panel_sort_kernel<<<(unsigned)((npan + 255) / 256), 256, 0, s>>>(npan, off, cand);
+        ECUDA(launch_check());
+        std::vector<int64_t> off_h((size_t)npan + 1);
+        ECUDA(cudaMemcpyAsync(off_h.data(), off, sizeof(int64_t) * (size_t)(npan + 1), cudaMemcpyDeviceToHost, s));
+        // ---- phase A: the bases of all panels at once (one CTA each)
+        panel_kernel<<<(unsigned)npan, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, n, off, cand, nullptr, inv_tab,
+                                                                   E.is_piv_row, W.t_slot, W.S_slot, W.pc_slot,
+                                                                   W.Gm_all, mp);
+        ECUDA(launch_check());
+        ECUDA(cudaStreamSynchronize(s));
+        // ---- phase B: apply them, chunk by chunk of panels (grouped products)
+        for (int64_t k0 = 0; k0 < npan;) {
+            std::vector<PanelPlan> plan;
+            int64_t boff = 0, k1 = k0;
+            while (k1 < npan) {
+                const int32_t nc = (int32_t)(n - k1 * PANEL);
+                if (!plan.empty() && boff + round_up(nc, 128) > BS_ROWS) break;
+                plan.push_back(PanelPlan{boff, (int32_t)k1, nc});
+                boff += round_up(nc, 128);
+                ++k1;
+            }
+            const int64_t rows = off_h[(size_t)k1] - off_h[(size_t)k0];
+            ESTEP(apply_panels(E, W, plan, off, cand, nullptr, (int)k0, off_h[(size_t)k0], rows,
+                               W.Gm_all + k0 * PANEL * PANEL));
+            if (rows > 0) {
+                row_leads_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(
+                    E.D16, E.ldd, n, rows, cand + off_h[(size_t)k0], nullptr, -1, E.is_piv_row, W.lead);
+                ECUDA(launch_check());
+            }
+            k0 = k1;
+        }
+        // ---- phase C: rows that were dependent on their panel moved right;
+        // revisit their panels one at a time (the panel's pivots re-enter first)
+        for (int64_t iter = 0;; ++iter) {
+            if (iter > m) { rc = GBLA_E_INTERNAL; goto done; }
+            revisit_kernel<<<1, 1024, 0, s>>>(m, W.lead, E.is_piv_row, W.t_slot, W.S_slot, cand, info, seg2);
+            ECUDA(launch_check());
+            int32_t k = -1;
+            int64_t seg_h[2];
+            ECUDA(cudaMemcpyAsync(&k, info, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            ECUDA(cudaMemcpyAsync(seg_h, seg2, sizeof(seg_h), cudaMemcpyDeviceToHost, s));
+            ECUDA(cudaStreamSynchronize(s));
+            if (k < 0) break;
+            panel_kernel<<<1, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, n, seg2, cand, info, inv_tab, E.is_piv_row,
+                                                          W.t_slot, W.S_slot, W.pc_slot, W.Gm_all, mp);
+            ECUDA(launch_check());
+            std::vector<PanelPlan> plan{PanelPlan{0, k, (int32_t)(n - (int64_t)k * PANEL)}};
+            ESTEP(apply_panels(E, W, plan, seg2, cand, info, 0, 0, seg_h[1], W.Gm_all + (int64_t)k * PANEL * PANEL));
+            row_leads_kernel<<<(unsigned)((seg_h[1] * 32 + 255) / 256), 256, 0, s>>>(
+                E.D16, E.ldd, n, m, cand, seg2, -1, E.is_piv_row, W.lead);
+            ECUDA(launch_check());
+        }
+        compact_slots_kernel<<<1, 32, 0, s>>>(npan, W.t_slot, W.S_slot, W.pc_slot, E.prow, E.pcol, rank_dev);
+        ECUDA(launch_check());
+        ECUDA(cudaMemcpyAsync(&rank, rank_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        ECUDA(cudaStreamSynchronize(s));
     }
-    dfree(rank_dev, s);
     // ---- backward pass: RREF rows into R (pivot column order)
-    if (rc == GBLA_OK && rank > 0) {
+    if (rank > 0) {
         const int64_t ldr = E.ldd;
         std::vector<int32_t> pcol_h((size_t)rank);
         uint16_t *Nm = nullptr;
@@ -773,18 +1026,26 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         planes_free(&Ap, s);
         planes_free(&Bp, s);
     }
-    dfree(X.info, s);
-    dfree(X.cand, s);
-    dfree(X.t_dev, s);
-    dfree(X.S, s);
-    dfree(X.Spos, s);
-    dfree(X.pc, s);
-    dfree(X.lead, s);
-    dfree(X.Gm, s);
-    dfree(X.inv_tab, s);
-    planes_free(&X.Gp, s);
-    planes_free(&X.Bs, s);
-    planes_free(&X.H, s);
+done:
+#undef ESTEP
+#undef ECUDA
+    dfree(W.lead, s);
+    dfree(cand, s);
+    dfree(fill, s);
+    dfree(off, s);
+    dfree(info, s);
+    dfree(seg2, s);
+    dfree(rank_dev, s);
+    dfree(W.t_slot, s);
+    dfree(W.S_slot, s);
+    dfree(W.pc_slot, s);
+    dfree(W.Gm_all, s);
+    dfree(W.plan_dev, s);
+    dfree(W.probs, s);
+    dfree(inv_tab, s);
+    planes_free(&W.Bs, s);
+    planes_free(&W.Gp, s);
+    planes_free(&W.H, s);
     *rank_out = rank;
     return rc;
 }
