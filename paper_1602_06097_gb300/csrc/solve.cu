@@ -424,54 +424,31 @@ __global__ void panel_sort_kernel(int64_t npan, const int64_t *__restrict__ off,
     }
 }
 
-// The panel revisited for rows whose lead moved: the panel of the smallest
-// lead among non-pivot rows; its list = the panel's current pivot rows (they
-// re-enter the basis first, unchanged) then those rows, in row order.
-// info = {slot or -1}, seg = {0, list length}.
-__global__ void __launch_bounds__(1024) revisit_kernel(int64_t m, const int32_t *__restrict__ lead,
-                                                       const int32_t *__restrict__ is_piv_row,
-                                                       const int32_t *__restrict__ t_slot,
-                                                       const int32_t *__restrict__ S_slot, int32_t *__restrict__ cand,
-                                                       int32_t *__restrict__ info, int64_t *__restrict__ seg)
+// Jobs of a wave: the panels with candidates, ascending; seg[j] = offset of
+// job j's candidates (candidates of consecutive non-empty panels are
+// contiguous).  njobs -> info[0].  One CTA.
+__global__ void __launch_bounds__(1024) make_jobs_kernel(int64_t npan, const int64_t *__restrict__ off,
+                                                         int32_t *__restrict__ job_slot, int64_t *__restrict__ seg,
+                                                         int32_t *__restrict__ info)
 {
-    __shared__ int smin;
     __shared__ int wsum[32];
     __shared__ int base;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) smin = INT32_MAX;
+    if (tid == 0) base = 0;
     __syncthreads();
-    int lmin = INT32_MAX;
-    for (int64_t r = tid; r < m; r += blockDim.x) {
-        const int l = lead[r];
-        if (!is_piv_row[r] && l >= 0 && l < lmin) lmin = l;
-    }
-    atomicMin(&smin, lmin);
-    __syncthreads();
-    if (smin == INT32_MAX) {
-        if (tid == 0) {
-            info[0] = -1;
-            seg[0] = seg[1] = 0;
-        }
-        return;
-    }
-    const int k = smin / PANEL;
-    const int tk = t_slot[k];
-    if (tid < tk) cand[tid] = S_slot[k * PANEL + tid];
-    if (tid == 0) base = tk;
-    __syncthreads();
-    for (int64_t r0 = 0; r0 < m; r0 += blockDim.x) {
-        const int64_t r = r0 + tid;
-        int f = 0;
-        if (r < m) {
-            const int l = lead[r];
-            f = (!is_piv_row[r] && l >= 0 && l / PANEL == k) ? 1 : 0;
-        }
+    for (int64_t k0 = 0; k0 < npan; k0 += blockDim.x) {
+        const int64_t k = k0 + tid;
+        const int f = (k < npan && off[k + 1] > off[k]) ? 1 : 0;
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
         if (lane == 0) wsum[wid] = __popc(bal);
         __syncthreads();
-        int offs = base;
-        for (int q = 0; q < wid; ++q) offs += wsum[q];
-        if (f) cand[offs + __popc(bal & ((1u << lane) - 1u))] = (int32_t)r;
+        int o = base;
+        for (int q = 0; q < wid; ++q) o += wsum[q];
+        if (f) {
+            const int j = o + __popc(bal & ((1u << lane) - 1u));
+            job_slot[j] = (int32_t)k;
+            seg[j] = off[k];
+        }
         __syncthreads();
         if (tid == 0) {
             int tot = 0;
@@ -481,9 +458,8 @@ __global__ void __launch_bounds__(1024) revisit_kernel(int64_t m, const int32_t 
         __syncthreads();
     }
     if (tid == 0) {
-        info[0] = k;
-        seg[0] = 0;
-        seg[1] = base;
+        seg[base] = off[npan];
+        info[0] = base;
     }
 }
 
@@ -497,17 +473,19 @@ __global__ void inverse_table_kernel(uint16_t *__restrict__ tab, ModP mp)
 constexpr size_t PANEL_SMEM = (size_t)PANEL * 2 * PANEL * sizeof(uint16_t) + 65536 * sizeof(uint16_t);
 
 // One CTA per job.  Job j works on panel slot = job_slot[j] (or j), columns
-// [128 slot, 128 slot + 128), with candidate rows cand[seg[j] .. seg[j+1]).
-// Outputs of the slot: t, S (physical row of the pivot with the i-th
-// smallest column, -1 beyond t), pc (pivot columns in the panel, ascending,
-// -1 beyond t), Gm = G - I (128 x 128, zero beyond t).
+// [128 slot, 128 slot + 128), with candidate rows cand[seg[j] .. seg[j+1]);
+// the slot's pivots from earlier waves are its first basis rows.  Outputs of
+// the slot: t, S (physical row of the pivot with the i-th smallest column,
+// -1 beyond t), pc (pivot columns in the panel, ascending, -1 beyond t),
+// Gm = G - I (128 x 128, zero beyond t) over all t pivot rows.
 __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t n,
                                                     const int64_t *__restrict__ seg, const int32_t *__restrict__ cand,
                                                     const int32_t *__restrict__ job_slot,
                                                     const uint16_t *__restrict__ inv_tab,
                                                     int32_t *__restrict__ is_piv_row, int32_t *__restrict__ t_slot,
                                                     int32_t *__restrict__ S_slot, int32_t *__restrict__ pc_slot,
-                                                    uint16_t *__restrict__ Gm_all, ModP mp)
+                                                    uint16_t *__restrict__ Gm_all, int32_t *__restrict__ wave_slot,
+                                                    ModP mp)
 {
     extern __shared__ __align__(16) uint16_t panel_smem[];
     uint16_t(*aug)[2 * PANEL] = reinterpret_cast<uint16_t(*)[2 * PANEL]>(panel_smem);  // [PANEL][256]
@@ -529,7 +507,8 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
     int32_t *S_out = S_slot + (int64_t)slot * PANEL;
     int32_t *pc_out = pc_slot + (int64_t)slot * PANEL;
     uint16_t *Gm_out = Gm_all + (int64_t)slot * PANEL * PANEL;
-    if (ncand > 0) {
+    if (ncand == 0) return;   // nothing new: the slot keeps its outputs
+    {
         // inverse table into shared memory (16-byte copies; p <= 65536 entries)
         const int nvec = (int)((p + 7) / 8);
         const uint4 *src = reinterpret_cast<const uint4 *>(inv_tab);
@@ -537,8 +516,22 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
         for (int i = c; i < nvec; i += 2 * PANEL) dst[i] = src[i];
     }
     if (c < PANEL) brow[c] = -1;     // basis row whose pivot is panel column c
+    // The slot's pivots from earlier waves are in reduced echelon form on the
+    // panel (identity at their columns): they enter the basis as they are,
+    // with unit coefficient rows.
+    const int tpre = t_slot[slot];
+    for (int i = 0; i < tpre; ++i) {
+        const int64_t row = S_out[i];
+        aug[i][c] = (uint16_t)((c < bw) ? D[row * ldd + c0 + c] : ((c - PANEL == i) ? 1u : 0u));
+    }
+    if (c < tpre) {
+        bcol[c] = pc_out[c];
+        S[c] = S_out[c];
+    }
     __syncthreads();
-    int t = 0;
+    if (c < tpre) brow[bcol[c]] = c;
+    __syncthreads();
+    int t = tpre;
     // software pipeline: the next candidate's panel entry is loaded while the
     // current one is processed
     uint32_t vnext = 0;
@@ -601,7 +594,12 @@ __global__ void __launch_bounds__(256) panel_kernel(const uint16_t *__restrict__
         rnk[c] = r;
     }
     __syncthreads();
-    if (c == 0) t_slot[slot] = t;
+    if (c == 0) {
+        t_slot[slot] = t;
+        // this wave: new pivots, and candidates that stayed dependent
+        wave_slot[2 * slot] = t - tpre;
+        wave_slot[2 * slot + 1] = ncand - (t - tpre);
+    }
     if (c < PANEL) {
         // the pivot with the c-th smallest column lands in physical row S[c];
         // entries beyond t are sentinels (-1): the products skip them
@@ -634,6 +632,20 @@ struct PanelPlan {
     int64_t boff;
     int32_t slot, nc;
 };
+
+// A-operand planes of G - I for the jobs of a chunk: rows q * 128 + i of dst
+// = row i of the slot's Gm (blockIdx.y = q, blockIdx.x = i).
+__global__ void gather_gm_planes_kernel(Planes dst, const uint16_t *__restrict__ Gm_all,
+                                        const PanelPlan *__restrict__ plan, uint32_t p)
+{
+    const int q = blockIdx.y, i = blockIdx.x, j = threadIdx.x;
+    const uint32_t a = Gm_all[(int64_t)plan[q].slot * PANEL * PANEL + i * PANEL + j];
+    int hi, lo;
+    digits(a, p, hi, lo);
+    const size_t off = (size_t)(q * PANEL + i) * (size_t)dst.kp + (size_t)j;
+    dst.plane(0)[off] = i2bf(hi);
+    dst.plane(1)[off] = i2bf(lo);
+}
 
 // B-operand planes of D[S]^T for every panel of a chunk (blockIdx.z):
 // dst[boff + i][j] = D[S_j][128 slot + i] for j < t, else 0.
@@ -703,8 +715,8 @@ __global__ void gather_h_planes_kernel(Planes dst, const uint16_t *__restrict__ 
 // mode 1: D[S] += (G - I) * D[S];  mode 2: D[cand] -= H * D[S].
 __global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const PanelPlan *__restrict__ plan,
                                   const int32_t *__restrict__ t_slot, const int32_t *__restrict__ S_slot,
-                                  const int64_t *__restrict__ seg, const int32_t *__restrict__ cand, int job0,
-                                  int64_t row_base)
+                                  const int32_t *__restrict__ wave_slot, const int64_t *__restrict__ seg,
+                                  const int32_t *__restrict__ cand, int job0, int64_t row_base)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int64_t off = 0;
@@ -716,13 +728,15 @@ __global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const P
         P.N = pl.nc;
         P.c_col0 = (int64_t)pl.slot * PANEL;
         if (mode == 1) {
+            // no new pivot on the panel: G = I, nothing to do
             P.a_row0 = q * PANEL;
-            P.M = t;
+            P.M = wave_slot[2 * pl.slot] > 0 ? t : 0;
             P.c_rows = S_slot + (int64_t)pl.slot * PANEL;
         } else {
+            // no dependent candidate: nothing to clear
             const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
             P.a_row0 = (int32_t)(b - row_base);
-            P.M = (e - b > t) ? (int32_t)(e - b) : 0;   // nothing to clear when every candidate is a pivot
+            P.M = wave_slot[2 * pl.slot + 1] > 0 ? (int32_t)(e - b) : 0;
             P.c_rows = cand + b;
         }
         if (t == 0) P.M = 0;
@@ -835,7 +849,7 @@ static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_
 // job_slot or equal to the job index): D[S] <- G * D[S], then clear the other
 // candidates on their panel and find their new leads.
 struct PanelWork {
-    int32_t *t_slot, *S_slot, *pc_slot;
+    int32_t *t_slot, *S_slot, *pc_slot, *wave_slot;
     uint16_t *Gm_all;
     int32_t *lead;
     PanelPlan *plan_dev;
@@ -844,8 +858,7 @@ struct PanelWork {
 };
 
 static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<PanelPlan> &plan, const int64_t *seg,
-                        const int32_t *cand, const int32_t *job_slot, int job0, int64_t row_base, int64_t rows_max,
-                        const uint16_t *Gm_first)
+                        const int32_t *cand, const int32_t *job_slot, int job0, int64_t row_base, int64_t rows_max)
 {
     const ModP &mp = *E.mp;
     cudaStream_t s = E.s;
@@ -855,12 +868,14 @@ static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<Panel
     for (const auto &pl : plan) ncmax = pl.nc > ncmax ? pl.nc : ncmax;
     GBLA_CUDA_TRY(cudaMemcpyAsync(W.plan_dev, plan.data(), sizeof(PanelPlan) * (size_t)nj, cudaMemcpyHostToDevice, s));
     // G - I of the jobs' slots as the A operand (rows q * 128 ..)
-    GBLA_TRY(to_planes(W.Gp, (int64_t)nj * PANEL, PANEL, Gm_first, PANEL, 0, false, nullptr, nullptr, mp, s));
+    gather_gm_planes_kernel<<<dim3(PANEL, (unsigned)nj), PANEL, 0, s>>>(W.Gp, W.Gm_all, W.plan_dev, mp.p);
+    GBLA_CUDA_TRY(launch_check());
     dim3 gt((unsigned)(round_up(ncmax, 128) / 32), PANEL / 32, (unsigned)nj);
     gather_t_planes_kernel<<<gt, dim3(32, 8), 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp.p,
                                                       mp.r256);
     GBLA_CUDA_TRY(launch_check());
-    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, seg, cand, job0, row_base);
+    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
+                                       row_base);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(modgemm_grouped(W.Gp, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, +1, mp, E.variant, E.err, s, E.ctr));
     // D[cand] -= D[cand, pc] * D[S]   (the pivot rows have zero multipliers)
@@ -871,7 +886,8 @@ static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<Panel
     gather_h_planes_kernel<<<dim3(rows_blocks, (unsigned)nj), PANEL, 0, s>>>(
         W.H, E.D16, E.ldd, seg, cand, job_slot, job0, row_base, W.pc_slot, W.t_slot, E.is_piv_row, mp.p);
     GBLA_CUDA_TRY(launch_check());
-    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 2, W.plan_dev, W.t_slot, W.S_slot, seg, cand, job0, row_base);
+    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 2, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
+                                       row_base);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(modgemm_grouped(W.H, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, -1, mp, E.variant, E.err, s, E.ctr));
     return GBLA_OK;
@@ -888,8 +904,8 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     int rc = GBLA_OK;
     int64_t rank = 0;
     PanelWork W{};
-    int32_t *cand = nullptr, *fill = nullptr, *info = nullptr;
-    int64_t *off = nullptr, *seg2 = nullptr, *rank_dev = nullptr;
+    int32_t *cand = nullptr, *fill = nullptr, *info = nullptr, *job_slot = nullptr;
+    int64_t *off = nullptr, *seg = nullptr, *rank_dev = nullptr;
     uint16_t *inv_tab = nullptr;
     // Phase B works on chunks of panels whose D[S]^T planes fit this many rows.
     const int64_t BS_ROWS = int64_t(1) << 20;
@@ -914,11 +930,13 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         ESTEP(dalloc_t(&fill, (size_t)npan + 1, s));
         ESTEP(dalloc_t(&off, (size_t)npan + 2, s));
         ESTEP(dalloc_t(&info, 4, s));
-        ESTEP(dalloc_t(&seg2, 4, s));
+        ESTEP(dalloc_t(&seg, (size_t)npan + 2, s));
+        ESTEP(dalloc_t(&job_slot, (size_t)npan + 1, s));
         ESTEP(dalloc_t(&rank_dev, 2, s));
         ESTEP(dalloc_t(&W.t_slot, (size_t)npan + 1, s));
         ESTEP(dalloc_t(&W.S_slot, (size_t)npan * PANEL, s));
         ESTEP(dalloc_t(&W.pc_slot, (size_t)npan * PANEL, s));
+        ESTEP(dalloc_t(&W.wave_slot, (size_t)npan * 2 + 2, s));
         ESTEP(dalloc_t(&W.Gm_all, (size_t)npan * PANEL * PANEL, s));
         ESTEP(dalloc_t(&W.plan_dev, (size_t)npan + 1, s));
         ESTEP(dalloc_t(&W.probs, (size_t)npan + 2, s));
@@ -928,69 +946,63 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         ESTEP(planes_alloc(&W.H, m + PANEL, PANEL, 2, s));
         ECUDA(cudaMemsetAsync(E.is_piv_row, 0, sizeof(int32_t) * (size_t)m, s));
         ECUDA(cudaMemsetAsync(W.t_slot, 0, sizeof(int32_t) * (size_t)(npan + 1), s));
-        ECUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)(npan + 1), s));
-        ECUDA(cudaMemsetAsync(off, 0, sizeof(int64_t) * (size_t)(npan + 2), s));
         inverse_table_kernel<<<(mp.p + 255) / 256, 256, 0, s>>>(inv_tab, mp);
         ECUDA(launch_check());
-        // ---- leads, and each panel's fresh candidates (rows leading in it)
+        // ---- leads of all rows
         row_leads_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(E.D16, E.ldd, n, m, nullptr, nullptr, 0,
                                                                          nullptr, W.lead);
         ECUDA(launch_check());
-        panel_count_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, W.lead, E.is_piv_row, off);
-        ECUDA(launch_check());
-        ESTEP(scan_i64(off, off, npan + 1, nullptr, s));
-        panel_scatter_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, W.lead, E.is_piv_row, off, fill, cand);
-        ECUDA(launch_check());
-        panel_sort_kernel<<<(unsigned)((npan + 255) / 256), 256, 0, s>>>(npan, off, cand);
-        ECUDA(launch_check());
-        std::vector<int64_t> off_h((size_t)npan + 1);
-        ECUDA(cudaMemcpyAsync(off_h.data(), off, sizeof(int64_t) * (size_t)(npan + 1), cudaMemcpyDeviceToHost, s));
-        // ---- phase A: the bases of all panels at once (one CTA each)
-        panel_kernel<<<(unsigned)npan, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, n, off, cand, nullptr, inv_tab,
-                                                                   E.is_piv_row, W.t_slot, W.S_slot, W.pc_slot,
-                                                                   W.Gm_all, mp);
-        ECUDA(launch_check());
-        ECUDA(cudaStreamSynchronize(s));
-        // ---- phase B: apply them, chunk by chunk of panels (grouped products)
-        for (int64_t k0 = 0; k0 < npan;) {
-            std::vector<PanelPlan> plan;
-            int64_t boff = 0, k1 = k0;
-            while (k1 < npan) {
-                const int32_t nc = (int32_t)(n - k1 * PANEL);
-                if (!plan.empty() && boff + round_up(nc, 128) > BS_ROWS) break;
-                plan.push_back(PanelPlan{boff, (int32_t)k1, nc});
-                boff += round_up(nc, 128);
-                ++k1;
-            }
-            const int64_t rows = off_h[(size_t)k1] - off_h[(size_t)k0];
-            ESTEP(apply_panels(E, W, plan, off, cand, nullptr, (int)k0, off_h[(size_t)k0], rows,
-                               W.Gm_all + k0 * PANEL * PANEL));
-            if (rows > 0) {
-                row_leads_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(
-                    E.D16, E.ldd, n, rows, cand + off_h[(size_t)k0], nullptr, -1, E.is_piv_row, W.lead);
-                ECUDA(launch_check());
-            }
-            k0 = k1;
-        }
-        // ---- phase C: rows that were dependent on their panel moved right;
-        // revisit their panels one at a time (the panel's pivots re-enter first)
-        for (int64_t iter = 0;; ++iter) {
-            if (iter > m) { rc = GBLA_E_INTERNAL; goto done; }
-            revisit_kernel<<<1, 1024, 0, s>>>(m, W.lead, E.is_piv_row, W.t_slot, W.S_slot, cand, info, seg2);
+        // ---- waves: every panel with candidates (non-pivot rows leading in
+        // it) is processed at once; rows that were dependent on their panel
+        // move right and are candidates of the next wave.  Leads only grow,
+        // so there are at most npan waves.
+        std::vector<int32_t> slots_h((size_t)npan + 1);
+        std::vector<int64_t> seg_h((size_t)npan + 2);
+        for (int64_t wave = 0;; ++wave) {
+            if (wave > npan) { rc = GBLA_E_INTERNAL; goto done; }
+            ECUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)(npan + 1), s));
+            ECUDA(cudaMemsetAsync(off, 0, sizeof(int64_t) * (size_t)(npan + 2), s));
+            panel_count_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, W.lead, E.is_piv_row, off);
             ECUDA(launch_check());
-            int32_t k = -1;
-            int64_t seg_h[2];
-            ECUDA(cudaMemcpyAsync(&k, info, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            ECUDA(cudaMemcpyAsync(seg_h, seg2, sizeof(seg_h), cudaMemcpyDeviceToHost, s));
+            ESTEP(scan_i64(off, off, npan + 1, nullptr, s));
+            panel_scatter_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, W.lead, E.is_piv_row, off, fill,
+                                                                             cand);
+            ECUDA(launch_check());
+            panel_sort_kernel<<<(unsigned)((npan + 255) / 256), 256, 0, s>>>(npan, off, cand);
+            ECUDA(launch_check());
+            make_jobs_kernel<<<1, 1024, 0, s>>>(npan, off, job_slot, seg, info);
+            ECUDA(launch_check());
+            int32_t njobs = 0;
+            ECUDA(cudaMemcpyAsync(&njobs, info, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             ECUDA(cudaStreamSynchronize(s));
-            if (k < 0) break;
-            panel_kernel<<<1, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, n, seg2, cand, info, inv_tab, E.is_piv_row,
-                                                          W.t_slot, W.S_slot, W.pc_slot, W.Gm_all, mp);
+            if (njobs == 0) break;
+            ECUDA(cudaMemcpyAsync(slots_h.data(), job_slot, sizeof(int32_t) * (size_t)njobs, cudaMemcpyDeviceToHost, s));
+            ECUDA(cudaMemcpyAsync(seg_h.data(), seg, sizeof(int64_t) * (size_t)(njobs + 1), cudaMemcpyDeviceToHost, s));
+            panel_kernel<<<(unsigned)njobs, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, n, seg, cand, job_slot, inv_tab,
+                                                                      E.is_piv_row, W.t_slot, W.S_slot, W.pc_slot,
+                                                                      W.Gm_all, W.wave_slot, mp);
             ECUDA(launch_check());
-            std::vector<PanelPlan> plan{PanelPlan{0, k, (int32_t)(n - (int64_t)k * PANEL)}};
-            ESTEP(apply_panels(E, W, plan, seg2, cand, info, 0, 0, seg_h[1], W.Gm_all + (int64_t)k * PANEL * PANEL));
-            row_leads_kernel<<<(unsigned)((seg_h[1] * 32 + 255) / 256), 256, 0, s>>>(
-                E.D16, E.ldd, n, m, cand, seg2, -1, E.is_piv_row, W.lead);
+            ECUDA(cudaStreamSynchronize(s));
+            // apply the new bases, chunk by chunk of jobs (grouped products)
+            for (int j0 = 0; j0 < njobs;) {
+                std::vector<PanelPlan> plan;
+                int64_t boff = 0;
+                int j1 = j0;
+                while (j1 < njobs) {
+                    const int32_t nc = (int32_t)(n - (int64_t)slots_h[(size_t)j1] * PANEL);
+                    if (!plan.empty() && boff + round_up(nc, 128) > BS_ROWS) break;
+                    plan.push_back(PanelPlan{boff, slots_h[(size_t)j1], nc});
+                    boff += round_up(nc, 128);
+                    ++j1;
+                }
+                const int64_t rows = seg_h[(size_t)j1] - seg_h[(size_t)j0];
+                ESTEP(apply_panels(E, W, plan, seg, cand, job_slot, j0, seg_h[(size_t)j0], rows));
+                j0 = j1;
+            }
+            // the candidates that did not become pivots lead right of their panel now
+            const int64_t ncand = seg_h[(size_t)njobs];
+            row_leads_kernel<<<(unsigned)((ncand * 32 + 255) / 256), 256, 0, s>>>(E.D16, E.ldd, n, ncand, cand,
+                                                                                  nullptr, -1, E.is_piv_row, W.lead);
             ECUDA(launch_check());
         }
         compact_slots_kernel<<<1, 32, 0, s>>>(npan, W.t_slot, W.S_slot, W.pc_slot, E.prow, E.pcol, rank_dev);
@@ -1034,11 +1046,13 @@ done:
     dfree(fill, s);
     dfree(off, s);
     dfree(info, s);
-    dfree(seg2, s);
+    dfree(seg, s);
+    dfree(job_slot, s);
     dfree(rank_dev, s);
     dfree(W.t_slot, s);
     dfree(W.S_slot, s);
     dfree(W.pc_slot, s);
+    dfree(W.wave_slot, s);
     dfree(W.Gm_all, s);
     dfree(W.plan_dev, s);
     dfree(W.probs, s);
