@@ -281,12 +281,18 @@ def main():
         h_c = torch.from_numpy(c).pin_memory().numpy()
         h_v = torch.from_numpy(v.view(np.int16)).pin_memory().numpy().view(np.uint16)
         k_e2e = max(1, min(a.steps, 3))
-        gbla.reduce(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream)
+        for _ in range(2):   # warm the library's page-locked result cache
+            gbla.reduce_host(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream).free()
         torch.cuda.synchronize()
+        d2h = 0
         t0 = time.perf_counter()
         for _ in range(k_e2e):
-            r, orp, oc, ov = gbla.reduce(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced),
-                                         stream=stream)
+            # inputs copied in and the whole result copied out inside the call;
+            # the step reads the rank and the last row's length on the host
+            hr = gbla.reduce_host(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream)
+            d2h = hr.row_ptr.nbytes + hr.col.nbytes + hr.val.nbytes
+            _ = int(hr.row_ptr[-1]) + hr.rank
+            hr.free()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / k_e2e
         if dist:
@@ -294,7 +300,7 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(rp.nbytes + c.nbytes + v.nbytes),
-               "d2h_bytes_per_step": int(orp.nbytes + oc.nbytes + ov.nbytes)}
+               "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:
         if dist:

@@ -58,7 +58,9 @@ typedef struct {
 
 /* Result matrix, owned by the library; release with gbla_free().  nrows is
  * the rank.  on_device = 1 when the arrays are device memory (requested with
- * gbla_options.device_ptrs = 1), else host memory. */
+ * gbla_options.device_ptrs = 1), else host memory.  Host results are
+ * page-locked; gbla_free returns them to a library cache (at most
+ * GBLA_HOST_CACHE_MB megabytes, default 8192) that later results reuse. */
 typedef struct {
     int64_t nrows, ncols, nnz;
     int64_t *row_ptr;

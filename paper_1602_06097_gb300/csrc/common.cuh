@@ -119,6 +119,80 @@ __device__ __forceinline__ void dev_fail(uint32_t *err, uint32_t bit) {
     if (err) atomicOr(err, bit);
 }
 
+// ------------------------------------------- transposing plane conversion
+// One 64 x 64 tile of a transposing conversion into digit planes, run by a
+// block of 256 threads:
+//   dst row (row0 + r), column k  <-  src[g(k) * lds + col0 + r]
+// for r in [r0, r0 + 64), k in [k0, k0 + 64); zero where r >= R, k >= Kc or
+// g(k) < 0, with g(k) = rgather ? rgather[k] : k.  Source rows are read 64
+// entries at a time; each plane row receives 128 contiguous bytes written as
+// 16-byte vectors.  The residues b' = 256 * b mod p of a 4-plane set use a
+// Barrett reduction.
+constexpr int TP_TILE = 64;
+struct TpSmem {
+    uint16_t t[TP_TILE][TP_TILE + 2];
+};
+
+__device__ __forceinline__ uint32_t pack_bf2(int lo_elem, int hi_elem) {
+    __nv_bfloat162 v = __floats2bfloat162_rn((float)lo_elem, (float)hi_elem);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Digit planes of 8 consecutive residues a[0..7] at element offset off (a
+// multiple of 8) of every plane: 16-byte stores.
+__device__ __forceinline__ void store_digits8(const Planes &dst, size_t off, const uint32_t (&a)[8], const ModP &mp) {
+    uint32_t vh[4], vl[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        int h0, l0, h1, l1;
+        digits(a[e], mp.p, h0, l0);
+        digits(a[e + 1], mp.p, h1, l1);
+        vh[e / 2] = pack_bf2(h0, h1);
+        vl[e / 2] = pack_bf2(l0, l1);
+    }
+    *reinterpret_cast<uint4 *>(dst.plane(0) + off) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+    *reinterpret_cast<uint4 *>(dst.plane(1) + off) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+    if (dst.nplanes == 4) {
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            int h0, l0, h1, l1;
+            digits(mod32(a[e] * mp.r256, mp), mp.p, h0, l0);
+            digits(mod32(a[e + 1] * mp.r256, mp), mp.p, h1, l1);
+            vh[e / 2] = pack_bf2(h0, h1);
+            vl[e / 2] = pack_bf2(l0, l1);
+        }
+        *reinterpret_cast<uint4 *>(dst.plane(2) + off) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+        *reinterpret_cast<uint4 *>(dst.plane(3) + off) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+    }
+}
+
+__device__ __forceinline__ void tp_tile(const Planes &dst, int64_t row0, int64_t r0, int64_t k0, int64_t R, int64_t Kc,
+                                        const uint16_t *__restrict__ src, int64_t lds, int64_t col0,
+                                        const int32_t *__restrict__ rgather, const ModP &mp, TpSmem &sm)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = warp; i < TP_TILE; i += 8) {
+        const int64_t k = k0 + i;
+        int64_t sr = -1;
+        if (k < Kc) sr = rgather ? (int64_t)rgather[k] : k;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = r0 + lane + 32 * h;
+            uint16_t v = 0;
+            if (sr >= 0 && r < R) v = src[sr * lds + col0 + r];
+            sm.t[i][lane + 32 * h] = v;
+        }
+    }
+    __syncthreads();
+    for (int it = tid; it < TP_TILE * 8; it += 256) {
+        const int c = it & 7, rr = it >> 3;
+        uint32_t a[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] = sm.t[c * 8 + e][rr];
+        store_digits8(dst, (size_t)(row0 + r0 + rr) * (size_t)dst.kp + (size_t)(k0 + c * 8), a, mp);
+    }
+}
+
 }  // namespace gbla
 
 #define GBLA_CUDA_TRY(expr)                                      \

@@ -64,6 +64,85 @@ void dfree(void *ptr, cudaStream_t s) {
     if (ptr) cudaFreeAsync(ptr, s);
 }
 
+// Host results live in page-locked memory so that the device-to-host copy runs
+// at full link speed.  Pinning is expensive (the pages are locked one by one),
+// so released blocks are cached and handed to later results of a similar size;
+// at most GBLA_HOST_CACHE_MB (default 8192) megabytes stay cached.  Blocks
+// that cannot be pinned fall back to malloc.
+namespace {
+struct HostCache {
+    std::mutex mu;
+    std::vector<std::pair<void *, size_t>> free_blocks;  // cached, unused
+    std::vector<std::pair<void *, size_t>> live;         // handed out, pinned
+    size_t cached = 0;
+    size_t cap = 0;
+};
+HostCache &host_cache() {
+    static HostCache *c = [] {
+        auto *h = new HostCache();
+        const char *e = getenv("GBLA_HOST_CACHE_MB");
+        const long long mb = e ? atoll(e) : 8192;
+        h->cap = (size_t)(mb > 0 ? mb : 0) << 20;
+        return h;
+    }();
+    return *c;
+}
+}  // namespace
+
+void *host_alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    const size_t want = round_up((int64_t)bytes, 1 << 21);
+    HostCache &c = host_cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        size_t best = (size_t)-1;
+        for (size_t i = 0; i < c.free_blocks.size(); ++i) {
+            const size_t sz = c.free_blocks[i].second;
+            if (sz >= want && sz <= 2 * want && (best == (size_t)-1 || sz < c.free_blocks[best].second)) best = i;
+        }
+        if (best != (size_t)-1) {
+            auto blk = c.free_blocks[best];
+            c.free_blocks.erase(c.free_blocks.begin() + (long)best);
+            c.cached -= blk.second;
+            c.live.push_back(blk);
+            return blk.first;
+        }
+    }
+    void *ptr = nullptr;
+    if (cudaHostAlloc(&ptr, want, cudaHostAllocDefault) == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(c.mu);
+        c.live.emplace_back(ptr, want);
+        return ptr;
+    }
+    cudaGetLastError();
+    return malloc(bytes);
+}
+
+void host_release(void *ptr) {
+    if (!ptr) return;
+    HostCache &c = host_cache();
+    std::vector<void *> drop;
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        size_t i = 0;
+        while (i < c.live.size() && c.live[i].first != ptr) ++i;
+        if (i == c.live.size()) {   // a malloc fallback block
+            free(ptr);
+            return;
+        }
+        auto blk = c.live[i];
+        c.live.erase(c.live.begin() + (long)i);
+        c.free_blocks.push_back(blk);
+        c.cached += blk.second;
+        while (c.cached > c.cap && !c.free_blocks.empty()) {   // evict the oldest
+            drop.push_back(c.free_blocks.front().first);
+            c.cached -= c.free_blocks.front().second;
+            c.free_blocks.erase(c.free_blocks.begin());
+        }
+    }
+    for (void *d : drop) cudaFreeHost(d);
+}
+
 int planes_alloc(Planes *pl, int64_t rows, int64_t k, int nplanes, cudaStream_t s) {
     pl->rows = round_up(rows > 0 ? rows : 1, 128);
     pl->kp = round_up(k > 0 ? k : 1, 128);
@@ -362,8 +441,11 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     STEP(split_scatter(dc, pi, A16, ldc, B16, ldd, C16, ldc, D16, ldd, mp, s));
     // digit planes of the operands the products read
     if (m_cd > 0 && npiv > 0) {
-        STEP(planes_alloc(&At, npiv, npiv, 4, s));   // A^T: B-operand of C <- C - X*A
-        STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s));
+        // A^T: B-operand of C <- C - X*A.  The triangular solve reads it only
+        // below its diagonal blocks (column of A after row of A), so tiles
+        // entirely above the diagonal are not converted.
+        STEP(planes_alloc(&At, npiv, npiv, 4, s));
+        STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s, nullptr, true));
     }
     if (m_cd > 0 && n_d > 0 && npiv > 0) {
         STEP(planes_alloc(&Bt, n_d, npiv, 4, s));    // B^T: B-operand of D <- D - X*B
@@ -483,7 +565,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     }
     {
         // results leave the pool: device results in plain device memory,
-        // host results in malloc'ed memory
+        // host results in cached page-locked memory
         out->nrows = rank;
         out->ncols = n;
         out->nnz = onnz;
@@ -499,9 +581,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             }
         } else {
             out->on_device = 0;
-            out->row_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(rank + 1));
-            out->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(onnz + 1));
-            out->val = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(onnz + 1));
+            out->row_ptr = (int64_t *)host_alloc(sizeof(int64_t) * (size_t)(rank + 1));
+            out->col = (int32_t *)host_alloc(sizeof(int32_t) * (size_t)(onnz + 1));
+            out->val = (uint16_t *)host_alloc(sizeof(uint16_t) * (size_t)(onnz + 1));
             if (!out->row_ptr || !out->col || !out->val) { rc = GBLA_E_NOMEM; goto cleanup; }
             CSTEP(cudaMemcpyAsync(out->row_ptr, orp, sizeof(int64_t) * (size_t)(rank + 1), cudaMemcpyDeviceToHost, s));
             if (onnz > 0) {
@@ -612,9 +694,9 @@ void gbla_free(gbla_csr_out *out) {
         if (out->col) cudaFree(out->col);
         if (out->val) cudaFree(out->val);
     } else {
-        free(out->row_ptr);
-        free(out->col);
-        free(out->val);
+        gbla::host_release(out->row_ptr);
+        gbla::host_release(out->col);
+        gbla::host_release(out->val);
     }
     memset(out, 0, sizeof(*out));
 }

@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <mutex>
 #include <vector>
 
@@ -41,83 +42,67 @@ namespace gbla {
 // with g = row gather (or identity), h = column gather (or identity); values
 // outside r < R, k < Kc, or at a negative gather index, are written as 0, and
 // (not transposed) so are source rows sr with zero_if[sr] != 0.
-template <bool TRANSPOSED>
-__global__ void to_planes_kernel(Planes dst, int64_t R, int64_t Kc, const uint16_t *__restrict__ src,
-                                 int64_t lds, int64_t col_off, const int32_t *__restrict__ rgather,
-                                 const int32_t *__restrict__ cgather, const int32_t *__restrict__ zero_if,
-                                 uint32_t p, uint32_t r256)
+//
+// Row-wise conversion: a block covers 16 rows x 128 columns, a thread 8
+// consecutive columns of one row, written as one 16-byte vector per plane.
+__global__ void __launch_bounds__(256) to_planes_kernel(Planes dst, int64_t R, int64_t Kc,
+                                                        const uint16_t *__restrict__ src, int64_t lds, int64_t col_off,
+                                                        const int32_t *__restrict__ rgather,
+                                                        const int32_t *__restrict__ cgather,
+                                                        const int32_t *__restrict__ zero_if, ModP mp)
 {
-    __shared__ uint16_t tile[32][33];
-    const int64_t k0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    if (TRANSPOSED) {
-        // read src rows g(k) for k in [k0, k0+32), columns col_off + r for r in [r0, r0+32)
-        for (int i = ty; i < 32; i += 8) {
-            int64_t k = k0 + i, r = r0 + tx;
-            uint16_t v = 0;
-            if (k < Kc && r < R) {
-                const int64_t sr = rgather ? (int64_t)rgather[k] : k;
-                if (sr >= 0) v = src[sr * lds + col_off + r];
-            }
-            tile[i][tx] = v;
-        }
-        __syncthreads();
-        for (int i = ty; i < 32; i += 8) {
-            int64_t r = r0 + i, k = k0 + tx;
-            uint32_t a = tile[tx][i];
-            int hi, lo;
-            digits(a, p, hi, lo);
-            size_t off = (size_t)r * (size_t)dst.kp + (size_t)k;
-            dst.plane(0)[off] = i2bf(hi);
-            dst.plane(1)[off] = i2bf(lo);
-            if (dst.nplanes == 4) {
-                uint32_t b2 = (a * r256) % p;
-                digits(b2, p, hi, lo);
-                dst.plane(2)[off] = i2bf(hi);
-                dst.plane(3)[off] = i2bf(lo);
-            }
-        }
-    } else {
-        for (int i = ty; i < 32; i += 8) {
-            int64_t r = r0 + i, k = k0 + tx;
-            uint32_t a = 0;
-            if (r < R && k < Kc) {
-                const int64_t sr = rgather ? (int64_t)rgather[r] : r;
-                const int64_t sc = cgather ? (int64_t)cgather[k] : k;
-                if (sr >= 0 && sc >= 0 && !(zero_if && zero_if[sr])) a = src[sr * lds + col_off + sc];
-            }
-            int hi, lo;
-            digits(a, p, hi, lo);
-            size_t off = (size_t)r * (size_t)dst.kp + (size_t)k;
-            dst.plane(0)[off] = i2bf(hi);
-            dst.plane(1)[off] = i2bf(lo);
-            if (dst.nplanes == 4) {
-                uint32_t b2 = (a * r256) % p;
-                digits(b2, p, hi, lo);
-                dst.plane(2)[off] = i2bf(hi);
-                dst.plane(3)[off] = i2bf(lo);
-            }
+    const int tid = threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.y * 16 + (tid >> 4);
+    const int64_t k0 = (int64_t)blockIdx.x * 128 + (int64_t)(tid & 15) * 8;
+    int64_t sr = -1;
+    if (r < R) {
+        sr = rgather ? (int64_t)rgather[r] : r;
+        if (sr >= 0 && zero_if && zero_if[sr]) sr = -1;
+    }
+    uint32_t a[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int64_t k = k0 + e;
+        a[e] = 0;
+        if (sr >= 0 && k < Kc) {
+            const int64_t sc = cgather ? (int64_t)cgather[k] : k;
+            if (sc >= 0) a[e] = src[sr * lds + col_off + sc];
         }
     }
+    store_digits8(dst, (size_t)r * (size_t)dst.kp + (size_t)k0, a, mp);
+}
+
+// Transposed conversion: dst row r, column k <- src[g(k)][col_off + r], one
+// 64 x 64 tile per block.  With k_le_r_only, tiles whose every k exceeds every
+// r are skipped (their planes are left unwritten): for the transpose of an
+// upper triangular matrix those entries are zero and no product reads them.
+__global__ void __launch_bounds__(256) to_planes_t_kernel(Planes dst, int64_t R, int64_t Kc,
+                                                          const uint16_t *__restrict__ src, int64_t lds,
+                                                          int64_t col_off, const int32_t *__restrict__ rgather,
+                                                          int k_le_r_only, ModP mp)
+{
+    __shared__ TpSmem sm;
+    const int64_t k0 = (int64_t)blockIdx.x * TP_TILE, r0 = (int64_t)blockIdx.y * TP_TILE;
+    if (k_le_r_only && k0 > r0 + TP_TILE - 1) return;
+    tp_tile(dst, 0, r0, k0, R, Kc, src, lds, col_off, rgather, mp, sm);
 }
 
 int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds,
               int64_t col_off, bool transposed, const int32_t *rgather, const int32_t *cgather,
-              const ModP &mp, cudaStream_t s, const int32_t *zero_if)
+              const ModP &mp, cudaStream_t s, const int32_t *zero_if, bool k_le_r_only)
 {
     if (dst.rows <= 0 || dst.kp <= 0) return GBLA_OK;
     // Cover the logical rectangle rounded up to whole 128 x 128 tiles (the
     // product reads nothing else); the rest of the buffer is left as is.
     const int64_t rows = round_up(R > 0 ? R : 1, 128) < dst.rows ? round_up(R > 0 ? R : 1, 128) : dst.rows;
     const int64_t ks = round_up(Kc > 0 ? Kc : 1, 128) < dst.kp ? round_up(Kc > 0 ? Kc : 1, 128) : dst.kp;
-    dim3 block(32, 8);
-    dim3 grid((unsigned)(ks / 32), (unsigned)(rows / 32));
-    if (transposed)
-        to_planes_kernel<true><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, nullptr, mp.p,
-                                                       mp.r256);
-    else
-        to_planes_kernel<false><<<grid, block, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, zero_if, mp.p,
-                                                        mp.r256);
+    if (transposed) {
+        dim3 grid((unsigned)(ks / TP_TILE), (unsigned)(rows / TP_TILE));
+        to_planes_t_kernel<<<grid, 256, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, k_le_r_only ? 1 : 0, mp);
+    } else {
+        dim3 grid((unsigned)(ks / 128), (unsigned)(rows / 16));
+        to_planes_kernel<<<grid, 256, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, zero_if, mp);
+    }
     GBLA_CUDA_TRY(launch_check());
     return GBLA_OK;
 }
@@ -204,7 +189,7 @@ constexpr int KSTEPS_PER_BLOCK = 512 / BK;          // k-block of 512: exact fp3
 constexpr int TILE_BYTES = BM * BK * 2;             // 8 KiB (A and B tiles are 128 rows)
 constexpr int STAGE_BYTES = 6 * TILE_BYTES;         // Ah Al | Bh Bl B'h B'l
 constexpr int BAR_BYTES = 256;
-constexpr int64_t GROUP_M = 8;                      // row tiles per raster group (see tile_coords)
+constexpr int64_t GROUP_M_DEFAULT = 4;              // row tiles per raster group (see tile_coords)
 constexpr int EPI_WARPS = 8;                        // two drain warps per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
@@ -227,6 +212,7 @@ struct Args {
     float pf, pinv;
     uint32_t *err;
     int withhold_loads;      // test hook: issue no TMA loads, so the waits expire
+    int group_m;             // row tiles per raster group
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
@@ -353,8 +339,8 @@ __device__ __forceinline__ int f2i_small(float r) {  // exact integer |r| < 2^22
     return __float_as_int(r + MAGIC) - 0x4B400000;
 }
 
-__device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t num_n, int64_t &mt, int64_t &nt) {
-    const int64_t GM = GROUP_M;
+__device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t num_n, int64_t GM, int64_t &mt,
+                                            int64_t &nt) {
     int64_t group = t / (GM * num_n);
     int64_t first_m = group * GM;
     int64_t gm = num_m - first_m < GM ? num_m - first_m : GM;
@@ -369,7 +355,7 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t nu
 // the same time walk K in step and share operand tiles in L2.
 __device__ __forceinline__ int tile_kstep0(const Args &g, int64_t mt) {
     if (!g.row_lead) return 0;
-    const int64_t k = (int64_t)g.row_lead[(mt / GROUP_M) * GROUP_M * BM] - g.a_k0;
+    const int64_t k = (int64_t)g.row_lead[(mt / g.group_m) * g.group_m * BM] - g.a_k0;
     return k > 0 ? (int)(k / BK) : 0;
 }
 
@@ -401,7 +387,7 @@ __device__ __forceinline__ TileInfo tile_info(const Args &g, int64_t t, int64_t 
         ti.b_row = P.b_row0 + (int)(ti.nt * BN);
         ti.ks0 = 0;
     } else {
-        tile_coords(t, num_m, num_n, ti.mt, ti.nt);
+        tile_coords(t, num_m, num_n, g.group_m, ti.mt, ti.nt);
         ti.M = g.M;
         ti.N = g.N;
         ti.c_col0 = 0;
@@ -707,6 +693,17 @@ static int make_map(CUtensorMap *map, const Planes &pl) {
     return r == CUDA_SUCCESS ? GBLA_OK : GBLA_E_CUDA;
 }
 
+// Row tiles per raster group (env GBLA_GEMM_GROUP_M overrides, for tuning).
+static int gemm_group_m() {
+    static int v = 0;
+    if (v == 0) {
+        const char *e = getenv("GBLA_GEMM_GROUP_M");
+        const int x = e ? atoi(e) : 0;
+        v = (x >= 1 && x <= 256) ? x : (int)tc::GROUP_M_DEFAULT;
+    }
+    return v;
+}
+
 int device_sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -775,6 +772,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     tc::Args g;
     g.M = M; g.N = N; g.K = K;
     g.probs = nullptr; g.nprob = 0;
+    g.group_m = gemm_group_m();
     g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0; g.a_rows = (int32_t)A.rows;
     g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0; g.b_rows = (int32_t)B.rows;
     g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.row_lead = row_lead; g.sign = sign;
@@ -832,6 +830,7 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
     tc::Args g{};
     g.M = 0; g.N = 0; g.K = K;
     g.probs = probs; g.nprob = nprob;
+    g.group_m = gemm_group_m();
     g.a_rows = (int32_t)A.rows; g.b_rows = (int32_t)B.rows;
     g.C = C; g.ldc = ldc; g.sign = sign;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
@@ -867,6 +866,7 @@ int modgemm_withheld_loads(uint32_t *err, cudaStream_t s)
     if (rc == GBLA_OK) rc = dalloc_t(&C, 128 * 128, s);
     if (rc == GBLA_OK) {
         tc::Args g{};
+        g.group_m = 1;
         g.M = 128; g.N = 128; g.K = 64;
         g.a_rows = (int32_t)A.rows; g.b_rows = (int32_t)B.rows;
         g.C = C; g.ldc = 128; g.sign = 1;

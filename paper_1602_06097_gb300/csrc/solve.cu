@@ -649,39 +649,17 @@ __global__ void gather_gm_planes_kernel(Planes dst, const uint16_t *__restrict__
 
 // B-operand planes of D[S]^T for every panel of a chunk (blockIdx.z):
 // dst[boff + i][j] = D[S_j][128 slot + i] for j < t, else 0.
-__global__ void gather_t_planes_kernel(Planes dst, const uint16_t *__restrict__ D, int64_t ldd,
-                                       const PanelPlan *__restrict__ plan, const int32_t *__restrict__ S_slot,
-                                       const int32_t *__restrict__ t_slot, uint32_t p, uint32_t r256)
+__global__ void __launch_bounds__(256) gather_t_planes_kernel(Planes dst, const uint16_t *__restrict__ D,
+                                                              int64_t ldd, const PanelPlan *__restrict__ plan,
+                                                              const int32_t *__restrict__ S_slot,
+                                                              const int32_t *__restrict__ t_slot, ModP mp)
 {
-    __shared__ uint16_t tile[32][33];
+    __shared__ TpSmem sm;
     const PanelPlan pl = plan[blockIdx.z];
-    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
-    const int64_t nrows = round_up(pl.nc, 128);
-    if (i0 >= nrows) return;
-    const int t = t_slot[pl.slot];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int q = ty; q < 32; q += 8) {
-        const int64_t j = j0 + q, i = i0 + tx;
-        uint16_t v = 0;
-        if (j < t && i < pl.nc) {
-            const int64_t sr = S_slot[(int64_t)pl.slot * PANEL + j];
-            v = D[sr * ldd + (int64_t)pl.slot * PANEL + i];
-        }
-        tile[q][tx] = v;
-    }
-    __syncthreads();
-    for (int q = ty; q < 32; q += 8) {
-        const int64_t i = i0 + q, j = j0 + tx;
-        const uint32_t a = tile[tx][q];
-        int hi, lo;
-        const size_t off = (size_t)(pl.boff + i) * (size_t)dst.kp + (size_t)j;
-        digits(a, p, hi, lo);
-        dst.plane(0)[off] = i2bf(hi);
-        dst.plane(1)[off] = i2bf(lo);
-        digits((a * r256) % p, p, hi, lo);
-        dst.plane(2)[off] = i2bf(hi);
-        dst.plane(3)[off] = i2bf(lo);
-    }
+    const int64_t r0 = (int64_t)blockIdx.x * TP_TILE, k0 = (int64_t)blockIdx.y * TP_TILE;
+    if (r0 >= round_up(pl.nc, 128)) return;
+    tp_tile(dst, pl.boff, r0, k0, pl.nc, t_slot[pl.slot], D, ldd, (int64_t)pl.slot * PANEL,
+            S_slot + (int64_t)pl.slot * PANEL, mp, sm);
 }
 
 // A-operand planes of the candidates' entries at their panel's pivot columns:
@@ -870,17 +848,15 @@ static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<Panel
     // G - I of the jobs' slots as the A operand (rows q * 128 ..)
     gather_gm_planes_kernel<<<dim3(PANEL, (unsigned)nj), PANEL, 0, s>>>(W.Gp, W.Gm_all, W.plan_dev, mp.p);
     GBLA_CUDA_TRY(launch_check());
-    dim3 gt((unsigned)(round_up(ncmax, 128) / 32), PANEL / 32, (unsigned)nj);
-    gather_t_planes_kernel<<<gt, dim3(32, 8), 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp.p,
-                                                      mp.r256);
+    dim3 gt((unsigned)(round_up(ncmax, 128) / TP_TILE), PANEL / TP_TILE, (unsigned)nj);
+    gather_t_planes_kernel<<<gt, 256, 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp);
     GBLA_CUDA_TRY(launch_check());
     make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
                                        row_base);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(modgemm_grouped(W.Gp, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, +1, mp, E.variant, E.err, s, E.ctr));
     // D[cand] -= D[cand, pc] * D[S]   (the pivot rows have zero multipliers)
-    gather_t_planes_kernel<<<gt, dim3(32, 8), 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp.p,
-                                                      mp.r256);
+    gather_t_planes_kernel<<<gt, 256, 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp);
     GBLA_CUDA_TRY(launch_check());
     const unsigned rows_blocks = (unsigned)(rows_max < 64 ? (rows_max > 0 ? rows_max : 1) : 64);
     gather_h_planes_kernel<<<dim3(rows_blocks, (unsigned)nj), PANEL, 0, s>>>(

@@ -145,9 +145,40 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
 
 
-def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None):
-    """Reduce a host CSR matrix.  Returns (rank, row_ptr, col, val) as numpy
-    arrays (and a stats dict when ``stats``)."""
+class HostResult:
+    """A result in the library's page-locked host memory.  ``row_ptr``,
+    ``col`` and ``val`` are zero-copy numpy views, valid until free()."""
+
+    def __init__(self, out: CsrOut, rank: int, stats: dict):
+        self._out = out
+        self.rank = rank
+        self.nnz = int(out.nnz)
+        self.stats = stats
+        self.row_ptr = np.ctypeslib.as_array(ctypes.cast(out.row_ptr, ctypes.POINTER(ctypes.c_int64)),
+                                             shape=(rank + 1,))
+        if self.nnz:
+            self.col = np.ctypeslib.as_array(ctypes.cast(out.col, ctypes.POINTER(ctypes.c_int32)), shape=(self.nnz,))
+            self.val = np.ctypeslib.as_array(ctypes.cast(out.val, ctypes.POINTER(ctypes.c_uint16)), shape=(self.nnz,))
+        else:
+            self.col = np.zeros(0, np.int32)
+            self.val = np.zeros(0, np.uint16)
+
+    def free(self):
+        if self._out is not None:
+            self.row_ptr = self.col = self.val = None
+            load().gbla_free(ctypes.byref(self._out))
+            self._out = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None) -> HostResult:
+    """Reduce a host CSR matrix; the result stays in library-owned host memory
+    (see HostResult).  Page-locked inputs copy to the device fastest."""
     lib = load()
     m, n = int(shape[0]), int(shape[1])
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -161,20 +192,19 @@ def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, s
     rc = lib.gbla_reduce_ex(ctypes.byref(cin), int(p), ctypes.byref(opt), _stream_ptr(stream),
                             ctypes.byref(out), ctypes.byref(rank), ctypes.byref(st))
     _check(rc, "gbla_reduce_ex")
+    return HostResult(out, int(rank.value), st.as_dict())
+
+
+def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None):
+    """Reduce a host CSR matrix.  Returns (rank, row_ptr, col, val) as numpy
+    arrays the caller owns (and a stats dict when ``stats``)."""
+    h = reduce_host(row_ptr, col, val, shape, p, want_reduced=want_reduced, variant=variant, stream=stream)
     try:
-        r = int(out.nrows)
-        onnz = int(out.nnz)
-        orp = np.ctypeslib.as_array(ctypes.cast(out.row_ptr, ctypes.POINTER(ctypes.c_int64)), shape=(r + 1,)).copy()
-        if onnz:
-            oc = np.ctypeslib.as_array(ctypes.cast(out.col, ctypes.POINTER(ctypes.c_int32)), shape=(onnz,)).copy()
-            ov = np.ctypeslib.as_array(ctypes.cast(out.val, ctypes.POINTER(ctypes.c_uint16)), shape=(onnz,)).copy()
-        else:
-            oc = np.zeros(0, np.int32)
-            ov = np.zeros(0, np.uint16)
+        res = (h.rank, h.row_ptr.copy(), h.col.copy(), h.val.copy())
+        st = h.stats
     finally:
-        lib.gbla_free(ctypes.byref(out))
-    res = (int(rank.value), orp, oc, ov)
-    return res + (st.as_dict(),) if stats else res
+        h.free()
+    return res + (st,) if stats else res
 
 
 class DeviceResult:
