@@ -348,6 +348,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     if (nnz > 0 && (!in->col || !in->val)) return GBLA_E_INVAL;
     GBLA_TRY(check_device());
     const ModP mp = make_modp(p);
+    // diagonal blocks of the triangular solve on the tensor cores too
+    const bool tc_leaves =
+        variant == GBLA_GEMM_TCGEN05 || (variant == GBLA_GEMM_AUTO && p >= 8 && tc_supported());
     GemmCounters ctr;
     const long long launches0 = g_launches;
     Timer tm;
@@ -363,7 +366,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     uint16_t *d_val = nullptr;
     PivotInfo pi;
     Multiline ml;
-    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{};
+    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{};
     uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
     uint16_t *A16 = nullptr, *B16 = nullptr;
     int32_t *is_piv_row = nullptr, *prow = nullptr, *pcol = nullptr;
@@ -446,6 +449,11 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         // entirely above the diagonal are not converted.
         STEP(planes_alloc(&At, npiv, npiv, 4, s));
         STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s, nullptr, true));
+        if (tc_leaves) {
+            // inverses of A's diagonal blocks for the tensor-core leaf solves
+            STEP(planes_alloc(&Zt, round_up(npiv, 128), 128, 4, s));
+            STEP(upper_leaf_inverses(A16, ldc, npiv, Zt, mp, s));
+        }
     }
     if (m_cd > 0 && n_d > 0 && npiv > 0) {
         STEP(planes_alloc(&Bt, n_d, npiv, 4, s));    // B^T: B-operand of D <- D - X*B
@@ -472,7 +480,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         lead_h.resize((size_t)m_cd);
         CSTEP(cudaMemcpyAsync(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, cudaMemcpyDeviceToHost, s));
         CSTEP(cudaStreamSynchronize(s));
-        TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr, pi.cd_lead, &lead_h};
+        if (tc_leaves) STEP(planes_alloc(&Ct, m_cd, 128, 2, s));
+        TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr, pi.cd_lead, &lead_h,
+                    tc_leaves ? &Zt : nullptr, tc_leaves ? &Ct : nullptr};
         NvtxRange r("gbla.trsm");
         STEP(trsm_upper(T));
     }
@@ -628,6 +638,8 @@ cleanup:
     multiline_free(&ml, s);
     planes_free(&At, s);
     planes_free(&Arow, s);
+    planes_free(&Zt, s);
+    planes_free(&Ct, s);
     planes_free(&Bt, s);
     planes_free(&Xp, s);
     planes_free(&Xq, s);

@@ -28,6 +28,14 @@ struct GroupProb {
 
 // Grouped product C[c_rows, c_col0:] += sign * A_p * B_p^T for every problem
 // p, one launch (see GroupProb).
+// True on a device with the tcgen05 tensor-core path (compute capability 10.3).
+bool tc_supported();
+
+// Product written as A-operand digit planes: Out[row, out_col0 + n] <- (A*B)[row, n]
+// mod p (tensor-core variant only).
+int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t b_row0, const Planes &Out,
+                      int64_t out_col0, int64_t M, int64_t N, int64_t K, const ModP &mp, uint32_t *err,
+                      cudaStream_t s, GemmCounters *ctr);
 int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K, uint16_t *C,
                     int64_t ldc, int sign, const ModP &mp, int variant, uint32_t *err, cudaStream_t s,
                     GemmCounters *ctr);

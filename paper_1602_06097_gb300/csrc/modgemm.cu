@@ -213,6 +213,8 @@ struct Args {
     uint32_t *err;
     int withhold_loads;      // test hook: issue no TMA loads, so the waits expire
     int group_m;             // row tiles per raster group
+    Planes xout;             // planes-out mode (xout.ptr set): the product itself, as
+    int64_t xout_col0;       // A-operand digit planes at column xout_col0 + n; C unused
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
@@ -599,6 +601,30 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 if (lane == 0) mbar_arrive(&acce[buf]);
             }
             if (!ok) break;
+            if (g.xout.ptr) {
+                // planes-out: the product's digits, 16-byte stores per plane
+                const int64_t row = ti.mt * BM + row_in_tile;
+                if (row < ti.M) {
+                    const size_t off0 =
+                        (size_t)row * (size_t)g.xout.kp + (size_t)(g.xout_col0 + ti.nt * BN + half * HC);
+#pragma unroll
+                    for (int v = 0; v < HC / 8; ++v) {
+                        uint32_t vh[4], vl[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const uint32_t rr = run[v * 4 + e];
+                            int h0, l0, h1, l1;
+                            digits(rr & 0xFFFFu, g.p, h0, l0);
+                            digits(rr >> 16, g.p, h1, l1);
+                            vh[e] = pack_bf2(h0, h1);
+                            vl[e] = pack_bf2(l0, l1);
+                        }
+                        *reinterpret_cast<uint4 *>(g.xout.plane(0) + off0 + v * 8) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+                        *reinterpret_cast<uint4 *>(g.xout.plane(1) + off0 + v * 8) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+                    }
+                }
+                continue;
+            }
             // C <- (C + sign * run) mod p for this thread's row segment.
             const int64_t row = ti.mt * BM + row_in_tile;
             const int64_t col0 = ti.c_col0 + ti.nt * BN + half * HC;   // column of C
@@ -715,7 +741,7 @@ int device_sm_count() {
     return n;
 }
 
-static bool tc_supported() {
+bool tc_supported() {
     static int ok = -1;
     if (ok < 0) {
         int dev = 0, major = 0, minor = 0;
@@ -769,7 +795,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
                                            tc::SMEM_BYTES));
         attr = true;
     }
-    tc::Args g;
+    tc::Args g{};
     g.M = M; g.N = N; g.K = K;
     g.probs = nullptr; g.nprob = 0;
     g.group_m = gemm_group_m();
@@ -779,6 +805,46 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
     g.withhold_loads = 0;
+    const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
+    const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+    tc::modgemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    GBLA_CUDA_TRY(launch_check());
+    if (ctr) ctr->tc_launches += 1;
+    return GBLA_OK;
+}
+
+// Planes-out product: Out[row, out_col0 + n] <- digits of (A * B)[row, n] mod p
+// for rows < M, n < round_up(N, 128); C is not involved.  Tensor-core variant
+// only; Out is an A-operand (2-plane) set whose columns out_col0 .. out_col0 +
+// round_up(N, 128) lie inside its padded width.
+int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t b_row0, const Planes &Out,
+                      int64_t out_col0, int64_t M, int64_t N, int64_t K, const ModP &mp, uint32_t *err,
+                      cudaStream_t s, GemmCounters *ctr)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return GBLA_OK;
+    if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
+    if (A.nplanes != 2 || B.nplanes != 4 || Out.nplanes != 2) return GBLA_E_INTERNAL;
+    if ((out_col0 % 8) || out_col0 + round_up(N, tc::BN) > Out.kp || M > Out.rows) return GBLA_E_INTERNAL;
+    if (ctr) ctr->launches += 1;   // the caller counts the algorithmic work
+    CUtensorMap ma, mb;
+    GBLA_TRY(make_map(&ma, A));
+    GBLA_TRY(make_map(&mb, B));
+    static bool attr = false;
+    if (!attr) {
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           tc::SMEM_BYTES));
+        attr = true;
+    }
+    tc::Args g{};
+    g.M = M; g.N = N; g.K = K;
+    g.group_m = gemm_group_m();
+    g.a_row0 = (int32_t)a_row0; g.a_k0 = 0; g.a_rows = (int32_t)A.rows;
+    g.b_row0 = (int32_t)b_row0; g.b_k0 = 0; g.b_rows = (int32_t)B.rows;
+    g.sign = 1;
+    g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+    g.err = err;
+    g.xout = Out;
+    g.xout_col0 = out_col0;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
     tc::modgemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);

@@ -174,8 +174,15 @@ static int trsm_upper_rec(const TrsmUpper &T, int64_t lo, int64_t hi)
     if (hi - lo <= LEAF) {
         // rows leading at or after hi have a zero block here (C and X alike)
         const int64_t rows = rows_before(T, hi);
+        if (rows == 0) return GBLA_OK;
+        if (T.Zt && T.Ct) {
+            // X_J = C_J * A_JJ^-1: digit planes of C_J, then one product whose
+            // epilogue writes the digit planes of X_J
+            const int w = (int)(hi - lo);
+            GBLA_TRY(to_planes(*T.Ct, rows, w, T.C16 + lo, T.ldc, 0, false, nullptr, nullptr, *T.mp, T.s));
+            return modgemm_to_planes(*T.Ct, 0, *T.Zt, lo, *T.Xp, lo, rows, w, w, *T.mp, T.err, T.s, T.ctr);
+        }
         const int64_t pairs = (rows + 1) / 2;
-        if (pairs == 0) return GBLA_OK;
         trsm_upper_leaf_kernel<<<(unsigned)((pairs + LEAF_WARPS - 1) / LEAF_WARPS), 32 * LEAF_WARPS,
                                  LEAF_SMEM_UPPER, T.s>>>(rows, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val,
                                                          T.ml->inblk, T.C16, T.ldc, *T.Xp, *T.mp);
@@ -758,6 +765,25 @@ __global__ void gather_rows_kernel(const uint16_t *__restrict__ D, int64_t ldd, 
 // The off-diagonal updates of the back-substitution only touch columns at or
 // right of the next block's pivots, so these blocks are final from the start
 // and all inverses are formed in one launch.
+// Z = T^-1 for the unit upper triangular w x w block T (shared memory), by
+// rows from the bottom: Z[i][j] = d_ij - sum_{i<k<=j} T[i][k] Z[k][j].  Thread
+// j owns column j; rows and columns w.. of Z are left untouched.
+__device__ __forceinline__ void unit_upper_inverse(const uint16_t (*T)[129], uint16_t (*Z)[129], int w,
+                                                   const ModP &mp)
+{
+    const int j = threadIdx.x;
+    const uint64_t P = mp.p;
+    for (int i = w - 1; i >= 0; --i) {
+        if (j < w) {
+            uint64_t acc = (i == j) ? 1 : 0;
+            uint64_t sub = 0;
+            for (int k = i + 1; k <= j; ++k) sub += (uint64_t)T[i][k] * Z[k][j];
+            Z[i][j] = (uint16_t)((j < i) ? 0u : mod40(acc + P * P - mod40(sub, mp), mp));
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__restrict__ R, int64_t ldr, int64_t rank,
                                                            const int32_t *__restrict__ pcol,
                                                            uint16_t *__restrict__ Nm_all, ModP mp)
@@ -772,17 +798,7 @@ __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__res
     for (int i = 0; i < w; ++i)
         T[i][j] = (j < w) ? R[(lo + i) * ldr + pcol[lo + j]] : 0;
     __syncthreads();
-    const uint64_t P = mp.p;
-    // column j of Z = T^-1, rows from the bottom: Z[i][j] = d_ij - sum_{i<k<=j} T[i][k] Z[k][j]
-    for (int i = w - 1; i >= 0; --i) {
-        if (j < w) {
-            uint64_t acc = (i == j) ? 1 : 0;
-            uint64_t sub = 0;
-            for (int k = i + 1; k <= j; ++k) sub += (uint64_t)T[i][k] * Z[k][j];
-            Z[i][j] = (uint16_t)((j < i) ? 0u : mod40(acc + P * P - mod40(sub, mp), mp));
-        }
-        __syncthreads();
-    }
+    unit_upper_inverse(T, Z, w, mp);
     for (int i = 0; i < w; ++i)
         if (j < PANEL) {
             uint32_t z = (j < w) ? Z[i][j] : 0u;
@@ -791,7 +807,52 @@ __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__res
         }
 }
 
+// B-operand planes of (A_JJ^-1)^T for every diagonal block J of A (blockIdx.x
+// = block): row 128 q + j, columns k = 0..127 <- Z[k][j], zero outside w.
+__global__ void __launch_bounds__(128) upper_inverse_planes_kernel(const uint16_t *__restrict__ A, int64_t lda,
+                                                                   int64_t npiv, Planes Zt, ModP mp)
+{
+    const int64_t lo = (int64_t)blockIdx.x * 128;
+    const int w = (int)((npiv - lo) < 128 ? (npiv - lo) : 128);
+    extern __shared__ uint16_t inv_smem[];
+    uint16_t(*T)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem);
+    uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem + 128 * 129);
+    const int j = threadIdx.x;
+    for (int i = 0; i < w; ++i)
+        T[i][j] = (j < w) ? A[(lo + i) * lda + lo + j] : 0;
+    __syncthreads();
+    unit_upper_inverse(T, Z, w, mp);
+    const size_t row = (size_t)(lo + j) * (size_t)Zt.kp;
+#pragma unroll 1
+    for (int c = 0; c < 16; ++c) {
+        uint32_t a[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = c * 8 + e;
+            a[e] = (j < w && k < w) ? Z[k][j] : 0u;
+        }
+        store_digits8(Zt, row + (size_t)c * 8, a, mp);
+    }
+}
+
 constexpr int LEAF_INV_SMEM = 2 * 128 * 129 * (int)sizeof(uint16_t);
+
+int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, const Planes &Zt, const ModP &mp,
+                        cudaStream_t s)
+{
+    if (npiv <= 0) return GBLA_OK;
+    const int64_t nb = (npiv + 127) / 128;
+    if (Zt.nplanes != 4 || Zt.kp != 128 || Zt.rows < nb * 128) return GBLA_E_INTERNAL;
+    static bool attr = false;
+    if (!attr) {
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(upper_inverse_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           LEAF_INV_SMEM));
+        attr = true;
+    }
+    upper_inverse_planes_kernel<<<(unsigned)nb, 128, LEAF_INV_SMEM, s>>>(A16, lda, npiv, Zt, mp);
+    GBLA_CUDA_TRY(launch_check());
+    return GBLA_OK;
+}
 
 
 
