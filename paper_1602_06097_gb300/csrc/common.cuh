@@ -93,15 +93,23 @@ __device__ __forceinline__ __nv_bfloat16 i2bf(int v) { return __float2bfloat16_r
 
 // Plane-set geometry.  An "A-operand" set holds 2 planes (hi, lo) of an
 // M x K matrix, a "B-operand" set holds 4 planes (hi, lo of b, hi, lo of
-// b' = 256*b mod p) of an N x K matrix (i.e. B transposed).  Each plane is
-// rows x kp bf16 row-major with rows and kp multiples of 128; padding is 0.
+// b' = 256*b mod p) of an N x K matrix (i.e. B transposed).  rows and kp (the
+// padded K) are multiples of 128; padding is 0.  The planes are interleaved
+// by 32-wide K chunks: a row is kp / 32 chunks, each holding 32 bf16 of every
+// plane in turn, so that one 128-byte row segment carries the (hi, lo) pair of
+// a chunk and the product loads operand tiles as 128-byte rows.
 struct Planes {
     __nv_bfloat16 *ptr;
-    int64_t rows;   // padded rows per plane
-    int64_t kp;     // padded K (row length)
+    int64_t rows;   // padded rows
+    int64_t kp;     // padded K
     int nplanes;    // 2 or 4
     __host__ __device__ size_t plane_elems() const { return (size_t)rows * (size_t)kp; }
-    __host__ __device__ __nv_bfloat16 *plane(int h) const { return ptr + (size_t)h * plane_elems(); }
+    __host__ __device__ int64_t row_elems() const { return kp * nplanes; }
+    // element (r, k) of plane h
+    __host__ __device__ __nv_bfloat16 *at(int h, int64_t r, int64_t k) const {
+        return ptr + (size_t)r * (size_t)row_elems() + (size_t)(k >> 5) * (size_t)(32 * nplanes) + (size_t)(h * 32) +
+               (size_t)(k & 31);
+    }
 };
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -138,9 +146,10 @@ __device__ __forceinline__ uint32_t pack_bf2(int lo_elem, int hi_elem) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-// Digit planes of 8 consecutive residues a[0..7] at element offset off (a
-// multiple of 8) of every plane: 16-byte stores.
-__device__ __forceinline__ void store_digits8(const Planes &dst, size_t off, const uint32_t (&a)[8], const ModP &mp) {
+// Digit planes of 8 consecutive residues a[0..7] at row r, columns k0 .. k0+7
+// (k0 a multiple of 8) of every plane: 16-byte stores.
+__device__ __forceinline__ void store_digits8(const Planes &dst, int64_t r, int64_t k0, const uint32_t (&a)[8],
+                                              const ModP &mp) {
     uint32_t vh[4], vl[4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
@@ -150,8 +159,8 @@ __device__ __forceinline__ void store_digits8(const Planes &dst, size_t off, con
         vh[e / 2] = pack_bf2(h0, h1);
         vl[e / 2] = pack_bf2(l0, l1);
     }
-    *reinterpret_cast<uint4 *>(dst.plane(0) + off) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
-    *reinterpret_cast<uint4 *>(dst.plane(1) + off) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+    *reinterpret_cast<uint4 *>(dst.at(0, r, k0)) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+    *reinterpret_cast<uint4 *>(dst.at(1, r, k0)) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
     if (dst.nplanes == 4) {
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
@@ -161,8 +170,8 @@ __device__ __forceinline__ void store_digits8(const Planes &dst, size_t off, con
             vh[e / 2] = pack_bf2(h0, h1);
             vl[e / 2] = pack_bf2(l0, l1);
         }
-        *reinterpret_cast<uint4 *>(dst.plane(2) + off) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
-        *reinterpret_cast<uint4 *>(dst.plane(3) + off) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+        *reinterpret_cast<uint4 *>(dst.at(2, r, k0)) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+        *reinterpret_cast<uint4 *>(dst.at(3, r, k0)) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
     }
 }
 
@@ -189,7 +198,7 @@ __device__ __forceinline__ void tp_tile(const Planes &dst, int64_t row0, int64_t
         uint32_t a[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) a[e] = sm.t[c * 8 + e][rr];
-        store_digits8(dst, (size_t)(row0 + r0 + rr) * (size_t)dst.kp + (size_t)(k0 + c * 8), a, mp);
+        store_digits8(dst, row0 + r0 + rr, k0 + c * 8, a, mp);
     }
 }
 

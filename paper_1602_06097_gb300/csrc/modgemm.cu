@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) to_planes_kernel(Planes dst, int64_t R, i
             if (sc >= 0) a[e] = src[sr * lds + col_off + sc];
         }
     }
-    store_digits8(dst, (size_t)r * (size_t)dst.kp + (size_t)k0, a, mp);
+    store_digits8(dst, r, k0, a, mp);
 }
 
 // Transposed conversion: dst row r, column k <- src[g(k)][col_off + r], one
@@ -133,12 +133,12 @@ __global__ void __launch_bounds__(256) modgemm_simt_kernel(Planes A, int64_t a_r
             int va = 0, vb = 0;
             if (kk + k < K) {
                 if (m0 + r < M) {
-                    size_t off = (size_t)(a_row0 + m0 + r) * A.kp + (size_t)(a_k0 + kk + k);
-                    va = 256 * bf2i(A.plane(0)[off]) + bf2i(A.plane(1)[off]);
+                    const int64_t ar = a_row0 + m0 + r, ak = a_k0 + kk + k;
+                    va = 256 * bf2i(*A.at(0, ar, ak)) + bf2i(*A.at(1, ar, ak));
                 }
                 if (n0 + r < N) {
-                    size_t off = (size_t)(b_row0 + n0 + r) * B.kp + (size_t)(b_k0 + kk + k);
-                    vb = 256 * bf2i(B.plane(0)[off]) + bf2i(B.plane(1)[off]);
+                    const int64_t br = b_row0 + n0 + r, bk = b_k0 + kk + k;
+                    vb = 256 * bf2i(*B.at(0, br, bk)) + bf2i(*B.at(1, br, bk));
                 }
             }
             sa[r][k] = va;
@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(256) modgemm_simt_kernel(Planes A, int64_t a_r
 // tcgen05 / TMA GEMM
 // ===================================================================
 namespace tc {
-constexpr int BM = 128, BN = 128, BK = 32;         // K step of 32 bf16 = 64-byte rows
+constexpr int BM = 128, BN = 128, BK = 32;         // K step: one 32-wide chunk of the interleaved planes
 constexpr int STAGES = 4;
 constexpr int KSTEPS_PER_BLOCK = 512 / BK;          // k-block of 512: exact fp32 sums
-constexpr int TILE_BYTES = BM * BK * 2;             // 8 KiB (A and B tiles are 128 rows)
-constexpr int STAGE_BYTES = 6 * TILE_BYTES;         // Ah Al | Bh Bl B'h B'l
+constexpr int BOX_BYTES = 128 * 128;                // one TMA box: 128 rows x 128 bytes (two planes)
+constexpr int STAGE_BYTES = 3 * BOX_BYTES;          // [Ah Al] | [Bh Bl] | [B'h B'l]
 constexpr int BAR_BYTES = 256;
 constexpr int64_t GROUP_M_DEFAULT = 4;              // row tiles per raster group (see tile_coords)
 constexpr int EPI_WARPS = 8;                        // two drain warps per TMEM lane quarter
@@ -201,8 +201,8 @@ struct Args {
     int64_t M, N, K;
     const GroupProb *probs;  // grouped mode: nprob problems (device), else null
     int nprob;
-    int32_t a_row0, a_k0, a_rows;   // a_rows = padded rows per A plane
-    int32_t b_row0, b_k0, b_rows;
+    int32_t a_row0, a_k0;    // first row and K column of the A and B operands
+    int32_t b_row0, b_k0;
     uint16_t *C;
     int64_t ldc;
     const int32_t *c_rows;   // optional: row r of the product goes to C row c_rows[r]
@@ -286,18 +286,21 @@ __device__ __forceinline__ void tcgen05_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand tile of 128 rows x 32 bf16
-// (64-byte rows) loaded by TMA with 64-byte swizzle.  8-row swizzle atoms
-// are 512 bytes apart (stride byte offset); the leading byte offset is unused
-// for swizzled K-major tiles.  Layout type 4 = 64-byte swizzle; bit 46 is the
-// fixed descriptor version of sm_100-family tcgen05.
+// Shared-memory matrix descriptor: K-major operand of 128 rows with 128-byte
+// rows, loaded by TMA with 128-byte swizzle.  Each 128-byte row holds two
+// planes' 32-wide K chunks; an operand (one plane, 16 K values) is selected
+// by the start address offset within the row (0, 32, 64 or 96 bytes), which
+// the swizzle applies to like any other address bits.  8-row swizzle atoms
+// are 1024 bytes apart (stride byte offset); the leading byte offset is unused
+// for swizzled K-major tiles.  Layout type 2 = 128-byte swizzle; bit 46 is
+// the fixed descriptor version of sm_100-family tcgen05.
 __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;                 // leading byte offset (16 B, unused)
-    d |= (uint64_t)((8 * BK * 2) >> 4) << 32;   // stride byte offset: 8 rows
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows of 128 B
     d |= (uint64_t)1 << 46;                 // descriptor version
-    d |= (uint64_t)4 << 61;                 // 64-byte swizzle
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
     return d;
 }
 
@@ -465,13 +468,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
                     uint8_t *st = tiles + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], STAGE_BYTES);
-                    const int ax = g.a_k0 + ks * BK, bx = g.b_k0 + ks * BK;
-                    tma_load_2d(st + 0 * TILE_BYTES, &tmA, &full[stage], ax, ay);
-                    tma_load_2d(st + 1 * TILE_BYTES, &tmA, &full[stage], ax, ay + g.a_rows);
-                    tma_load_2d(st + 2 * TILE_BYTES, &tmB, &full[stage], bx, by);
-                    tma_load_2d(st + 3 * TILE_BYTES, &tmB, &full[stage], bx, by + g.b_rows);
-                    tma_load_2d(st + 4 * TILE_BYTES, &tmB, &full[stage], bx, by + 2 * g.b_rows);
-                    tma_load_2d(st + 5 * TILE_BYTES, &tmB, &full[stage], bx, by + 3 * g.b_rows);
+                    // chunk c of K sits at element 64 c of an A row (2 planes)
+                    // and 128 c of a B row (4 planes)
+                    const int ax = (g.a_k0 / BK + ks) * 2 * BK, bx = (g.b_k0 / BK + ks) * 4 * BK;
+                    tma_load_2d(st + 0 * BOX_BYTES, &tmA, &full[stage], ax, ay);
+                    tma_load_2d(st + 1 * BOX_BYTES, &tmB, &full[stage], bx, by);
+                    tma_load_2d(st + 2 * BOX_BYTES, &tmB, &full[stage], bx + 2 * BK, by);
                     issued[stage] = 1;
                     issued_parity[stage] = phase;
                     if (++stage == STAGES) stage = 0, phase ^= 1u;
@@ -516,12 +518,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
                             const uint32_t ko = kk * 32;  // 16 bf16 = 32 bytes along K
-                            const uint64_t ah = make_sdesc(sb + 0 * TILE_BYTES + ko);
-                            const uint64_t al = make_sdesc(sb + 1 * TILE_BYTES + ko);
-                            const uint64_t bh = make_sdesc(sb + 2 * TILE_BYTES + ko);
-                            const uint64_t bl = make_sdesc(sb + 3 * TILE_BYTES + ko);
-                            const uint64_t b2h = make_sdesc(sb + 4 * TILE_BYTES + ko);
-                            const uint64_t b2l = make_sdesc(sb + 5 * TILE_BYTES + ko);
+                            const uint64_t ah = make_sdesc(sb + 0 * BOX_BYTES + ko);
+                            const uint64_t al = make_sdesc(sb + 0 * BOX_BYTES + 64 + ko);
+                            const uint64_t bh = make_sdesc(sb + 1 * BOX_BYTES + ko);
+                            const uint64_t bl = make_sdesc(sb + 1 * BOX_BYTES + 64 + ko);
+                            const uint64_t b2h = make_sdesc(sb + 2 * BOX_BYTES + ko);
+                            const uint64_t b2l = make_sdesc(sb + 2 * BOX_BYTES + 64 + ko);
                             const uint32_t acc0 = (ks > ks_beg || kk > 0) ? 1u : 0u;
                             mma_bf16(dP, ah, b2h, acc0);
                             mma_bf16(dP, al, bh, 1u);
@@ -605,8 +607,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 // planes-out: the product's digits, 16-byte stores per plane
                 const int64_t row = ti.mt * BM + row_in_tile;
                 if (row < ti.M) {
-                    const size_t off0 =
-                        (size_t)row * (size_t)g.xout.kp + (size_t)(g.xout_col0 + ti.nt * BN + half * HC);
+                    const int64_t k0 = g.xout_col0 + ti.nt * BN + half * HC;
 #pragma unroll
                     for (int v = 0; v < HC / 8; ++v) {
                         uint32_t vh[4], vl[4];
@@ -619,8 +620,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             vh[e] = pack_bf2(h0, h1);
                             vl[e] = pack_bf2(l0, l1);
                         }
-                        *reinterpret_cast<uint4 *>(g.xout.plane(0) + off0 + v * 8) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
-                        *reinterpret_cast<uint4 *>(g.xout.plane(1) + off0 + v * 8) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+                        *reinterpret_cast<uint4 *>(g.xout.at(0, row, k0 + v * 8)) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+                        *reinterpret_cast<uint4 *>(g.xout.at(1, row, k0 + v * 8)) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
                     }
                 }
                 continue;
@@ -709,12 +710,14 @@ static int get_encode() {
 
 static int make_map(CUtensorMap *map, const Planes &pl) {
     GBLA_TRY(get_encode());
-    cuuint64_t dims[2] = {(cuuint64_t)pl.kp, (cuuint64_t)pl.rows * (cuuint64_t)pl.nplanes};
-    cuuint64_t strides[1] = {(cuuint64_t)pl.kp * 2};
-    cuuint32_t box[2] = {tc::BK, tc::BM};
+    // rows of kp * nplanes interleaved elements; a box is 128 rows x 64
+    // elements (128 bytes: one K chunk of two planes)
+    cuuint64_t dims[2] = {(cuuint64_t)pl.row_elems(), (cuuint64_t)pl.rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pl.row_elems() * 2};
+    cuuint32_t box[2] = {2 * tc::BK, tc::BM};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)pl.ptr, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? GBLA_OK : GBLA_E_CUDA;
 }
@@ -799,8 +802,8 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     g.M = M; g.N = N; g.K = K;
     g.probs = nullptr; g.nprob = 0;
     g.group_m = gemm_group_m();
-    g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0; g.a_rows = (int32_t)A.rows;
-    g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0; g.b_rows = (int32_t)B.rows;
+    g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0;
+    g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0;
     g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.row_lead = row_lead; g.sign = sign;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
@@ -838,8 +841,8 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     tc::Args g{};
     g.M = M; g.N = N; g.K = K;
     g.group_m = gemm_group_m();
-    g.a_row0 = (int32_t)a_row0; g.a_k0 = 0; g.a_rows = (int32_t)A.rows;
-    g.b_row0 = (int32_t)b_row0; g.b_k0 = 0; g.b_rows = (int32_t)B.rows;
+    g.a_row0 = (int32_t)a_row0; g.a_k0 = 0;
+    g.b_row0 = (int32_t)b_row0; g.b_k0 = 0;
     g.sign = 1;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
@@ -897,7 +900,6 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
     g.M = 0; g.N = 0; g.K = K;
     g.probs = probs; g.nprob = nprob;
     g.group_m = gemm_group_m();
-    g.a_rows = (int32_t)A.rows; g.b_rows = (int32_t)B.rows;
     g.C = C; g.ldc = ldc; g.sign = sign;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
@@ -934,8 +936,7 @@ int modgemm_withheld_loads(uint32_t *err, cudaStream_t s)
         tc::Args g{};
         g.group_m = 1;
         g.M = 128; g.N = 128; g.K = 64;
-        g.a_rows = (int32_t)A.rows; g.b_rows = (int32_t)B.rows;
-        g.C = C; g.ldc = 128; g.sign = 1;
+            g.C = C; g.ldc = 128; g.sign = 1;
         const ModP mp = make_modp(65521);
         g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
         g.err = err;

@@ -147,16 +147,14 @@ __global__ void __launch_bounds__(256) trsm_upper_leaf_kernel(int64_t mrows, int
         C16[r1 * ldc + j0 + c] = (uint16_t)x1;
         int hi, lo;
         digits(x1, p, hi, lo);
-        size_t off = (size_t)r1 * Xp.kp + (size_t)(j0 + c);
-        Xp.plane(0)[off] = i2bf(hi);
-        Xp.plane(1)[off] = i2bf(lo);
+        *Xp.at(0, r1, j0 + c) = i2bf(hi);
+        *Xp.at(1, r1, j0 + c) = i2bf(lo);
         if (has2) {
             const uint32_t x2 = (uint32_t)acc[1][c];
             C16[r2 * ldc + j0 + c] = (uint16_t)x2;
             digits(x2, p, hi, lo);
-            off = (size_t)r2 * Xp.kp + (size_t)(j0 + c);
-            Xp.plane(0)[off] = i2bf(hi);
-            Xp.plane(1)[off] = i2bf(lo);
+            *Xp.at(0, r2, j0 + c) = i2bf(hi);
+            *Xp.at(1, r2, j0 + c) = i2bf(lo);
         }
     }
 }
@@ -273,16 +271,14 @@ __global__ void __launch_bounds__(256) trsm_lower_leaf_kernel(int64_t mrows, int
         C16[r1 * ldc + j0 + c] = (uint16_t)x1;
         int hi, lo;
         digits(x1, p, hi, lo);
-        size_t off = (size_t)r1 * Xp.kp + (size_t)(j0 + c);
-        Xp.plane(0)[off] = i2bf(hi);
-        Xp.plane(1)[off] = i2bf(lo);
+        *Xp.at(0, r1, j0 + c) = i2bf(hi);
+        *Xp.at(1, r1, j0 + c) = i2bf(lo);
         if (has2) {
             const uint32_t x2 = xs[1][c];
             C16[r2 * ldc + j0 + c] = (uint16_t)x2;
             digits(x2, p, hi, lo);
-            off = (size_t)r2 * Xp.kp + (size_t)(j0 + c);
-            Xp.plane(0)[off] = i2bf(hi);
-            Xp.plane(1)[off] = i2bf(lo);
+            *Xp.at(0, r2, j0 + c) = i2bf(hi);
+            *Xp.at(1, r2, j0 + c) = i2bf(lo);
         }
     }
 }
@@ -649,9 +645,8 @@ __global__ void gather_gm_planes_kernel(Planes dst, const uint16_t *__restrict__
     const uint32_t a = Gm_all[(int64_t)plan[q].slot * PANEL * PANEL + i * PANEL + j];
     int hi, lo;
     digits(a, p, hi, lo);
-    const size_t off = (size_t)(q * PANEL + i) * (size_t)dst.kp + (size_t)j;
-    dst.plane(0)[off] = i2bf(hi);
-    dst.plane(1)[off] = i2bf(lo);
+    *dst.at(0, (int64_t)q * PANEL + i, j) = i2bf(hi);
+    *dst.at(1, (int64_t)q * PANEL + i, j) = i2bf(lo);
 }
 
 // B-operand planes of D[S]^T for every panel of a chunk (blockIdx.z):
@@ -690,9 +685,8 @@ __global__ void gather_h_planes_kernel(Planes dst, const uint16_t *__restrict__ 
         if (pcj >= 0 && !is_piv_row[row]) a = D[row * ldd + (int64_t)slot * PANEL + pcj];
         int hi, lo;
         digits(a, p, hi, lo);
-        const size_t off = (size_t)(r - row_base) * (size_t)dst.kp + (size_t)j;
-        dst.plane(0)[off] = i2bf(hi);
-        dst.plane(1)[off] = i2bf(lo);
+        *dst.at(0, r - row_base, j) = i2bf(hi);
+        *dst.at(1, r - row_base, j) = i2bf(lo);
     }
 }
 
@@ -822,7 +816,6 @@ __global__ void __launch_bounds__(128) upper_inverse_planes_kernel(const uint16_
         T[i][j] = (j < w) ? A[(lo + i) * lda + lo + j] : 0;
     __syncthreads();
     unit_upper_inverse(T, Z, w, mp);
-    const size_t row = (size_t)(lo + j) * (size_t)Zt.kp;
 #pragma unroll 1
     for (int c = 0; c < 16; ++c) {
         uint32_t a[8];
@@ -831,7 +824,7 @@ __global__ void __launch_bounds__(128) upper_inverse_planes_kernel(const uint16_
             const int k = c * 8 + e;
             a[e] = (j < w && k < w) ? Z[k][j] : 0u;
         }
-        store_digits8(Zt, row + (size_t)c * 8, a, mp);
+        store_digits8(Zt, lo + j, c * 8, a, mp);
     }
 }
 
