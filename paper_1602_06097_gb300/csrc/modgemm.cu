@@ -189,10 +189,16 @@ constexpr int KSTEPS_PER_BLOCK = 512 / BK;          // k-block of 512: exact fp3
 constexpr int BOX_BYTES = 128 * 128;                // one TMA box: 128 rows x 128 bytes (two planes)
 constexpr int STAGE_BYTES = 3 * BOX_BYTES;          // [Ah Al] | [Bh Bl] | [B'h B'l]
 constexpr int BAR_BYTES = 256;
+// CTA pair (cta_group::2): one 256 x 128 tile per pair, each CTA holding 128
+// rows of A and 64 rows of B per stage, so a stage is 32 KiB and six fit.
+constexpr int PAIR_STAGES = 6;
+constexpr int PAIR_B_BOX_BYTES = 64 * 128;                          // 64 rows x 128 bytes
+constexpr int PAIR_STAGE_BYTES = BOX_BYTES + 2 * PAIR_B_BOX_BYTES;  // [Ah Al] | [Bh Bl] | [B'h B'l]
 constexpr int64_t GROUP_M_DEFAULT = 4;              // row tiles per raster group (see tile_coords)
 constexpr int EPI_WARPS = 8;                        // two drain warps per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr int PAIR_SMEM_BYTES = PAIR_STAGES * PAIR_STAGE_BYTES + BAR_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;                 // 2 buffers x (P 128 + Q 128)
 constexpr float MAGIC = 12582912.0f;                // 1.5 * 2^23
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000ll;  // ~1 s
@@ -274,6 +280,38 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// CTA-pair forms.  The pair's loads all complete on the leader's (rank 0)
+// barrier, given as a shared::cluster address.
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cluster, int x,
+                                                 int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the variable at saddr in the CTA of the given rank
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
 __device__ __forceinline__ void tcgen05_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -281,9 +319,29 @@ __device__ __forceinline__ void tcgen05_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+template <bool PAIR>
 __device__ __forceinline__ void tcgen05_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    if (PAIR)
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+}
+
+// Pair: arrive on the barrier at the same offset in both CTAs of the pair.
+template <bool PAIR>
+__device__ __forceinline__ void tcgen05_commit_both(uint64_t *bar) {
+    if (PAIR)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                smem_u32(bar)),
+            "h"((uint16_t)3)
+            : "memory");
+    else
+        tcgen05_commit<false>(bar);
 }
 
 // Shared-memory matrix descriptor: K-major operand of 128 rows with 128-byte
@@ -309,14 +367,37 @@ __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-        : "memory");
+// CTA pair: M = 256 (rows 0..127 in the leader's TMEM, 128..255 in the peer's).
+constexpr uint32_t IDESC_PAIR = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)((2 * BM) >> 4) << 24);
+
+// The MMA issuer must keep up with the tensor core (one 128 x 128 x 16 MMA
+// every 64 cycles) from a single thread, so its instruction stream is kept
+// short: the descriptors' high words are one constant, the low words (start
+// address >> 4 in bits 0..13, the leading byte offset above) are formed per
+// operand by a 32-bit add, and the pair is joined inside the asm.
+template <bool PAIR>
+__device__ __forceinline__ void mma_bf16_lo(uint32_t d_tmem, uint32_t alo, uint32_t blo, uint32_t dhi, uint32_t accumulate) {
+    if (PAIR)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %5, 0;\n\t"
+            "mov.b64 da, {%1, %3};\n\t"
+            "mov.b64 db, {%2, %3};\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
+            "r"(alo), "r"(blo), "r"(dhi), "r"(IDESC_PAIR), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %5, 0;\n\t"
+            "mov.b64 da, {%1, %3};\n\t"
+            "mov.b64 db, {%2, %3};\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
+            "r"(alo), "r"(blo), "r"(dhi), "r"(IDESC), "r"(accumulate)
+            : "memory");
 }
+
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
@@ -358,9 +439,9 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t nu
 // leads ascending the first row of the tile's raster group has the smallest
 // one.  All tiles of a group start there, so the CTAs working on the group at
 // the same time walk K in step and share operand tiles in L2.
-__device__ __forceinline__ int tile_kstep0(const Args &g, int64_t mt) {
+__device__ __forceinline__ int tile_kstep0(const Args &g, int64_t mt, int64_t tbm) {
     if (!g.row_lead) return 0;
-    const int64_t k = (int64_t)g.row_lead[(mt / g.group_m) * g.group_m * BM] - g.a_k0;
+    const int64_t k = (int64_t)g.row_lead[(mt / g.group_m) * g.group_m * tbm] - g.a_k0;
     return k > 0 ? (int)(k / BK) : 0;
 }
 
@@ -370,7 +451,10 @@ struct TileInfo {
     const int32_t *c_rows;
 };
 
-__device__ __forceinline__ TileInfo tile_info(const Args &g, int64_t t, int64_t num_m, int64_t num_n) {
+// Tile t of the launch.  Pair tiles are 256 rows high: the CTA of rank 1
+// loads A rows 128.. and B rows 64.. of it and drains rows 128.. of C.
+template <bool PAIR>
+__device__ __forceinline__ TileInfo tile_info(const Args &g, int64_t t, int64_t num_m, int64_t num_n, uint32_t rank) {
     TileInfo ti;
     if (g.probs) {
         int lo = 0, hi = g.nprob - 1;   // last problem with tile_off <= t
@@ -392,41 +476,57 @@ __device__ __forceinline__ TileInfo tile_info(const Args &g, int64_t t, int64_t 
         ti.b_row = P.b_row0 + (int)(ti.nt * BN);
         ti.ks0 = 0;
     } else {
+        constexpr int64_t TBM = PAIR ? 2 * BM : BM;
         tile_coords(t, num_m, num_n, g.group_m, ti.mt, ti.nt);
         ti.M = g.M;
         ti.N = g.N;
         ti.c_col0 = 0;
         ti.c_rows = g.c_rows;
-        ti.a_row = g.a_row0 + (int)(ti.mt * BM);
-        ti.b_row = g.b_row0 + (int)(ti.nt * BN);
-        ti.ks0 = tile_kstep0(g, ti.mt);
+        ti.a_row = g.a_row0 + (int)(ti.mt * TBM) + (int)rank * BM;
+        ti.b_row = g.b_row0 + (int)(ti.nt * BN) + (int)rank * (BN / 2);
+        ti.ks0 = tile_kstep0(g, ti.mt, TBM);
     }
     return ti;
 }
 
+// PAIR = false: one CTA per 128 x 128 tile (cta_group::1).  PAIR = true: a
+// cluster of two CTAs per 256 x 128 tile (cta_group::2, launched with cluster
+// dimension 2); the leader (rank 0) issues the MMAs, which read A and B from
+// both CTAs' shared memory and write each CTA's 128 rows of the accumulators
+// into its own TMEM.  All loads of a stage complete on the leader's full
+// barrier; the MMA commits arrive on the empty and accumulator barriers of
+// both CTAs; both CTAs' drain warps release an accumulator buffer on the
+// leader's barrier.
+template <bool PAIR>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     modgemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args g)
 {
+    constexpr int NST = PAIR ? PAIR_STAGES : STAGES;
+    constexpr int SBYTES = PAIR ? PAIR_STAGE_BYTES : STAGE_BYTES;
+    constexpr int BBOX = PAIR ? PAIR_B_BOX_BYTES : BOX_BYTES;
+    constexpr int64_t TBM = PAIR ? 2 * BM : BM;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + STAGES * STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + NST * SBYTES);
     uint64_t *full = bars;
-    uint64_t *empty = bars + STAGES;
-    uint64_t *accf = bars + 2 * STAGES;
+    uint64_t *empty = bars + NST;
+    uint64_t *accf = bars + 2 * NST;
     uint64_t *acce = accf + 2;
     uint64_t *done = acce + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], EPI_WARPS);
+            mbar_init(&acce[b], PAIR ? 2 * EPI_WARPS : EPI_WARPS);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
@@ -434,10 +534,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     if (warp == 0 && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
@@ -445,64 +554,87 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
     tcgen05_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();   // the peer's barriers exist before any remote signal
     tcgen05_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int64_t num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
+    const int64_t num_m = (g.M + TBM - 1) / TBM, num_n = (g.N + BN - 1) / BN;
     const int64_t num_tiles = g.probs ? g.probs[g.nprob].tile_off : num_m * num_n;
     const int ksteps = (int)((g.K + BK - 1) / BK);
+    const int64_t tile0 = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+    const int64_t tstep = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer
             int stage = 0;
             uint32_t phase = 0;
-            int issued[STAGES];
-            uint32_t issued_parity[STAGES];
-            for (int s = 0; s < STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
+            int issued[NST];
+            uint32_t issued_parity[NST];
+            for (int s = 0; s < NST; ++s) issued[s] = 0, issued_parity[s] = 0;
             bool ok = !g.withhold_loads;
-            for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                const TileInfo ti = tile_info(g, t, num_m, num_n);
+            for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
+                const TileInfo ti = tile_info<PAIR>(g, t, num_m, num_n, rank);
                 const int ay = ti.a_row, by = ti.b_row;
                 for (int ks = ti.ks0; ks < ksteps; ++ks) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
-                    uint8_t *st = tiles + stage * STAGE_BYTES;
-                    mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    uint8_t *st = tiles + stage * SBYTES;
                     // chunk c of K sits at element 64 c of an A row (2 planes)
                     // and 128 c of a B row (4 planes)
                     const int ax = (g.a_k0 / BK + ks) * 2 * BK, bx = (g.b_k0 / BK + ks) * 4 * BK;
-                    tma_load_2d(st + 0 * BOX_BYTES, &tmA, &full[stage], ax, ay);
-                    tma_load_2d(st + 1 * BOX_BYTES, &tmB, &full[stage], bx, by);
-                    tma_load_2d(st + 2 * BOX_BYTES, &tmB, &full[stage], bx + 2 * BK, by);
+                    if (PAIR) {
+                        const uint32_t fb = mapa_rank(smem_u32(&full[stage]), 0);
+                        if (leader) mbar_expect_tx(&full[stage], 2 * SBYTES);
+                        tma_load_2d_pair(st, &tmA, fb, ax, ay);
+                        tma_load_2d_pair(st + BOX_BYTES, &tmB, fb, bx, by);
+                        tma_load_2d_pair(st + BOX_BYTES + BBOX, &tmB, fb, bx + 2 * BK, by);
+                    } else {
+                        mbar_expect_tx(&full[stage], SBYTES);
+                        tma_load_2d(st, &tmA, &full[stage], ax, ay);
+                        tma_load_2d(st + BOX_BYTES, &tmB, &full[stage], bx, by);
+                        tma_load_2d(st + BOX_BYTES + BBOX, &tmB, &full[stage], bx + 2 * BK, by);
+                    }
                     issued[stage] = 1;
                     issued_parity[stage] = phase;
-                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                    if (++stage == NST) stage = 0, phase ^= 1u;
                 }
             }
             // Never leave with copies in flight: wait (bounded) for the last
-            // load issued into every stage.
-            for (int s = 0; s < STAGES; ++s) {
-                if (!issued[s]) continue;
-                const uint32_t addr = smem_u32(&full[s]);
-                long long start = clock64();
-                while (!mbar_try_wait(addr, issued_parity[s])) {
-                    if (clock64() - start > WAIT_LIMIT_CYCLES) {
-                        dev_fail(g.err, DEV_ERR_TIMEOUT);
-                        break;
+            // load issued into every stage.  A pair's copies complete on the
+            // leader's barriers, which count the peer's bytes too; the peer,
+            // which cannot wait on them, pauses after an abort instead.
+            if (PAIR && !leader) {
+                if (!ok) {
+                    const long long start = clock64();
+                    while (clock64() - start < 4000000ll) __nanosleep(1000);
+                }
+            } else {
+                for (int s = 0; s < NST; ++s) {
+                    if (!issued[s]) continue;
+                    const uint32_t addr = smem_u32(&full[s]);
+                    long long start = clock64();
+                    while (!mbar_try_wait(addr, issued_parity[s])) {
+                        if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                            dev_fail(g.err, DEV_ERR_TIMEOUT);
+                            break;
+                        }
                     }
                 }
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             // ---------------- MMA issuer
             int stage = 0;
             uint32_t phase = 0;
             uint32_t kbc = 0;
             bool ok = true;
-            const uint32_t tiles_base = smem_u32(tiles);
-            for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                const int ks0 = tile_info(g, t, num_m, num_n).ks0;
+            const uint64_t d0 = make_sdesc(smem_u32(tiles));
+            const uint32_t dhi = (uint32_t)(d0 >> 32), lo0 = (uint32_t)d0;
+            uint32_t lo_stage = lo0;   // descriptor low word of the current stage
+            constexpr uint32_t B1 = BOX_BYTES >> 4, B2 = (BOX_BYTES + BBOX) >> 4, HALF = 64 >> 4;
+            for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
+                const int ks0 = tile_info<PAIR>(g, t, num_m, num_n, rank).ks0;
                 const int kbt = (ksteps - ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
                 for (int kb = 0; kb < kbt && ok; ++kb, ++kbc) {
                     const uint32_t buf = kbc & 1u, use = kbc >> 1;
@@ -511,34 +643,33 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     const uint32_t dP = tmem + buf * 256u, dQ = dP + 128u;
                     const int ks_beg = ks0 + kb * KSTEPS_PER_BLOCK;
                     const int ks_end = min(ksteps, ks_beg + KSTEPS_PER_BLOCK);
+                    uint32_t acc0 = 0;
                     for (int ks = ks_beg; ks < ks_end; ++ks) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, g.err)) { ok = false; break; }
-                        tcgen05_fence_after();
-                        const uint32_t sb = tiles_base + stage * STAGE_BYTES;
+                        // the stage's operands were written by TMA and the
+                        // barrier completes with them: no thread-sync fence
+                        if (!mbar_try_wait(smem_u32(&full[stage]), phase) &&
+                            !mbar_wait(&full[stage], phase, abort_flag, g.err)) { ok = false; break; }
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint32_t ko = kk * 32;  // 16 bf16 = 32 bytes along K
-                            const uint64_t ah = make_sdesc(sb + 0 * BOX_BYTES + ko);
-                            const uint64_t al = make_sdesc(sb + 0 * BOX_BYTES + 64 + ko);
-                            const uint64_t bh = make_sdesc(sb + 1 * BOX_BYTES + ko);
-                            const uint64_t bl = make_sdesc(sb + 1 * BOX_BYTES + 64 + ko);
-                            const uint64_t b2h = make_sdesc(sb + 2 * BOX_BYTES + ko);
-                            const uint64_t b2l = make_sdesc(sb + 2 * BOX_BYTES + 64 + ko);
-                            const uint32_t acc0 = (ks > ks_beg || kk > 0) ? 1u : 0u;
-                            mma_bf16(dP, ah, b2h, acc0);
-                            mma_bf16(dP, al, bh, 1u);
-                            mma_bf16(dQ, ah, b2l, acc0);
-                            mma_bf16(dQ, al, bl, 1u);
+                            const uint32_t a = lo_stage + kk * 2;   // 16 bf16 = 32 bytes along K
+                            // alternate the accumulators: an MMA into the
+                            // accumulator the previous one writes waits for it
+                            mma_bf16_lo<PAIR>(dP, a, a + B2, dhi, acc0);            // ah * b'h
+                            mma_bf16_lo<PAIR>(dQ, a, a + B2 + HALF, dhi, acc0);     // ah * b'l
+                            mma_bf16_lo<PAIR>(dP, a + HALF, a + B1, dhi, 1u);       // al * bh
+                            mma_bf16_lo<PAIR>(dQ, a + HALF, a + B1 + HALF, dhi, 1u);  // al * bl
+                            acc0 = 1u;
                         }
-                        tcgen05_commit(&empty[stage]);
-                        if (++stage == STAGES) stage = 0, phase ^= 1u;
+                        tcgen05_commit_both<PAIR>(&empty[stage]);
+                        lo_stage += SBYTES >> 4;
+                        if (++stage == NST) stage = 0, phase ^= 1u, lo_stage = lo0;
                     }
-                    tcgen05_commit(&accf[buf]);
+                    tcgen05_commit_both<PAIR>(&accf[buf]);
                 }
             }
             // Wait (bounded) until every issued MMA has completed before the
             // accumulators are released.
-            tcgen05_commit(done);
+            tcgen05_commit<PAIR>(done);
             const uint32_t addr = smem_u32(done);
             long long start = clock64();
             while (!mbar_try_wait(addr, 0)) {
@@ -559,13 +690,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         constexpr int HC = BN / 2;    // columns per drain warp
         uint32_t kbc = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-            const TileInfo ti = tile_info(g, t, num_m, num_n);
+        for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
+            const TileInfo ti = tile_info<PAIR>(g, t, num_m, num_n, rank);
             const int kbt = (ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
             if (kbt <= 0) continue;   // the product is zero on this tile: C stays as it is
             uint32_t run[HC / 2];
 #pragma unroll
             for (int i = 0; i < HC / 2; ++i) run[i] = 0;
+            int chain = 0;
             for (int kb = 0; kb < kbt; ++kb, ++kbc) {
                 const uint32_t buf = kbc & 1u, use = kbc >> 1;
                 if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
@@ -581,6 +713,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     for (int j = 0; j < 16; j += 2) {
                         uint32_t pair = run[c * 8 + j / 2];
                         int lo16 = (int)(pair & 0xFFFFu), hi16 = (int)(pair >> 16);
+                        // One element after the other (an empty asm ties each
+                        // element's inputs to the previous result): a burst of
+                        // independent FP32 reductions saturates the FP32 pipe,
+                        // and a saturated FP32 pipe slows the concurrent MMAs
+                        // of the SM several fold (measured).  Serialised, the
+                        // drain still ends well within the next k-block.
+                        asm volatile("" : "+f"(pv[j]), "+f"(qv[j]) : "r"(chain));
                         {
                             float v = fmaf(256.0f, fred(pv[j], pf, pinv), fred(qv[j], pf, pinv));
                             int s = lo16 + f2i_small(fred(v, pf, pinv));
@@ -588,6 +727,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             s -= (s >= P) ? P : 0;
                             lo16 = s;
                         }
+                        asm volatile("" : "+f"(pv[j + 1]), "+f"(qv[j + 1]) : "r"(lo16));
                         {
                             float v = fmaf(256.0f, fred(pv[j + 1], pf, pinv), fred(qv[j + 1], pf, pinv));
                             int s = hi16 + f2i_small(fred(v, pf, pinv));
@@ -595,17 +735,21 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             s -= (s >= P) ? P : 0;
                             hi16 = s;
                         }
+                        chain = hi16;
                         run[c * 8 + j / 2] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
                     }
                 }
                 tcgen05_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[buf]);
+                if (lane == 0) {
+                    if (PAIR) mbar_arrive_cluster(mapa_rank(smem_u32(&acce[buf]), 0));
+                    else mbar_arrive(&acce[buf]);
+                }
             }
             if (!ok) break;
             if (g.xout.ptr) {
                 // planes-out: the product's digits, 16-byte stores per plane
-                const int64_t row = ti.mt * BM + row_in_tile;
+                const int64_t row = ti.mt * TBM + (int64_t)rank * BM + row_in_tile;
                 if (row < ti.M) {
                     const int64_t k0 = g.xout_col0 + ti.nt * BN + half * HC;
 #pragma unroll
@@ -627,7 +771,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 continue;
             }
             // C <- (C + sign * run) mod p for this thread's row segment.
-            const int64_t row = ti.mt * BM + row_in_tile;
+            const int64_t row = ti.mt * TBM + (int64_t)rank * BM + row_in_tile;
             const int64_t col0 = ti.c_col0 + ti.nt * BN + half * HC;   // column of C
             const int64_t ncol = ti.c_col0 + ti.N;                        // column limit
             const int64_t prow = (row < ti.M && ti.c_rows) ? (int64_t)ti.c_rows[row] : row;
@@ -685,9 +829,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 
     tcgen05_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();   // the leader's MMAs may write the peer's TMEM until here
     if (warp == 1) {
         tcgen05_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        if (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                         : "memory");
     }
 }
 }  // namespace tc
@@ -708,13 +858,13 @@ static int get_encode() {
     return g_encode ? GBLA_OK : GBLA_E_UNSUPPORTED;
 }
 
-static int make_map(CUtensorMap *map, const Planes &pl) {
+static int make_map(CUtensorMap *map, const Planes &pl, int box_rows = tc::BM) {
     GBLA_TRY(get_encode());
     // rows of kp * nplanes interleaved elements; a box is 128 rows x 64
     // elements (128 bytes: one K chunk of two planes)
     cuuint64_t dims[2] = {(cuuint64_t)pl.row_elems(), (cuuint64_t)pl.rows};
     cuuint64_t strides[1] = {(cuuint64_t)pl.row_elems() * 2};
-    cuuint32_t box[2] = {2 * tc::BK, tc::BM};
+    cuuint32_t box[2] = {2 * tc::BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)pl.ptr, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -756,6 +906,38 @@ bool tc_supported() {
     return ok == 1;
 }
 
+// Clusters of two CTAs that can be resident at once for the CTA-pair kernel
+// (0 if such clusters cannot be launched or the pair kernel is not enabled;
+// GBLA_GEMM_PAIR=1 enables it).
+static int pair_max_clusters() {
+    static int n = -1;
+    if (n < 0) {
+        n = 0;
+        const char *e = getenv("GBLA_GEMM_PAIR");
+        if (!e || atoi(e) == 0) return n;
+        if (cudaFuncSetAttribute(tc::modgemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::PAIR_SMEM_BYTES) != cudaSuccess) {
+            cudaGetLastError();
+            return n;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * (unsigned)device_sm_count());
+        cfg.blockDim = dim3(tc::THREADS);
+        cfg.dynamicSmemBytes = tc::PAIR_SMEM_BYTES;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, tc::modgemm_tc_kernel<true>, &cfg) == cudaSuccess && c > 0) n = c;
+        cudaGetLastError();
+    }
+    return n;
+}
+
 int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
             uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
             uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows, const int32_t *row_lead,
@@ -789,12 +971,15 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
     if (A.nplanes != 2 || B.nplanes != 4) return GBLA_E_INTERNAL;
     if ((a_k0 % tc::BK) || (b_k0 % tc::BK)) return GBLA_E_INTERNAL;
+    // Products with more than one row tile and a long K run on CTA pairs.
+    const int clusters = (M > tc::BM && K >= 256) ? pair_max_clusters() : 0;
+    const bool pair = clusters > 0;
     CUtensorMap ma, mb;
     GBLA_TRY(make_map(&ma, A));
-    GBLA_TRY(make_map(&mb, B));
+    GBLA_TRY(make_map(&mb, B, pair ? tc::BN / 2 : tc::BM));
     static bool attr = false;
     if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            tc::SMEM_BYTES));
         attr = true;
     }
@@ -808,9 +993,27 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
     g.withhold_loads = 0;
-    const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
-    const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
-    tc::modgemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    if (pair) {
+        const int64_t tiles = ((M + 2 * tc::BM - 1) / (2 * tc::BM)) * ((N + tc::BN - 1) / tc::BN);
+        const int nc = (int)(tiles < clusters ? tiles : clusters);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * (unsigned)nc);
+        cfg.blockDim = dim3(tc::THREADS);
+        cfg.dynamicSmemBytes = tc::PAIR_SMEM_BYTES;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        GBLA_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::modgemm_tc_kernel<true>, ma, mb, g));
+    } else {
+        const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
+        const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+        tc::modgemm_tc_kernel<false><<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    }
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
@@ -834,7 +1037,7 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     GBLA_TRY(make_map(&mb, B));
     static bool attr = false;
     if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            tc::SMEM_BYTES));
         attr = true;
     }
@@ -850,7 +1053,7 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     g.xout_col0 = out_col0;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
-    tc::modgemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    tc::modgemm_tc_kernel<false><<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
@@ -892,7 +1095,7 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
     GBLA_TRY(make_map(&mb, B));
     static bool attr = false;
     if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            tc::SMEM_BYTES));
         attr = true;
     }
@@ -903,7 +1106,7 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
     g.C = C; g.ldc = ldc; g.sign = sign;
     g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
     g.err = err;
-    tc::modgemm_tc_kernel<<<device_sm_count(), tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    tc::modgemm_tc_kernel<false><<<device_sm_count(), tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
@@ -925,7 +1128,7 @@ int modgemm_withheld_loads(uint32_t *err, cudaStream_t s)
     if (rc == GBLA_OK) {
         static bool attr = false;
         if (!attr) {
-            if (cudaFuncSetAttribute(tc::modgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if (cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      tc::SMEM_BYTES) != cudaSuccess) rc = GBLA_E_CUDA;
             attr = true;
         }
@@ -941,7 +1144,7 @@ int modgemm_withheld_loads(uint32_t *err, cudaStream_t s)
         g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
         g.err = err;
         g.withhold_loads = 1;
-        tc::modgemm_tc_kernel<<<1, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+        tc::modgemm_tc_kernel<false><<<1, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
     dfree(C, s);

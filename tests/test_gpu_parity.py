@@ -57,11 +57,13 @@ def test_modmatmul_random(variant, shape, p, sign):
 @pytest.mark.parametrize("variant", [gbla.GEMM_SIMT, gbla.GEMM_TCGEN05])
 @pytest.mark.parametrize("K", [511, 512, 513, 1024, 2048 + 64])
 @pytest.mark.parametrize("fill", ["pm1", "half", "halfp1", "digit_extreme", "mixed"])
-def test_modmatmul_at_the_k_block_bound(variant, K, fill):
+@pytest.mark.parametrize("M", [128, 384])
+def test_modmatmul_at_the_k_block_bound(variant, K, fill, M):
     """All-extreme operands at and around the 512-deep exact fp32 block: every
-    digit product has the largest magnitude the split allows."""
+    digit product has the largest magnitude the split allows.  M = 384 runs
+    the tensor-core product on CTA pairs (256-row tiles, a ragged last one)."""
     p = 65521
-    M, N = 128, 128
+    N = 128
     h = (p - 1) // 2
     vals = {"pm1": p - 1, "half": h, "halfp1": h + 1, "digit_extreme": (128 * 256 - 128) % p}
     if fill == "mixed":
