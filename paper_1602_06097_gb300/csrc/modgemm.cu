@@ -190,8 +190,8 @@ constexpr int BOX_BYTES = 128 * 128;                // one TMA box: 128 rows x 1
 constexpr int STAGE_BYTES = 3 * BOX_BYTES;          // [Ah Al] | [Bh Bl] | [B'h B'l]
 constexpr int BAR_BYTES = 256;
 // CTA pair (cta_group::2): one 256 x 128 tile per pair, each CTA holding 128
-// rows of A and 64 rows of B per stage, so a stage is 32 KiB and six fit.
-constexpr int PAIR_STAGES = 6;
+// rows of A and 64 rows of B per stage (32 KiB).
+constexpr int PAIR_STAGES = 4;
 constexpr int PAIR_B_BOX_BYTES = 64 * 128;                          // 64 rows x 128 bytes
 constexpr int PAIR_STAGE_BYTES = BOX_BYTES + 2 * PAIR_B_BOX_BYTES;  // [Ah Al] | [Bh Bl] | [B'h B'l]
 constexpr int64_t GROUP_M_DEFAULT = 4;              // row tiles per raster group (see tile_coords)
@@ -319,31 +319,6 @@ __device__ __forceinline__ void tcgen05_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-template <bool PAIR>
-__device__ __forceinline__ void tcgen05_commit(uint64_t *bar) {
-    if (PAIR)
-        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(bar))
-                     : "memory");
-    else
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(bar))
-                     : "memory");
-}
-
-// Pair: arrive on the barrier at the same offset in both CTAs of the pair.
-template <bool PAIR>
-__device__ __forceinline__ void tcgen05_commit_both(uint64_t *bar) {
-    if (PAIR)
-        asm volatile(
-            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                smem_u32(bar)),
-            "h"((uint16_t)3)
-            : "memory");
-    else
-        tcgen05_commit<false>(bar);
-}
-
 // Shared-memory matrix descriptor: K-major operand of 128 rows with 128-byte
 // rows, loaded by TMA with 128-byte swizzle.  Each 128-byte row holds two
 // planes' 32-wide K chunks; an operand (one plane, 16 K values) is selected
@@ -371,32 +346,90 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
 constexpr uint32_t IDESC_PAIR = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                 ((uint32_t)((2 * BM) >> 4) << 24);
 
-// The MMA issuer must keep up with the tensor core (one 128 x 128 x 16 MMA
-// every 64 cycles) from a single thread, so its instruction stream is kept
-// short: the descriptors' high words are one constant, the low words (start
-// address >> 4 in bits 0..13, the leading byte offset above) are formed per
-// operand by a 32-bit add, and the pair is joined inside the asm.
+// One K = 16 step of the digit products for a stage: four MMAs issued by an
+// elected lane of the converged MMA warp,
+//   P += ah * b'h,  Q += ah * b'l,  P += al * bh,  Q += al * bl,
+// with descriptor low words a (ah; al = a + 4), b1 (bh; bl = b1 + 4) and b2
+// (b'h; b'l = b2 + 4) and the common high word hi.
 template <bool PAIR>
-__device__ __forceinline__ void mma_bf16_lo(uint32_t d_tmem, uint32_t alo, uint32_t blo, uint32_t dhi, uint32_t accumulate) {
+__device__ __forceinline__ void mma_step(uint32_t dP, uint32_t dQ, uint32_t a, uint32_t b1, uint32_t b2, uint32_t hi,
+                                         uint32_t acc0) {
     if (PAIR)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
-            "setp.ne.b32 p, %5, 0;\n\t"
-            "mov.b64 da, {%1, %3};\n\t"
-            "mov.b64 db, {%2, %3};\n\t"
-            "tcgen05.mma.cta_group::2.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
-            "r"(alo), "r"(blo), "r"(dhi), "r"(IDESC_PAIR), "r"(accumulate)
-            : "memory");
+        asm volatile("{\n\t.reg .pred p, e;\n\t.reg .b32 r;\n\t.reg .b64 a0, a1, x0, x1, y0, y1;\n\t"
+                     "elect.sync r|e, 0xffffffff;\n\t"
+                     "setp.ne.b32 p, %7, 0;\n\t"
+                     "mov.b64 a0, {%2, %5};\n\t"
+                     "add.u32 r, %2, 4;\n\tmov.b64 a1, {r, %5};\n\t"
+                     "mov.b64 x0, {%3, %5};\n\t"
+                     "add.u32 r, %3, 4;\n\tmov.b64 x1, {r, %5};\n\t"
+                     "mov.b64 y0, {%4, %5};\n\t"
+                     "add.u32 r, %4, 4;\n\tmov.b64 y1, {r, %5};\n\t"
+                     "@e tcgen05.mma.cta_group::2.kind::f16 [%0], a0, y0, %6, p;\n\t"
+                     "@e tcgen05.mma.cta_group::2.kind::f16 [%1], a0, y1, %6, p;\n\t"
+                     "@e tcgen05.mma.cta_group::2.kind::f16 [%0], a1, x0, %6, 1;\n\t"
+                     "@e tcgen05.mma.cta_group::2.kind::f16 [%1], a1, x1, %6, 1;\n\t}" ::"r"(dP),
+                     "r"(dQ), "r"(a), "r"(b1), "r"(b2), "r"(hi), "r"(IDESC_PAIR), "r"(acc0)
+                     : "memory");
     else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
-            "setp.ne.b32 p, %5, 0;\n\t"
-            "mov.b64 da, {%1, %3};\n\t"
-            "mov.b64 db, {%2, %3};\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
-            "r"(alo), "r"(blo), "r"(dhi), "r"(IDESC), "r"(accumulate)
-            : "memory");
+        asm volatile("{\n\t.reg .pred p, e;\n\t.reg .b32 r;\n\t.reg .b64 a0, a1, x0, x1, y0, y1;\n\t"
+                     "elect.sync r|e, 0xffffffff;\n\t"
+                     "setp.ne.b32 p, %7, 0;\n\t"
+                     "mov.b64 a0, {%2, %5};\n\t"
+                     "add.u32 r, %2, 4;\n\tmov.b64 a1, {r, %5};\n\t"
+                     "mov.b64 x0, {%3, %5};\n\t"
+                     "add.u32 r, %3, 4;\n\tmov.b64 x1, {r, %5};\n\t"
+                     "mov.b64 y0, {%4, %5};\n\t"
+                     "add.u32 r, %4, 4;\n\tmov.b64 y1, {r, %5};\n\t"
+                     "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, y0, %6, p;\n\t"
+                     "@e tcgen05.mma.cta_group::1.kind::f16 [%1], a0, y1, %6, p;\n\t"
+                     "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a1, x0, %6, 1;\n\t"
+                     "@e tcgen05.mma.cta_group::1.kind::f16 [%1], a1, x1, %6, 1;\n\t}" ::"r"(dP),
+                     "r"(dQ), "r"(a), "r"(b1), "r"(b2), "r"(hi), "r"(IDESC), "r"(acc0)
+                     : "memory");
 }
+
+// tcgen05.commit from an elected lane of a converged warp.
+template <bool PAIR, bool BOTH>
+__device__ __forceinline__ void commit_elected(uint64_t *bar) {
+    if (PAIR && BOTH)
+        asm volatile("{\n\t.reg .pred e;\n\t.reg .b32 r;\n\telect.sync r|e, 0xffffffff;\n\t"
+                     "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}"
+                     ::"r"(smem_u32(bar)), "h"((uint16_t)3)
+                     : "memory");
+    else if (PAIR)
+        asm volatile("{\n\t.reg .pred e;\n\t.reg .b32 r;\n\telect.sync r|e, 0xffffffff;\n\t"
+                     "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+    else
+        asm volatile("{\n\t.reg .pred e;\n\t.reg .b32 r;\n\telect.sync r|e, 0xffffffff;\n\t"
+                     "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+}
+
+// Warp-uniform bounded wait: every lane polls; a completed phase stays
+// complete until this warp consumes it, so any lane's success is the warp's.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag, uint32_t *err) {
+    const uint32_t addr = smem_u32(bar);
+    if (__any_sync(0xffffffffu, mbar_try_wait(addr, parity))) return true;
+    long long start = clock64();
+    for (uint32_t it = 0;; ++it) {
+        if (__any_sync(0xffffffffu, mbar_try_wait(addr, parity))) return true;
+        if ((it & 255u) == 255u) {
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) return false;
+            if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                if ((threadIdx.x & 31) == 0) {
+                    *abort_flag = 1;
+                    dev_fail(err, DEV_ERR_TIMEOUT);
+                }
+                __syncwarp();
+                return false;
+            }
+        }
+    }
+}
+
 
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -442,7 +475,7 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t nu
 __device__ __forceinline__ int tile_kstep0(const Args &g, int64_t mt, int64_t tbm) {
     if (!g.row_lead) return 0;
     const int64_t k = (int64_t)g.row_lead[(mt / g.group_m) * g.group_m * tbm] - g.a_k0;
-    return k > 0 ? (int)(k / BK) : 0;
+    return k > 0 ? (int)(k / BK) & ~(STAGES - 1) : 0;   // whole rounds of the stage ring
 }
 
 struct TileInfo {
@@ -560,7 +593,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 
     const int64_t num_m = (g.M + TBM - 1) / TBM, num_n = (g.N + BN - 1) / BN;
     const int64_t num_tiles = g.probs ? g.probs[g.nprob].tile_off : num_m * num_n;
-    const int ksteps = (int)((g.K + BK - 1) / BK);
+    // K steps run in whole rounds of the 4-stage ring (steps past K read zero
+    // padding): every tile starts at stage 0, and the MMA issuer's stage
+    // offsets are compile-time constants.
+    static_assert(STAGES == 4 && PAIR_STAGES == 4 && KSTEPS_PER_BLOCK % 4 == 0, "ring rounds");
+    const int ksteps = (int)(((g.K + BK - 1) / BK + 3) & ~int64_t(3));
     const int64_t tile0 = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
     const int64_t tstep = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
 
@@ -623,58 +660,54 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0 && leader) {
-            // ---------------- MMA issuer
-            int stage = 0;
+        if (leader) {
+            // ---------------- MMA issuer: the whole warp runs the loop, an
+            // elected lane issues.  The loop is unrolled over the 4 stages of
+            // the ring so that every descriptor is a constant offset from one
+            // register: the tensor core starves if the issuing warp spends
+            // more than a few instructions between MMAs (measured).
             uint32_t phase = 0;
             uint32_t kbc = 0;
             bool ok = true;
             const uint64_t d0 = make_sdesc(smem_u32(tiles));
             const uint32_t dhi = (uint32_t)(d0 >> 32), lo0 = (uint32_t)d0;
-            uint32_t lo_stage = lo0;   // descriptor low word of the current stage
-            constexpr uint32_t B1 = BOX_BYTES >> 4, B2 = (BOX_BYTES + BBOX) >> 4, HALF = 64 >> 4;
+            constexpr uint32_t SB = SBYTES >> 4, B1 = BOX_BYTES >> 4, B2 = (BOX_BYTES + BBOX) >> 4;
             for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
                 const int ks0 = tile_info<PAIR>(g, t, num_m, num_n, rank).ks0;
                 const int kbt = (ksteps - ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
                 for (int kb = 0; kb < kbt && ok; ++kb, ++kbc) {
                     const uint32_t buf = kbc & 1u, use = kbc >> 1;
-                    if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                    if (!mbar_wait_warp(&acce[buf], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
                     tcgen05_fence_after();
                     const uint32_t dP = tmem + buf * 256u, dQ = dP + 128u;
                     const int ks_beg = ks0 + kb * KSTEPS_PER_BLOCK;
                     const int ks_end = min(ksteps, ks_beg + KSTEPS_PER_BLOCK);
                     uint32_t acc0 = 0;
-                    for (int ks = ks_beg; ks < ks_end; ++ks) {
-                        // the stage's operands were written by TMA and the
-                        // barrier completes with them: no thread-sync fence
-                        if (!mbar_try_wait(smem_u32(&full[stage]), phase) &&
-                            !mbar_wait(&full[stage], phase, abort_flag, g.err)) { ok = false; break; }
+                    for (int ks = ks_beg; ks < ks_end && ok; ks += NST) {
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint32_t a = lo_stage + kk * 2;   // 16 bf16 = 32 bytes along K
-                            // alternate the accumulators: an MMA into the
-                            // accumulator the previous one writes waits for it
-                            mma_bf16_lo<PAIR>(dP, a, a + B2, dhi, acc0);            // ah * b'h
-                            mma_bf16_lo<PAIR>(dQ, a, a + B2 + HALF, dhi, acc0);     // ah * b'l
-                            mma_bf16_lo<PAIR>(dP, a + HALF, a + B1, dhi, 1u);       // al * bh
-                            mma_bf16_lo<PAIR>(dQ, a + HALF, a + B1 + HALF, dhi, 1u);  // al * bl
+                        for (int st = 0; st < NST; ++st) {
+                            // the stage's operands were written by TMA and the
+                            // barrier completes with them: no thread-sync fence
+                            if (!mbar_wait_warp(&full[st], phase, abort_flag, g.err)) { ok = false; break; }
+                            const uint32_t a = lo0 + st * SB;
+                            mma_step<PAIR>(dP, dQ, a, a + B1, a + B2, dhi, acc0);
+                            mma_step<PAIR>(dP, dQ, a + 2, a + 2 + B1, a + 2 + B2, dhi, 1u);   // next 16 of K
                             acc0 = 1u;
+                            commit_elected<PAIR, true>(&empty[st]);
                         }
-                        tcgen05_commit_both<PAIR>(&empty[stage]);
-                        lo_stage += SBYTES >> 4;
-                        if (++stage == NST) stage = 0, phase ^= 1u, lo_stage = lo0;
+                        phase ^= 1u;
                     }
-                    tcgen05_commit_both<PAIR>(&accf[buf]);
+                    if (ok) commit_elected<PAIR, true>(&accf[buf]);
                 }
             }
             // Wait (bounded) until every issued MMA has completed before the
             // accumulators are released.
-            tcgen05_commit<PAIR>(done);
+            commit_elected<PAIR, false>(done);
             const uint32_t addr = smem_u32(done);
             long long start = clock64();
-            while (!mbar_try_wait(addr, 0)) {
+            while (!__any_sync(0xffffffffu, mbar_try_wait(addr, 0))) {
                 if (clock64() - start > WAIT_LIMIT_CYCLES) {
-                    dev_fail(g.err, DEV_ERR_TIMEOUT);
+                    if (lane == 0) dev_fail(g.err, DEV_ERR_TIMEOUT);
                     break;
                 }
             }
