@@ -321,7 +321,8 @@ def main():
         "rank": int(r_out), "out_nnz": int(nnz_out),
         "shape": {"npiv": npiv, "m_cd": m_cd, "n_d": n_d, "rank_d": st0["rank_d"]},
         "phase_ms": {k: float(np.mean([s[k] for s in stats])) for k in
-                     ("ms_split", "ms_trsm", "ms_schur", "ms_echelon", "ms_backsub", "ms_output", "ms_total")},
+                     ("ms_split", "ms_trsm", "ms_schur", "ms_echelon", "ms_echelon_back", "ms_backsub", "ms_output",
+                      "ms_total")},
         "wall_ms_per_step": wall * 1e3 / a.steps,
         "roofline": {"kernel": "modgemm_tc_kernel (Schur update launch)", "bound": "tensor",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -90,6 +90,7 @@ typedef struct {
     double mod_ops;    /* modular multiply-adds of the dense products (zero staircase excluded) */
     int64_t launches;  /* CUDA kernels launched by the call */
     double schur_mod_ops; /* the same for the Schur update D <- D - X*B alone */
+    double ms_echelon_back; /* part of ms_echelon: the backward pass (RREF rows from the echelon form) */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */

@@ -130,7 +130,7 @@ __device__ __forceinline__ void dev_fail(uint32_t *err, uint32_t bit) {
 // ------------------------------------------- transposing plane conversion
 // One 64 x 64 tile of a transposing conversion into digit planes, run by a
 // block of 256 threads:
-//   dst row (row0 + r), column k  <-  src[g(k) * lds + col0 + r]
+//   dst row (row0 + r), column (dcol0 + k)  <-  src[g(k) * lds + col0 + r]
 // for r in [r0, r0 + 64), k in [k0, k0 + 64); zero where r >= R, k >= Kc or
 // g(k) < 0, with g(k) = rgather ? rgather[k] : k.  Source rows are read 64
 // entries at a time; each plane row receives 128 contiguous bytes written as
@@ -177,7 +177,8 @@ __device__ __forceinline__ void store_digits8(const Planes &dst, int64_t r, int6
 
 __device__ __forceinline__ void tp_tile(const Planes &dst, int64_t row0, int64_t r0, int64_t k0, int64_t R, int64_t Kc,
                                         const uint16_t *__restrict__ src, int64_t lds, int64_t col0,
-                                        const int32_t *__restrict__ rgather, const ModP &mp, TpSmem &sm)
+                                        const int32_t *__restrict__ rgather, const ModP &mp, TpSmem &sm,
+                                        int64_t dcol0 = 0)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = warp; i < TP_TILE; i += 8) {
@@ -198,7 +199,7 @@ __device__ __forceinline__ void tp_tile(const Planes &dst, int64_t row0, int64_t
         uint32_t a[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) a[e] = sm.t[c * 8 + e][rr];
-        store_digits8(dst, row0 + r0 + rr, k0 + c * 8, a, mp);
+        store_digits8(dst, row0 + r0 + rr, dcol0 + k0 + c * 8, a, mp);
     }
 }
 

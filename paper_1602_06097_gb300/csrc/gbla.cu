@@ -321,8 +321,8 @@ struct Timer {
         if (on)
             for (auto &e : ev) cudaEventCreate(&e);
     }
-    void mark(cudaStream_t s) {
-        if (on && n < 8) cudaEventRecord(ev[n++], s);
+    void mark(cudaStream_t s) {   // events 0..6 mark the phases; 7 is recorded inside the echelon
+        if (on && n < 7) cudaEventRecord(ev[n++], s);
     }
     double ms(int a, int b) {
         float t = 0;
@@ -470,7 +470,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     dfree(A16, s);
     dfree(B16, s);
     A16 = B16 = nullptr;
-    STEP(multiline_build(dc, pi, &ml, mp, s));
+    // the 2-multiline form of A drives the sparse leaf solves: those of the
+    // first pass unless they run on the tensor cores, those of the second
+    if (!tc_leaves || want_reduced) STEP(multiline_build(dc, pi, &ml, mp, s));
     tm.mark(s);  // 1
 
     // ---- new order: X = C A^-1, then D <- D - X B
@@ -500,7 +502,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     STEP(dalloc_t(&prow, (size_t)m_cd + 1, s));
     STEP(dalloc_t(&pcol, (size_t)m_cd + 1, s));
     {
-        EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, variant, err, s, &ctr};
+        EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, variant, err, s, &ctr,
+                   tm.on ? tm.ev[7] : nullptr};
         NvtxRange r("gbla.echelon");
         STEP(echelon_d(E, &rank_d));
     }
@@ -620,6 +623,12 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             stats->ms_trsm = tm.ms(1, 2);
             stats->ms_schur = tm.ms(2, 3);
             stats->ms_echelon = tm.ms(3, 4);
+            if (tm.on && tm.n >= 5) {   // event 7: start of the backward pass of the echelon
+                float t = 0;
+                if (cudaEventQuery(tm.ev[7]) == cudaSuccess && cudaEventElapsedTime(&t, tm.ev[7], tm.ev[4]) == cudaSuccess)
+                    stats->ms_echelon_back = t;
+                cudaGetLastError();
+            }
             stats->ms_backsub = tm.ms(4, 5);
             stats->ms_output = tm.ms(5, 6);
             stats->ms_total = tm.ms(0, 6);

@@ -67,7 +67,7 @@ int modgemm_withheld_loads(uint32_t *err, cudaStream_t s);
 // u16 -> digit planes (see modgemm.cu).
 int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds, int64_t col_off,
               bool transposed, const int32_t *rgather, const int32_t *cgather, const ModP &mp, cudaStream_t s,
-              const int32_t *zero_if = nullptr, bool k_le_r_only = false);
+              const int32_t *zero_if = nullptr, bool k_le_r_only = false, int64_t dst_col0 = 0);
 
 // Stream-ordered device allocation helpers (memory pool of the device).
 int dalloc(void **ptr, size_t bytes, cudaStream_t s);

@@ -72,33 +72,37 @@ __global__ void __launch_bounds__(256) to_planes_kernel(Planes dst, int64_t R, i
     store_digits8(dst, r, k0, a, mp);
 }
 
-// Transposed conversion: dst row r, column k <- src[g(k)][col_off + r], one
-// 64 x 64 tile per block.  With k_le_r_only, tiles whose every k exceeds every
+// Transposed conversion: dst row r, column dst_col0 + k <- src[g(k)][col_off + r],
+// one 64 x 64 tile per block.  With k_le_r_only, tiles whose every k exceeds every
 // r are skipped (their planes are left unwritten): for the transpose of an
 // upper triangular matrix those entries are zero and no product reads them.
 __global__ void __launch_bounds__(256) to_planes_t_kernel(Planes dst, int64_t R, int64_t Kc,
                                                           const uint16_t *__restrict__ src, int64_t lds,
                                                           int64_t col_off, const int32_t *__restrict__ rgather,
-                                                          int k_le_r_only, ModP mp)
+                                                          int k_le_r_only, int64_t dst_col0, ModP mp)
 {
     __shared__ TpSmem sm;
     const int64_t k0 = (int64_t)blockIdx.x * TP_TILE, r0 = (int64_t)blockIdx.y * TP_TILE;
     if (k_le_r_only && k0 > r0 + TP_TILE - 1) return;
-    tp_tile(dst, 0, r0, k0, R, Kc, src, lds, col_off, rgather, mp, sm);
+    tp_tile(dst, 0, r0, k0, R, Kc, src, lds, col_off, rgather, mp, sm, dst_col0);
 }
 
 int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int64_t lds,
               int64_t col_off, bool transposed, const int32_t *rgather, const int32_t *cgather,
-              const ModP &mp, cudaStream_t s, const int32_t *zero_if, bool k_le_r_only)
+              const ModP &mp, cudaStream_t s, const int32_t *zero_if, bool k_le_r_only, int64_t dst_col0)
 {
     if (dst.rows <= 0 || dst.kp <= 0) return GBLA_OK;
+    if (dst_col0 % 128 || (dst_col0 && !transposed)) return GBLA_E_INTERNAL;
     // Cover the logical rectangle rounded up to whole 128 x 128 tiles (the
     // product reads nothing else); the rest of the buffer is left as is.
     const int64_t rows = round_up(R > 0 ? R : 1, 128) < dst.rows ? round_up(R > 0 ? R : 1, 128) : dst.rows;
-    const int64_t ks = round_up(Kc > 0 ? Kc : 1, 128) < dst.kp ? round_up(Kc > 0 ? Kc : 1, 128) : dst.kp;
+    const int64_t kav = dst.kp - dst_col0;   // columns available from dst_col0
+    const int64_t ks = round_up(Kc > 0 ? Kc : 1, 128) < kav ? round_up(Kc > 0 ? Kc : 1, 128) : kav;
+    if (ks <= 0) return GBLA_E_INTERNAL;
     if (transposed) {
         dim3 grid((unsigned)(ks / TP_TILE), (unsigned)(rows / TP_TILE));
-        to_planes_t_kernel<<<grid, 256, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, k_le_r_only ? 1 : 0, mp);
+        to_planes_t_kernel<<<grid, 256, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, k_le_r_only ? 1 : 0,
+                                                 dst_col0, mp);
     } else {
         dim3 grid((unsigned)(ks / 128), (unsigned)(rows / 16));
         to_planes_kernel<<<grid, 256, 0, s>>>(dst, R, Kc, src, lds, col_off, rgather, cgather, zero_if, mp);

@@ -849,8 +849,14 @@ int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, const Pl
 
 
 
+// R <- T^-1 R for the rows [lo, hi) of R (T = R at the pivot columns, unit
+// upper triangular), by halving: the lower half first, then its product into
+// the upper half, then the upper half.  RT holds the B-operand planes of R^T
+// (row = column of R, K = row of R); a 128-row block is written there before
+// its leaf product (which reads the block itself) and again once final, so
+// the products of the internal nodes read final rows without converting them.
 static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_t *pcol_dev,
-                       const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &Bp,
+                       const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &RT,
                        const uint16_t *Nm_all)
 {
     const ModP &mp = *E.mp;
@@ -862,19 +868,19 @@ static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_
         const int64_t cs = pcol[lo] & ~int64_t(63);   // rows lo.. are zero left of pcol[lo]
         const uint16_t *Nm = Nm_all + (size_t)(lo / PANEL) * PANEL * PANEL;
         GBLA_TRY(to_planes(Ap, w, w, Nm, PANEL, 0, false, nullptr, nullptr, mp, s));
-        GBLA_TRY(to_planes(Bp, n - cs, w, R + lo * ldr, ldr, cs, true, nullptr, nullptr, mp, s));
-        return modgemm(Ap, 0, 0, Bp, 0, 0, R + lo * ldr + cs, ldr, w, n - cs, w, -1, mp, E.variant, E.err, s,
-                       E.ctr);
+        GBLA_TRY(to_planes(RT, n, w, R + lo * ldr, ldr, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo));
+        GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, lo, R + lo * ldr + cs, ldr, w, n - cs, w, -1, mp, E.variant, E.err, s,
+                         E.ctr));
+        return to_planes(RT, n, w, R + lo * ldr, ldr, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo);
     }
     const int64_t mid = lo + round_up((hi - lo) / 2, PANEL);
-    GBLA_TRY(backsub_rec(E, R, ldr, pcol_dev, pcol, mid, hi, Ap, Bp, Nm_all));
+    GBLA_TRY(backsub_rec(E, R, ldr, pcol_dev, pcol, mid, hi, Ap, RT, Nm_all));
     // R[lo:mid] -= R[lo:mid, P_D[mid:hi]] * R[mid:hi]   (rows mid.. are zero left of P_D[mid])
     const int64_t cs = pcol[mid] & ~int64_t(63);
     GBLA_TRY(to_planes(Ap, mid - lo, hi - mid, R + lo * ldr, ldr, 0, false, nullptr, pcol_dev + mid, mp, s));
-    GBLA_TRY(to_planes(Bp, n - cs, hi - mid, R + mid * ldr, ldr, cs, true, nullptr, nullptr, mp, s));
-    GBLA_TRY(modgemm(Ap, 0, 0, Bp, 0, 0, R + lo * ldr + cs, ldr, mid - lo, n - cs, hi - mid, -1, mp, E.variant,
+    GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, mid, R + lo * ldr + cs, ldr, mid - lo, n - cs, hi - mid, -1, mp, E.variant,
                      E.err, s, E.ctr));
-    return backsub_rec(E, R, ldr, pcol_dev, pcol, lo, mid, Ap, Bp, Nm_all);
+    return backsub_rec(E, R, ldr, pcol_dev, pcol, lo, mid, Ap, RT, Nm_all);
 }
 
 // Apply the panel bases of jobs [job0, job0 + njobs) (slots given by
@@ -1041,6 +1047,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         ECUDA(cudaStreamSynchronize(s));
     }
     // ---- backward pass: RREF rows into R (pivot column order)
+    if (E.back_start) cudaEventRecord(E.back_start, s);
     if (rank > 0) {
         const int64_t ldr = E.ldd;
         std::vector<int32_t> pcol_h((size_t)rank);
@@ -1062,7 +1069,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
         if (rc == GBLA_OK) rc = planes_alloc(&Ap, rank, rank < 2 * PANEL ? PANEL : rank, 2, s);
-        if (rc == GBLA_OK) rc = planes_alloc(&Bp, n, rank < 2 * PANEL ? PANEL : rank, 4, s);
+        if (rc == GBLA_OK) rc = planes_alloc(&Bp, n, rank, 4, s);   // R^T
         if (rc == GBLA_OK) rc = backsub_rec(E, E.R[0], ldr, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm);
         dfree(Nm, s);
         planes_free(&Ap, s);

@@ -71,6 +71,7 @@ struct EchelonD {
     uint32_t *err;
     cudaStream_t s;
     GemmCounters *ctr;
+    cudaEvent_t back_start = nullptr;   // optional: recorded when the backward pass begins
 };
 int echelon_d(const EchelonD &E, int64_t *rank_out);
 

@@ -46,7 +46,7 @@ class Stats(ctypes.Structure):
                 ("ms_schur", ctypes.c_double), ("ms_echelon", ctypes.c_double),
                 ("ms_backsub", ctypes.c_double), ("ms_output", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("mod_ops", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("schur_mod_ops", ctypes.c_double)]
+                ("schur_mod_ops", ctypes.c_double), ("ms_echelon_back", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
