@@ -743,22 +743,11 @@ __global__ void compact_slots_kernel(int64_t npan, const int32_t *__restrict__ t
     *rank = r;
 }
 
-__global__ void gather_rows_kernel(const uint16_t *__restrict__ D, int64_t ldd, const int32_t *__restrict__ rows,
-                                   int64_t nrows, int64_t n, uint16_t *__restrict__ R, int64_t ldr)
-{
-    for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
-        const uint16_t *src = D + (int64_t)rows[k] * ldd;
-        uint16_t *dst = R + k * ldr;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-            dst[i] = src[i];
-    }
-}
-
 // For every diagonal block b of 128 rows: Nm_b = I - T^-1 with
-// T = R[lo + i][pcol[lo + j]], lo = 128 b (w x w, unit upper triangular).
-// The off-diagonal updates of the back-substitution only touch columns at or
-// right of the next block's pivots, so these blocks are final from the start
-// and all inverses are formed in one launch.
+// T = R[rows[lo + i]][pcol[lo + j]], lo = 128 b (w x w, unit upper
+// triangular).  The back-substitution never modifies the pivot columns, so
+// these blocks are final from the start and all inverses are formed in one
+// launch.
 // Z = T^-1 for the unit upper triangular w x w block T (shared memory), by
 // rows from the bottom: Z[i][j] = d_ij - sum_{i<k<=j} T[i][k] Z[k][j].  Thread
 // j owns column j; rows and columns w.. of Z are left untouched.
@@ -778,7 +767,8 @@ __device__ __forceinline__ void unit_upper_inverse(const uint16_t (*T)[129], uin
     }
 }
 
-__global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__restrict__ R, int64_t ldr, int64_t rank,
+__global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__restrict__ R, int64_t ldr,
+                                                           const int32_t *__restrict__ rows, int64_t rank,
                                                            const int32_t *__restrict__ pcol,
                                                            uint16_t *__restrict__ Nm_all, ModP mp)
 {
@@ -790,7 +780,7 @@ __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__res
     uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem + 128 * 129);  // [128][129]
     const int j = threadIdx.x;
     for (int i = 0; i < w; ++i)
-        T[i][j] = (j < w) ? R[(lo + i) * ldr + pcol[lo + j]] : 0;
+        T[i][j] = (j < w) ? R[(int64_t)rows[lo + i] * ldr + pcol[lo + j]] : 0;
     __syncthreads();
     unit_upper_inverse(T, Z, w, mp);
     for (int i = 0; i < w; ++i)
@@ -849,38 +839,92 @@ int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, const Pl
 
 
 
-// R <- T^-1 R for the rows [lo, hi) of R (T = R at the pivot columns, unit
-// upper triangular), by halving: the lower half first, then its product into
-// the upper half, then the upper half.  RT holds the B-operand planes of R^T
-// (row = column of R, K = row of R); a 128-row block is written there before
-// its leaf product (which reads the block itself) and again once final, so
-// the products of the internal nodes read final rows without converting them.
-static int backsub_rec(const EchelonD &E, uint16_t *R, int64_t ldr, const int32_t *pcol_dev,
+// Column map of the echelon rows: colmap[c] = index of c among the non-pivot
+// columns, or -(j + 1) if c = pcol[j]; npc[i] = i-th non-pivot column.  pcol
+// is ascending, so the pivots left of c are found by binary search.
+__global__ void colmap_np_kernel(const int32_t *__restrict__ pcol, int64_t rank, int64_t n, int32_t *__restrict__ colmap,
+                                 int32_t *__restrict__ npc)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int64_t lo = 0, hi = rank;   // first j with pcol[j] >= c
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pcol[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < rank && pcol[lo] == c) {
+        colmap[c] = -(int32_t)(lo + 1);
+    } else {
+        colmap[c] = (int32_t)(c - lo);
+        npc[c - lo] = (int32_t)c;
+    }
+}
+
+// Rnp[k][i] = D[rows[k]][npc[i]]: the echelon rows at the non-pivot columns.
+__global__ void gather_np_kernel(const uint16_t *__restrict__ D, int64_t ldd, const int32_t *__restrict__ rows,
+                                 int64_t nrows, const int32_t *__restrict__ npc, int64_t nnp, uint16_t *__restrict__ Rnp,
+                                 int64_t ldnp)
+{
+    for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
+        const uint16_t *src = D + (int64_t)rows[k] * ldd;
+        uint16_t *dst = Rnp + k * ldnp;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnp; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = src[npc[i]];
+    }
+}
+
+// RREF rows in full: R[k][c] = Rnp[k][colmap[c]] at non-pivot columns, the
+// unit vector at the pivot columns (R[k][pcol[j]] = [j == k]).
+__global__ void expand_rref_kernel(const uint16_t *__restrict__ Rnp, int64_t ldnp, const int32_t *__restrict__ colmap,
+                                   int64_t nrows, int64_t n, uint16_t *__restrict__ R, int64_t ldr)
+{
+    for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
+        const uint16_t *src = Rnp + k * ldnp;
+        uint16_t *dst = R + k * ldr;
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+            const int32_t m = colmap[c];
+            dst[c] = m >= 0 ? src[m] : (uint16_t)((int64_t)(-m - 1) == k ? 1 : 0);
+        }
+    }
+}
+
+// Rnp <- T^-1 Rnp for the rows [lo, hi), where Rnp holds the echelon rows at
+// the non-pivot columns only (the pivot columns of the reduced form are the
+// unit vectors, nothing to compute) and T = the echelon rows at the pivot
+// columns (unit upper triangular; read from D through the row map, never
+// modified: the updates below only touch non-pivot columns).  By halving: the
+// lower half first, then its product into the upper half, then the upper
+// half.  RT holds the B-operand planes of Rnp^T (row = non-pivot column, K =
+// row); a 128-row block is written there before its leaf product (which reads
+// the block itself) and again once final, so the products of the internal
+// nodes read final rows without converting them.  Rows lo.. are zero left of
+// pcol[lo], i.e. left of non-pivot column pcol[lo] - lo.
+static int backsub_rec(const EchelonD &E, uint16_t *Rnp, int64_t ldnp, int64_t nnp, const int32_t *pcol_dev,
                        const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &RT,
                        const uint16_t *Nm_all)
 {
     const ModP &mp = *E.mp;
     cudaStream_t s = E.s;
-    const int64_t n = E.n;
     if (hi - lo <= PANEL) {
         // leaves are the 128-row blocks (splits fall on multiples of 128)
         const int w = (int)(hi - lo);
-        const int64_t cs = pcol[lo] & ~int64_t(63);   // rows lo.. are zero left of pcol[lo]
+        const int64_t cs = (pcol[lo] - lo) & ~int64_t(63);
         const uint16_t *Nm = Nm_all + (size_t)(lo / PANEL) * PANEL * PANEL;
         GBLA_TRY(to_planes(Ap, w, w, Nm, PANEL, 0, false, nullptr, nullptr, mp, s));
-        GBLA_TRY(to_planes(RT, n, w, R + lo * ldr, ldr, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo));
-        GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, lo, R + lo * ldr + cs, ldr, w, n - cs, w, -1, mp, E.variant, E.err, s,
-                         E.ctr));
-        return to_planes(RT, n, w, R + lo * ldr, ldr, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo);
+        GBLA_TRY(to_planes(RT, nnp, w, Rnp + lo * ldnp, ldnp, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo));
+        GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, lo, Rnp + lo * ldnp + cs, ldnp, w, nnp - cs, w, -1, mp, E.variant, E.err,
+                         s, E.ctr));
+        return to_planes(RT, nnp, w, Rnp + lo * ldnp, ldnp, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo);
     }
     const int64_t mid = lo + round_up((hi - lo) / 2, PANEL);
-    GBLA_TRY(backsub_rec(E, R, ldr, pcol_dev, pcol, mid, hi, Ap, RT, Nm_all));
-    // R[lo:mid] -= R[lo:mid, P_D[mid:hi]] * R[mid:hi]   (rows mid.. are zero left of P_D[mid])
-    const int64_t cs = pcol[mid] & ~int64_t(63);
-    GBLA_TRY(to_planes(Ap, mid - lo, hi - mid, R + lo * ldr, ldr, 0, false, nullptr, pcol_dev + mid, mp, s));
-    GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, mid, R + lo * ldr + cs, ldr, mid - lo, n - cs, hi - mid, -1, mp, E.variant,
-                     E.err, s, E.ctr));
-    return backsub_rec(E, R, ldr, pcol_dev, pcol, lo, mid, Ap, RT, Nm_all);
+    GBLA_TRY(backsub_rec(E, Rnp, ldnp, nnp, pcol_dev, pcol, mid, hi, Ap, RT, Nm_all));
+    // Rnp[lo:mid] -= T[lo:mid, mid:hi] * Rnp[mid:hi]
+    const int64_t cs = (pcol[mid] - mid) & ~int64_t(63);
+    GBLA_TRY(to_planes(Ap, mid - lo, hi - mid, E.D16, E.ldd, 0, false, E.prow + lo, pcol_dev + mid, mp, s));
+    GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, mid, Rnp + lo * ldnp + cs, ldnp, mid - lo, nnp - cs, hi - mid, -1, mp,
+                     E.variant, E.err, s, E.ctr));
+    return backsub_rec(E, Rnp, ldnp, nnp, pcol_dev, pcol, lo, mid, Ap, RT, Nm_all);
 }
 
 // Apply the panel bases of jobs [job0, job0 + njobs) (slots given by
@@ -1050,28 +1094,46 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     if (E.back_start) cudaEventRecord(E.back_start, s);
     if (rank > 0) {
         const int64_t ldr = E.ldd;
+        const int64_t nnp = n - rank;
+        const int64_t ldnp = round_up(nnp > 0 ? nnp : 1, 64);
         std::vector<int32_t> pcol_h((size_t)rank);
-        uint16_t *Nm = nullptr;
+        uint16_t *Nm = nullptr, *Rnp = nullptr;
+        int32_t *colmap = nullptr, *npc = nullptr;
         Planes Ap{}, Bp{};
         rc = dalloc_t(&E.R[0], (size_t)rank * (size_t)ldr, s);
+        if (rc == GBLA_OK) rc = dalloc_t(&colmap, (size_t)n, s);
+        if (rc == GBLA_OK) rc = dalloc_t(&npc, (size_t)(nnp > 0 ? nnp : 1), s);
+        if (rc == GBLA_OK) rc = dalloc_t(&Rnp, (size_t)rank * (size_t)ldnp, s);
         if (rc == GBLA_OK && cudaMemcpyAsync(pcol_h.data(), E.pcol, sizeof(int32_t) * (size_t)rank,
                                              cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = GBLA_E_CUDA;
         if (rc == GBLA_OK) {
-            dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64), (unsigned)(rank < 65535 ? rank : 65535));
-            gather_rows_kernel<<<grid, 256, 0, s>>>(E.D16, E.ldd, E.prow, rank, n, E.R[0], ldr);
+            colmap_np_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E.pcol, rank, n, colmap, npc);
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+        }
+        const dim3 rgrid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64), (unsigned)(rank < 65535 ? rank : 65535));
+        if (rc == GBLA_OK && nnp > 0) {
+            gather_np_kernel<<<rgrid, 256, 0, s>>>(E.D16, E.ldd, E.prow, rank, npc, nnp, Rnp, ldnp);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
         if (rc == GBLA_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
         const int64_t nleaves = (rank + PANEL - 1) / PANEL;
-        if (rc == GBLA_OK) rc = dalloc_t(&Nm, (size_t)nleaves * PANEL * PANEL, s);
-        if (rc == GBLA_OK) {
-            leaf_inverse_kernel<<<(unsigned)nleaves, 128, LEAF_INV_SMEM, s>>>(E.R[0], ldr, rank, E.pcol, Nm, mp);
+        if (rc == GBLA_OK && nnp > 0) rc = dalloc_t(&Nm, (size_t)nleaves * PANEL * PANEL, s);
+        if (rc == GBLA_OK && nnp > 0) {
+            leaf_inverse_kernel<<<(unsigned)nleaves, 128, LEAF_INV_SMEM, s>>>(E.D16, E.ldd, E.prow, rank, E.pcol, Nm,
+                                                                                mp);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
-        if (rc == GBLA_OK) rc = planes_alloc(&Ap, rank, rank < 2 * PANEL ? PANEL : rank, 2, s);
-        if (rc == GBLA_OK) rc = planes_alloc(&Bp, n, rank, 4, s);   // R^T
-        if (rc == GBLA_OK) rc = backsub_rec(E, E.R[0], ldr, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm);
+        if (rc == GBLA_OK && nnp > 0) rc = planes_alloc(&Ap, rank, rank < 2 * PANEL ? PANEL : rank, 2, s);
+        if (rc == GBLA_OK && nnp > 0) rc = planes_alloc(&Bp, nnp, rank, 4, s);   // Rnp^T
+        if (rc == GBLA_OK && nnp > 0) rc = backsub_rec(E, Rnp, ldnp, nnp, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm);
+        if (rc == GBLA_OK) {
+            expand_rref_kernel<<<rgrid, 256, 0, s>>>(Rnp, ldnp, colmap, rank, n, E.R[0], ldr);
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+        }
         dfree(Nm, s);
+        dfree(Rnp, s);
+        dfree(colmap, s);
+        dfree(npc, s);
         planes_free(&Ap, s);
         planes_free(&Bp, s);
     }
