@@ -336,6 +336,19 @@ struct Timer {
     }
 };
 
+// Column width of the tensor-core leaf solves of C*A^-1 (env GBLA_TRSM_LEAF
+// overrides: 128, 256, 512 or 1024).  Wider leaves mean fewer, larger products
+// and two fewer levels of small block updates, for a little more product work.
+static int trsm_leaf_width() {
+    static int v = 0;
+    if (v == 0) {
+        const char *e = getenv("GBLA_TRSM_LEAF");
+        const int x = e ? atoi(e) : 0;
+        v = (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 512;
+    }
+    return v;
+}
+
 int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
                 int64_t *rank_out, gbla_stats *stats) {
     const int want_reduced = opt ? opt->want_reduced : 0;
@@ -351,6 +364,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     // diagonal blocks of the triangular solve on the tensor cores too
     const bool tc_leaves =
         variant == GBLA_GEMM_TCGEN05 || (variant == GBLA_GEMM_AUTO && p >= 8 && tc_supported());
+    const int tc_leaf_w = trsm_leaf_width();
     GemmCounters ctr;
     const long long launches0 = g_launches;
     Timer tm;
@@ -451,8 +465,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s, nullptr, true));
         if (tc_leaves) {
             // inverses of A's diagonal blocks for the tensor-core leaf solves
-            STEP(planes_alloc(&Zt, round_up(npiv, 128), 128, 4, s));
-            STEP(upper_leaf_inverses(A16, ldc, npiv, Zt, mp, s));
+            STEP(planes_alloc(&Zt, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
+            STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, s));
         }
     }
     if (m_cd > 0 && n_d > 0 && npiv > 0) {
@@ -482,9 +496,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         lead_h.resize((size_t)m_cd);
         CSTEP(cudaMemcpyAsync(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, cudaMemcpyDeviceToHost, s));
         CSTEP(cudaStreamSynchronize(s));
-        if (tc_leaves) STEP(planes_alloc(&Ct, m_cd, 128, 2, s));
+        if (tc_leaves) STEP(planes_alloc(&Ct, m_cd, tc_leaf_w, 2, s));
         TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr, pi.cd_lead, &lead_h,
-                    tc_leaves ? &Zt : nullptr, tc_leaves ? &Ct : nullptr};
+                    tc_leaves ? &Zt : nullptr, tc_leaves ? &Ct : nullptr, tc_leaf_w};
         NvtxRange r("gbla.trsm");
         STEP(trsm_upper(T));
     }

@@ -734,7 +734,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             uint32_t run[HC / 2];
 #pragma unroll
             for (int i = 0; i < HC / 2; ++i) run[i] = 0;
-            int chain = 0;
             for (int kb = 0; kb < kbt; ++kb, ++kbc) {
                 const uint32_t buf = kbc & 1u, use = kbc >> 1;
                 if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
@@ -750,13 +749,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     for (int j = 0; j < 16; j += 2) {
                         uint32_t pair = run[c * 8 + j / 2];
                         int lo16 = (int)(pair & 0xFFFFu), hi16 = (int)(pair >> 16);
-                        // One element after the other (an empty asm ties each
-                        // element's inputs to the previous result): a burst of
-                        // independent FP32 reductions saturates the FP32 pipe,
-                        // and a saturated FP32 pipe slows the concurrent MMAs
-                        // of the SM several fold (measured).  Serialised, the
-                        // drain still ends well within the next k-block.
-                        asm volatile("" : "+f"(pv[j]), "+f"(qv[j]) : "r"(chain));
                         {
                             float v = fmaf(256.0f, fred(pv[j], pf, pinv), fred(qv[j], pf, pinv));
                             int s = lo16 + f2i_small(fred(v, pf, pinv));
@@ -764,7 +756,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             s -= (s >= P) ? P : 0;
                             lo16 = s;
                         }
-                        asm volatile("" : "+f"(pv[j + 1]), "+f"(qv[j + 1]) : "r"(lo16));
                         {
                             float v = fmaf(256.0f, fred(pv[j + 1], pf, pinv), fred(qv[j + 1], pf, pinv));
                             int s = hi16 + f2i_small(fred(v, pf, pinv));
@@ -772,7 +763,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             s -= (s >= P) ? P : 0;
                             hi16 = s;
                         }
-                        chain = hi16;
                         run[c * 8 + j / 2] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
                     }
                 }

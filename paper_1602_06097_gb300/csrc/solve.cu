@@ -169,11 +169,13 @@ static int64_t rows_before(const TrsmUpper &T, int64_t bound)
 
 static int trsm_upper_rec(const TrsmUpper &T, int64_t lo, int64_t hi)
 {
-    if (hi - lo <= LEAF) {
+    const bool tc_leaf = T.Zt && T.Ct;
+    const int64_t LW = tc_leaf ? T.tc_leaf : LEAF;   // leaf width
+    if (hi - lo <= LW) {
         // rows leading at or after hi have a zero block here (C and X alike)
         const int64_t rows = rows_before(T, hi);
         if (rows == 0) return GBLA_OK;
-        if (T.Zt && T.Ct) {
+        if (tc_leaf) {
             // X_J = C_J * A_JJ^-1: digit planes of C_J, then one product whose
             // epilogue writes the digit planes of X_J
             const int w = (int)(hi - lo);
@@ -187,7 +189,7 @@ static int trsm_upper_rec(const TrsmUpper &T, int64_t lo, int64_t hi)
         GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
-    const int64_t mid = lo + round_up((hi - lo) / 2, LEAF);
+    const int64_t mid = lo + round_up((hi - lo) / 2, LW);
     GBLA_TRY(trsm_upper_rec(T, lo, mid));
     // C[:, mid:hi] -= X[:, lo:mid] * A[lo:mid, mid:hi]   (A^T planes: row = column of A);
     // only rows leading before mid have X[:, lo:mid] != 0.
@@ -791,10 +793,17 @@ __global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__res
         }
 }
 
-// B-operand planes of (A_JJ^-1)^T for every diagonal block J of A (blockIdx.x
-// = block): row 128 q + j, columns k = 0..127 <- Z[k][j], zero outside w.
-__global__ void __launch_bounds__(128) upper_inverse_planes_kernel(const uint16_t *__restrict__ A, int64_t lda,
-                                                                   int64_t npiv, Planes Zt, ModP mp)
+// Inverses of A's diagonal blocks of width L (a multiple of 128), for the
+// tensor-core leaf solves X_J = C_J * A_JJ^-1.  Z_J = A_JJ^-1 is built in ZN
+// (u16, row-major, leaf J at rows J L .. J L + L, row length L, zero outside
+// the upper triangle and outside A):
+//   1. the 128-blocks on the diagonal, inverted in shared memory;
+//   2. for w = 128, 256, .. < L, every pair of neighbouring w-blocks (o1, o2 =
+//      o1 + w) of a leaf gets its upper-right block from the block inverse
+//      formula  Z12 = -Z11 * A12 * Z22  (two batched products);
+//   3. the B-operand planes of Z_J^T (row J L + j, column k <- Z_J[k][j]).
+__global__ void __launch_bounds__(128) upper_inverse128_kernel(const uint16_t *__restrict__ A, int64_t lda,
+                                                               int64_t npiv, int L, uint16_t *__restrict__ ZN, ModP mp)
 {
     const int64_t lo = (int64_t)blockIdx.x * 128;
     const int w = (int)((npiv - lo) < 128 ? (npiv - lo) : 128);
@@ -806,35 +815,124 @@ __global__ void __launch_bounds__(128) upper_inverse_planes_kernel(const uint16_
         T[i][j] = (j < w) ? A[(lo + i) * lda + lo + j] : 0;
     __syncthreads();
     unit_upper_inverse(T, Z, w, mp);
-#pragma unroll 1
-    for (int c = 0; c < 16; ++c) {
-        uint32_t a[8];
+    // lo = J L + o: rows lo + k of ZN, columns o + j
+    const int64_t o = lo % L;
+    if (j < w)
+        for (int k = 0; k <= j; ++k) ZN[(lo + k) * L + o + j] = Z[k][j];
+}
+
+// One level of the block inverse formula, batched over all block pairs
+// (blockIdx.z = pair; 64 x 64 output tile per CTA, exact uint64 sums):
+//   mode 0: T1_b = A[lo+o1.., lo+o2..] * Z22,   mode 1: Z12 = -Z11 * T1_b.
+__global__ void __launch_bounds__(256) tri_combine_kernel(int mode, int w, int L, const uint16_t *__restrict__ A,
+                                                          int64_t lda, int64_t npiv, uint16_t *__restrict__ ZN,
+                                                          uint16_t *__restrict__ T1, ModP mp)
+{
+    __shared__ uint32_t sx[64][33];
+    __shared__ uint32_t sy[32][65];
+    const int pairs_per_leaf = L / (2 * w);
+    const int64_t b = blockIdx.z;
+    const int64_t lo = (b / pairs_per_leaf) * L;
+    const int o1 = 2 * w * (int)(b % pairs_per_leaf), o2 = o1 + w;
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    const int tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+    uint16_t *t1 = T1 + b * (int64_t)w * w;
+    unsigned long long acc[4][4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int k = c * 8 + e;
-            a[e] = (j < w && k < w) ? Z[k][j] : 0u;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = 0;
+    for (int k0 = 0; k0 < w; k0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int r = e >> 5, k = e & 31;
+            uint32_t v;
+            if (mode == 0) {
+                const int64_t ar = lo + o1 + i0 + r, ac = lo + o2 + k0 + k;
+                v = (ar < npiv && ac < npiv) ? A[ar * lda + ac] : 0u;
+            } else {
+                v = ZN[(lo + o1 + i0 + r) * L + o1 + k0 + k];
+            }
+            sx[r][k] = v;
         }
-        store_digits8(Zt, lo + j, c * 8, a, mp);
+        for (int e = tid; e < 32 * 64; e += 256) {
+            const int k = e >> 6, c = e & 63;
+            sy[k][c] = (mode == 0) ? ZN[(lo + o2 + k0 + k) * L + o2 + j0 + c] : t1[(int64_t)(k0 + k) * w + j0 + c];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            uint32_t xv[4], yv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xv[i] = sx[tr * 4 + i][k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) yv[q] = sy[k][tc * 4 + q];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] += (unsigned long long)xv[i] * yv[q];
+        }
+        __syncthreads();
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t r = mod64(acc[i][q], mp);
+            const int row = i0 + tr * 4 + i, col = j0 + tc * 4 + q;
+            if (mode == 0) t1[(int64_t)row * w + col] = (uint16_t)r;
+            else ZN[(lo + o1 + row) * L + o2 + col] = (uint16_t)(r ? mp.p - r : 0u);
+        }
+}
+
+// Zt row J L + j, column k <- Z_J[k][j]  (tiles of 64 x 64, blockIdx.z = leaf)
+__global__ void __launch_bounds__(256) zt_planes_kernel(const uint16_t *__restrict__ ZN, int L, Planes Zt, ModP mp)
+{
+    __shared__ TpSmem sm;
+    const int64_t J = blockIdx.z;
+    tp_tile(Zt, J * L, (int64_t)blockIdx.x * TP_TILE, (int64_t)blockIdx.y * TP_TILE, L, L, ZN + J * L * L, L, 0,
+            nullptr, mp, sm);
 }
 
 constexpr int LEAF_INV_SMEM = 2 * 128 * 129 * (int)sizeof(uint16_t);
 
-int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, const Planes &Zt, const ModP &mp,
+int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
                         cudaStream_t s)
 {
     if (npiv <= 0) return GBLA_OK;
-    const int64_t nb = (npiv + 127) / 128;
-    if (Zt.nplanes != 4 || Zt.kp != 128 || Zt.rows < nb * 128) return GBLA_E_INTERNAL;
+    if (L < 128 || L % 128 || (L & (L - 1)) != 0) return GBLA_E_INTERNAL;
+    const int64_t nleaves = (npiv + L - 1) / L;
+    if (Zt.nplanes != 4 || Zt.kp != L || Zt.rows < nleaves * L) return GBLA_E_INTERNAL;
     static bool attr = false;
     if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(upper_inverse_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GBLA_CUDA_TRY(cudaFuncSetAttribute(upper_inverse128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            LEAF_INV_SMEM));
         attr = true;
     }
-    upper_inverse_planes_kernel<<<(unsigned)nb, 128, LEAF_INV_SMEM, s>>>(A16, lda, npiv, Zt, mp);
-    GBLA_CUDA_TRY(launch_check());
-    return GBLA_OK;
+    uint16_t *ZN = nullptr, *T1 = nullptr;
+    int rc = dalloc_t(&ZN, (size_t)nleaves * L * L, s);
+    if (rc == GBLA_OK) rc = dalloc_t(&T1, (size_t)nleaves * L * L / 4 + 1, s);
+    if (rc == GBLA_OK && cudaMemsetAsync(ZN, 0, sizeof(uint16_t) * (size_t)nleaves * L * L, s) != cudaSuccess)
+        rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK) {
+        upper_inverse128_kernel<<<(unsigned)((npiv + 127) / 128), 128, LEAF_INV_SMEM, s>>>(A16, lda, npiv, L, ZN, mp);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    for (int w = 128; rc == GBLA_OK && w < L; w *= 2) {
+        const dim3 grid((unsigned)(w / 64), (unsigned)(w / 64), (unsigned)(nleaves * (L / (2 * w))));
+        tri_combine_kernel<<<grid, 256, 0, s>>>(0, w, L, A16, lda, npiv, ZN, T1, mp);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+        if (rc != GBLA_OK) break;
+        tri_combine_kernel<<<grid, 256, 0, s>>>(1, w, L, A16, lda, npiv, ZN, T1, mp);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    if (rc == GBLA_OK) {
+        zt_planes_kernel<<<dim3((unsigned)(L / TP_TILE), (unsigned)(L / TP_TILE), (unsigned)nleaves), 256, 0, s>>>(
+            ZN, L, Zt, mp);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    dfree(ZN, s);
+    dfree(T1, s);
+    return rc;
 }
 
 

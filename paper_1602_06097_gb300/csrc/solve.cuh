@@ -25,19 +25,20 @@ struct TrsmUpper {
     const int32_t *lead_dev;                 // optional: ascending lead of each row (device)
     const std::vector<int32_t> *lead_host;   // the same on the host
     // Optional (tensor-core variant): B-operand planes of the inverses of A's
-    // diagonal blocks (upper_leaf_inverses) and an A-operand scratch set of
-    // mrows x 128.  With both, a diagonal block is solved as X_J = C_J * A_JJ^-1
-    // on the tensor cores instead of by the multiline kernel.
+    // diagonal blocks of width tc_leaf (upper_leaf_inverses) and an A-operand
+    // scratch set of mrows x tc_leaf.  With both, a diagonal block is solved as
+    // X_J = C_J * A_JJ^-1 on the tensor cores instead of by the multiline kernel.
     const Planes *Zt;
     const Planes *Ct;
+    int tc_leaf;
 };
 int trsm_upper(const TrsmUpper &T);
 
-// B-operand planes (4 planes, 128 * ceil(npiv / 128) rows x 128) of the
-// inverses of the unit upper triangular diagonal blocks A[J, J] of A (dense
-// uint16, lda): row 128 q + j, column k of Zt holds (A_JJ^-1)[k][j] for block
-// J = [128 q, 128 q + 128), zero outside the block.
-int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, const Planes &Zt, const ModP &mp,
+// B-operand planes (4 planes, L * ceil(npiv / L) rows x L) of the inverses of
+// the unit upper triangular diagonal blocks A[J, J] of width L (a power of two,
+// multiple of 128) of A (dense uint16, lda): row L q + j, column k of Zt holds
+// (A_JJ^-1)[k][j] for block J = [L q, L q + L), zero outside A.
+int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
                         cudaStream_t s);
 
 // X' * A^T = C' (A^T unit lower triangular), X' overwrites C'.
