@@ -336,6 +336,29 @@ struct Timer {
     }
 };
 
+// A second stream (and a fork/join event pair) per host thread, for work of
+// one reduction that can overlap its main stream.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int dev = -1;
+    bool get() {
+        int d = 0;
+        if (cudaGetDevice(&d) != cudaSuccess) return false;
+        if (s && dev == d) return true;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            s = nullptr;
+            return false;
+        }
+        dev = d;
+        return true;
+    }
+};
+static thread_local SideStream g_side;
+
 // Column width of the tensor-core leaf solves of C*A^-1 (env GBLA_TRSM_LEAF
 // overrides: 128, 256, 512 or 1024).  Wider leaves mean fewer, larger products
 // and two fewer levels of small block updates, for a little more product work.
@@ -392,6 +415,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     DevCSR dc;
     std::vector<int32_t> lead_h;
     double schur_ops = 0;
+    bool side_pending = false;   // work on g_side.s not yet joined into s
 
 #define STEP(expr)                 \
     do {                           \
@@ -456,6 +480,21 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         CSTEP(cudaMemsetAsync(D16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldd, s));
     }
     STEP(split_scatter(dc, pi, A16, ldc, B16, ldd, C16, ldc, D16, ldd, mp, s));
+    if (m_cd > 0 && npiv > 0 && tc_leaves) {
+        // inverses of A's diagonal blocks for the tensor-core leaf solves, on
+        // the side stream while the main stream converts A and B
+        STEP(planes_alloc(&Zt, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
+        if (g_side.get()) {
+            CSTEP(cudaEventRecord(g_side.fork, s));
+            CSTEP(cudaStreamWaitEvent(g_side.s, g_side.fork, 0));
+            side_pending = true;
+            rc = upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, g_side.s);
+            CSTEP(cudaEventRecord(g_side.join, g_side.s));
+            STEP(rc);
+        } else {
+            STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, s));
+        }
+    }
     // digit planes of the operands the products read
     if (m_cd > 0 && npiv > 0) {
         // A^T: B-operand of C <- C - X*A.  The triangular solve reads it only
@@ -463,11 +502,6 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         // entirely above the diagonal are not converted.
         STEP(planes_alloc(&At, npiv, npiv, 4, s));
         STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s, nullptr, true));
-        if (tc_leaves) {
-            // inverses of A's diagonal blocks for the tensor-core leaf solves
-            STEP(planes_alloc(&Zt, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
-            STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, s));
-        }
     }
     if (m_cd > 0 && n_d > 0 && npiv > 0) {
         STEP(planes_alloc(&Bt, n_d, npiv, 4, s));    // B^T: B-operand of D <- D - X*B
@@ -480,6 +514,10 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         dim3 grid((unsigned)((n_d + 31) / 32), (unsigned)((npiv + 31) / 32));
         transpose_u16_kernel<<<grid, dim3(32, 8), 0, s>>>(B16, ldd, npiv, n_d, Bt16, ldbt);
         CSTEP(launch_check());
+    }
+    if (side_pending) {
+        CSTEP(cudaStreamWaitEvent(s, g_side.join, 0));
+        side_pending = false;
     }
     dfree(A16, s);
     dfree(B16, s);
@@ -653,6 +691,10 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     }
 
 cleanup:
+    if (side_pending) {   // nothing the side stream uses may be freed before it is done
+        cudaStreamSynchronize(g_side.s);
+        cudaGetLastError();
+    }
     dfree(err, s);
     dfree(d_rp, s);
     dfree(d_col, s);
