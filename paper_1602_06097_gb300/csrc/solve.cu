@@ -669,8 +669,8 @@ __global__ void __launch_bounds__(256) gather_t_planes_kernel(Planes dst, const 
 // A-operand planes of the candidates' entries at their panel's pivot columns:
 // row r - row_base of dst = D[cand[r]][128 slot + pc_j] for j < t (zero for
 // rows that are pivots now).  blockIdx.y = job of the chunk.
-__global__ void gather_h_planes_kernel(Planes dst, const uint16_t *__restrict__ D, int64_t ldd,
-                                       const int64_t *__restrict__ seg, const int32_t *__restrict__ cand,
+__global__ void gather_h_planes_kernel(Planes dst, uint16_t *__restrict__ H16, const uint16_t *__restrict__ D,
+                                       int64_t ldd, const int64_t *__restrict__ seg, const int32_t *__restrict__ cand,
                                        const int32_t *__restrict__ job_slot, int job0, int64_t row_base,
                                        const int32_t *__restrict__ pc_slot, const int32_t *__restrict__ t_slot,
                                        const int32_t *__restrict__ is_piv_row, uint32_t p)
@@ -689,15 +689,41 @@ __global__ void gather_h_planes_kernel(Planes dst, const uint16_t *__restrict__ 
         digits(a, p, hi, lo);
         *dst.at(0, r - row_base, j) = i2bf(hi);
         *dst.at(1, r - row_base, j) = i2bf(lo);
+        H16[(r - row_base) * PANEL + j] = (uint16_t)a;
     }
 }
 
-// Problem tables of the two grouped products of a chunk (one thread).
-// mode 1: D[S] += (G - I) * D[S];  mode 2: D[cand] -= H * D[S].
+// B-operand planes of (G - I)^T for the jobs of a chunk: row q * 128 + j,
+// column k <- (G - I)[k][j] of the slot's Gm (blockIdx.y = q, blockIdx.x = j).
+__global__ void gather_gmt_planes_kernel(Planes dst, const uint16_t *__restrict__ Gm_all,
+                                         const PanelPlan *__restrict__ plan, ModP mp)
+{
+    const int q = blockIdx.y, j = blockIdx.x, k = threadIdx.x;
+    const uint32_t a = Gm_all[(int64_t)plan[q].slot * PANEL * PANEL + k * PANEL + j];
+    const int64_t row = (int64_t)q * PANEL + j;
+    int hi, lo;
+    digits(a, mp.p, hi, lo);
+    *dst.at(0, row, k) = i2bf(hi);
+    *dst.at(1, row, k) = i2bf(lo);
+    digits(mod32(a * mp.r256, mp), mp.p, hi, lo);
+    *dst.at(2, row, k) = i2bf(hi);
+    *dst.at(3, row, k) = i2bf(lo);
+}
+
+__global__ void iota_kernel(int32_t *v, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)i;
+}
+
+// Problem tables of the grouped products of a chunk (one thread).
+// mode 1: D[S] += (G - I) * D[S];  mode 2: D[cand] -= (H G) * D[S]_old;
+// mode 3: H16 += H * (G - I), i.e. H16 <- H G, where H = D[cand, pc].
 __global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const PanelPlan *__restrict__ plan,
                                   const int32_t *__restrict__ t_slot, const int32_t *__restrict__ S_slot,
                                   const int32_t *__restrict__ wave_slot, const int64_t *__restrict__ seg,
-                                  const int32_t *__restrict__ cand, int job0, int64_t row_base)
+                                  const int32_t *__restrict__ cand, int job0, int64_t row_base,
+                                  const int32_t *__restrict__ iota)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int64_t off = 0;
@@ -713,6 +739,15 @@ __global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const P
             P.a_row0 = q * PANEL;
             P.M = wave_slot[2 * pl.slot] > 0 ? t : 0;
             P.c_rows = S_slot + (int64_t)pl.slot * PANEL;
+        } else if (mode == 3) {
+            // H G = H when G = I; nothing needed without dependent candidates
+            const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
+            P.a_row0 = (int32_t)(b - row_base);
+            P.b_row0 = q * PANEL;
+            P.N = t;
+            P.c_col0 = 0;
+            P.M = (wave_slot[2 * pl.slot] > 0 && wave_slot[2 * pl.slot + 1] > 0) ? (int32_t)(e - b) : 0;
+            P.c_rows = iota + (b - row_base);
         } else {
             // no dependent candidate: nothing to clear
             const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
@@ -1051,7 +1086,9 @@ struct PanelWork {
     int32_t *lead;
     PanelPlan *plan_dev;
     GroupProb *probs;
-    Planes Gp, Bs, H;
+    Planes Gp, Bs, H, GmT;
+    uint16_t *H16;    // multipliers H = D[cand, pc], then H G (rows as in H)
+    int32_t *iota;    // 0, 1, 2, .. (row maps of the H G products)
 };
 
 static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<PanelPlan> &plan, const int64_t *seg,
@@ -1064,25 +1101,35 @@ static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<Panel
     int64_t ncmax = 0;
     for (const auto &pl : plan) ncmax = pl.nc > ncmax ? pl.nc : ncmax;
     GBLA_CUDA_TRY(cudaMemcpyAsync(W.plan_dev, plan.data(), sizeof(PanelPlan) * (size_t)nj, cudaMemcpyHostToDevice, s));
-    // G - I of the jobs' slots as the A operand (rows q * 128 ..)
+    // G - I of the jobs' slots as the A operand (rows q * 128 ..), and D[S]^T
+    // as the B operand, converted once: both products below read D[S] as it
+    // is before the first one updates it.
     gather_gm_planes_kernel<<<dim3(PANEL, (unsigned)nj), PANEL, 0, s>>>(W.Gp, W.Gm_all, W.plan_dev, mp.p);
     GBLA_CUDA_TRY(launch_check());
     dim3 gt((unsigned)(round_up(ncmax, 128) / TP_TILE), PANEL / TP_TILE, (unsigned)nj);
     gather_t_planes_kernel<<<gt, 256, 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp);
     GBLA_CUDA_TRY(launch_check());
-    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
-                                       row_base);
-    GBLA_CUDA_TRY(launch_check());
-    GBLA_TRY(modgemm_grouped(W.Gp, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, +1, mp, E.variant, E.err, s, E.ctr));
-    // D[cand] -= D[cand, pc] * D[S]   (the pivot rows have zero multipliers)
-    gather_t_planes_kernel<<<gt, 256, 0, s>>>(W.Bs, E.D16, E.ldd, W.plan_dev, W.S_slot, W.t_slot, mp);
-    GBLA_CUDA_TRY(launch_check());
+    // H = D[cand, pc] (zero for rows that are pivots now), as planes and u16
     const unsigned rows_blocks = (unsigned)(rows_max < 64 ? (rows_max > 0 ? rows_max : 1) : 64);
     gather_h_planes_kernel<<<dim3(rows_blocks, (unsigned)nj), PANEL, 0, s>>>(
-        W.H, E.D16, E.ldd, seg, cand, job_slot, job0, row_base, W.pc_slot, W.t_slot, E.is_piv_row, mp.p);
+        W.H, W.H16, E.D16, E.ldd, seg, cand, job_slot, job0, row_base, W.pc_slot, W.t_slot, E.is_piv_row, mp.p);
     GBLA_CUDA_TRY(launch_check());
+    gather_gmt_planes_kernel<<<dim3(PANEL, (unsigned)nj), PANEL, 0, s>>>(W.GmT, W.Gm_all, W.plan_dev, mp);
+    GBLA_CUDA_TRY(launch_check());
+    // D[S] += (G - I) * D[S]
+    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
+                                       row_base, W.iota);
+    GBLA_CUDA_TRY(launch_check());
+    GBLA_TRY(modgemm_grouped(W.Gp, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, +1, mp, E.variant, E.err, s, E.ctr));
+    // H G = H + H (G - I), then its planes replace those of H
+    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 3, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
+                                       row_base, W.iota);
+    GBLA_CUDA_TRY(launch_check());
+    GBLA_TRY(modgemm_grouped(W.H, W.GmT, W.probs, nj, PANEL, W.H16, PANEL, +1, mp, E.variant, E.err, s, E.ctr));
+    GBLA_TRY(to_planes(W.H, W.H.rows, PANEL, W.H16, PANEL, 0, false, nullptr, nullptr, mp, s));
+    // D[cand] -= (H G) * D[S]_old  (= H * D[S]_new; pivot rows have zero multipliers)
     make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 2, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
-                                       row_base);
+                                       row_base, W.iota);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(modgemm_grouped(W.H, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, -1, mp, E.variant, E.err, s, E.ctr));
     return GBLA_OK;
@@ -1139,6 +1186,11 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         ESTEP(planes_alloc(&W.Bs, BS_ROWS + n, PANEL, 4, s));
         ESTEP(planes_alloc(&W.Gp, npan * PANEL, PANEL, 2, s));
         ESTEP(planes_alloc(&W.H, m + PANEL, PANEL, 2, s));
+        ESTEP(planes_alloc(&W.GmT, npan * PANEL, PANEL, 4, s));
+        ESTEP(dalloc_t(&W.H16, (size_t)W.H.rows * PANEL, s));
+        ESTEP(dalloc_t(&W.iota, (size_t)W.H.rows, s));
+        iota_kernel<<<(unsigned)((W.H.rows + 255) / 256), 256, 0, s>>>(W.iota, W.H.rows);
+        ECUDA(launch_check());
         ECUDA(cudaMemsetAsync(E.is_piv_row, 0, sizeof(int32_t) * (size_t)m, s));
         ECUDA(cudaMemsetAsync(W.t_slot, 0, sizeof(int32_t) * (size_t)(npan + 1), s));
         inverse_table_kernel<<<(mp.p + 255) / 256, 256, 0, s>>>(inv_tab, mp);
@@ -1275,6 +1327,9 @@ done:
     planes_free(&W.Bs, s);
     planes_free(&W.Gp, s);
     planes_free(&W.H, s);
+    planes_free(&W.GmT, s);
+    dfree(W.H16, s);
+    dfree(W.iota, s);
     *rank_out = rank;
     return rc;
 }
