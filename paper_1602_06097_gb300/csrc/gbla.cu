@@ -372,6 +372,18 @@ static int trsm_leaf_width() {
     return v;
 }
 
+// Row width of the leaves of the back-substitution of the echelon form (env
+// GBLA_BACK_LEAF overrides: 128, 256, 512 or 1024).
+static int back_leaf_width() {
+    static int v = 0;
+    if (v == 0) {
+        const char *e = getenv("GBLA_BACK_LEAF");
+        const int x = e ? atoi(e) : 0;
+        v = (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 512;
+    }
+    return v;
+}
+
 int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
                 int64_t *rank_out, gbla_stats *stats) {
     const int want_reduced = opt ? opt->want_reduced : 0;
@@ -555,7 +567,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     STEP(dalloc_t(&pcol, (size_t)m_cd + 1, s));
     {
         EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, variant, err, s, &ctr,
-                   tm.on ? tm.ev[7] : nullptr};
+                   tm.on ? tm.ev[7] : nullptr, back_leaf_width()};
         NvtxRange r("gbla.echelon");
         STEP(echelon_d(E, &rank_d));
     }

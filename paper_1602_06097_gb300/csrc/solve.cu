@@ -780,11 +780,6 @@ __global__ void compact_slots_kernel(int64_t npan, const int32_t *__restrict__ t
     *rank = r;
 }
 
-// For every diagonal block b of 128 rows: Nm_b = I - T^-1 with
-// T = R[rows[lo + i]][pcol[lo + j]], lo = 128 b (w x w, unit upper
-// triangular).  The back-substitution never modifies the pivot columns, so
-// these blocks are final from the start and all inverses are formed in one
-// launch.
 // Z = T^-1 for the unit upper triangular w x w block T (shared memory), by
 // rows from the bottom: Z[i][j] = d_ij - sum_{i<k<=j} T[i][k] Z[k][j].  Thread
 // j owns column j; rows and columns w.. of Z are left untouched.
@@ -804,41 +799,22 @@ __device__ __forceinline__ void unit_upper_inverse(const uint16_t (*T)[129], uin
     }
 }
 
-__global__ void __launch_bounds__(128) leaf_inverse_kernel(const uint16_t *__restrict__ R, int64_t ldr,
-                                                           const int32_t *__restrict__ rows, int64_t rank,
-                                                           const int32_t *__restrict__ pcol,
-                                                           uint16_t *__restrict__ Nm_all, ModP mp)
-{
-    const int64_t lo = (int64_t)blockIdx.x * 128;
-    const int w = (int)((rank - lo) < 128 ? (rank - lo) : 128);
-    uint16_t *Nm = Nm_all + (size_t)blockIdx.x * PANEL * PANEL;
-    extern __shared__ uint16_t inv_smem[];
-    uint16_t(*T)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem);             // [128][129]
-    uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem + 128 * 129);  // [128][129]
-    const int j = threadIdx.x;
-    for (int i = 0; i < w; ++i)
-        T[i][j] = (j < w) ? R[(int64_t)rows[lo + i] * ldr + pcol[lo + j]] : 0;
-    __syncthreads();
-    unit_upper_inverse(T, Z, w, mp);
-    for (int i = 0; i < w; ++i)
-        if (j < PANEL) {
-            uint32_t z = (j < w) ? Z[i][j] : 0u;
-            uint32_t v = ((i == j) ? 1u : 0u) + mp.p - z;
-            Nm[i * PANEL + j] = (uint16_t)(v % mp.p);
-        }
-}
-
-// Inverses of A's diagonal blocks of width L (a multiple of 128), for the
-// tensor-core leaf solves X_J = C_J * A_JJ^-1.  Z_J = A_JJ^-1 is built in ZN
-// (u16, row-major, leaf J at rows J L .. J L + L, row length L, zero outside
-// the upper triangle and outside A):
+// Inverses of the diagonal blocks of width L (a power of two, multiple of
+// 128) of a unit upper triangular n x n matrix T, given as T[i][j] =
+// A[r(i) * lda + c(j)] with r, c optional row / column maps (identity when
+// null): A itself for the leaf solves X_J = C_J * A_JJ^-1, the echelon rows
+// at the pivot columns for the back-substitution.  Z_J = T_JJ^-1 is built in
+// ZN (u16, row-major, leaf J at rows J L .. J L + L, row length L, zero
+// outside the upper triangle and outside T):
 //   1. the 128-blocks on the diagonal, inverted in shared memory;
 //   2. for w = 128, 256, .. < L, every pair of neighbouring w-blocks (o1, o2 =
 //      o1 + w) of a leaf gets its upper-right block from the block inverse
 //      formula  Z12 = -Z11 * A12 * Z22  (two batched products);
 //   3. the B-operand planes of Z_J^T (row J L + j, column k <- Z_J[k][j]).
 __global__ void __launch_bounds__(128) upper_inverse128_kernel(const uint16_t *__restrict__ A, int64_t lda,
-                                                               int64_t npiv, int L, uint16_t *__restrict__ ZN, ModP mp)
+                                                               const int32_t *__restrict__ rmap,
+                                                               const int32_t *__restrict__ cmap, int64_t npiv, int L,
+                                                               uint16_t *__restrict__ ZN, ModP mp)
 {
     const int64_t lo = (int64_t)blockIdx.x * 128;
     const int w = (int)((npiv - lo) < 128 ? (npiv - lo) : 128);
@@ -846,8 +822,9 @@ __global__ void __launch_bounds__(128) upper_inverse128_kernel(const uint16_t *_
     uint16_t(*T)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem);
     uint16_t(*Z)[129] = reinterpret_cast<uint16_t(*)[129]>(inv_smem + 128 * 129);
     const int j = threadIdx.x;
+    const int64_t cj = (j < w) ? (cmap ? (int64_t)cmap[lo + j] : lo + j) : 0;
     for (int i = 0; i < w; ++i)
-        T[i][j] = (j < w) ? A[(lo + i) * lda + lo + j] : 0;
+        T[i][j] = (j < w) ? A[(rmap ? (int64_t)rmap[lo + i] : lo + i) * lda + cj] : 0;
     __syncthreads();
     unit_upper_inverse(T, Z, w, mp);
     // lo = J L + o: rows lo + k of ZN, columns o + j
@@ -860,8 +837,10 @@ __global__ void __launch_bounds__(128) upper_inverse128_kernel(const uint16_t *_
 // (blockIdx.z = pair; 64 x 64 output tile per CTA, exact uint64 sums):
 //   mode 0: T1_b = A[lo+o1.., lo+o2..] * Z22,   mode 1: Z12 = -Z11 * T1_b.
 __global__ void __launch_bounds__(256) tri_combine_kernel(int mode, int w, int L, const uint16_t *__restrict__ A,
-                                                          int64_t lda, int64_t npiv, uint16_t *__restrict__ ZN,
-                                                          uint16_t *__restrict__ T1, ModP mp)
+                                                          int64_t lda, const int32_t *__restrict__ rmap,
+                                                          const int32_t *__restrict__ cmap, int64_t npiv,
+                                                          uint16_t *__restrict__ ZN, uint16_t *__restrict__ T1,
+                                                          ModP mp)
 {
     __shared__ uint32_t sx[64][33];
     __shared__ uint32_t sy[32][65];
@@ -883,7 +862,9 @@ __global__ void __launch_bounds__(256) tri_combine_kernel(int mode, int w, int L
             uint32_t v;
             if (mode == 0) {
                 const int64_t ar = lo + o1 + i0 + r, ac = lo + o2 + k0 + k;
-                v = (ar < npiv && ac < npiv) ? A[ar * lda + ac] : 0u;
+                v = (ar < npiv && ac < npiv)
+                        ? A[(rmap ? (int64_t)rmap[ar] : ar) * lda + (cmap ? (int64_t)cmap[ac] : ac)]
+                        : 0u;
             } else {
                 v = ZN[(lo + o1 + i0 + r) * L + o1 + k0 + k];
             }
@@ -930,44 +911,66 @@ __global__ void __launch_bounds__(256) zt_planes_kernel(const uint16_t *__restri
 
 constexpr int LEAF_INV_SMEM = 2 * 128 * 129 * (int)sizeof(uint16_t);
 
-int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
-                        cudaStream_t s)
+// ZN (nleaves L x L, allocated by the caller) <- the block inverses Z_J.
+static int block_inverses(const uint16_t *A, int64_t lda, const int32_t *rmap, const int32_t *cmap, int64_t n, int L,
+                          uint16_t *ZN, const ModP &mp, cudaStream_t s)
 {
-    if (npiv <= 0) return GBLA_OK;
     if (L < 128 || L % 128 || (L & (L - 1)) != 0) return GBLA_E_INTERNAL;
-    const int64_t nleaves = (npiv + L - 1) / L;
-    if (Zt.nplanes != 4 || Zt.kp != L || Zt.rows < nleaves * L) return GBLA_E_INTERNAL;
+    const int64_t nleaves = (n + L - 1) / L;
     static bool attr = false;
     if (!attr) {
         GBLA_CUDA_TRY(cudaFuncSetAttribute(upper_inverse128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            LEAF_INV_SMEM));
         attr = true;
     }
-    uint16_t *ZN = nullptr, *T1 = nullptr;
-    int rc = dalloc_t(&ZN, (size_t)nleaves * L * L, s);
-    if (rc == GBLA_OK) rc = dalloc_t(&T1, (size_t)nleaves * L * L / 4 + 1, s);
+    uint16_t *T1 = nullptr;
+    int rc = dalloc_t(&T1, (size_t)nleaves * L * L / 4 + 1, s);
     if (rc == GBLA_OK && cudaMemsetAsync(ZN, 0, sizeof(uint16_t) * (size_t)nleaves * L * L, s) != cudaSuccess)
         rc = GBLA_E_CUDA;
     if (rc == GBLA_OK) {
-        upper_inverse128_kernel<<<(unsigned)((npiv + 127) / 128), 128, LEAF_INV_SMEM, s>>>(A16, lda, npiv, L, ZN, mp);
+        upper_inverse128_kernel<<<(unsigned)((n + 127) / 128), 128, LEAF_INV_SMEM, s>>>(A, lda, rmap, cmap, n, L, ZN,
+                                                                                        mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
     for (int w = 128; rc == GBLA_OK && w < L; w *= 2) {
         const dim3 grid((unsigned)(w / 64), (unsigned)(w / 64), (unsigned)(nleaves * (L / (2 * w))));
-        tri_combine_kernel<<<grid, 256, 0, s>>>(0, w, L, A16, lda, npiv, ZN, T1, mp);
+        tri_combine_kernel<<<grid, 256, 0, s>>>(0, w, L, A, lda, rmap, cmap, n, ZN, T1, mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         if (rc != GBLA_OK) break;
-        tri_combine_kernel<<<grid, 256, 0, s>>>(1, w, L, A16, lda, npiv, ZN, T1, mp);
+        tri_combine_kernel<<<grid, 256, 0, s>>>(1, w, L, A, lda, rmap, cmap, n, ZN, T1, mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
+    dfree(T1, s);
+    return rc;
+}
+
+int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
+                        cudaStream_t s)
+{
+    if (npiv <= 0) return GBLA_OK;
+    const int64_t nleaves = (npiv + L - 1) / L;
+    if (Zt.nplanes != 4 || Zt.kp != L || Zt.rows < nleaves * L) return GBLA_E_INTERNAL;
+    uint16_t *ZN = nullptr;
+    int rc = dalloc_t(&ZN, (size_t)nleaves * L * L, s);
+    if (rc == GBLA_OK) rc = block_inverses(A16, lda, nullptr, nullptr, npiv, L, ZN, mp, s);
     if (rc == GBLA_OK) {
         zt_planes_kernel<<<dim3((unsigned)(L / TP_TILE), (unsigned)(L / TP_TILE), (unsigned)nleaves), 256, 0, s>>>(
             ZN, L, Zt, mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
     dfree(ZN, s);
-    dfree(T1, s);
     return rc;
+}
+
+// Nm = I - Z elementwise (u16, n_total elements of L x L blocks).
+__global__ void i_minus_kernel(uint16_t *__restrict__ Z, int L, int64_t total, uint32_t p)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t i = (e / L) % L, j = e % L;
+    const uint32_t z = Z[e];
+    const uint32_t v = (i == j ? 1u : 0u) + p - z;
+    Z[e] = (uint16_t)(v >= p ? v - p : v);
 }
 
 
@@ -1052,29 +1055,30 @@ __global__ void expand_rref_kernel(const uint16_t *__restrict__ Rnp, int64_t ldn
 // pcol[lo], i.e. left of non-pivot column pcol[lo] - lo.
 static int backsub_rec(const EchelonD &E, uint16_t *Rnp, int64_t ldnp, int64_t nnp, const int32_t *pcol_dev,
                        const std::vector<int32_t> &pcol, int64_t lo, int64_t hi, Planes &Ap, Planes &RT,
-                       const uint16_t *Nm_all)
+                       const uint16_t *Nm_all, int BL)
 {
     const ModP &mp = *E.mp;
     cudaStream_t s = E.s;
-    if (hi - lo <= PANEL) {
-        // leaves are the 128-row blocks (splits fall on multiples of 128)
+    if (hi - lo <= BL) {
+        // leaves are the BL-row blocks (splits fall on multiples of BL):
+        // Rnp_J <- Rnp_J - (I - T_JJ^-1) Rnp_J
         const int w = (int)(hi - lo);
         const int64_t cs = (pcol[lo] - lo) & ~int64_t(63);
-        const uint16_t *Nm = Nm_all + (size_t)(lo / PANEL) * PANEL * PANEL;
-        GBLA_TRY(to_planes(Ap, w, w, Nm, PANEL, 0, false, nullptr, nullptr, mp, s));
+        const uint16_t *Nm = Nm_all + (size_t)(lo / BL) * BL * BL;
+        GBLA_TRY(to_planes(Ap, w, w, Nm, BL, 0, false, nullptr, nullptr, mp, s));
         GBLA_TRY(to_planes(RT, nnp, w, Rnp + lo * ldnp, ldnp, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo));
         GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, lo, Rnp + lo * ldnp + cs, ldnp, w, nnp - cs, w, -1, mp, E.variant, E.err,
                          s, E.ctr));
         return to_planes(RT, nnp, w, Rnp + lo * ldnp, ldnp, 0, true, nullptr, nullptr, mp, s, nullptr, false, lo);
     }
-    const int64_t mid = lo + round_up((hi - lo) / 2, PANEL);
-    GBLA_TRY(backsub_rec(E, Rnp, ldnp, nnp, pcol_dev, pcol, mid, hi, Ap, RT, Nm_all));
+    const int64_t mid = lo + round_up((hi - lo) / 2, BL);
+    GBLA_TRY(backsub_rec(E, Rnp, ldnp, nnp, pcol_dev, pcol, mid, hi, Ap, RT, Nm_all, BL));
     // Rnp[lo:mid] -= T[lo:mid, mid:hi] * Rnp[mid:hi]
     const int64_t cs = (pcol[mid] - mid) & ~int64_t(63);
     GBLA_TRY(to_planes(Ap, mid - lo, hi - mid, E.D16, E.ldd, 0, false, E.prow + lo, pcol_dev + mid, mp, s));
     GBLA_TRY(modgemm(Ap, 0, 0, RT, cs, mid, Rnp + lo * ldnp + cs, ldnp, mid - lo, nnp - cs, hi - mid, -1, mp,
                      E.variant, E.err, s, E.ctr));
-    return backsub_rec(E, Rnp, ldnp, nnp, pcol_dev, pcol, lo, mid, Ap, RT, Nm_all);
+    return backsub_rec(E, Rnp, ldnp, nnp, pcol_dev, pcol, lo, mid, Ap, RT, Nm_all, BL);
 }
 
 // Apply the panel bases of jobs [job0, job0 + njobs) (slots given by
@@ -1154,8 +1158,6 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     static bool attr = false;
     if (!attr) {
         GBLA_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM));
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(leaf_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           LEAF_INV_SMEM));
         attr = true;
     }
 #define ESTEP(expr)                         \
@@ -1284,16 +1286,19 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
         if (rc == GBLA_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
-        const int64_t nleaves = (rank + PANEL - 1) / PANEL;
-        if (rc == GBLA_OK && nnp > 0) rc = dalloc_t(&Nm, (size_t)nleaves * PANEL * PANEL, s);
+        // leaves of BL rows: the inverses of T's diagonal BL-blocks in one go
+        const int BL = E.back_leaf > 0 ? E.back_leaf : PANEL;
+        const int64_t nleaves = (rank + BL - 1) / BL;
+        if (rc == GBLA_OK && nnp > 0) rc = dalloc_t(&Nm, (size_t)nleaves * BL * BL, s);
+        if (rc == GBLA_OK && nnp > 0) rc = block_inverses(E.D16, E.ldd, E.prow, E.pcol, rank, BL, Nm, mp, s);
         if (rc == GBLA_OK && nnp > 0) {
-            leaf_inverse_kernel<<<(unsigned)nleaves, 128, LEAF_INV_SMEM, s>>>(E.D16, E.ldd, E.prow, rank, E.pcol, Nm,
-                                                                                mp);
+            const int64_t total = nleaves * BL * BL;
+            i_minus_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Nm, BL, total, mp.p);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
-        if (rc == GBLA_OK && nnp > 0) rc = planes_alloc(&Ap, rank, rank < 2 * PANEL ? PANEL : rank, 2, s);
+        if (rc == GBLA_OK && nnp > 0) rc = planes_alloc(&Ap, rank, rank, 2, s);   // K up to a leaf or half the rows
         if (rc == GBLA_OK && nnp > 0) rc = planes_alloc(&Bp, nnp, rank, 4, s);   // Rnp^T
-        if (rc == GBLA_OK && nnp > 0) rc = backsub_rec(E, Rnp, ldnp, nnp, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm);
+        if (rc == GBLA_OK && nnp > 0) rc = backsub_rec(E, Rnp, ldnp, nnp, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm, BL);
         if (rc == GBLA_OK) {
             expand_rref_kernel<<<rgrid, 256, 0, s>>>(Rnp, ldnp, colmap, rank, n, E.R[0], ldr);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;

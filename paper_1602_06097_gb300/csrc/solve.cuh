@@ -73,6 +73,7 @@ struct EchelonD {
     cudaStream_t s;
     GemmCounters *ctr;
     cudaEvent_t back_start = nullptr;   // optional: recorded when the backward pass begins
+    int back_leaf = 0;                  // leaf rows of the back-substitution (power of two >= 128; 0: 128)
 };
 int echelon_d(const EchelonD &E, int64_t *rank_out);
 
