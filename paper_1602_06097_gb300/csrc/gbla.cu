@@ -456,8 +456,25 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         STEP(dalloc_t(&d_val, (size_t)nnz + 1, s));
         if (m > 0) CSTEP(cudaMemcpyAsync(d_rp, in->row_ptr, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyHostToDevice, s));
         if (nnz > 0) {
-            CSTEP(cudaMemcpyAsync(d_col, in->col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
-            CSTEP(cudaMemcpyAsync(d_val, in->val, sizeof(uint16_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+            // two copy streams: the values and the first quarter of the
+            // columns on the side stream, the rest of the columns here
+            const int64_t c0 = g_side.get() ? nnz / 4 : 0;
+            if (c0 > 0) {
+                CSTEP(cudaEventRecord(g_side.fork, s));
+                CSTEP(cudaStreamWaitEvent(g_side.s, g_side.fork, 0));
+                side_pending = true;
+                CSTEP(cudaMemcpyAsync(d_val, in->val, sizeof(uint16_t) * (size_t)nnz, cudaMemcpyHostToDevice, g_side.s));
+                CSTEP(cudaMemcpyAsync(d_col, in->col, sizeof(int32_t) * (size_t)c0, cudaMemcpyHostToDevice, g_side.s));
+                CSTEP(cudaEventRecord(g_side.join, g_side.s));
+            } else {
+                CSTEP(cudaMemcpyAsync(d_val, in->val, sizeof(uint16_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+            }
+            CSTEP(cudaMemcpyAsync(d_col + c0, in->col + c0, sizeof(int32_t) * (size_t)(nnz - c0), cudaMemcpyHostToDevice,
+                                  s));
+            if (side_pending) {
+                CSTEP(cudaStreamWaitEvent(s, g_side.join, 0));
+                side_pending = false;
+            }
         }
         dc.row_ptr = d_rp;
         dc.col = d_col;
@@ -664,8 +681,26 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             if (!out->row_ptr || !out->col || !out->val) { rc = GBLA_E_NOMEM; goto cleanup; }
             CSTEP(cudaMemcpyAsync(out->row_ptr, orp, sizeof(int64_t) * (size_t)(rank + 1), cudaMemcpyDeviceToHost, s));
             if (onnz > 0) {
-                CSTEP(cudaMemcpyAsync(out->col, ocol, sizeof(int32_t) * (size_t)onnz, cudaMemcpyDeviceToHost, s));
-                CSTEP(cudaMemcpyAsync(out->val, oval, sizeof(uint16_t) * (size_t)onnz, cudaMemcpyDeviceToHost, s));
+                // two copy streams, as for the input
+                const int64_t c0 = g_side.get() ? onnz / 4 : 0;
+                if (c0 > 0) {
+                    CSTEP(cudaEventRecord(g_side.fork, s));
+                    CSTEP(cudaStreamWaitEvent(g_side.s, g_side.fork, 0));
+                    side_pending = true;
+                    CSTEP(cudaMemcpyAsync(out->val, oval, sizeof(uint16_t) * (size_t)onnz, cudaMemcpyDeviceToHost,
+                                          g_side.s));
+                    CSTEP(cudaMemcpyAsync(out->col, ocol, sizeof(int32_t) * (size_t)c0, cudaMemcpyDeviceToHost,
+                                          g_side.s));
+                    CSTEP(cudaEventRecord(g_side.join, g_side.s));
+                } else {
+                    CSTEP(cudaMemcpyAsync(out->val, oval, sizeof(uint16_t) * (size_t)onnz, cudaMemcpyDeviceToHost, s));
+                }
+                CSTEP(cudaMemcpyAsync(out->col + c0, ocol + c0, sizeof(int32_t) * (size_t)(onnz - c0),
+                                      cudaMemcpyDeviceToHost, s));
+                if (side_pending) {
+                    CSTEP(cudaStreamWaitEvent(s, g_side.join, 0));
+                    side_pending = false;
+                }
             }
         }
     }
