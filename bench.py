@@ -48,6 +48,10 @@ def args_parse():
     ap.add_argument("--want-reduced", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--extras", action="store_true", help="add the batched-vs-plain and serving measurements")
+    ap.add_argument("--batch", type=int, default=32, help="matrices in the batched-vs-plain measurement")
+    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (req/s)")
+    ap.add_argument("--serve-requests", type=int, default=160)
     return ap.parse_args()
 
 
@@ -204,6 +208,61 @@ def config_of(spec, a):
             "input": "resident in HBM"}
 
 
+BATCH_SEED = 20160223   # batched / serving mix
+
+
+def batched_vs_plain(gbla, synth, count):
+    """A batch of F4-shaped matrices of uneven sizes (rows log-uniform in
+    500-20,000, columns 1.3-1.6 x rows, 60-80% pivots, 1-5% density, p in
+    {65521, 32003}) reduced one call per matrix, then through the batch entry
+    point; host inputs and results, copies included in both."""
+    specs = synth.mixed_batch(count, BATCH_SEED)
+    mats = [synth.fl_matrix(sp) + ((sp.m, sp.n), sp.p) for sp in specs]
+    gbla.reduce_batch(mats[:4])                                   # warm-up
+    for rp, c, v, shape, p in mats[:4]:
+        gbla.reduce(rp, c, v, shape, p)
+    t0 = time.perf_counter()
+    plain = [gbla.reduce(rp, c, v, shape, p)[0] for rp, c, v, shape, p in mats]
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batched = [r[0] for r in gbla.reduce_batch(mats)]
+    t_batch = time.perf_counter() - t0
+    assert plain == batched, "batched ranks differ from one-at-a-time ranks"
+    nnz = int(sum(len(mt[1]) for mt in mats))
+    return mats, {"matrices": count, "rows": [int(min(sp.m for sp in specs)), int(max(sp.m for sp in specs))],
+                  "input_nnz": nnz, "plain_matrices_per_s": count / t_plain, "batched_matrices_per_s": count / t_batch,
+                  "speedup": t_plain / t_batch, "includes": "host inputs and results (H2D/D2H inside)"}
+
+
+def serving(gbla, mats, rate, nreq):
+    """Poisson arrivals (rate req/s) of requests drawn from the batch's
+    matrices, served by the request server with continuous batching; latency
+    from submit to result ready."""
+    rng = np.random.default_rng(BATCH_SEED)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    pick = rng.integers(0, len(mats), size=nreq)
+    with gbla.Server(workers=4) as srv:
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            rp, c, v, shape, p = mats[pick[i]]
+            tickets.append(srv.submit(rp, c, v, shape, p))
+        lat = []
+        for t in tickets:
+            code, _, ms = srv.wait(t, 120.0)
+            if code != 0:
+                raise RuntimeError(f"served request failed with code {code}")
+            lat.append(ms)
+        wall = time.perf_counter() - t0
+    lat = np.asarray(lat)
+    return {"rate_req_per_s": rate, "requests": nreq, "matrices_per_s": nreq / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "workers": 4}
+
+
 # --------------------------------------------------------------- GPU arm
 def main():
     a = args_parse()
@@ -306,6 +365,10 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
+    extras = {}
+    if world == 1 and a.extras:
+        mats, extras["batched"] = batched_vs_plain(gbla, synth, a.batch)
+        extras["serving"] = serving(gbla, mats, a.serve_rate, a.serve_requests)
     cpu = None
     if world == 1 and not a.no_cpu_baseline:
         cb = cpu_oracle_sample(rp, c, v, m, n, p, CPU_SAMPLE_ROWS)
@@ -331,6 +394,7 @@ def main():
                      "peak_kind": f"bf16 dense sustained, {kind}"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

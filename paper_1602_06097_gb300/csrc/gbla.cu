@@ -12,6 +12,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -67,8 +68,8 @@ void dfree(void *ptr, cudaStream_t s) {
 // Host results live in page-locked memory so that the device-to-host copy runs
 // at full link speed.  Pinning is expensive (the pages are locked one by one),
 // so released blocks are cached and handed to later results of a similar size;
-// at most GBLA_HOST_CACHE_MB (default 8192) megabytes stay cached.  Blocks
-// that cannot be pinned fall back to malloc.
+// at most GBLA_HOST_CACHE_MB (default 8192) megabytes stay cached.  A new
+// Blocks that cannot be pinned fall back to malloc.
 namespace {
 struct HostCache {
     std::mutex mu;
@@ -88,6 +89,58 @@ HostCache &host_cache() {
     return *c;
 }
 }  // namespace
+
+static std::atomic<int> g_active_reductions{0};
+
+// Readbacks of sizes, indices and status words go through a page-locked
+// buffer per host thread: a device-to-host copy into pageable memory is staged
+// by the driver and was measured to block for 20 s while another thread's
+// reduction ran (two batch workers); into page-locked memory it does not.
+struct Scratch {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+static thread_local Scratch g_scratch;
+
+int readback(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return GBLA_OK;
+    if (g_scratch.cap < bytes) {
+        size_t want = (size_t)1 << 20;
+        while (want < bytes) want <<= 1;
+        void *np = nullptr;
+        if (cudaHostAlloc(&np, want, cudaHostAllocDefault) == cudaSuccess) {
+            // freeing page-locked memory waits for an idle device: the
+            // outgrown buffer is kept while other reductions are in flight
+            if (g_scratch.p && g_active_reductions.load() <= 1) cudaFreeHost(g_scratch.p);
+            g_scratch.p = np;
+            g_scratch.cap = want;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (g_scratch.cap >= bytes) {
+        GBLA_CUDA_TRY(cudaMemcpyAsync(g_scratch.p, src, bytes, cudaMemcpyDeviceToHost, s));
+        GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+        memcpy(dst, g_scratch.p, bytes);
+    } else {   // no page-locked memory: copy directly
+        GBLA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return GBLA_OK;
+}
+
+struct ActiveReduction {
+    ActiveReduction() { ++g_active_reductions; }
+    ~ActiveReduction() { --g_active_reductions; }
+};
+
+// One reduction at a time runs its device work.  Two reductions whose
+// kernels overlapped on the GPU (batch workers, each on its own stream) were
+// measured to block each other for 40 s of device time in the triangular
+// solve and the echelonisation, with no error reported, where each alone
+// takes milliseconds; the cause has not been identified, so concurrent calls
+// are serialised here and overlap only their host-side work.
+static std::mutex g_device_mu;
 
 void *host_alloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -134,7 +187,9 @@ void host_release(void *ptr) {
         c.live.erase(c.live.begin() + (long)i);
         c.free_blocks.push_back(blk);
         c.cached += blk.second;
-        while (c.cached > c.cap && !c.free_blocks.empty()) {   // evict the oldest
+        // evict the oldest; freeing page-locked memory also waits for an idle
+        // device, so not while reductions are in flight
+        while (c.cached > c.cap && !c.free_blocks.empty() && g_active_reductions.load() == 0) {
             drop.push_back(c.free_blocks.front().first);
             c.cached -= c.free_blocks.front().second;
             c.free_blocks.erase(c.free_blocks.begin());
@@ -395,6 +450,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     if (m > 0 && !in->row_ptr) return GBLA_E_INVAL;
     if (nnz > 0 && (!in->col || !in->val)) return GBLA_E_INVAL;
     GBLA_TRY(check_device());
+    std::lock_guard<std::mutex> device_lock(g_device_mu);
+    const ActiveReduction active;
     const ModP mp = make_modp(p);
     // diagonal blocks of the triangular solve on the tensor cores too
     const bool tc_leaves =
@@ -561,8 +618,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         STEP(planes_alloc(&Xp, m_cd, npiv, 2, s));
         STEP(planes_zero(Xp, s));
         lead_h.resize((size_t)m_cd);
-        CSTEP(cudaMemcpyAsync(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, cudaMemcpyDeviceToHost, s));
-        CSTEP(cudaStreamSynchronize(s));
+        STEP(readback(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, s));
         if (tc_leaves) STEP(planes_alloc(&Ct, m_cd, tc_leaf_w, 2, s));
         TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr, pi.cd_lead, &lead_h,
                     tc_leaves ? &Zt : nullptr, tc_leaves ? &Ct : nullptr, tc_leaf_w};
@@ -642,8 +698,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         CSTEP(launch_check());
     }
     STEP(scan_i64(cnt, orp, rank, orp + rank, s));
-    CSTEP(cudaMemcpyAsync(&onnz, orp + rank, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CSTEP(cudaStreamSynchronize(s));
+    STEP(readback(&onnz, orp + rank, sizeof(int64_t), s));
     STEP(dalloc_t(&ocol, (size_t)onnz + 1, s));
     STEP(dalloc_t(&oval, (size_t)onnz + 1, s));
     if (npiv > 0) {
@@ -708,7 +763,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     CSTEP(cudaStreamSynchronize(s));
     {
         uint32_t herr = 0;
-        CSTEP(cudaMemcpy(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost));
+        STEP(readback(&herr, err, sizeof(herr), s));
         rc = map_dev_err(herr);
     }
     if (rc == GBLA_OK) {
@@ -863,7 +918,7 @@ int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t l
         if (rc == GBLA_OK) rc = modgemm(Ap, 0, 0, Bp, 0, 0, C, ldc, M, N, K, sign, mp, variant, err, s, nullptr);
         if (cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
         uint32_t herr = 0;
-        if (rc == GBLA_OK && cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost) == cudaSuccess) rc = map_dev_err(herr);
+        if (rc == GBLA_OK && readback(&herr, err, 4, s) == GBLA_OK) rc = map_dev_err(herr);
     }
     planes_free(&Ap, s);
     planes_free(&Bp, s);
@@ -881,7 +936,7 @@ int gbla_selftest_wait_timeout(void *stream) {
     if (rc == GBLA_OK) rc = modgemm_withheld_loads(err, s);
     uint32_t herr = 0;
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = GBLA_E_CUDA;
-    if (rc == GBLA_OK && cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK && readback(&herr, err, 4, s) != GBLA_OK) rc = GBLA_E_CUDA;
     dfree(err, s);
     cudaStreamSynchronize(s);
     if (rc != GBLA_OK) return rc;

@@ -33,6 +33,10 @@ bool tc_supported();
 
 // Product written as A-operand digit planes: Out[row, out_col0 + n] <- (A*B)[row, n]
 // mod p (tensor-core variant only).
+// Device-to-host copy of `bytes` into pageable host memory `dst` through a
+// page-locked scratch buffer of the calling thread; synchronises stream s.
+int readback(void *dst, const void *src, size_t bytes, cudaStream_t s);
+
 int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t b_row0, const Planes &Out,
                       int64_t out_col0, int64_t M, int64_t N, int64_t K, const ModP &mp, uint32_t *err,
                       cudaStream_t s, GemmCounters *ctr);

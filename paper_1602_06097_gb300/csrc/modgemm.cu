@@ -1092,8 +1092,7 @@ static int modgemm_grouped_simt(const Planes &A, const Planes &B, const GroupPro
                                 uint16_t *C, int64_t ldc, int sign, const ModP &mp, cudaStream_t s)
 {
     std::vector<GroupProb> h((size_t)nprob + 1);
-    GBLA_CUDA_TRY(cudaMemcpyAsync(h.data(), probs, sizeof(GroupProb) * h.size(), cudaMemcpyDeviceToHost, s));
-    GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+    GBLA_TRY(readback(h.data(), probs, sizeof(GroupProb) * h.size(), s));
     for (int i = 0; i < nprob; ++i) {
         const GroupProb &P = h[(size_t)i];
         if (P.M <= 0 || P.N <= 0) continue;

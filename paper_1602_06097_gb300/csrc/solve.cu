@@ -1222,11 +1222,10 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
             make_jobs_kernel<<<1, 1024, 0, s>>>(npan, off, job_slot, seg, info);
             ECUDA(launch_check());
             int32_t njobs = 0;
-            ECUDA(cudaMemcpyAsync(&njobs, info, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            ECUDA(cudaStreamSynchronize(s));
+            ESTEP(readback(&njobs, info, sizeof(int32_t), s));
             if (njobs == 0) break;
-            ECUDA(cudaMemcpyAsync(slots_h.data(), job_slot, sizeof(int32_t) * (size_t)njobs, cudaMemcpyDeviceToHost, s));
-            ECUDA(cudaMemcpyAsync(seg_h.data(), seg, sizeof(int64_t) * (size_t)(njobs + 1), cudaMemcpyDeviceToHost, s));
+            ESTEP(readback(slots_h.data(), job_slot, sizeof(int32_t) * (size_t)njobs, s));
+            ESTEP(readback(seg_h.data(), seg, sizeof(int64_t) * (size_t)(njobs + 1), s));
             panel_kernel<<<(unsigned)njobs, 2 * PANEL, PANEL_SMEM, s>>>(E.D16, E.ldd, n, seg, cand, job_slot, inv_tab,
                                                                       E.is_piv_row, W.t_slot, W.S_slot, W.pc_slot,
                                                                       W.Gm_all, W.wave_slot, mp);
@@ -1256,8 +1255,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         }
         compact_slots_kernel<<<1, 32, 0, s>>>(npan, W.t_slot, W.S_slot, W.pc_slot, E.prow, E.pcol, rank_dev);
         ECUDA(launch_check());
-        ECUDA(cudaMemcpyAsync(&rank, rank_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        ECUDA(cudaStreamSynchronize(s));
+        ESTEP(readback(&rank, rank_dev, sizeof(int64_t), s));
     }
     // ---- backward pass: RREF rows into R (pivot column order)
     if (E.back_start) cudaEventRecord(E.back_start, s);
@@ -1273,8 +1271,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         if (rc == GBLA_OK) rc = dalloc_t(&colmap, (size_t)n, s);
         if (rc == GBLA_OK) rc = dalloc_t(&npc, (size_t)(nnp > 0 ? nnp : 1), s);
         if (rc == GBLA_OK) rc = dalloc_t(&Rnp, (size_t)rank * (size_t)ldnp, s);
-        if (rc == GBLA_OK && cudaMemcpyAsync(pcol_h.data(), E.pcol, sizeof(int32_t) * (size_t)rank,
-                                             cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = GBLA_E_CUDA;
+        if (rc == GBLA_OK) rc = readback(pcol_h.data(), E.pcol, sizeof(int32_t) * (size_t)rank, s);
         if (rc == GBLA_OK) {
             colmap_np_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E.pcol, rank, n, colmap, npc);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;

@@ -261,11 +261,9 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
     }
     GBLA_TRY(scan_i64(rflag, rpos, m, pi->dev_counts + 1, s));
     int64_t host_counts[2] = {0, 0};
-    GBLA_CUDA_TRY(cudaMemcpyAsync(host_counts, pi->dev_counts, sizeof(host_counts), cudaMemcpyDeviceToHost, s));
-    GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+    GBLA_TRY(readback(host_counts, pi->dev_counts, sizeof(host_counts), s));
     uint32_t herr = 0;
-    GBLA_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
-    GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+    GBLA_TRY(readback(&herr, err, sizeof(herr), s));
     if (herr & DEV_ERR_INVAL) {
         dfree(cflag, s);
         dfree(rflag, s);
@@ -470,8 +468,7 @@ int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const 
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(scan_i64(ml->ptr, ml->ptr, npairs, ml->ptr + npairs, s));
     int64_t total = 0;
-    GBLA_CUDA_TRY(cudaMemcpyAsync(&total, ml->ptr + npairs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+    GBLA_TRY(readback(&total, ml->ptr + npairs, sizeof(int64_t), s));
     ml->total = total;
     GBLA_TRY(dalloc_t(&ml->pos, (size_t)total + 1, s));
     GBLA_TRY(dalloc_t(&ml->val, (size_t)total + 1, s));
@@ -531,8 +528,7 @@ int multiline_pairs(int64_t m, const int64_t *row_ptr, const int32_t *col, const
     multiline_pairs_kernel<<<nb, 128, 0, s>>>(npairs, m, row_ptr, col, val, ml_ptr_dev, nullptr, nullptr, 0);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(scan_i64(ml_ptr_dev, ml_ptr_dev, npairs, ml_ptr_dev + npairs, s));
-    GBLA_CUDA_TRY(cudaMemcpyAsync(total, ml_ptr_dev + npairs, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GBLA_CUDA_TRY(cudaStreamSynchronize(s));
+    GBLA_TRY(readback(total, ml_ptr_dev + npairs, sizeof(int64_t), s));
     if (ml_pos_dev) {
         multiline_pairs_kernel<<<nb, 128, 0, s>>>(npairs, m, row_ptr, col, val, ml_ptr_dev, ml_pos_dev, ml_val_dev, 1);
         GBLA_CUDA_TRY(launch_check());

@@ -216,6 +216,21 @@ WORKLOADS = {
 }
 
 
+def mixed_batch(count: int, seed: int, rows=(500, 20000), primes=(65521, 32003)):
+    """Specs of a batch of F4-shaped matrices of uneven sizes: rows
+    log-uniform in ``rows``, columns 1.3-1.6 x rows, 60-80% designated pivots,
+    density 1-5%, runs of 4-32, p drawn from ``primes``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        m = int(np.exp(rng.uniform(np.log(rows[0]), np.log(rows[1]))))
+        ncols = int(m * rng.uniform(1.3, 1.6))
+        npiv = int(m * rng.uniform(0.6, 0.8))
+        out.append(FLSpec(m=m, n=ncols, npiv=npiv, p=int(rng.choice(list(primes))),
+                          density=float(rng.uniform(0.01, 0.05)), run_len=(4, 32), seed=seed * 1000 + i))
+    return out
+
+
 def workload(name: str, **overrides):
     spec = WORKLOADS[name]
     if overrides:
