@@ -716,7 +716,38 @@ __global__ void iota_kernel(int32_t *v, int64_t n)
     if (i < n) v[i] = (int32_t)i;
 }
 
-// Problem tables of the grouped products of a chunk (one thread).
+// Exclusive prefix sum of v across the block (blockDim.x a multiple of 32,
+// at most 1024); *total receives the block's sum.  All threads must call it.
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *total)
+{
+    __shared__ int64_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < nw) wsum[lane] = w;   // inclusive warp prefixes
+    }
+    __syncthreads();
+    const int64_t before = warp > 0 ? wsum[warp - 1] : 0;
+    *total = wsum[nw - 1];
+    __syncthreads();   // wsum is reused by the next call
+    return before + incl - v;
+}
+
+// Problem tables of the grouped products of a chunk (one block, the jobs in
+// chunks of blockDim.x, tile offsets by a block-wide prefix sum).
 // mode 1: D[S] += (G - I) * D[S];  mode 2: D[cand] -= (H G) * D[S]_old;
 // mode 3: H16 += H * (G - I), i.e. H16 <- H G, where H = D[cand, pc].
 __global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const PanelPlan *__restrict__ plan,
@@ -725,59 +756,74 @@ __global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const P
                                   const int32_t *__restrict__ cand, int job0, int64_t row_base,
                                   const int32_t *__restrict__ iota)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t off = 0;
-    for (int q = 0; q < nprob; ++q) {
-        const PanelPlan pl = plan[q];
-        const int t = t_slot[pl.slot];
-        GroupProb P;
-        P.b_row0 = (int32_t)pl.boff;
-        P.N = pl.nc;
-        P.c_col0 = (int64_t)pl.slot * PANEL;
-        if (mode == 1) {
-            // no new pivot on the panel: G = I, nothing to do
-            P.a_row0 = q * PANEL;
-            P.M = wave_slot[2 * pl.slot] > 0 ? t : 0;
-            P.c_rows = S_slot + (int64_t)pl.slot * PANEL;
-        } else if (mode == 3) {
-            // H G = H when G = I; nothing needed without dependent candidates
-            const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
-            P.a_row0 = (int32_t)(b - row_base);
-            P.b_row0 = q * PANEL;
-            P.N = t;
-            P.c_col0 = 0;
-            P.M = (wave_slot[2 * pl.slot] > 0 && wave_slot[2 * pl.slot + 1] > 0) ? (int32_t)(e - b) : 0;
-            P.c_rows = iota + (b - row_base);
-        } else {
-            // no dependent candidate: nothing to clear
-            const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
-            P.a_row0 = (int32_t)(b - row_base);
-            P.M = wave_slot[2 * pl.slot + 1] > 0 ? (int32_t)(e - b) : 0;
-            P.c_rows = cand + b;
+    int64_t off = 0;   // tiles of the chunks before
+    for (int q0 = 0; q0 < nprob; q0 += blockDim.x) {
+        const int q = q0 + (int)threadIdx.x;
+        GroupProb P{};
+        int64_t cnt = 0;
+        if (q < nprob) {
+            const PanelPlan pl = plan[q];
+            const int t = t_slot[pl.slot];
+            P.b_row0 = (int32_t)pl.boff;
+            P.N = pl.nc;
+            P.c_col0 = (int64_t)pl.slot * PANEL;
+            if (mode == 1) {
+                // no new pivot on the panel: G = I, nothing to do
+                P.a_row0 = q * PANEL;
+                P.M = wave_slot[2 * pl.slot] > 0 ? t : 0;
+                P.c_rows = S_slot + (int64_t)pl.slot * PANEL;
+            } else if (mode == 3) {
+                // H G = H when G = I; nothing needed without dependent candidates
+                const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
+                P.a_row0 = (int32_t)(b - row_base);
+                P.b_row0 = q * PANEL;
+                P.N = t;
+                P.c_col0 = 0;
+                P.M = (wave_slot[2 * pl.slot] > 0 && wave_slot[2 * pl.slot + 1] > 0) ? (int32_t)(e - b) : 0;
+                P.c_rows = iota + (b - row_base);
+            } else {
+                // no dependent candidate: nothing to clear
+                const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
+                P.a_row0 = (int32_t)(b - row_base);
+                P.M = wave_slot[2 * pl.slot + 1] > 0 ? (int32_t)(e - b) : 0;
+                P.c_rows = cand + b;
+            }
+            if (t == 0) P.M = 0;
+            cnt = (P.M > 0 && P.N > 0) ? ((int64_t)(P.M + 127) / 128) * ((int64_t)(P.N + 127) / 128) : 0;
         }
-        if (t == 0) P.M = 0;
-        P.tile_off = off;
-        probs[q] = P;
-        off += (P.M > 0 && P.N > 0) ? ((int64_t)(P.M + 127) / 128) * ((int64_t)(P.N + 127) / 128) : 0;
+        int64_t total = 0;
+        const int64_t ex = block_exclusive_scan(cnt, &total);
+        if (q < nprob) {
+            P.tile_off = off + ex;
+            probs[q] = P;
+        }
+        off += total;
     }
-    probs[nprob].tile_off = off;
+    if (threadIdx.x == 0) probs[nprob].tile_off = off;
 }
 
 // Pivot records in pivot-column order (slots ascending, columns ascending
-// inside a slot); *rank receives their number.  One thread.
-__global__ void compact_slots_kernel(int64_t npan, const int32_t *__restrict__ t_slot,
-                                     const int32_t *__restrict__ S_slot, const int32_t *__restrict__ pc_slot,
-                                     int32_t *__restrict__ prow, int32_t *__restrict__ pcol, int64_t *rank)
+// inside a slot); *rank receives their number.  One block: a thread per slot,
+// record offsets by a block-wide prefix sum.
+__global__ void __launch_bounds__(1024) compact_slots_kernel(int64_t npan, const int32_t *__restrict__ t_slot,
+                                                             const int32_t *__restrict__ S_slot,
+                                                             const int32_t *__restrict__ pc_slot,
+                                                             int32_t *__restrict__ prow, int32_t *__restrict__ pcol,
+                                                             int64_t *rank)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t r = 0;
-    for (int64_t k = 0; k < npan; ++k)
-        for (int i = 0; i < t_slot[k]; ++i) {
-            prow[r] = S_slot[k * PANEL + i];
-            pcol[r] = (int32_t)(k * PANEL + pc_slot[k * PANEL + i]);
-            ++r;
+    int64_t off = 0;
+    for (int64_t k0 = 0; k0 < npan; k0 += blockDim.x) {
+        const int64_t k = k0 + threadIdx.x;
+        const int t = k < npan ? t_slot[k] : 0;
+        int64_t total = 0;
+        const int64_t r = off + block_exclusive_scan(t, &total);
+        for (int i = 0; i < t; ++i) {
+            prow[r + i] = S_slot[k * PANEL + i];
+            pcol[r + i] = (int32_t)(k * PANEL + pc_slot[k * PANEL + i]);
         }
-    *rank = r;
+        off += total;
+    }
+    if (threadIdx.x == 0) *rank = off;
 }
 
 // Z = T^-1 for the unit upper triangular w x w block T (shared memory), by
@@ -1121,18 +1167,18 @@ static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<Panel
     gather_gmt_planes_kernel<<<dim3(PANEL, (unsigned)nj), PANEL, 0, s>>>(W.GmT, W.Gm_all, W.plan_dev, mp);
     GBLA_CUDA_TRY(launch_check());
     // D[S] += (G - I) * D[S]
-    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
+    make_probs_kernel<<<1, 256, 0, s>>>(W.probs, nj, 1, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
                                        row_base, W.iota);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(modgemm_grouped(W.Gp, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, +1, mp, E.variant, E.err, s, E.ctr));
     // H G = H + H (G - I), then its planes replace those of H
-    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 3, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
+    make_probs_kernel<<<1, 256, 0, s>>>(W.probs, nj, 3, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
                                        row_base, W.iota);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(modgemm_grouped(W.H, W.GmT, W.probs, nj, PANEL, W.H16, PANEL, +1, mp, E.variant, E.err, s, E.ctr));
     GBLA_TRY(to_planes(W.H, W.H.rows, PANEL, W.H16, PANEL, 0, false, nullptr, nullptr, mp, s));
     // D[cand] -= (H G) * D[S]_old  (= H * D[S]_new; pivot rows have zero multipliers)
-    make_probs_kernel<<<1, 32, 0, s>>>(W.probs, nj, 2, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
+    make_probs_kernel<<<1, 256, 0, s>>>(W.probs, nj, 2, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand, job0,
                                        row_base, W.iota);
     GBLA_CUDA_TRY(launch_check());
     GBLA_TRY(modgemm_grouped(W.H, W.Bs, W.probs, nj, PANEL, E.D16, E.ldd, -1, mp, E.variant, E.err, s, E.ctr));
@@ -1253,7 +1299,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
                                                                                   nullptr, -1, E.is_piv_row, W.lead);
             ECUDA(launch_check());
         }
-        compact_slots_kernel<<<1, 32, 0, s>>>(npan, W.t_slot, W.S_slot, W.pc_slot, E.prow, E.pcol, rank_dev);
+        compact_slots_kernel<<<1, 1024, 0, s>>>(npan, W.t_slot, W.S_slot, W.pc_slot, E.prow, E.pcol, rank_dev);
         ECUDA(launch_check());
         ESTEP(readback(&rank, rank_dev, sizeof(int64_t), s));
     }
