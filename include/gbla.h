@@ -109,11 +109,14 @@ int gbla_reduce_ex(const gbla_csr_in *in, uint32_t p, const gbla_options *opt,
 /* ---- many matrices ----------------------------------------------------- */
 /* Batch: reduce n independent matrices (in[i] over GF(p[i]), options opt for
  * all, NULL = defaults).  `workers` host threads (0 = 8), each with its own
- * CUDA stream on the current device, run whole reductions concurrently,
- * largest matrices first, so that the latency-bound phases of one matrix
- * overlap with the work of others.  outs[i], ranks[i], codes[i] receive each
- * result (release outs with gbla_free).  Returns GBLA_OK, or the first
- * failing code (the other results are still valid where codes[i] == 0). */
+ * CUDA stream on the current device, take the matrices largest first.  The
+ * device work of one reduction (its copies included) runs under a
+ * process-wide lock, so reductions follow one another on the device and
+ * overlap only their host-side work; concurrent device work of several
+ * reductions has been seen to stall for tens of seconds.  outs[i], ranks[i],
+ * codes[i] receive each result (release outs with gbla_free).  Returns
+ * GBLA_OK, or the first failing code (the other results are still valid
+ * where codes[i] == 0). */
 int gbla_reduce_batch(int n, const gbla_csr_in *in, const uint32_t *p, const gbla_options *opt,
                       int workers, gbla_csr_out *outs, int64_t *ranks, int *codes);
 
@@ -121,8 +124,10 @@ int gbla_reduce_batch(int n, const gbla_csr_in *in, const uint32_t *p, const gbl
  * copied at submit) are admitted in arrival order whenever a worker is free
  * and the request's estimated device footprint fits in mem_budget next to
  * the requests already running; a request larger than the budget runs alone.
- * Admitted requests run concurrently on the workers' streams.  Latency is
- * measured from submit to result ready. */
+ * Admitted requests run on the workers' streams; as in gbla_reduce_batch
+ * their device work is serialised by the process-wide lock, so requests
+ * overlap on the host only.  Latency is measured from submit to result
+ * ready. */
 typedef struct gbla_server gbla_server;
 typedef struct {
     int64_t submitted, completed, failed, cancelled, queued, running;

@@ -1,12 +1,13 @@
 // runtime.cu -- many reductions at once: the batch entry point and the
 // request server.
 //
-// Both run whole reductions (gbla.cu) concurrently: a pool of host worker
-// threads, each owning a non-blocking CUDA stream on the caller's device,
-// takes reductions from a shared queue.  The latency-bound parts of one
-// reduction (the sparse leaf solves, the single-CTA echelon panels, the host
-// reads of sizes) leave most of the GPU idle; other workers' reductions fill
-// it, and large products of different matrices share the SMs.
+// Both hand whole reductions (gbla.cu) to a pool of host worker threads,
+// each owning a non-blocking CUDA stream on the caller's device, that take
+// them from a shared queue.  The device work of one reduction runs under a
+// process-wide lock in gbla.cu: when several reductions' kernels ran at once,
+// single phases stalled for tens of seconds, so reductions follow one another
+// on the device and the workers overlap only host-side work (queueing,
+// request copies, result hand-off).
 //
 // Batch: every matrix is known up front; workers take them largest first
 // (longest-processing-time order) so the tail of the batch is short.
