@@ -414,6 +414,21 @@ struct SideStream {
 };
 static thread_local SideStream g_side;
 
+void release_thread_resources() {
+    if (g_side.s) {
+        cudaStreamDestroy(g_side.s);
+        cudaEventDestroy(g_side.fork);
+        cudaEventDestroy(g_side.join);
+        g_side = SideStream{};
+    }
+    // freeing page-locked memory waits for an idle device: left allocated
+    // while reductions of other threads are in flight
+    if (g_scratch.p && g_active_reductions.load() == 0) {
+        cudaFreeHost(g_scratch.p);
+        g_scratch = Scratch{};
+    }
+}
+
 // Column width of the tensor-core leaf solves of C*A^-1 (env GBLA_TRSM_LEAF
 // overrides: 128, 256, 512 or 1024).  Wider leaves mean fewer, larger products
 // and two fewer levels of small block updates, for a little more product work.

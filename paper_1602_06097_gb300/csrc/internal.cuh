@@ -26,27 +26,32 @@ struct GroupProb {
     int64_t tile_off;
 };
 
-// Grouped product C[c_rows, c_col0:] += sign * A_p * B_p^T for every problem
-// p, one launch (see GroupProb).
 // True on a device with the tcgen05 tensor-core path (compute capability 10.3).
 bool tc_supported();
 
-// Product written as A-operand digit planes: Out[row, out_col0 + n] <- (A*B)[row, n]
-// mod p (tensor-core variant only).
 // Device-to-host copy of `bytes` into pageable host memory `dst` through a
 // page-locked scratch buffer of the calling thread; synchronises stream s.
 int readback(void *dst, const void *src, size_t bytes, cudaStream_t s);
 
+// Releases what the reductions keep per host thread (a side stream and its
+// events, the page-locked readback buffer); for worker threads about to exit.
+void release_thread_resources();
+
+// Product written as A-operand digit planes: Out[row, out_col0 + n] <- (A*B)[row, n]
+// mod p (tensor-core variant only).
 int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t b_row0, const Planes &Out,
                       int64_t out_col0, int64_t M, int64_t N, int64_t K, const ModP &mp, uint32_t *err,
                       cudaStream_t s, GemmCounters *ctr);
+// Grouped product C[c_rows, c_col0:] += sign * A_p * B_p^T for every problem
+// p, one launch (see GroupProb).
 int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K, uint16_t *C,
                     int64_t ldc, int sign, const ModP &mp, int variant, uint32_t *err, cudaStream_t s,
                     GemmCounters *ctr);
 
 // One whole reduction on stream s (the body of gbla_reduce_ex; arguments
 // already checked for null pointers and p).  Thread-safe: calls from
-// different host threads on different streams run concurrently.
+// different host threads take a process-wide lock around their device work,
+// so they follow one another on the device.
 int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
                 int64_t *rank_out, gbla_stats *stats);
 bool is_prime(uint32_t p);

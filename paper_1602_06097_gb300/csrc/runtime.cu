@@ -48,6 +48,102 @@ struct StreamGuard {
 
 int default_workers(int w) { return w > 0 ? (w > 64 ? 64 : w) : 8; }
 
+// One gbla_reduce_batch call as the workers see it.
+struct BatchJob {
+    int n = 0, nw = 0, dev = 0;
+    const int *order = nullptr;   // matrices, largest first
+    const gbla_csr_in *in = nullptr;
+    const uint32_t *p = nullptr;
+    const gbla_options *opt = nullptr;
+    gbla_csr_out *outs = nullptr;
+    int64_t *ranks = nullptr;
+    int *codes = nullptr;
+    std::atomic<int> next{0};
+};
+
+// Batch workers start on first use and live as long as the process, so each
+// keeps its streams, and the per-thread state of the reductions (side stream,
+// page-locked readback buffer), from one call to the next instead of
+// creating it per call.  Calls are served one at a time; worker w takes part
+// in a call that asks for more than w workers.  The pool is never destroyed:
+// its threads are detached and wait on its condition variable until the
+// process ends.
+class BatchPool {
+public:
+    static BatchPool &get() {
+        static BatchPool *pool = new BatchPool();
+        return *pool;
+    }
+
+    int run(BatchJob &job) {
+        std::lock_guard<std::mutex> call(call_mu_);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            while (started_ < job.nw) {
+                const int w = started_;
+                try {
+                    std::thread([this, w] { loop(w); }).detach();
+                } catch (...) {   // no more threads: run with those already started
+                    break;
+                }
+                ++started_;
+            }
+            job.nw = std::min(job.nw, started_);
+            if (job.nw == 0) return GBLA_E_NOMEM;
+            job_ = &job;
+            pending_ = job.nw;
+            ++gen_;
+        }
+        cv_job_.notify_all();
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_done_.wait(lk, [&] { return pending_ == 0; });
+        job_ = nullptr;
+        return GBLA_OK;
+    }
+
+private:
+    void loop(int w) {
+        std::vector<cudaStream_t> streams;   // one per device, created on first use
+        uint64_t seen = 0;
+        for (;;) {
+            BatchJob *job;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_job_.wait(lk, [&] { return job_ && gen_ != seen && w < job_->nw; });
+                seen = gen_;
+                job = job_;
+            }
+            int rc0 = cudaSetDevice(job->dev) == cudaSuccess ? GBLA_OK : GBLA_E_CUDA;
+            if (rc0 == GBLA_OK && (int)streams.size() <= job->dev) streams.resize(job->dev + 1, nullptr);
+            if (rc0 == GBLA_OK && !streams[job->dev] &&
+                cudaStreamCreateWithFlags(&streams[job->dev], cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                streams[job->dev] = nullptr;
+                rc0 = GBLA_E_CUDA;
+            }
+            for (;;) {
+                const int k = job->next.fetch_add(1);
+                if (k >= job->n) break;
+                const int i = job->order[k];
+                if (rc0 != GBLA_OK) { job->codes[i] = rc0; continue; }
+                if (job->p[i] >= 65536u || !is_prime(job->p[i])) { job->codes[i] = GBLA_E_INVAL; continue; }
+                job->codes[i] = reduce_impl(&job->in[i], job->p[i], job->opt, streams[job->dev], &job->outs[i],
+                                            &job->ranks[i], nullptr);
+            }
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--pending_ == 0) cv_done_.notify_all();
+        }
+    }
+
+    std::mutex call_mu_;   // one batch call at a time
+    std::mutex mu_;
+    std::condition_variable cv_job_, cv_done_;
+    BatchJob *job_ = nullptr;
+    uint64_t gen_ = 0;
+    int pending_ = 0;
+    int started_ = 0;
+};
+
 }  // namespace
 }  // namespace gbla
 
@@ -63,33 +159,25 @@ extern "C" int gbla_reduce_batch(int n, const gbla_csr_in *in, const uint32_t *p
         codes[i] = GBLA_E_INTERNAL;
     }
     if (n == 0) return GBLA_OK;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GBLA_E_CUDA;
+    BatchJob job;
+    if (cudaGetDevice(&job.dev) != cudaSuccess) return GBLA_E_CUDA;
     // largest first
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (double)in[a].nrows * (double)in[a].ncols > (double)in[b].nrows * (double)in[b].ncols;
     });
-    std::atomic<int> next{0};
-    const int nw = std::min(default_workers(workers), n);
-    std::vector<std::thread> pool;
-    pool.reserve(nw);
-    for (int w = 0; w < nw; ++w) {
-        pool.emplace_back([&] {
-            StreamGuard sg;
-            const int rc0 = sg.create(dev);
-            for (;;) {
-                const int k = next.fetch_add(1);
-                if (k >= n) break;
-                const int i = order[k];
-                if (rc0 != GBLA_OK) { codes[i] = rc0; continue; }
-                if (p[i] >= 65536u || !is_prime(p[i])) { codes[i] = GBLA_E_INVAL; continue; }
-                codes[i] = reduce_impl(&in[i], p[i], opt, sg.s, &outs[i], &ranks[i], nullptr);
-            }
-        });
-    }
-    for (auto &t : pool) t.join();
+    job.n = n;
+    job.nw = std::min(default_workers(workers), n);
+    job.order = order.data();
+    job.in = in;
+    job.p = p;
+    job.opt = opt;
+    job.outs = outs;
+    job.ranks = ranks;
+    job.codes = codes;
+    const int rc = BatchPool::get().run(job);
+    if (rc != GBLA_OK) return rc;
     for (int i = 0; i < n; ++i)
         if (codes[i] != GBLA_OK) return codes[i];
     return GBLA_OK;
@@ -139,6 +227,9 @@ struct gbla_server {
     }
 
     void worker_main() {
+        struct ReleaseAtExit {
+            ~ReleaseAtExit() { release_thread_resources(); }
+        } release_at_exit;   // runs after the stream below is destroyed
         StreamGuard sg;
         const int rc0 = sg.create(dev);
         std::unique_lock<std::mutex> lk(mu);

@@ -102,3 +102,33 @@ def test_server_budget_admission_and_cancel():
         assert code in (0, gbla.GBLA_E_CANCELLED)
         code, res, _ = srv.wait(tbad, timeout=120.0)
         assert code == 1 and res is None
+
+
+def test_batch_workers_persist_across_calls():
+    """Batch workers are kept between calls: calls with growing, shrinking and
+    default worker counts, and with fewer matrices than workers, all return
+    the one-at-a-time results."""
+    specs = mixed_specs(9, 11)
+    mats = [synth.fl_matrix(s) + ((s.m, s.n), s.p) for s in specs]
+    solo = [gbla.reduce(*mt) for mt in mats]
+    for workers, count in ((2, 9), (12, 9), (1, 9), (0, 9), (16, 3), (5, 1)):
+        res = gbla.reduce_batch(mats[:count], workers=workers)
+        assert len(res) == count
+        for r, ref in zip(res, solo):
+            same(r, ref)
+    assert gbla.reduce_batch([], workers=4) == []
+
+
+def test_server_create_destroy_cycles():
+    """Servers created and destroyed in turn (their worker threads release
+    their streams and buffers on exit) keep serving exact results."""
+    specs = mixed_specs(3, 12)
+    mats = [synth.fl_matrix(s) + ((s.m, s.n), s.p) for s in specs]
+    solo = [gbla.reduce(*mt) for mt in mats]
+    for cycle in range(4):
+        with gbla.Server(workers=1 + cycle) as srv:
+            tickets = [srv.submit(*mt) for mt in mats]
+            for t, ref in zip(tickets, solo):
+                code, res, _ = srv.wait(t, timeout=120.0)
+                assert code == 0
+                same(res, ref)
