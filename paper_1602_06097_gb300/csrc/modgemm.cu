@@ -13,8 +13,9 @@
 // suffice.  Every digit product is at most 2^14 in magnitude and each k adds
 // two of them, so over a k-block of 512 every partial sum stays below 2^24 and
 // fp32 accumulation is exact whatever the order of additions.  After each
-// k-block the accumulators are drained from TMEM, reduced mod p and added to
-// a running residue kept in registers.  The kernel is a persistent,
+// k-block the accumulators are drained from TMEM, reduced mod p (fp32 for each
+// accumulator, integers for the combination) and added to a running residue
+// kept in registers.  The kernel is a persistent,
 // warp-specialised tcgen05 pipeline: one thread issues TMA loads into a
 // 4-stage shared-memory ring, one thread issues tcgen05.mma into a
 // double-buffered TMEM accumulator pair, eight warps drain TMEM.
@@ -462,6 +463,23 @@ __device__ __forceinline__ int f2i_small(float r) {  // exact integer |r| < 2^22
     return __float_as_int(r + MAGIC) - 0x4B400000;
 }
 
+// One drained k-block of one element: returns (run + 256*pa + qa) mod p in
+// [0, p) for run in [0, p) and exact accumulators |pa|, |qa| <= 2^24.  Each
+// accumulator is reduced in fp32 (|r| <= 5p/8) and converted exactly; the
+// rest is integer work, which unlike fp32 work does not slow the concurrent
+// tensor-core MMAs.  t = run + 256*rp + rq + 256p lies in (95p, 418p), below
+// 2^25, so q = floor(t * bm / 2^32) with bm = floor(2^32 / p) is floor(t/p) or
+// one less and a single conditional subtraction finishes the reduction.
+__device__ __forceinline__ int drain_step(int run, float pa, float qa, float pf, float pinv, int P, int bias,
+                                          uint32_t bm) {
+    const int rp = f2i_small(fred(pa, pf, pinv));
+    const int rq = f2i_small(fred(qa, pf, pinv));
+    const uint32_t t = (uint32_t)(run + bias + rq + 256 * rp);
+    int s = (int)(t - __umulhi(t, bm) * (uint32_t)P);
+    s -= (s >= P) ? P : 0;
+    return s;
+}
+
 __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t num_n, int64_t GM, int64_t &mt,
                                             int64_t &nt) {
     int64_t group = t / (GM * num_n);
@@ -724,6 +742,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int row_in_tile = quarter * 32 + lane;
         const float pf = g.pf, pinv = g.pinv;
         const int P = (int)g.p;
+        // Barrett multiplier floor(2^32 / p) (p odd) and a bias that keeps the
+        // combined value positive
+        const uint32_t bm = 0xFFFFFFFFu / g.p;
+        const int bias = 256 * P;
         constexpr int HC = BN / 2;    // columns per drain warp
         uint32_t kbc = 0;
         bool ok = true;
@@ -748,21 +770,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         uint32_t pair = run[c * 8 + j / 2];
-                        int lo16 = (int)(pair & 0xFFFFu), hi16 = (int)(pair >> 16);
-                        {
-                            float v = fmaf(256.0f, fred(pv[j], pf, pinv), fred(qv[j], pf, pinv));
-                            int s = lo16 + f2i_small(fred(v, pf, pinv));
-                            s += (s < 0) ? P : 0;
-                            s -= (s >= P) ? P : 0;
-                            lo16 = s;
-                        }
-                        {
-                            float v = fmaf(256.0f, fred(pv[j + 1], pf, pinv), fred(qv[j + 1], pf, pinv));
-                            int s = hi16 + f2i_small(fred(v, pf, pinv));
-                            s += (s < 0) ? P : 0;
-                            s -= (s >= P) ? P : 0;
-                            hi16 = s;
-                        }
+                        const int lo16 = drain_step((int)(pair & 0xFFFFu), pv[j], qv[j], pf, pinv, P, bias, bm);
+                        const int hi16 = drain_step((int)(pair >> 16), pv[j + 1], qv[j + 1], pf, pinv, P, bias, bm);
                         run[c * 8 + j / 2] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
                     }
                 }
