@@ -13,9 +13,9 @@
 // suffice.  Every digit product is at most 2^14 in magnitude and each k adds
 // two of them, so over a k-block of 512 every partial sum stays below 2^24 and
 // fp32 accumulation is exact whatever the order of additions.  After each
-// k-block the accumulators are drained from TMEM, reduced mod p (fp32 for each
-// accumulator, integers for the combination) and added to a running residue
-// kept in registers.  The kernel is a persistent,
+// k-block the accumulators are drained from TMEM, converted to integers and
+// reduced mod p (integer arithmetic apart from one fp32 quotient estimate) into
+// a running residue kept in registers.  The kernel is a persistent,
 // warp-specialised tcgen05 pipeline: one thread issues TMA loads into a
 // 4-stage shared-memory ring, one thread issues tcgen05.mma into a
 // double-buffered TMEM accumulator pair, eight warps drain TMEM.
@@ -220,7 +220,7 @@ struct Args {
     const int32_t *row_lead; // optional: ascending first nonzero K index of each A row
     int sign;
     uint32_t p;
-    float pf, pinv;
+    float pinv;              // 1/p rounded to fp32 (p >= 8)
     uint32_t *err;
     int withhold_loads;      // test hook: issue no TMA loads, so the waits expire
     int group_m;             // row tiles per raster group
@@ -450,31 +450,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// x an exact integer in fp32 with |x| <= 2^24 and p >= 8: returns an exact
-// integer r == x (mod p) with |r| <= 5p/8.  q = round(x * (1/p)) is formed by
-// one fused multiply-add into the 2^23 rounding window; the error of the
-// rounded reciprocal moves x/p by at most 1/8.
-__device__ __forceinline__ float fred(float x, float pf, float pinv) {
-    float q = fmaf(x, pinv, MAGIC) - MAGIC;
-    return fmaf(-q, pf, x);
-}
-
-__device__ __forceinline__ int f2i_small(float r) {  // exact integer |r| < 2^22
-    return __float_as_int(r + MAGIC) - 0x4B400000;
-}
-
 // One drained k-block of one element: returns (run + 256*pa + qa) mod p in
-// [0, p) for run in [0, p) and exact accumulators |pa|, |qa| <= 2^24.  Each
-// accumulator is reduced in fp32 (|r| <= 5p/8) and converted exactly; the
-// rest is integer work, which unlike fp32 work does not slow the concurrent
-// tensor-core MMAs.  t = run + 256*rp + rq + 256p lies in (95p, 418p), below
-// 2^25, so q = floor(t * bm / 2^32) with bm = floor(2^32 / p) is floor(t/p) or
+// [0, p) for run in [0, p) and exact accumulators |pa|, |qa| <= 2^24.  Both
+// accumulators convert exactly to integers; pa's quotient q by p comes from
+// one fused multiply-add into the 2^23 rounding window (the rounded
+// reciprocal moves pa/p by at most 1/8 for p >= 8, so |pa - q*p| <= 5p/8).
+// Everything else is integer work, which unlike fp32 work does not slow the
+// concurrent tensor-core MMAs.  With bias = 256p + ceil(2^24/p)*p, the value
+// t = run + 256*(pa - q*p) + qa + bias lies in [96p, 2^25 + 418p), below
+// 2^26, so floor(t * bm / 2^32) with bm = floor(2^32 / p) is floor(t/p) or
 // one less and a single conditional subtraction finishes the reduction.
-__device__ __forceinline__ int drain_step(int run, float pa, float qa, float pf, float pinv, int P, int bias,
-                                          uint32_t bm) {
-    const int rp = f2i_small(fred(pa, pf, pinv));
-    const int rq = f2i_small(fred(qa, pf, pinv));
-    const uint32_t t = (uint32_t)(run + bias + rq + 256 * rp);
+__device__ __forceinline__ int drain_step(int run, float pa, float qa, float pinv, int P, int bias, uint32_t bm) {
+    const int ip = __float2int_rn(pa);
+    const int iq = __float2int_rn(qa);
+    const int qp = __float_as_int(fmaf(pa, pinv, MAGIC)) - 0x4B400000;
+    const int rp = ip - qp * P;
+    const uint32_t t = (uint32_t)(run + bias + iq + 256 * rp);
     int s = (int)(t - __umulhi(t, bm) * (uint32_t)P);
     s -= (s >= P) ? P : 0;
     return s;
@@ -740,12 +731,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
-        const float pf = g.pf, pinv = g.pinv;
+        const float pinv = g.pinv;
         const int P = (int)g.p;
-        // Barrett multiplier floor(2^32 / p) (p odd) and a bias that keeps the
-        // combined value positive
+        // Barrett multiplier floor(2^32 / p) (p odd) and a multiple of p that
+        // keeps the combined value positive
         const uint32_t bm = 0xFFFFFFFFu / g.p;
-        const int bias = 256 * P;
+        const int bias = 256 * P + (int)(((1u << 24) + g.p - 1) / g.p) * P;
         constexpr int HC = BN / 2;    // columns per drain warp
         uint32_t kbc = 0;
         bool ok = true;
@@ -770,8 +761,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         uint32_t pair = run[c * 8 + j / 2];
-                        const int lo16 = drain_step((int)(pair & 0xFFFFu), pv[j], qv[j], pf, pinv, P, bias, bm);
-                        const int hi16 = drain_step((int)(pair >> 16), pv[j + 1], qv[j + 1], pf, pinv, P, bias, bm);
+                        const int lo16 = drain_step((int)(pair & 0xFFFFu), pv[j], qv[j], pinv, P, bias, bm);
+                        const int hi16 = drain_step((int)(pair >> 16), pv[j + 1], qv[j + 1], pinv, P, bias, bm);
                         run[c * 8 + j / 2] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
                     }
                 }
@@ -1026,7 +1017,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     g.a_row0 = (int32_t)a_row0; g.a_k0 = (int32_t)a_k0;
     g.b_row0 = (int32_t)b_row0; g.b_k0 = (int32_t)b_k0;
     g.C = C; g.ldc = ldc; g.c_rows = c_rows; g.row_lead = row_lead; g.sign = sign;
-    g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+    g.p = mp.p; g.pinv = mp.pinv;
     g.err = err;
     g.withhold_loads = 0;
     if (pair) {
@@ -1083,7 +1074,7 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     g.a_row0 = (int32_t)a_row0; g.a_k0 = 0;
     g.b_row0 = (int32_t)b_row0; g.b_k0 = 0;
     g.sign = 1;
-    g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+    g.p = mp.p; g.pinv = mp.pinv;
     g.err = err;
     g.xout = Out;
     g.xout_col0 = out_col0;
@@ -1139,7 +1130,7 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
     g.probs = probs; g.nprob = nprob;
     g.group_m = gemm_group_m();
     g.C = C; g.ldc = ldc; g.sign = sign;
-    g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+    g.p = mp.p; g.pinv = mp.pinv;
     g.err = err;
     tc::modgemm_tc_kernel<false><<<device_sm_count(), tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
     GBLA_CUDA_TRY(launch_check());
@@ -1176,7 +1167,7 @@ int modgemm_withheld_loads(uint32_t *err, cudaStream_t s)
         g.M = 128; g.N = 128; g.K = 64;
             g.C = C; g.ldc = 128; g.sign = 1;
         const ModP mp = make_modp(65521);
-        g.p = mp.p; g.pf = mp.pf; g.pinv = mp.pinv;
+        g.p = mp.p; g.pinv = mp.pinv;
         g.err = err;
         g.withhold_loads = 1;
         tc::modgemm_tc_kernel<false><<<1, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
