@@ -89,7 +89,17 @@ __device__ __forceinline__ void digits(uint32_t a, uint32_t p, int &hi, int &lo)
     lo = s - (hi << 8);
 }
 
-__device__ __forceinline__ __nv_bfloat16 i2bf(int v) { return __float2bfloat16_rn((float)v); }
+// fp32 pattern of a digit |v| <= 256: v added to the pattern of 1.5 * 2^23
+// (one unit in the last place each), then one fp32 subtraction; no
+// integer-to-float conversion.  A digit has at most 8 significant bits, so the
+// low half of the pattern is zero and the high half is the exact bf16.
+__device__ __forceinline__ uint32_t digit_f32_bits(int v) {
+    return __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f);
+}
+
+__device__ __forceinline__ __nv_bfloat16 i2bf(int v) {
+    return __ushort_as_bfloat16((unsigned short)(digit_f32_bits(v) >> 16));
+}
 
 // Plane-set geometry.  An "A-operand" set holds 2 planes (hi, lo) of an
 // M x K matrix, a "B-operand" set holds 4 planes (hi, lo of b, hi, lo of
@@ -141,9 +151,9 @@ struct TpSmem {
     uint16_t t[TP_TILE][TP_TILE + 2];
 };
 
+// Two digits as a bf16 pair (lo_elem in the low half).
 __device__ __forceinline__ uint32_t pack_bf2(int lo_elem, int hi_elem) {
-    __nv_bfloat162 v = __floats2bfloat162_rn((float)lo_elem, (float)hi_elem);
-    return *reinterpret_cast<uint32_t *>(&v);
+    return __byte_perm(digit_f32_bits(lo_elem), digit_f32_bits(hi_elem), 0x7632);
 }
 
 // Digit planes of 8 consecutive residues a[0..7] at row r, columns k0 .. k0+7
