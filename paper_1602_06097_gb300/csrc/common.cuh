@@ -191,18 +191,24 @@ __device__ __forceinline__ void tp_tile(const Planes &dst, int64_t row0, int64_t
                                         int64_t dcol0 = 0)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = warp; i < TP_TILE; i += 8) {
-        const int64_t k = k0 + i;
+    // all of this thread's loads are issued before any of them is used, so
+    // that 16 are in flight at once
+    uint16_t v[TP_TILE / 8][2];
+#pragma unroll
+    for (int j = 0; j < TP_TILE / 8; ++j) {
+        const int64_t k = k0 + warp + 8 * j;
         int64_t sr = -1;
         if (k < Kc) sr = rgather ? (int64_t)rgather[k] : k;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t r = r0 + lane + 32 * h;
-            uint16_t v = 0;
-            if (sr >= 0 && r < R) v = src[sr * lds + col0 + r];
-            sm.t[i][lane + 32 * h] = v;
+            v[j][h] = (sr >= 0 && r < R) ? src[sr * lds + col0 + r] : (uint16_t)0;
         }
     }
+#pragma unroll
+    for (int j = 0; j < TP_TILE / 8; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) sm.t[warp + 8 * j][lane + 32 * h] = v[j][h];
     __syncthreads();
     for (int it = tid; it < TP_TILE * 8; it += 256) {
         const int c = it & 7, rr = it >> 3;
