@@ -363,7 +363,10 @@ constexpr int PANEL = 128;
 // search starts at `from`, or, with from < 0, at the panel boundary after
 // the row's current lead (the row was just cleared on its lead's panel).
 // Rows: rows[seg[0] .. seg[1]) with seg on the device, else rows[0 .. count)
-// (or rows 0 .. count when rows is null).
+// (or rows 0 .. count when rows is null).  One warp per row; every lane loads
+// two 16-byte vectors (8 columns each; the start is a multiple of 8 and ldd a
+// multiple of 64, so they are aligned and inside the row) before testing any,
+// so a step covers 512 columns with a single memory round trip.
 __global__ void row_leads_kernel(const uint16_t *__restrict__ D, int64_t ldd, int64_t n, int64_t count,
                                  const int32_t *__restrict__ rows, const int64_t *__restrict__ seg,
                                  int64_t from, const int32_t *__restrict__ skip, int32_t *__restrict__ lead)
@@ -377,11 +380,23 @@ __global__ void row_leads_kernel(const uint16_t *__restrict__ D, int64_t ldd, in
     const uint16_t *row = D + r * ldd;
     const int64_t start = from >= 0 ? from : ((int64_t)lead[r] / PANEL + 1) * PANEL;
     int64_t found = -1;
-    for (int64_t base = start; base < n && found < 0; base += 32 * 8) {
+    for (int64_t base = start; base < n && found < 0; base += 512) {
+        uint4 v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t c0 = base + u * 256 + lane * 8;
+            v[u] = (c0 < n) ? *reinterpret_cast<const uint4 *>(row + c0) : make_uint4(0u, 0u, 0u, 0u);
+        }
         int64_t best = INT64_MAX;
-        for (int e = 0; e < 8; ++e) {
-            const int64_t c = base + (int64_t)e * 32 + lane;
-            if (c < n && row[c] != 0) { best = c; break; }
+#pragma unroll
+        for (int u = 1; u >= 0; --u) {   // the lower vector last: its hit wins
+            const uint32_t wd[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+            int idx = -1;
+#pragma unroll
+            for (int q = 3; q >= 0; --q)
+                if (wd[q]) idx = 2 * q + ((wd[q] & 0xFFFFu) ? 0 : 1);
+            const int64_t c = base + u * 256 + lane * 8 + idx;
+            if (idx >= 0 && c < n) best = c;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -413,20 +428,36 @@ __global__ void panel_scatter_kernel(int64_t m, const int32_t *__restrict__ lead
     cand[off[k] + atomicAdd(&fill[k], 1)] = (int32_t)r;
 }
 
-__global__ void panel_sort_kernel(int64_t npan, const int64_t *__restrict__ off, int32_t *__restrict__ cand)
+// Each panel's candidate list into ascending row order (lists longer than
+// 2048 are left as they are): one CTA per panel, a bitonic sort in shared
+// memory over the list padded to a power of two.
+constexpr int PANEL_SORT_MAX = 2048;
+__global__ void __launch_bounds__(256) panel_sort_kernel(int64_t npan, const int64_t *__restrict__ off,
+                                                         int32_t *__restrict__ cand)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int32_t sv[PANEL_SORT_MAX];
+    const int64_t k = blockIdx.x;
     if (k >= npan) return;
-    const int64_t b = off[k], e = off[k + 1];
-    for (int64_t i = b + 1; i < e && e - b <= 2048; ++i) {
-        const int32_t v = cand[i];
-        int64_t j = i - 1;
-        while (j >= b && cand[j] > v) {
-            cand[j + 1] = cand[j];
-            --j;
+    const int64_t b = off[k];
+    const int64_t len = off[k + 1] - b;
+    if (len <= 1 || len > PANEL_SORT_MAX) return;
+    int n2 = 2;
+    while (n2 < len) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) sv[i] = (i < len) ? cand[b + i] : INT32_MAX;
+    __syncthreads();
+    for (int size = 2; size <= n2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n2 / 2; i += blockDim.x) {
+                const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+                const int32_t x = sv[lo], y = sv[hi];
+                if ((x > y) == ((lo & size) == 0)) {
+                    sv[lo] = y;
+                    sv[hi] = x;
+                }
+            }
+            __syncthreads();
         }
-        cand[j + 1] = v;
-    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) cand[b + i] = sv[i];
 }
 
 // Jobs of a wave: the panels with candidates, ascending; seg[j] = offset of
@@ -1263,7 +1294,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
             panel_scatter_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, W.lead, E.is_piv_row, off, fill,
                                                                              cand);
             ECUDA(launch_check());
-            panel_sort_kernel<<<(unsigned)((npan + 255) / 256), 256, 0, s>>>(npan, off, cand);
+            panel_sort_kernel<<<(unsigned)npan, 256, 0, s>>>(npan, off, cand);
             ECUDA(launch_check());
             make_jobs_kernel<<<1, 1024, 0, s>>>(npan, off, job_slot, seg, info);
             ECUDA(launch_check());
