@@ -1075,46 +1075,52 @@ __global__ void colmap_np_kernel(const int32_t *__restrict__ pcol, int64_t rank,
 }
 
 // Rnp[k][i] = D[rows[k]][npc[i]]: the echelon rows at the non-pivot columns.
-// A thread writes 8 consecutive outputs with one 16-byte store (ldnp is a
-// multiple of 64, so rows start 128-byte aligned).
+// A thread owns 8 consecutive outputs of a row (one 16-byte store; ldnp is a
+// multiple of 64, so rows start 128-byte aligned) and keeps their column
+// indices in registers for all the rows its block visits.
 __global__ void gather_np_kernel(const uint16_t *__restrict__ D, int64_t ldd, const int32_t *__restrict__ rows,
                                  int64_t nrows, const int32_t *__restrict__ npc, int64_t nnp, uint16_t *__restrict__ Rnp,
                                  int64_t ldnp)
 {
-    for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
-        const uint16_t *src = D + (int64_t)rows[k] * ldd;
-        uint16_t *dst = Rnp + k * ldnp;
-        for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; i0 < nnp;
-             i0 += (int64_t)gridDim.x * blockDim.x * 8) {
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; i0 < nnp;
+         i0 += (int64_t)gridDim.x * blockDim.x * 8) {
+        int32_t col[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) col[e] = (i0 + e < nnp) ? npc[i0 + e] : -1;
+        for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
+            const uint16_t *src = D + (int64_t)rows[k] * ldd;
             uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
             for (int e = 0; e < 8; ++e)
-                if (i0 + e < nnp) w[e >> 1] |= (uint32_t)src[npc[i0 + e]] << ((e & 1) * 16);
-            if (i0 + 8 <= ldnp) *reinterpret_cast<uint4 *>(dst + i0) = make_uint4(w[0], w[1], w[2], w[3]);
+                if (col[e] >= 0) w[e >> 1] |= (uint32_t)src[col[e]] << ((e & 1) * 16);
+            if (i0 + 8 <= ldnp) *reinterpret_cast<uint4 *>(Rnp + k * ldnp + i0) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
 
 // RREF rows in full: R[k][c] = Rnp[k][colmap[c]] at non-pivot columns, the
 // unit vector at the pivot columns (R[k][pcol[j]] = [j == k]).  8 columns per
-// thread, one 16-byte store (ldr is a multiple of 64).
+// thread, one 16-byte store (ldr is a multiple of 64); the column map of a
+// thread's 8 columns stays in registers for all the rows its block visits.
 __global__ void expand_rref_kernel(const uint16_t *__restrict__ Rnp, int64_t ldnp, const int32_t *__restrict__ colmap,
                                    int64_t nrows, int64_t n, uint16_t *__restrict__ R, int64_t ldr)
 {
-    for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
-        const uint16_t *src = Rnp + k * ldnp;
-        uint16_t *dst = R + k * ldr;
-        for (int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; c0 < n;
-             c0 += (int64_t)gridDim.x * blockDim.x * 8) {
+    for (int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; c0 < n;
+         c0 += (int64_t)gridDim.x * blockDim.x * 8) {
+        int32_t m[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m[e] = (c0 + e < n) ? colmap[c0 + e] : INT32_MIN;
+        for (int64_t k = blockIdx.y; k < nrows; k += gridDim.y) {
+            const uint16_t *src = Rnp + k * ldnp;
             uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                if (c0 + e >= n) break;
-                const int32_t m = colmap[c0 + e];
-                const uint32_t v = m >= 0 ? src[m] : ((int64_t)(-m - 1) == k ? 1u : 0u);
+                uint32_t v = 0;
+                if (m[e] >= 0) v = src[m[e]];
+                else if (m[e] != INT32_MIN && (int64_t)(-m[e] - 1) == k) v = 1u;
                 w[e >> 1] |= v << ((e & 1) * 16);
             }
-            if (c0 + 8 <= ldr) *reinterpret_cast<uint4 *>(dst + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+            if (c0 + 8 <= ldr) *reinterpret_cast<uint4 *>(R + k * ldr + c0) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -1354,7 +1360,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
         const int64_t xb = (n + 8 * 256 - 1) / (8 * 256);
-        const dim3 rgrid((unsigned)(xb < 64 ? xb : 64), (unsigned)(rank < 65535 ? rank : 65535));
+        const dim3 rgrid((unsigned)(xb < 64 ? xb : 64), (unsigned)(rank < 1024 ? rank : 1024));
         if (rc == GBLA_OK && nnp > 0) {
             gather_np_kernel<<<rgrid, 256, 0, s>>>(E.D16, E.ldd, E.prow, rank, npc, nnp, Rnp, ldnp);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
