@@ -429,17 +429,24 @@ void release_thread_resources() {
     }
 }
 
-// Column width of the tensor-core leaf solves of C*A^-1 (env GBLA_TRSM_LEAF
-// overrides: 128, 256, 512 or 1024).  Wider leaves mean fewer, larger products
-// and two fewer levels of small block updates, for a little more product work.
+// Column width of the tensor-core leaf solves of C*A^-1: env GBLA_TRSM_LEAF
+// (128, 256, 512 or 1024), else 0 = chosen per matrix (trsm_leaf_for).
 static int trsm_leaf_width() {
-    static int v = 0;
-    if (v == 0) {
+    static int v = -1;
+    if (v < 0) {
         const char *e = getenv("GBLA_TRSM_LEAF");
         const int x = e ? atoi(e) : 0;
-        v = (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 512;
+        v = (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 0;
     }
     return v;
+}
+
+// Wider leaves mean fewer, larger products and two fewer levels of small block
+// updates, for a little more product work and larger diagonal-block inverses:
+// 1024 columns once there are enough pivots to fill them, else 512.
+static int trsm_leaf_for(int64_t npiv) {
+    const int v = trsm_leaf_width();
+    return v > 0 ? v : (npiv >= 4096 ? 1024 : 512);
 }
 
 // Row width of the leaves of the back-substitution of the echelon form (env
@@ -471,7 +478,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     // diagonal blocks of the triangular solve on the tensor cores too
     const bool tc_leaves =
         variant == GBLA_GEMM_TCGEN05 || (variant == GBLA_GEMM_AUTO && p >= 8 && tc_supported());
-    const int tc_leaf_w = trsm_leaf_width();
+    int tc_leaf_w = 512;
     GemmCounters ctr;
     const long long launches0 = g_launches;
     Timer tm;
@@ -562,6 +569,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     nvtxRangePop();
     if (rc != GBLA_OK) goto cleanup;
     npiv = pi.npiv;
+    tc_leaf_w = trsm_leaf_for(npiv);
     m_cd = pi.m_cd;
     n_d = pi.n_d;
     ldc = round_up(npiv > 0 ? npiv : 1, 64);
@@ -589,11 +597,11 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             CSTEP(cudaEventRecord(g_side.fork, s));
             CSTEP(cudaStreamWaitEvent(g_side.s, g_side.fork, 0));
             side_pending = true;
-            rc = upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, g_side.s);
+            rc = upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, err, g_side.s);
             CSTEP(cudaEventRecord(g_side.join, g_side.s));
             STEP(rc);
         } else {
-            STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, s));
+            STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, err, s));
         }
     }
     // digit planes of the operands the products read

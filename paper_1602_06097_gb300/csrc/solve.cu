@@ -977,6 +977,88 @@ __global__ void __launch_bounds__(256) tri_combine_kernel(int mode, int w, int L
         }
 }
 
+// The same level on the tensor cores, for w >= 256: with pair b's w x w
+// operands at plane rows b w .. of shared plane sets,
+//   U = Z11 * A12 (into scratch, rows b w ..),  Z12 = -U * Z22 (into ZN),
+// two grouped products.  Digit planes of the operands:
+//   mode 0: A-operand Z11    row i, K k  <- ZN[lo+o1+i][o1+k]
+//   mode 1: B-operand A12^T  row j, K i  <- T[lo+o1+i][lo+o2+j]
+//   mode 2: A-operand U      row i, K k  <- U[b w+i][k]
+//   mode 3: B-operand Z22^T  row j, K i  <- ZN[lo+o2+i][o2+j]
+// 64 x 64 tiles (blockIdx.x: K, blockIdx.y: rows, blockIdx.z: pair), read
+// along the source rows into shared memory, written as 16-byte digit vectors.
+__global__ void __launch_bounds__(256) pair_planes_kernel(int mode, int w, int L, const uint16_t *__restrict__ A,
+                                                          int64_t lda, const int32_t *__restrict__ rmap,
+                                                          const int32_t *__restrict__ cmap, int64_t npiv,
+                                                          const uint16_t *__restrict__ ZN,
+                                                          const uint16_t *__restrict__ U, Planes dst, ModP mp)
+{
+    __shared__ TpSmem sm;
+    const int pairs_per_leaf = L / (2 * w);
+    const int64_t b = blockIdx.z;
+    const int64_t lo = (b / pairs_per_leaf) * L;
+    const int o1 = 2 * w * (int)(b % pairs_per_leaf), o2 = o1 + w;
+    const int k0 = blockIdx.x * TP_TILE, r0 = blockIdx.y * TP_TILE;
+    const bool transposed = (mode == 1 || mode == 3);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < TP_TILE * TP_TILE; e += 256) {
+        const int sr = e / TP_TILE, sc = e % TP_TILE;   // source row / column within the tile
+        const int i = transposed ? sc : sr, k = transposed ? sr : sc;   // operand row / K
+        const int rr = r0 + i, kk = k0 + k;
+        uint16_t v;
+        if (mode == 0) {
+            v = ZN[(lo + o1 + rr) * (int64_t)L + o1 + kk];
+        } else if (mode == 2) {
+            v = U[(b * w + rr) * (int64_t)w + kk];
+        } else if (mode == 1) {
+            const int64_t ar = lo + o1 + kk, ac = lo + o2 + rr;
+            v = (ar < npiv && ac < npiv) ? A[(rmap ? (int64_t)rmap[ar] : ar) * lda + (cmap ? (int64_t)cmap[ac] : ac)]
+                                         : (uint16_t)0;
+        } else {
+            v = ZN[(lo + o2 + kk) * (int64_t)L + o2 + rr];
+        }
+        sm.t[i][k] = v;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < TP_TILE * 8; it += 256) {
+        const int c = it & 7, i = it >> 3;
+        uint32_t a[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] = sm.t[i][c * 8 + e];
+        store_digits8(dst, b * w + r0 + i, k0 + c * 8, a, mp);
+    }
+}
+
+// Problem tables of the two grouped products of a tensor-core level:
+// pu[b]: U rows b w .. (ldc w), pz[b]: ZN rows lo + o1 .. at column o2.
+__global__ void pair_probs_kernel(int64_t npairs, int w, int L, const int32_t *__restrict__ iota,
+                                  GroupProb *__restrict__ pu, GroupProb *__restrict__ pz)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > npairs) return;
+    const int64_t tiles = (int64_t)(w / 128) * (w / 128);
+    GroupProb g{};
+    g.tile_off = b * tiles;
+    if (b < npairs) {
+        const int pairs_per_leaf = L / (2 * w);
+        const int64_t lo = (b / pairs_per_leaf) * L;
+        const int o1 = 2 * w * (int)(b % pairs_per_leaf);
+        g.a_row0 = (int32_t)(b * w);
+        g.b_row0 = (int32_t)(b * w);
+        g.M = w;
+        g.N = w;
+        g.c_col0 = 0;
+        g.c_rows = iota + b * w;
+        pu[b] = g;
+        g.c_col0 = o1 + w;
+        g.c_rows = iota + lo + o1;
+        pz[b] = g;
+    } else {
+        pu[b] = g;
+        pz[b] = g;
+    }
+}
+
 // Zt row J L + j, column k <- Z_J[k][j]  (tiles of 64 x 64, blockIdx.z = leaf)
 __global__ void __launch_bounds__(256) zt_planes_kernel(const uint16_t *__restrict__ ZN, int L, Planes Zt, ModP mp)
 {
@@ -989,8 +1071,10 @@ __global__ void __launch_bounds__(256) zt_planes_kernel(const uint16_t *__restri
 constexpr int LEAF_INV_SMEM = 2 * 128 * 129 * (int)sizeof(uint16_t);
 
 // ZN (nleaves L x L, allocated by the caller) <- the block inverses Z_J.
+// With use_tc the levels w >= 256 run as grouped tensor-core products
+// (err: the device status word of those products).
 static int block_inverses(const uint16_t *A, int64_t lda, const int32_t *rmap, const int32_t *cmap, int64_t n, int L,
-                          uint16_t *ZN, const ModP &mp, cudaStream_t s)
+                          uint16_t *ZN, const ModP &mp, bool use_tc, uint32_t *err, cudaStream_t s)
 {
     if (L < 128 || L % 128 || (L & (L - 1)) != 0) return GBLA_E_INTERNAL;
     const int64_t nleaves = (n + L - 1) / L;
@@ -1000,36 +1084,88 @@ static int block_inverses(const uint16_t *A, int64_t lda, const int32_t *rmap, c
                                            LEAF_INV_SMEM));
         attr = true;
     }
+    use_tc = use_tc && L >= 512 && mp.p >= 8 && tc_supported();
     uint16_t *T1 = nullptr;
+    int32_t *iota = nullptr;
+    GroupProb *probs = nullptr;
+    Planes Ap{}, Bp{};
+    const int64_t level_rows = nleaves * L / 2;   // rows of a level's operands, all pairs
     int rc = dalloc_t(&T1, (size_t)nleaves * L * L / 4 + 1, s);
     if (rc == GBLA_OK && cudaMemsetAsync(ZN, 0, sizeof(uint16_t) * (size_t)nleaves * L * L, s) != cudaSuccess)
         rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK && use_tc) {
+        const int64_t max_pairs = nleaves * (L / 512);   // at w = 256
+        rc = dalloc_t(&iota, (size_t)(nleaves * L), s);
+        if (rc == GBLA_OK) rc = dalloc_t(&probs, (size_t)(2 * (max_pairs + 1)), s);
+        if (rc == GBLA_OK) rc = planes_alloc(&Ap, level_rows, L / 2, 2, s);
+        if (rc == GBLA_OK) rc = planes_alloc(&Bp, level_rows, L / 2, 4, s);
+        if (rc == GBLA_OK) {
+            iota_kernel<<<(unsigned)((nleaves * L + 255) / 256), 256, 0, s>>>(iota, nleaves * L);
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+        }
+    }
     if (rc == GBLA_OK) {
         upper_inverse128_kernel<<<(unsigned)((n + 127) / 128), 128, LEAF_INV_SMEM, s>>>(A, lda, rmap, cmap, n, L, ZN,
                                                                                         mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
     for (int w = 128; rc == GBLA_OK && w < L; w *= 2) {
-        const dim3 grid((unsigned)(w / 64), (unsigned)(w / 64), (unsigned)(nleaves * (L / (2 * w))));
+        const int64_t npairs = nleaves * (L / (2 * w));
+        if (use_tc && w >= 256) {
+            const Planes Aw{Ap.ptr, npairs * w, w, 2}, Bw{Bp.ptr, npairs * w, w, 4};
+            GroupProb *pu = probs, *pz = probs + (npairs + 1);
+            const dim3 g((unsigned)(w / TP_TILE), (unsigned)(w / TP_TILE), (unsigned)npairs);
+            pair_probs_kernel<<<(unsigned)((npairs + 1 + 255) / 256), 256, 0, s>>>(npairs, w, L, iota, pu, pz);
+            if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+            if (rc == GBLA_OK) {
+                pair_planes_kernel<<<g, 256, 0, s>>>(0, w, L, A, lda, rmap, cmap, n, ZN, T1, Aw, mp);
+                if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+            }
+            if (rc == GBLA_OK) {
+                pair_planes_kernel<<<g, 256, 0, s>>>(1, w, L, A, lda, rmap, cmap, n, ZN, T1, Bw, mp);
+                if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+            }
+            if (rc == GBLA_OK &&
+                cudaMemsetAsync(T1, 0, sizeof(uint16_t) * (size_t)(npairs * w) * (size_t)w, s) != cudaSuccess)
+                rc = GBLA_E_CUDA;
+            if (rc == GBLA_OK)
+                rc = modgemm_grouped(Aw, Bw, pu, (int)npairs, w, T1, w, +1, mp, GBLA_GEMM_TCGEN05, err, s, nullptr);
+            if (rc == GBLA_OK) {
+                pair_planes_kernel<<<g, 256, 0, s>>>(2, w, L, A, lda, rmap, cmap, n, ZN, T1, Aw, mp);
+                if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+            }
+            if (rc == GBLA_OK) {
+                pair_planes_kernel<<<g, 256, 0, s>>>(3, w, L, A, lda, rmap, cmap, n, ZN, T1, Bw, mp);
+                if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+            }
+            if (rc == GBLA_OK)
+                rc = modgemm_grouped(Aw, Bw, pz, (int)npairs, w, ZN, L, -1, mp, GBLA_GEMM_TCGEN05, err, s, nullptr);
+            continue;
+        }
+        const dim3 grid((unsigned)(w / 64), (unsigned)(w / 64), (unsigned)npairs);
         tri_combine_kernel<<<grid, 256, 0, s>>>(0, w, L, A, lda, rmap, cmap, n, ZN, T1, mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         if (rc != GBLA_OK) break;
         tri_combine_kernel<<<grid, 256, 0, s>>>(1, w, L, A, lda, rmap, cmap, n, ZN, T1, mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
+    planes_free(&Ap, s);
+    planes_free(&Bp, s);
+    dfree(probs, s);
+    dfree(iota, s);
     dfree(T1, s);
     return rc;
 }
 
 int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
-                        cudaStream_t s)
+                        uint32_t *err, cudaStream_t s)
 {
     if (npiv <= 0) return GBLA_OK;
     const int64_t nleaves = (npiv + L - 1) / L;
     if (Zt.nplanes != 4 || Zt.kp != L || Zt.rows < nleaves * L) return GBLA_E_INTERNAL;
     uint16_t *ZN = nullptr;
     int rc = dalloc_t(&ZN, (size_t)nleaves * L * L, s);
-    if (rc == GBLA_OK) rc = block_inverses(A16, lda, nullptr, nullptr, npiv, L, ZN, mp, s);
+    if (rc == GBLA_OK) rc = block_inverses(A16, lda, nullptr, nullptr, npiv, L, ZN, mp, true, err, s);
     if (rc == GBLA_OK) {
         zt_planes_kernel<<<dim3((unsigned)(L / TP_TILE), (unsigned)(L / TP_TILE), (unsigned)nleaves), 256, 0, s>>>(
             ZN, L, Zt, mp);
@@ -1370,7 +1506,8 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         const int BL = E.back_leaf > 0 ? E.back_leaf : PANEL;
         const int64_t nleaves = (rank + BL - 1) / BL;
         if (rc == GBLA_OK && nnp > 0) rc = dalloc_t(&Nm, (size_t)nleaves * BL * BL, s);
-        if (rc == GBLA_OK && nnp > 0) rc = block_inverses(E.D16, E.ldd, E.prow, E.pcol, rank, BL, Nm, mp, s);
+        if (rc == GBLA_OK && nnp > 0)
+            rc = block_inverses(E.D16, E.ldd, E.prow, E.pcol, rank, BL, Nm, mp, E.variant != GBLA_GEMM_SIMT, E.err, s);
         if (rc == GBLA_OK && nnp > 0) {
             const int64_t total = nleaves * BL * BL;
             i_minus_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Nm, BL, total, mp.p);

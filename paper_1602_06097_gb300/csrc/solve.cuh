@@ -37,9 +37,11 @@ int trsm_upper(const TrsmUpper &T);
 // B-operand planes (4 planes, L * ceil(npiv / L) rows x L) of the inverses of
 // the unit upper triangular diagonal blocks A[J, J] of width L (a power of two,
 // multiple of 128) of A (dense uint16, lda): row L q + j, column k of Zt holds
-// (A_JJ^-1)[k][j] for block J = [L q, L q + L), zero outside A.
+// (A_JJ^-1)[k][j] for block J = [L q, L q + L), zero outside A.  For L >= 512
+// the wider levels of the inverses are tensor-core products (err: their
+// device status word).
 int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
-                        cudaStream_t s);
+                        uint32_t *err, cudaStream_t s);
 
 // X' * A^T = C' (A^T unit lower triangular), X' overwrites C'.
 struct TrsmLower {
