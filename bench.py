@@ -36,7 +36,7 @@ WORKLOAD = "fl_40000x60000"
 CPU_SAMPLE_ROWS = 1500
 
 
-def args_parse():
+def args_parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -52,7 +52,7 @@ def args_parse():
     ap.add_argument("--batch", type=int, default=32, help="matrices in the batched-vs-plain measurement")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (req/s)")
     ap.add_argument("--serve-requests", type=int, default=160)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -60,6 +60,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_workload(name, scale, rank):
+    """One rank's matrix: the named workload (scaled), with a seed of its own,
+    so that the ranks reduce independent matrices (weak scaling)."""
+    from paper_1602_06097_gb300 import synth
+    spec = synth.workload(name) if scale == 1.0 else synth.scaled(name, scale)
+    return dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
 
 
 # ------------------------------------------------------------------ clocks
@@ -285,8 +303,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     gbla.load()
-    spec = synth.workload(a.workload) if a.scale == 1.0 else synth.scaled(a.workload, a.scale)
-    spec = dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
+    spec = rank_workload(a.workload, a.scale, rank)
     rp, c, v = synth.fl_matrix(spec)
     m, n, p = spec.m, spec.n, spec.p
     d_rp = torch.from_numpy(rp).cuda()
@@ -319,11 +336,7 @@ def main():
         wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     ms_step = ms_total / a.steps
     value = world * a.steps / (ms_total / 1e3)
 
@@ -360,11 +373,7 @@ def main():
             _ = int(hr.row_ptr[-1]) + hr.rank
             hr.free()
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / k_e2e
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e, dist, "cuda")
         e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(rp.nbytes + c.nbytes + v.nbytes),
                "d2h_bytes_per_step": int(d2h)}
 
