@@ -9,7 +9,7 @@
  *   - want_reduced = 1: the reduced row echelon form RREF(M) (FL steps 1-5 and
  *     the second FL pass on the right block, Sec. 4.1), or
  *   - want_reduced = 0: the echelon form of the new order of operations
- *     (Alg. 2, Sec. 4.2): the chosen pivot rows of M normalised to a leading
+ *     (Alg. 2, Sec. 4.3): the chosen pivot rows of M normalised to a leading
  *     1, plus the reduced echelon form of the Schur complement D - C A^-1 B.
  * In both cases rows are sorted by pivot column (leftmost nonzero, always 1),
  * zero rows are dropped, and columns are back in the input (monomial) order

@@ -13,7 +13,7 @@ followed (GBLA paper, arXiv 1602.06097):
 
 * :func:`rref`     -- textbook Gauss-Jordan on the whole matrix: FL steps 4-5
   and the reduced-echelon pass (Sec. 4.1), Alg. 3's normalise/reduce rule.
-* :func:`echelon`  -- the new order of operations (Alg. 2, Sec. 4.2) in plain
+* :func:`echelon`  -- the new order of operations (Alg. 2, Sec. 4.3) in plain
   row form, then Gauss-Jordan of the Schur complement.
 * :func:`pivots`   -- the FL step-1 pivot choice (Sec. 3.1, Sec. 4.1 step 1).
 * :func:`multiline` -- the 2-multiline vector of Definition 1 (Sec. 4.2).

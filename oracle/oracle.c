@@ -18,7 +18,7 @@
  *                      in input order: FL steps 4-5 plus the reduced-echelon
  *                      pass (Sec. 4.1, the RREF remark after step 5), and
  *                      the "normalize, reduce by matching head" rule of
- *                      Alg. 3 (Sec. 4.3).  Output: the unique reduced row
+ *                      Alg. 3 (Sec. 4.4).  Output: the unique reduced row
  *                      echelon form of M, rows sorted by pivot column.
  *   oracle_pivots   -- FL step 1 pivot choice (Sec. 3.1, Sec. 4.1 step 1):
  *                      the leading (leftmost) nonzero of a row is its pivot
@@ -26,7 +26,7 @@
  *                      the one keeping A sparsest is chosen.  The paper does
  *                      not fix the tie-break; this oracle reads it as
  *                      (fewest nonzeros, then smallest input row index).
- *   oracle_echelon  -- the "new order of operations" (Alg. 2, Sec. 4.2) in
+ *   oracle_echelon  -- the "new order of operations" (Alg. 2, Sec. 4.3) in
  *                      plain row form: every non-pivot row is reduced by the
  *                      normalised pivot rows in ascending pivot column order
  *                      (this is C <- C*A^-1 with D <- D - C*A^-1*B applied on

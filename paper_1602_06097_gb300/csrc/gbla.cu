@@ -1,7 +1,7 @@
 // gbla.cu -- C ABI entry points and the host orchestration of one reduction.
 //
 // One call runs the whole Faugere-Lachartre reduction (GBLA paper Sec. 4.1,
-// new order of Sec. 4.2) on the caller's stream:
+// new order of Sec. 4.3) on the caller's stream:
 //   step 1  pivot analysis and split (split.cu)
 //   step 2' X = C * A^-1 by the blocked multiline solve (solve.cu)
 //   step 3' D <- D - X * B, exact tensor-core product (modgemm.cu)

@@ -1,7 +1,7 @@
 // modgemm.cu -- exact modular matrix product C <- (C + sign * A * B) mod p.
 //
 // This is the dense Schur update of the FL reduction, D <- D - C*A^-1*B
-// (GBLA paper Sec. 4.1 steps 2-3; Sec. 4.2 step 4 of the new order), and the
+// (GBLA paper Sec. 4.1 steps 2-3; Sec. 4.3 step 4 of the new order), and the
 // block updates of the triangular solves and of the echelonisation of D.
 //
 // Tensor-core path (sm_103a).  Residues are written in balanced form and

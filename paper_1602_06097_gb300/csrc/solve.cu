@@ -1,5 +1,5 @@
 // solve.cu -- the sparse reduction C <- C*A^-1 (new order of operations,
-// Alg. 2 and its four-step implementation, GBLA paper Sec. 4.2), the
+// Alg. 2 and its four-step implementation, GBLA paper Sec. 4.3), the
 // triangular solve A^-1*B of the second FL pass (Sec. 4.1 step 2 and the
 // reduced-echelon remark after step 5), and the echelonisation of the Schur
 // complement D' (Sec. 4.1 step 4, Alg. 3 / Sec. 5.1).
