@@ -5,7 +5,7 @@
  * m x n matrix over GF(p), p a prime < 2^16, stored as CSR with uint16
  * coefficients and int32 column indices, rows = polynomials, columns =
  * monomials in decreasing monomial order (the layout of the paper's binary
- * Format 1, Table 3).  The library returns either
+ * Format 1, Table 2).  The library returns either
  *   - want_reduced = 1: the reduced row echelon form RREF(M) (FL steps 1-5 and
  *     the second FL pass on the right block, Sec. 4.1), or
  *   - want_reduced = 0: the echelon form of the new order of operations

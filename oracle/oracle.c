@@ -426,7 +426,7 @@ fail0:
 }
 
 /*
- * Reference split of a matrix into the FL blocks (Sec. 4.1 step 1, Table 2),
+ * Reference split of a matrix into the FL blocks (Sec. 4.1 step 1, Table 4),
  * used only to pin the shapes of the split.  Outputs the pivot count and the
  * number of non-pivot non-empty rows.
  */

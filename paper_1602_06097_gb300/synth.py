@@ -5,7 +5,7 @@ arithmetic.  Both the CUDA path's tests/benchmarks and the CPU oracle's tests
 read their inputs from here.
 
 The shapes follow the statistics the GBLA paper gives for matrices out of F4
-and F5 symbolic preprocessing (Sec. 3.1, Sec. 4.2 and Tables 2 and 6): rows are
+and F5 symbolic preprocessing (Sec. 3.1, Sec. 4.2 and Tables 4 and 5): rows are
 polynomials, columns monomials in decreasing order; a row's leftmost nonzero
 is its pivoting candidate; many rows share a leading column; nonzeros come in
 horizontal runs of consecutive columns, and neighbouring rows repeat one
