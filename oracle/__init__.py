@@ -17,10 +17,13 @@ followed (GBLA paper, arXiv 1602.06097):
   row form, then Gauss-Jordan of the Schur complement.
 * :func:`pivots`   -- the FL step-1 pivot choice (Sec. 3.1, Sec. 4.1 step 1).
 * :func:`multiline` -- the 2-multiline vector of Definition 1 (Sec. 4.2).
+* :mod:`oracle.formats` -- readers of the two binary matrix files of Sec. 3.2
+  (Table 2) into the reduction's CSR input.
 
 Every function is pinned by ``tests/test_oracle.py`` against results fixed by
 the mathematics (brute-force row spaces, determinant ranks, closed forms,
-invariants) and, for :func:`multiline`, by the paper's Example 1.
+invariants) and, for :func:`multiline`, by the paper's Example 1; the file
+readers by ``tests/test_formats.py`` (files assembled by hand from Table 2).
 """
 from __future__ import annotations
 

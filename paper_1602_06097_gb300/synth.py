@@ -271,3 +271,75 @@ def csr_to_dense(m, n, row_ptr, col, val):
     rows = np.repeat(np.arange(m), np.diff(row_ptr))
     out[rows, np.asarray(col, np.int64)] = np.asarray(val, np.int64)
     return out
+
+
+# ------------------------------------------------------------- matrix files
+# Writers of the paper's two binary matrix files (Sec. 3.2, Table 2), used to
+# feed matrices to the file readers in tests: little-endian, fields in the
+# table's order.
+
+def encode_format1(m, n, p, row_ptr, col, val) -> bytes:
+    """Format 1: u32 m, n, p; u64 nnz; u16 data; u32 cols; u32 row lengths."""
+    row_ptr = np.asarray(row_ptr, np.int64)
+    nnz = int(row_ptr[-1])
+    parts = [np.array([m, n, p], "<u4").tobytes(), np.array([nnz], "<u8").tobytes(),
+             np.asarray(val, "<u2").tobytes(), np.asarray(col, "<u4").tobytes(),
+             np.diff(row_ptr).astype("<u4").tobytes()]
+    return b"".join(parts)
+
+
+_CODES = {"u1": (1, 0), "u2": (1, 1), "u4": (1, 2), "u8": (1, 3),
+          "i1": (0, 0), "i2": (0, 1), "i4": (0, 2), "i8": (0, 3)}
+
+
+def encode_format2(m, n, p, row_ptr, col, val, vtype=None) -> bytes:
+    """Format 2.  Rows whose coefficient sequences are equal share one
+    polynomial (numbered in order of first use); each row's columns are cut
+    into maximal runs of consecutive columns, a run of s >= 2 written as the
+    pair (first, s), a lone column c as c | 2^31.  ``vtype`` is a numpy type
+    code (default: the smallest unsigned type that holds p - 1); a signed type
+    stores the residues balanced, in (-p/2, p/2]."""
+    row_ptr = np.asarray(row_ptr, np.int64)
+    col = np.asarray(col, np.int64)
+    val = np.asarray(val, np.int64)
+    nnz = int(row_ptr[-1])
+    lengths = np.diff(row_ptr)
+    if vtype is None:
+        vtype = next(t for t, bits in (("u1", 8), ("u2", 16), ("u4", 32), ("u8", 64)) if p - 1 < 1 << bits)
+    u, v = _CODES[vtype]
+    b = u | (v << 1)
+    # polynomials
+    poly_of = {}
+    polmap = np.zeros(m, np.int64)
+    pdata, prow = [], []
+    for i in range(m):
+        key = val[row_ptr[i]:row_ptr[i + 1]].tobytes()
+        j = poly_of.get(key)
+        if j is None:
+            j = poly_of[key] = len(prow)
+            prow.append(int(lengths[i]))
+            pdata.append(val[row_ptr[i]:row_ptr[i + 1]])
+        polmap[i] = j
+    coeffs = np.concatenate(pdata) if pdata else np.zeros(0, np.int64)
+    if u == 0:
+        coeffs = np.where(coeffs > p // 2, coeffs - p, coeffs)
+    # column runs
+    rid = np.repeat(np.arange(m), lengths)
+    start = np.ones(nnz, bool)
+    if nnz:
+        start[1:] = (col[1:] != col[:-1] + 1) | (rid[1:] != rid[:-1])
+    first = np.nonzero(start)[0]
+    size = np.diff(np.append(first, nnz))
+    width = np.where(size > 1, 2, 1)
+    pos = np.concatenate([[0], np.cumsum(width)[:-1]]) if len(first) else np.zeros(0, np.int64)
+    colid = np.zeros(int(width.sum()), np.uint64)
+    single = size == 1
+    colid[pos[single]] = col[first[single]].astype(np.uint64) | np.uint64(1 << 31)
+    colid[pos[~single]] = col[first[~single]].astype(np.uint64)
+    colid[pos[~single] + 1] = size[~single].astype(np.uint64)
+    parts = [np.array([b, m, n], "<u4").tobytes(), np.array([p, nnz], "<u8").tobytes(),
+             lengths.astype("<u4").tobytes(), polmap.astype("<u4").tobytes(),
+             np.array([len(colid)], "<u8").tobytes(), colid.astype("<u8").tobytes(),
+             np.array([len(prow)], "<u4").tobytes(), np.array([len(coeffs)], "<u8").tobytes(),
+             np.asarray(prow, np.int64).astype("<u4").tobytes(), coeffs.astype("<" + vtype).tobytes()]
+    return b"".join(parts)
