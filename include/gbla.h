@@ -216,6 +216,23 @@ int gbla_selftest_wait_timeout(void *stream);
 int gbla_pivots_noalloc(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev,
                         int64_t *npiv, void *stream);
 
+/* Format 2 matrix file (Sec. 3.2, Table 2) -> device CSR input.  `file` is
+ * the whole file in host memory (borrowed, `bytes` long, little-endian):
+ * u32 b (bits 0-2: coefficient type u | v << 1, 8 * 2^v bits, u = 1 unsigned;
+ * the higher bits are a version and are ignored), u32 m, u32 n, u64 p,
+ * u64 nnz, u32 rows[m] (row lengths), u32 polmap[m] (row i carries the
+ * coefficients of polynomial polmap[i]), u64 k, u64 colid[k] (the rows'
+ * columns in order: a run of s >= 2 consecutive columns from f is the pair
+ * f, s, a lone column f is f | 2^31, runs never cross a row), u32 pnb,
+ * u64 pnnz, u32 prow[pnb] (polynomial lengths), pdata[pnnz] (the
+ * polynomials' coefficients in that type, signed ones taken mod p).  On
+ * success *out holds device arrays (on_device = 1, nrows = m; release with
+ * gbla_free) in the form gbla_reduce_ex takes, and *p the prime.  A file that
+ * breaks any of these rules, a column >= n, columns not increasing within a
+ * row, a coefficient that is 0 mod p, p outside [2, 2^16) or bytes after the
+ * last field gives GBLA_E_INVAL and *out zeroed.  Synchronises `stream`. */
+int gbla_decode_format2(const void *file, size_t bytes, void *stream, gbla_csr_out *out, uint32_t *p);
+
 #ifdef __cplusplus
 }
 #endif

@@ -224,7 +224,7 @@ bool is_prime(uint32_t p) {
     return true;
 }
 
-static int check_device() {
+int check_device() {
     int dev = 0, major = 0, minor = 0, n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
         cudaGetLastError();
@@ -238,7 +238,7 @@ static int check_device() {
     return GBLA_OK;
 }
 
-static int map_dev_err(uint32_t e) {
+int map_dev_err(uint32_t e) {
     if (e & DEV_ERR_TIMEOUT) return GBLA_E_TIMEOUT;
     if (e & DEV_ERR_INVAL) return GBLA_E_INVAL;
     if (e & DEV_ERR_INTERNAL) return GBLA_E_INTERNAL;

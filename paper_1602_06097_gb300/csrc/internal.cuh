@@ -29,6 +29,13 @@ struct GroupProb {
 // True on a device with the tcgen05 tensor-core path (compute capability 10.3).
 bool tc_supported();
 
+// GBLA_OK on a compute capability 10.3 device (and the memory pool set up),
+// else GBLA_E_UNSUPPORTED.
+int check_device();
+
+// GBLA_* code of a device status word (DEV_ERR_* bits).
+int map_dev_err(uint32_t e);
+
 // Device-to-host copy of `bytes` into pageable host memory `dst` through a
 // page-locked scratch buffer of the calling thread; synchronises stream s.
 int readback(void *dst, const void *src, size_t bytes, cudaStream_t s);

@@ -123,6 +123,9 @@ def load():
         lib.gbla_server_get_stats.restype = i32
         lib.gbla_server_destroy.argtypes = [vp]
         lib.gbla_server_destroy.restype = None
+        lib.gbla_decode_format2.argtypes = [ctypes.c_char_p, ctypes.c_size_t, vp, ctypes.POINTER(CsrOut),
+                                            ctypes.POINTER(u32)]
+        lib.gbla_decode_format2.restype = i32
         _lib = lib
         return lib
 
@@ -241,6 +244,28 @@ class DeviceResult:
             self.free()
         except Exception:
             pass
+
+
+class DecodedMatrix(DeviceResult):
+    """A matrix decoded on the device (owned by the library until free()):
+    m x n over GF(p); tensors() gives its row_ptr, col and val, the input
+    form of reduce_device."""
+
+    def __init__(self, out: CsrOut, p: int):
+        super().__init__(out, int(out.nrows), {})
+        self.m, self.n, self.p = int(out.nrows), int(out.ncols), int(p)
+
+
+def decode_format2(buf, stream=None) -> DecodedMatrix:
+    """Decode a Format 2 matrix file (bytes, Sec. 3.2 of the paper) on the
+    device; raises GblaError (GBLA_E_INVAL) on a malformed file."""
+    lib = load()
+    data = bytes(buf)
+    out = CsrOut()
+    p = ctypes.c_uint32(0)
+    rc = lib.gbla_decode_format2(data, len(data), _stream_ptr(stream), ctypes.byref(out), ctypes.byref(p))
+    _check(rc, "gbla_decode_format2")
+    return DecodedMatrix(out, p.value)
 
 
 class _CudaArray:
