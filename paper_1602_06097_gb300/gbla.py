@@ -21,7 +21,8 @@ GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT = 0, 1, 2
 EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
            "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc",
            "gbla_selftest_wait_timeout", "gbla_reduce_batch", "gbla_server_create", "gbla_server_submit",
-           "gbla_server_wait", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy"]
+           "gbla_server_wait", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy",
+           "gbla_decode_format2"]
 
 
 class CsrIn(ctypes.Structure):

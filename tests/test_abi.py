@@ -31,6 +31,14 @@ def test_library_builds_and_exports_every_symbol():
     assert set(gbla.EXPORTS) <= set(declared_symbols())
 
 
+def test_binding_covers_every_entry_point():
+    """The Python binding lists and declares every entry point of gbla.h."""
+    lib = gbla.load()
+    assert set(declared_symbols()) <= set(gbla.EXPORTS)
+    for name in gbla.EXPORTS:
+        assert getattr(lib, name).argtypes is not None, f"{name} has no declared argument types"
+
+
 def test_strerror_and_version():
     lib = gbla.load()
     assert lib.gbla_version() >= 100
