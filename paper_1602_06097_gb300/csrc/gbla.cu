@@ -67,9 +67,10 @@ void dfree(void *ptr, cudaStream_t s) {
 
 // Host results live in page-locked memory so that the device-to-host copy runs
 // at full link speed.  Pinning is expensive (the pages are locked one by one),
-// so released blocks are cached and handed to later results of a similar size;
-// at most GBLA_HOST_CACHE_MB (default 8192) megabytes stay cached.  A new
-// Blocks that cannot be pinned fall back to malloc.
+// so released blocks are cached and handed to later results of a similar size
+// (a block of 1 to 2 times the rounded request); at most GBLA_HOST_CACHE_MB
+// (default 8192) megabytes stay cached, the oldest evicted first.  Blocks that
+// cannot be pinned fall back to malloc.
 namespace {
 struct HostCache {
     std::mutex mu;
