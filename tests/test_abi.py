@@ -53,3 +53,81 @@ def test_invalid_prime_rejected_on_host():
     with pytest.raises(gbla.GblaError) as e:
         gbla.reduce(np.array([0, 1]), np.array([0]), np.array([1]), (1, 1), 65535)
     assert e.value.code == 1
+
+
+def _csr_in(m, n, nnz, rp=None, col=None, val=None):
+    return gbla.CsrIn(m, n, nnz, rp, col, val)
+
+
+@pytest.mark.parametrize("case", ["p not prime", "p too large", "p one", "negative rows", "entries without arrays",
+                                  "rows without pointers", "bad product variant"])
+def test_reduce_arguments_rejected_on_host(case):
+    """The boundary's argument checks run on the host, before any device call:
+    each bad argument gives GBLA_E_INVAL and a zeroed result."""
+    import ctypes
+    lib = gbla.load()
+    import numpy as np
+    rp = np.array([0, 1], np.int64)
+    p, cin, variant = 65521, _csr_in(1, 1, 1, rp.ctypes.data, rp.ctypes.data, rp.ctypes.data), 0
+    if case == "p not prime":
+        p = 65535
+    elif case == "p too large":
+        p = 65537
+    elif case == "p one":
+        p = 1
+    elif case == "negative rows":
+        cin = _csr_in(-1, 1, 0)
+    elif case == "entries without arrays":
+        cin = _csr_in(1, 1, 1, rp.ctypes.data, None, None)
+    elif case == "rows without pointers":
+        cin = _csr_in(3, 1, 0, None, None, None)
+    else:
+        variant = 7
+    out = gbla.CsrOut()
+    out.nnz = 99
+    rank = ctypes.c_int64(5)
+    opt = gbla.Options(0, variant, 0, 0)
+    rc = lib.gbla_reduce_ex(ctypes.byref(cin), p, ctypes.byref(opt), None, ctypes.byref(out), ctypes.byref(rank), None)
+    assert rc == 1
+    assert out.nnz == 0 and not out.row_ptr
+
+
+def test_batch_and_server_arguments_rejected_on_host():
+    import ctypes
+    lib = gbla.load()
+    assert lib.gbla_reduce_batch(-1, None, None, None, 0, None, None, None) == 1
+    assert lib.gbla_reduce_batch(0, None, None, None, 0, None, None, None) == 0
+    assert lib.gbla_server_create(0, 1, None) == 1
+    assert lib.gbla_server_cancel(None, 1) == 1
+
+
+def _format2_rc(buf):
+    import ctypes
+    lib = gbla.load()
+    out = gbla.CsrOut()
+    p = ctypes.c_uint32(0)
+    return lib.gbla_decode_format2(buf, len(buf), None, ctypes.byref(out), ctypes.byref(p)), out
+
+
+def test_format2_header_checks_on_host():
+    """The decoder checks the file's fixed fields and section sizes on the host;
+    a well-formed file then reaches the device check (GBLA_E_UNSUPPORTED on a
+    machine without an sm_103a GPU)."""
+    import struct
+    from test_formats import hand_format2
+    good = hand_format2(1, 251, "B", [5, 6, 7, 9, 3, 250])
+    bad = [good[:10], good[:-1], good + b"\0",
+           good[:12] + struct.pack("<Q", 1 << 16) + good[20:],          # p = 2^16
+           good[:12] + struct.pack("<Q", 1) + good[20:],                # p = 1
+           good[:52] + struct.pack("<Q", 1 << 40) + good[60:]]          # k far past the file
+    for buf in bad:
+        rc, out = _format2_rc(buf)
+        assert rc == 1 and out.nnz == 0 and not out.row_ptr
+    rc, _ = _format2_rc(good)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:
+        assert rc == 6
