@@ -1,8 +1,10 @@
 """The device decoder of Format 2 files (Sec. 3.2) against the oracle reader,
 and the decoded matrix through the reduction.
 
-Skipped until the decoder has run on a GB300: its parallel algorithm is
-checked on the CPU (test_format2_parallel_model.py), the CUDA code is not.
+The decoder's parallel algorithm is also checked on the CPU
+(test_format2_parallel_model.py).  The cases marked "not yet run on a GPU"
+(32-bit unsigned and 64-bit signed coefficients, a decoded matrix reduced in
+place) stay skipped until a GB300 run has passed them.
 """
 import numpy as np
 import pytest
@@ -11,9 +13,13 @@ import oracle
 from oracle import formats as F
 from paper_1602_06097_gb300 import gbla, synth
 
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="device decoder not yet run on a GB300")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+NOT_YET = pytest.mark.skip(reason="not yet run on a GPU")
 
 
 def decoded(buf):
@@ -31,7 +37,7 @@ def same(a, b):
         assert np.array_equal(np.asarray(x, np.int64), np.asarray(y, np.int64))
 
 
-@pytest.mark.parametrize("vtype", [None, "u4", "i2", "i8"])
+@pytest.mark.parametrize("vtype", [None, "i2", pytest.param("u4", marks=NOT_YET), pytest.param("i8", marks=NOT_YET)])
 def test_decoder_equals_oracle_reader(vtype):
     spec = synth.workload("fl_2000x3000")
     rp, c, v = synth.fl_matrix(spec)
@@ -60,6 +66,7 @@ def test_decoder_rejects_malformed_files():
             gbla.decode_format2(buf)
 
 
+@NOT_YET
 def test_decoded_matrix_reduces_like_the_file():
     spec = synth.workload("fl_2000x3000")
     rp, c, v = synth.fl_matrix(spec)
