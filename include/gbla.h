@@ -209,10 +209,13 @@ int gbla_selftest_wait_timeout(void *stream);
  * CSR in, device piv_row[ncols] out, *npiv on the host), but its only scratch
  * is a fixed 8 MiB device array inside the library, held by every GPU that
  * loads the library until the process exits.  ncols above 1,048,576 (2^20)
- * is rejected with GBLA_E_INVAL.  The first call on a device looks up that
- * array's device address; make that first call before any stream capture.
- * All calls share the array (each clears what it uses), so calls that
- * overlap on the GPU race: serialise them.  Synchronises `stream`. */
+ * is rejected with GBLA_E_INVAL; so is a malformed CSR, in which case
+ * piv_row is left unwritten.  The first call on a device (and the first after
+ * its context was recreated, e.g. by cudaDeviceReset) looks up that array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array (each clears what it uses), so calls that overlap on the
+ * GPU race: serialise them.  GBLA_E_UNSUPPORTED without a compute capability
+ * 10.3 device.  Synchronises `stream`. */
 int gbla_pivots_noalloc(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_dev,
                         int64_t *npiv, void *stream);
 

@@ -74,7 +74,8 @@ def _lib(mutant: int = 0):
         lib.oracle_echelon.restype = ctypes.c_int
         lib.oracle_echelon.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, vp, vp, vp,
                                        i64p, ctypes.POINTER(i64p), ctypes.POINTER(i32p),
-                                       ctypes.POINTER(u16p), i64p, ctypes.POINTER(ctypes.c_double)]
+                                       ctypes.POINTER(u16p), i64p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
         lib.oracle_pivots.restype = ctypes.c_int64
         lib.oracle_pivots.argtypes = [ctypes.c_int64, ctypes.c_int64, vp, vp, vp]
         lib.oracle_free.restype = None
@@ -120,11 +121,16 @@ def rref(m, n, p, row_ptr, col, val, mutant: int = 0):
     return _take(lib, rank, rp, cl, vl)
 
 
-def echelon(m, n, p, row_ptr, col, val, mutant: int = 0, phase_seconds=None):
+def echelon(m, n, p, row_ptr, col, val, mutant: int = 0, phase_seconds=None, ops=None):
     """Canonical echelon form (normalised pivot rows + RREF of the Schur
     complement): returns (rank, row_ptr, col, val, npiv).  If
     ``phase_seconds`` is a list it receives the wall times of the row
-    reduction by the pivot rows and of the Gauss-Jordan pass."""
+    reduction by the pivot rows and of the Gauss-Jordan pass.  If ``ops`` is
+    a list it receives the work counts [ops_b, ops_c, ops_d, ops_e] in
+    modular multiply-adds with a nonzero operand entry: the sparse C*A^-1
+    (Alg. 2), the Schur update, the Gauss-Jordan pass on the Schur
+    complement, and the back-substitution of the top block (0 in this
+    form)."""
     lib = _lib(mutant)
     row_ptr, col, val = _csr_args(row_ptr, col, val)
     rank = ctypes.c_int64(0)
@@ -133,11 +139,14 @@ def echelon(m, n, p, row_ptr, col, val, mutant: int = 0, phase_seconds=None):
     cl = ctypes.POINTER(ctypes.c_int32)()
     vl = ctypes.POINTER(ctypes.c_uint16)()
     secs = (ctypes.c_double * 2)()
+    counts = (ctypes.c_double * 4)()
     rc = lib.oracle_echelon(m, n, p, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
                             ctypes.byref(rank), ctypes.byref(rp), ctypes.byref(cl),
-                            ctypes.byref(vl), ctypes.byref(npiv), secs)
+                            ctypes.byref(vl), ctypes.byref(npiv), secs, counts)
     if phase_seconds is not None:
         phase_seconds[:] = [secs[0], secs[1]]
+    if ops is not None:
+        ops[:] = [counts[i] for i in range(4)]
     if rc != 0:
         raise OracleError(f"oracle_echelon failed with code {rc}")
     return _take(lib, rank, rp, cl, vl) + (int(npiv.value),)

@@ -103,6 +103,7 @@ typedef struct {
     int64_t n, count, cap;
     uint32_t *rows;   /* count x n */
     int64_t *pcol;    /* pivot column of each row */
+    int64_t *nz;      /* nonzero entries of each row */
 } ora_rows;
 
 static int ora_rows_push(ora_rows *R, const uint64_t *w, int64_t pc)
@@ -115,11 +116,19 @@ static int ora_rows_push(ora_rows *R, const uint64_t *w, int64_t pc)
         int64_t *np = (int64_t *)realloc(R->pcol, (size_t)nc * sizeof(int64_t));
         if (!np) return ORA_E_NOMEM;
         R->pcol = np;
+        int64_t *nzp = (int64_t *)realloc(R->nz, (size_t)nc * sizeof(int64_t));
+        if (!nzp) return ORA_E_NOMEM;
+        R->nz = nzp;
         R->cap = nc;
     }
     uint32_t *dst = R->rows + (size_t)R->count * (size_t)R->n;
-    for (int64_t k = 0; k < R->n; ++k) dst[k] = (uint32_t)w[k];
+    int64_t nz = 0;
+    for (int64_t k = 0; k < R->n; ++k) {
+        dst[k] = (uint32_t)w[k];
+        nz += dst[k] != 0;
+    }
     R->pcol[R->count] = pc;
+    R->nz[R->count] = nz;
     R->count++;
     return ORA_OK;
 }
@@ -141,14 +150,20 @@ static int ora_rows_push(ora_rows *R, const uint64_t *w, int64_t pc)
  *
  * `in` holds `m_in` dense input rows of width n with entries in [0,p).
  * Result rows (sorted by pivot column, entries in [0,p)) go to *out.
+ *
+ * Work counter (optional): *ops is increased by the number of modular
+ * multiply-adds with a nonzero pivot-row entry, pivot entry excluded: one
+ * subtraction of a multiple of row P adds nnz(P) - 1, in the forward pass
+ * and in the backward pass alike.
  */
 static int ora_gauss_jordan(int64_t n, uint32_t p, int64_t m_in,
-                            const uint32_t *in, ora_rows *out)
+                            const uint32_t *in, ora_rows *out, double *ops)
 {
+    double work = 0;
     int rc = ORA_OK;
     int64_t *pivot_of = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
     uint64_t *w = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
-    ora_rows E = {n, 0, 0, NULL, NULL};
+    ora_rows E = {n, 0, 0, NULL, NULL, NULL};
     if (!pivot_of || !w) { rc = ORA_E_NOMEM; goto done; }
     for (int64_t j = 0; j < n; ++j) pivot_of[j] = -1;
 
@@ -160,6 +175,7 @@ static int ora_gauss_jordan(int64_t n, uint32_t p, int64_t m_in,
             if (f == 0) continue;
             if (pivot_of[j] >= 0) {
                 const uint32_t *P = E.rows + (size_t)pivot_of[j] * (size_t)n;
+                work += (double)(E.nz[pivot_of[j]] - 1);
                 uint64_t g = p - f;            /* subtract f * P */
 #if ORACLE_MUTANT == 1
                 g = f;                          /* planted: wrong sign */
@@ -193,13 +209,19 @@ static int ora_gauss_jordan(int64_t n, uint32_t p, int64_t m_in,
                 uint64_t f = w[c] % p;
                 if (f == 0) continue;
                 const uint32_t *P = E.rows + (size_t)order[b] * (size_t)n;
+                work += (double)(E.nz[order[b]] - 1);
                 uint64_t g = p - f;
 #if ORACLE_MUTANT == 2
                 if (b == a + 1) continue;       /* planted: dropped term */
 #endif
                 for (int64_t k = c; k < n; ++k) w[k] += g * P[k];
             }
-            for (int64_t k = qc; k < n; ++k) Q[k] = (uint32_t)(w[k] % p);
+            int64_t nz = 0;
+            for (int64_t k = qc; k < n; ++k) {
+                Q[k] = (uint32_t)(w[k] % p);
+                nz += Q[k] != 0;
+            }
+            E.nz[order[a]] = nz;
         }
         /* Emit in ascending pivot column order. */
         for (int64_t a = 0; a < r; ++a) {
@@ -210,10 +232,12 @@ static int ora_gauss_jordan(int64_t n, uint32_t p, int64_t m_in,
         free(order);
     }
 done:
+    if (ops) *ops += work;
     free(pivot_of);
     free(w);
     free(E.rows);
     free(E.pcol);
+    free(E.nz);
     return rc;
 }
 
@@ -257,13 +281,14 @@ int oracle_rref(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
     for (int64_t i = 0; i < m; ++i)
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
             dense[(size_t)i * (size_t)n + (size_t)col[e]] = val[e];
-    ora_rows R = {n, 0, 0, NULL, NULL};
-    rc = ora_gauss_jordan(n, p, m, dense, &R);
+    ora_rows R = {n, 0, 0, NULL, NULL, NULL};
+    rc = ora_gauss_jordan(n, p, m, dense, &R, NULL);
     free(dense);
     if (rc == ORA_OK) rc = ora_rows_to_csr(&R, out_row_ptr, out_col, out_val);
     if (rc == ORA_OK) *rank = R.count;
     free(R.rows);
     free(R.pcol);
+    free(R.nz);
     return rc;
 }
 
@@ -302,11 +327,23 @@ int64_t oracle_pivots(int64_t m, int64_t n, const int64_t *row_ptr, const int32_
 int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
                    const int32_t *col, const uint16_t *val, int64_t *rank,
                    int64_t **out_row_ptr, int32_t **out_col, uint16_t **out_val,
-                   int64_t *npiv_out, double *seconds)
+                   int64_t *npiv_out, double *seconds, double *ops)
 {
     /* seconds (optional, 2 entries): wall time of the row reduction by the
-     * pivot rows, and of the Gauss-Jordan pass on the Schur complement. */
+     * pivot rows, and of the Gauss-Jordan pass on the Schur complement.
+     * ops (optional, 4 entries): modular multiply-adds with a nonzero operand
+     * entry, counted as the work is done (one op = one multiply-add):
+     *   [0] ops_b: a non-pivot row reduced by pivot row j (x_j != 0) does
+     *       one per entry of that row at the other pivot columns -- the
+     *       sparse C <- C*A^-1 (Alg. 2);
+     *   [1] ops_c: ... and one per entry at the non-pivot columns -- the
+     *       Schur update D <- D - X*B;
+     *   [2] ops_d: the Gauss-Jordan pass on the Schur complement (forward
+     *       and backward, nnz(P) - 1 per row subtraction);
+     *   [3] ops_e: the back-substitution of the top block, 0 here (this
+     *       form keeps the pivot rows as they are). */
     double t0 = ora_now(), t1 = t0;
+    double ops_b = 0, ops_c = 0, ops_d = 0;
     int rc = ora_validate(m, n, p, row_ptr, col, val);
     if (rc) return rc;
     int64_t *piv_row = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
@@ -319,6 +356,17 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
             is_piv_row[piv_row[c]] = 1;
             inv_lead[c] = ora_inv(val[row_ptr[piv_row[c]]], p);
         }
+    /* entries of each pivot row at other pivot columns (na) and at the
+     * non-pivot columns (nb), for the work counter */
+    int64_t *na = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+    int64_t *nb = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+    if (!na || !nb) { free(na); free(nb); rc = ORA_E_NOMEM; goto fail0; }
+    for (int64_t c = 0; c < n; ++c)
+        if (piv_row[c] >= 0)
+            for (int64_t e = row_ptr[piv_row[c]] + 1; e < row_ptr[piv_row[c] + 1]; ++e) {
+                if (piv_row[col[e]] >= 0) na[c]++;
+                else nb[c]++;
+            }
 
     /* Non-pivot, non-empty rows in input order. */
     int64_t mcd = 0;
@@ -326,7 +374,7 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
         if (!is_piv_row[i] && row_ptr[i + 1] > row_ptr[i]) mcd++;
     int64_t *cd_rows = (int64_t *)malloc((size_t)(mcd ? mcd : 1) * sizeof(int64_t));
     uint32_t *left = (uint32_t *)calloc((size_t)(mcd ? mcd : 1) * (size_t)(n ? n : 1), sizeof(uint32_t));
-    if (!cd_rows || !left) { free(cd_rows); free(left); rc = ORA_E_NOMEM; goto fail0; }
+    if (!cd_rows || !left) { free(cd_rows); free(left); free(na); free(nb); rc = ORA_E_NOMEM; goto fail0; }
     mcd = 0;
     for (int64_t i = 0; i < m; ++i)
         if (!is_piv_row[i] && row_ptr[i + 1] > row_ptr[i]) cd_rows[mcd++] = i;
@@ -336,7 +384,7 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
      * columns are cleared, since the pivot rows are zero left of their
      * leading column).  Rows are independent of one another. */
     int fail = 0;
-#pragma omp parallel
+#pragma omp parallel reduction(+ : ops_b, ops_c)
     {
         uint64_t *w = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
         if (!w) {
@@ -356,6 +404,8 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
                 /* multiplier of the normalised pivot row = f; the pivot row
                  * holds val * inv_lead, so subtract (f * inv_lead) * val. */
                 int64_t r = piv_row[j];
+                ops_b += (double)na[j];
+                ops_c += (double)nb[j];
                 uint64_t g = (p - f) * inv_lead[j] % p;
                 for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
                     w[col[e]] += g * val[e];
@@ -365,15 +415,18 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
         }
         free(w);
     }
+    free(na);
+    free(nb);
     if (fail) { free(cd_rows); free(left); rc = ORA_E_NOMEM; goto fail0; }
 
     t1 = ora_now();
-    ora_rows B = {n, 0, 0, NULL, NULL};
-    rc = ora_gauss_jordan(n, p, mcd, left, &B);
+    ora_rows B = {n, 0, 0, NULL, NULL, NULL};
+    rc = ora_gauss_jordan(n, p, mcd, left, &B, &ops_d);
+    if (ops) { ops[0] = ops_b; ops[1] = ops_c; ops[2] = ops_d; ops[3] = 0; }
     if (seconds) { seconds[0] = t1 - t0; seconds[1] = ora_now() - t1; }
     free(left);
     free(cd_rows);
-    if (rc) { free(B.rows); free(B.pcol); goto fail0; }
+    if (rc) { free(B.rows); free(B.pcol); free(B.nz); goto fail0; }
 
     /* Merge: top rows (pivot columns of A) and bottom rows (pivots of D'). */
     {
@@ -388,7 +441,7 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
         uint16_t *vl = (uint16_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint16_t));
         int64_t *bottom_of = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
         if (!rp || !cl || !vl || !bottom_of) {
-            free(rp); free(cl); free(vl); free(bottom_of); free(B.rows); free(B.pcol);
+            free(rp); free(cl); free(vl); free(bottom_of); free(B.rows); free(B.pcol); free(B.nz);
             rc = ORA_E_NOMEM; goto fail0;
         }
         for (int64_t c = 0; c < n; ++c) bottom_of[c] = -1;
@@ -414,6 +467,7 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
         free(bottom_of);
         free(B.rows);
         free(B.pcol);
+        free(B.nz);
         *out_row_ptr = rp; *out_col = cl; *out_val = vl;
         *rank = r;
         if (npiv_out) *npiv_out = npiv;
@@ -423,22 +477,4 @@ fail0:
     free(inv_lead);
     free(is_piv_row);
     return rc;
-}
-
-/*
- * Reference split of a matrix into the FL blocks (Sec. 4.1 step 1, Table 4),
- * used only to pin the shapes of the split.  Outputs the pivot count and the
- * number of non-pivot non-empty rows.
- */
-int oracle_split_shape(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
-                       int64_t *npiv, int64_t *m_cd)
-{
-    int64_t *piv_row = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
-    if (!piv_row) return ORA_E_NOMEM;
-    *npiv = oracle_pivots(m, n, row_ptr, col, piv_row);
-    int64_t cnt = 0;
-    for (int64_t i = 0; i < m; ++i) if (row_ptr[i + 1] > row_ptr[i]) cnt++;
-    *m_cd = cnt - *npiv;
-    free(piv_row);
-    return ORA_OK;
 }

@@ -13,6 +13,8 @@
 // each call clears the part it uses before using it.  Two calls that
 // overlap on the GPU (different streams, or different host threads) use the
 // same array and race; callers must serialise them.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <mutex>
 
 #include "common.cuh"
@@ -31,14 +33,35 @@ namespace {
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 unsigned long long *g_scratch_ptr[MAX_DEVICES] = {};
+CUcontext g_scratch_ctx[MAX_DEVICES] = {};
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+std::once_flag g_ctx_once;
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device address).
+// Device address of the scratch array on the current device, looked up at
+// set-up: once per device and context (host code cannot use the symbol itself
+// as a device address).  A context that was destroyed and recreated on the
+// device (cudaDeviceReset) reloads the library's module, which may place the
+// array elsewhere, so the address is looked up again for the new context.
 int scratch_for_current_device(unsigned long long **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return GBLA_E_CUDA;
+    std::call_once(g_ctx_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+    });
+    // make the device's primary context current (cudaSetDevice initialises
+    // it; nothing is allocated)
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GBLA_E_CUDA;
+    }
+    CUcontext ctx = nullptr;
+    if (!g_ctx_current || g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return GBLA_E_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void *ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) {
@@ -46,9 +69,24 @@ int scratch_for_current_device(unsigned long long **out) {
             return GBLA_E_CUDA;
         }
         g_scratch_ptr[dev] = static_cast<unsigned long long *>(ptr);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return GBLA_OK;
+}
+
+// GBLA_OK on a compute capability 10.3 device (the only target of this
+// build), without touching any memory pool.
+int device_is_sm103() {
+    int dev = 0, major = 0, minor = 0, n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return GBLA_E_UNSUPPORTED;
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess) return GBLA_E_CUDA;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return (major == 10 && minor == 3) ? GBLA_OK : GBLA_E_UNSUPPORTED;
 }
 
 __global__ void noalloc_clear_kernel(unsigned long long *scratch, int64_t n) {
@@ -83,7 +121,11 @@ __global__ void noalloc_scan_rows_kernel(int64_t m, int64_t n, int64_t nnz, cons
         atomicMin(&scratch[col[b]], ((unsigned long long)(e - b) << 32) | (unsigned long long)r);
 }
 
+// piv_row is written only if every row was valid (the error word is still
+// zero once the scan kernel has finished), so on GBLA_E_INVAL the caller's
+// array is left as it was.
 __global__ void noalloc_finish_kernel(int64_t n, unsigned long long *scratch, int64_t *piv_row) {
+    if (*(volatile unsigned long long *)&scratch[NOALLOC_MAX_COLS + 1] != 0ull) return;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long k = scratch[c];
         piv_row[c] = (k == ~0ull) ? -1 : (int64_t)(k & 0xFFFFFFFFull);
@@ -109,6 +151,7 @@ extern "C" int gbla_pivots_noalloc(const gbla_csr_in *in_dev, uint32_t p, int64_
     if (m < 0 || n < 0 || nnz < 0 || m >= (int64_t(1) << 31)) return GBLA_E_INVAL;
     if (n > NOALLOC_MAX_COLS) return GBLA_E_INVAL;   // beyond the fixed scratch size
     if ((m > 0 && !in_dev->row_ptr) || (nnz > 0 && (!in_dev->col || !in_dev->val))) return GBLA_E_INVAL;
+    GBLA_TRY(device_is_sm103());
     unsigned long long *scratch = nullptr;
     GBLA_TRY(scratch_for_current_device(&scratch));
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -431,17 +431,52 @@ def pivots(row_ptr, col, val, shape, p, stream=None):
     return out[:n], int(npiv.value)
 
 
+def _check_noalloc_args(row_ptr, col, val, m, n, out):
+    """The library writes n int64 values through ``out`` and reads the CSR
+    through the other pointers without knowing their sizes, so every tensor
+    is checked here: contiguous CUDA tensors of the right type and length,
+    all on one device."""
+    import torch
+    named = (("row_ptr", row_ptr, (torch.int64,)), ("col", col, (torch.int32,)),
+             ("val", val, (torch.int16, getattr(torch, "uint16", torch.int16))), ("out", out, (torch.int64,)))
+    for name, t, dtypes in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} has dtype {t.dtype}, expected {dtypes[0]}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if m < 0 or n < 0:
+        raise ValueError("negative shape")
+    if row_ptr.numel() != m + 1:
+        raise ValueError(f"row_ptr has {row_ptr.numel()} entries, expected m + 1 = {m + 1}")
+    if val.numel() != col.numel():
+        raise ValueError("col and val differ in length")
+    if out.numel() < n:
+        raise ValueError(f"out has {out.numel()} entries, expected at least ncols = {n}")
+    for name, t, _ in named:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device != out.device:
+            raise ValueError(f"{name} is on {t.device}, out on {out.device}")
+
+
 def pivots_noalloc(row_ptr, col, val, shape, p, out, stream=None):
     """Pivot choice without any allocation in the library: writes piv_row into
     the caller's int64 CUDA tensor ``out`` (at least ncols long) and returns
     npiv.  For callers that must not allocate device memory during a call;
-    at most 2^20 columns; calls that overlap on the GPU race."""
-    lib = load()
+    at most 2^20 columns; calls that overlap on the GPU race.  The tensors
+    are checked (ValueError) before the library sees them; the call runs with
+    ``out``'s device current."""
+    import torch
     m, n = int(shape[0]), int(shape[1])
+    _check_noalloc_args(row_ptr, col, val, m, n, out)
+    lib = load()
     cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
     npiv = ctypes.c_int64(0)
-    rc = lib.gbla_pivots_noalloc(ctypes.byref(cin), int(p), out.data_ptr(), ctypes.byref(npiv),
-                                 _stream_ptr(stream))
+    with torch.cuda.device(out.device):
+        rc = lib.gbla_pivots_noalloc(ctypes.byref(cin), int(p), out.data_ptr(), ctypes.byref(npiv),
+                                     _stream_ptr(stream))
     _check(rc, "gbla_pivots_noalloc")
     return int(npiv.value)
 

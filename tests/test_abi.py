@@ -131,3 +131,30 @@ def test_format2_header_checks_on_host():
         has_gpu = False
     if not has_gpu:
         assert rc == 6
+
+
+def test_noalloc_binding_checks_its_tensors_before_the_library():
+    """pivots_noalloc hands raw pointers to a library that writes ncols int64
+    values through ``out``: wrong types, lengths, layouts and host tensors
+    are rejected in Python (no GPU needed)."""
+    torch = pytest.importorskip("torch")
+    rp = torch.tensor([0, 1, 2], dtype=torch.int64)
+    col = torch.tensor([0, 1], dtype=torch.int32)
+    val = torch.tensor([1, 1], dtype=torch.int16)
+    out = torch.empty(3, dtype=torch.int64)
+    bad = [
+        dict(out=torch.empty(2, dtype=torch.int64)),                 # shorter than ncols
+        dict(out=torch.empty(3, dtype=torch.int32)),                 # wrong dtype
+        dict(out=torch.empty(6, dtype=torch.int64)[::2]),            # not contiguous
+        dict(row_ptr=torch.tensor([0, 2], dtype=torch.int64)),       # m + 1 entries expected
+        dict(col=torch.tensor([0, 1], dtype=torch.int64)),           # int32 columns expected
+        dict(val=torch.tensor([1, 1], dtype=torch.int32)),           # 16-bit values expected
+        dict(val=torch.tensor([1], dtype=torch.int16)),              # col and val differ
+        dict(row_ptr=[0, 1, 2]),                                     # not a tensor
+        dict(),                                                      # host tensors
+    ]
+    for change in bad:
+        args = dict(row_ptr=rp, col=col, val=val, out=out)
+        args.update(change)
+        with pytest.raises(ValueError):
+            gbla.pivots_noalloc(args["row_ptr"], args["col"], args["val"], (2, 3), 7, args["out"])
