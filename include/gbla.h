@@ -73,11 +73,22 @@ typedef struct {
 #define GBLA_GEMM_TCGEN05 1  /* bf16 8-bit digits on tcgen05.mma, fp32 TMEM accumulators */
 #define GBLA_GEMM_SIMT 2     /* exact int64 CUDA-core kernel (reference variant) */
 
+/* How C*A^-1 and the Schur update treat the pivot rows (Sec. 4.1, Table 4's
+ * block densities). */
+#define GBLA_PATH_AUTO 0    /* sparse where the tensor-core path applies, else dense */
+#define GBLA_PATH_DENSE 1   /* A and B materialised densely, dense tensor-core products */
+#define GBLA_PATH_SPARSE 2  /* A and B kept sparse: products with K compacted per
+                               128-column tile to the rows that meet it (needs
+                               the tensor-core variant, p >= 8) */
+
 typedef struct {
     int want_reduced;  /* 1: RREF(M); 0: echelon form of the new order */
     int gemm_variant;  /* GBLA_GEMM_* for every dense modular product */
     int device_ptrs;   /* 1: input and output arrays live on the device */
     int panel_width;   /* column panel of the D echelonisation, 0 = default (128) */
+    int path;          /* GBLA_PATH_* */
+    int leaf_width;    /* leaf columns of the triangular solve: 0 = chosen per matrix,
+                          else 128, 256, 512 or 1024 */
 } gbla_options;
 
 /* Per-call statistics (optional out-parameter). */
@@ -91,6 +102,10 @@ typedef struct {
     int64_t launches;  /* CUDA kernels launched by the call */
     double schur_mod_ops; /* the same for the Schur update D <- D - X*B alone */
     double ms_echelon_back; /* part of ms_echelon: the backward pass (RREF rows from the echelon form) */
+    int64_t path;      /* GBLA_PATH_DENSE or GBLA_PATH_SPARSE: the path taken */
+    int64_t list_a, list_b; /* sparse path: compacted K entries (all tiles) of A's
+                               off-diagonal blocks and of B */
+    int64_t leaf_width;     /* leaf columns of the triangular solve */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */
@@ -173,6 +188,23 @@ int gbla_version(void);
 int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t lda,
                    const uint16_t *B, int64_t ldb, uint16_t *C, int64_t ldc,
                    uint32_t p, int sign, int variant, void *stream);
+
+/* Sparse-path product (the Schur update D <- D - X*B of the new order,
+ * Sec. 4.3, with B kept sparse as in Table 4):
+ *     C <- (C + sign * X * S) mod p
+ * X: M x K dense row-major uint16 (device, leading dimension ldx), entries in
+ * [0, p); S: K x N sparse CSR on the device (int64 row_ptr[K+1], int32 col
+ * strictly increasing per row, uint16 val in [1, p)); C: M x N dense
+ * row-major uint16 (device, ldc).  x_lead (device, may be NULL): ascending
+ * index of each X row's first nonzero column (X must be zero left of it); a
+ * 128-row tile then skips the rows of S left of its first row's lead.  S is
+ * compacted per 128-column tile to the rows that meet the tile, and the
+ * product runs on the tensor cores with that compacted K.  A malformed S
+ * gives GBLA_E_INVAL (C untouched); p < 8 gives GBLA_E_UNSUPPORTED.  Scratch
+ * is allocated on `stream` and released before return; synchronises
+ * `stream`. */
+int gbla_spmm(int64_t M, int64_t N, int64_t K, const uint16_t *X, int64_t ldx, const gbla_csr_in *S_dev,
+              const int32_t *x_lead, uint16_t *C, int64_t ldc, uint32_t p, int sign, void *stream);
 
 /* FL step 1 pivot analysis on device memory (Sec. 3.1, Sec. 4.1 step 1):
  * validates the CSR (device pointers), and writes for every column c

@@ -444,8 +444,10 @@ static int trsm_leaf_width() {
 
 // Wider leaves mean fewer, larger products and two fewer levels of small block
 // updates, for a little more product work and larger diagonal-block inverses:
-// 1024 columns once there are enough pivots to fill them, else 512.
-static int trsm_leaf_for(int64_t npiv) {
+// 1024 columns once there are enough pivots to fill them, else 512.  An
+// explicit option wins over the environment.
+static int trsm_leaf_for(int64_t npiv, int opt_leaf) {
+    if (opt_leaf == 128 || opt_leaf == 256 || opt_leaf == 512 || opt_leaf == 1024) return opt_leaf;
     const int v = trsm_leaf_width();
     return v > 0 ? v : (npiv >= 4096 ? 1024 : 512);
 }
@@ -467,7 +469,12 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     const int want_reduced = opt ? opt->want_reduced : 0;
     const int variant = opt ? opt->gemm_variant : GBLA_GEMM_AUTO;
     const int device_ptrs = opt ? opt->device_ptrs : 0;
+    const int path_opt = opt ? opt->path : GBLA_PATH_AUTO;
+    const int leaf_opt = opt ? opt->leaf_width : 0;
     if (variant < 0 || variant > GBLA_GEMM_SIMT) return GBLA_E_INVAL;
+    if (path_opt < GBLA_PATH_AUTO || path_opt > GBLA_PATH_SPARSE) return GBLA_E_INVAL;
+    if (leaf_opt != 0 && leaf_opt != 128 && leaf_opt != 256 && leaf_opt != 512 && leaf_opt != 1024)
+        return GBLA_E_INVAL;
     const int64_t m = in->nrows, n = in->ncols, nnz = in->nnz;
     if (m < 0 || n < 0 || nnz < 0 || m >= (1ll << 31) || n >= (1ll << 31)) return GBLA_E_INVAL;
     if (m > 0 && !in->row_ptr) return GBLA_E_INVAL;
@@ -479,6 +486,13 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     // diagonal blocks of the triangular solve on the tensor cores too
     const bool tc_leaves =
         variant == GBLA_GEMM_TCGEN05 || (variant == GBLA_GEMM_AUTO && p >= 8 && tc_supported());
+    // The sparse path keeps A and B sparse and runs C*A^-1 and the Schur
+    // update as K-compacted tensor-core products; it needs the tensor-core
+    // variant.  The dense path materialises A and B (and serves p < 8 and the
+    // exact SIMT variant).
+    const bool tc_ok = variant != GBLA_GEMM_SIMT && p >= 8 && tc_supported();
+    if (path_opt == GBLA_PATH_SPARSE && !tc_ok) return GBLA_E_UNSUPPORTED;
+    const bool sparse = tc_ok && path_opt != GBLA_PATH_DENSE;
     int tc_leaf_w = 512;
     GemmCounters ctr;
     const long long launches0 = g_launches;
@@ -495,7 +509,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     uint16_t *d_val = nullptr;
     PivotInfo pi;
     Multiline ml;
-    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{};
+    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{}, XT{};
+    Compact SA, SB;
+    uint16_t *Adiag = nullptr;
     uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
     uint16_t *A16 = nullptr, *B16 = nullptr;
     int32_t *is_piv_row = nullptr, *prow = nullptr, *pcol = nullptr;
@@ -570,27 +586,51 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     nvtxRangePop();
     if (rc != GBLA_OK) goto cleanup;
     npiv = pi.npiv;
-    tc_leaf_w = trsm_leaf_for(npiv);
+    tc_leaf_w = trsm_leaf_for(npiv, leaf_opt);
     m_cd = pi.m_cd;
     n_d = pi.n_d;
     ldc = round_up(npiv > 0 ? npiv : 1, 64);
     ldd = round_up(n_d > 0 ? n_d : 1, 64);
     ldbt = ldc;
-    // dense uint16 blocks: A, B (pivot rows, normalised), C, D (other rows)
-    STEP(dalloc_t(&A16, (size_t)(npiv > 0 ? npiv : 1) * (size_t)ldc, s));
-    STEP(dalloc_t(&B16, (size_t)(npiv > 0 ? npiv : 1) * (size_t)ldd, s));
-    STEP(dalloc_t(&C16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldc, s));
-    STEP(dalloc_t(&D16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldd, s));
-    if (npiv > 0) {
-        CSTEP(cudaMemsetAsync(A16, 0, sizeof(uint16_t) * (size_t)npiv * (size_t)ldc, s));
-        CSTEP(cudaMemsetAsync(B16, 0, sizeof(uint16_t) * (size_t)npiv * (size_t)ldd, s));
-    }
-    if (m_cd > 0) {
-        CSTEP(cudaMemsetAsync(C16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldc, s));
-        CSTEP(cudaMemsetAsync(D16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldd, s));
+    {
+        // dense uint16 blocks: C, D (other rows); A, B (pivot rows, normalised)
+        // on the dense path, and for the second pass of the reduced form
+        const bool dense_ab = !sparse || (want_reduced && npiv > 0 && n_d > 0);
+        if (dense_ab) {
+            STEP(dalloc_t(&A16, (size_t)(npiv > 0 ? npiv : 1) * (size_t)ldc, s));
+            STEP(dalloc_t(&B16, (size_t)(npiv > 0 ? npiv : 1) * (size_t)ldd, s));
+        }
+        STEP(dalloc_t(&C16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldc, s));
+        STEP(dalloc_t(&D16, (size_t)(m_cd > 0 ? m_cd : 1) * (size_t)ldd, s));
+        if (npiv > 0 && dense_ab) {
+            CSTEP(cudaMemsetAsync(A16, 0, sizeof(uint16_t) * (size_t)npiv * (size_t)ldc, s));
+            CSTEP(cudaMemsetAsync(B16, 0, sizeof(uint16_t) * (size_t)npiv * (size_t)ldd, s));
+        }
+        if (m_cd > 0) {
+            CSTEP(cudaMemsetAsync(C16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldc, s));
+            CSTEP(cudaMemsetAsync(D16, 0, sizeof(uint16_t) * (size_t)m_cd * (size_t)ldd, s));
+        }
     }
     STEP(split_scatter(dc, pi, A16, ldc, B16, ldd, C16, ldc, D16, ldd, mp, s));
-    if (m_cd > 0 && npiv > 0 && tc_leaves) {
+    if (sparse && m_cd > 0 && npiv > 0) {
+        // pivot rows as sparse operands, then the inverses of A's diagonal
+        // blocks from their dense copies (on the side stream: the main stream
+        // goes on with the second pass's conversions, if any)
+        STEP(dalloc_t(&Adiag, (size_t)round_up(npiv, tc_leaf_w) * (size_t)tc_leaf_w, s));
+        STEP(sparse_build(dc, pi, tc_leaf_w, Adiag, &SA, &SB, mp, s));
+        STEP(planes_alloc(&Zt, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
+        if (g_side.get()) {
+            CSTEP(cudaEventRecord(g_side.fork, s));
+            CSTEP(cudaStreamWaitEvent(g_side.s, g_side.fork, 0));
+            side_pending = true;
+            rc = upper_leaf_inverses_diag(Adiag, npiv, tc_leaf_w, Zt, mp, err, g_side.s);
+            CSTEP(cudaEventRecord(g_side.join, g_side.s));
+            STEP(rc);
+        } else {
+            STEP(upper_leaf_inverses_diag(Adiag, npiv, tc_leaf_w, Zt, mp, err, s));
+        }
+    }
+    if (!sparse && m_cd > 0 && npiv > 0 && tc_leaves) {
         // inverses of A's diagonal blocks for the tensor-core leaf solves, on
         // the side stream while the main stream converts A and B
         STEP(planes_alloc(&Zt, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
@@ -605,15 +645,15 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, err, s));
         }
     }
-    // digit planes of the operands the products read
-    if (m_cd > 0 && npiv > 0) {
+    // digit planes of the operands the dense products read
+    if (!sparse && m_cd > 0 && npiv > 0) {
         // A^T: B-operand of C <- C - X*A.  The triangular solve reads it only
         // below its diagonal blocks (column of A after row of A), so tiles
         // entirely above the diagonal are not converted.
         STEP(planes_alloc(&At, npiv, npiv, 4, s));
         STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s, nullptr, true));
     }
-    if (m_cd > 0 && n_d > 0 && npiv > 0) {
+    if (!sparse && m_cd > 0 && n_d > 0 && npiv > 0) {
         STEP(planes_alloc(&Bt, n_d, npiv, 4, s));    // B^T: B-operand of D <- D - X*B
         STEP(to_planes(Bt, n_d, npiv, B16, ldd, 0, true, nullptr, nullptr, mp, s));
     }
@@ -632,13 +672,26 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     dfree(A16, s);
     dfree(B16, s);
     A16 = B16 = nullptr;
+    dfree(Adiag, s);   // the side stream's work is joined into s above
+    Adiag = nullptr;
     // the 2-multiline form of A drives the sparse leaf solves: those of the
     // first pass unless they run on the tensor cores, those of the second
-    if (!tc_leaves || want_reduced) STEP(multiline_build(dc, pi, &ml, mp, s));
+    if ((!sparse && !tc_leaves) || want_reduced) STEP(multiline_build(dc, pi, &ml, mp, s));
     tm.mark(s);  // 1
 
     // ---- new order: X = C A^-1, then D <- D - X B
-    if (m_cd > 0 && npiv > 0) {
+    if (sparse && m_cd > 0 && npiv > 0) {
+        // X^T as A-operand planes (rows = pivots, K = rows of C), zero where
+        // no leaf writes (the staircase left of each row's lead)
+        STEP(planes_alloc(&XT, npiv, m_cd, 2, s));
+        STEP(planes_zero(XT, s));
+        STEP(planes_alloc(&Ct, m_cd, tc_leaf_w, 4, s));
+        lead_h.resize((size_t)m_cd);
+        STEP(readback(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, s));
+        TrsmSparse T{m_cd, npiv, C16, ldc, &SA, &Zt, &Ct, &XT, tc_leaf_w, &mp, err, s, &ctr, pi.cd_lead, &lead_h};
+        NvtxRange r("gbla.trsm");
+        STEP(trsm_sparse(T));
+    } else if (m_cd > 0 && npiv > 0) {
         STEP(planes_alloc(&Xp, m_cd, npiv, 2, s));
         STEP(planes_zero(Xp, s));
         lead_h.resize((size_t)m_cd);
@@ -650,12 +703,15 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         STEP(trsm_upper(T));
     }
     tm.mark(s);  // 2
-    if (m_cd > 0 && npiv > 0 && n_d > 0) {
+    if (sparse && m_cd > 0 && npiv > 0 && n_d > 0) {
+        NvtxRange r("gbla.schur");
+        STEP(modgemm_gather(SB, 0, XT, npiv, D16, ldd, m_cd, n_d, -1, pi.cd_lead, mp, err, s, &ctr));
+    } else if (m_cd > 0 && npiv > 0 && n_d > 0) {
         NvtxRange r("gbla.schur");
         STEP(modgemm(Xp, 0, 0, Bt, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr, nullptr,
                      pi.cd_lead, lead_h.data()));
+        schur_ops = ctr.last_ops;
     }
-    schur_ops = ctr.last_ops;
     tm.mark(s);  // 3
 
     // ---- step 4: RREF of D'
@@ -813,6 +869,10 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             stats->mod_ops = ctr.mod_ops;
             stats->launches = g_launches - launches0;
             stats->schur_mod_ops = schur_ops;
+            stats->path = sparse ? GBLA_PATH_SPARSE : GBLA_PATH_DENSE;
+            stats->list_a = SA.total;
+            stats->list_b = SB.total;
+            stats->leaf_width = tc_leaf_w;
         }
     }
 
@@ -836,6 +896,10 @@ cleanup:
     planes_free(&Xq, s);
     planes_free(&RdT, s);
     planes_free(&XpdT, s);
+    planes_free(&XT, s);
+    compact_free(&SA, s);
+    compact_free(&SB, s);
+    dfree(Adiag, s);
     dfree(A16, s);
     dfree(B16, s);
     dfree(C16, s);
@@ -946,6 +1010,45 @@ int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t l
     }
     planes_free(&Ap, s);
     planes_free(&Bp, s);
+    dfree(err, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+int gbla_spmm(int64_t M, int64_t N, int64_t K, const uint16_t *X, int64_t ldx, const gbla_csr_in *S_dev,
+              const int32_t *x_lead, uint16_t *C, int64_t ldc, uint32_t p, int sign, void *stream) {
+    if (M < 0 || N < 0 || K < 0 || !S_dev || p >= 65536u || !is_prime(p) || (sign != 1 && sign != -1))
+        return GBLA_E_INVAL;
+    if (S_dev->nrows != K || S_dev->ncols != N || S_dev->nnz < 0) return GBLA_E_INVAL;
+    if (M == 0 || N == 0 || K == 0) return GBLA_OK;
+    if (!X || !C || ldx < K || ldc < N || !S_dev->row_ptr || (S_dev->nnz > 0 && (!S_dev->col || !S_dev->val)))
+        return GBLA_E_INVAL;
+    GBLA_TRY(check_device());
+    if (!tc_supported() || p < 8) return GBLA_E_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const ModP mp = make_modp(p);
+    DevCSR S;
+    S.m = K;
+    S.n = N;
+    S.nnz = S_dev->nnz;
+    S.row_ptr = S_dev->row_ptr;
+    S.col = S_dev->col;
+    S.val = S_dev->val;
+    Compact SB;
+    Planes XT{};
+    uint32_t *err = nullptr;
+    int rc = dalloc_t(&err, 4, s);
+    if (rc == GBLA_OK && cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK) rc = compact_from_csr(S, &SB, mp, err, s);
+    if (rc == GBLA_OK) rc = planes_alloc(&XT, K, M, 2, s);
+    if (rc == GBLA_OK) rc = planes_zero(XT, s);
+    if (rc == GBLA_OK) rc = to_planes(XT, K, M, X, ldx, 0, true, nullptr, nullptr, mp, s);
+    if (rc == GBLA_OK) rc = modgemm_gather(SB, 0, XT, K, C, ldc, M, N, sign, x_lead, mp, err, s, nullptr);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == GBLA_OK) rc = GBLA_E_CUDA;
+    uint32_t herr = 0;
+    if (rc == GBLA_OK && readback(&herr, err, 4, s) == GBLA_OK) rc = map_dev_err(herr);
+    compact_free(&SB, s);
+    planes_free(&XT, s);
     dfree(err, s);
     cudaStreamSynchronize(s);
     return rc;

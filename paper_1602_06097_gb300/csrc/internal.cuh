@@ -44,11 +44,38 @@ int readback(void *dst, const void *src, size_t bytes, cudaStream_t s);
 // events, the page-locked readback buffer); for worker threads about to exit.
 void release_thread_resources();
 
-// Product written as A-operand digit planes: Out[row, out_col0 + n] <- (A*B)[row, n]
-// mod p (tensor-core variant only).
+// Product written as A-operand digit planes: Out[out_row0 + m, out_col0 + n] <-
+// (A*B)[m, n] mod p (tensor-core variant only).  A may be a 4-plane set, read
+// as its first two planes.
 int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t b_row0, const Planes &Out,
                       int64_t out_col0, int64_t M, int64_t N, int64_t K, const ModP &mp, uint32_t *err,
-                      cudaStream_t s, GemmCounters *ctr);
+                      cudaStream_t s, GemmCounters *ctr, int64_t out_row0 = 0);
+
+// K-compacted sparse operand S (npiv rows) of the gathered product, built by
+// sparse_build (sparse.cu): for 128-column tile t, the rows with a nonzero in
+// the tile are kidx[koff[t] .. koff[t+1]) (ascending, padded with KIDX_PAD to
+// a multiple of 128), and the tile restricted to them is stored as B-operand
+// digit planes, chunk-major (list entries 32 q .. 32 q + 31: 128 rows of 128
+// bf16 at planes + 128 * 128 * q).
+constexpr int32_t KIDX_PAD = 0x7F7F7F7F;
+struct Compact {
+    int64_t ntiles = 0;        // column tiles
+    int64_t total = 0;         // list entries of all tiles (multiple of 128)
+    int32_t *kidx = nullptr;   // [total]
+    int64_t *koff = nullptr;   // [ntiles + 1]
+    __nv_bfloat16 *planes = nullptr;   // [total / 32 chunks][128 rows][128 bf16] = total * 512
+};
+void compact_free(Compact *c, cudaStream_t s);
+
+// Gathered product C[r, c] <- (C[r, c] + sign * sum_j X[r, j] * S[j, c]) mod p
+// for rows r < M and columns c < N of C, c in tile nt0 + c / 128 of S; X is
+// read from the A-operand plane set XT of its transpose (row j = column j of
+// X, K = r; rows xt_rows and beyond read as zero).  With row_lead (device,
+// ascending absolute lead of each row of X) a row tile skips the list entries
+// left of its raster group's first lead.  Tensor-core variant only (p >= 8).
+int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_rows, uint16_t *C, int64_t ldc,
+                   int64_t M, int64_t N, int sign, const int32_t *row_lead, const ModP &mp, uint32_t *err,
+                   cudaStream_t s, GemmCounters *ctr);
 // Grouped product C[c_rows, c_col0:] += sign * A_p * B_p^T for every problem
 // p, one launch (see GroupProb).
 int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K, uint16_t *C,

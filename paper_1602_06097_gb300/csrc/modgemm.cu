@@ -225,7 +225,10 @@ struct Args {
     int withhold_loads;      // test hook: issue no TMA loads, so the waits expire
     int group_m;             // row tiles per raster group
     Planes xout;             // planes-out mode (xout.ptr set): the product itself, as
-    int64_t xout_col0;       // A-operand digit planes at column xout_col0 + n; C unused
+    int64_t xout_col0;       // A-operand digit planes at row xout_row0 + m, column
+    int64_t xout_row0;       // xout_col0 + n; C unused
+    int a_pitch;             // elements per 32-wide K chunk of an A row: 64 (2 planes) or
+                             // 128 (a 4-plane set read as its first two planes); 0 = 64
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
@@ -471,6 +474,60 @@ __device__ __forceinline__ int drain_step(int run, float pa, float qa, float pin
     return s;
 }
 
+// C <- (C + sign * run) mod p on one drain thread's row segment: HC columns
+// from column col0 of C (crow points at it), columns >= ncol untouched.
+constexpr int HC_COLS = BN / 2;   // columns per drain warp
+__device__ __forceinline__ void rmw_segment(uint16_t *crow, int64_t col0, int64_t ncol,
+                                            const uint32_t (&run)[HC_COLS / 2], int sign, int P) {
+    constexpr int HC = HC_COLS;
+    const bool aligned = (reinterpret_cast<uintptr_t>(crow) & 15u) == 0;
+    // Chunks of 8 columns: whole in-range chunks move as 16-byte vectors, a
+    // ragged or unaligned chunk element by element.  Every load is issued
+    // before the first store.
+    uint4 cv[HC / 8];
+#pragma unroll
+    for (int v = 0; v < HC / 8; ++v) {
+        const int64_t cbase = col0 + v * 8;
+        if (aligned && cbase + 8 <= ncol) {
+            cv[v] = reinterpret_cast<const uint4 *>(crow)[v];
+        } else {
+            uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (cbase + e < ncol) w[e >> 1] |= (uint32_t)crow[v * 8 + e] << ((e & 1) * 16);
+            cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < HC / 8; ++v) {
+        uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint32_t rr = run[v * 4 + e];
+            int c0 = (int)(w[e] & 0xFFFFu), c1 = (int)(w[e] >> 16);
+            int r0 = (int)(rr & 0xFFFFu), r1 = (int)(rr >> 16);
+            int o0 = sign > 0 ? c0 + r0 : c0 - r0;
+            int o1 = sign > 0 ? c1 + r1 : c1 - r1;
+            o0 += (o0 < 0) ? P : 0; o0 -= (o0 >= P) ? P : 0;
+            o1 += (o1 < 0) ? P : 0; o1 -= (o1 >= P) ? P : 0;
+            w[e] = (uint32_t)o0 | ((uint32_t)o1 << 16);
+        }
+        cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+#pragma unroll
+    for (int v = 0; v < HC / 8; ++v) {
+        const int64_t cbase = col0 + v * 8;
+        if (aligned && cbase + 8 <= ncol) {
+            reinterpret_cast<uint4 *>(crow)[v] = cv[v];
+        } else {
+            const uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (cbase + e < ncol) crow[v * 8 + e] = (uint16_t)(w[e >> 1] >> ((e & 1) * 16));
+        }
+    }
+}
+
 __device__ __forceinline__ void tile_coords(int64_t t, int64_t num_m, int64_t num_n, int64_t GM, int64_t &mt,
                                             int64_t &nt) {
     int64_t group = t / (GM * num_n);
@@ -631,7 +688,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     uint8_t *st = tiles + stage * SBYTES;
                     // chunk c of K sits at element 64 c of an A row (2 planes)
                     // and 128 c of a B row (4 planes)
-                    const int ax = (g.a_k0 / BK + ks) * 2 * BK, bx = (g.b_k0 / BK + ks) * 4 * BK;
+                    const int ax = (g.a_k0 / BK + ks) * (g.a_pitch ? g.a_pitch : 2 * BK),
+                              bx = (g.b_k0 / BK + ks) * 4 * BK;
                     if (PAIR) {
                         const uint32_t fb = mapa_rank(smem_u32(&full[stage]), 0);
                         if (leader) mbar_expect_tx(&full[stage], 2 * SBYTES);
@@ -778,6 +836,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 // planes-out: the product's digits, 16-byte stores per plane
                 const int64_t row = ti.mt * TBM + (int64_t)rank * BM + row_in_tile;
                 if (row < ti.M) {
+                    const int64_t orow = g.xout_row0 + row;
                     const int64_t k0 = g.xout_col0 + ti.nt * BN + half * HC;
 #pragma unroll
                     for (int v = 0; v < HC / 8; ++v) {
@@ -791,8 +850,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             vh[e] = pack_bf2(h0, h1);
                             vl[e] = pack_bf2(l0, l1);
                         }
-                        *reinterpret_cast<uint4 *>(g.xout.at(0, row, k0 + v * 8)) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
-                        *reinterpret_cast<uint4 *>(g.xout.at(1, row, k0 + v * 8)) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+                        *reinterpret_cast<uint4 *>(g.xout.at(0, orow, k0 + v * 8)) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+                        *reinterpret_cast<uint4 *>(g.xout.at(1, orow, k0 + v * 8)) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
                     }
                 }
                 continue;
@@ -802,58 +861,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int64_t col0 = ti.c_col0 + ti.nt * BN + half * HC;   // column of C
             const int64_t ncol = ti.c_col0 + ti.N;                        // column limit
             const int64_t prow = (row < ti.M && ti.c_rows) ? (int64_t)ti.c_rows[row] : row;
-            if (row < ti.M && col0 < ncol && prow >= 0) {
-                uint16_t *crow = g.C + prow * g.ldc + col0;
-                const bool aligned = (reinterpret_cast<uintptr_t>(crow) & 15u) == 0;
-                // Chunks of 8 columns: whole in-range chunks move as 16-byte
-                // vectors, a ragged or unaligned chunk element by element.
-                // Every load is issued before the first store.
-                uint4 cv[HC / 8];
-#pragma unroll
-                for (int v = 0; v < HC / 8; ++v) {
-                    const int64_t cbase = col0 + v * 8;
-                    if (aligned && cbase + 8 <= ncol) {
-                        cv[v] = reinterpret_cast<const uint4 *>(crow)[v];
-                    } else {
-                        uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            if (cbase + e < ncol) w[e >> 1] |= (uint32_t)crow[v * 8 + e] << ((e & 1) * 16);
-                        cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < HC / 8; ++v) {
-                    uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        uint32_t rr = run[v * 4 + e];
-                        int c0 = (int)(w[e] & 0xFFFFu), c1 = (int)(w[e] >> 16);
-                        int r0 = (int)(rr & 0xFFFFu), r1 = (int)(rr >> 16);
-                        int o0 = g.sign > 0 ? c0 + r0 : c0 - r0;
-                        int o1 = g.sign > 0 ? c1 + r1 : c1 - r1;
-                        o0 += (o0 < 0) ? P : 0; o0 -= (o0 >= P) ? P : 0;
-                        o1 += (o1 < 0) ? P : 0; o1 -= (o1 >= P) ? P : 0;
-                        w[e] = (uint32_t)o0 | ((uint32_t)o1 << 16);
-                    }
-                    cv[v] = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-#pragma unroll
-                for (int v = 0; v < HC / 8; ++v) {
-                    const int64_t cbase = col0 + v * 8;
-                    if (aligned && cbase + 8 <= ncol) {
-                        reinterpret_cast<uint4 *>(crow)[v] = cv[v];
-                    } else {
-                        const uint32_t w[4] = {cv[v].x, cv[v].y, cv[v].z, cv[v].w};
-#pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            if (cbase + e < ncol) crow[v * 8 + e] = (uint16_t)(w[e >> 1] >> ((e & 1) * 16));
-                    }
-                }
-            }
+            if (row < ti.M && col0 < ncol && prow >= 0)
+                rmw_segment(g.C + prow * g.ldc + col0, col0, ncol, run, g.sign, P);
         }
     }
-
     tcgen05_fence_before();
     __syncthreads();
     if (PAIR) cluster_sync();   // the leader's MMAs may write the peer's TMEM until here
@@ -865,6 +876,351 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         else
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                          : "memory");
+    }
+}
+
+// ===================================================================
+// Gathered product: the sparse operand compacted per column tile
+// ===================================================================
+// C[r, c] <- (C[r, c] + sign * sum_j X[r, j] * S[j, c]) mod p for the output
+// column tiles nt0 .. of a compacted sparse operand S (sparse.cu): the rows j
+// of S with a nonzero in tile t are listed in kidx[koff[t] .. koff[t + 1])
+// (ascending, padded to whole ring rounds of 128 entries with KIDX_PAD), and S
+// restricted to those rows and the tile's 128 columns is stored densely as
+// B-operand digit planes, 32 list entries per 128 x 128-bf16 chunk.  The
+// product's K is the list: K-compaction keeps the tensor cores on the
+// nonzero part of S.  X is read through its transpose: row j of the
+// A-operand plane set XT holds column j of X, so the 128 values of a row tile
+// and both planes are 512 contiguous bytes; the gather warps copy them for
+// every listed j into shared memory in the MN-major 128-byte-swizzled layout
+// (cp.async), while one thread loads the compacted S chunk by TMA.  Rows of X
+// are ascending by lead (first nonzero column), so a tile skips the list
+// entries left of its raster group's first lead.
+constexpr int G_WARPS = 2;
+constexpr int G_THREADS = 64 + 32 * EPI_WARPS + 32 * G_WARPS;
+constexpr int G_LAG = 2;   // stages a gather thread keeps in flight before signalling the oldest
+constexpr int G_CHUNKS = (2 * BM * BK * 2) / 16;   // 16-byte copies per stage (1024)
+
+struct GArgs {
+    int64_t M, N;            // rows of X taking part; output columns (from column 0 of C)
+    int64_t nt0;             // list of output tile nt is list nt0 + nt
+    const int32_t *kidx;     // compacted lists
+    const int64_t *koff;     // list offsets
+    const __nv_bfloat16 *xt; // XT plane set (2 planes, rows = j, K = r)
+    int64_t xt_row_elems;    // elements per XT row
+    int64_t xt_rows;         // list entries >= xt_rows (padding) read as zero
+    const int32_t *row_lead; // ascending lead (absolute j) of each row of X, or null
+    uint16_t *C;
+    int64_t ldc;
+    int sign;
+    uint32_t p;
+    float pinv;
+    uint32_t *err;
+    int group_m;
+};
+
+struct GTile {
+    int64_t mt, nt, chunk0;
+    int ks0, ksteps;
+};
+
+__device__ __forceinline__ GTile gtile(const GArgs &g, int64_t t, int64_t num_m, int64_t num_n) {
+    GTile ti;
+    tile_coords(t, num_m, num_n, g.group_m, ti.mt, ti.nt);
+    const int64_t kb = g.koff[g.nt0 + ti.nt], ke = g.koff[g.nt0 + ti.nt + 1];
+    ti.chunk0 = kb / BK;
+    ti.ksteps = (int)((ke - kb) / BK);
+    int64_t s = 0;
+    if (g.row_lead) {   // first list entry at or after the group's first lead
+        const int32_t L = g.row_lead[(ti.mt / g.group_m) * g.group_m * BM];
+        int64_t lo = kb, hi = ke;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (g.kidx[mid] < L) lo = mid + 1;
+            else hi = mid;
+        }
+        s = lo - kb;
+    }
+    ti.ks0 = (int)(s / BK) & ~(STAGES - 1);   // whole rounds of the stage ring
+    return ti;
+}
+
+// Shared-memory descriptor of an MN-major operand with 128-byte swizzle:
+// atoms of 8 K-rows x 128 bytes (64 values of M), atoms along M 1024 bytes
+// apart (leading byte offset), along K 2048 bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t make_sdesc_mn(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(1024 >> 4) << 16;       // leading byte offset: next 64 rows of M
+    d |= (uint64_t)(2048 >> 4) << 32;       // stride byte offset: next 8 values of K
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor with A MN-major (transposed), B K-major.
+constexpr uint32_t IDESC_G = IDESC | (1u << 15);
+
+// One K = 16 step: A planes ah (a) and al (a + 8 KB), B as in mma_step.
+__device__ __forceinline__ void mma_step_g(uint32_t dP, uint32_t dQ, uint32_t a, uint32_t b1, uint32_t b2,
+                                           uint32_t ahi, uint32_t bhi, uint32_t acc0) {
+    asm volatile("{\n\t.reg .pred p, e;\n\t.reg .b32 r;\n\t.reg .b64 a0, a1, x0, x1, y0, y1;\n\t"
+                 "elect.sync r|e, 0xffffffff;\n\t"
+                 "setp.ne.b32 p, %8, 0;\n\t"
+                 "mov.b64 a0, {%2, %5};\n\t"
+                 "add.u32 r, %2, 512;\n\tmov.b64 a1, {r, %5};\n\t"
+                 "mov.b64 x0, {%3, %6};\n\t"
+                 "add.u32 r, %3, 4;\n\tmov.b64 x1, {r, %6};\n\t"
+                 "mov.b64 y0, {%4, %6};\n\t"
+                 "add.u32 r, %4, 4;\n\tmov.b64 y1, {r, %6};\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, y0, %7, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%1], a0, y1, %7, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a1, x0, %7, 1;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%1], a1, x1, %7, 1;\n\t}" ::"r"(dP),
+                 "r"(dQ), "r"(a), "r"(b1), "r"(b2), "r"(ahi), "r"(bhi), "r"(IDESC_G), "r"(acc0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(tc::G_THREADS, 1)
+    modgemm_gather_kernel(const __grid_constant__ CUtensorMap tmB, const GArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + STAGES * STAGE_BYTES);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + STAGES;
+    uint64_t *accf = bars + 2 * STAGES;
+    uint64_t *acce = accf + 2;
+    uint64_t *done = acce + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1 + 32 * G_WARPS);   // the TMA thread and every gather thread
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], EPI_WARPS);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    tcgen05_fence_before();
+    __syncthreads();
+    tcgen05_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
+    const int64_t num_tiles = num_m * num_n;
+    const int64_t tile0 = blockIdx.x, tstep = gridDim.x;
+    static_assert(STAGES == 4 && KSTEPS_PER_BLOCK % 4 == 0, "ring rounds");
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer of the compacted operand
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[STAGES];
+            uint32_t issued_parity[STAGES];
+            for (int s = 0; s < STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
+            bool ok = true;
+            for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
+                const GTile ti = gtile(g, t, num_m, num_n);
+                for (int ks = ti.ks0; ks < ti.ksteps; ++ks) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                    uint8_t *st = tiles + stage * STAGE_BYTES;
+                    const int y = (int)((ti.chunk0 + ks) * BN);
+                    mbar_expect_tx(&full[stage], 2 * BOX_BYTES);
+                    tma_load_2d(st + BOX_BYTES, &tmB, &full[stage], 0, y);
+                    tma_load_2d(st + 2 * BOX_BYTES, &tmB, &full[stage], 2 * BK, y);
+                    issued[stage] = 1;
+                    issued_parity[stage] = phase;
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+            }
+            for (int s = 0; s < STAGES; ++s) {   // never leave with copies in flight
+                if (!issued[s]) continue;
+                const uint32_t addr = smem_u32(&full[s]);
+                long long start = clock64();
+                while (!mbar_try_wait(addr, issued_parity[s])) {
+                    if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                        dev_fail(g.err, DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (converged warp, elected lane)
+        uint32_t phase = 0;
+        uint32_t kbc = 0;
+        bool ok = true;
+        const uint32_t s0 = smem_u32(tiles);
+        const uint64_t da = make_sdesc_mn(s0), db = make_sdesc(s0);
+        const uint32_t ahi = (uint32_t)(da >> 32), alo = (uint32_t)da;
+        const uint32_t bhi = (uint32_t)(db >> 32), blo = (uint32_t)db;
+        constexpr uint32_t SB = STAGE_BYTES >> 4, B1 = BOX_BYTES >> 4, B2 = (2 * BOX_BYTES) >> 4;
+        for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
+            const GTile ti = gtile(g, t, num_m, num_n);
+            const int kbt = (ti.ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+            for (int kb = 0; kb < kbt && ok; ++kb, ++kbc) {
+                const uint32_t buf = kbc & 1u, use = kbc >> 1;
+                if (!mbar_wait_warp(&acce[buf], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                tcgen05_fence_after();
+                const uint32_t dP = tmem + buf * 256u, dQ = dP + 128u;
+                const int ks_beg = ti.ks0 + kb * KSTEPS_PER_BLOCK;
+                const int ks_end = min(ti.ksteps, ks_beg + KSTEPS_PER_BLOCK);
+                uint32_t acc0 = 0;
+                for (int ks = ks_beg; ks < ks_end && ok; ks += STAGES) {
+#pragma unroll
+                    for (int st = 0; st < STAGES; ++st) {
+                        if (!mbar_wait_warp(&full[st], phase, abort_flag, g.err)) { ok = false; break; }
+                        // the gather threads' copies are made visible to the
+                        // tensor core by their proxy fence before they arrive
+                        tcgen05_fence_after();
+                        const uint32_t a = alo + st * SB, b = blo + st * SB;
+                        mma_step_g(dP, dQ, a, b + B1, b + B2, ahi, bhi, acc0);
+                        mma_step_g(dP, dQ, a + 256, b + B1 + 2, b + B2 + 2, ahi, bhi, 1u);   // next 16 of K
+                        acc0 = 1u;
+                        commit_elected<false, true>(&empty[st]);
+                    }
+                    phase ^= 1u;
+                }
+                if (ok) commit_elected<false, true>(&accf[buf]);
+            }
+        }
+        commit_elected<false, false>(done);
+        const uint32_t addr = smem_u32(done);
+        long long start = clock64();
+        while (!__any_sync(0xffffffffu, mbar_try_wait(addr, 0))) {
+            if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                if (lane == 0) dev_fail(g.err, DEV_ERR_TIMEOUT);
+                break;
+            }
+        }
+    } else if (warp < 2 + EPI_WARPS) {
+        // ---------------- drain: as in modgemm_tc_kernel
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row_in_tile = quarter * 32 + lane;
+        const float pinv = g.pinv;
+        const int P = (int)g.p;
+        const uint32_t bm = 0xFFFFFFFFu / g.p;
+        const int bias = 256 * P + (int)(((1u << 24) + g.p - 1) / g.p) * P;
+        constexpr int HC = BN / 2;
+        uint32_t kbc = 0;
+        bool ok = true;
+        for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
+            const GTile ti = gtile(g, t, num_m, num_n);
+            const int kbt = (ti.ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+            if (kbt <= 0) continue;   // no list entry on this tile: C stays as it is
+            uint32_t run[HC / 2];
+#pragma unroll
+            for (int i = 0; i < HC / 2; ++i) run[i] = 0;
+            for (int kb = 0; kb < kbt; ++kb, ++kbc) {
+                const uint32_t buf = kbc & 1u, use = kbc >> 1;
+                if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
+                tcgen05_fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * 256u + half * HC;
+#pragma unroll
+                for (int c = 0; c < HC / 16; ++c) {
+                    float pv[16], qv[16];
+                    tmem_ld16(tbase + c * 16, pv);
+                    tmem_ld16(tbase + 128 + c * 16, qv);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        uint32_t pair = run[c * 8 + j / 2];
+                        const int lo16 = drain_step((int)(pair & 0xFFFFu), pv[j], qv[j], pinv, P, bias, bm);
+                        const int hi16 = drain_step((int)(pair >> 16), pv[j + 1], qv[j + 1], pinv, P, bias, bm);
+                        run[c * 8 + j / 2] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
+                    }
+                }
+                tcgen05_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[buf]);
+            }
+            if (!ok) break;
+            const int64_t row = ti.mt * BM + row_in_tile;
+            const int64_t col0 = ti.nt * BN + half * HC;
+            if (row < g.M && col0 < g.N) rmw_segment(g.C + row * g.ldc + col0, col0, g.N, run, g.sign, P);
+        }
+    } else {
+        // ---------------- gather warps: X^T rows of the listed j into the
+        // A stage (MN-major, 128-byte swizzle), cp.async 16 bytes at a time.
+        // Copy i of a stage: list entry kk = i / 32 (one warp instruction
+        // moves one entry's 512 bytes), 16-byte piece q = i % 32 of it, which
+        // holds rows rl .. rl + 7 (rl = 32 (q / 8) + 8 (q % 4)) of plane
+        // (q / 4) % 2.
+        const int gt = threadIdx.x - (64 + 32 * EPI_WARPS);
+        const uint32_t sbase = smem_u32(tiles);
+        int stage = 0, last = 0, npend = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
+            const GTile ti = gtile(g, t, num_m, num_n);
+            const __nv_bfloat16 *xseg = g.xt + (ti.mt * BM / 32) * 64;   // the row tile's 512 bytes in an XT row
+            for (int ks = ti.ks0; ks < ti.ksteps; ++ks) {
+                if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                const uint32_t abase = sbase + stage * STAGE_BYTES;
+                const int64_t kbase = (ti.chunk0 + ks) * BK;
+#pragma unroll 4
+                for (int i = gt; i < G_CHUNKS; i += 32 * G_WARPS) {
+                    const int q = i & 31, kk = i >> 5;
+                    const int64_t j = g.kidx[kbase + kk];
+                    const bool valid = j < g.xt_rows;
+                    const int rl = (q >> 3) * 32 + (q & 3) * 8;
+                    const uint32_t dst = abase + ((q >> 2) & 1) * 8192 + (kk >> 3) * 2048 + (rl >> 6) * 1024 +
+                                         (kk & 7) * 128 + ((((rl & 63) >> 3) ^ (kk & 7)) << 4);
+                    const __nv_bfloat16 *src = valid ? xseg + j * g.xt_row_elems + q * 8 : g.xt;
+                    cp_async16(dst, src, valid ? 16u : 0u);
+                }
+                cp_async_commit();
+                last = stage;
+                if (++npend > G_LAG) {
+                    cp_async_wait<G_LAG>();
+                    fence_proxy_async();
+                    mbar_arrive(&full[(last + STAGES - G_LAG) % STAGES]);
+                    --npend;
+                }
+                if (++stage == STAGES) stage = 0, phase ^= 1u;
+            }
+        }
+        // every copy completes before the thread leaves; the stages still
+        // owed a signal get it
+        cp_async_wait<0>();
+        fence_proxy_async();
+        for (int i = npend - 1; i >= 0; --i) mbar_arrive(&full[(last + STAGES - i) % STAGES]);
+    }
+
+    tcgen05_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tcgen05_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 }  // namespace tc
@@ -1052,12 +1408,13 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
 // round_up(N, 128) lie inside its padded width.
 int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t b_row0, const Planes &Out,
                       int64_t out_col0, int64_t M, int64_t N, int64_t K, const ModP &mp, uint32_t *err,
-                      cudaStream_t s, GemmCounters *ctr)
+                      cudaStream_t s, GemmCounters *ctr, int64_t out_row0)
 {
     if (M <= 0 || N <= 0 || K <= 0) return GBLA_OK;
     if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
-    if (A.nplanes != 2 || B.nplanes != 4 || Out.nplanes != 2) return GBLA_E_INTERNAL;
-    if ((out_col0 % 8) || out_col0 + round_up(N, tc::BN) > Out.kp || M > Out.rows) return GBLA_E_INTERNAL;
+    if ((A.nplanes != 2 && A.nplanes != 4) || B.nplanes != 4 || Out.nplanes != 2) return GBLA_E_INTERNAL;
+    if ((out_col0 % 8) || out_col0 + round_up(N, tc::BN) > Out.kp || out_row0 < 0 || out_row0 + M > Out.rows)
+        return GBLA_E_INTERNAL;
     if (ctr) ctr->launches += 1;   // the caller counts the algorithmic work
     CUtensorMap ma, mb;
     GBLA_TRY(make_map(&ma, A));
@@ -1078,9 +1435,56 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     g.err = err;
     g.xout = Out;
     g.xout_col0 = out_col0;
+    g.xout_row0 = out_row0;
+    g.a_pitch = 32 * A.nplanes;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
     tc::modgemm_tc_kernel<false><<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    GBLA_CUDA_TRY(launch_check());
+    if (ctr) ctr->tc_launches += 1;
+    return GBLA_OK;
+}
+
+// Gathered product (see tc::modgemm_gather_kernel).
+int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_rows, uint16_t *C, int64_t ldc,
+                   int64_t M, int64_t N, int sign, const int32_t *row_lead, const ModP &mp, uint32_t *err,
+                   cudaStream_t s, GemmCounters *ctr)
+{
+    if (M <= 0 || N <= 0 || S.total <= 0) return GBLA_OK;
+    if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
+    if (XT.nplanes != 2 || XT.kp % 128 || round_up(M, 128) > XT.kp || xt_rows > XT.rows || S.total % 128 ||
+        nt0 < 0 || nt0 + (N + 127) / 128 > S.ntiles)
+        return GBLA_E_INTERNAL;
+    if (ctr) ctr->launches += 1;
+    GBLA_TRY(get_encode());
+    CUtensorMap mb;
+    cuuint64_t dims[2] = {128, (cuuint64_t)(S.total / tc::BK) * 128};
+    cuuint64_t strides[1] = {128 * 2};
+    cuuint32_t box[2] = {2 * tc::BK, 128};
+    cuuint32_t estr[2] = {1, 1};
+    if (g_encode(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)S.planes, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return GBLA_E_CUDA;
+    static std::once_flag attr_once;
+    static cudaError_t attr_rc = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_rc = cudaFuncSetAttribute(tc::modgemm_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tc::SMEM_BYTES);
+    });
+    GBLA_CUDA_TRY(attr_rc);
+    tc::GArgs g{};
+    g.M = M; g.N = N; g.nt0 = nt0;
+    g.kidx = S.kidx; g.koff = S.koff;
+    g.xt = XT.ptr; g.xt_row_elems = XT.row_elems(); g.xt_rows = xt_rows;
+    g.row_lead = row_lead;
+    g.C = C; g.ldc = ldc; g.sign = sign;
+    g.p = mp.p; g.pinv = mp.pinv;
+    g.err = err;
+    g.group_m = gemm_group_m();
+    const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
+    const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+    tc::modgemm_gather_kernel<<<grid, tc::G_THREADS, tc::SMEM_BYTES, s>>>(mb, g);
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;

@@ -1175,6 +1175,67 @@ int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, c
     return rc;
 }
 
+// cmap[j] = j % L: column map of the diagonal-block storage Adiag.
+__global__ void iota_mod_kernel(int32_t *v, int64_t n, int L)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)(i % L);
+}
+
+int upper_leaf_inverses_diag(const uint16_t *Adiag, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
+                             uint32_t *err, cudaStream_t s)
+{
+    if (npiv <= 0) return GBLA_OK;
+    const int64_t nleaves = (npiv + L - 1) / L;
+    if (Zt.nplanes != 4 || Zt.kp != L || Zt.rows < nleaves * L) return GBLA_E_INTERNAL;
+    uint16_t *ZN = nullptr;
+    int32_t *cmap = nullptr;
+    int rc = dalloc_t(&ZN, (size_t)nleaves * L * L, s);
+    if (rc == GBLA_OK) rc = dalloc_t(&cmap, (size_t)npiv, s);
+    if (rc == GBLA_OK) {
+        iota_mod_kernel<<<(unsigned)((npiv + 255) / 256), 256, 0, s>>>(cmap, npiv, L);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    // T[i][j] = Adiag[i * L + j % L]: row i, column j of A inside i's block
+    if (rc == GBLA_OK) rc = block_inverses(Adiag, L, nullptr, cmap, npiv, L, ZN, mp, true, err, s);
+    if (rc == GBLA_OK) {
+        zt_planes_kernel<<<dim3((unsigned)(L / TP_TILE), (unsigned)(L / TP_TILE), (unsigned)nleaves), 256, 0, s>>>(
+            ZN, L, Zt, mp);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    dfree(cmap, s);
+    dfree(ZN, s);
+    return rc;
+}
+
+int trsm_sparse(const TrsmSparse &T)
+{
+    const int64_t L = T.L;
+    if (T.npiv <= 0 || T.mrows <= 0) return GBLA_OK;
+    if (L % 128 || T.Ct->nplanes != 4 || T.Ct->kp < L || T.Zt->kp != L) return GBLA_E_INTERNAL;
+    const auto rows_before = [&](int64_t bound) -> int64_t {
+        if (!T.lead_host) return T.mrows;
+        const auto &ld = *T.lead_host;
+        return std::lower_bound(ld.begin(), ld.end(), (int32_t)bound) - ld.begin();
+    };
+    for (int64_t lo = 0; lo < T.npiv; lo += L) {
+        const int64_t hi = std::min(lo + L, T.npiv), w = hi - lo;
+        const int64_t rows_hi = rows_before(hi);   // rows with X_J != 0 possible
+        if (rows_hi == 0) continue;
+        const int64_t rows_lo = rows_before(lo);   // rows with X_{<J} != 0 possible
+        // C_J -= X_{<J} * A_{<J,J}: the lists of J's column tiles hold only rows
+        // of earlier leaves
+        if (rows_lo > 0)
+            GBLA_TRY(modgemm_gather(*T.SA, lo / 128, *T.XT, T.npiv, T.C16 + lo, T.ldc, rows_lo, w, -1, T.lead_dev,
+                                    *T.mp, T.err, T.s, T.ctr));
+        // X_J^T = Z_J^T * C_J^T: A-operand = the inverse's planes (row j, K k
+        // = Z_J[k][j]), B-operand = C_J (row r, K k), out = XT rows lo..hi
+        GBLA_TRY(to_planes(*T.Ct, rows_hi, w, T.C16 + lo, T.ldc, 0, false, nullptr, nullptr, *T.mp, T.s));
+        GBLA_TRY(modgemm_to_planes(*T.Zt, lo, *T.Ct, 0, *T.XT, 0, w, rows_hi, w, *T.mp, T.err, T.s, T.ctr, lo));
+    }
+    return GBLA_OK;
+}
+
 // Nm = I - Z elementwise (u16, n_total elements of L x L blocks).
 __global__ void i_minus_kernel(uint16_t *__restrict__ Z, int L, int64_t total, uint32_t p)
 {

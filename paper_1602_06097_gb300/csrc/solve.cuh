@@ -43,6 +43,37 @@ int trsm_upper(const TrsmUpper &T);
 int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
                         uint32_t *err, cudaStream_t s);
 
+// Leaf inverses as upper_leaf_inverses, from A's diagonal blocks alone:
+// Adiag (round_up(npiv, L) x L uint16) row k holds A[k][c] at column c % L for
+// the columns c of k's own block (sparse_build).
+int upper_leaf_inverses_diag(const uint16_t *Adiag, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
+                             uint32_t *err, cudaStream_t s);
+
+// X * A = C on the sparse path (tensor-core variant): the transposed solution
+// X^T is written to the A-operand planes XT (rows = pivots, K = rows of C).
+// Left-looking over leaves J of width L:
+//   C_J -= X_{<J} * A_{<J,J}   gathered product over SA (K-compacted A),
+//   X_J^T = Z_J^T * C_J^T      one product with Z_J = A_JJ^-1 (Zt),
+// only for the rows whose lead is left of the leaf's end (rows ascending by
+// lead).  C16 is modified; XT must be zero on entry.
+struct TrsmSparse {
+    int64_t mrows, npiv;
+    uint16_t *C16;
+    int64_t ldc;
+    const Compact *SA;
+    const Planes *Zt;     // B-operand planes of the leaf inverses (rows npiv, K = L)
+    const Planes *Ct;     // 4-plane scratch of mrows x L: C_J as B-operand
+    const Planes *XT;     // out
+    int L;
+    const ModP *mp;
+    uint32_t *err;
+    cudaStream_t s;
+    GemmCounters *ctr;
+    const int32_t *lead_dev;
+    const std::vector<int32_t> *lead_host;
+};
+int trsm_sparse(const TrsmSparse &T);
+
 // X' * A^T = C' (A^T unit lower triangular), X' overwrites C'.
 struct TrsmLower {
     int64_t mrows, npiv;

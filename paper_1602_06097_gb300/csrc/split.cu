@@ -336,8 +336,9 @@ void pivot_free(PivotInfo *pi, cudaStream_t s)
 
 // ---------------------------------------------------------------- (a3)
 // One warp per input row.  Pivot rows are normalised by the inverse of their
-// leading coefficient and go to A (pivot columns) and B (other columns);
-// other rows go to C and D.  All four blocks are dense uint16 row-major here;
+// leading coefficient and go to A (pivot columns) and B (other columns),
+// unless A16 is null (the sparse path keeps them sparse); other rows go to C
+// and D.  All four blocks are dense uint16 row-major here;
 // the digit planes the tensor-core product reads are made from A and B by a
 // tiled transposing conversion (coalesced on both sides).
 __global__ void split_scatter_kernel(int64_t m, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
@@ -356,6 +357,7 @@ __global__ void split_scatter_kernel(int64_t m, const int64_t *__restrict__ row_
     const int64_t b = row_ptr[r], e = row_ptr[r + 1];
     const bool is_piv = (int64_t)(best[l] & 0xFFFFFFFFull) == r;
     if (is_piv) {
+        if (!A16) return;   // sparse path: pivot rows go to sparse_build
         const int64_t k = colmap[l];
         const uint32_t inv = inv_lead[k];
         for (int64_t i = b + lane; i < e; i += 32) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace gbla {
 
@@ -54,6 +55,16 @@ int split_scatter(const DevCSR &in, const PivotInfo &pi, uint16_t *A16, int64_t 
                   uint16_t *C16, int64_t ldc, uint16_t *D16, int64_t ldd, const ModP &mp, cudaStream_t s);
 
 int multiline_build(const DevCSR &in, const PivotInfo &pi, Multiline *ml, const ModP &mp, cudaStream_t s);
+
+// The pivot rows as sparse operands (sparse.cu): Adiag (round_up(npiv, L) x L
+// uint16, zeroed here) <- A's diagonal blocks of width L; SA <- A's
+// off-diagonal blocks and SB <- B, K-compacted per 128-column tile.
+int sparse_build(const DevCSR &in, const PivotInfo &pi, int L, uint16_t *Adiag, Compact *SA, Compact *SB,
+                 const ModP &mp, cudaStream_t s);
+
+// A sparse K x N matrix S (device CSR, validated here: GBLA_E_INVAL on a
+// malformed one) as a compacted operand (rows = K).
+int compact_from_csr(const DevCSR &S, Compact *out, const ModP &mp, uint32_t *err, cudaStream_t s);
 void multiline_free(Multiline *ml, cudaStream_t s);
 
 int multiline_pairs(int64_t m, const int64_t *row_ptr, const int32_t *col, const uint16_t *val, int64_t *ml_ptr_dev,

@@ -17,12 +17,13 @@ LIB_PATH = os.path.join(_HERE, "libgbla.so")
 
 GBLA_OK = 0
 GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT = 0, 1, 2
+PATH_AUTO, PATH_DENSE, PATH_SPARSE = 0, 1, 2
 
 EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
            "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc",
            "gbla_selftest_wait_timeout", "gbla_reduce_batch", "gbla_server_create", "gbla_server_submit",
            "gbla_server_wait", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy",
-           "gbla_decode_format2"]
+           "gbla_decode_format2", "gbla_spmm"]
 
 
 class CsrIn(ctypes.Structure):
@@ -38,7 +39,12 @@ class CsrOut(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("want_reduced", ctypes.c_int), ("gemm_variant", ctypes.c_int),
-                ("device_ptrs", ctypes.c_int), ("panel_width", ctypes.c_int)]
+                ("device_ptrs", ctypes.c_int), ("panel_width", ctypes.c_int),
+                ("path", ctypes.c_int), ("leaf_width", ctypes.c_int)]
+
+
+def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0):
+    return Options(1 if want_reduced else 0, int(variant), int(device_ptrs), 0, int(path), int(leaf))
 
 
 class Stats(ctypes.Structure):
@@ -47,7 +53,9 @@ class Stats(ctypes.Structure):
                 ("ms_schur", ctypes.c_double), ("ms_echelon", ctypes.c_double),
                 ("ms_backsub", ctypes.c_double), ("ms_output", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("mod_ops", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("schur_mod_ops", ctypes.c_double), ("ms_echelon_back", ctypes.c_double)]
+                ("schur_mod_ops", ctypes.c_double), ("ms_echelon_back", ctypes.c_double),
+                ("path", ctypes.c_int64), ("list_a", ctypes.c_int64), ("list_b", ctypes.c_int64),
+                ("leaf_width", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -100,6 +108,8 @@ def load():
         lib.gbla_modmatmul.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, u32, i32, i32, vp]
         lib.gbla_modmatmul.restype = i32
         lib.gbla_pivots.argtypes = [ctypes.POINTER(CsrIn), u32, vp, ctypes.POINTER(i64), vp]
+        lib.gbla_spmm.restype = i32
+        lib.gbla_spmm.argtypes = [i64, i64, i64, vp, i64, ctypes.POINTER(CsrIn), vp, vp, i64, u32, i32, vp]
         lib.gbla_pivots.restype = i32
         lib.gbla_multiline.argtypes = [ctypes.POINTER(CsrIn), vp, vp, vp, vp]
         lib.gbla_multiline.restype = i32
@@ -180,16 +190,19 @@ class HostResult:
             pass
 
 
-def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None) -> HostResult:
+def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
+                path=PATH_AUTO, leaf=0) -> HostResult:
     """Reduce a host CSR matrix; the result stays in library-owned host memory
-    (see HostResult).  Page-locked inputs copy to the device fastest."""
+    (see HostResult).  Page-locked inputs copy to the device fastest.
+    ``path`` is PATH_AUTO, PATH_DENSE or PATH_SPARSE, ``leaf`` the leaf width
+    of the triangular solve (0 = chosen per matrix)."""
     lib = load()
     m, n = int(shape[0]), int(shape[1])
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.uint16)
     cin = CsrIn(m, n, int(len(col)), row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data)
-    opt = Options(1 if want_reduced else 0, int(variant), 0, 0)
+    opt = _options(want_reduced, variant, 0, path, leaf)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
@@ -199,10 +212,12 @@ def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AU
     return HostResult(out, int(rank.value), st.as_dict())
 
 
-def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None):
+def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None,
+           path=PATH_AUTO, leaf=0):
     """Reduce a host CSR matrix.  Returns (rank, row_ptr, col, val) as numpy
     arrays the caller owns (and a stats dict when ``stats``)."""
-    h = reduce_host(row_ptr, col, val, shape, p, want_reduced=want_reduced, variant=variant, stream=stream)
+    h = reduce_host(row_ptr, col, val, shape, p, want_reduced=want_reduced, variant=variant, stream=stream,
+                    path=path, leaf=leaf)
     try:
         res = (h.rank, h.row_ptr.copy(), h.col.copy(), h.val.copy())
         st = h.stats
@@ -277,14 +292,15 @@ class _CudaArray:
                                          "data": (int(ptr or 0), False), "version": 3, "strides": None}
 
 
-def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None):
+def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
+                  path=PATH_AUTO, leaf=0):
     """Reduce a CSR matrix already on the device (torch CUDA tensors: int64
     row_ptr, int32 col, int16/uint16 val).  Returns a DeviceResult whose
     arrays stay in device memory."""
     lib = load()
     m, n = int(shape[0]), int(shape[1])
     cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
-    opt = Options(1 if want_reduced else 0, int(variant), 1, 0)
+    opt = _options(want_reduced, variant, 1, path, leaf)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
@@ -320,7 +336,7 @@ def _csr_in(row_ptr, col, val, shape):
     return cin, (row_ptr, col, val)
 
 
-def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0):
+def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PATH_AUTO):
     """Reduce many host CSR matrices on a pool of worker threads (their device
     work is serialised by the library's device lock).  ``mats`` is a list of
     (row_ptr, col, val, shape, p).  Returns a list of (rank, row_ptr, col, val)
@@ -335,7 +351,7 @@ def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0):
         keep.append(arrs)
         ins[i] = cin
         ps[i] = int(p)
-    opt = Options(1 if want_reduced else 0, int(variant), 0, 0)
+    opt = _options(want_reduced, variant, 0, path)
     outs = (CsrOut * max(n, 1))()
     ranks = (ctypes.c_int64 * max(n, 1))()
     codes = (ctypes.c_int * max(n, 1))()
@@ -360,9 +376,9 @@ class Server:
         _check(self._lib.gbla_server_create(int(mem_budget), int(workers), ctypes.byref(self._h)),
                "gbla_server_create")
 
-    def submit(self, row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO):
+    def submit(self, row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, path=PATH_AUTO):
         cin, _arrs = _csr_in(row_ptr, col, val, shape)   # copied by the server at submit
-        opt = Options(1 if want_reduced else 0, int(variant), 0, 0)
+        opt = _options(want_reduced, variant, 0, path)
         t = ctypes.c_int64(0)
         _check(self._lib.gbla_server_submit(self._h, ctypes.byref(cin), int(p), ctypes.byref(opt), ctypes.byref(t)),
                "gbla_server_submit")
@@ -416,6 +432,21 @@ def modmatmul(A, B, C, p, sign=-1, variant=GEMM_AUTO, stream=None):
     rc = lib.gbla_modmatmul(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                             C.data_ptr(), C.stride(0), int(p), int(sign), int(variant), _stream_ptr(stream))
     _check(rc, "gbla_modmatmul")
+
+
+def spmm(X, S_row_ptr, S_col, S_val, N, C, p, sign=-1, x_lead=None, stream=None):
+    """C <- (C + sign * X * S) mod p in place: X (M x K) and C (M x N) 2-D
+    row-major CUDA tensors of 16-bit values, S a K x N CSR matrix given by
+    CUDA tensors (int64 row_ptr, int32 col, 16-bit val); x_lead an optional
+    int32 CUDA tensor of ascending row leads of X.  Runs the K-compacted
+    tensor-core product of the sparse path."""
+    lib = load()
+    M, K = X.shape
+    cin = CsrIn(K, int(N), int(S_col.numel()), S_row_ptr.data_ptr(), S_col.data_ptr(), S_val.data_ptr())
+    rc = lib.gbla_spmm(M, int(N), K, X.data_ptr(), X.stride(0), ctypes.byref(cin),
+                       None if x_lead is None else x_lead.data_ptr(), C.data_ptr(), C.stride(0), int(p),
+                       int(sign), _stream_ptr(stream))
+    _check(rc, "gbla_spmm")
 
 
 def pivots(row_ptr, col, val, shape, p, stream=None):

@@ -38,14 +38,17 @@ def test_clock_summary_skips_malformed_lines():
 
 
 def test_traffic_reported_only_for_the_measured_kernel_source(tmp_path, monkeypatch):
+    import hashlib
     rel_src = os.path.join("paper_1602_06097_gb300", "csrc", "modgemm.cu")
     rel_prof = os.path.join("profiles", "modgemm_tc_schur_traffic_fl_40000x60000.md")
-    for rel in (rel_src, rel_prof):
-        os.makedirs(tmp_path / os.path.dirname(rel), exist_ok=True)
-        shutil.copy(os.path.join(ROOT, rel), tmp_path / rel)
+    os.makedirs(tmp_path / os.path.dirname(rel_src), exist_ok=True)
+    os.makedirs(tmp_path / "profiles", exist_ok=True)
+    shutil.copy(os.path.join(ROOT, rel_src), tmp_path / rel_src)
+    digest = hashlib.sha256(open(tmp_path / rel_src, "rb").read()).hexdigest()
+    (tmp_path / rel_prof).write_text(f"traffic_bytes_per_launch: 81070000000\nkernel_source_sha256: {digest}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     figure = bench.profiled_traffic()
-    assert isinstance(figure, int) and figure > 10 ** 10
+    assert isinstance(figure, int) and figure == 81070000000
     with open(tmp_path / rel_src, "a") as f:
         f.write("\n// edited\n")
     assert bench.profiled_traffic() is None
