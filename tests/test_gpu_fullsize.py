@@ -2,9 +2,13 @@
 configuration the benchmark times (input resident on the device, echelon
 form of the new order).
 
-The oracle cannot reduce this matrix within test time, so the result is
-checked against what the oracle computes exactly at this size and against
-properties that hold at any size:
+The oracle needs about ten minutes of CPU for this matrix, so its result was
+computed once by ``tests/golden/make_oracle_digest.py`` (which calls only the
+oracle and the input generator) and stored as a SHA-256 digest of its CSR
+arrays in ``tests/golden/oracle_fl_40000x60000.json``: the GPU result must
+hash to the same digest (bit-exact, both paths).  Beside that exact check the
+result is checked against what the oracle computes exactly at this size and
+against properties that hold at any size:
 
 1. The top block is exactly the oracle's choice of pivot rows (FL step 1,
    Sec. 3.1: fewest nonzeros, then smallest row index), each row multiplied by
@@ -19,6 +23,10 @@ properties that hold at any size:
    up) are annihilated by every input row.  An input row outside the span
    passes one such vector with probability 1/p.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -67,6 +75,40 @@ def full():
         res.free()
     out = (int(rank), orp.astype(np.int64), oc.astype(np.int64), ov.astype(np.int64))
     return spec, (rp, c.astype(np.int64), v.astype(np.int64)), out, stats
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_fl_40000x60000.json")
+
+
+def sha256_csr(row_ptr, col, val):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(row_ptr, dtype="<i8").tobytes())
+    h.update(np.ascontiguousarray(col, dtype="<i4").tobytes())
+    h.update(np.ascontiguousarray(val, dtype="<u2").tobytes())
+    return h.hexdigest()
+
+
+def test_fullsize_equals_the_oracle_bit_for_bit(full):
+    spec, (rp, c, v), (rank, orp, oc, ov), st = full
+    g = json.load(open(GOLDEN))
+    assert sha256_csr(rp, c, v) == g["input_sha256"], "the generated input is not the one the oracle reduced"
+    assert rank == g["rank"] and st["npiv"] == g["npiv"] and len(oc) == g["nnz"]
+    assert sha256_csr(orp, oc, ov) == g["result_sha256"]
+
+
+def test_fullsize_dense_path_equals_the_oracle_bit_for_bit(full):
+    spec, (rp, c, v), _, _ = full
+    g = json.load(open(GOLDEN))
+    d = (torch.from_numpy(rp).cuda(), torch.from_numpy(c.astype(np.int32)).cuda(),
+         torch.from_numpy(v.astype(np.uint16).view(np.int16)).cuda())
+    res = gbla.reduce_device(*d, (spec.m, spec.n), spec.p, path=gbla.PATH_DENSE)
+    try:
+        rank, orp, oc, ov = res.to_host()
+        assert res.stats["path"] == gbla.PATH_DENSE
+    finally:
+        res.free()
+    assert rank == g["rank"]
+    assert sha256_csr(orp, oc, ov) == g["result_sha256"]
 
 
 def test_fullsize_counts(full):
