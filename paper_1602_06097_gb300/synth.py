@@ -49,6 +49,11 @@ class FLSpec:
     group: tuple | None = None
     share: float = 0.8
     seed: int = 20160219
+    # banded layout (see banded_matrix): band and block widths in pivot
+    # columns, fraction of A entries crossing into the next block
+    band: int | None = None
+    block: int = 4096
+    cross: float = 0.05
 
 
 def _runs(rng, lead, k, n, run_len):
@@ -107,6 +112,8 @@ def _row_counts(rng, nrows, density, n, spread):
 
 def fl_matrix(spec: FLSpec):
     """Draw one matrix.  Returns (row_ptr int64[m+1], col int32[nnz], val uint16[nnz])."""
+    if spec.band is not None:
+        return banded_matrix(spec)
     rng = np.random.Generator(np.random.PCG64(spec.seed))
     m, n, npiv, p = spec.m, spec.n, spec.npiv, spec.p
     if not (0 <= npiv <= min(m, n)):
@@ -205,6 +212,125 @@ def _grouped(rng, spec, lead, k, piv_leads, from_piv, which):
     return rows.astype(np.int64), cols.astype(np.int64)
 
 
+def _assemble(rng, m, p, lead, rows, cols, monic_rows):
+    """CSR of rows with leading column lead[i] and other entries (rows, cols)
+    (sorted by row then column, all right of the lead); values uniform in
+    [1, p-1], the leads of monic_rows set to 1; rows shuffled."""
+    counts = np.bincount(rows, minlength=m).astype(np.int64) + 1
+    row_ptr = np.zeros(m + 1, np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    nnz = int(row_ptr[-1])
+    col = np.empty(nnz, np.int64)
+    col[row_ptr[:-1]] = lead
+    rank_in_row = np.arange(len(rows), dtype=np.int64) - np.repeat(
+        np.concatenate([[0], np.cumsum(counts - 1)[:-1]]), counts - 1)
+    col[row_ptr[rows] + 1 + rank_in_row] = cols
+    del rank_in_row
+    val = rng.integers(1, p, size=nnz, dtype=np.int64).astype(np.uint16)
+    val[row_ptr[monic_rows]] = 1
+    perm = rng.permutation(m)
+    cnt = counts[perm]
+    new_ptr = np.zeros(m + 1, np.int64)
+    np.cumsum(cnt, out=new_ptr[1:])
+    src = np.repeat(row_ptr[perm] - new_ptr[:-1], cnt) + np.arange(nnz, dtype=np.int64)
+    return new_ptr, col[src].astype(np.int32), val[src]
+
+
+def banded_matrix(spec: FLSpec):
+    """A matrix whose A block is banded and nearly block-diagonal, with rows
+    in multiline pairs (the large F4 shape of Sec. 4.2).
+
+    Recipe (``numpy.random.Generator(PCG64(seed))``):
+
+    1. ``npiv`` distinct pivot columns P (sorted) are drawn uniformly in
+       [0, n); Q are the other columns.  Pivot row i leads at P[i] with a 1.
+    2. Each row gets ``k = density * n * U[1-spread, 1+spread]`` entries
+       right of its lead, a share npiv/n of them at pivot columns (the A or C
+       part) and the rest at the other columns (B or D), in runs of lengths
+       ``run_len``.  A-part runs lie in pivot indices (i, i + band], cut at the
+       end of i's block of ``block`` pivot indices; a fraction ``cross`` of
+       them lies in the next block.  B-part runs lie in the window of
+       ``block * (n - npiv) / npiv`` other columns that follows the lead.
+    3. Pivot rows come in pairs (2q, 2q + 1): the second copies the runs of
+       the first that lie right of its own lead, each run kept with
+       probability ``share``, and is topped up with fresh runs to its count.
+    4. The other m - npiv rows lead, with probability ``lead_from_pivot``, at
+       the lead of a random pivot row, else at a random other column (their
+       lead value uniform in [1, p-1]), and get runs by the same rule from
+       their lead.
+    5. All other values are uniform in [1, p-1]; rows are shuffled.
+    """
+    rng = np.random.Generator(np.random.PCG64(spec.seed))
+    m, n, npiv, p = spec.m, spec.n, spec.npiv, spec.p
+    if not (0 < npiv <= min(m, n)):
+        raise ValueError("need 0 < npiv <= min(m, n)")
+    band, block = int(spec.band), int(spec.block)
+    P = np.sort(rng.choice(n, size=npiv, replace=False)).astype(np.int64)
+    is_piv = np.zeros(n, bool)
+    is_piv[P] = True
+    Q = np.nonzero(~is_piv)[0].astype(np.int64)
+    nq = len(Q)
+    wb = max(1, int(block * nq / npiv))
+    mnp = m - npiv
+    from_piv = rng.random(mnp) < spec.lead_from_pivot
+    which = rng.integers(0, npiv, size=mnp)
+    lead_np = np.where(from_piv, P[which], Q[rng.integers(0, max(nq, 1), size=mnp)] if nq else P[which])
+    lead = np.concatenate([P, lead_np]).astype(np.int64)
+    # first pivot index and first other-column index right of each lead
+    ia = np.searchsorted(P, lead, side="right")
+    ib = np.searchsorted(Q, lead, side="right")
+    k = _row_counts(rng, m, spec.density, n, spec.spread) - 1
+    ka = np.rint(k * (npiv / n)).astype(np.int64)
+    kb = k - ka
+    kc = np.rint(ka * spec.cross).astype(np.int64)
+    ka -= kc
+    blk_end = np.minimum((np.maximum(ia - 1, 0) // block + 1) * block, npiv)
+    hi_a = np.minimum(ia + band, blk_end)
+    ka = np.clip(np.minimum(ka, hi_a - ia), 0, None)
+    hi_c = np.minimum(blk_end + block, npiv)
+    kc = np.clip(np.minimum(kc, hi_c - blk_end), 0, None)
+    hi_b = np.minimum(ib + wb, nq)
+    kb = np.clip(np.minimum(kb, hi_b - ib), 0, None)
+    # runs inside windows: _runs places k[i] entries in runs right of
+    # lead[i] and below its (per-row) bound
+    ra, ca = _runs(rng, ia - 1, ka, hi_a, spec.run_len)
+    rc, cc = _runs(rng, blk_end - 1, kc, hi_c, spec.run_len)
+    rb, cb = _runs(rng, ib - 1, kb, hi_b, spec.run_len)
+    rows = np.concatenate([ra, rc, rb])
+    cols = np.concatenate([P[ca], P[cc], Q[cb]])
+    del ra, ca, rc, cc, rb, cb
+    # multiline pairs: row 2q+1 shares the runs of row 2q right of its lead
+    key = rows * (n + 1) + cols
+    first = rows < npiv
+    first &= (rows % 2 == 0) & (rows + 1 < npiv)
+    fr, fc = rows[first], cols[first]
+    brk = np.ones(len(fc), bool)
+    if len(fc):
+        brk[1:] = (fc[1:] != fc[:-1] + 1) | (fr[1:] != fr[:-1])
+    run_id = np.cumsum(brk) - 1
+    keep_run = rng.random(int(run_id[-1]) + 1 if len(run_id) else 0) < spec.share
+    keep = keep_run[run_id] & (fc > lead[fr + 1]) if len(fc) else np.zeros(0, bool)
+    second_rows = fr[keep] + 1
+    second_cols = fc[keep]
+    del fr, fc, brk, run_id, keep
+    drop = (rows % 2 == 1) & (rows < npiv)
+    # the second row's own runs fill up to its count after the shared ones
+    have = np.bincount(second_rows, minlength=m)
+    own = np.nonzero(drop)[0]
+    rank_in_row = np.arange(len(rows), dtype=np.int64) - np.repeat(
+        np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=m))[:-1]]), np.bincount(rows, minlength=m))
+    keep_own = ~drop | (rank_in_row < np.maximum(np.bincount(rows, minlength=m) - have, 0)[rows])
+    del rank_in_row, own
+    rows = np.concatenate([rows[keep_own], second_rows])
+    cols = np.concatenate([cols[keep_own], second_cols])
+    del keep_own, second_rows, second_cols, key
+    key = _sorted_unique(rows * (n + 1) + cols)
+    rows = key // (n + 1)
+    cols = key % (n + 1)
+    del key
+    return _assemble(rng, m, p, lead, rows, cols, np.arange(npiv))
+
+
 # Named workloads (sizes from the F4 shape statistics quoted above).
 WORKLOADS = {
     # 2,000 x 3,000, 1,200 pivots, 4% density, runs of 4-32: the small case.
@@ -213,6 +339,11 @@ WORKLOADS = {
     # groups of 2-16 rows sharing ~80% of their pattern.
     "fl_40000x60000": FLSpec(m=40000, n=60000, npiv=30000, density=0.015, run_len=(112, 450),
                              group=(2, 16), share=0.8, seed=20160220),
+    # 150,000 x 200,000, 120,000 pivots, 0.5% density (~150M nonzeros), rows
+    # in multiline pairs sharing ~90% of their pattern, A banded (2,048
+    # pivot columns) in diagonal blocks of 4,096 with 5% cross-block entries.
+    "fl_150000x200000": FLSpec(m=150000, n=200000, npiv=120000, density=0.005, run_len=(4, 32),
+                               share=0.9, band=2048, block=4096, cross=0.05, seed=20160221),
 }
 
 
