@@ -896,10 +896,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // (cp.async), while one thread loads the compacted S chunk by TMA.  Rows of X
 // are ascending by lead (first nonzero column), so a tile skips the list
 // entries left of its raster group's first lead.
-constexpr int G_WARPS = 2;
-constexpr int G_THREADS = 64 + 32 * EPI_WARPS + 32 * G_WARPS;
-constexpr int G_LAG = 2;   // stages a gather thread keeps in flight before signalling the oldest
+// Warp roles: 0 TMA producer of the compacted operand, 1 MMA issuer, 2..5
+// drain (one per TMEM lane quarter, all 128 columns), 6..9 gather (warp
+// 6 + s fills ring slot s).
+constexpr int G_EPI_WARPS = 4;
+constexpr int G_GATHER_WARPS = STAGES;
+constexpr int G_THREADS = 64 + 32 * G_EPI_WARPS + 32 * G_GATHER_WARPS;
 constexpr int G_CHUNKS = (2 * BM * BK * 2) / 16;   // 16-byte copies per stage (1024)
+// The drain's running residues (128 rows x 128 columns, two per word) live in
+// shared memory after the ring, column pair major so that the 32 lanes of a
+// warp (32 rows) touch 32 banks.
+constexpr int G_RUN_BYTES = BM * BN * 2;
+constexpr int G_SMEM_BYTES = SMEM_BYTES + G_RUN_BYTES;
 
 struct GArgs {
     int64_t M, N;            // rows of X taking part; output columns (from column 0 of C)
@@ -909,7 +917,8 @@ struct GArgs {
     const __nv_bfloat16 *xt; // XT plane set (2 planes, rows = j, K = r)
     int64_t xt_row_elems;    // elements per XT row
     int64_t xt_rows;         // list entries >= xt_rows (padding) read as zero
-    const int32_t *row_lead; // ascending lead (absolute j) of each row of X, or null
+    const int32_t *kstart;   // [raster groups x output tiles]: first list entry of the tile's
+                             // K range (0 without row leads), from gather_starts_kernel
     uint16_t *C;
     int64_t ldc;
     int sign;
@@ -918,6 +927,28 @@ struct GArgs {
     uint32_t *err;
     int group_m;
 };
+
+// First list entry at or after the raster group's first lead, for every
+// (raster group, output tile): all tiles of a group walk K from there (X is
+// zero left of a row's lead, rows ascending by lead), so that concurrent CTAs
+// share operand tiles in L2.  One thread per entry, a binary search.
+__global__ void gather_starts_kernel(int64_t ngroups, int64_t num_n, int64_t nt0, int group_m,
+                                     const int64_t *__restrict__ koff, const int32_t *__restrict__ kidx,
+                                     const int32_t *__restrict__ row_lead, int32_t *__restrict__ kstart)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ngroups * num_n) return;
+    const int64_t grp = i / num_n, nt = i % num_n;
+    const int64_t kb = koff[nt0 + nt], ke = koff[nt0 + nt + 1];
+    const int32_t L = row_lead[grp * group_m * BM];
+    int64_t lo = kb, hi = ke;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (kidx[mid] < L) lo = mid + 1;
+        else hi = mid;
+    }
+    kstart[i] = (int32_t)(lo - kb);
+}
 
 struct GTile {
     int64_t mt, nt, chunk0;
@@ -930,17 +961,7 @@ __device__ __forceinline__ GTile gtile(const GArgs &g, int64_t t, int64_t num_m,
     const int64_t kb = g.koff[g.nt0 + ti.nt], ke = g.koff[g.nt0 + ti.nt + 1];
     ti.chunk0 = kb / BK;
     ti.ksteps = (int)((ke - kb) / BK);
-    int64_t s = 0;
-    if (g.row_lead) {   // first list entry at or after the group's first lead
-        const int32_t L = g.row_lead[(ti.mt / g.group_m) * g.group_m * BM];
-        int64_t lo = kb, hi = ke;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (g.kidx[mid] < L) lo = mid + 1;
-            else hi = mid;
-        }
-        s = lo - kb;
-    }
+    const int64_t s = g.kstart ? (int64_t)g.kstart[(ti.mt / g.group_m) * num_n + ti.nt] : 0;
     ti.ks0 = (int)(s / BK) & ~(STAGES - 1);   // whole rounds of the stage ring
     return ti;
 }
@@ -1004,16 +1025,17 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
     uint64_t *done = acce + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint32_t *run_s = reinterpret_cast<uint32_t *>(tiles + STAGES * STAGE_BYTES + BAR_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1 + 32 * G_WARPS);   // the TMA thread and every gather thread
+            mbar_init(&full[s], 1 + 32);   // the TMA thread and the slot's gather warp
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], EPI_WARPS);
+            mbar_init(&acce[b], G_EPI_WARPS);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
@@ -1121,10 +1143,10 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
                 break;
             }
         }
-    } else if (warp < 2 + EPI_WARPS) {
-        // ---------------- drain: as in modgemm_tc_kernel
+    } else if (warp < 2 + G_EPI_WARPS) {
+        // ---------------- drain: one warp per TMEM lane quarter, all 128
+        // columns; otherwise as in modgemm_tc_kernel
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
         const float pinv = g.pinv;
         const int P = (int)g.p;
@@ -1137,26 +1159,26 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
             const GTile ti = gtile(g, t, num_m, num_n);
             const int kbt = (ti.ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
             if (kbt <= 0) continue;   // no list entry on this tile: C stays as it is
-            uint32_t run[HC / 2];
-#pragma unroll
-            for (int i = 0; i < HC / 2; ++i) run[i] = 0;
+            uint32_t *rs = run_s + row_in_tile;   // column pair i at rs[128 i]
+#pragma unroll 8
+            for (int i = 0; i < BN / 2; ++i) rs[BM * i] = 0;
             for (int kb = 0; kb < kbt; ++kb, ++kbc) {
                 const uint32_t buf = kbc & 1u, use = kbc >> 1;
                 if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
                 tcgen05_fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * 256u + half * HC;
-#pragma unroll
-                for (int c = 0; c < HC / 16; ++c) {
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * 256u;
+#pragma unroll 2
+                for (int c = 0; c < BN / 16; ++c) {
                     float pv[16], qv[16];
                     tmem_ld16(tbase + c * 16, pv);
                     tmem_ld16(tbase + 128 + c * 16, qv);
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
-                        uint32_t pair = run[c * 8 + j / 2];
+                        const uint32_t pair = rs[BM * (c * 8 + j / 2)];
                         const int lo16 = drain_step((int)(pair & 0xFFFFu), pv[j], qv[j], pinv, P, bias, bm);
                         const int hi16 = drain_step((int)(pair >> 16), pv[j + 1], qv[j + 1], pinv, P, bias, bm);
-                        run[c * 8 + j / 2] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
+                        rs[BM * (c * 8 + j / 2)] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
                     }
                 }
                 tcgen05_fence_before();
@@ -1165,55 +1187,59 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
             }
             if (!ok) break;
             const int64_t row = ti.mt * BM + row_in_tile;
-            const int64_t col0 = ti.nt * BN + half * HC;
-            if (row < g.M && col0 < g.N) rmw_segment(g.C + row * g.ldc + col0, col0, g.N, run, g.sign, P);
+            if (row < g.M) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t col0 = ti.nt * BN + h * HC;
+                    if (col0 >= g.N) break;
+                    uint32_t part[HC / 2];
+#pragma unroll
+                    for (int i = 0; i < HC / 2; ++i) part[i] = rs[BM * (h * (HC / 2) + i)];
+                    rmw_segment(g.C + row * g.ldc + col0, col0, g.N, part, g.sign, P);
+                }
+            }
         }
     } else {
-        // ---------------- gather warps: X^T rows of the listed j into the
-        // A stage (MN-major, 128-byte swizzle), cp.async 16 bytes at a time.
-        // Copy i of a stage: list entry kk = i / 32 (one warp instruction
-        // moves one entry's 512 bytes), 16-byte piece q = i % 32 of it, which
-        // holds rows rl .. rl + 7 (rl = 32 (q / 8) + 8 (q % 4)) of plane
-        // (q / 4) % 2.
-        const int gt = threadIdx.x - (64 + 32 * EPI_WARPS);
-        const uint32_t sbase = smem_u32(tiles);
-        int stage = 0, last = 0, npend = 0;
-        uint32_t phase = 0;
+        // ---------------- gather warps: warp 6 + s fills ring slot s with
+        // the X^T rows of the stage's 32 listed j (MN-major, 128-byte
+        // swizzle), cp.async 16 bytes at a time.  Copy i: list entry kk =
+        // i / 32 (one instruction moves an entry's 512 bytes), piece q = i % 32
+        // = lane, holding rows rl .. rl + 7 (rl = 32 (q / 8) + 8 (q % 4)) of
+        // plane (q / 4) % 2.  The warp reads the stage's list entries with one
+        // load (lane l: entry l) before its wait for the slot, waits for its
+        // own copies, fences them to the tensor core's proxy and signals; the
+        // other slots' warps go on independently.
+        const int slot = warp - 2 - G_EPI_WARPS;
+        const uint32_t abase = smem_u32(tiles) + slot * STAGE_BYTES;
+        const int q = lane;
+        const int rl = (q >> 3) * 32 + (q & 3) * 8;
+        const uint32_t dst_lane = ((q >> 2) & 1) * 8192 + (rl >> 6) * 1024 + ((((rl & 63) >> 3)) << 4);
+        uint32_t seq = 0, use = 0;
         bool ok = true;
         for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
             const GTile ti = gtile(g, t, num_m, num_n);
-            const __nv_bfloat16 *xseg = g.xt + (ti.mt * BM / 32) * 64;   // the row tile's 512 bytes in an XT row
-            for (int ks = ti.ks0; ks < ti.ksteps; ++ks) {
-                if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
-                const uint32_t abase = sbase + stage * STAGE_BYTES;
+            const __nv_bfloat16 *xseg = g.xt + (ti.mt * BM / 32) * 64 + q * 8;   // this lane's piece
+            for (int ks = ti.ks0; ks < ti.ksteps; ++ks, ++seq) {
+                if ((int)(seq & (STAGES - 1)) != slot) continue;
                 const int64_t kbase = (ti.chunk0 + ks) * BK;
-#pragma unroll 4
-                for (int i = gt; i < G_CHUNKS; i += 32 * G_WARPS) {
-                    const int q = i & 31, kk = i >> 5;
-                    const int64_t j = g.kidx[kbase + kk];
+                const int32_t jl = g.kidx[kbase + lane];
+                if (!mbar_wait_warp(&empty[slot], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+#pragma unroll 8
+                for (int kk = 0; kk < BK; ++kk) {
+                    const int64_t j = __shfl_sync(0xFFFFFFFFu, jl, kk);
                     const bool valid = j < g.xt_rows;
-                    const int rl = (q >> 3) * 32 + (q & 3) * 8;
-                    const uint32_t dst = abase + ((q >> 2) & 1) * 8192 + (kk >> 3) * 2048 + (rl >> 6) * 1024 +
-                                         (kk & 7) * 128 + ((((rl & 63) >> 3) ^ (kk & 7)) << 4);
-                    const __nv_bfloat16 *src = valid ? xseg + j * g.xt_row_elems + q * 8 : g.xt;
-                    cp_async16(dst, src, valid ? 16u : 0u);
+                    // 16-byte chunk index XOR the row within the swizzle atom
+                    const uint32_t dst = abase + (kk >> 3) * 2048 + (kk & 7) * 128 + (dst_lane ^ ((kk & 7) << 4));
+                    cp_async16(dst, valid ? xseg + j * g.xt_row_elems : g.xt, valid ? 16u : 0u);
                 }
                 cp_async_commit();
-                last = stage;
-                if (++npend > G_LAG) {
-                    cp_async_wait<G_LAG>();
-                    fence_proxy_async();
-                    mbar_arrive(&full[(last + STAGES - G_LAG) % STAGES]);
-                    --npend;
-                }
-                if (++stage == STAGES) stage = 0, phase ^= 1u;
+                cp_async_wait<0>();
+                fence_proxy_async();
+                mbar_arrive(&full[slot]);
+                ++use;
             }
         }
-        // every copy completes before the thread leaves; the stages still
-        // owed a signal get it
-        cp_async_wait<0>();
-        fence_proxy_async();
-        for (int i = npend - 1; i >= 0; --i) mbar_arrive(&full[(last + STAGES - i) % STAGES]);
+        cp_async_wait<0>();   // nothing in flight when the warp leaves
     }
 
     tcgen05_fence_before();
@@ -1262,6 +1288,18 @@ static int gemm_group_m() {
         const char *e = getenv("GBLA_GEMM_GROUP_M");
         const int x = e ? atoi(e) : 0;
         v = (x >= 1 && x <= 256) ? x : (int)tc::GROUP_M_DEFAULT;
+    }
+    return v;
+}
+
+// Row tiles per raster group of the gathered product (env GBLA_GATHER_GROUP_M
+// overrides; 0 = chosen per launch).
+static int gather_group_m_env() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("GBLA_GATHER_GROUP_M");
+        const int x = e ? atoi(e) : 0;
+        v = (x >= 1 && x <= 1024) ? x : 0;
     }
     return v;
 }
@@ -1468,24 +1506,47 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
         return GBLA_E_CUDA;
     static std::once_flag attr_once;
     static cudaError_t attr_rc = cudaSuccess;
+    static int attr_threads = 0;
     std::call_once(attr_once, [] {
         attr_rc = cudaFuncSetAttribute(tc::modgemm_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tc::SMEM_BYTES);
+                                       tc::G_SMEM_BYTES);
+        cudaFuncAttributes fa;
+        if (attr_rc == cudaSuccess && (attr_rc = cudaFuncGetAttributes(&fa, tc::modgemm_gather_kernel)) == cudaSuccess)
+            attr_threads = fa.maxThreadsPerBlock;
     });
     GBLA_CUDA_TRY(attr_rc);
+    if (attr_threads < tc::G_THREADS) return GBLA_E_INTERNAL;   // the block would not fit the SM's registers
     tc::GArgs g{};
     g.M = M; g.N = N; g.nt0 = nt0;
     g.kidx = S.kidx; g.koff = S.koff;
     g.xt = XT.ptr; g.xt_row_elems = XT.row_elems(); g.xt_rows = xt_rows;
-    g.row_lead = row_lead;
     g.C = C; g.ldc = ldc; g.sign = sign;
     g.p = mp.p; g.pinv = mp.pinv;
     g.err = err;
-    g.group_m = gemm_group_m();
-    const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
+    g.group_m = gather_group_m_env() ? gather_group_m_env() : gemm_group_m();
+    const int64_t num_m = (M + tc::BM - 1) / tc::BM, num_n = (N + tc::BN - 1) / tc::BN;
+    int32_t *kstart = nullptr;
+    if (row_lead) {
+        const int64_t ngroups = (num_m + g.group_m - 1) / g.group_m;
+        GBLA_TRY(dalloc_t(&kstart, (size_t)(ngroups * num_n), s));
+        tc::gather_starts_kernel<<<(unsigned)((ngroups * num_n + 255) / 256), 256, 0, s>>>(
+            ngroups, num_n, nt0, g.group_m, S.koff, S.kidx, row_lead, kstart);
+        if (launch_check() != cudaSuccess) {
+            dfree(kstart, s);
+            return GBLA_E_CUDA;
+        }
+    }
+    g.kstart = kstart;
+    const int64_t tiles = num_m * num_n;
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
-    tc::modgemm_gather_kernel<<<grid, tc::G_THREADS, tc::SMEM_BYTES, s>>>(mb, g);
-    GBLA_CUDA_TRY(launch_check());
+    tc::modgemm_gather_kernel<<<grid, tc::G_THREADS, tc::G_SMEM_BYTES, s>>>(mb, g);
+    const cudaError_t e = cudaGetLastError();
+    ++g_launches;
+    dfree(kstart, s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "modgemm_gather_kernel", __FILE__, __LINE__);
+        return GBLA_E_CUDA;
+    }
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
 }
