@@ -15,6 +15,7 @@ followed (GBLA paper, arXiv 1602.06097):
   and the reduced-echelon pass (Sec. 4.1), Alg. 3's normalise/reduce rule.
 * :func:`echelon`  -- the new order of operations (Alg. 2, Sec. 4.3) in plain
   row form, then Gauss-Jordan of the Schur complement.
+* :func:`row_counts` -- the work counts of Alg. 2's row reduction alone.
 * :func:`pivots`   -- the FL step-1 pivot choice (Sec. 3.1, Sec. 4.1 step 1).
 * :func:`multiline` -- the 2-multiline vector of Definition 1 (Sec. 4.2).
 * :mod:`oracle.formats` -- readers of the two binary matrix files of Sec. 3.2
@@ -76,6 +77,9 @@ def _lib(mutant: int = 0):
                                        i64p, ctypes.POINTER(i64p), ctypes.POINTER(i32p),
                                        ctypes.POINTER(u16p), i64p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_row_counts.restype = ctypes.c_int
+        lib.oracle_row_counts.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, vp, vp, vp,
+                                          ctypes.POINTER(ctypes.c_double), i64p, ctypes.POINTER(ctypes.c_double)]
         lib.oracle_pivots.restype = ctypes.c_int64
         lib.oracle_pivots.argtypes = [ctypes.c_int64, ctypes.c_int64, vp, vp, vp]
         lib.oracle_free.restype = None
@@ -150,6 +154,23 @@ def echelon(m, n, p, row_ptr, col, val, mutant: int = 0, phase_seconds=None, ops
     if rc != 0:
         raise OracleError(f"oracle_echelon failed with code {rc}")
     return _take(lib, rank, rp, cl, vl) + (int(npiv.value),)
+
+
+def row_counts(m, n, p, row_ptr, col, val, mutant: int = 0):
+    """Work counts of Alg. 2's row reduction alone: returns (ops_b, ops_c,
+    npiv, seconds), the first two exactly as :func:`echelon` counts them,
+    without the Gauss-Jordan pass (for matrices whose Schur complement is too
+    large for it)."""
+    lib = _lib(mutant)
+    row_ptr, col, val = _csr_args(row_ptr, col, val)
+    ops = (ctypes.c_double * 2)()
+    npiv = ctypes.c_int64(0)
+    secs = ctypes.c_double(0)
+    rc = lib.oracle_row_counts(m, n, p, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data, ops,
+                               ctypes.byref(npiv), ctypes.byref(secs))
+    if rc != 0:
+        raise OracleError(f"oracle_row_counts failed with code {rc}")
+    return float(ops[0]), float(ops[1]), int(npiv.value), float(secs.value)
 
 
 def pivots(m, n, row_ptr, col, mutant: int = 0):

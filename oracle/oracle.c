@@ -478,3 +478,76 @@ fail0:
     free(is_piv_row);
     return rc;
 }
+
+/*
+ * Work counts of the row reduction of Alg. 2 alone (no Gauss-Jordan pass, no
+ * output), for matrices whose Schur complement is too large for the textbook
+ * pass: ops[0] = ops_b and ops[1] = ops_c exactly as oracle_echelon counts
+ * them (every non-pivot row reduced by the normalised pivot rows in ascending
+ * pivot column order, one op per entry of a pivot row with a nonzero
+ * multiplier), *npiv_out the pivot count.  seconds (optional) receives the
+ * wall time.
+ */
+int oracle_row_counts(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr, const int32_t *col,
+                      const uint16_t *val, double *ops, int64_t *npiv_out, double *seconds)
+{
+    double t0 = ora_now();
+    int rc = ora_validate(m, n, p, row_ptr, col, val);
+    if (rc) return rc;
+    int64_t *piv_row = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    uint64_t *inv_lead = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    char *is_piv_row = (char *)calloc((size_t)(m ? m : 1), 1);
+    int64_t *na = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+    int64_t *nb = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+    double ops_b = 0, ops_c = 0;
+    int fail = 0;
+    if (!piv_row || !inv_lead || !is_piv_row || !na || !nb) { rc = ORA_E_NOMEM; goto done; }
+    int64_t npiv = oracle_pivots(m, n, row_ptr, col, piv_row);
+    for (int64_t c = 0; c < n; ++c)
+        if (piv_row[c] >= 0) {
+            is_piv_row[piv_row[c]] = 1;
+            inv_lead[c] = ora_inv(val[row_ptr[piv_row[c]]], p);
+            for (int64_t e = row_ptr[piv_row[c]] + 1; e < row_ptr[piv_row[c] + 1]; ++e) {
+                if (piv_row[col[e]] >= 0) na[c]++;
+                else nb[c]++;
+            }
+        }
+#pragma omp parallel reduction(+ : ops_b, ops_c)
+    {
+        uint64_t *w = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+        if (!w) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < m; ++i) {
+            if (!w || is_piv_row[i] || row_ptr[i + 1] == row_ptr[i]) continue;
+            memset(w, 0, (size_t)n * sizeof(uint64_t));
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) w[col[e]] = val[e];
+            for (int64_t j = 0; j < n; ++j) {
+                if (piv_row[j] < 0) continue;
+                uint64_t f = w[j] % p;
+                if (f == 0) { w[j] = 0; continue; }
+                int64_t r = piv_row[j];
+                ops_b += (double)na[j];
+                ops_c += (double)nb[j];
+                uint64_t g = (p - f) * inv_lead[j] % p;
+                for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) w[col[e]] += g * val[e];
+            }
+        }
+        free(w);
+    }
+    if (fail) { rc = ORA_E_NOMEM; goto done; }
+    ops[0] = ops_b;
+    ops[1] = ops_c;
+    if (npiv_out) *npiv_out = npiv;
+    if (seconds) *seconds = ora_now() - t0;
+done:
+    free(piv_row);
+    free(inv_lead);
+    free(is_piv_row);
+    free(na);
+    free(nb);
+    return rc;
+}
+

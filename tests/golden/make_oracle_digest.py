@@ -11,6 +11,12 @@ oracle's wall time with the thread count and CPU model of the machine that
 ran it.  Only ``oracle/`` and the input generator are called.
 
     python tests/golden/make_oracle_digest.py fl_40000x60000
+
+With ``--counts-only`` it runs only the oracle's row reduction of Alg. 2
+(``oracle.row_counts``) and stores the input digest, the pivot count and the
+work counts ops_b and ops_c in ``oracle_counts_<workload>.json``: for a
+workload whose Gauss-Jordan pass on the Schur complement the oracle cannot
+finish in bounded time.
 """
 import hashlib
 import json
@@ -47,6 +53,28 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
+def counts_only(name):
+    spec = synth.workload(name)
+    rp, c, v = synth.fl_matrix(spec)
+    ops_b, ops_c, npiv, secs = oracle.row_counts(spec.m, spec.n, spec.p, rp, c, v)
+    rec = {
+        "workload": name,
+        "spec": {k: (list(x) if isinstance(x, tuple) else x) for k, x in vars(spec).items()},
+        "input_sha256": sha256_csr(rp, c, v),
+        "npiv": int(npiv),
+        "ops_b": ops_b,
+        "ops_c": ops_c,
+        "oracle_seconds_row_reduction": secs,
+        "threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+        "cpu": cpu_model(),
+        "machine": platform.machine(),
+    }
+    out = os.path.join(HERE, f"oracle_counts_{name}.json")
+    with open(out, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+
+
 def main(name):
     spec = synth.workload(name)
     rp, c, v = synth.fl_matrix(spec)
@@ -75,4 +103,6 @@ def main(name):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "fl_40000x60000")
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    name = args[0] if args else "fl_40000x60000"
+    counts_only(name) if "--counts-only" in sys.argv else main(name)

@@ -147,3 +147,17 @@ def test_counts_of_a_generated_matrix_are_consistent():
     assert a == b
     assert all(float(x).is_integer() and x >= 0 for x in a)
     assert a[0] > 0 and a[1] > 0 and a[3] == 0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_row_counts_equal_the_echelon_counters(seed):
+    """The counts-only entry point reduces the same rows in the same order as
+    oracle.echelon (whose counters are pinned above)."""
+    spec = synth.FLSpec(m=400, n=600, npiv=250, density=0.04, run_len=(3, 16), seed=900 + seed,
+                        p=[65521, 32003, 11][seed])
+    rp, c, v = synth.fl_matrix(spec)
+    ops = []
+    _, _, _, _, npiv = oracle.echelon(spec.m, spec.n, spec.p, rp, c, v, ops=ops)
+    b, cc, npiv2, secs = oracle.row_counts(spec.m, spec.n, spec.p, rp, c, v)
+    assert (b, cc, npiv2) == (ops[0], ops[1], npiv)
+    assert secs >= 0
