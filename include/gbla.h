@@ -19,8 +19,10 @@
  *
  * All arithmetic is exact modular integer arithmetic.
  *
- * Threading: calls are independent; a call may run concurrently with others
- * on different streams.  Errors are returned as codes, never thrown.
+ * Threading: calls are independent and thread-safe; calls on different
+ * streams run their device work concurrently (GBLA_SERIALIZE=1 in the
+ * environment makes them follow one another).  Errors are returned as codes,
+ * never thrown.
  */
 #ifndef GBLA_H
 #define GBLA_H
@@ -124,11 +126,8 @@ int gbla_reduce_ex(const gbla_csr_in *in, uint32_t p, const gbla_options *opt,
 /* ---- many matrices ----------------------------------------------------- */
 /* Batch: reduce n independent matrices (in[i] over GF(p[i]), options opt for
  * all, NULL = defaults).  `workers` host threads (0 = 8), each with its own
- * CUDA stream on the current device, take the matrices largest first.  The
- * device work of one reduction (its copies included) runs under a
- * process-wide lock, so reductions follow one another on the device and
- * overlap only their host-side work; concurrent device work of several
- * reductions has been seen to stall for tens of seconds.  outs[i], ranks[i],
+ * CUDA stream on the current device, take the matrices largest first; their
+ * reductions overlap on the device.  outs[i], ranks[i],
  * codes[i] receive each result (release outs with gbla_free).  Returns
  * GBLA_OK, or the first failing code (the other results are still valid
  * where codes[i] == 0). */
@@ -139,10 +138,9 @@ int gbla_reduce_batch(int n, const gbla_csr_in *in, const uint32_t *p, const gbl
  * copied at submit) are admitted in arrival order whenever a worker is free
  * and the request's estimated device footprint fits in mem_budget next to
  * the requests already running; a request larger than the budget runs alone.
- * Admitted requests run on the workers' streams; as in gbla_reduce_batch
- * their device work is serialised by the process-wide lock, so requests
- * overlap on the host only.  Latency is measured from submit to result
- * ready. */
+ * Admitted requests run on the workers' streams and overlap on the device
+ * with the requests already running.  Latency is measured from submit to
+ * result ready. */
 typedef struct gbla_server gbla_server;
 typedef struct {
     int64_t submitted, completed, failed, cancelled, queued, running;

@@ -135,13 +135,20 @@ struct ActiveReduction {
     ~ActiveReduction() { --g_active_reductions; }
 };
 
-// One reduction at a time runs its device work.  Two reductions whose
-// kernels overlapped on the GPU (batch workers, each on its own stream) were
-// measured to block each other for 40 s of device time in the triangular
-// solve and the echelonisation, with no error reported, where each alone
-// takes milliseconds; the cause has not been identified, so concurrent calls
-// are serialised here and overlap only their host-side work.
+// Reductions on different streams run their device work concurrently (the
+// batch workers and the server's requests overlap on the GPU).  With
+// GBLA_SERIALIZE=1 in the environment a process-wide lock makes them follow
+// one another instead (kept for diagnosis: an earlier version of the library
+// stalled for tens of seconds with overlapping reductions; the current one,
+// traced around every host synchronisation and allocation, does not).
 static std::mutex g_device_mu;
+static bool serialize_reductions() {
+    static const bool v = [] {
+        const char *e = getenv("GBLA_SERIALIZE");
+        return e && atoi(e) != 0;
+    }();
+    return v;
+}
 
 void *host_alloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -433,12 +440,11 @@ void release_thread_resources() {
 // Column width of the tensor-core leaf solves of C*A^-1: env GBLA_TRSM_LEAF
 // (128, 256, 512 or 1024), else 0 = chosen per matrix (trsm_leaf_for).
 static int trsm_leaf_width() {
-    static int v = -1;
-    if (v < 0) {
+    static const int v = [] {
         const char *e = getenv("GBLA_TRSM_LEAF");
         const int x = e ? atoi(e) : 0;
-        v = (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 0;
-    }
+        return (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 0;
+    }();
     return v;
 }
 
@@ -455,12 +461,11 @@ static int trsm_leaf_for(int64_t npiv, int opt_leaf) {
 // Row width of the leaves of the back-substitution of the echelon form (env
 // GBLA_BACK_LEAF overrides: 128, 256, 512 or 1024).
 static int back_leaf_width() {
-    static int v = 0;
-    if (v == 0) {
+    static const int v = [] {
         const char *e = getenv("GBLA_BACK_LEAF");
         const int x = e ? atoi(e) : 0;
-        v = (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 512;
-    }
+        return (x == 128 || x == 256 || x == 512 || x == 1024) ? x : 512;
+    }();
     return v;
 }
 
@@ -480,7 +485,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     if (m > 0 && !in->row_ptr) return GBLA_E_INVAL;
     if (nnz > 0 && (!in->col || !in->val)) return GBLA_E_INVAL;
     GBLA_TRY(check_device());
-    std::lock_guard<std::mutex> device_lock(g_device_mu);
+    std::unique_lock<std::mutex> device_lock(g_device_mu, std::defer_lock);
+    if (serialize_reductions()) device_lock.lock();
     const ActiveReduction active;
     const ModP mp = make_modp(p);
     // diagonal blocks of the triangular solve on the tensor cores too

@@ -84,8 +84,7 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
 
 // One whole reduction on stream s (the body of gbla_reduce_ex; arguments
 // already checked for null pointers and p).  Thread-safe: calls from
-// different host threads take a process-wide lock around their device work,
-// so they follow one another on the device.
+// different host threads on different streams run concurrently.
 int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
                 int64_t *rank_out, gbla_stats *stats);
 bool is_prime(uint32_t p);

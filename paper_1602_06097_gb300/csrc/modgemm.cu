@@ -902,7 +902,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 constexpr int G_EPI_WARPS = 4;
 constexpr int G_GATHER_WARPS = STAGES;
 constexpr int G_THREADS = 64 + 32 * G_EPI_WARPS + 32 * G_GATHER_WARPS;
-constexpr int G_CHUNKS = (2 * BM * BK * 2) / 16;   // 16-byte copies per stage (1024)
 // The drain's running residues (128 rows x 128 columns, two per word) live in
 // shared memory after the ring, column pair major so that the 32 lanes of a
 // warp (32 rows) touch 32 banks.
@@ -1281,59 +1280,61 @@ static int make_map(CUtensorMap *map, const Planes &pl, int box_rows = tc::BM) {
     return r == CUDA_SUCCESS ? GBLA_OK : GBLA_E_CUDA;
 }
 
+// The product kernel's shared-memory limit, set once per process (thread-safe).
+static cudaError_t tc_kernel_attrs() {
+    static const cudaError_t rc = cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    return rc;
+}
+
 // Row tiles per raster group (env GBLA_GEMM_GROUP_M overrides, for tuning).
 static int gemm_group_m() {
-    static int v = 0;
-    if (v == 0) {
+    static const int v = [] {
         const char *e = getenv("GBLA_GEMM_GROUP_M");
         const int x = e ? atoi(e) : 0;
-        v = (x >= 1 && x <= 256) ? x : (int)tc::GROUP_M_DEFAULT;
-    }
+        return (x >= 1 && x <= 256) ? x : (int)tc::GROUP_M_DEFAULT;
+    }();
     return v;
 }
 
 // Row tiles per raster group of the gathered product (env GBLA_GATHER_GROUP_M
 // overrides; 0 = chosen per launch).
 static int gather_group_m_env() {
-    static int v = -1;
-    if (v < 0) {
+    static const int v = [] {
         const char *e = getenv("GBLA_GATHER_GROUP_M");
         const int x = e ? atoi(e) : 0;
-        v = (x >= 1 && x <= 1024) ? x : 0;
-    }
+        return (x >= 1 && x <= 1024) ? x : 0;
+    }();
     return v;
 }
 
 int device_sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, c = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        return c > 0 ? c : 1;
+    }();
     return n;
 }
 
 bool tc_supported() {
-    static int ok = -1;
-    if (ok < 0) {
+    static const bool ok = [] {
         int dev = 0, major = 0, minor = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-        ok = (major == 10 && minor == 3) ? 1 : 0;
-    }
-    return ok == 1;
+        return major == 10 && minor == 3;
+    }();
+    return ok;
 }
 
 // Clusters of two CTAs that can be resident at once for the CTA-pair kernel
 // (0 if such clusters cannot be launched or the pair kernel is not enabled;
 // GBLA_GEMM_PAIR=1 enables it).
 static int pair_max_clusters() {
-    static int n = -1;
-    if (n < 0) {
-        n = 0;
+    static const int clusters = [] {
+        int n = 0;
         const char *e = getenv("GBLA_GEMM_PAIR");
         if (!e || atoi(e) == 0) return n;
         if (cudaFuncSetAttribute(tc::modgemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1355,8 +1356,9 @@ static int pair_max_clusters() {
         int c = 0;
         if (cudaOccupancyMaxActiveClusters(&c, tc::modgemm_tc_kernel<true>, &cfg) == cudaSuccess && c > 0) n = c;
         cudaGetLastError();
-    }
-    return n;
+        return n;
+    }();
+    return clusters;
 }
 
 int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
@@ -1398,12 +1400,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
     CUtensorMap ma, mb;
     GBLA_TRY(make_map(&ma, A));
     GBLA_TRY(make_map(&mb, B, pair ? tc::BN / 2 : tc::BM));
-    static bool attr = false;
-    if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           tc::SMEM_BYTES));
-        attr = true;
-    }
+    GBLA_CUDA_TRY(tc_kernel_attrs());
     tc::Args g{};
     g.M = M; g.N = N; g.K = K;
     g.probs = nullptr; g.nprob = 0;
@@ -1457,12 +1454,7 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     CUtensorMap ma, mb;
     GBLA_TRY(make_map(&ma, A));
     GBLA_TRY(make_map(&mb, B));
-    static bool attr = false;
-    if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           tc::SMEM_BYTES));
-        attr = true;
-    }
+    GBLA_CUDA_TRY(tc_kernel_attrs());
     tc::Args g{};
     g.M = M; g.N = N; g.K = K;
     g.group_m = gemm_group_m();
@@ -1584,12 +1576,7 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
     CUtensorMap ma, mb;
     GBLA_TRY(make_map(&ma, A));
     GBLA_TRY(make_map(&mb, B));
-    static bool attr = false;
-    if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           tc::SMEM_BYTES));
-        attr = true;
-    }
+    GBLA_CUDA_TRY(tc_kernel_attrs());
     tc::Args g{};
     g.M = 0; g.N = 0; g.K = K;
     g.probs = probs; g.nprob = nprob;
@@ -1617,12 +1604,7 @@ int modgemm_withheld_loads(uint32_t *err, cudaStream_t s)
     if (rc == GBLA_OK) rc = make_map(&ma, A);
     if (rc == GBLA_OK) rc = make_map(&mb, B);
     if (rc == GBLA_OK) {
-        static bool attr = false;
-        if (!attr) {
-            if (cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     tc::SMEM_BYTES) != cudaSuccess) rc = GBLA_E_CUDA;
-            attr = true;
-        }
+        if (tc_kernel_attrs() != cudaSuccess) rc = GBLA_E_CUDA;
     }
     uint16_t *C = nullptr;
     if (rc == GBLA_OK) rc = dalloc_t(&C, 128 * 128, s);

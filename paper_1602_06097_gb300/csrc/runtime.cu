@@ -3,11 +3,9 @@
 //
 // Both hand whole reductions (gbla.cu) to a pool of host worker threads,
 // each owning a non-blocking CUDA stream on the caller's device, that take
-// them from a shared queue.  The device work of one reduction runs under a
-// process-wide lock in gbla.cu: when several reductions' kernels ran at once,
-// single phases stalled for tens of seconds, so reductions follow one another
-// on the device and the workers overlap only host-side work (queueing,
-// request copies, result hand-off).
+// them from a shared queue.  The reductions' kernels overlap on the device:
+// one small reduction leaves most of the GPU idle (short launches, readbacks
+// of sizes between phases), so several run side by side.
 //
 // Batch: every matrix is known up front; workers take them largest first
 // (longest-processing-time order) so the tail of the batch is short.

@@ -287,14 +287,15 @@ __global__ void __launch_bounds__(256) trsm_lower_leaf_kernel(int64_t mrows, int
 
 static int leaf_attrs()
 {
-    static bool done = false;
-    if (!done) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(trsm_upper_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           LEAF_SMEM_UPPER));
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(trsm_lower_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           LEAF_SMEM_LOWER));
-        done = true;
-    }
+    static const cudaError_t rc = [] {
+        cudaError_t e = cudaFuncSetAttribute(trsm_upper_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             LEAF_SMEM_UPPER);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(trsm_lower_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     LEAF_SMEM_LOWER);
+        return e;
+    }();
+    GBLA_CUDA_TRY(rc);
     return GBLA_OK;
 }
 
@@ -1078,12 +1079,9 @@ static int block_inverses(const uint16_t *A, int64_t lda, const int32_t *rmap, c
 {
     if (L < 128 || L % 128 || (L & (L - 1)) != 0) return GBLA_E_INTERNAL;
     const int64_t nleaves = (n + L - 1) / L;
-    static bool attr = false;
-    if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(upper_inverse128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           LEAF_INV_SMEM));
-        attr = true;
-    }
+    static const cudaError_t attr_rc =
+        cudaFuncSetAttribute(upper_inverse128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LEAF_INV_SMEM);
+    GBLA_CUDA_TRY(attr_rc);
     use_tc = use_tc && L >= 512 && mp.p >= 8 && tc_supported();
     uint16_t *T1 = nullptr;
     int32_t *iota = nullptr;
@@ -1435,11 +1433,9 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     uint16_t *inv_tab = nullptr;
     // Phase B works on chunks of panels whose D[S]^T planes fit this many rows.
     const int64_t BS_ROWS = int64_t(1) << 20;
-    static bool attr = false;
-    if (!attr) {
-        GBLA_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM));
-        attr = true;
-    }
+    static const cudaError_t attr_rc =
+        cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM);
+    GBLA_CUDA_TRY(attr_rc);
 #define ESTEP(expr)                         \
     do {                                    \
         if ((rc = (expr)) != GBLA_OK) goto done; \

@@ -337,8 +337,8 @@ def _csr_in(row_ptr, col, val, shape):
 
 
 def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PATH_AUTO):
-    """Reduce many host CSR matrices on a pool of worker threads (their device
-    work is serialised by the library's device lock).  ``mats`` is a list of
+    """Reduce many host CSR matrices on a pool of worker threads whose
+    reductions overlap on the device.  ``mats`` is a list of
     (row_ptr, col, val, shape, p).  Returns a list of (rank, row_ptr, col, val)
     (raises on the first failure)."""
     lib = load()
