@@ -1,22 +1,33 @@
 #!/usr/bin/env python3
-"""Benchmark: F4-shaped matrices reduced per second on GB300.
+"""Benchmark: F4-shaped matrices reduced per second on one GB300, modular GOPS
+against the roofline of the dominant kernel, batched against plain.
 
 One step = one whole Faugere-Lachartre reduction (pivot analysis and split,
-C*A^-1, Schur update, reduced echelon form of D', output assembly) of the
-40,000 x 60,000 grouped workload (30,000 designated pivots, 1.5% density,
-2-8 runs per row, groups of 2-16 rows sharing ~80% of their pattern; the
-non-reduced echelon form), inputs resident in device memory.
+C*A^-1, Schur update, reduced echelon form of D', output assembly; the
+echelon form of the new order) of the 150,000 x 200,000 workload: 120,000
+designated pivots, 0.5% density (~149M nonzeros), rows in multiline pairs
+sharing ~90% of their pattern, A banded (2,048 pivot columns) in diagonal
+blocks of 4,096 with 5% cross-block entries.  Inputs resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbla|reference]
 
 Prints one JSON line (rank 0).  Under torchrun every rank reduces its own
 matrix (replicas; no data-path collective) and the time is the maximum over
-ranks.
+ranks.  On one GPU the line also carries:
+  * "fl_40000x60000": the 40,000 x 60,000 workload on the sparse and the
+    dense path, with the oracle's full work counts (modular GOPS) and a
+    bit-exact check of the result against the oracle's stored digest;
+  * "batched": 256 F4 matrices of uneven sizes (rows log-uniform in
+    500-20,000, p in {65521, 32003}) one call per matrix against the batch
+    entry point, whose reductions overlap on the device;
+  * "serving": Poisson request streams at 50-500 req/s served with continuous
+    batching, p50/p99 latency and matrices/s.
 """
 from __future__ import annotations
 
 import argparse
 import dataclasses
+import hashlib
 import json
 import os
 import statistics
@@ -32,26 +43,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "F4 matrices reduced/sec and modular GOPS vs roofline, batched vs plain, bit-exact"
 UNIT = "matrices/s"
-WORKLOAD = "fl_40000x60000"
-CPU_SAMPLE_ROWS = 1500
+WORKLOAD = "fl_150000x200000"
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def args_parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbla", choices=["gbla", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink rows, columns and pivots (small cases for profiling)")
     ap.add_argument("--want-reduced", type=int, default=0)
+    ap.add_argument("--path", type=int, default=0, help="0 auto, 1 dense, 2 sparse")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--extras", action="store_true", help="add the batched-vs-plain and serving measurements")
-    ap.add_argument("--batch", type=int, default=32, help="matrices in the batched-vs-plain measurement")
-    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (req/s)")
-    ap.add_argument("--serve-requests", type=int, default=160)
+    ap.add_argument("--no-extras", action="store_true", help="skip the 40k x 60k, batched and serving blocks")
+    ap.add_argument("--batch", type=int, default=256, help="matrices in the batched-vs-plain measurement")
+    ap.add_argument("--serve-rates", default="50,100,200,500", help="Poisson arrival rates (req/s)")
+    ap.add_argument("--serve-pool", type=int, default=12, help="matrices in the serving pool")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (at most 400 requests)")
     return ap.parse_args(argv)
 
 
@@ -135,19 +148,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic():
+# ------------------------------------------------------ committed records
+def profiled_traffic(name="modgemm_gather_schur_traffic_fl_150000x200000.md",
+                     src=os.path.join("paper_1602_06097_gb300", "csrc", "modgemm.cu")):
     """DRAM bytes per Schur launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    import hashlib
     import re
     try:
-        txt = open(os.path.join(ROOT, "profiles", "modgemm_tc_schur_traffic_fl_40000x60000.md")).read()
-        src = open(os.path.join(ROOT, "paper_1602_06097_gb300", "csrc", "modgemm.cu"), "rb").read()
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
+        code = open(os.path.join(ROOT, src), "rb").read()
     except OSError:
         return None
     m1 = re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt)
     m2 = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
-    if not (m1 and m2) or hashlib.sha256(src).hexdigest() != m2.group(1):
+    if not (m1 and m2) or hashlib.sha256(code).hexdigest() != m2.group(1):
         return None
     return int(m1.group(1))
 
@@ -160,132 +174,271 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def oracle_record(kind, name):
+    """The oracle's stored record of a workload (written by
+    tests/golden/make_oracle_digest.py), or None."""
+    path = os.path.join(GOLDEN, f"oracle_{kind}{name}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def sha256_csr(row_ptr, col, val):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(row_ptr, dtype="<i8").tobytes())
+    h.update(np.ascontiguousarray(col, dtype="<i4").tobytes())
+    h.update(np.ascontiguousarray(val, dtype="<u2").tobytes())
+    return h.hexdigest()
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 # --------------------------------------------------------------- CPU oracle
-def cpu_oracle_sample(rp, c, v, m, n, p, rows):
-    """Time the oracle on a row sample of the workload: every pivot row plus
-    the first `rows` non-pivot rows.  The row reduction by the pivot rows costs
-    the same per non-pivot row, and the Gauss-Jordan pass on the Schur
-    complement grows with the square of its row count, so the whole matrix
-    takes t_rows * (m_cd / s) + t_gj * (m_cd / s)^2."""
+def cpu_oracle_sample(rp, c, v, m, n, p, budget_s=15.0):
+    """Time the oracle's row reduction of Alg. 2 (every non-pivot row reduced
+    by the normalised pivot rows) on a sample of the non-pivot rows, doubling
+    the sample until it takes budget_s / 3 or more.  The rows are reduced
+    independently, so the whole matrix's row reduction takes
+    t_sample * m_cd / s; the Gauss-Jordan pass on the Schur complement, which
+    the oracle cannot finish at this size in bounded time, is not included:
+    1 / t is an upper bound on the oracle's matrices per second."""
     import oracle
     piv = oracle.pivots(m, n, rp, c)
     is_piv = np.zeros(m, bool)
     is_piv[piv[piv >= 0]] = True
-    nonempty = np.diff(rp) > 0
-    cd = np.nonzero(~is_piv & nonempty)[0]
+    cd = np.nonzero(~is_piv & (np.diff(rp) > 0))[0]
     m_cd = len(cd)
-    s = min(rows, m_cd)
-    keep = np.sort(np.concatenate([np.nonzero(is_piv)[0], cd[:s]]))
-    lens = np.diff(rp)[keep]
-    srp = np.zeros(len(keep) + 1, np.int64)
-    np.cumsum(lens, out=srp[1:])
-    idx = np.repeat(rp[keep], lens) + (np.arange(srp[-1]) - np.repeat(srp[:-1], lens))
-    secs = [0.0, 0.0]
-    t0 = time.perf_counter()
-    oracle.echelon(len(keep), n, p, srp, c[idx], v[idx], phase_seconds=secs)
-    wall = time.perf_counter() - t0
-    f = m_cd / max(s, 1)
-    t_full = secs[0] * f + secs[1] * f * f
+    rng = np.random.default_rng(1602)
+    order = rng.permutation(m_cd)
+    s = 16
+    while True:
+        s = min(s, m_cd)
+        keep = np.sort(np.concatenate([np.nonzero(is_piv)[0], cd[order[:s]]]))
+        lens = np.diff(rp)[keep]
+        srp = np.zeros(len(keep) + 1, np.int64)
+        np.cumsum(lens, out=srp[1:])
+        idx = np.repeat(rp[keep], lens) + (np.arange(srp[-1]) - np.repeat(srp[:-1], lens))
+        t0 = time.perf_counter()
+        oracle.row_counts(len(keep), n, p, srp, c[idx], v[idx])
+        wall = time.perf_counter() - t0
+        if wall >= budget_s / 3 or s >= m_cd:
+            break
+        s *= 2
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"t_full_s": t_full, "sample_wall_s": wall, "rows": s, "m_cd": m_cd, "phase_s": secs,
-            "threads": threads}
+    t_full = wall * m_cd / s
+    return {"t_full_s": t_full, "sample_wall_s": wall, "rows": s, "m_cd": m_cd, "threads": threads}
+
+
+def cpu_sample_text(cb):
+    return (f"oracle row reduction of Alg. 2 for {cb['rows']} of the {cb['m_cd']} non-pivot rows "
+            f"(random sample, every pivot row) in {cb['sample_wall_s']:.1f} s on {cb['threads']} threads "
+            f"({cpu_model()}), scaled by m_cd/rows to {cb['t_full_s']:.0f} s per matrix; the Gauss-Jordan "
+            f"pass on the Schur complement is not timed, so the value is an upper bound on the oracle's rate")
 
 
 def run_reference(a, world, rank):
-    """The oracle on the host cores, each step a bounded row sample of the
-    same workload scaled to whole matrices per second."""
+    """The oracle on the host cores (rank 0 only), each step a bounded sample
+    of the same workload scaled to matrices per second."""
     if rank != 0:
         return
     from paper_1602_06097_gb300 import synth
-    spec = synth.workload(a.workload)
+    spec = synth.workload(a.workload) if a.scale == 1.0 else synth.scaled(a.workload, a.scale)
     rp, c, v = synth.fl_matrix(spec)
-    vals = []
-    last = None
+    budget = max(2.0, 120.0 / max(1, a.steps + a.warmup))
+    vals, last = [], None
     for i in range(a.warmup + a.steps):
-        last = cpu_oracle_sample(rp, c, v, spec.m, spec.n, spec.p, CPU_SAMPLE_ROWS)
+        last = cpu_oracle_sample(rp, c, v, spec.m, spec.n, spec.p, budget)
         if i >= a.warmup:
             vals.append(1.0 / last["t_full_s"])
     value = float(np.mean(vals))
-    sample = (f"oracle echelon on all pivot rows + the first {last['rows']} of {last['m_cd']} non-pivot rows; "
-              f"whole-matrix time = t_rows*(m_cd/s) + t_gauss_jordan*(m_cd/s)^2")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
             "config": config_of(spec, a),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["threads"], "kind": "oracle",
-                             "sample": sample},
+                             "sample": cpu_sample_text(last)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def config_of(spec, a):
-    return {"workload": a.workload + ("" if a.scale == 1.0 else f"@scale{a.scale}"), "rows": spec.m, "cols": spec.n, "designated_pivots": spec.npiv,
-            "p": spec.p, "density": spec.density, "run_len": list(spec.run_len),
+    return {"workload": a.workload + ("" if a.scale == 1.0 else f"@scale{a.scale}"), "rows": spec.m,
+            "cols": spec.n, "designated_pivots": spec.npiv, "p": spec.p, "density": spec.density,
+            "run_len": list(spec.run_len), "band": spec.band, "block": spec.block if spec.band else None,
             "groups": list(spec.group) if spec.group else None, "want_reduced": a.want_reduced,
-            "l2": "inputs larger than L2 (231 MB CSR; >10 GB working set per step)",
-            "input": "resident in HBM"}
+            "path": ["auto", "dense", "sparse"][a.path],
+            "l2": "inputs larger than L2 (the CSR input alone exceeds 129 MB)", "input": "resident in HBM"}
 
 
-BATCH_SEED = 20160223   # batched / serving mix
+# ------------------------------------------------------------ extra blocks
+def reduce_steps(gbla, d, shape, p, stream, steps, path=0):
+    import torch
+    stats = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        r = gbla.reduce_device(*d, shape, p, stream=stream, path=path)
+        stats.append(r.stats)
+        r.free()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps, stats
+
+
+def mean_of(stats, key):
+    return float(np.mean([s[key] for s in stats]))
+
+
+def block_40000x60000(gbla, synth, peak, stream):
+    """The 40,000 x 60,000 workload on both paths with the oracle's full work
+    counts, and its result against the oracle's stored digest."""
+    import torch
+    name = "fl_40000x60000"
+    spec = synth.workload(name)
+    rp, c, v = synth.fl_matrix(spec)
+    d = (torch.from_numpy(rp).cuda(), torch.from_numpy(c).cuda(), torch.from_numpy(v.view(np.int16)).cuda())
+    rec = oracle_record("", name)
+    out = {"rows": spec.m, "cols": spec.n}
+    for path, label in ((2, "sparse"), (1, "dense")):
+        reduce_steps(gbla, d, (spec.m, spec.n), spec.p, stream, 2, path)
+        ms, stats = reduce_steps(gbla, d, (spec.m, spec.n), spec.p, stream, 5, path)
+        blk = {"ms_per_matrix": ms, "matrices_per_s": 1e3 / ms,
+               "phase_ms": {k: mean_of(stats, k) for k in ("ms_split", "ms_trsm", "ms_schur", "ms_echelon",
+                                                           "ms_output")}}
+        if rec:
+            ops = rec["ops"]
+            blk["modular_gops"] = (ops[0] + ops[1] + ops[2] + ops[3]) / (ms / 1e3) / 1e9
+            schur_ms = blk["phase_ms"]["ms_schur"]
+            blk["schur_tflops_algorithmic"] = 8.0 * ops[1] / (schur_ms / 1e3) / 1e12
+            blk["schur_frac_algorithmic"] = blk["schur_tflops_algorithmic"] / peak
+        if label == "sparse":
+            ex = mean_of(stats, "schur_exec_mod_ops")
+            blk["schur_tflops_executed"] = 8.0 * ex / (blk["phase_ms"]["ms_schur"] / 1e3) / 1e12
+        out[label] = blk
+    r = gbla.reduce_device(*d, (spec.m, spec.n), spec.p, stream=stream)
+    rank, orp, oc, ov = r.to_host()
+    r.free()
+    digest = sha256_csr(orp, oc, ov)
+    out["bit_exact_vs_oracle"] = bool(rec and digest == rec["result_sha256"] and
+                                      sha256_csr(rp, c, v) == rec["input_sha256"])
+    if rec:
+        out["oracle_counts"] = {"ops_b": rec["ops"][0], "ops_c": rec["ops"][1], "ops_d": rec["ops"][2],
+                                "ops_e": rec["ops"][3]}
+        out["oracle_whole_matrix"] = {"seconds": rec["oracle_seconds"]["total"], "threads": rec["threads"],
+                                      "cpu": rec["cpu"], "kind": "measured, whole matrix (recorded run)"}
+    out["speedup_sparse_over_dense"] = out["dense"]["ms_per_matrix"] / out["sparse"]["ms_per_matrix"]
+    return out
+
+
+BATCH_SEED = 20160223   # batched mix (256 matrices)
+SERVE_SEED = 20160224   # serving pool
 
 
 def batched_vs_plain(gbla, synth, count):
     """A batch of F4-shaped matrices of uneven sizes (rows log-uniform in
     500-20,000, columns 1.3-1.6 x rows, 60-80% pivots, 1-5% density, p in
     {65521, 32003}) reduced one call per matrix, then through the batch entry
-    point; host inputs and results, copies included in both."""
+    point (8 workers whose reductions overlap on the device); host inputs and
+    results, copies included in both."""
     specs = synth.mixed_batch(count, BATCH_SEED)
+    t0 = time.perf_counter()
     mats = [synth.fl_matrix(sp) + ((sp.m, sp.n), sp.p) for sp in specs]
-    gbla.reduce_batch(mats[:8])                 # warm-up; starts the 8 default batch workers
+    gen_s = time.perf_counter() - t0
+    gbla.reduce_batch(mats[:16], workers=8)   # warm-up; starts the batch workers
     for rp, c, v, shape, p in mats[:4]:
         gbla.reduce(rp, c, v, shape, p)
     t0 = time.perf_counter()
-    plain = [gbla.reduce(rp, c, v, shape, p)[0] for rp, c, v, shape, p in mats]
+    plain = [gbla.reduce(rp, c, v, shape, p) for rp, c, v, shape, p in mats]
     t_plain = time.perf_counter() - t0
-    # The first call holds all its results at once and pins new host memory
-    # for most of them; a repeated call finds the page-locked result cache
-    # warm, as the one-at-a-time calls above do.
     t0 = time.perf_counter()
-    first = [r[0] for r in gbla.reduce_batch(mats)]
-    t_first = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    batched = [r[0] for r in gbla.reduce_batch(mats)]
+    batched = gbla.reduce_batch(mats, workers=8)
     t_batch = time.perf_counter() - t0
-    assert plain == batched == first, "batched ranks differ from one-at-a-time ranks"
+    same = all(a[0] == b[0] and all(np.array_equal(x, y) for x, y in zip(a[1:], b[1:]))
+               for a, b in zip(plain, batched))
     nnz = int(sum(len(mt[1]) for mt in mats))
-    return mats, {"matrices": count, "rows": [int(min(sp.m for sp in specs)), int(max(sp.m for sp in specs))],
-                  "input_nnz": nnz, "plain_matrices_per_s": count / t_plain, "batched_matrices_per_s": count / t_batch,
-                  "batched_first_call_matrices_per_s": count / t_first,
-                  "speedup": t_plain / t_batch, "includes": "host inputs and results (H2D/D2H inside)"}
+    return {"matrices": count, "rows": [int(min(sp.m for sp in specs)), int(max(sp.m for sp in specs))],
+            "primes": sorted({int(sp.p) for sp in specs}), "input_nnz": nnz, "generate_s": gen_s,
+            "plain_matrices_per_s": count / t_plain, "batched_matrices_per_s": count / t_batch,
+            "speedup": t_plain / t_batch, "batched_equals_plain": bool(same), "workers": 8,
+            "includes": "host inputs and results (H2D/D2H inside both)"}
 
 
-def serving(gbla, mats, rate, nreq):
-    """Poisson arrivals (rate req/s) of requests drawn from the batch's
-    matrices, served by the request server with continuous batching; latency
-    from submit to result ready."""
-    rng = np.random.default_rng(BATCH_SEED)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
-    pick = rng.integers(0, len(mats), size=nreq)
-    with gbla.Server(workers=4) as srv:
-        tickets = []
-        t0 = time.perf_counter()
-        for i in range(nreq):
-            dt = t0 + arrivals[i] - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            rp, c, v, shape, p = mats[pick[i]]
-            tickets.append(srv.submit(rp, c, v, shape, p))
-        lat = []
-        for t in tickets:
-            code, _, ms = srv.wait(t, 120.0)
-            if code != 0:
-                raise RuntimeError(f"served request failed with code {code}")
-            lat.append(ms)
-        wall = time.perf_counter() - t0
-    lat = np.asarray(lat)
-    return {"rate_req_per_s": rate, "requests": nreq, "matrices_per_s": nreq / wall,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "workers": 4}
+def fingerprint(res):
+    """A cheap exact-match key of a result (rank, row pointers, and the
+    column and value arrays summed with position weights)."""
+    r, rp, c, v = res
+    w = np.arange(len(c), dtype=np.int64) % 65521 + 1
+    return (int(r), hashlib.sha256(np.ascontiguousarray(rp, dtype="<i8").tobytes()).hexdigest(),
+            int(np.dot(np.asarray(c, np.int64), w)), int(np.dot(np.asarray(v, np.int64), w)))
+
+
+def serving(gbla, synth, rates, pool, seconds, max_requests=400):
+    """Poisson request streams drawn from a pool of seeded F4 matrices (rows
+    log-uniform in 1,000-50,000, p in {32003, 65521}), served by the request
+    server (8 workers, admission by device-memory footprint, requests overlap
+    on the device); latency from submit to result ready (server-side); a
+    waiter thread collects results as they complete, and every served result
+    must match the same request reduced alone."""
+    specs = synth.mixed_batch(pool, SERVE_SEED, rows=(1000, 50000), primes=(32003, 65521))
+    mats = [synth.fl_matrix(sp) + ((sp.m, sp.n), sp.p) for sp in specs]
+    solo = [fingerprint(gbla.reduce(*m)) for m in mats]
+    out = []
+    for rate in rates:
+        rng = np.random.default_rng(SERVE_SEED + int(rate))
+        nreq = int(max(20, min(max_requests, rate * seconds)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+        pick = rng.integers(0, len(mats), size=nreq)
+        lat, ok, failed = [], [True], []
+        with gbla.Server(workers=8) as srv:
+            tickets = []
+            cv = threading.Condition()
+
+            def waiter():
+                for i in range(nreq):
+                    with cv:
+                        cv.wait_for(lambda: len(tickets) > i)
+                        t = tickets[i]
+                    code, res, ms = srv.wait(t, 300.0)
+                    if code != 0:
+                        failed.append(code)
+                        continue
+                    ok[0] = ok[0] and fingerprint(res) == solo[pick[i]]
+                    lat.append(ms)
+
+            th = threading.Thread(target=waiter)
+            th.start()
+            t0 = time.perf_counter()
+            for i in range(nreq):
+                dt = t0 + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                t = srv.submit(*mats[pick[i]])
+                with cv:
+                    tickets.append(t)
+                    cv.notify()
+            th.join()
+            wall = time.perf_counter() - t0
+        if failed:
+            raise RuntimeError(f"served requests failed with codes {sorted(set(failed))}")
+        lat = np.asarray(lat)
+        out.append({"rate_req_per_s": rate, "requests": nreq, "matrices_per_s": nreq / wall,
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "mean_ms": float(lat.mean()), "results_equal_solo": bool(ok[0])})
+    return {"pool": pool, "pool_rows": [int(min(sp.m for sp in specs)), int(max(sp.m for sp in specs))],
+            "pool_nnz": int(sum(len(mt[1]) for mt in mats)), "workers": 8, "rates": out}
 
 
 # --------------------------------------------------------------- GPU arm
@@ -312,7 +465,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        res = gbla.reduce_device(d_rp, d_c, d_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream)
+        res = gbla.reduce_device(d_rp, d_c, d_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream,
+                                 path=a.path)
         st, r, nnz = res.stats, res.rank, res.nnz
         res.free()
         return st, r, nnz
@@ -340,18 +494,31 @@ def main():
     ms_step = ms_total / a.steps
     value = world * a.steps / (ms_total / 1e3)
 
-    # dominant kernel: the Schur-update launch of the tensor-core product
     st0 = stats[0]
-    m_cd, n_d, npiv = st0["m_cd"], st0["n_d"], st0["npiv"]
-    schur_ms = float(np.mean([s["ms_schur"] for s in stats]))
-    # algorithmic flops of the Schur launch: its modular multiply-adds over the
-    # nonzero staircase of X, times four bf16 digit products of 2 flops each
-    flops = 8.0 * float(np.mean([s["schur_mod_ops"] for s in stats]))
     peaks, kind = measured_peaks()
-    achieved = flops / (schur_ms / 1e3) / 1e12 if schur_ms > 0 else None
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    mod_ops = float(np.mean([s["mod_ops"] for s in stats]))
+    schur_ms = mean_of(stats, "ms_schur")
     launches = int(sum(s["launches"] for s in stats))
+    # Algorithmic work from the oracle's counters (not from the GPU code):
+    # ops_b, ops_c of Alg. 2's row reduction on this exact input.
+    counts = oracle_record("counts_", a.workload) if (a.scale == 1.0 and rank == 0) else None
+    if counts and counts.get("input_sha256") != sha256_csr(rp, c, v):
+        counts = None
+    ops_c = counts["ops_c"] if counts else None
+    exec_ops = mean_of(stats, "schur_exec_mod_ops")
+    roofline = {"kernel": "modgemm_gather_kernel: the Schur update D <- D - X*B, one launch per step "
+                          "(K compacted per 128-column tile)",
+                "bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                "peak_kind": f"bf16 dense sustained, {kind}",
+                "achieved": None, "frac": None,
+                "algorithmic": "8 flops (4 bf16 digit products) per modular multiply-add of the oracle's ops_c",
+                "executed_tflops": 8.0 * exec_ops / (schur_ms / 1e3) / 1e12 if schur_ms > 0 else None,
+                "executed_frac": (8.0 * exec_ops / (schur_ms / 1e3) / 1e12 / peak) if schur_ms > 0 else None,
+                "launch_ms": schur_ms,
+                "traffic": profiled_traffic() if (a.workload == WORKLOAD and a.scale == 1.0) else None}
+    if ops_c and schur_ms > 0:
+        roofline["achieved"] = 8.0 * ops_c / (schur_ms / 1e3) / 1e12
+        roofline["frac"] = roofline["achieved"] / peak
 
     e2e = None
     if not a.no_e2e:
@@ -361,14 +528,16 @@ def main():
         h_v = torch.from_numpy(v.view(np.int16)).pin_memory().numpy().view(np.uint16)
         k_e2e = max(1, min(a.steps, 3))
         for _ in range(2):   # warm the library's page-locked result cache
-            gbla.reduce_host(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream).free()
+            gbla.reduce_host(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream,
+                             path=a.path).free()
         torch.cuda.synchronize()
         d2h = 0
         t0 = time.perf_counter()
         for _ in range(k_e2e):
             # inputs copied in and the whole result copied out inside the call;
             # the step reads the rank and the last row's length on the host
-            hr = gbla.reduce_host(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream)
+            hr = gbla.reduce_host(h_rp, h_c, h_v, (m, n), p, want_reduced=bool(a.want_reduced), stream=stream,
+                                  path=a.path)
             d2h = hr.row_ptr.nbytes + hr.col.nbytes + hr.val.nbytes
             _ = int(hr.row_ptr[-1]) + hr.rank
             hr.free()
@@ -381,36 +550,44 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    extras = {}
-    if world == 1 and a.extras:
-        mats, extras["batched"] = batched_vs_plain(gbla, synth, a.batch)
-        extras["serving"] = serving(gbla, mats, a.serve_rate, a.serve_requests)
     cpu = None
     if world == 1 and not a.no_cpu_baseline:
-        cb = cpu_oracle_sample(rp, c, v, m, n, p, CPU_SAMPLE_ROWS)
+        cb = cpu_oracle_sample(rp, c, v, m, n, p)
         cpu = {"value": 1.0 / cb["t_full_s"], "unit": UNIT, "cores": cb["threads"], "kind": "oracle",
-               "sample": (f"oracle echelon on all pivot rows + the first {cb['rows']} of {cb['m_cd']} "
-                          f"non-pivot rows ({cb['sample_wall_s']:.1f} s); whole-matrix time = "
-                          f"t_rows*(m_cd/s) + t_gauss_jordan*(m_cd/s)^2 = {cb['t_full_s']:.0f} s")}
+               "sample": cpu_sample_text(cb)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u16", "data": "synthetic", "config": config_of(spec, a),
-        "modular_gops": mod_ops / (ms_step / 1e3) / 1e9,
+        "modular_gops": ((counts["ops_b"] + counts["ops_c"]) / (ms_step / 1e3) / 1e9) if counts else None,
+        "modular_ops": ({"ops_b": counts["ops_b"], "ops_c": counts["ops_c"], "ops_d": None, "ops_e": 0,
+                         "source": "oracle.row_counts on this input (tests/golden/oracle_counts_"
+                                   f"{a.workload}.json); ops_d (Gauss-Jordan of the Schur complement) is beyond "
+                                   "the oracle's bounded time at this size and not included"} if counts else None),
         "rank": int(r_out), "out_nnz": int(nnz_out),
-        "shape": {"npiv": npiv, "m_cd": m_cd, "n_d": n_d, "rank_d": st0["rank_d"]},
-        "phase_ms": {k: float(np.mean([s[k] for s in stats])) for k in
+        "shape": {"npiv": st0["npiv"], "m_cd": st0["m_cd"], "n_d": st0["n_d"], "rank_d": st0["rank_d"],
+                  "path": ["", "dense", "sparse"][int(st0["path"])], "list_a": st0["list_a"],
+                  "list_b": st0["list_b"], "leaf_width": st0["leaf_width"]},
+        "phase_ms": {k: mean_of(stats, k) for k in
                      ("ms_split", "ms_trsm", "ms_schur", "ms_echelon", "ms_echelon_back", "ms_backsub", "ms_output",
                       "ms_total")},
         "wall_ms_per_step": wall * 1e3 / a.steps,
-        "roofline": {"kernel": "modgemm_tc_kernel (Schur update launch)", "bound": "tensor",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None,
-                     "traffic": profiled_traffic() if a.workload == WORKLOAD and a.scale == 1.0 else None,
-                     "peak_kind": f"bf16 dense sustained, {kind}"},
+        "roofline": roofline,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
     }
-    line.update(extras)
+    if world == 1 and not a.no_extras:
+        extras = {}
+        for key, fn in (("fl_40000x60000", lambda: block_40000x60000(gbla, synth, peak, stream)),
+                        ("batched", lambda: batched_vs_plain(gbla, synth, a.batch)),
+                        ("serving", lambda: serving(gbla, synth, [float(x) for x in a.serve_rates.split(",")],
+                                                    a.serve_pool, a.serve_seconds))):
+            try:
+                t0 = time.perf_counter()
+                extras[key] = fn()
+                extras[key]["block_wall_s"] = time.perf_counter() - t0
+            except Exception as exc:   # an extra block never hides the main measurement
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -108,6 +108,8 @@ typedef struct {
     int64_t list_a, list_b; /* sparse path: compacted K entries (all tiles) of A's
                                off-diagonal blocks and of B */
     int64_t leaf_width;     /* leaf columns of the triangular solve */
+    double schur_exec_mod_ops; /* sparse path: multiply-adds the Schur launch runs on the tensor
+                                  cores (its compacted tiles, zeros included) */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */

@@ -510,6 +510,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     // releases it on every path.
     int rc = GBLA_OK;
     uint32_t *err = nullptr;
+    unsigned long long *exec_ctr = nullptr;   // executed list entries x row tiles of the Schur launch
     int64_t *d_rp = nullptr;
     int32_t *d_col = nullptr;
     uint16_t *d_val = nullptr;
@@ -711,7 +712,11 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     tm.mark(s);  // 2
     if (sparse && m_cd > 0 && npiv > 0 && n_d > 0) {
         NvtxRange r("gbla.schur");
-        STEP(modgemm_gather(SB, 0, XT, npiv, D16, ldd, m_cd, n_d, -1, pi.cd_lead, mp, err, s, &ctr));
+        if (stats) {
+            STEP(dalloc_t(&exec_ctr, 1, s));
+            CSTEP(cudaMemsetAsync(exec_ctr, 0, sizeof(unsigned long long), s));
+        }
+        STEP(modgemm_gather(SB, 0, XT, npiv, D16, ldd, m_cd, n_d, -1, pi.cd_lead, mp, err, s, &ctr, exec_ctr));
     } else if (m_cd > 0 && npiv > 0 && n_d > 0) {
         NvtxRange r("gbla.schur");
         STEP(modgemm(Xp, 0, 0, Bt, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr, nullptr,
@@ -879,6 +884,10 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             stats->list_a = SA.total;
             stats->list_b = SB.total;
             stats->leaf_width = tc_leaf_w;
+            if (exec_ctr) {
+                unsigned long long e = 0;
+                if (readback(&e, exec_ctr, sizeof(e), s) == GBLA_OK) stats->schur_exec_mod_ops = (double)e * 128.0 * 128.0;
+            }
         }
     }
 
@@ -888,6 +897,7 @@ cleanup:
         cudaGetLastError();
     }
     dfree(err, s);
+    dfree(exec_ctr, s);
     dfree(d_rp, s);
     dfree(d_col, s);
     dfree(d_val, s);

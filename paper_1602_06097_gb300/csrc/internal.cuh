@@ -73,9 +73,11 @@ void compact_free(Compact *c, cudaStream_t s);
 // X, K = r; rows xt_rows and beyond read as zero).  With row_lead (device,
 // ascending absolute lead of each row of X) a row tile skips the list entries
 // left of its raster group's first lead.  Tensor-core variant only (p >= 8).
+// With exec (device, optional), adds the list entries times row tiles the
+// launch runs through (executed multiply-adds = exec * 128 * 128).
 int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_rows, uint16_t *C, int64_t ldc,
                    int64_t M, int64_t N, int sign, const int32_t *row_lead, const ModP &mp, uint32_t *err,
-                   cudaStream_t s, GemmCounters *ctr);
+                   cudaStream_t s, GemmCounters *ctr, unsigned long long *exec = nullptr);
 // Grouped product C[c_rows, c_col0:] += sign * A_p * B_p^T for every problem
 // p, one launch (see GroupProb).
 int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K, uint16_t *C,

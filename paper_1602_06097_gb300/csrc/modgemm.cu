@@ -931,22 +931,33 @@ struct GArgs {
 // (raster group, output tile): all tiles of a group walk K from there (X is
 // zero left of a row's lead, rows ascending by lead), so that concurrent CTAs
 // share operand tiles in L2.  One thread per entry, a binary search.
-__global__ void gather_starts_kernel(int64_t ngroups, int64_t num_n, int64_t nt0, int group_m,
+// With exec (optional), also adds the list entries the launch runs through
+// (from each tile's rounded start to the list end, times the raster group's
+// row tiles): the executed product is exec * 128 * 128 multiply-adds.
+__global__ void gather_starts_kernel(int64_t ngroups, int64_t num_n, int64_t num_m, int64_t nt0, int group_m,
                                      const int64_t *__restrict__ koff, const int32_t *__restrict__ kidx,
-                                     const int32_t *__restrict__ row_lead, int32_t *__restrict__ kstart)
+                                     const int32_t *__restrict__ row_lead, int32_t *__restrict__ kstart,
+                                     unsigned long long *exec)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ngroups * num_n) return;
     const int64_t grp = i / num_n, nt = i % num_n;
     const int64_t kb = koff[nt0 + nt], ke = koff[nt0 + nt + 1];
-    const int32_t L = row_lead[grp * group_m * BM];
     int64_t lo = kb, hi = ke;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (kidx[mid] < L) lo = mid + 1;
-        else hi = mid;
+    if (row_lead) {
+        const int32_t L = row_lead[grp * group_m * BM];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (kidx[mid] < L) lo = mid + 1;
+            else hi = mid;
+        }
     }
     kstart[i] = (int32_t)(lo - kb);
+    if (exec) {
+        const int64_t s = ((lo - kb) / BK & ~(int64_t)(STAGES - 1)) * BK;   // as gtile rounds it
+        const int64_t rows = min((int64_t)group_m, num_m - grp * group_m);
+        atomicAdd(exec, (unsigned long long)((ke - kb - s) * rows));
+    }
 }
 
 struct GTile {
@@ -1478,7 +1489,7 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
 // Gathered product (see tc::modgemm_gather_kernel).
 int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_rows, uint16_t *C, int64_t ldc,
                    int64_t M, int64_t N, int sign, const int32_t *row_lead, const ModP &mp, uint32_t *err,
-                   cudaStream_t s, GemmCounters *ctr)
+                   cudaStream_t s, GemmCounters *ctr, unsigned long long *exec)
 {
     if (M <= 0 || N <= 0 || S.total <= 0) return GBLA_OK;
     if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
@@ -1518,11 +1529,11 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
     g.group_m = gather_group_m_env() ? gather_group_m_env() : gemm_group_m();
     const int64_t num_m = (M + tc::BM - 1) / tc::BM, num_n = (N + tc::BN - 1) / tc::BN;
     int32_t *kstart = nullptr;
-    if (row_lead) {
+    if (row_lead || exec) {
         const int64_t ngroups = (num_m + g.group_m - 1) / g.group_m;
         GBLA_TRY(dalloc_t(&kstart, (size_t)(ngroups * num_n), s));
         tc::gather_starts_kernel<<<(unsigned)((ngroups * num_n + 255) / 256), 256, 0, s>>>(
-            ngroups, num_n, nt0, g.group_m, S.koff, S.kidx, row_lead, kstart);
+            ngroups, num_n, num_m, nt0, g.group_m, S.koff, S.kidx, row_lead, kstart, exec);
         if (launch_check() != cudaSuccess) {
             dfree(kstart, s);
             return GBLA_E_CUDA;

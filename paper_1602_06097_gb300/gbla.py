@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("mod_ops", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("schur_mod_ops", ctypes.c_double), ("ms_echelon_back", ctypes.c_double),
                 ("path", ctypes.c_int64), ("list_a", ctypes.c_int64), ("list_b", ctypes.c_int64),
-                ("leaf_width", ctypes.c_int64)]
+                ("leaf_width", ctypes.c_int64), ("schur_exec_mod_ops", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

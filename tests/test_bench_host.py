@@ -40,7 +40,7 @@ def test_clock_summary_skips_malformed_lines():
 def test_traffic_reported_only_for_the_measured_kernel_source(tmp_path, monkeypatch):
     import hashlib
     rel_src = os.path.join("paper_1602_06097_gb300", "csrc", "modgemm.cu")
-    rel_prof = os.path.join("profiles", "modgemm_tc_schur_traffic_fl_40000x60000.md")
+    rel_prof = os.path.join("profiles", "modgemm_gather_schur_traffic_fl_150000x200000.md")
     os.makedirs(tmp_path / os.path.dirname(rel_src), exist_ok=True)
     os.makedirs(tmp_path / "profiles", exist_ok=True)
     shutil.copy(os.path.join(ROOT, rel_src), tmp_path / rel_src)
