@@ -210,14 +210,22 @@ struct gbla_server {
     bool stop = false;
     int dev = 0;
 
-    // Device bytes a reduction of an m x n matrix can need: input, the digit
-    // planes of A^T, B^T and X (at most 12 bytes per entry of an m x n dense
-    // matrix when pivots fill the smaller side) and the uint16 blocks.
-    static size_t estimate(const gbla_csr_in &in) {
+    // Device bytes a reduction of an m x n matrix can need.  The dense path
+    // holds the digit planes of A^T, B^T and X (at most 12 bytes per entry of
+    // an m x n dense matrix when pivots fill the smaller side) and the
+    // uint16 blocks.  The sparse path (the default where the tensor cores
+    // apply, see reduce_impl) holds C and D as uint16 and X^T as two digit
+    // planes (at most 6 bytes per entry of the m x min(m, n) block C), the
+    // compacted sparse operands (at most 24 bytes per input nonzero: a 128-
+    // column tile's list entry stores 128 values of four planes) and the
+    // echelonisation of D (at most 12 bytes per entry of m x n).
+    static size_t estimate(const gbla_csr_in &in, uint32_t p, const gbla_options &opt) {
         const double m = (double)in.nrows, n = (double)in.ncols;
         const double k = std::min(m, n);
-        const double b = 8.0 * (m + 1) + 6.0 * (double)in.nnz + 12.0 * k * n + 6.0 * m * n + (64 << 20);
-        return (size_t)b;
+        const bool sparse = opt.path != GBLA_PATH_DENSE && opt.gemm_variant != GBLA_GEMM_SIMT && p >= 8;
+        const double work = sparse ? 6.0 * m * k + 24.0 * (double)in.nnz + 12.0 * m * n
+                                   : 12.0 * k * n + 6.0 * m * n;
+        return (size_t)(8.0 * (m + 1) + 6.0 * (double)in.nnz + work + (64 << 20));
     }
 
     bool admissible(const Request *r) const {
@@ -315,7 +323,7 @@ int gbla_server_submit(gbla_server *s, const gbla_csr_in *in, uint32_t p, const 
     r->p = p;
     if (opt) r->opt = *opt;
     r->opt.device_ptrs = 0;
-    r->est_bytes = gbla_server::estimate(*in);
+    r->est_bytes = gbla_server::estimate(*in, p, r->opt);
     r->t_submit = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     r->ticket = s->next_ticket++;

@@ -367,6 +367,31 @@ def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PA
     return res
 
 
+def reduce_batch_device(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PATH_AUTO):
+    """Reduce many matrices already on the device through the batch entry
+    point (workers whose reductions overlap on the device).  ``mats`` is a
+    list of (row_ptr, col, val, shape, p) with int64 / int32 / 16-bit CUDA
+    tensors.  Returns a list of DeviceResult (raises on the first failure)."""
+    lib = load()
+    n = len(mats)
+    ins = (CsrIn * max(n, 1))()
+    ps = (ctypes.c_uint32 * max(n, 1))()
+    for i, (rp, c, v, shape, p) in enumerate(mats):
+        ins[i] = CsrIn(int(shape[0]), int(shape[1]), int(c.numel()), rp.data_ptr(), c.data_ptr(), v.data_ptr())
+        ps[i] = int(p)
+    opt = _options(want_reduced, variant, 1, path)
+    outs = (CsrOut * max(n, 1))()
+    ranks = (ctypes.c_int64 * max(n, 1))()
+    codes = (ctypes.c_int * max(n, 1))()
+    rc = lib.gbla_reduce_batch(n, ins, ps, ctypes.byref(opt), int(workers), outs, ranks, codes)
+    res = [DeviceResult(outs[i], int(ranks[i]), {}) for i in range(n)]
+    if rc != GBLA_OK:
+        for r in res:
+            r.free()
+    _check(rc, "gbla_reduce_batch")
+    return res
+
+
 class Server:
     """Request server with continuous batching (see gbla_server_* in gbla.h)."""
 
