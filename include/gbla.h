@@ -91,6 +91,9 @@ typedef struct {
     int path;          /* GBLA_PATH_* */
     int leaf_width;    /* leaf columns of the triangular solve: 0 = chosen per matrix,
                           else 128, 256, 512 or 1024 */
+    int kernel_times;  /* 1: time every launch of the two tensor-core kernels with events
+                          and count the dense product's tile work (gbla_stats.tc_*,
+                          gather_*); needs stats */
 } gbla_options;
 
 /* Per-call statistics (optional out-parameter). */
@@ -110,6 +113,12 @@ typedef struct {
     int64_t leaf_width;     /* leaf columns of the triangular solve */
     double schur_exec_mod_ops; /* sparse path: multiply-adds the Schur launch runs on the tensor
                                   cores (its compacted tiles, zeros included) */
+    /* with gbla_options.kernel_times: the dense tensor-core product (all its
+     * launches: leaf solves, echelon waves, back-substitution) and the gathered
+     * product (triangular-solve updates and the Schur update) */
+    int64_t tc_launches, gather_launches;
+    double tc_ms, gather_ms;     /* sums of the event-timed launch durations */
+    double tc_mod_ops;           /* dense product: valid rows x columns x K run of its tiles */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */

@@ -475,6 +475,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     const int variant = opt ? opt->gemm_variant : GBLA_GEMM_AUTO;
     const int device_ptrs = opt ? opt->device_ptrs : 0;
     const int path_opt = opt ? opt->path : GBLA_PATH_AUTO;
+    const bool ktimes = opt && opt->kernel_times && stats;
     const int leaf_opt = opt ? opt->leaf_width : 0;
     if (variant < 0 || variant > GBLA_GEMM_SIMT) return GBLA_E_INVAL;
     if (path_opt < GBLA_PATH_AUTO || path_opt > GBLA_PATH_SPARSE) return GBLA_E_INVAL;
@@ -511,6 +512,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     int rc = GBLA_OK;
     uint32_t *err = nullptr;
     unsigned long long *exec_ctr = nullptr;   // executed list entries x row tiles of the Schur launch
+    unsigned long long *tc_work = nullptr;    // dense product tile work (kernel timing)
+    KernelTimeTotals kt;
     int64_t *d_rp = nullptr;
     int32_t *d_col = nullptr;
     uint16_t *d_val = nullptr;
@@ -549,6 +552,11 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
 
     STEP(dalloc_t(&err, 4, s));
     CSTEP(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    if (ktimes) {
+        STEP(dalloc_t(&tc_work, 1, s));
+        CSTEP(cudaMemsetAsync(tc_work, 0, sizeof(unsigned long long), s));
+        kernel_times_begin(tc_work);
+    }
     if (device_ptrs) {
         dc.row_ptr = in->row_ptr;
         dc.col = in->col;
@@ -888,16 +896,27 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
                 unsigned long long e = 0;
                 if (readback(&e, exec_ctr, sizeof(e), s) == GBLA_OK) stats->schur_exec_mod_ops = (double)e * 128.0 * 128.0;
             }
+            if (ktimes) {
+                kernel_times_end(&kt);
+                stats->tc_launches = kt.launches[0];
+                stats->gather_launches = kt.launches[1];
+                stats->tc_ms = kt.ms[0];
+                stats->gather_ms = kt.ms[1];
+                unsigned long long w = 0;
+                if (readback(&w, tc_work, sizeof(w), s) == GBLA_OK) stats->tc_mod_ops = (double)w;
+            }
         }
     }
 
 cleanup:
+    if (ktimes && rc != GBLA_OK) kernel_times_end(&kt);
     if (side_pending) {   // nothing the side stream uses may be freed before it is done
         cudaStreamSynchronize(g_side.s);
         cudaGetLastError();
     }
     dfree(err, s);
     dfree(exec_ctr, s);
+    dfree(tc_work, s);
     dfree(d_rp, s);
     dfree(d_col, s);
     dfree(d_val, s);

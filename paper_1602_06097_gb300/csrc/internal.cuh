@@ -26,6 +26,19 @@ struct GroupProb {
     int64_t tile_off;
 };
 
+// Per-launch timing of the tensor-core kernels on the calling thread (kind 0:
+// the dense product modgemm_tc_kernel, 1: the gathered product), opt-in per
+// reduction: between begin and end every launch is bracketed by events on its
+// stream, and the dense product adds valid rows x valid columns x K run of
+// each tile to *tc_work_dev (device counter, may be null).  end() needs the
+// stream synchronised.
+struct KernelTimeTotals {
+    double ms[2] = {0, 0};
+    int64_t launches[2] = {0, 0};
+};
+void kernel_times_begin(unsigned long long *tc_work_dev);
+void kernel_times_end(KernelTimeTotals *t);
+
 // True on a device with the tcgen05 tensor-core path (compute capability 10.3).
 bool tc_supported();
 

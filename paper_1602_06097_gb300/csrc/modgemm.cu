@@ -229,6 +229,7 @@ struct Args {
     int64_t xout_row0;       // xout_col0 + n; C unused
     int a_pitch;             // elements per 32-wide K chunk of an A row: 64 (2 planes) or
                              // 128 (a 4-plane set read as its first two planes); 0 = 64
+    unsigned long long *work; // optional: += valid rows x valid columns x K run, per tile
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
@@ -802,6 +803,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const TileInfo ti = tile_info<PAIR>(g, t, num_m, num_n, rank);
             const int kbt = (ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
             if (kbt <= 0) continue;   // the product is zero on this tile: C stays as it is
+            if (g.work && warp == 2 && lane == 0) {
+                const int64_t vr = min((int64_t)TBM, ti.M - ti.mt * TBM), vc = min((int64_t)BN, ti.N - ti.nt * BN);
+                const int64_t kr = g.K - (int64_t)ti.ks0 * BK;
+                if (vr > 0 && vc > 0 && kr > 0 && (!PAIR || rank == 0))
+                    atomicAdd(g.work, (unsigned long long)(vr * vc * kr));
+            }
             uint32_t run[HC / 2];
 #pragma unroll
             for (int i = 0; i < HC / 2; ++i) run[i] = 0;
@@ -1291,6 +1298,81 @@ static int make_map(CUtensorMap *map, const Planes &pl, int box_rows = tc::BM) {
     return r == CUDA_SUCCESS ? GBLA_OK : GBLA_E_CUDA;
 }
 
+// ----------------------------------------------- per-launch timing (opt-in)
+// While a reduction runs with kernel timing on, every launch of the two
+// tensor-core kernels on the calling thread is bracketed by a pair of events
+// on its stream (events from a per-thread pool), and the dense product
+// counts its tiles' work on the device.
+namespace {
+struct KernelTimes {
+    bool on = false;
+    unsigned long long *tc_work = nullptr;   // device counter of the dense product's tile work
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, size_t>> marks;   // (kind, index of the start event)
+    size_t used = 0;
+    int dev = -1;
+};
+thread_local KernelTimes g_kt;
+
+cudaEvent_t kt_event() {
+    if (g_kt.used == g_kt.pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_kt.pool.push_back(e);
+    }
+    return g_kt.pool[g_kt.used++];
+}
+
+// kind 0: modgemm_tc_kernel, 1: modgemm_gather_kernel
+void kt_start(int kind, cudaStream_t s) {
+    if (!g_kt.on) return;
+    const size_t i = g_kt.used;
+    cudaEvent_t a = kt_event();
+    if (a && cudaEventRecord(a, s) == cudaSuccess) g_kt.marks.emplace_back(kind, i);
+}
+void kt_stop(cudaStream_t s) {
+    if (!g_kt.on || g_kt.marks.empty() || g_kt.marks.back().second + 1 != g_kt.used) return;
+    cudaEvent_t b = kt_event();
+    if (b) cudaEventRecord(b, s);
+}
+}  // namespace
+
+void kernel_times_begin(unsigned long long *tc_work_dev) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_kt.dev != dev) {   // events belong to the device that was current when they were made
+        for (cudaEvent_t e : g_kt.pool) cudaEventDestroy(e);
+        g_kt.pool.clear();
+        g_kt.dev = dev;
+    }
+    g_kt.on = true;
+    g_kt.tc_work = tc_work_dev;
+    g_kt.marks.clear();
+    g_kt.used = 0;
+}
+
+void kernel_times_end(KernelTimeTotals *t) {
+    *t = KernelTimeTotals{};
+    if (g_kt.on)
+        for (const auto &mk : g_kt.marks) {
+            if (mk.second + 1 >= g_kt.used) continue;
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, g_kt.pool[mk.second], g_kt.pool[mk.second + 1]) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            t->ms[mk.first] += ms;
+            t->launches[mk.first] += 1;
+        }
+    g_kt.on = false;
+    g_kt.tc_work = nullptr;
+    g_kt.marks.clear();
+    g_kt.used = 0;
+}
+
 // The product kernel's shared-memory limit, set once per process (thread-safe).
 static cudaError_t tc_kernel_attrs() {
     static const cudaError_t rc = cudaFuncSetAttribute(tc::modgemm_tc_kernel<false>,
@@ -1437,11 +1519,17 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
         cfg.stream = s;
         cfg.attrs = at;
         cfg.numAttrs = 1;
+        g.work = g_kt.tc_work;
+        kt_start(0, s);
         GBLA_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::modgemm_tc_kernel<true>, ma, mb, g));
+        kt_stop(s);
     } else {
         const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
         const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+        g.work = g_kt.tc_work;
+        kt_start(0, s);
         tc::modgemm_tc_kernel<false><<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+        kt_stop(s);
     }
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
@@ -1478,9 +1566,12 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     g.xout_col0 = out_col0;
     g.xout_row0 = out_row0;
     g.a_pitch = 32 * A.nplanes;
+    g.work = g_kt.tc_work;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+    kt_start(0, s);
     tc::modgemm_tc_kernel<false><<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    kt_stop(s);
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
@@ -1542,7 +1633,9 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
     g.kstart = kstart;
     const int64_t tiles = num_m * num_n;
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+    kt_start(1, s);
     tc::modgemm_gather_kernel<<<grid, tc::G_THREADS, tc::G_SMEM_BYTES, s>>>(mb, g);
+    kt_stop(s);
     const cudaError_t e = cudaGetLastError();
     ++g_launches;
     dfree(kstart, s);
@@ -1595,7 +1688,10 @@ int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, in
     g.C = C; g.ldc = ldc; g.sign = sign;
     g.p = mp.p; g.pinv = mp.pinv;
     g.err = err;
+    g.work = g_kt.tc_work;
+    kt_start(0, s);
     tc::modgemm_tc_kernel<false><<<device_sm_count(), tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
+    kt_stop(s);
     GBLA_CUDA_TRY(launch_check());
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;

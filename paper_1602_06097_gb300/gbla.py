@@ -40,11 +40,12 @@ class CsrOut(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("want_reduced", ctypes.c_int), ("gemm_variant", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("panel_width", ctypes.c_int),
-                ("path", ctypes.c_int), ("leaf_width", ctypes.c_int)]
+                ("path", ctypes.c_int), ("leaf_width", ctypes.c_int), ("kernel_times", ctypes.c_int)]
 
 
-def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0):
-    return Options(1 if want_reduced else 0, int(variant), int(device_ptrs), 0, int(path), int(leaf))
+def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0, kernel_times=False):
+    return Options(1 if want_reduced else 0, int(variant), int(device_ptrs), 0, int(path), int(leaf),
+                   1 if kernel_times else 0)
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +56,9 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("mod_ops", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("schur_mod_ops", ctypes.c_double), ("ms_echelon_back", ctypes.c_double),
                 ("path", ctypes.c_int64), ("list_a", ctypes.c_int64), ("list_b", ctypes.c_int64),
-                ("leaf_width", ctypes.c_int64), ("schur_exec_mod_ops", ctypes.c_double)]
+                ("leaf_width", ctypes.c_int64), ("schur_exec_mod_ops", ctypes.c_double),
+                ("tc_launches", ctypes.c_int64), ("gather_launches", ctypes.c_int64),
+                ("tc_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("tc_mod_ops", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -293,14 +296,14 @@ class _CudaArray:
 
 
 def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
-                  path=PATH_AUTO, leaf=0):
+                  path=PATH_AUTO, leaf=0, kernel_times=False):
     """Reduce a CSR matrix already on the device (torch CUDA tensors: int64
     row_ptr, int32 col, int16/uint16 val).  Returns a DeviceResult whose
     arrays stay in device memory."""
     lib = load()
     m, n = int(shape[0]), int(shape[1])
     cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
-    opt = _options(want_reduced, variant, 1, path, leaf)
+    opt = _options(want_reduced, variant, 1, path, leaf, kernel_times)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
