@@ -16,7 +16,9 @@ matrix (replicas; no data-path collective) and the time is the maximum over
 ranks.  On one GPU the line also carries:
   * "fl_40000x60000": the 40,000 x 60,000 workload on the sparse and the
     dense path, with the oracle's full work counts (modular GOPS) and a
-    bit-exact check of the result against the oracle's stored digest;
+    bit-exact check of the result against the oracle's stored digest, and
+    its dense Schur update on each exact product (tcgen05 bf16 digits,
+    mma.sync u8, mma.sync f64) against that pipe's own measured peak;
   * "batched": 256 F4 matrices of uneven sizes (rows log-uniform in
     500-20,000, p in {65521, 32003}) one call per matrix against the batch
     entry point, whose reductions overlap on the device;
@@ -344,6 +346,33 @@ def block_40000x60000(gbla, synth, peak, stream):
         out["oracle_whole_matrix"] = {"seconds": rec["oracle_seconds"]["total"], "threads": rec["threads"],
                                       "cpu": rec["cpu"], "kind": "measured, whole matrix (recorded run)"}
     out["speedup_sparse_over_dense"] = out["dense"]["ms_per_matrix"] / out["sparse"]["ms_per_matrix"]
+    out["schur_variants"] = schur_variants(gbla, d, (spec.m, spec.n), spec.p, stream, peak, rec)
+    return out
+
+
+def schur_variants(gbla, d, shape, p, stream, bf16_peak, rec):
+    """The dense path's Schur update D <- D - X*B on each exact product
+    (tcgen05 bf16 digits; mma.sync u8 bytes; mma.sync f64 balanced residues),
+    one reduction each, the Schur phase event-timed.  Each is set against its
+    own pipe's peak: bf16 the measured cuBLAS figure, u8 and f64 the library's
+    issue-rate microbenchmark run here.  Work = the product's multiply-adds
+    (zero staircase excluded) x the instruction ops each needs: 4 bf16 digit
+    products (8 flops), 4 byte products (8 ops), 1 fp64 fma (2 flops)."""
+    peaks = {"fp64": gbla.pipe_peak(gbla.GEMM_FP64, stream), "u8": gbla.pipe_peak(gbla.GEMM_U8, stream)}
+    out = {"peaks": {"tcgen05_bf16_tflops": bf16_peak, "mma_sync_u8_tops_measured": peaks["u8"],
+                     "mma_sync_fp64_tflops_measured": peaks["fp64"]}}
+    for variant, label, per_op, pk in ((gbla.GEMM_TCGEN05, "tcgen05_bf16", 8.0, bf16_peak),
+                                       (gbla.GEMM_U8, "mma_sync_u8", 8.0, peaks["u8"]),
+                                       (gbla.GEMM_FP64, "mma_sync_fp64", 2.0, peaks["fp64"])):
+        r = gbla.reduce_device(*d, shape, p, stream=stream, path=1, variant=variant)
+        st = r.stats
+        rank, orp, oc, ov = r.to_host()
+        r.free()
+        ms, ops = st["ms_schur"], st["schur_mod_ops"]
+        ach = per_op * ops / (ms / 1e3) / 1e12 if ms > 0 else None
+        out[label] = {"schur_ms": ms, "reduction_ms": st["ms_total"], "schur_mod_ops": ops, "ops_per_mod_op": per_op,
+                      "achieved": ach, "peak": pk, "frac_of_own_peak": ach / pk if ach else None,
+                      "bit_exact_vs_oracle": bool(rec and sha256_csr(orp, oc, ov) == rec["result_sha256"])}
     return out
 
 

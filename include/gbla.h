@@ -74,6 +74,14 @@ typedef struct {
 #define GBLA_GEMM_AUTO 0     /* tensor-core path where it applies */
 #define GBLA_GEMM_TCGEN05 1  /* bf16 8-bit digits on tcgen05.mma, fp32 TMEM accumulators */
 #define GBLA_GEMM_SIMT 2     /* exact int64 CUDA-core kernel (reference variant) */
+/* Measured alternatives of the Schur update D <- D - X*B (Sec. 4.3) on the
+ * legacy warp-level tensor-core instructions.  In gbla_options they select the
+ * dense path with the Schur update on that pipe (every other product on
+ * tcgen05; needs p >= 8); gbla_modmatmul runs the whole product on it. */
+#define GBLA_GEMM_FP64 3     /* mma.sync m8n8k4 f64 on balanced residues: exact while
+                                k-blocks of 2^23 keep sums below 2^53 (delayed reduction) */
+#define GBLA_GEMM_U8 4       /* mma.sync m16n8k32 u8 x u8 -> s32 on the residues' bytes,
+                                three accumulators, exact over k-blocks of 2^14 */
 
 /* How C*A^-1 and the Schur update treat the pivot rows (Sec. 4.1, Table 4's
  * block densities). */
@@ -85,7 +93,8 @@ typedef struct {
 
 typedef struct {
     int want_reduced;  /* 1: RREF(M); 0: echelon form of the new order */
-    int gemm_variant;  /* GBLA_GEMM_* for every dense modular product */
+    int gemm_variant;  /* GBLA_GEMM_AUTO, _TCGEN05 or _SIMT: every dense modular product;
+                          GBLA_GEMM_FP64 or _U8: the Schur update only (dense path) */
     int device_ptrs;   /* 1: input and output arrays live on the device */
     int panel_width;   /* column panel of the D echelonisation, 0 = default (128) */
     int path;          /* GBLA_PATH_* */
@@ -119,6 +128,8 @@ typedef struct {
     int64_t tc_launches, gather_launches;
     double tc_ms, gather_ms;     /* sums of the event-timed launch durations */
     double tc_mod_ops;           /* dense product: valid rows x columns x K run of its tiles */
+    int64_t tc_pair_launches;    /* dense product launches that ran on CTA pairs (cta_group::2,
+                                    enabled by the environment switch GBLA_GEMM_PAIR=1) */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */
@@ -197,6 +208,15 @@ int gbla_version(void);
 int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t lda,
                    const uint16_t *B, int64_t ldb, uint16_t *C, int64_t ldc,
                    uint32_t p, int sign, int variant, void *stream);
+
+/* Issue-rate microbenchmark of a legacy tensor-core pipe: variant
+ * GBLA_GEMM_FP64 (mma.sync m8n8k4 f64) or GBLA_GEMM_U8 (mma.sync m16n8k32
+ * u8).  Every warp runs eight independent accumulator chains on operands held
+ * in registers; the loop grows until one launch lasts at least 20 ms, timed
+ * with CUDA events on `stream`.  *tops receives the instruction's operations
+ * (2*M*N*K per instruction) per second in units of 1e12.  Synchronises
+ * `stream`.  GBLA_E_INVAL for another variant or a null tops. */
+int gbla_pipe_peak(int variant, double *tops, void *stream);
 
 /* Sparse-path product (the Schur update D <- D - X*B of the new order,
  * Sec. 4.3, with B kept sparse as in Table 4):

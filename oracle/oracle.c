@@ -358,8 +358,8 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
         }
     /* entries of each pivot row at other pivot columns (na) and at the
      * non-pivot columns (nb), for the work counter */
-    int64_t *na = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
-    int64_t *nb = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+    int64_t *na = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    int64_t *nb = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
     if (!na || !nb) { free(na); free(nb); rc = ORA_E_NOMEM; goto fail0; }
     for (int64_t c = 0; c < n; ++c)
         if (piv_row[c] >= 0)

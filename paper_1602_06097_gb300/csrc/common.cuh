@@ -240,6 +240,8 @@ namespace gbla {
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 // Kernel launches made by this thread (reported in gbla_stats.launches).
 extern thread_local long long g_launches;
+// Dense-product launches on CTA pairs made by this thread.
+extern thread_local long long g_pair_launches;
 // Call right after a kernel launch: counts it and returns the launch status.
 inline cudaError_t launch_check() {
     ++g_launches;

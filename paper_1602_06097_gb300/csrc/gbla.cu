@@ -27,6 +27,7 @@ namespace gbla {
 
 static thread_local char g_last_err[512];
 thread_local long long g_launches = 0;
+thread_local long long g_pair_launches = 0;
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
     snprintf(g_last_err, sizeof(g_last_err), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what, file, line,
@@ -477,8 +478,12 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     const int path_opt = opt ? opt->path : GBLA_PATH_AUTO;
     const bool ktimes = opt && opt->kernel_times && stats;
     const int leaf_opt = opt ? opt->leaf_width : 0;
-    if (variant < 0 || variant > GBLA_GEMM_SIMT) return GBLA_E_INVAL;
+    if (variant < 0 || variant > GBLA_GEMM_U8) return GBLA_E_INVAL;
     if (path_opt < GBLA_PATH_AUTO || path_opt > GBLA_PATH_SPARSE) return GBLA_E_INVAL;
+    // FP64 and U8 name the pipe of the Schur update on the dense path; every
+    // other product of the reduction runs on the tcgen05 tensor cores.
+    const bool alt_schur = variant == GBLA_GEMM_FP64 || variant == GBLA_GEMM_U8;
+    const int pvariant = alt_schur ? GBLA_GEMM_TCGEN05 : variant;
     if (leaf_opt != 0 && leaf_opt != 128 && leaf_opt != 256 && leaf_opt != 512 && leaf_opt != 1024)
         return GBLA_E_INVAL;
     const int64_t m = in->nrows, n = in->ncols, nnz = in->nnz;
@@ -492,17 +497,18 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     const ModP mp = make_modp(p);
     // diagonal blocks of the triangular solve on the tensor cores too
     const bool tc_leaves =
-        variant == GBLA_GEMM_TCGEN05 || (variant == GBLA_GEMM_AUTO && p >= 8 && tc_supported());
+        pvariant == GBLA_GEMM_TCGEN05 || (pvariant == GBLA_GEMM_AUTO && p >= 8 && tc_supported());
     // The sparse path keeps A and B sparse and runs C*A^-1 and the Schur
     // update as K-compacted tensor-core products; it needs the tensor-core
     // variant.  The dense path materialises A and B (and serves p < 8 and the
     // exact SIMT variant).
-    const bool tc_ok = variant != GBLA_GEMM_SIMT && p >= 8 && tc_supported();
-    if (path_opt == GBLA_PATH_SPARSE && !tc_ok) return GBLA_E_UNSUPPORTED;
-    const bool sparse = tc_ok && path_opt != GBLA_PATH_DENSE;
+    const bool tc_ok = pvariant != GBLA_GEMM_SIMT && p >= 8 && tc_supported();
+    if (path_opt == GBLA_PATH_SPARSE && (!tc_ok || alt_schur)) return GBLA_E_UNSUPPORTED;
+    if (alt_schur && !tc_ok) return GBLA_E_UNSUPPORTED;
+    const bool sparse = tc_ok && path_opt != GBLA_PATH_DENSE && !alt_schur;
     int tc_leaf_w = 512;
     GemmCounters ctr;
-    const long long launches0 = g_launches;
+    const long long launches0 = g_launches, pair_launches0 = g_pair_launches;
     Timer tm;
     tm.init(stats != nullptr);
     tm.mark(s);
@@ -712,7 +718,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         lead_h.resize((size_t)m_cd);
         STEP(readback(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, s));
         if (tc_leaves) STEP(planes_alloc(&Ct, m_cd, tc_leaf_w, 2, s));
-        TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, variant, err, s, &ctr, pi.cd_lead, &lead_h,
+        TrsmUpper T{m_cd, npiv, C16, ldc, &ml, &Xp, &At, &mp, pvariant, err, s, &ctr, pi.cd_lead, &lead_h,
                     tc_leaves ? &Zt : nullptr, tc_leaves ? &Ct : nullptr, tc_leaf_w};
         NvtxRange r("gbla.trsm");
         STEP(trsm_upper(T));
@@ -738,7 +744,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     STEP(dalloc_t(&prow, (size_t)m_cd + 1, s));
     STEP(dalloc_t(&pcol, (size_t)m_cd + 1, s));
     {
-        EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, variant, err, s, &ctr,
+        EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, pvariant, err, s, &ctr,
                    tm.on ? tm.ev[7] : nullptr, back_leaf_width()};
         NvtxRange r("gbla.echelon");
         STEP(echelon_d(E, &rank_d));
@@ -749,7 +755,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     if (want_reduced && npiv > 0 && n_d > 0) {
         STEP(planes_alloc(&Xq, n_d, npiv, 2, s));
         STEP(planes_zero(Xq, s));
-        TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, variant, err, s, &ctr};
+        TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr};
         STEP(trsm_lower(T));
         if (rank_d > 0) {
             // Y^T[c][j] -= sum_k RREF(D')[k][c] * Y^T[P_D[k]][j]
@@ -757,7 +763,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             STEP(planes_alloc(&XpdT, npiv, rank_d, 4, s));
             STEP(to_planes(RdT, n_d, rank_d, R16, ldd, 0, true, nullptr, nullptr, mp, s));
             STEP(to_planes(XpdT, npiv, rank_d, Bt16, ldbt, 0, true, pcol, nullptr, mp, s));
-            STEP(modgemm(RdT, 0, 0, XpdT, 0, 0, Bt16, ldbt, n_d, npiv, rank_d, -1, mp, variant, err, s, &ctr));
+            STEP(modgemm(RdT, 0, 0, XpdT, 0, 0, Bt16, ldbt, n_d, npiv, rank_d, -1, mp, pvariant, err, s, &ctr));
         }
         STEP(dalloc_t(&Y16, (size_t)npiv * (size_t)ldd, s));
         dim3 grid((unsigned)((npiv + 31) / 32), (unsigned)((n_d + 31) / 32));
@@ -887,6 +893,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             stats->ms_total = tm.ms(0, 6);
             stats->mod_ops = ctr.mod_ops;
             stats->launches = g_launches - launches0;
+            stats->tc_pair_launches = g_pair_launches - pair_launches0;
             stats->schur_mod_ops = schur_ops;
             stats->path = sparse ? GBLA_PATH_SPARSE : GBLA_PATH_DENSE;
             stats->list_a = SA.total;
@@ -1024,7 +1031,7 @@ int gbla_reduce(const gbla_csr_in *in, uint32_t p, int want_reduced, gbla_csr_ou
 int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb,
                    uint16_t *C, int64_t ldc, uint32_t p, int sign, int variant, void *stream) {
     if (M < 0 || N < 0 || K < 0 || p >= 65536u || !is_prime(p) || (sign != 1 && sign != -1)) return GBLA_E_INVAL;
-    if (variant < 0 || variant > GBLA_GEMM_SIMT) return GBLA_E_INVAL;
+    if (variant < 0 || variant > GBLA_GEMM_U8) return GBLA_E_INVAL;
     if (M == 0 || N == 0 || K == 0) return GBLA_OK;
     if (!A || !B || !C || lda < K || ldb < N || ldc < N) return GBLA_E_INVAL;
     GBLA_TRY(check_device());
@@ -1048,6 +1055,12 @@ int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t l
     dfree(err, s);
     cudaStreamSynchronize(s);
     return rc;
+}
+
+int gbla_pipe_peak(int variant, double *tops, void *stream) {
+    if (!tops || (variant != GBLA_GEMM_FP64 && variant != GBLA_GEMM_U8)) return GBLA_E_INVAL;
+    GBLA_TRY(check_device());
+    return pipe_peak(variant, tops, (cudaStream_t)stream);
 }
 
 int gbla_spmm(int64_t M, int64_t N, int64_t K, const uint16_t *X, int64_t ldx, const gbla_csr_in *S_dev,

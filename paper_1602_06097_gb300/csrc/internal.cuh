@@ -117,6 +117,20 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
             uint32_t *err, cudaStream_t s, GemmCounters *ctr, const int32_t *c_rows = nullptr,
             const int32_t *row_lead = nullptr, const int32_t *row_lead_host = nullptr);
 
+// The same product on the legacy warp-level tensor-core instructions
+// (modgemm_alt.cu): variant GBLA_GEMM_FP64 (mma.sync f64, exact over k-blocks
+// of 2^23) or GBLA_GEMM_U8 (mma.sync u8 -> s32 on the bytes of the residues,
+// exact over k-blocks of 2^14).  Reads planes 0 and 1 of both sets; a_k0 and
+// b_k0 multiples of 32; with row_lead (ascending, product-row indexed) each
+// 64-row tile starts at its first row's lead.
+int modgemm_alt(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int64_t b_row0, int64_t b_k0,
+                uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
+                cudaStream_t s, const int32_t *c_rows, const int32_t *row_lead);
+
+// Issue-rate microbenchmark of the FP64 or U8 mma.sync pipe (ops of the
+// instruction per second, in units of 1e12), timed with events on s.
+int pipe_peak(int variant, double *tops, cudaStream_t s);
+
 // Test hook: a product whose loads are withheld, so that its bounded waits
 // expire; sets DEV_ERR_TIMEOUT in *err (see modgemm.cu).
 int modgemm_withheld_loads(uint32_t *err, cudaStream_t s);

@@ -1477,6 +1477,8 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
         ctr->mod_ops += ops;
         ctr->last_ops = ops;
     }
+    if (variant == GBLA_GEMM_FP64 || variant == GBLA_GEMM_U8)
+        return modgemm_alt(A, a_row0, a_k0, B, b_row0, b_k0, C, ldc, M, N, K, sign, mp, variant, s, c_rows, row_lead);
     if (variant == GBLA_GEMM_SIMT) {
         dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
         modgemm_simt_kernel<<<grid, 256, 0, s>>>(A, a_row0, a_k0, B, b_row0, b_k0, C, ldc, c_rows, M, N, K, sign, mp);
@@ -1523,6 +1525,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
         kt_start(0, s);
         GBLA_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::modgemm_tc_kernel<true>, ma, mb, g));
         kt_stop(s);
+        ++g_pair_launches;
     } else {
         const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
         const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());

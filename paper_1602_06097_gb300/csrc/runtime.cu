@@ -222,7 +222,8 @@ struct gbla_server {
     static size_t estimate(const gbla_csr_in &in, uint32_t p, const gbla_options &opt) {
         const double m = (double)in.nrows, n = (double)in.ncols;
         const double k = std::min(m, n);
-        const bool sparse = opt.path != GBLA_PATH_DENSE && opt.gemm_variant != GBLA_GEMM_SIMT && p >= 8;
+        const bool sparse = opt.path != GBLA_PATH_DENSE && p >= 8 &&
+                            (opt.gemm_variant == GBLA_GEMM_AUTO || opt.gemm_variant == GBLA_GEMM_TCGEN05);
         const double work = sparse ? 6.0 * m * k + 24.0 * (double)in.nnz + 12.0 * m * n
                                    : 12.0 * k * n + 6.0 * m * n;
         return (size_t)(8.0 * (m + 1) + 6.0 * (double)in.nnz + work + (64 << 20));

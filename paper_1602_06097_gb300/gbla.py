@@ -16,14 +16,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbla.so")
 
 GBLA_OK = 0
-GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT = 0, 1, 2
+GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT, GEMM_FP64, GEMM_U8 = 0, 1, 2, 3, 4
 PATH_AUTO, PATH_DENSE, PATH_SPARSE = 0, 1, 2
 
 EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
            "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc",
            "gbla_selftest_wait_timeout", "gbla_reduce_batch", "gbla_server_create", "gbla_server_submit",
            "gbla_server_wait", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy",
-           "gbla_decode_format2", "gbla_spmm"]
+           "gbla_decode_format2", "gbla_spmm", "gbla_pipe_peak"]
 
 
 class CsrIn(ctypes.Structure):
@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("path", ctypes.c_int64), ("list_a", ctypes.c_int64), ("list_b", ctypes.c_int64),
                 ("leaf_width", ctypes.c_int64), ("schur_exec_mod_ops", ctypes.c_double),
                 ("tc_launches", ctypes.c_int64), ("gather_launches", ctypes.c_int64),
-                ("tc_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("tc_mod_ops", ctypes.c_double)]
+                ("tc_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("tc_mod_ops", ctypes.c_double),
+                ("tc_pair_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -112,6 +113,8 @@ def load():
         lib.gbla_modmatmul.restype = i32
         lib.gbla_pivots.argtypes = [ctypes.POINTER(CsrIn), u32, vp, ctypes.POINTER(i64), vp]
         lib.gbla_spmm.restype = i32
+        lib.gbla_pipe_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+        lib.gbla_pipe_peak.restype = i32
         lib.gbla_spmm.argtypes = [i64, i64, i64, vp, i64, ctypes.POINTER(CsrIn), vp, vp, i64, u32, i32, vp]
         lib.gbla_pivots.restype = i32
         lib.gbla_multiline.argtypes = [ctypes.POINTER(CsrIn), vp, vp, vp, vp]
@@ -460,6 +463,14 @@ def modmatmul(A, B, C, p, sign=-1, variant=GEMM_AUTO, stream=None):
     rc = lib.gbla_modmatmul(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                             C.data_ptr(), C.stride(0), int(p), int(sign), int(variant), _stream_ptr(stream))
     _check(rc, "gbla_modmatmul")
+
+
+def pipe_peak(variant, stream=None):
+    """Measured issue rate (1e12 ops/s) of the FP64 or U8 mma.sync pipe."""
+    lib = load()
+    out = ctypes.c_double(0.0)
+    _check(lib.gbla_pipe_peak(int(variant), ctypes.byref(out), _stream_ptr(stream)), "gbla_pipe_peak")
+    return out.value
 
 
 def spmm(X, S_row_ptr, S_col, S_val, N, C, p, sign=-1, x_lead=None, stream=None):

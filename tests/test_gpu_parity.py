@@ -60,8 +60,9 @@ def test_modmatmul_random(variant, shape, p, sign):
 @pytest.mark.parametrize("M", [128, 384])
 def test_modmatmul_at_the_k_block_bound(variant, K, fill, M):
     """All-extreme operands at and around the 512-deep exact fp32 block: every
-    digit product has the largest magnitude the split allows.  M = 384 runs
-    the tensor-core product on CTA pairs (256-row tiles, a ragged last one)."""
+    digit product has the largest magnitude the split allows.  M = 384 gives
+    three row tiles, a ragged raster group (the CTA-pair form of the same
+    product runs in tests/test_gpu_env_variants.py)."""
     p = 65521
     N = 128
     h = (p - 1) // 2

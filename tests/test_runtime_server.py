@@ -57,6 +57,8 @@ const int cudaSuccess = 0, cudaStreamNonBlocking = 1;
 struct gbla_csr_in { int64_t nrows, ncols, nnz; const int64_t *row_ptr; const int32_t *col; const uint16_t *val; };
 struct gbla_csr_out { int64_t nrows, ncols, nnz; int64_t *row_ptr; int32_t *col; uint16_t *val; int on_device; };
 struct gbla_options { int want_reduced, gemm_variant, device_ptrs, panel_width, path, leaf_width, kernel_times; };
+#define GBLA_GEMM_AUTO 0
+#define GBLA_GEMM_TCGEN05 1
 #define GBLA_GEMM_SIMT 2
 #define GBLA_PATH_DENSE 1
 typedef struct {
