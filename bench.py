@@ -347,6 +347,31 @@ def block_40000x60000(gbla, synth, peak, stream):
                                       "cpu": rec["cpu"], "kind": "measured, whole matrix (recorded run)"}
     out["speedup_sparse_over_dense"] = out["dense"]["ms_per_matrix"] / out["sparse"]["ms_per_matrix"]
     out["schur_variants"] = schur_variants(gbla, d, (spec.m, spec.n), spec.p, stream, peak, rec)
+    out["reduced_form_orders"] = reduced_form_orders(gbla, d, (spec.m, spec.n), spec.p, stream)
+    return out
+
+
+def reduced_form_orders(gbla, d, shape, p, stream):
+    """RREF of the workload in the new order (Sec. 4.3: C A^-1, Schur update,
+    echelon of D', then A^-1 B and its fix-up) against the original order
+    (Sec. 4.1: A^-1 B first, Schur update with C, echelon, fix-up), one
+    event-timed reduction each after a warm-up, and the two results compared
+    on the device."""
+    import torch
+    out, res = {}, {}
+    for order, label in ((0, "new_order"), (1, "trsm_first")):
+        gbla.reduce_device(*d, shape, p, want_reduced=True, order=order, stream=stream).free()
+        r = gbla.reduce_device(*d, shape, p, want_reduced=True, order=order, stream=stream)
+        st = r.stats
+        res[label] = r
+        out[label] = {"ms": st["ms_total"], "path": ["", "dense", "sparse"][int(st["path"])],
+                      "phase_ms": {k: st[k] for k in ("ms_split", "ms_trsm", "ms_schur", "ms_echelon", "ms_backsub",
+                                                      "ms_output")}}
+    a, b = res["new_order"], res["trsm_first"]
+    out["equal"] = bool(a.rank == b.rank and a.nnz == b.nnz and
+                        all(torch.equal(x, y) for x, y in zip(a.tensors(), b.tensors())))
+    a.free()
+    b.free()
     return out
 
 
@@ -373,6 +398,55 @@ def schur_variants(gbla, d, shape, p, stream, bf16_peak, rec):
         out[label] = {"schur_ms": ms, "reduction_ms": st["ms_total"], "schur_mod_ops": ops, "ops_per_mod_op": per_op,
                       "achieved": ach, "peak": pk, "frac_of_own_peak": ach / pk if ach else None,
                       "bit_exact_vs_oracle": bool(rec and sha256_csr(orp, oc, ov) == rec["result_sha256"])}
+    return out
+
+
+def format2_block(gbla, synth, spec, rp, c, v, d, stream, hbm_peak):
+    """The workload written as a Format 2 file (Sec. 3.2: column runs,
+    coefficients stored once per polynomial) and decoded on the device from a
+    page-locked host buffer.  Decode time = the decoder's event-timed device
+    work after the file's sections are on the device; its algorithmic bytes =
+    the file's sections read once + the CSR written (8 (m+1) + 6 nnz).  The
+    decoded CSR must equal the generated one, and the decoded matrix,
+    reduced in place, must give the direct reduction's rank and result."""
+    import torch
+    t0 = time.perf_counter()
+    buf = synth.encode_format2(spec.m, spec.n, spec.p, rp, c, v)
+    enc_s = time.perf_counter() - t0
+    pinned = torch.frombuffer(bytearray(buf), dtype=torch.uint8).pin_memory().numpy()
+    gbla.decode_format2(pinned, stream=stream, timed=True).free()
+    dev_ms, e2e_ms = [], []
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dm = gbla.decode_format2(pinned, stream=stream, timed=True)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        dev_ms.append(dm.decode_ms)
+        if i < 2:
+            dm.free()
+    csr_bytes = 8 * (spec.m + 1) + 6 * len(c)
+    file_bytes = len(buf)
+    ms = statistics.median(dev_ms)
+    out = {"file_bytes": file_bytes, "csr_bytes": csr_bytes, "file_over_csr": file_bytes / csr_bytes,
+           "encode_s_host": enc_s, "decode_ms": ms,
+           "roofline": {"bound": "hbm", "unit": "GB/s", "algorithmic_bytes": file_bytes + csr_bytes,
+                        "achieved": (file_bytes + csr_bytes) / (ms / 1e3) / 1e9, "peak": hbm_peak,
+                        "frac": (file_bytes + csr_bytes) / (ms / 1e3) / 1e9 / hbm_peak},
+           "e2e_ms_from_pinned_host": statistics.median(e2e_ms)}
+    try:
+        trp, tc, tv = dm.tensors()
+        out["decoded_equals_input"] = bool(torch.equal(trp, d[0]) and torch.equal(tc, d[1]) and torch.equal(tv, d[2]))
+        r1 = gbla.reduce_device(trp, tc, tv, (dm.m, dm.n), dm.p, stream=stream)
+        r2 = gbla.reduce_device(*d, (spec.m, spec.n), spec.p, stream=stream)
+        try:
+            out["reduced_in_place_equals_direct"] = bool(
+                r1.rank == r2.rank and r1.nnz == r2.nnz and all(torch.equal(x, y) for x, y in
+                                                                 zip(r1.tensors(), r2.tensors())))
+        finally:
+            r1.free()
+            r2.free()
+    finally:
+        dm.free()
     return out
 
 
@@ -673,7 +747,9 @@ def main():
     }
     if world == 1 and not a.no_extras:
         extras = {}
-        for key, fn in (("fl_40000x60000", lambda: block_40000x60000(gbla, synth, peak, stream)),
+        hbm = peaks.get("hbm_gbs")
+        for key, fn in (("format2", lambda: format2_block(gbla, synth, spec, rp, c, v, (d_rp, d_c, d_v), stream, hbm)),
+                        ("fl_40000x60000", lambda: block_40000x60000(gbla, synth, peak, stream)),
                         ("batched", lambda: batched_vs_plain(gbla, synth, a.batch)),
                         ("serving", lambda: serving(gbla, synth, [float(x) for x in a.serve_rates.split(",")],
                                                     a.serve_pool, a.serve_seconds))):

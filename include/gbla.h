@@ -103,7 +103,16 @@ typedef struct {
     int kernel_times;  /* 1: time every launch of the two tensor-core kernels with events
                           and count the dense product's tile work (gbla_stats.tc_*,
                           gather_*); needs stats */
+    int fl_order;      /* GBLA_ORDER_*: order of the FL steps */
 } gbla_options;
+
+/* Order of the FL steps.  The new order (Sec. 4.3) computes X = C*A^-1 and
+ * D <- D - X*B, and A^-1*B only for the reduced form.  The original order
+ * (Sec. 4.1 steps 2-3) computes B <- A^-1*B first and D <- D - C*B, so the
+ * reduced form needs one triangular solve instead of two; it runs on the
+ * dense path (GBLA_PATH_SPARSE with it gives GBLA_E_UNSUPPORTED). */
+#define GBLA_ORDER_NEW 0
+#define GBLA_ORDER_TRSM_FIRST 1
 
 /* Per-call statistics (optional out-parameter). */
 typedef struct {
@@ -168,7 +177,26 @@ typedef struct {
     int64_t submitted, completed, failed, cancelled, queued, running;
     double p50_ms, p99_ms, mean_ms;   /* submit-to-ready latency of completed requests */
     size_t mem_budget, mem_in_use;    /* bytes, estimated footprints of running requests */
+    int64_t peak_running;             /* most requests running at once so far */
 } gbla_server_stats;
+
+/* One request's timeline (gbla_server_wait_ex).  The device times come from
+ * CUDA events recorded on the worker's stream right before and right after
+ * the reduction, in ms since a reference event recorded when the server was
+ * created; two requests whose [device_start_ms, device_end_ms] intervals
+ * intersect had device work in flight at the same time.  -1 where events
+ * were not available. */
+typedef struct {
+    double latency_ms;        /* submit to result ready (host clock) */
+    double queue_ms;          /* submit to the start of the reduction */
+    double device_start_ms, device_end_ms;
+    int64_t running_at_start; /* requests running when this one started, itself included */
+} gbla_request_info;
+
+#define GBLA_REQ_QUEUED 0
+#define GBLA_REQ_RUNNING 1
+#define GBLA_REQ_DONE 2
+#define GBLA_REQ_CANCELLED 3
 
 /* mem_budget 0 = 80% of the device memory free now; workers 0 = 8. */
 int gbla_server_create(size_t mem_budget, int workers, gbla_server **srv);
@@ -181,6 +209,12 @@ int gbla_server_submit(gbla_server *srv, const gbla_csr_in *in_host, uint32_t p,
  * GBLA_E_CANCELLED if it was cancelled. */
 int gbla_server_wait(gbla_server *srv, int64_t ticket, double timeout_s,
                      gbla_csr_out *out, int64_t *rank, double *latency_ms);
+/* The same, filling *info (may be NULL) with the request's timeline. */
+int gbla_server_wait_ex(gbla_server *srv, int64_t ticket, double timeout_s,
+                        gbla_csr_out *out, int64_t *rank, gbla_request_info *info);
+/* State of a request without waiting: *state = GBLA_REQ_*.  The ticket stays
+ * valid.  GBLA_E_INVAL for an unknown (or already consumed) ticket. */
+int gbla_server_poll(gbla_server *srv, int64_t ticket, int *state);
 /* Cancel a request that is still queued (GBLA_E_INVAL if running or done). */
 int gbla_server_cancel(gbla_server *srv, int64_t ticket);
 int gbla_server_get_stats(gbla_server *srv, gbla_server_stats *st);
@@ -296,6 +330,11 @@ int gbla_pivots_noalloc(const gbla_csr_in *in_dev, uint32_t p, int64_t *piv_row_
  * row, a coefficient that is 0 mod p, p outside [2, 2^16) or bytes after the
  * last field gives GBLA_E_INVAL and *out zeroed.  Synchronises `stream`. */
 int gbla_decode_format2(const void *file, size_t bytes, void *stream, gbla_csr_out *out, uint32_t *p);
+/* The same; *decode_ms (may be NULL) receives the event-timed duration of the
+ * decode's device work on `stream` after the file's sections are on the
+ * device (host-to-device copies excluded), or -1 on failure. */
+int gbla_decode_format2_ex(const void *file, size_t bytes, void *stream, gbla_csr_out *out, uint32_t *p,
+                           double *decode_ms);
 
 #ifdef __cplusplus
 }

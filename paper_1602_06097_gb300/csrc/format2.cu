@@ -223,6 +223,13 @@ using namespace gbla;
 
 extern "C" int gbla_decode_format2(const void *file, size_t bytes, void *stream, gbla_csr_out *out, uint32_t *p_out)
 {
+    return gbla_decode_format2_ex(file, bytes, stream, out, p_out, nullptr);
+}
+
+extern "C" int gbla_decode_format2_ex(const void *file, size_t bytes, void *stream, gbla_csr_out *out,
+                                      uint32_t *p_out, double *decode_ms)
+{
+    if (decode_ms) *decode_ms = -1.0;
     if (!out) return GBLA_E_INVAL;
     memset(out, 0, sizeof(*out));
     if (!file || !p_out) return GBLA_E_INVAL;
@@ -294,6 +301,13 @@ extern "C" int gbla_decode_format2(const void *file, size_t bytes, void *stream,
     if (k) F2CUDA(cudaMemcpyAsync(colid, f + colid_off, 8 * (size_t)k, cudaMemcpyHostToDevice, s));
     if (pnb) F2CUDA(cudaMemcpyAsync(prow32, f + prow_off, 4 * (size_t)pnb, cudaMemcpyHostToDevice, s));
     if (pnnz) F2CUDA(cudaMemcpyAsync(pdata, f + pdata_off, tsize * (size_t)pnnz, cudaMemcpyHostToDevice, s));
+    // the decode proper (device work after the copies) is event-timed on request
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (decode_ms && rc == GBLA_OK) {
+        F2CUDA(cudaEventCreate(&ev[0]));
+        F2CUDA(cudaEventCreate(&ev[1]));
+        F2CUDA(cudaEventRecord(ev[0], s));
+    }
     // 1. scans of the lengths
     if (m && rc == GBLA_OK) {
         f2_widen_kernel<<<blocks((int64_t)m), 256, 0, s>>>(rows32, row_ptr, (int64_t)m);
@@ -352,8 +366,15 @@ extern "C" int gbla_decode_format2(const void *file, size_t bytes, void *stream,
         default: rc = sgn ? f2_values<int64_t>(R, pdata, p, val, err, s) : f2_values<uint64_t>(R, pdata, p, val, err, s); break;
         }
     }
+    if (ev[1] && rc == GBLA_OK) F2CUDA(cudaEventRecord(ev[1], s));
     F2STEP(readback(&err_h, err, sizeof(uint32_t), s));
     if (rc == GBLA_OK) rc = map_dev_err(err_h);
+    if (ev[1] && rc == GBLA_OK) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) *decode_ms = ms;
+    }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
     dfree(rows32, s);
     dfree(polmap32, s);
     dfree(colid, s);

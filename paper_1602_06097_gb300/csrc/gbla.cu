@@ -483,6 +483,14 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     // FP64 and U8 name the pipe of the Schur update on the dense path; every
     // other product of the reduction runs on the tcgen05 tensor cores.
     const bool alt_schur = variant == GBLA_GEMM_FP64 || variant == GBLA_GEMM_U8;
+    // Order of the FL steps: the new order (Sec. 4.3: X = C A^-1, then
+    // D <- D - X B) or the original one (Sec. 4.1 steps 2-3: B <- A^-1 B
+    // first, then D <- D - C B), which saves the solve with C when the
+    // reduced form needs A^-1 B anyway.  The original order runs on the dense
+    // path.
+    const int order_opt = opt ? opt->fl_order : GBLA_ORDER_NEW;
+    if (order_opt != GBLA_ORDER_NEW && order_opt != GBLA_ORDER_TRSM_FIRST) return GBLA_E_INVAL;
+    const bool trsm_first = order_opt == GBLA_ORDER_TRSM_FIRST;
     const int pvariant = alt_schur ? GBLA_GEMM_TCGEN05 : variant;
     if (leaf_opt != 0 && leaf_opt != 128 && leaf_opt != 256 && leaf_opt != 512 && leaf_opt != 1024)
         return GBLA_E_INVAL;
@@ -503,9 +511,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     // variant.  The dense path materialises A and B (and serves p < 8 and the
     // exact SIMT variant).
     const bool tc_ok = pvariant != GBLA_GEMM_SIMT && p >= 8 && tc_supported();
-    if (path_opt == GBLA_PATH_SPARSE && (!tc_ok || alt_schur)) return GBLA_E_UNSUPPORTED;
+    if (path_opt == GBLA_PATH_SPARSE && (!tc_ok || alt_schur || trsm_first)) return GBLA_E_UNSUPPORTED;
     if (alt_schur && !tc_ok) return GBLA_E_UNSUPPORTED;
-    const bool sparse = tc_ok && path_opt != GBLA_PATH_DENSE && !alt_schur;
+    const bool sparse = tc_ok && path_opt != GBLA_PATH_DENSE && !alt_schur && !trsm_first;
     int tc_leaf_w = 512;
     GemmCounters ctr;
     const long long launches0 = g_launches, pair_launches0 = g_pair_launches;
@@ -525,7 +533,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     uint16_t *d_val = nullptr;
     PivotInfo pi;
     Multiline ml;
-    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{}, XT{};
+    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{}, XT{}, Cp{}, Yb{};
     Compact SA, SB;
     uint16_t *Adiag = nullptr;
     uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
@@ -651,7 +659,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             STEP(upper_leaf_inverses_diag(Adiag, npiv, tc_leaf_w, Zt, mp, err, s));
         }
     }
-    if (!sparse && m_cd > 0 && npiv > 0 && tc_leaves) {
+    if (!sparse && !trsm_first && m_cd > 0 && npiv > 0 && tc_leaves) {
         // inverses of A's diagonal blocks for the tensor-core leaf solves, on
         // the side stream while the main stream converts A and B
         STEP(planes_alloc(&Zt, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
@@ -667,19 +675,19 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         }
     }
     // digit planes of the operands the dense products read
-    if (!sparse && m_cd > 0 && npiv > 0) {
+    if (!sparse && !trsm_first && m_cd > 0 && npiv > 0) {
         // A^T: B-operand of C <- C - X*A.  The triangular solve reads it only
         // below its diagonal blocks (column of A after row of A), so tiles
         // entirely above the diagonal are not converted.
         STEP(planes_alloc(&At, npiv, npiv, 4, s));
         STEP(to_planes(At, npiv, npiv, A16, ldc, 0, true, nullptr, nullptr, mp, s, nullptr, true));
     }
-    if (!sparse && m_cd > 0 && n_d > 0 && npiv > 0) {
+    if (!sparse && !trsm_first && m_cd > 0 && n_d > 0 && npiv > 0) {
         STEP(planes_alloc(&Bt, n_d, npiv, 4, s));    // B^T: B-operand of D <- D - X*B
         STEP(to_planes(Bt, n_d, npiv, B16, ldd, 0, true, nullptr, nullptr, mp, s));
     }
-    if (want_reduced && npiv > 0 && n_d > 0) {
-        STEP(planes_alloc(&Arow, npiv, npiv, 4, s)); // A: B-operand of the second pass
+    if ((want_reduced || trsm_first) && npiv > 0 && n_d > 0) {
+        STEP(planes_alloc(&Arow, npiv, npiv, 4, s)); // A: B-operand of the solve with B
         STEP(to_planes(Arow, npiv, npiv, A16, ldc, 0, false, nullptr, nullptr, mp, s));
         STEP(dalloc_t(&Bt16, (size_t)n_d * (size_t)ldbt, s));
         dim3 grid((unsigned)((n_d + 31) / 32), (unsigned)((npiv + 31) / 32));
@@ -697,7 +705,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     Adiag = nullptr;
     // the 2-multiline form of A drives the sparse leaf solves: those of the
     // first pass unless they run on the tensor cores, those of the second
-    if ((!sparse && !tc_leaves) || want_reduced) STEP(multiline_build(dc, pi, &ml, mp, s));
+    if ((!sparse && !tc_leaves) || want_reduced || trsm_first) STEP(multiline_build(dc, pi, &ml, mp, s));
     tm.mark(s);  // 1
 
     // ---- new order: X = C A^-1, then D <- D - X B
@@ -712,6 +720,16 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         TrsmSparse T{m_cd, npiv, C16, ldc, &SA, &Zt, &Ct, &XT, tc_leaf_w, &mp, err, s, &ctr, pi.cd_lead, &lead_h};
         NvtxRange r("gbla.trsm");
         STEP(trsm_sparse(T));
+    } else if (trsm_first) {
+        // original order: Y = A^-1 B as the lower solve Y^T A^T = B^T (in place
+        // in Bt16), before the Schur update
+        if (npiv > 0 && n_d > 0) {
+            STEP(planes_alloc(&Xq, n_d, npiv, 2, s));
+            STEP(planes_zero(Xq, s));
+            TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr};
+            NvtxRange r("gbla.trsm");
+            STEP(trsm_lower(T));
+        }
     } else if (m_cd > 0 && npiv > 0) {
         STEP(planes_alloc(&Xp, m_cd, npiv, 2, s));
         STEP(planes_zero(Xp, s));
@@ -731,6 +749,20 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             CSTEP(cudaMemsetAsync(exec_ctr, 0, sizeof(unsigned long long), s));
         }
         STEP(modgemm_gather(SB, 0, XT, npiv, D16, ldd, m_cd, n_d, -1, pi.cd_lead, mp, err, s, &ctr, exec_ctr));
+    } else if (trsm_first && m_cd > 0 && npiv > 0 && n_d > 0) {
+        // D <- D - C Y: C's rows are zero left of their leads like X's
+        NvtxRange r("gbla.schur");
+        lead_h.resize((size_t)m_cd);
+        STEP(readback(lead_h.data(), pi.cd_lead, sizeof(int32_t) * (size_t)m_cd, s));
+        STEP(planes_alloc(&Cp, m_cd, npiv, 2, s));
+        STEP(to_planes(Cp, m_cd, npiv, C16, ldc, 0, false, nullptr, nullptr, mp, s));
+        STEP(planes_alloc(&Yb, n_d, npiv, 4, s));
+        STEP(to_planes(Yb, n_d, npiv, Bt16, ldbt, 0, false, nullptr, nullptr, mp, s));
+        STEP(modgemm(Cp, 0, 0, Yb, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr, nullptr,
+                     pi.cd_lead, lead_h.data()));
+        schur_ops = ctr.last_ops;
+        planes_free(&Cp, s);
+        planes_free(&Yb, s);
     } else if (m_cd > 0 && npiv > 0 && n_d > 0) {
         NvtxRange r("gbla.schur");
         STEP(modgemm(Xp, 0, 0, Bt, 0, 0, D16, ldd, m_cd, n_d, npiv, -1, mp, variant, err, s, &ctr, nullptr,
@@ -753,10 +785,12 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
 
     // ---- second FL pass: Y = A^-1 B, then clear the columns P_D of Y
     if (want_reduced && npiv > 0 && n_d > 0) {
-        STEP(planes_alloc(&Xq, n_d, npiv, 2, s));
-        STEP(planes_zero(Xq, s));
-        TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr};
-        STEP(trsm_lower(T));
+        if (!trsm_first) {
+            STEP(planes_alloc(&Xq, n_d, npiv, 2, s));
+            STEP(planes_zero(Xq, s));
+            TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr};
+            STEP(trsm_lower(T));
+        }
         if (rank_d > 0) {
             // Y^T[c][j] -= sum_k RREF(D')[k][c] * Y^T[P_D[k]][j]
             STEP(planes_alloc(&RdT, n_d, rank_d, 2, s));
@@ -939,6 +973,8 @@ cleanup:
     planes_free(&RdT, s);
     planes_free(&XpdT, s);
     planes_free(&XT, s);
+    planes_free(&Cp, s);
+    planes_free(&Yb, s);
     compact_free(&SA, s);
     compact_free(&SB, s);
     dfree(Adiag, s);

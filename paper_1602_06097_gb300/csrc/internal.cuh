@@ -85,7 +85,7 @@ void compact_free(Compact *c, cudaStream_t s);
 // read from the A-operand plane set XT of its transpose (row j = column j of
 // X, K = r; rows xt_rows and beyond read as zero).  With row_lead (device,
 // ascending absolute lead of each row of X) a row tile skips the list entries
-// left of its raster group's first lead.  Tensor-core variant only (p >= 8).
+// left of its first row's lead.  Tensor-core variant only (p >= 8).
 // With exec (device, optional), adds the list entries times row tiles the
 // launch runs through (executed multiply-adds = exec * 128 * 128).
 int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_rows, uint16_t *C, int64_t ldc,

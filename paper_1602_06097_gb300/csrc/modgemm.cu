@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // every listed j into shared memory in the MN-major 128-byte-swizzled layout
 // (cp.async), while one thread loads the compacted S chunk by TMA.  Rows of X
 // are ascending by lead (first nonzero column), so a tile skips the list
-// entries left of its raster group's first lead.
+// entries left of its first row's lead.
 // Warp roles: 0 TMA producer of the compacted operand, 1 MMA issuer, 2..5
 // drain (one per TMEM lane quarter, all 128 columns), 6..9 gather (warp
 // 6 + s fills ring slot s).
@@ -923,7 +923,7 @@ struct GArgs {
     const __nv_bfloat16 *xt; // XT plane set (2 planes, rows = j, K = r)
     int64_t xt_row_elems;    // elements per XT row
     int64_t xt_rows;         // list entries >= xt_rows (padding) read as zero
-    const int32_t *kstart;   // [raster groups x output tiles]: first list entry of the tile's
+    const int32_t *kstart;   // [row tiles x output tiles]: first list entry of the tile's
                              // K range (0 without row leads), from gather_starts_kernel
     uint16_t *C;
     int64_t ldc;
@@ -934,25 +934,23 @@ struct GArgs {
     int group_m;
 };
 
-// First list entry at or after the raster group's first lead, for every
-// (raster group, output tile): all tiles of a group walk K from there (X is
-// zero left of a row's lead, rows ascending by lead), so that concurrent CTAs
-// share operand tiles in L2.  One thread per entry, a binary search.
-// With exec (optional), also adds the list entries the launch runs through
-// (from each tile's rounded start to the list end, times the raster group's
-// row tiles): the executed product is exec * 128 * 128 multiply-adds.
-__global__ void gather_starts_kernel(int64_t ngroups, int64_t num_n, int64_t num_m, int64_t nt0, int group_m,
-                                     const int64_t *__restrict__ koff, const int32_t *__restrict__ kidx,
-                                     const int32_t *__restrict__ row_lead, int32_t *__restrict__ kstart,
-                                     unsigned long long *exec)
+// First list entry at or after the first lead of the row tile, for every
+// (row tile, output tile): the tile walks K from there (X is zero left of a
+// row's lead, rows ascending by lead).  One thread per entry, a binary
+// search.  With exec (optional), also adds the list entries the launch runs
+// through (from each tile's rounded start to the list end): the executed
+// product is exec * 128 * 128 multiply-adds.
+__global__ void gather_starts_kernel(int64_t num_m, int64_t num_n, int64_t nt0, const int64_t *__restrict__ koff,
+                                     const int32_t *__restrict__ kidx, const int32_t *__restrict__ row_lead,
+                                     int32_t *__restrict__ kstart, unsigned long long *exec)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ngroups * num_n) return;
-    const int64_t grp = i / num_n, nt = i % num_n;
+    if (i >= num_m * num_n) return;
+    const int64_t mt = i / num_n, nt = i % num_n;
     const int64_t kb = koff[nt0 + nt], ke = koff[nt0 + nt + 1];
     int64_t lo = kb, hi = ke;
     if (row_lead) {
-        const int32_t L = row_lead[grp * group_m * BM];
+        const int32_t L = row_lead[mt * BM];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
             if (kidx[mid] < L) lo = mid + 1;
@@ -962,8 +960,7 @@ __global__ void gather_starts_kernel(int64_t ngroups, int64_t num_n, int64_t num
     kstart[i] = (int32_t)(lo - kb);
     if (exec) {
         const int64_t s = ((lo - kb) / BK & ~(int64_t)(STAGES - 1)) * BK;   // as gtile rounds it
-        const int64_t rows = min((int64_t)group_m, num_m - grp * group_m);
-        atomicAdd(exec, (unsigned long long)((ke - kb - s) * rows));
+        atomicAdd(exec, (unsigned long long)(ke - kb - s));
     }
 }
 
@@ -978,7 +975,7 @@ __device__ __forceinline__ GTile gtile(const GArgs &g, int64_t t, int64_t num_m,
     const int64_t kb = g.koff[g.nt0 + ti.nt], ke = g.koff[g.nt0 + ti.nt + 1];
     ti.chunk0 = kb / BK;
     ti.ksteps = (int)((ke - kb) / BK);
-    const int64_t s = g.kstart ? (int64_t)g.kstart[(ti.mt / g.group_m) * num_n + ti.nt] : 0;
+    const int64_t s = g.kstart ? (int64_t)g.kstart[ti.mt * num_n + ti.nt] : 0;
     ti.ks0 = (int)(s / BK) & ~(STAGES - 1);   // whole rounds of the stage ring
     return ti;
 }
@@ -1624,10 +1621,11 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
     const int64_t num_m = (M + tc::BM - 1) / tc::BM, num_n = (N + tc::BN - 1) / tc::BN;
     int32_t *kstart = nullptr;
     if (row_lead || exec) {
-        const int64_t ngroups = (num_m + g.group_m - 1) / g.group_m;
-        GBLA_TRY(dalloc_t(&kstart, (size_t)(ngroups * num_n), s));
-        tc::gather_starts_kernel<<<(unsigned)((ngroups * num_n + 255) / 256), 256, 0, s>>>(
-            ngroups, num_n, num_m, nt0, g.group_m, S.koff, S.kidx, row_lead, kstart, exec);
+        // first list entry of every (row tile, column tile) at or after the
+        // row tile's first lead
+        GBLA_TRY(dalloc_t(&kstart, (size_t)(num_m * num_n), s));
+        tc::gather_starts_kernel<<<(unsigned)((num_m * num_n + 255) / 256), 256, 0, s>>>(
+            num_m, num_n, nt0, S.koff, S.kidx, row_lead, kstart, exec);
         if (launch_check() != cudaSuccess) {
             dfree(kstart, s);
             return GBLA_E_CUDA;

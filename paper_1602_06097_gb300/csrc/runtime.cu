@@ -196,7 +196,9 @@ struct gbla_server {
         gbla_csr_out out{};
         int64_t rank = 0;
         int code = GBLA_OK;
-        std::chrono::steady_clock::time_point t_submit, t_done;
+        std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+        double dev_t0 = -1.0, dev_t1 = -1.0;   // device timeline (ms since ref)
+        int64_t running_at_start = 0;
     };
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -206,6 +208,8 @@ struct gbla_server {
     std::vector<double> latencies_ms;
     size_t budget = 0, in_use = 0;
     int running = 0;
+    int64_t peak_running = 0;
+    cudaEvent_t ref = nullptr;   // device time origin of the request timelines
     int64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0, cancelled = 0;
     bool stop = false;
     int dev = 0;
@@ -222,7 +226,7 @@ struct gbla_server {
     static size_t estimate(const gbla_csr_in &in, uint32_t p, const gbla_options &opt) {
         const double m = (double)in.nrows, n = (double)in.ncols;
         const double k = std::min(m, n);
-        const bool sparse = opt.path != GBLA_PATH_DENSE && p >= 8 &&
+        const bool sparse = opt.path != GBLA_PATH_DENSE && p >= 8 && opt.fl_order == GBLA_ORDER_NEW &&
                             (opt.gemm_variant == GBLA_GEMM_AUTO || opt.gemm_variant == GBLA_GEMM_TCGEN05);
         const double work = sparse ? 6.0 * m * k + 24.0 * (double)in.nnz + 12.0 * m * n
                                    : 12.0 * k * n + 6.0 * m * n;
@@ -239,6 +243,20 @@ struct gbla_server {
         } release_at_exit;   // runs after the stream below is destroyed
         StreamGuard sg;
         const int rc0 = sg.create(dev);
+        // events around each reduction on this worker's stream (timeline only)
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (rc0 == GBLA_OK && ref && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess)) {
+            cudaGetLastError();
+            if (ev0) cudaEventDestroy(ev0);
+            ev0 = ev1 = nullptr;
+        }
+        struct DestroyEvents {
+            cudaEvent_t &a, &b;
+            ~DestroyEvents() {
+                if (a) cudaEventDestroy(a);
+                if (b) cudaEventDestroy(b);
+            }
+        } destroy_events{ev0, ev1};
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
             cv_work.wait(lk, [&] { return stop || (!queue.empty() && admissible(queue.front())); });
@@ -249,11 +267,22 @@ struct gbla_server {
             r->state = Request::RUNNING;
             in_use += r->est_bytes;
             ++running;
+            if (running > peak_running) peak_running = running;
+            r->running_at_start = running;
+            r->t_start = std::chrono::steady_clock::now();
             lk.unlock();
             int64_t rank = 0;
             gbla_csr_out out{};
+            const bool timeline = ev0 && cudaEventRecord(ev0, sg.s) == cudaSuccess;
             const int code = rc0 != GBLA_OK ? rc0 : reduce_impl(&r->in, r->p, &r->opt, sg.s, &out, &rank, nullptr);
+            float t0 = -1.f, t1 = -1.f;
+            if (timeline && cudaEventRecord(ev1, sg.s) == cudaSuccess && cudaEventSynchronize(ev1) == cudaSuccess &&
+                (cudaEventElapsedTime(&t0, ref, ev0) != cudaSuccess || cudaEventElapsedTime(&t1, ref, ev1) != cudaSuccess))
+                t0 = t1 = -1.f;
+            if (!timeline || t1 < 0.f) cudaGetLastError();
             lk.lock();
+            r->dev_t0 = t0;
+            r->dev_t1 = t1;
             r->out = out;
             r->rank = rank;
             r->code = code;
@@ -294,6 +323,19 @@ int gbla_server_create(size_t mem_budget, int workers, gbla_server **out) {
         mem_budget = free_b / 10 * 8;
     }
     s->budget = mem_budget;
+    {
+        // reference event of the request timelines, recorded and completed here
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&s->ref) == cudaSuccess && cudaEventRecord(s->ref, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess) {
+        } else {
+            if (s->ref) cudaEventDestroy(s->ref);
+            s->ref = nullptr;
+            cudaGetLastError();
+        }
+        if (st) cudaStreamDestroy(st);
+    }
     const int nw = default_workers(workers);
     for (int w = 0; w < nw; ++w) s->workers.emplace_back([s] { s->worker_main(); });
     *out = s;
@@ -338,6 +380,14 @@ int gbla_server_submit(gbla_server *s, const gbla_csr_in *in, uint32_t p, const 
 
 int gbla_server_wait(gbla_server *s, int64_t ticket, double timeout_s, gbla_csr_out *out, int64_t *rank,
                      double *latency_ms) {
+    gbla_request_info info;
+    const int code = gbla_server_wait_ex(s, ticket, timeout_s, out, rank, latency_ms ? &info : nullptr);
+    if (latency_ms && code != GBLA_E_TIMEOUT && code != GBLA_E_INVAL) *latency_ms = info.latency_ms;
+    return code;
+}
+
+int gbla_server_wait_ex(gbla_server *s, int64_t ticket, double timeout_s, gbla_csr_out *out, int64_t *rank,
+                        gbla_request_info *info) {
     if (!s || !out || !rank) return GBLA_E_INVAL;
     memset(out, 0, sizeof(*out));
     std::unique_lock<std::mutex> lk(s->mu);
@@ -356,11 +406,32 @@ int gbla_server_wait(gbla_server *s, int64_t ticket, double timeout_s, gbla_csr_
     if (r->state == gbla_server::Request::CANCELLED) code = GBLA_E_CANCELLED;
     *out = r->out;
     *rank = r->rank;
-    if (latency_ms)
-        *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    if (info) {
+        using ms = std::chrono::duration<double, std::milli>;
+        info->latency_ms = ms(r->t_done - r->t_submit).count();
+        const bool started = r->running_at_start > 0;
+        info->queue_ms = started ? ms(r->t_start - r->t_submit).count() : info->latency_ms;
+        info->device_start_ms = r->dev_t0;
+        info->device_end_ms = r->dev_t1;
+        info->running_at_start = r->running_at_start;
+    }
     s->reqs.erase(it);
     delete r;
     return code;
+}
+
+int gbla_server_poll(gbla_server *s, int64_t ticket, int *state) {
+    if (!s || !state) return GBLA_E_INVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return GBLA_E_INVAL;
+    switch (it->second->state) {
+    case gbla_server::Request::QUEUED: *state = GBLA_REQ_QUEUED; break;
+    case gbla_server::Request::RUNNING: *state = GBLA_REQ_RUNNING; break;
+    case gbla_server::Request::DONE: *state = GBLA_REQ_DONE; break;
+    default: *state = GBLA_REQ_CANCELLED; break;
+    }
+    return GBLA_OK;
 }
 
 int gbla_server_cancel(gbla_server *s, int64_t ticket) {
@@ -390,6 +461,7 @@ int gbla_server_get_stats(gbla_server *s, gbla_server_stats *st) {
     st->running = s->running;
     st->mem_budget = s->budget;
     st->mem_in_use = s->in_use;
+    st->peak_running = s->peak_running;
     if (!s->latencies_ms.empty()) {
         std::vector<double> v = s->latencies_ms;
         std::sort(v.begin(), v.end());
@@ -425,6 +497,7 @@ void gbla_server_destroy(gbla_server *s) {
         gbla_free(&kv.second->out);
         delete kv.second;
     }
+    if (s->ref) cudaEventDestroy(s->ref);
     delete s;
 }
 

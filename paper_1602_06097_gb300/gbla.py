@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(_HERE, "libgbla.so")
 GBLA_OK = 0
 GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT, GEMM_FP64, GEMM_U8 = 0, 1, 2, 3, 4
 PATH_AUTO, PATH_DENSE, PATH_SPARSE = 0, 1, 2
+ORDER_NEW, ORDER_TRSM_FIRST = 0, 1
 
 EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
            "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc",
            "gbla_selftest_wait_timeout", "gbla_reduce_batch", "gbla_server_create", "gbla_server_submit",
-           "gbla_server_wait", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy",
-           "gbla_decode_format2", "gbla_spmm", "gbla_pipe_peak"]
+           "gbla_server_wait", "gbla_server_wait_ex", "gbla_server_poll", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy",
+           "gbla_decode_format2", "gbla_decode_format2_ex", "gbla_spmm", "gbla_pipe_peak"]
 
 
 class CsrIn(ctypes.Structure):
@@ -40,12 +41,13 @@ class CsrOut(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("want_reduced", ctypes.c_int), ("gemm_variant", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("panel_width", ctypes.c_int),
-                ("path", ctypes.c_int), ("leaf_width", ctypes.c_int), ("kernel_times", ctypes.c_int)]
+                ("path", ctypes.c_int), ("leaf_width", ctypes.c_int), ("kernel_times", ctypes.c_int),
+                ("fl_order", ctypes.c_int)]
 
 
-def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0, kernel_times=False):
+def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0, kernel_times=False, order=0):
     return Options(1 if want_reduced else 0, int(variant), int(device_ptrs), 0, int(path), int(leaf),
-                   1 if kernel_times else 0)
+                   1 if kernel_times else 0, int(order))
 
 
 class Stats(ctypes.Structure):
@@ -69,10 +71,22 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("cancelled", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("mem_budget", ctypes.c_size_t), ("mem_in_use", ctypes.c_size_t)]
+                ("mem_budget", ctypes.c_size_t), ("mem_in_use", ctypes.c_size_t), ("peak_running", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("device_start_ms", ctypes.c_double), ("device_end_ms", ctypes.c_double),
+                ("running_at_start", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED = 0, 1, 2, 3
 
 
 GBLA_E_TIMEOUT, GBLA_E_CANCELLED = 4, 7
@@ -134,6 +148,11 @@ def load():
         lib.gbla_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(CsrOut), ctypes.POINTER(i64),
                                          ctypes.POINTER(ctypes.c_double)]
         lib.gbla_server_wait.restype = i32
+        lib.gbla_server_wait_ex.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(CsrOut), ctypes.POINTER(i64),
+                                            ctypes.POINTER(RequestInfo)]
+        lib.gbla_server_wait_ex.restype = i32
+        lib.gbla_server_poll.argtypes = [vp, i64, ctypes.POINTER(i32)]
+        lib.gbla_server_poll.restype = i32
         lib.gbla_server_cancel.argtypes = [vp, i64]
         lib.gbla_server_cancel.restype = i32
         lib.gbla_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
@@ -143,6 +162,9 @@ def load():
         lib.gbla_decode_format2.argtypes = [ctypes.c_char_p, ctypes.c_size_t, vp, ctypes.POINTER(CsrOut),
                                             ctypes.POINTER(u32)]
         lib.gbla_decode_format2.restype = i32
+        lib.gbla_decode_format2_ex.argtypes = [vp, ctypes.c_size_t, vp, ctypes.POINTER(CsrOut),
+                                               ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]
+        lib.gbla_decode_format2_ex.restype = i32
         _lib = lib
         return lib
 
@@ -197,7 +219,7 @@ class HostResult:
 
 
 def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
-                path=PATH_AUTO, leaf=0) -> HostResult:
+                path=PATH_AUTO, leaf=0, order=ORDER_NEW) -> HostResult:
     """Reduce a host CSR matrix; the result stays in library-owned host memory
     (see HostResult).  Page-locked inputs copy to the device fastest.
     ``path`` is PATH_AUTO, PATH_DENSE or PATH_SPARSE, ``leaf`` the leaf width
@@ -208,7 +230,7 @@ def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AU
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.uint16)
     cin = CsrIn(m, n, int(len(col)), row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data)
-    opt = _options(want_reduced, variant, 0, path, leaf)
+    opt = _options(want_reduced, variant, 0, path, leaf, order=order)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
@@ -219,11 +241,11 @@ def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AU
 
 
 def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None,
-           path=PATH_AUTO, leaf=0):
+           path=PATH_AUTO, leaf=0, order=ORDER_NEW):
     """Reduce a host CSR matrix.  Returns (rank, row_ptr, col, val) as numpy
     arrays the caller owns (and a stats dict when ``stats``)."""
     h = reduce_host(row_ptr, col, val, shape, p, want_reduced=want_reduced, variant=variant, stream=stream,
-                    path=path, leaf=leaf)
+                    path=path, leaf=leaf, order=order)
     try:
         res = (h.rank, h.row_ptr.copy(), h.col.copy(), h.val.copy())
         st = h.stats
@@ -278,16 +300,29 @@ class DecodedMatrix(DeviceResult):
         self.m, self.n, self.p = int(out.nrows), int(out.ncols), int(p)
 
 
-def decode_format2(buf, stream=None) -> DecodedMatrix:
-    """Decode a Format 2 matrix file (bytes, Sec. 3.2 of the paper) on the
-    device; raises GblaError (GBLA_E_INVAL) on a malformed file."""
+def decode_format2(buf, stream=None, timed=False) -> DecodedMatrix:
+    """Decode a Format 2 matrix file (bytes, or a contiguous uint8 numpy
+    array such as a page-locked buffer; Sec. 3.2 of the paper) on the
+    device; raises GblaError (GBLA_E_INVAL) on a malformed file.  With
+    timed=True the result's ``decode_ms`` is the event-timed device work of
+    the decode (host-to-device copies excluded)."""
     lib = load()
-    data = bytes(buf)
+    if isinstance(buf, np.ndarray):
+        assert buf.dtype == np.uint8 and buf.flags["C_CONTIGUOUS"]
+        keep, ptr, nbytes = buf, ctypes.c_void_p(buf.ctypes.data), buf.nbytes
+    else:
+        keep = bytes(buf)
+        ptr, nbytes = ctypes.cast(ctypes.c_char_p(keep), ctypes.c_void_p), len(keep)
     out = CsrOut()
     p = ctypes.c_uint32(0)
-    rc = lib.gbla_decode_format2(data, len(data), _stream_ptr(stream), ctypes.byref(out), ctypes.byref(p))
+    ms = ctypes.c_double(-1.0)
+    rc = lib.gbla_decode_format2_ex(ptr, nbytes, _stream_ptr(stream), ctypes.byref(out), ctypes.byref(p),
+                                    ctypes.byref(ms) if timed else None)
+    del keep
     _check(rc, "gbla_decode_format2")
-    return DecodedMatrix(out, p.value)
+    d = DecodedMatrix(out, p.value)
+    d.decode_ms = float(ms.value) if timed else None
+    return d
 
 
 class _CudaArray:
@@ -299,14 +334,14 @@ class _CudaArray:
 
 
 def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
-                  path=PATH_AUTO, leaf=0, kernel_times=False):
+                  path=PATH_AUTO, leaf=0, kernel_times=False, order=ORDER_NEW):
     """Reduce a CSR matrix already on the device (torch CUDA tensors: int64
     row_ptr, int32 col, int16/uint16 val).  Returns a DeviceResult whose
     arrays stay in device memory."""
     lib = load()
     m, n = int(shape[0]), int(shape[1])
     cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
-    opt = _options(want_reduced, variant, 1, path, leaf, kernel_times)
+    opt = _options(want_reduced, variant, 1, path, leaf, kernel_times, order)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
@@ -426,6 +461,26 @@ class Server:
             return rc, (int(rank.value),) + _host_result(self._lib, out), float(lat.value)
         self._lib.gbla_free(ctypes.byref(out))
         return rc, None, float(lat.value)
+
+    def wait_ex(self, ticket, timeout=-1.0):
+        """Returns (code, result or None, timeline dict: latency_ms, queue_ms,
+        device_start_ms, device_end_ms, running_at_start)."""
+        out = CsrOut()
+        rank = ctypes.c_int64(0)
+        info = RequestInfo()
+        rc = self._lib.gbla_server_wait_ex(self._h, int(ticket), float(timeout), ctypes.byref(out),
+                                           ctypes.byref(rank), ctypes.byref(info))
+        if rc == GBLA_OK:
+            return rc, (int(rank.value),) + _host_result(self._lib, out), info.as_dict()
+        self._lib.gbla_free(ctypes.byref(out))
+        return rc, None, info.as_dict()
+
+    def poll(self, ticket):
+        """REQ_QUEUED, REQ_RUNNING, REQ_DONE or REQ_CANCELLED (raises for an
+        unknown or consumed ticket)."""
+        st = ctypes.c_int(-1)
+        _check(self._lib.gbla_server_poll(self._h, int(ticket), ctypes.byref(st)), "gbla_server_poll")
+        return int(st.value)
 
     def cancel(self, ticket):
         return int(self._lib.gbla_server_cancel(self._h, int(ticket)))

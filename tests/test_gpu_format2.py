@@ -2,9 +2,7 @@
 and the decoded matrix through the reduction.
 
 The decoder's parallel algorithm is also checked on the CPU
-(test_format2_parallel_model.py).  The cases marked "not yet run on a GPU"
-(32-bit unsigned and 64-bit signed coefficients, a decoded matrix reduced in
-place) stay skipped until a GB300 run has passed them.
+(test_format2_parallel_model.py).
 """
 import numpy as np
 import pytest
@@ -18,8 +16,6 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
-
-NOT_YET = pytest.mark.skip(reason="not yet run on a GPU")
 
 
 def decoded(buf):
@@ -37,9 +33,10 @@ def same(a, b):
         assert np.array_equal(np.asarray(x, np.int64), np.asarray(y, np.int64))
 
 
-@pytest.mark.parametrize("vtype", [None, "i2", pytest.param("u4", marks=NOT_YET), pytest.param("i8", marks=NOT_YET)])
-def test_decoder_equals_oracle_reader(vtype):
-    spec = synth.workload("fl_2000x3000")
+@pytest.mark.parametrize("vtype,p", [(None, 65521), ("u1", 251), ("i1", 251), ("i2", 65521), ("u4", 65521),
+                                     ("i4", 32003), ("u8", 65521), ("i8", 65521)])
+def test_decoder_equals_oracle_reader(vtype, p):
+    spec = synth.workload("fl_2000x3000", p=p)
     rp, c, v = synth.fl_matrix(spec)
     buf = synth.encode_format2(spec.m, spec.n, spec.p, rp, c, v, vtype)
     same(decoded(buf), F.decode_format2(buf))
@@ -66,11 +63,11 @@ def test_decoder_rejects_malformed_files():
             gbla.decode_format2(buf)
 
 
-@NOT_YET
-def test_decoded_matrix_reduces_like_the_file():
+@pytest.mark.parametrize("vtype", [None, "i8"])
+def test_decoded_matrix_reduces_like_the_file(vtype):
     spec = synth.workload("fl_2000x3000")
     rp, c, v = synth.fl_matrix(spec)
-    d = gbla.decode_format2(synth.encode_format2(spec.m, spec.n, spec.p, rp, c, v))
+    d = gbla.decode_format2(synth.encode_format2(spec.m, spec.n, spec.p, rp, c, v, vtype))
     try:
         trp, tc, tv = d.tensors()
         res = gbla.reduce_device(trp, tc, tv, (d.m, d.n), d.p, want_reduced=True)
@@ -82,3 +79,19 @@ def test_decoded_matrix_reduces_like_the_file():
         d.free()
     want = oracle.rref(spec.m, spec.n, spec.p, rp, c, v)
     same((0, 0, 0) + tuple(got), (0, 0, 0) + tuple(want[:4]))
+
+
+def test_timed_decode_from_a_page_locked_buffer():
+    """The timed entry point from a numpy (page-locked) buffer decodes the
+    same matrix and reports a positive device time."""
+    spec = synth.scaled("fl_40000x60000", 0.3)
+    rp, c, v = synth.fl_matrix(spec)
+    buf = synth.encode_format2(spec.m, spec.n, spec.p, rp, c, v)
+    pinned = torch.frombuffer(bytearray(buf), dtype=torch.uint8).pin_memory().numpy()
+    d = gbla.decode_format2(pinned, timed=True)
+    try:
+        assert d.decode_ms is not None and d.decode_ms > 0
+        m, drp, dc, dv = d.to_host()
+    finally:
+        d.free()
+    same((m, 0, 0, drp, dc, dv), (spec.m, 0, 0, rp, c, v))

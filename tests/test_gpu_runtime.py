@@ -132,3 +132,62 @@ def test_server_create_destroy_cycles():
                 code, res, _ = srv.wait(t, timeout=120.0)
                 assert code == 0
                 same(res, ref)
+
+
+BATCH_MIX_SEED = 20160223   # the benchmark's 256-matrix batch
+
+
+def test_batch_mix_of_the_benchmark_members_equal_oracle():
+    """The benchmark's 256-matrix batch (rows log-uniform in 500-20,000, p in
+    {65521, 32003}) through both batch entry points: every member up to 5,000
+    rows equals the oracle bit for bit, every larger one the solo reduction;
+    device-resident and host results agree."""
+    specs = synth.mixed_batch(256, BATCH_MIX_SEED)
+    mats = [synth.fl_matrix(s) + ((s.m, s.n), s.p) for s in specs]
+    host = gbla.reduce_batch(mats, workers=8)
+    dev_in = [(torch.from_numpy(rp).cuda(), torch.from_numpy(c).cuda(), torch.from_numpy(v.view(np.int16)).cuda(),
+               shape, p) for rp, c, v, shape, p in mats]
+    dev = gbla.reduce_batch_device(dev_in, workers=8)
+    checked = 0
+    for s, mt, h, d in zip(specs, mats, host, dev):
+        rp, c, v, shape, p = mt
+        rank, orp, oc, ov = d.to_host()
+        d.free()
+        same(h, (rank, orp, oc, ov))
+        if s.m <= 5000:
+            same(h, oracle.echelon(s.m, s.n, s.p, rp, c, v)[:4])
+            checked += 1
+        else:
+            same(h, gbla.reduce(rp, c, v, shape, p))
+    assert checked >= 100
+
+
+def test_served_requests_overlap_and_equal_solo_and_oracle():
+    """Requests submitted together run concurrently (the server admits
+    several at once and their device intervals, from events on the workers'
+    streams, intersect) and each result equals the solo reduction and the
+    oracle."""
+    specs = mixed_specs(24, 11) + synth.mixed_batch(8, 77, rows=(3000, 6000))
+    mats = [synth.fl_matrix(s) + ((s.m, s.n), s.p) for s in specs]
+    solo = [gbla.reduce(rp, c, v, shape, p) for rp, c, v, shape, p in mats]
+    with gbla.Server(workers=8) as srv:
+        tickets = [srv.submit(rp, c, v, shape, p) for rp, c, v, shape, p in mats]
+        infos = []
+        for t, ref in zip(tickets, solo):
+            code, res, info = srv.wait_ex(t, timeout=120.0)
+            assert code == 0
+            same(res, ref)
+            infos.append(info)
+        st = srv.stats()
+    for s, mt, ref in zip(specs, mats, solo):
+        rp, c, v, shape, p = mt
+        same(ref, oracle.echelon(s.m, s.n, s.p, rp, c, v)[:4])
+    assert st["peak_running"] >= 2
+    iv = sorted((i["device_start_ms"], i["device_end_ms"]) for i in infos)
+    assert all(a >= 0 and b >= a for a, b in iv)
+    overlapping = sum(1 for (a0, b0), (a1, b1) in zip(iv, iv[1:]) if a1 < b0)
+    assert overlapping >= 1, iv
+    busy = sum(b - a for a, b in iv)
+    span = max(b for _, b in iv) - iv[0][0]
+    assert busy > span, (busy, span)   # more device time in flight than wall time: overlap
+    assert max(i["running_at_start"] for i in infos) >= 2

@@ -56,16 +56,39 @@ const int cudaSuccess = 0, cudaStreamNonBlocking = 1;
 #define GBLA_E_CANCELLED 7
 struct gbla_csr_in { int64_t nrows, ncols, nnz; const int64_t *row_ptr; const int32_t *col; const uint16_t *val; };
 struct gbla_csr_out { int64_t nrows, ncols, nnz; int64_t *row_ptr; int32_t *col; uint16_t *val; int on_device; };
-struct gbla_options { int want_reduced, gemm_variant, device_ptrs, panel_width, path, leaf_width, kernel_times; };
+struct gbla_options { int want_reduced, gemm_variant, device_ptrs, panel_width, path, leaf_width, kernel_times, fl_order; };
 #define GBLA_GEMM_AUTO 0
 #define GBLA_GEMM_TCGEN05 1
 #define GBLA_GEMM_SIMT 2
 #define GBLA_PATH_DENSE 1
+#define GBLA_ORDER_NEW 0
 typedef struct {
     int64_t submitted, completed, failed, cancelled, queued, running;
     double p50_ms, p99_ms, mean_ms;
     size_t mem_budget, mem_in_use;
+    int64_t peak_running;
 } gbla_server_stats;
+typedef struct {
+    double latency_ms, queue_ms, device_start_ms, device_end_ms;
+    int64_t running_at_start;
+} gbla_request_info;
+#define GBLA_REQ_QUEUED 0
+#define GBLA_REQ_RUNNING 1
+#define GBLA_REQ_DONE 2
+#define GBLA_REQ_CANCELLED 3
+struct gbla_server;
+extern "C" int gbla_server_wait_ex(gbla_server *, int64_t, double, gbla_csr_out *, int64_t *, gbla_request_info *);
+// events: a host timestamp taken at record time
+typedef void *cudaEvent_t;
+int cudaEventCreate(cudaEvent_t *e) { *e = new double(0.0); return 0; }
+int cudaEventDestroy(cudaEvent_t e) { delete (double *)e; return 0; }
+int cudaEventRecord(cudaEvent_t e, cudaStream_t) {
+    *(double *)e = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    return 0;
+}
+int cudaEventSynchronize(cudaEvent_t) { return 0; }
+int cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) { *ms = (float)(*(double *)b - *(double *)a); return 0; }
+int cudaStreamSynchronize(cudaStream_t) { return 0; }
 int cudaSetDevice(int) { return 0; }
 int cudaGetDevice(int *d) { *d = 0; return 0; }
 std::atomic<int> g_streams{0};
@@ -141,6 +164,7 @@ int main() {
         }
         const gbla_server_stats st = stats(s);
         CHECK(st.submitted == 50 && st.completed == 50 && st.failed == 0 && st.cancelled == 0);
+        CHECK(st.peak_running >= 2 && st.peak_running <= 4);
         CHECK(st.queued == 0 && st.running == 0 && st.mem_in_use == 0);
         CHECK(st.p50_ms > 0 && st.p50_ms <= st.p99_ms);
         gbla_server_destroy(s);
@@ -171,12 +195,26 @@ int main() {
         const int64_t t1 = submit(s, small), t2 = submit(s, small);
         for (int i = 0; i < 2000 && stats(s).running == 0; ++i) std::this_thread::sleep_for(std::chrono::milliseconds(1));
         CHECK(stats(s).running == 1);
+        int state = -1;
+        CHECK(gbla_server_poll(s, t0, &state) == GBLA_OK && state == GBLA_REQ_RUNNING);
+        CHECK(gbla_server_poll(s, t1, &state) == GBLA_OK && state == GBLA_REQ_QUEUED);
         CHECK(gbla_server_cancel(s, t0) == GBLA_E_INVAL);        // running
         CHECK(gbla_server_cancel(s, t2) == GBLA_OK);             // queued
+        CHECK(gbla_server_poll(s, t2, &state) == GBLA_OK && state == GBLA_REQ_CANCELLED);
         gbla_csr_out o;
         int64_t rank;
         CHECK(gbla_server_wait(s, t0, 0.001, &o, &rank, nullptr) == GBLA_E_TIMEOUT);
-        CHECK(gbla_server_wait(s, t0, -1.0, &o, &rank, nullptr) == GBLA_OK && rank == 1000 * 7 + 65521);
+        gbla_request_info info;
+        CHECK(gbla_server_wait_ex(s, t0, -1.0, &o, &rank, &info) == GBLA_OK && rank == 1000 * 7 + 65521);
+        CHECK(info.running_at_start == 1 && info.queue_ms >= 0 && info.latency_ms >= info.queue_ms);
+        CHECK(info.device_start_ms >= 0 && info.device_end_ms >= info.device_start_ms + 50);   // slept 100 ms
+        CHECK(gbla_server_poll(s, t0, &state) == GBLA_E_INVAL);  // consumed
+        for (int i = 0; i < 2000; ++i) {
+            CHECK(gbla_server_poll(s, t1, &state) == GBLA_OK);
+            if (state == GBLA_REQ_DONE) break;
+            std::this_thread::sleep_for(std::chrono::milliseconds(1));
+        }
+        CHECK(state == GBLA_REQ_DONE);
         CHECK(gbla_server_wait(s, t1, -1.0, &o, &rank, nullptr) == GBLA_OK && rank == 3 * 7 + 65521);
         CHECK(gbla_server_wait(s, t2, -1.0, &o, &rank, nullptr) == GBLA_E_CANCELLED);
         CHECK(gbla_server_wait(s, t2, -1.0, &o, &rank, nullptr) == GBLA_E_INVAL);   // ticket consumed
