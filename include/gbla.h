@@ -231,6 +231,23 @@ const char *gbla_strerror(int code);
 /* ABI version (major*100 + minor). */
 int gbla_version(void);
 
+/* Environment switches read once per process: GBLA_LOG=1 prints one line per
+ * reduction on stderr (path, order, variant, leaf width, block shapes, list
+ * sizes, phase times); GBLA_FAULT_ALLOC_AFTER=n arms the allocation fault
+ * below at the first allocation. */
+
+/* Fault injection for tests (host side, no device fault): every device and
+ * host allocation of the library counts against one process-wide counter;
+ * the allocation that follows the next n fails once (the call returns
+ * GBLA_E_NOMEM, or the batch member / server request does), after which
+ * allocations succeed again.  n < 0 disarms. */
+int gbla_selftest_fail_alloc_after(int64_t n);
+
+/* Bytes of the device's stream-ordered memory pool currently allocated (the
+ * library's scratch; 0 when no call is in flight and nothing leaked).
+ * Synchronises the device. */
+int gbla_device_bytes_in_use(int64_t *bytes);
+
 /* ---- building blocks, exposed for testing ----------------------------- */
 /* Modular matrix product on device memory (FL steps 2-3, the dense Schur
  * update D <- D - C*A^-1*B of Sec. 4.1, done as an exact GEMM):

@@ -271,9 +271,12 @@ extern "C" int gbla_decode_format2_ex(const void *file, size_t bytes, void *stre
     do {                                     \
         if (rc == GBLA_OK) rc = (expr);      \
     } while (0)
-#define F2CUDA(expr)                                                  \
-    do {                                                              \
-        if (rc == GBLA_OK && (expr) != cudaSuccess) rc = GBLA_E_CUDA; \
+#define F2CUDA(expr)                                                                \
+    do {                                                                            \
+        if (rc == GBLA_OK) {                                                        \
+            const cudaError_t _e = (expr);                                          \
+            if (_e != cudaSuccess) rc = _e == cudaErrorMemoryAllocation ? GBLA_E_NOMEM : GBLA_E_CUDA; \
+        }                                                                           \
     } while (0)
     F2STEP(dalloc_t(&rows32, m + 1, s));
     F2STEP(dalloc_t(&polmap32, m + 1, s));
@@ -289,9 +292,9 @@ extern "C" int gbla_decode_format2_ex(const void *file, size_t bytes, void *stre
     F2STEP(dalloc_t(&role, (size_t)k + 1, s));
     F2STEP(dalloc_t(&flag, (size_t)nnz + 1, s));
     F2STEP(dalloc_t(&err, 1, s));
-    F2CUDA(cudaMalloc(&row_ptr, sizeof(int64_t) * (m + 1)));
-    F2CUDA(cudaMalloc(&col, sizeof(int32_t) * (size_t)(nnz + 1)));
-    F2CUDA(cudaMalloc(&val, sizeof(uint16_t) * (size_t)(nnz + 1)));
+    F2CUDA(out_malloc((void **)&row_ptr, sizeof(int64_t) * (m + 1)));
+    F2CUDA(out_malloc((void **)&col, sizeof(int32_t) * (size_t)(nnz + 1)));
+    F2CUDA(out_malloc((void **)&val, sizeof(uint16_t) * (size_t)(nnz + 1)));
     F2CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
     F2CUDA(cudaMemsetAsync(flag, 0, (size_t)nnz + 1, s));
     F2CUDA(cudaMemsetAsync(total, 0, 2 * sizeof(int64_t), s));

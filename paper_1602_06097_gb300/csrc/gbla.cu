@@ -49,9 +49,42 @@ static void setup_pool() {
     });
 }
 
+// Host-side fault injection: every device and host allocation of the library
+// counts against one process-wide counter; once armed with n (the environment
+// switch GBLA_FAULT_ALLOC_AFTER=n at the first allocation, or
+// gbla_selftest_fail_alloc_after), the allocation that follows the next n
+// fails once, as if the memory were exhausted.  Tests use it to drive every
+// error path of a reduction and check that it releases what it holds.
+static std::atomic<long long> g_fault_at{-1};   // allocation index that fails
+static std::atomic<long long> g_alloc_count{0};
+static std::once_flag g_fault_env_once;
+
+bool inject_alloc_fault() {
+    std::call_once(g_fault_env_once, [] {
+        const char *e = getenv("GBLA_FAULT_ALLOC_AFTER");
+        if (e && atoll(e) >= 0) g_fault_at = atoll(e);
+    });
+    const long long at = g_fault_at.load();
+    const long long i = g_alloc_count.fetch_add(1);
+    if (at < 0 || i != at) return false;
+    long long expect = at;
+    g_fault_at.compare_exchange_strong(expect, -1);   // one shot
+    return true;
+}
+
+cudaError_t out_malloc(void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(ptr, bytes);
+}
+
 int dalloc(void **ptr, size_t bytes, cudaStream_t s) {
     *ptr = nullptr;
     if (bytes == 0) bytes = 16;
+    if (inject_alloc_fault()) {
+        set_last_cuda_error(cudaErrorMemoryAllocation, "injected allocation fault", __FILE__, __LINE__);
+        return GBLA_E_NOMEM;
+    }
     cudaError_t e = cudaMallocAsync(ptr, bytes, s);
     if (e != cudaSuccess) {
         set_last_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -152,6 +185,7 @@ static bool serialize_reductions() {
 }
 
 void *host_alloc(size_t bytes) {
+    if (inject_alloc_fault()) return nullptr;
     if (bytes == 0) bytes = 16;
     const size_t want = round_up((int64_t)bytes, 1 << 21);
     HostCache &c = host_cache();
@@ -400,6 +434,17 @@ struct Timer {
     }
 };
 
+// GBLA_LOG=1 in the environment: one line per reduction on stderr with the
+// planner's choices (path, order, product variant, leaf width), the block
+// shapes, the compacted list sizes and the phase times.
+static bool log_enabled() {
+    static const bool v = [] {
+        const char *e = getenv("GBLA_LOG");
+        return e && atoi(e) != 0;
+    }();
+    return v;
+}
+
 // A second stream (and a fork/join event pair) per host thread, for work of
 // one reduction that can overlap its main stream.
 struct SideStream {
@@ -518,7 +563,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     GemmCounters ctr;
     const long long launches0 = g_launches, pair_launches0 = g_pair_launches;
     Timer tm;
-    tm.init(stats != nullptr);
+    const bool log_on = log_enabled();
+    tm.init(stats != nullptr || log_on);
     tm.mark(s);
 
     // Everything below allocates from the stream-ordered pool; `cleanup`
@@ -559,7 +605,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         cudaError_t _e = (expr);                                  \
         if (_e != cudaSuccess) {                                  \
             set_last_cuda_error(_e, #expr, __FILE__, __LINE__);   \
-            rc = GBLA_E_CUDA;                                     \
+            rc = _e == cudaErrorMemoryAllocation ? GBLA_E_NOMEM : GBLA_E_CUDA; \
             goto cleanup;                                         \
         }                                                         \
     } while (0)
@@ -859,9 +905,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         out->nnz = onnz;
         if (device_ptrs) {
             out->on_device = 1;
-            CSTEP(cudaMalloc(&out->row_ptr, sizeof(int64_t) * (size_t)(rank + 1)));
-            CSTEP(cudaMalloc(&out->col, sizeof(int32_t) * (size_t)(onnz + 1)));
-            CSTEP(cudaMalloc(&out->val, sizeof(uint16_t) * (size_t)(onnz + 1)));
+            CSTEP(out_malloc((void **)&out->row_ptr, sizeof(int64_t) * (size_t)(rank + 1)));
+            CSTEP(out_malloc((void **)&out->col, sizeof(int32_t) * (size_t)(onnz + 1)));
+            CSTEP(out_malloc((void **)&out->val, sizeof(uint16_t) * (size_t)(onnz + 1)));
             CSTEP(cudaMemcpyAsync(out->row_ptr, orp, sizeof(int64_t) * (size_t)(rank + 1), cudaMemcpyDeviceToDevice, s));
             if (onnz > 0) {
                 CSTEP(cudaMemcpyAsync(out->col, ocol, sizeof(int32_t) * (size_t)onnz, cudaMemcpyDeviceToDevice, s));
@@ -950,6 +996,18 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     }
 
 cleanup:
+    if (log_on) {
+        fprintf(stderr,
+                "gbla: m=%lld n=%lld nnz=%lld p=%u path=%s order=%s variant=%d reduced=%d leaf=%d npiv=%lld "
+                "m_cd=%lld n_d=%lld list_a=%lld list_b=%lld rank_d=%lld rc=%d ms split=%.3f trsm=%.3f schur=%.3f "
+                "echelon=%.3f backsub=%.3f output=%.3f total=%.3f\n",
+                (long long)m, (long long)n, (long long)nnz, p, sparse ? "sparse" : "dense",
+                trsm_first ? "trsm_first" : "new", variant, want_reduced, tc_leaf_w, (long long)npiv, (long long)m_cd,
+                (long long)n_d, (long long)SA.total, (long long)SB.total, (long long)rank_d, rc,
+                rc == GBLA_OK ? tm.ms(0, 1) : 0.0, rc == GBLA_OK ? tm.ms(1, 2) : 0.0, rc == GBLA_OK ? tm.ms(2, 3) : 0.0,
+                rc == GBLA_OK ? tm.ms(3, 4) : 0.0, rc == GBLA_OK ? tm.ms(4, 5) : 0.0, rc == GBLA_OK ? tm.ms(5, 6) : 0.0,
+                rc == GBLA_OK ? tm.ms(0, 6) : 0.0);
+    }
     if (ktimes && rc != GBLA_OK) kernel_times_end(&kt);
     if (side_pending) {   // nothing the side stream uses may be freed before it is done
         cudaStreamSynchronize(g_side.s);
@@ -1017,6 +1075,28 @@ using namespace gbla;
 extern "C" {
 
 int gbla_version(void) { return 100; }
+
+int gbla_selftest_fail_alloc_after(int64_t n) {
+    inject_alloc_fault();   // reads the environment switch once, before it is overridden
+    g_alloc_count = 0;
+    g_fault_at = n < 0 ? -1 : (long long)n;
+    return GBLA_OK;
+}
+
+int gbla_device_bytes_in_use(int64_t *bytes) {
+    if (!bytes) return GBLA_E_INVAL;
+    *bytes = 0;
+    GBLA_TRY(check_device());
+    GBLA_CUDA_TRY(cudaDeviceSynchronize());
+    int dev = 0;
+    cudaMemPool_t pool;
+    uint64_t used = 0;
+    GBLA_CUDA_TRY(cudaGetDevice(&dev));
+    GBLA_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    GBLA_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    *bytes = (int64_t)used;
+    return GBLA_OK;
+}
 
 const char *gbla_strerror(int code) {
     switch (code) {

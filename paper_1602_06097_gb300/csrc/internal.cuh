@@ -140,6 +140,13 @@ int to_planes(const Planes &dst, int64_t R, int64_t Kc, const uint16_t *src, int
               bool transposed, const int32_t *rgather, const int32_t *cgather, const ModP &mp, cudaStream_t s,
               const int32_t *zero_if = nullptr, bool k_le_r_only = false, int64_t dst_col0 = 0);
 
+// One-shot allocation fault injection (see gbla.cu): true when this
+// allocation is to fail.
+bool inject_alloc_fault();
+// cudaMalloc for memory that leaves the library (results), with fault
+// injection.
+cudaError_t out_malloc(void **ptr, size_t bytes);
+
 // Stream-ordered device allocation helpers (memory pool of the device).
 int dalloc(void **ptr, size_t bytes, cudaStream_t s);
 void dfree(void *ptr, cudaStream_t s);
@@ -148,6 +155,20 @@ template <typename T>
 inline int dalloc_t(T **ptr, size_t count, cudaStream_t s) {
     return dalloc(reinterpret_cast<void **>(ptr), count * sizeof(T) + 16, s);
 }
+
+// A scratch device array owned by one scope: released (stream-ordered on s)
+// on every exit from it, early error returns included.
+template <typename T>
+struct DevTemp {
+    T *p = nullptr;
+    cudaStream_t s = nullptr;
+    explicit DevTemp(cudaStream_t st) : s(st) {}
+    DevTemp(const DevTemp &) = delete;
+    DevTemp &operator=(const DevTemp &) = delete;
+    ~DevTemp() { dfree(p, s); }
+    int alloc(size_t count) { return dalloc_t(&p, count, s); }
+    operator T *() const { return p; }
+};
 
 int planes_alloc(Planes *pl, int64_t rows, int64_t k, int nplanes, cudaStream_t s);
 void planes_free(Planes *pl, cudaStream_t s);

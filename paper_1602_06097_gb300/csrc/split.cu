@@ -74,8 +74,8 @@ int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, cud
         return GBLA_OK;
     }
     const int64_t nb = (n + 1023) / 1024;
-    int64_t *sums = nullptr;
-    GBLA_TRY(dalloc_t(&sums, (size_t)nb + 1, s));
+    DevTemp<int64_t> sums(s);
+    GBLA_TRY(sums.alloc((size_t)nb + 1));
     scan_block_kernel<<<(unsigned)nb, 256, 0, s>>>(in, out, n, sums);
     GBLA_CUDA_TRY(launch_check());
     int rc = GBLA_OK;
@@ -87,17 +87,16 @@ int scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, cud
         }
     } else {
         // scan the block sums (sums[nb] receives the grand total), add them back
-        rc = scan_i64(sums, sums, nb, sums + nb, s);
+        rc = scan_i64(sums, sums, nb, sums.p + nb, s);
         if (rc == GBLA_OK) {
             scan_add_kernel<<<(unsigned)nb, 256, 0, s>>>(out, n, sums);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
         if (rc == GBLA_OK && total_dev) {
-            copy_i64_kernel<<<1, 1, 0, s>>>(total_dev, sums + nb);
+            copy_i64_kernel<<<1, 1, 0, s>>>(total_dev, sums.p + nb);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }
     }
-    dfree(sums, s);
     return rc;
 }
 
@@ -245,10 +244,10 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
                                                                            mp.p, pi->lead, pi->best, err);
         GBLA_CUDA_TRY(launch_check());
     }
-    int64_t *cflag = nullptr, *rflag = nullptr, *rpos = nullptr;
-    GBLA_TRY(dalloc_t(&cflag, (size_t)n + 1, s));
-    GBLA_TRY(dalloc_t(&rflag, (size_t)m + 1, s));
-    GBLA_TRY(dalloc_t(&rpos, (size_t)(m > n ? m : n) + 2, s));
+    DevTemp<int64_t> cflag(s), rflag(s), rpos(s);
+    GBLA_TRY(cflag.alloc((size_t)n + 1));
+    GBLA_TRY(rflag.alloc((size_t)m + 1));
+    GBLA_TRY(rpos.alloc((size_t)(m > n ? m : n) + 2));
     GBLA_TRY(dalloc_t(&pi->dev_counts, 2, s));
     if (n > 0) {
         col_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pi->best, cflag);
@@ -264,12 +263,7 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
     GBLA_TRY(readback(host_counts, pi->dev_counts, sizeof(host_counts), s));
     uint32_t herr = 0;
     GBLA_TRY(readback(&herr, err, sizeof(herr), s));
-    if (herr & DEV_ERR_INVAL) {
-        dfree(cflag, s);
-        dfree(rflag, s);
-        dfree(rpos, s);
-        return GBLA_E_INVAL;
-    }
+    if (herr & DEV_ERR_INVAL) return GBLA_E_INVAL;
     pi->npiv = host_counts[0];
     pi->m_cd = host_counts[1];
     pi->n_d = n - pi->npiv;
@@ -288,9 +282,9 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
     }
     if (m > 0) {
         // counting sort of the C/D rows by leading pivot column (rpos reused as counts/offsets)
-        int32_t *fill = nullptr;
+        DevTemp<int32_t> fill(s);
         const int64_t nk = pi->npiv + 1;
-        GBLA_TRY(dalloc_t(&fill, (size_t)nk, s));
+        GBLA_TRY(fill.alloc((size_t)nk));
         GBLA_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)nk, s));
         GBLA_CUDA_TRY(cudaMemsetAsync(rpos, 0, sizeof(int64_t) * (size_t)(nk < m + 1 ? m + 1 : nk), s));
         GBLA_CUDA_TRY(cudaMemsetAsync(pi->cd_index, 0xFF, sizeof(int32_t) * (size_t)m, s));
@@ -305,16 +299,12 @@ int pivot_analysis(const DevCSR &in, const ModP &mp, PivotInfo *pi, uint32_t *er
                                                                                 pi->cd_index, pi->cd_lead);
             GBLA_CUDA_TRY(launch_check());
         }
-        dfree(fill, s);
     }
     if (pi->npiv > 0) {
         inv_lead_kernel<<<(unsigned)((pi->npiv + 255) / 256), 256, 0, s>>>(pi->npiv, pi->piv_row, in.row_ptr, in.val,
                                                                           pi->inv_lead, mp);
         GBLA_CUDA_TRY(launch_check());
     }
-    dfree(cflag, s);
-    dfree(rflag, s);
-    dfree(rpos, s);
     return GBLA_OK;
 }
 

@@ -24,7 +24,8 @@ EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_
            "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc",
            "gbla_selftest_wait_timeout", "gbla_reduce_batch", "gbla_server_create", "gbla_server_submit",
            "gbla_server_wait", "gbla_server_wait_ex", "gbla_server_poll", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy",
-           "gbla_decode_format2", "gbla_decode_format2_ex", "gbla_spmm", "gbla_pipe_peak"]
+           "gbla_decode_format2", "gbla_decode_format2_ex", "gbla_spmm", "gbla_pipe_peak",
+           "gbla_selftest_fail_alloc_after", "gbla_device_bytes_in_use"]
 
 
 class CsrIn(ctypes.Structure):
@@ -127,6 +128,10 @@ def load():
         lib.gbla_modmatmul.restype = i32
         lib.gbla_pivots.argtypes = [ctypes.POINTER(CsrIn), u32, vp, ctypes.POINTER(i64), vp]
         lib.gbla_spmm.restype = i32
+        lib.gbla_selftest_fail_alloc_after.argtypes = [i64]
+        lib.gbla_selftest_fail_alloc_after.restype = i32
+        lib.gbla_device_bytes_in_use.argtypes = [ctypes.POINTER(i64)]
+        lib.gbla_device_bytes_in_use.restype = i32
         lib.gbla_pipe_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
         lib.gbla_pipe_peak.restype = i32
         lib.gbla_spmm.argtypes = [i64, i64, i64, vp, i64, ctypes.POINTER(CsrIn), vp, vp, i64, u32, i32, vp]
@@ -518,6 +523,19 @@ def modmatmul(A, B, C, p, sign=-1, variant=GEMM_AUTO, stream=None):
     rc = lib.gbla_modmatmul(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                             C.data_ptr(), C.stride(0), int(p), int(sign), int(variant), _stream_ptr(stream))
     _check(rc, "gbla_modmatmul")
+
+
+def fail_alloc_after(n):
+    """Arm the one-shot allocation fault: the allocation after the next n
+    fails (n < 0 disarms).  Test hook."""
+    _check(load().gbla_selftest_fail_alloc_after(int(n)), "gbla_selftest_fail_alloc_after")
+
+
+def device_bytes_in_use():
+    """Bytes of the device pool held by the library (synchronises the device)."""
+    v = ctypes.c_int64(0)
+    _check(load().gbla_device_bytes_in_use(ctypes.byref(v)), "gbla_device_bytes_in_use")
+    return int(v.value)
 
 
 def pipe_peak(variant, stream=None):

@@ -43,6 +43,7 @@ cudaError_t cudaFreeHost(void *p) { free(p); ++g_unpins; return cudaSuccess; }
 cudaError_t cudaGetLastError() { return cudaSuccess; }
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 namespace gbla {
+bool inject_alloc_fault() { return false; }
 namespace {
 """
 
