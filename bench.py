@@ -151,19 +151,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------ committed records
-def profiled_traffic(name="modgemm_gather_schur_traffic_fl_150000x200000.md",
+def profiled_traffic(name="dram_traffic_fl_150000x200000.md",
                      src=os.path.join("paper_1602_06097_gb300", "csrc", "modgemm.cu")):
-    """DRAM bytes per Schur launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """DRAM bytes per launch of the dense product from the committed ncu
+    summary, if the kernel's source region (named in the summary) still
+    hashes as it did when the counters were taken (else None)."""
     import re
     try:
         txt = open(os.path.join(ROOT, "profiles", name)).read()
-        code = open(os.path.join(ROOT, src), "rb").read()
+        code = open(os.path.join(ROOT, src)).read()
     except OSError:
         return None
     m1 = re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt)
     m2 = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
-    if not (m1 and m2) or hashlib.sha256(code).hexdigest() != m2.group(1):
+    m3 = re.search(r'kernel_region: \S+ "([^"]+)" \.\. "([^"]+)"', txt)
+    if not (m1 and m2 and m3):
+        return None
+    a, b = code.find(m3.group(1)), code.find(m3.group(2))
+    if a < 0 or b <= a or hashlib.sha256(code[a:b].encode()).hexdigest() != m2.group(1):
         return None
     return int(m1.group(1))
 
@@ -683,10 +688,11 @@ def main():
                     "algorithmic": "M x N x K of the dense products over each tile's K run, 8 flops per modular "
                                    "multiply-add (4 bf16 digit products)",
                     "avg_launch_ms": kernels["modgemm_tc_kernel"]["avg_launch_ms"],
-                    "traffic": None}
+                    "traffic": profiled_traffic() if (a.workload == WORKLOAD and a.scale == 1.0) else None,
+                    "traffic_source": "profiles/dram_traffic_fl_150000x200000.md (ncu, mean over the 340 "
+                                      "launches of one reduction)"}
     else:
-        roofline = dict(schur, peak_kind=f"bf16 dense sustained, {kind}",
-                        traffic=profiled_traffic() if (a.workload == WORKLOAD and a.scale == 1.0) else None)
+        roofline = dict(schur, peak_kind=f"bf16 dense sustained, {kind}", traffic=None)
         roofline["kernel"] = (f"modgemm_gather_kernel (dominant: {g_ms:.1f} ms per step over {g_n:.0f} launches); "
                               "figures of its Schur launch")
 

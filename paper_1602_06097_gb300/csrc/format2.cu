@@ -21,8 +21,9 @@
 //      when e - last[e] is odd and a run length when it is even;
 //   3. entries emit 1 (lone), s (run start, s read from the next entry) or 0
 //      columns; off = the exclusive scan of those counts;
-//   4. output position q takes its column from the last entry with off <= q
-//      (binary search): the lone column, or the run start plus q - off;
+//   4. entry e writes positions off[e] .. off[e] + count - 1: the lone
+//      column, or the run start plus q - off[e] (a warp per 32 entries, the
+//      lanes writing consecutive positions);
 //   5. checks: a run stays inside the row of its first column (no row starts
 //      strictly inside it), columns rise within a row and stay below n;
 //   6. row i copies polynomial polmap[i]'s coefficients (one warp per row),
@@ -111,38 +112,48 @@ __global__ void f2_row_flags_kernel(const int64_t *__restrict__ row_ptr, int64_t
     if (r < m && row_ptr[r + 1] > row_ptr[r] && row_ptr[r] < nnz) flag[row_ptr[r]] = 1;
 }
 
+// Columns of the rows: one warp per 32 consecutive column entries, which it
+// expands one after the other, the lanes writing 32 consecutive positions of
+// the entry's run at a time (coalesced).  An entry covers positions
+// off[e] .. off[e] + cnt[e] (a lone column one, a run start s, a run length
+// none).  A run must not cross into the next row (flag marks row starts) and
+// no column may reach n.  Skipped when an earlier check already failed (the
+// totals then need not match nnz).
 __global__ void f2_expand_kernel(const uint64_t *__restrict__ colid, const int64_t *__restrict__ off,
-                                 const int8_t *__restrict__ role, int64_t k, const int8_t *__restrict__ flag,
-                                 int64_t nnz, int64_t n, int32_t *__restrict__ col, uint32_t *err)
+                                 const int64_t *__restrict__ cnt, const int8_t *__restrict__ role, int64_t k,
+                                 const int8_t *__restrict__ flag, int64_t nnz, int64_t n, int32_t *__restrict__ col,
+                                 uint32_t *err)
 {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nnz) return;
-    if (k <= 0) {
-        dev_fail(err, DEV_ERR_INVAL);
-        return;
+    if (*(volatile uint32_t *)err) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    if (e0 >= k) return;
+    const int64_t e = e0 + lane;
+    const bool has = e < k;
+    const uint64_t x_l = has ? colid[e] : 0;
+    const int64_t o_l = has ? off[e] : 0, c_l = has ? cnt[e] : 0;
+    const int r_l = has ? (int)role[e] : (int)F2_LEN;
+    const int last = (int)min((int64_t)32, k - e0);
+    for (int i = 0; i < last; ++i) {
+        const uint64_t x = __shfl_sync(0xffffffffu, x_l, i);
+        const int64_t o = __shfl_sync(0xffffffffu, o_l, i), c = __shfl_sync(0xffffffffu, c_l, i);
+        const int r = __shfl_sync(0xffffffffu, r_l, i);
+        if (r == F2_LEN || c == 0) continue;
+        if (c < 0 || o < 0 || o + c > nnz) {
+            if (lane == 0) dev_fail(err, DEV_ERR_INVAL);
+            return;
+        }
+        const int64_t base = r == F2_LONE ? (int64_t)(x & 0x7FFFFFFFull) : (int64_t)x;
+        if (base + c > n) {
+            if (lane == 0) dev_fail(err, DEV_ERR_INVAL);
+            return;
+        }
+        for (int64_t t = lane; t < c; t += 32) {
+            const int64_t q = o + t;
+            if (t > 0 && flag[q]) dev_fail(err, DEV_ERR_INVAL);   // the run crosses into the next row
+            col[q] = (int32_t)(base + t);
+        }
     }
-    int64_t lo = 0, hi = k;   // off[lo] <= q; the answer is the last such entry
-    while (hi - lo > 1) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (off[mid] <= q) lo = mid;
-        else hi = mid;
-    }
-    const uint64_t x = colid[lo];
-    int64_t c;
-    if (role[lo] == F2_LONE) {
-        c = (int64_t)(x & 0x7FFFFFFFull);
-    } else if (role[lo] == F2_START) {
-        c = (int64_t)x + (q - off[lo]);
-        if (q > off[lo] && flag[q]) dev_fail(err, DEV_ERR_INVAL);   // the run crosses into the next row
-    } else {
-        dev_fail(err, DEV_ERR_INVAL);
-        c = 0;
-    }
-    if (c >= n) {
-        dev_fail(err, DEV_ERR_INVAL);
-        c = 0;
-    }
-    col[q] = (int32_t)c;
 }
 
 __global__ void f2_order_kernel(const int32_t *__restrict__ col, const int8_t *__restrict__ flag, int64_t nnz,
@@ -350,8 +361,9 @@ extern "C" int gbla_decode_format2_ex(const void *file, size_t bytes, void *stre
         f2_row_flags_kernel<<<blocks((int64_t)m), 256, 0, s>>>(row_ptr, (int64_t)m, nnz, flag);
         F2CUDA(launch_check());
     }
-    if (nnz && rc == GBLA_OK) {
-        f2_expand_kernel<<<blocks(nnz), 256, 0, s>>>(colid, off, role, k, flag, nnz, n, col, err);
+    if (nnz && k && rc == GBLA_OK) {
+        f2_expand_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(colid, off, cnt, role, k, flag, nnz, n, col,
+                                                                     err);
         F2CUDA(launch_check());
     }
     if (nnz && rc == GBLA_OK) {

@@ -38,19 +38,28 @@ def test_clock_summary_skips_malformed_lines():
 
 
 def test_traffic_reported_only_for_the_measured_kernel_source(tmp_path, monkeypatch):
+    """The figure is used only while the kernel's source region hashes as
+    when the counters were taken: an edit inside the region drops it, an
+    edit outside does not."""
     import hashlib
     rel_src = os.path.join("paper_1602_06097_gb300", "csrc", "modgemm.cu")
-    rel_prof = os.path.join("profiles", "modgemm_gather_schur_traffic_fl_150000x200000.md")
+    rel_prof = os.path.join("profiles", "dram_traffic_fl_150000x200000.md")
     os.makedirs(tmp_path / os.path.dirname(rel_src), exist_ok=True)
     os.makedirs(tmp_path / "profiles", exist_ok=True)
     shutil.copy(os.path.join(ROOT, rel_src), tmp_path / rel_src)
-    digest = hashlib.sha256(open(tmp_path / rel_src, "rb").read()).hexdigest()
-    (tmp_path / rel_prof).write_text(f"traffic_bytes_per_launch: 81070000000\nkernel_source_sha256: {digest}\n")
+    code = open(tmp_path / rel_src).read()
+    begin, end = "namespace tc {", "// Gathered product: the sparse operand compacted per column tile"
+    a, b = code.index(begin), code.index(end)
+    digest = hashlib.sha256(code[a:b].encode()).hexdigest()
+    (tmp_path / rel_prof).write_text(f"traffic_bytes_per_launch: 739917251\n"
+                                     f'kernel_region: modgemm.cu "{begin}" .. "{end}"\n'
+                                     f"kernel_source_sha256: {digest}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    figure = bench.profiled_traffic()
-    assert isinstance(figure, int) and figure == 81070000000
-    with open(tmp_path / rel_src, "a") as f:
+    assert bench.profiled_traffic() == 739917251
+    with open(tmp_path / rel_src, "a") as f:          # outside the region
         f.write("\n// edited\n")
+    assert bench.profiled_traffic() == 739917251
+    open(tmp_path / rel_src, "w").write(code[:a + 20] + "// edited\n" + code[a + 20:])   # inside
     assert bench.profiled_traffic() is None
     os.remove(tmp_path / rel_prof)
     assert bench.profiled_traffic() is None
