@@ -104,6 +104,12 @@ typedef struct {
                           and count the dense product's tile work (gbla_stats.tc_*,
                           gather_*); needs stats */
     int fl_order;      /* GBLA_ORDER_*: order of the FL steps */
+    int autotune;      /* 1: the choices left open here (path on GBLA_PATH_AUTO, leaf_width
+                          0, the gathered product's raster group) are made per shape
+                          bucket by measurement: the first calls of a bucket (rows, columns
+                          and density rounded to powers of two, tensor-core paths only) try
+                          the candidates in turn, later calls take the fastest.  Every
+                          candidate gives the same exact result. */
 } gbla_options;
 
 /* Order of the FL steps.  The new order (Sec. 4.3) computes X = C*A^-1 and
@@ -139,6 +145,10 @@ typedef struct {
     double tc_mod_ops;           /* dense product: valid rows x columns x K run of its tiles */
     int64_t tc_pair_launches;    /* dense product launches that ran on CTA pairs (cta_group::2,
                                     enabled by the environment switch GBLA_GEMM_PAIR=1) */
+    int64_t gather_group_m;      /* row tiles per raster group of the gathered product */
+    int64_t tune_state;          /* with autotune: 1 = a trial of one candidate, 2 = the bucket's
+                                    fastest candidate, 3 = default while trials are in flight;
+                                    0 without autotune */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */

@@ -13,6 +13,8 @@
 #include <string.h>
 
 #include <atomic>
+#include <cmath>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -515,16 +517,107 @@ static int back_leaf_width() {
     return v;
 }
 
+// ------------------------------------------------------------ autotuner
+// With gbla_options.autotune the choices a caller leaves open are made per
+// shape bucket (rows, columns and density rounded to powers of two) by
+// measurement.  The candidates differ only in how the same exact result is
+// computed: the sparse path with leaves of 512 or 1024 columns, with raster
+// groups of 4 or 8 row tiles in the gathered product, and (for matrices of at
+// most 20,000 rows) the dense path.  The first calls of a bucket claim the
+// candidates one by one as trials; a call that finds every candidate claimed
+// but not all timed runs the default; once all are timed (event-timed whole
+// reduction, a failed trial counts as infinitely slow) every later call runs
+// the fastest.
+namespace {
+struct TuneCand {
+    int path, leaf, group_m;
+};
+struct TuneBucket {
+    std::vector<TuneCand> cands;
+    std::vector<double> ms;
+    int claimed = 0, timed = 0, best = -1;
+};
+std::mutex g_tune_mu;
+std::map<uint64_t, TuneBucket> g_tune;
+
+uint64_t tune_key(int64_t m, int64_t n, int64_t nnz, bool free_path, bool free_leaf) {
+    auto lg = [](double x) { return (uint64_t)std::ceil(std::log2(x < 1.0 ? 1.0 : x)); };
+    const double dens = (double)nnz / ((double)(m > 0 ? m : 1) * (double)(n > 0 ? n : 1));
+    return lg((double)m) | lg((double)n) << 8 | lg(1.0 / (dens > 1e-12 ? dens : 1e-12)) << 16 |
+           (uint64_t)free_path << 24 | (uint64_t)free_leaf << 25;
+}
+
+struct TuneTicket {
+    uint64_t key = 0;
+    int idx = -1;   // candidate run (-1: none)
+    int state = 0;  // gbla_stats.tune_state
+    TuneCand cand{GBLA_PATH_AUTO, 0, 0};
+};
+
+TuneTicket tune_pick(int64_t m, int64_t n, int64_t nnz, bool free_path, bool free_leaf) {
+    TuneTicket t;
+    t.key = tune_key(m, n, nnz, free_path, free_leaf);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneBucket &b = g_tune[t.key];
+    if (b.cands.empty()) {
+        const int path0 = free_path ? GBLA_PATH_SPARSE : GBLA_PATH_AUTO;
+        const int gm0 = gather_group_m_default();
+        for (int leaf : {512, 1024})
+            for (int gm : {gm0, 2 * gm0}) {
+                if (!free_leaf && leaf != 512) continue;
+                b.cands.push_back({path0, free_leaf ? leaf : 0, gm});
+            }
+        if (free_path && m <= 20000) b.cands.push_back({GBLA_PATH_DENSE, 0, 0});
+        b.ms.assign(b.cands.size(), -1.0);
+    }
+    if (b.best >= 0) {
+        t.idx = b.best;
+        t.state = 2;
+    } else if (b.claimed < (int)b.cands.size()) {
+        t.idx = b.claimed++;
+        t.state = 1;
+    } else {
+        t.state = 3;   // trials in flight: the default
+        return t;
+    }
+    t.cand = b.cands[(size_t)t.idx];
+    return t;
+}
+
+void tune_report(const TuneTicket &t, double ms) {
+    if (t.state != 1) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneBucket &b = g_tune[t.key];
+    if (b.ms[(size_t)t.idx] >= 0.0) return;
+    b.ms[(size_t)t.idx] = ms;
+    if (++b.timed == (int)b.cands.size()) {
+        b.best = 0;
+        for (size_t i = 1; i < b.ms.size(); ++i)
+            if (b.ms[i] < b.ms[(size_t)b.best]) b.best = (int)i;
+    }
+}
+
+// Sets the gathered product's raster group for this thread while in scope.
+struct GroupOverride {
+    int prev;
+    explicit GroupOverride(int v) : prev(g_gather_group_m_override) {
+        if (v > 0) g_gather_group_m_override = v;
+    }
+    ~GroupOverride() { g_gather_group_m_override = prev; }
+};
+}  // namespace
+
 int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cudaStream_t s, gbla_csr_out *out,
                 int64_t *rank_out, gbla_stats *stats) {
     const int want_reduced = opt ? opt->want_reduced : 0;
     const int variant = opt ? opt->gemm_variant : GBLA_GEMM_AUTO;
     const int device_ptrs = opt ? opt->device_ptrs : 0;
-    const int path_opt = opt ? opt->path : GBLA_PATH_AUTO;
+    const int path_req = opt ? opt->path : GBLA_PATH_AUTO;
     const bool ktimes = opt && opt->kernel_times && stats;
-    const int leaf_opt = opt ? opt->leaf_width : 0;
+    const int leaf_req = opt ? opt->leaf_width : 0;
+    const bool autotune = opt && opt->autotune;
     if (variant < 0 || variant > GBLA_GEMM_U8) return GBLA_E_INVAL;
-    if (path_opt < GBLA_PATH_AUTO || path_opt > GBLA_PATH_SPARSE) return GBLA_E_INVAL;
+    if (path_req < GBLA_PATH_AUTO || path_req > GBLA_PATH_SPARSE) return GBLA_E_INVAL;
     // FP64 and U8 name the pipe of the Schur update on the dense path; every
     // other product of the reduction runs on the tcgen05 tensor cores.
     const bool alt_schur = variant == GBLA_GEMM_FP64 || variant == GBLA_GEMM_U8;
@@ -537,7 +630,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     if (order_opt != GBLA_ORDER_NEW && order_opt != GBLA_ORDER_TRSM_FIRST) return GBLA_E_INVAL;
     const bool trsm_first = order_opt == GBLA_ORDER_TRSM_FIRST;
     const int pvariant = alt_schur ? GBLA_GEMM_TCGEN05 : variant;
-    if (leaf_opt != 0 && leaf_opt != 128 && leaf_opt != 256 && leaf_opt != 512 && leaf_opt != 1024)
+    if (leaf_req != 0 && leaf_req != 128 && leaf_req != 256 && leaf_req != 512 && leaf_req != 1024)
         return GBLA_E_INVAL;
     const int64_t m = in->nrows, n = in->ncols, nnz = in->nnz;
     if (m < 0 || n < 0 || nnz < 0 || m >= (1ll << 31) || n >= (1ll << 31)) return GBLA_E_INVAL;
@@ -556,15 +649,22 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     // variant.  The dense path materialises A and B (and serves p < 8 and the
     // exact SIMT variant).
     const bool tc_ok = pvariant != GBLA_GEMM_SIMT && p >= 8 && tc_supported();
-    if (path_opt == GBLA_PATH_SPARSE && (!tc_ok || alt_schur || trsm_first)) return GBLA_E_UNSUPPORTED;
+    if (path_req == GBLA_PATH_SPARSE && (!tc_ok || alt_schur || trsm_first)) return GBLA_E_UNSUPPORTED;
     if (alt_schur && !tc_ok) return GBLA_E_UNSUPPORTED;
+    // choices left open, made by the autotuner where it applies
+    TuneTicket tune;
+    if (autotune && tc_ok && !alt_schur && !trsm_first && (path_req == GBLA_PATH_AUTO || leaf_req == 0))
+        tune = tune_pick(m, n, nnz, path_req == GBLA_PATH_AUTO, leaf_req == 0);
+    const int path_opt = (tune.idx >= 0 && path_req == GBLA_PATH_AUTO) ? tune.cand.path : path_req;
+    const int leaf_opt = (tune.idx >= 0 && leaf_req == 0) ? tune.cand.leaf : leaf_req;
+    const GroupOverride group_override(tune.idx >= 0 ? tune.cand.group_m : 0);
     const bool sparse = tc_ok && path_opt != GBLA_PATH_DENSE && !alt_schur && !trsm_first;
     int tc_leaf_w = 512;
     GemmCounters ctr;
     const long long launches0 = g_launches, pair_launches0 = g_pair_launches;
     Timer tm;
     const bool log_on = log_enabled();
-    tm.init(stats != nullptr || log_on);
+    tm.init(stats != nullptr || log_on || tune.state == 1);
     tm.mark(s);
 
     // Everything below allocates from the stream-ordered pool; `cleanup`
@@ -974,6 +1074,10 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             stats->mod_ops = ctr.mod_ops;
             stats->launches = g_launches - launches0;
             stats->tc_pair_launches = g_pair_launches - pair_launches0;
+            stats->gather_group_m = sparse ? (g_gather_group_m_override ? g_gather_group_m_override
+                                                                        : gather_group_m_default())
+                                           : 0;
+            stats->tune_state = tune.state;
             stats->schur_mod_ops = schur_ops;
             stats->path = sparse ? GBLA_PATH_SPARSE : GBLA_PATH_DENSE;
             stats->list_a = SA.total;
@@ -996,6 +1100,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     }
 
 cleanup:
+    if (tune.state == 1) tune_report(tune, rc == GBLA_OK ? tm.ms(0, 6) : 1e30);
     if (log_on) {
         fprintf(stderr,
                 "gbla: m=%lld n=%lld nnz=%lld p=%u path=%s order=%s variant=%d reduced=%d leaf=%d npiv=%lld "

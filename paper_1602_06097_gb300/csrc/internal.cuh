@@ -14,6 +14,12 @@ struct GemmCounters {
 
 int device_sm_count();
 
+// Raster group of the gathered product: a per-thread override (0 = none) and
+// the default (environment switch GBLA_GATHER_GROUP_M, else the dense
+// product's).
+extern thread_local int g_gather_group_m_override;
+int gather_group_m_default();
+
 // One problem of a grouped product: rows a_row0.. of the A plane set times
 // rows b_row0.. of the B plane set (the same K for all problems), into C
 // rows c_rows[0..M) at columns c_col0 .. c_col0 + N.  tile_off = exclusive

@@ -1398,6 +1398,12 @@ static int gather_group_m_env() {
     return v;
 }
 
+// Per-thread override of the raster group (set by a reduction that the
+// autotuner configures; 0 = none).
+thread_local int g_gather_group_m_override = 0;
+
+int gather_group_m_default() { return gather_group_m_env() ? gather_group_m_env() : gemm_group_m(); }
+
 int device_sm_count() {
     static const int n = [] {
         int dev = 0, c = 0;
@@ -1617,7 +1623,8 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
     g.C = C; g.ldc = ldc; g.sign = sign;
     g.p = mp.p; g.pinv = mp.pinv;
     g.err = err;
-    g.group_m = gather_group_m_env() ? gather_group_m_env() : gemm_group_m();
+    g.group_m = g_gather_group_m_override ? g_gather_group_m_override
+                                          : (gather_group_m_env() ? gather_group_m_env() : gemm_group_m());
     const int64_t num_m = (M + tc::BM - 1) / tc::BM, num_n = (N + tc::BN - 1) / tc::BN;
     int32_t *kstart = nullptr;
     if (row_lead || exec) {

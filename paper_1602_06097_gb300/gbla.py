@@ -43,12 +43,13 @@ class Options(ctypes.Structure):
     _fields_ = [("want_reduced", ctypes.c_int), ("gemm_variant", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("panel_width", ctypes.c_int),
                 ("path", ctypes.c_int), ("leaf_width", ctypes.c_int), ("kernel_times", ctypes.c_int),
-                ("fl_order", ctypes.c_int)]
+                ("fl_order", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
-def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0, kernel_times=False, order=0):
+def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0, kernel_times=False, order=0,
+             autotune=False):
     return Options(1 if want_reduced else 0, int(variant), int(device_ptrs), 0, int(path), int(leaf),
-                   1 if kernel_times else 0, int(order))
+                   1 if kernel_times else 0, int(order), 1 if autotune else 0)
 
 
 class Stats(ctypes.Structure):
@@ -62,7 +63,8 @@ class Stats(ctypes.Structure):
                 ("leaf_width", ctypes.c_int64), ("schur_exec_mod_ops", ctypes.c_double),
                 ("tc_launches", ctypes.c_int64), ("gather_launches", ctypes.c_int64),
                 ("tc_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("tc_mod_ops", ctypes.c_double),
-                ("tc_pair_launches", ctypes.c_int64)]
+                ("tc_pair_launches", ctypes.c_int64), ("gather_group_m", ctypes.c_int64),
+                ("tune_state", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -224,7 +226,7 @@ class HostResult:
 
 
 def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
-                path=PATH_AUTO, leaf=0, order=ORDER_NEW) -> HostResult:
+                path=PATH_AUTO, leaf=0, order=ORDER_NEW, autotune=False) -> HostResult:
     """Reduce a host CSR matrix; the result stays in library-owned host memory
     (see HostResult).  Page-locked inputs copy to the device fastest.
     ``path`` is PATH_AUTO, PATH_DENSE or PATH_SPARSE, ``leaf`` the leaf width
@@ -235,7 +237,7 @@ def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AU
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.uint16)
     cin = CsrIn(m, n, int(len(col)), row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data)
-    opt = _options(want_reduced, variant, 0, path, leaf, order=order)
+    opt = _options(want_reduced, variant, 0, path, leaf, order=order, autotune=autotune)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
@@ -246,11 +248,11 @@ def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AU
 
 
 def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None,
-           path=PATH_AUTO, leaf=0, order=ORDER_NEW):
+           path=PATH_AUTO, leaf=0, order=ORDER_NEW, autotune=False):
     """Reduce a host CSR matrix.  Returns (rank, row_ptr, col, val) as numpy
     arrays the caller owns (and a stats dict when ``stats``)."""
     h = reduce_host(row_ptr, col, val, shape, p, want_reduced=want_reduced, variant=variant, stream=stream,
-                    path=path, leaf=leaf, order=order)
+                    path=path, leaf=leaf, order=order, autotune=autotune)
     try:
         res = (h.rank, h.row_ptr.copy(), h.col.copy(), h.val.copy())
         st = h.stats
@@ -339,14 +341,14 @@ class _CudaArray:
 
 
 def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
-                  path=PATH_AUTO, leaf=0, kernel_times=False, order=ORDER_NEW):
+                  path=PATH_AUTO, leaf=0, kernel_times=False, order=ORDER_NEW, autotune=False):
     """Reduce a CSR matrix already on the device (torch CUDA tensors: int64
     row_ptr, int32 col, int16/uint16 val).  Returns a DeviceResult whose
     arrays stay in device memory."""
     lib = load()
     m, n = int(shape[0]), int(shape[1])
     cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
-    opt = _options(want_reduced, variant, 1, path, leaf, kernel_times, order)
+    opt = _options(want_reduced, variant, 1, path, leaf, kernel_times, order, autotune)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
@@ -382,7 +384,7 @@ def _csr_in(row_ptr, col, val, shape):
     return cin, (row_ptr, col, val)
 
 
-def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PATH_AUTO):
+def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PATH_AUTO, autotune=False):
     """Reduce many host CSR matrices on a pool of worker threads whose
     reductions overlap on the device.  ``mats`` is a list of
     (row_ptr, col, val, shape, p).  Returns a list of (rank, row_ptr, col, val)
@@ -397,7 +399,7 @@ def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PA
         keep.append(arrs)
         ins[i] = cin
         ps[i] = int(p)
-    opt = _options(want_reduced, variant, 0, path)
+    opt = _options(want_reduced, variant, 0, path, autotune=autotune)
     outs = (CsrOut * max(n, 1))()
     ranks = (ctypes.c_int64 * max(n, 1))()
     codes = (ctypes.c_int * max(n, 1))()
@@ -413,7 +415,8 @@ def reduce_batch(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PA
     return res
 
 
-def reduce_batch_device(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PATH_AUTO):
+def reduce_batch_device(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, path=PATH_AUTO,
+                        autotune=False):
     """Reduce many matrices already on the device through the batch entry
     point (workers whose reductions overlap on the device).  ``mats`` is a
     list of (row_ptr, col, val, shape, p) with int64 / int32 / 16-bit CUDA
@@ -425,7 +428,7 @@ def reduce_batch_device(mats, want_reduced=False, variant=GEMM_AUTO, workers=0, 
     for i, (rp, c, v, shape, p) in enumerate(mats):
         ins[i] = CsrIn(int(shape[0]), int(shape[1]), int(c.numel()), rp.data_ptr(), c.data_ptr(), v.data_ptr())
         ps[i] = int(p)
-    opt = _options(want_reduced, variant, 1, path)
+    opt = _options(want_reduced, variant, 1, path, autotune=autotune)
     outs = (CsrOut * max(n, 1))()
     ranks = (ctypes.c_int64 * max(n, 1))()
     codes = (ctypes.c_int * max(n, 1))()
@@ -447,9 +450,10 @@ class Server:
         _check(self._lib.gbla_server_create(int(mem_budget), int(workers), ctypes.byref(self._h)),
                "gbla_server_create")
 
-    def submit(self, row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, path=PATH_AUTO):
+    def submit(self, row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, path=PATH_AUTO,
+               autotune=False):
         cin, _arrs = _csr_in(row_ptr, col, val, shape)   # copied by the server at submit
-        opt = _options(want_reduced, variant, 0, path)
+        opt = _options(want_reduced, variant, 0, path, autotune=autotune)
         t = ctypes.c_int64(0)
         _check(self._lib.gbla_server_submit(self._h, ctypes.byref(cin), int(p), ctypes.byref(opt), ctypes.byref(t)),
                "gbla_server_submit")
