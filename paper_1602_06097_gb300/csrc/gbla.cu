@@ -679,7 +679,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     uint16_t *d_val = nullptr;
     PivotInfo pi;
     Multiline ml;
-    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{}, XT{}, Cp{}, Yb{};
+    Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{}, XT{}, Cp{}, Yb{}, Zr{}, CtL{};
+    bool need_zr = false;   // the solve with B takes tensor-core leaves
     Compact SA, SB;
     uint16_t *Adiag = nullptr;
     uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
@@ -787,6 +788,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         }
     }
     STEP(split_scatter(dc, pi, A16, ldc, B16, ldd, C16, ldc, D16, ldd, mp, s));
+    // the solve with B (A^-1 B) also takes tensor-core leaves: Z_J as B-operand planes
+    need_zr = tc_leaves && (want_reduced || trsm_first) && npiv > 0 && n_d > 0;
+    if (need_zr && ((sparse && m_cd > 0) || !sparse)) STEP(planes_alloc(&Zr, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
     if (sparse && m_cd > 0 && npiv > 0) {
         // pivot rows as sparse operands, then the inverses of A's diagonal
         // blocks from their dense copies (on the side stream: the main stream
@@ -798,14 +802,14 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             CSTEP(cudaEventRecord(g_side.fork, s));
             CSTEP(cudaStreamWaitEvent(g_side.s, g_side.fork, 0));
             side_pending = true;
-            rc = upper_leaf_inverses_diag(Adiag, npiv, tc_leaf_w, Zt, mp, err, g_side.s);
+            rc = upper_leaf_inverses_diag(Adiag, npiv, tc_leaf_w, Zt, mp, err, g_side.s, Zr.ptr ? &Zr : nullptr);
             CSTEP(cudaEventRecord(g_side.join, g_side.s));
             STEP(rc);
         } else {
-            STEP(upper_leaf_inverses_diag(Adiag, npiv, tc_leaf_w, Zt, mp, err, s));
+            STEP(upper_leaf_inverses_diag(Adiag, npiv, tc_leaf_w, Zt, mp, err, s, Zr.ptr ? &Zr : nullptr));
         }
     }
-    if (!sparse && !trsm_first && m_cd > 0 && npiv > 0 && tc_leaves) {
+    if (!sparse && npiv > 0 && tc_leaves && ((!trsm_first && m_cd > 0) || need_zr)) {
         // inverses of A's diagonal blocks for the tensor-core leaf solves, on
         // the side stream while the main stream converts A and B
         STEP(planes_alloc(&Zt, round_up(npiv, tc_leaf_w), tc_leaf_w, 4, s));
@@ -813,11 +817,11 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             CSTEP(cudaEventRecord(g_side.fork, s));
             CSTEP(cudaStreamWaitEvent(g_side.s, g_side.fork, 0));
             side_pending = true;
-            rc = upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, err, g_side.s);
+            rc = upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, err, g_side.s, Zr.ptr ? &Zr : nullptr);
             CSTEP(cudaEventRecord(g_side.join, g_side.s));
             STEP(rc);
         } else {
-            STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, err, s));
+            STEP(upper_leaf_inverses(A16, ldc, npiv, tc_leaf_w, Zt, mp, err, s, Zr.ptr ? &Zr : nullptr));
         }
     }
     // digit planes of the operands the dense products read
@@ -851,7 +855,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     Adiag = nullptr;
     // the 2-multiline form of A drives the sparse leaf solves: those of the
     // first pass unless they run on the tensor cores, those of the second
-    if ((!sparse && !tc_leaves) || want_reduced || trsm_first) STEP(multiline_build(dc, pi, &ml, mp, s));
+    if ((!sparse && !tc_leaves) || ((want_reduced || trsm_first) && !Zr.ptr)) STEP(multiline_build(dc, pi, &ml, mp, s));
     tm.mark(s);  // 1
 
     // ---- new order: X = C A^-1, then D <- D - X B
@@ -872,7 +876,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         if (npiv > 0 && n_d > 0) {
             STEP(planes_alloc(&Xq, n_d, npiv, 2, s));
             STEP(planes_zero(Xq, s));
-            TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr};
+            if (Zr.ptr && !CtL.ptr) STEP(planes_alloc(&CtL, n_d, tc_leaf_w, 2, s));
+            TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr,
+                        Zr.ptr ? &Zr : nullptr, Zr.ptr ? &CtL : nullptr, Zr.ptr ? tc_leaf_w : 0};
             NvtxRange r("gbla.trsm");
             STEP(trsm_lower(T));
         }
@@ -934,7 +940,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
         if (!trsm_first) {
             STEP(planes_alloc(&Xq, n_d, npiv, 2, s));
             STEP(planes_zero(Xq, s));
-            TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr};
+            if (Zr.ptr && !CtL.ptr) STEP(planes_alloc(&CtL, n_d, tc_leaf_w, 2, s));
+            TrsmLower T{n_d, npiv, Bt16, ldbt, &ml, &Xq, &Arow, &mp, pvariant, err, s, &ctr,
+                        Zr.ptr ? &Zr : nullptr, Zr.ptr ? &CtL : nullptr, Zr.ptr ? tc_leaf_w : 0};
             STEP(trsm_lower(T));
         }
         if (rank_d > 0) {
@@ -1138,6 +1146,8 @@ cleanup:
     planes_free(&XT, s);
     planes_free(&Cp, s);
     planes_free(&Yb, s);
+    planes_free(&Zr, s);
+    planes_free(&CtL, s);
     compact_free(&SA, s);
     compact_free(&SB, s);
     dfree(Adiag, s);

@@ -306,9 +306,30 @@ int trsm_upper(const TrsmUpper &T)
     return trsm_upper_rec(T, 0, T.npiv);
 }
 
+// dst[r][c] <- the residue whose digits X holds at (r, c), r < rows, c < cols.
+__global__ void __launch_bounds__(256) planes_to_u16_kernel(Planes X, int64_t rows, int64_t cols, uint16_t *dst,
+                                                            int64_t ld, ModP mp)
+{
+    const int64_t r = blockIdx.x;   // one block per row
+    if (r >= rows) return;
+    for (int64_t c = threadIdx.x; c < cols; c += 256) {
+        const int v = 256 * __float2int_rz(__bfloat162float(*X.at(0, r, c))) +
+                      __float2int_rz(__bfloat162float(*X.at(1, r, c)));
+        dst[r * ld + c] = (uint16_t)(v < 0 ? v + (int)mp.p : v);
+    }
+}
+
 static int trsm_lower_rec(const TrsmLower &T, int64_t lo, int64_t hi)
 {
-    if (hi - lo <= LEAF) {
+    const bool tc_leaf = T.Zr && T.Ct && T.tc_leaf > 0;
+    if (tc_leaf && hi - lo <= T.tc_leaf) {
+        // X'_J = C'_J Z_J^T: digit planes of C'_J, then one product whose
+        // epilogue writes the digit planes of X'_J
+        const int w = (int)(hi - lo);
+        GBLA_TRY(to_planes(*T.Ct, T.mrows, w, T.C16 + lo, T.ldc, 0, false, nullptr, nullptr, *T.mp, T.s));
+        return modgemm_to_planes(*T.Ct, 0, *T.Zr, lo, *T.Xp, lo, T.mrows, w, w, *T.mp, T.err, T.s, T.ctr);
+    }
+    if (!tc_leaf && hi - lo <= LEAF) {
         const int64_t pairs = (T.mrows + 1) / 2;
         trsm_lower_leaf_kernel<<<(unsigned)((pairs + LEAF_WARPS - 1) / LEAF_WARPS), 32 * LEAF_WARPS,
                                  LEAF_SMEM_LOWER, T.s>>>(T.mrows, lo, (int)(hi - lo), T.ml->ptr, T.ml->pos, T.ml->val,
@@ -316,7 +337,7 @@ static int trsm_lower_rec(const TrsmLower &T, int64_t lo, int64_t hi)
         GBLA_CUDA_TRY(launch_check());
         return GBLA_OK;
     }
-    const int64_t mid = lo + round_up((hi - lo) / 2, LEAF);
+    const int64_t mid = lo + round_up((hi - lo) / 2, tc_leaf ? T.tc_leaf : LEAF);
     GBLA_TRY(trsm_lower_rec(T, mid, hi));
     // C'[:, lo:mid] -= X'[:, mid:hi] * A'[mid:hi, lo:mid],  A'[k][n] = A[n][k]
     GBLA_TRY(modgemm(*T.Xp, 0, mid, *T.Arow, lo, mid, T.C16 + lo, T.ldc, T.mrows, mid - lo, hi - mid, -1, *T.mp,
@@ -328,7 +349,13 @@ int trsm_lower(const TrsmLower &T)
 {
     if (T.mrows <= 0 || T.npiv <= 0) return GBLA_OK;
     GBLA_TRY(leaf_attrs());
-    return trsm_lower_rec(T, 0, T.npiv);
+    GBLA_TRY(trsm_lower_rec(T, 0, T.npiv));
+    if (T.Zr && T.Ct && T.tc_leaf > 0) {
+        // the tensor-core leaves wrote X' as digit planes only: its residues
+        planes_to_u16_kernel<<<(unsigned)T.mrows, 256, 0, T.s>>>(*T.Xp, T.mrows, T.npiv, T.C16, T.ldc, *T.mp);
+        GBLA_CUDA_TRY(launch_check());
+    }
+    return GBLA_OK;
 }
 
 // ================================================================ echelon
@@ -1156,7 +1183,7 @@ static int block_inverses(const uint16_t *A, int64_t lda, const int32_t *rmap, c
 }
 
 int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
-                        uint32_t *err, cudaStream_t s)
+                        uint32_t *err, cudaStream_t s, const Planes *Zr)
 {
     if (npiv <= 0) return GBLA_OK;
     const int64_t nleaves = (npiv + L - 1) / L;
@@ -1169,6 +1196,8 @@ int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, c
             ZN, L, Zt, mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
+    // ZN is nleaves L x L row-major: as an (nleaves L) x L matrix its rows are Zr's
+    if (rc == GBLA_OK && Zr) rc = to_planes(*Zr, nleaves * L, L, ZN, L, 0, false, nullptr, nullptr, mp, s);
     dfree(ZN, s);
     return rc;
 }
@@ -1181,7 +1210,7 @@ __global__ void iota_mod_kernel(int32_t *v, int64_t n, int L)
 }
 
 int upper_leaf_inverses_diag(const uint16_t *Adiag, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
-                             uint32_t *err, cudaStream_t s)
+                             uint32_t *err, cudaStream_t s, const Planes *Zr)
 {
     if (npiv <= 0) return GBLA_OK;
     const int64_t nleaves = (npiv + L - 1) / L;
@@ -1201,6 +1230,7 @@ int upper_leaf_inverses_diag(const uint16_t *Adiag, int64_t npiv, int L, const P
             ZN, L, Zt, mp);
         if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
     }
+    if (rc == GBLA_OK && Zr) rc = to_planes(*Zr, nleaves * L, L, ZN, L, 0, false, nullptr, nullptr, mp, s);
     dfree(cmap, s);
     dfree(ZN, s);
     return rc;

@@ -40,14 +40,16 @@ int trsm_upper(const TrsmUpper &T);
 // (A_JJ^-1)[k][j] for block J = [L q, L q + L), zero outside A.  For L >= 512
 // the wider levels of the inverses are tensor-core products (err: their
 // device status word).
+// With Zr (optional), the same inverses also as B-operand planes of Z_J
+// itself: Zr row J L + k, column j = Z_J[k][j] (the lower solve's leaves).
 int upper_leaf_inverses(const uint16_t *A16, int64_t lda, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
-                        uint32_t *err, cudaStream_t s);
+                        uint32_t *err, cudaStream_t s, const Planes *Zr = nullptr);
 
 // Leaf inverses as upper_leaf_inverses, from A's diagonal blocks alone:
 // Adiag (round_up(npiv, L) x L uint16) row k holds A[k][c] at column c % L for
 // the columns c of k's own block (sparse_build).
 int upper_leaf_inverses_diag(const uint16_t *Adiag, int64_t npiv, int L, const Planes &Zt, const ModP &mp,
-                             uint32_t *err, cudaStream_t s);
+                             uint32_t *err, cudaStream_t s, const Planes *Zr = nullptr);
 
 // X * A = C on the sparse path (tensor-core variant): the transposed solution
 // X^T is written to the A-operand planes XT (rows = pivots, K = rows of C).
@@ -74,7 +76,11 @@ struct TrsmSparse {
 };
 int trsm_sparse(const TrsmSparse &T);
 
-// X' * A^T = C' (A^T unit lower triangular), X' overwrites C'.
+// X' * A^T = C' (A^T unit lower triangular), X' overwrites C'.  Right-
+// looking from the last columns: a leaf J solves X'_J A'_JJ = C'_J, then
+// C'_{<J} -= X'_J A'_{J,<J} for the columns left of it.  With Zr and Ct a
+// leaf of width tc_leaf is X'_J = C'_J Z_J^T (Z_J = A_JJ^-1) on the tensor
+// cores, else the multiline leaf kernel solves it.
 struct TrsmLower {
     int64_t mrows, npiv;
     uint16_t *C16;
@@ -87,6 +93,9 @@ struct TrsmLower {
     uint32_t *err;
     cudaStream_t s;
     GemmCounters *ctr;
+    const Planes *Zr = nullptr;   // B-operand planes of the leaf inverses Z_J (rows npiv, K = tc_leaf)
+    const Planes *Ct = nullptr;   // A-operand scratch of mrows x tc_leaf
+    int tc_leaf = 0;
 };
 int trsm_lower(const TrsmLower &T);
 
