@@ -455,6 +455,42 @@ def format2_block(gbla, synth, spec, rp, c, v, d, stream, hbm_peak):
     return out
 
 
+def sparse_d_block(gbla, synth, stream):
+    """The echelon step's forward passes on a workload whose Schur complement
+    stays sparse: column panels against the sparse SGE (Alg. 3, Sec. 5.1)
+    and the automatic choice, one warm-up and three event-timed reductions
+    each; the results are compared on the device."""
+    import torch
+    name = "fl_sparse_d_40000x120000"
+    spec = synth.workload(name)
+    rp, c, v = synth.fl_matrix(spec)
+    d = (torch.from_numpy(rp).cuda(), torch.from_numpy(c).cuda(), torch.from_numpy(v.view(np.int16)).cuda())
+    out = {"workload": name, "rows": spec.m, "cols": spec.n, "nnz": int(len(c))}
+    keep = {}
+    for ech, label in ((1, "panels"), (2, "sge"), (0, "auto")):
+        gbla.reduce_device(*d, (spec.m, spec.n), spec.p, echelon=ech, stream=stream).free()
+        runs = []
+        for i in range(3):
+            r = gbla.reduce_device(*d, (spec.m, spec.n), spec.p, echelon=ech, stream=stream)
+            runs.append(r.stats)
+            if i == 2:
+                keep[label] = r
+            else:
+                r.free()
+        out[label] = {"ms_per_matrix": statistics.median(x["ms_total"] for x in runs),
+                      "ms_echelon": statistics.median(x["ms_echelon"] for x in runs),
+                      "forward_pass": ["", "panels", "sge"][int(runs[-1]["echelon_method"])],
+                      "d_density": runs[-1]["d_density"]}
+    ref = keep["panels"]
+    out["results_equal"] = all(
+        r.rank == ref.rank and r.nnz == ref.nnz and all(torch.equal(x, y) for x, y in zip(r.tensors(), ref.tensors()))
+        for r in keep.values())
+    for r in keep.values():
+        r.free()
+    out["sge_speedup_on_echelon"] = out["panels"]["ms_echelon"] / out["sge"]["ms_echelon"]
+    return out
+
+
 BATCH_SEED = 20160223   # batched mix (256 matrices)
 SERVE_SEED = 20160224   # serving pool
 
@@ -773,6 +809,7 @@ def main():
         hbm = peaks.get("hbm_gbs")
         for key, fn in (("format2", lambda: format2_block(gbla, synth, spec, rp, c, v, (d_rp, d_c, d_v), stream, hbm)),
                         ("fl_40000x60000", lambda: block_40000x60000(gbla, synth, peak, stream)),
+                        ("sparse_d", lambda: sparse_d_block(gbla, synth, stream)),
                         ("batched", lambda: batched_vs_plain(gbla, synth, a.batch)),
                         ("serving", lambda: serving(gbla, synth, [float(x) for x in a.serve_rates.split(",")],
                                                     a.serve_pool, a.serve_seconds))):

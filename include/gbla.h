@@ -110,7 +110,22 @@ typedef struct {
                           and density rounded to powers of two, tensor-core paths only) try
                           the candidates in turn, later calls take the fastest.  Every
                           candidate gives the same exact result. */
+    int echelon;       /* GBLA_ECHELON_*: forward pass of the echelon step of D' */
 } gbla_options;
+
+/* Forward pass of the echelon step of the Schur complement D'.  Column panels
+ * eliminate 128 columns at a time with tensor-core updates; SGE is the
+ * paper's structured Gaussian elimination with sparse pivot rows (Alg. 3,
+ * its parallel form in Sec. 5.1), for a D' that stays sparse: each warp
+ * reduces one row at a time by the sparse pivots found so far and claims the
+ * row's leading column when it has none.  If its pivot pool (about four times
+ * the nonzeros of D') fills up, the panels finish the pass.  AUTO samples the
+ * rows of D' and takes SGE when at most 30% of its entries are nonzero
+ * (measured 1.6-2.1x faster than the panels there), else the panels.  The
+ * result is the same either way. */
+#define GBLA_ECHELON_AUTO 0
+#define GBLA_ECHELON_PANELS 1
+#define GBLA_ECHELON_SGE 2
 
 /* Order of the FL steps.  The new order (Sec. 4.3) computes X = C*A^-1 and
  * D <- D - X*B, and A^-1*B only for the reduced form.  The original order
@@ -149,6 +164,10 @@ typedef struct {
     int64_t tune_state;          /* with autotune: 1 = a trial of one candidate, 2 = the bucket's
                                     fastest candidate, 3 = default while trials are in flight;
                                     0 without autotune */
+    int64_t echelon_method;      /* GBLA_ECHELON_PANELS or GBLA_ECHELON_SGE: the forward pass that
+                                    finished the echelon step */
+    double d_density;            /* with GBLA_ECHELON_SGE or _AUTO: nonzero share of D' on at most
+                                    4,096 evenly spaced rows (else -1) */
 } gbla_stats;
 
 /* ---- whole reduction -------------------------------------------------- */

@@ -616,6 +616,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     const bool ktimes = opt && opt->kernel_times && stats;
     const int leaf_req = opt ? opt->leaf_width : 0;
     const bool autotune = opt && opt->autotune;
+    const int echelon_opt = opt ? opt->echelon : GBLA_ECHELON_AUTO;
     if (variant < 0 || variant > GBLA_GEMM_U8) return GBLA_E_INVAL;
     if (path_req < GBLA_PATH_AUTO || path_req > GBLA_PATH_SPARSE) return GBLA_E_INVAL;
     // FP64 and U8 name the pipe of the Schur update on the dense path; every
@@ -632,6 +633,7 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     const int pvariant = alt_schur ? GBLA_GEMM_TCGEN05 : variant;
     if (leaf_req != 0 && leaf_req != 128 && leaf_req != 256 && leaf_req != 512 && leaf_req != 1024)
         return GBLA_E_INVAL;
+    if (echelon_opt < GBLA_ECHELON_AUTO || echelon_opt > GBLA_ECHELON_SGE) return GBLA_E_INVAL;
     const int64_t m = in->nrows, n = in->ncols, nnz = in->nnz;
     if (m < 0 || n < 0 || nnz < 0 || m >= (1ll << 31) || n >= (1ll << 31)) return GBLA_E_INVAL;
     if (m > 0 && !in->row_ptr) return GBLA_E_INVAL;
@@ -681,6 +683,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     Multiline ml;
     Planes At{}, Arow{}, Bt{}, Xp{}, Xq{}, RdT{}, XpdT{}, Zt{}, Ct{}, XT{}, Cp{}, Yb{}, Zr{}, CtL{};
     bool need_zr = false;   // the solve with B takes tensor-core leaves
+    double d_density = -1.0;
+    int sge_done = 0;
     Compact SA, SB;
     uint16_t *Adiag = nullptr;
     uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
@@ -929,7 +933,9 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     STEP(dalloc_t(&pcol, (size_t)m_cd + 1, s));
     {
         EchelonD E{m_cd, n_d, D16, ldd, is_piv_row, prow, pcol, &R16, &mp, pvariant, err, s, &ctr,
-                   tm.on ? tm.ev[7] : nullptr, back_leaf_width()};
+                   tm.on ? tm.ev[7] : nullptr, back_leaf_width(),
+                   echelon_opt == GBLA_ECHELON_SGE ? 1 : (echelon_opt == GBLA_ECHELON_AUTO ? 2 : 0),
+                   &d_density, &sge_done};
         NvtxRange r("gbla.echelon");
         STEP(echelon_d(E, &rank_d));
     }
@@ -1086,6 +1092,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
                                                                         : gather_group_m_default())
                                            : 0;
             stats->tune_state = tune.state;
+            stats->echelon_method = sge_done ? GBLA_ECHELON_SGE : GBLA_ECHELON_PANELS;
+            stats->d_density = d_density;
             stats->schur_mod_ops = schur_ops;
             stats->path = sparse ? GBLA_PATH_SPARSE : GBLA_PATH_DENSE;
             stats->list_a = SA.total;

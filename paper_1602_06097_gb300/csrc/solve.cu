@@ -1474,6 +1474,19 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
     do {                                              \
         if ((expr) != cudaSuccess) { rc = GBLA_E_CUDA; goto done; } \
     } while (0)
+    if (E.method == 1 || E.method == 2) {
+        // sparse SGE (for the automatic choice only on a sparse enough D'); if
+        // its pivot pool fills up, the panels finish the job
+        double dens = 0.0;
+        ESTEP(dprime_density(E, &dens));
+        if (E.density) *E.density = dens;
+        if (E.method == 1 || dens <= SGE_MAX_DENSITY) {
+            bool overflow = false;
+            ESTEP(sge_forward(E, dens, &rank, &overflow));
+            if (E.sge_completed) *E.sge_completed = overflow ? 0 : 1;
+            if (!overflow) goto backward;
+        }
+    }
     {
         ESTEP(dalloc_t(&W.lead, (size_t)m + 1, s));
         ESTEP(dalloc_t(&cand, (size_t)m + PANEL + 1, s));
@@ -1564,6 +1577,7 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         ESTEP(readback(&rank, rank_dev, sizeof(int64_t), s));
     }
     // ---- backward pass: RREF rows into R (pivot column order)
+backward:
     if (E.back_start) cudaEventRecord(E.back_start, s);
     if (rank > 0) {
         const int64_t ldr = E.ldd;

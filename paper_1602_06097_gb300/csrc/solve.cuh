@@ -116,7 +116,25 @@ struct EchelonD {
     GemmCounters *ctr;
     cudaEvent_t back_start = nullptr;   // optional: recorded when the backward pass begins
     int back_leaf = 0;                  // leaf rows of the back-substitution (power of two >= 128; 0: 128)
+    int method = 0;                     // forward pass: 0 column panels, 1 sparse SGE (sge.cu), 2 SGE when
+                                        // D' has at most SGE_MAX_DENSITY nonzeros, else panels
+    double *density = nullptr;          // out (methods 1, 2): nonzero share of D' before the pass
+    int *sge_completed = nullptr;       // out (methods 1, 2): 1 if SGE finished the forward pass
 };
 int echelon_d(const EchelonD &E, int64_t *rank_out);
+
+// Forward pass of the echelon step by structured Gaussian elimination with
+// sparse pivot rows (Alg. 3, parallel form of Sec. 5.1): on success prow,
+// pcol hold the pivots in ascending column order, their rows of D16 are
+// normalised and zero left of the lead, *rank their number.  *overflow: the
+// sparse pivot pool filled up; D16 then holds valid row combinations of D'
+// and the caller continues with the panel method.  *density: nonzero share
+// of D' on entry (dprime_density: counted on at most 4,096 evenly spaced rows).
+int sge_forward(const EchelonD &E, double density, int64_t *rank, bool *overflow);
+int dprime_density(const EchelonD &E, double *density);
+
+// Largest nonzero share of D' for which the automatic choice takes SGE
+// (measured: SGE 1.6-2.1x faster than the panels up to a share of 0.30).
+constexpr double SGE_MAX_DENSITY = 0.3;
 
 }  // namespace gbla

@@ -19,6 +19,7 @@ GBLA_OK = 0
 GEMM_AUTO, GEMM_TCGEN05, GEMM_SIMT, GEMM_FP64, GEMM_U8 = 0, 1, 2, 3, 4
 PATH_AUTO, PATH_DENSE, PATH_SPARSE = 0, 1, 2
 ORDER_NEW, ORDER_TRSM_FIRST = 0, 1
+ECHELON_AUTO, ECHELON_PANELS, ECHELON_SGE = 0, 1, 2
 
 EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_version",
            "gbla_modmatmul", "gbla_pivots", "gbla_multiline", "gbla_pivots_noalloc",
@@ -43,13 +44,13 @@ class Options(ctypes.Structure):
     _fields_ = [("want_reduced", ctypes.c_int), ("gemm_variant", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("panel_width", ctypes.c_int),
                 ("path", ctypes.c_int), ("leaf_width", ctypes.c_int), ("kernel_times", ctypes.c_int),
-                ("fl_order", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("fl_order", ctypes.c_int), ("autotune", ctypes.c_int), ("echelon", ctypes.c_int)]
 
 
 def _options(want_reduced, variant, device_ptrs, path=PATH_AUTO, leaf=0, kernel_times=False, order=0,
-             autotune=False):
+             autotune=False, echelon=0):
     return Options(1 if want_reduced else 0, int(variant), int(device_ptrs), 0, int(path), int(leaf),
-                   1 if kernel_times else 0, int(order), 1 if autotune else 0)
+                   1 if kernel_times else 0, int(order), 1 if autotune else 0, int(echelon))
 
 
 class Stats(ctypes.Structure):
@@ -64,7 +65,8 @@ class Stats(ctypes.Structure):
                 ("tc_launches", ctypes.c_int64), ("gather_launches", ctypes.c_int64),
                 ("tc_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("tc_mod_ops", ctypes.c_double),
                 ("tc_pair_launches", ctypes.c_int64), ("gather_group_m", ctypes.c_int64),
-                ("tune_state", ctypes.c_int64)]
+                ("tune_state", ctypes.c_int64), ("echelon_method", ctypes.c_int64),
+                ("d_density", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -226,7 +228,7 @@ class HostResult:
 
 
 def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
-                path=PATH_AUTO, leaf=0, order=ORDER_NEW, autotune=False) -> HostResult:
+                path=PATH_AUTO, leaf=0, order=ORDER_NEW, autotune=False, echelon=ECHELON_AUTO) -> HostResult:
     """Reduce a host CSR matrix; the result stays in library-owned host memory
     (see HostResult).  Page-locked inputs copy to the device fastest.
     ``path`` is PATH_AUTO, PATH_DENSE or PATH_SPARSE, ``leaf`` the leaf width
@@ -237,7 +239,7 @@ def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AU
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.uint16)
     cin = CsrIn(m, n, int(len(col)), row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data)
-    opt = _options(want_reduced, variant, 0, path, leaf, order=order, autotune=autotune)
+    opt = _options(want_reduced, variant, 0, path, leaf, order=order, autotune=autotune, echelon=echelon)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()
@@ -248,11 +250,11 @@ def reduce_host(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AU
 
 
 def reduce(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stats=False, stream=None,
-           path=PATH_AUTO, leaf=0, order=ORDER_NEW, autotune=False):
+           path=PATH_AUTO, leaf=0, order=ORDER_NEW, autotune=False, echelon=ECHELON_AUTO):
     """Reduce a host CSR matrix.  Returns (rank, row_ptr, col, val) as numpy
     arrays the caller owns (and a stats dict when ``stats``)."""
     h = reduce_host(row_ptr, col, val, shape, p, want_reduced=want_reduced, variant=variant, stream=stream,
-                    path=path, leaf=leaf, order=order, autotune=autotune)
+                    path=path, leaf=leaf, order=order, autotune=autotune, echelon=echelon)
     try:
         res = (h.rank, h.row_ptr.copy(), h.col.copy(), h.val.copy())
         st = h.stats
@@ -341,14 +343,15 @@ class _CudaArray:
 
 
 def reduce_device(row_ptr, col, val, shape, p, want_reduced=False, variant=GEMM_AUTO, stream=None,
-                  path=PATH_AUTO, leaf=0, kernel_times=False, order=ORDER_NEW, autotune=False):
+                  path=PATH_AUTO, leaf=0, kernel_times=False, order=ORDER_NEW, autotune=False,
+                  echelon=ECHELON_AUTO):
     """Reduce a CSR matrix already on the device (torch CUDA tensors: int64
     row_ptr, int32 col, int16/uint16 val).  Returns a DeviceResult whose
     arrays stay in device memory."""
     lib = load()
     m, n = int(shape[0]), int(shape[1])
     cin = CsrIn(m, n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
-    opt = _options(want_reduced, variant, 1, path, leaf, kernel_times, order, autotune)
+    opt = _options(want_reduced, variant, 1, path, leaf, kernel_times, order, autotune, echelon)
     out = CsrOut()
     rank = ctypes.c_int64(0)
     st = Stats()

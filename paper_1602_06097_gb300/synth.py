@@ -344,6 +344,12 @@ WORKLOADS = {
     # pivot columns) in diagonal blocks of 4,096 with 5% cross-block entries.
     "fl_150000x200000": FLSpec(m=150000, n=200000, npiv=120000, density=0.005, run_len=(4, 32),
                                share=0.9, band=2048, block=4096, cross=0.05, seed=20160221),
+    # 40,000 x 120,000, 15,000 pivots, 0.02% density (24 entries per row in
+    # runs of 1-3): few pivots and short rows, so that the Schur complement
+    # stays sparse (about 4% of its entries nonzero) -- the case the sparse
+    # SGE of the echelon step is for.
+    "fl_sparse_d_40000x120000": FLSpec(m=40000, n=120000, npiv=15000, density=0.0002, run_len=(1, 3),
+                                       seed=1602),
 }
 
 

@@ -127,3 +127,11 @@ def test_a_failed_request_does_not_disturb_the_server(mat):
         st = srv.stats()
         assert st["failed"] == 1 and st["completed"] == 4
     assert gbla.device_bytes_in_use() == base
+
+
+def test_every_allocation_failure_of_a_reduction_with_the_sparse_echelon_pass():
+    spec = synth.FLSpec(m=3000, n=9000, npiv=1500, density=0.002, run_len=(1, 4), seed=1501)
+    rp, c, v = synth.fl_matrix(spec)
+    n, res = sweep(lambda: gbla.reduce(rp, c, v, (spec.m, spec.n), spec.p, echelon=gbla.ECHELON_SGE))
+    assert n > 10
+    same(res, oracle.echelon(spec.m, spec.n, spec.p, rp, c, v))

@@ -56,7 +56,7 @@ const int cudaSuccess = 0, cudaStreamNonBlocking = 1;
 #define GBLA_E_CANCELLED 7
 struct gbla_csr_in { int64_t nrows, ncols, nnz; const int64_t *row_ptr; const int32_t *col; const uint16_t *val; };
 struct gbla_csr_out { int64_t nrows, ncols, nnz; int64_t *row_ptr; int32_t *col; uint16_t *val; int on_device; };
-struct gbla_options { int want_reduced, gemm_variant, device_ptrs, panel_width, path, leaf_width, kernel_times, fl_order, autotune; };
+struct gbla_options { int want_reduced, gemm_variant, device_ptrs, panel_width, path, leaf_width, kernel_times, fl_order, autotune, echelon; };
 #define GBLA_GEMM_AUTO 0
 #define GBLA_GEMM_TCGEN05 1
 #define GBLA_GEMM_SIMT 2
