@@ -491,6 +491,43 @@ def sparse_d_block(gbla, synth, stream):
     return out
 
 
+def wide_limbs_block(gbla, stream, peak):
+    """The exact modular product for 32-bit coefficients (four bf16 digits per
+    residue, seven fp32 accumulators) on an 8,192^3 product with p = 2^31 - 1,
+    against the 16-bit product (two digits) on the same shape with p = 65521:
+    each call event-timed including its digit-plane conversions, after a
+    warm-up.  Work: 16 (32-bit) or 4 (16-bit) digit products per modular
+    multiply-add, 2 flops each."""
+    import torch
+    n = 8192
+    out = {"shape": [n, n, n]}
+    for label, p, dt, fn, prods in (("u32_p2147483647", 2147483647, torch.int32, gbla.modmatmul32, 16),
+                                    ("u16_p65521", 65521, torch.int16, gbla.modmatmul, 4)):
+        hi = min(p, 2 ** 31 - 1)
+        A = torch.randint(0, hi, (n, n), dtype=torch.int64, device="cuda")
+        B = torch.randint(0, hi, (n, n), dtype=torch.int64, device="cuda")
+        if dt == torch.int16:
+            A, B = (A.to(torch.int32).to(torch.int16)), (B.to(torch.int32).to(torch.int16))
+        else:
+            A, B = A.to(torch.int32), B.to(torch.int32)
+        C = torch.zeros((n, n), dtype=dt, device="cuda")
+        fn(A, B, C, p, stream=stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(3):
+            ev0.record(stream)
+            fn(A, B, C, p, stream=stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        t = min(ms) / 1e3
+        out[label] = {"ms": t * 1e3, "modular_tops": n ** 3 / t / 1e12,
+                      "bf16_tflops": 2 * prods * n ** 3 / t / 1e12, "frac_of_bf16_peak": 2 * prods * n ** 3 / t / 1e12 / peak}
+        del A, B, C
+    torch.cuda.empty_cache()
+    return out
+
+
 BATCH_SEED = 20160223   # batched mix (256 matrices)
 SERVE_SEED = 20160224   # serving pool
 
@@ -810,6 +847,7 @@ def main():
         for key, fn in (("format2", lambda: format2_block(gbla, synth, spec, rp, c, v, (d_rp, d_c, d_v), stream, hbm)),
                         ("fl_40000x60000", lambda: block_40000x60000(gbla, synth, peak, stream)),
                         ("sparse_d", lambda: sparse_d_block(gbla, synth, stream)),
+                        ("wide_limbs", lambda: wide_limbs_block(gbla, stream, peak)),
                         ("batched", lambda: batched_vs_plain(gbla, synth, a.batch)),
                         ("serving", lambda: serving(gbla, synth, [float(x) for x in a.serve_rates.split(",")],
                                                     a.serve_pool, a.serve_seconds))):

@@ -289,6 +289,19 @@ int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t l
                    const uint16_t *B, int64_t ldb, uint16_t *C, int64_t ldc,
                    uint32_t p, int sign, int variant, void *stream);
 
+/* The exact modular product for 32-bit coefficients (wider limbs): C <- (C +
+ * sign * A * B) mod p for a prime 2 < p < 2^31, A: M x K, B: K x N, C: M x N
+ * row-major uint32 device arrays (leading dimensions in elements), entries in
+ * [0, p).  Each residue, in balanced form, is split into four 8-bit digits
+ * exact in bf16 (the coefficient representations of Sec. 2: uint16 for 16-bit
+ * primes, uint32 for 32-bit ones); the sixteen digit products of a pair land
+ * in seven fp32 tensor-memory accumulators by digit position, exact over
+ * k-blocks of 256, and are reduced mod p in 64-bit integers.  tcgen05 only
+ * (GBLA_E_UNSUPPORTED elsewhere).  Scratch on `stream`; synchronises it. */
+int gbla_modmatmul32(int64_t M, int64_t N, int64_t K, const uint32_t *A, int64_t lda,
+                     const uint32_t *B, int64_t ldb, uint32_t *C, int64_t ldc,
+                     uint32_t p, int sign, void *stream);
+
 /* Issue-rate microbenchmark of a legacy tensor-core pipe: variant
  * GBLA_GEMM_FP64 (mma.sync m8n8k4 f64) or GBLA_GEMM_U8 (mma.sync m16n8k32
  * u8).  Every warp runs eight independent accumulator chains on operands held

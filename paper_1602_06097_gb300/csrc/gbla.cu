@@ -1296,6 +1296,16 @@ int gbla_modmatmul(int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t l
     return rc;
 }
 
+int gbla_modmatmul32(int64_t M, int64_t N, int64_t K, const uint32_t *A, int64_t lda, const uint32_t *B,
+                     int64_t ldb, uint32_t *C, int64_t ldc, uint32_t p, int sign, void *stream) {
+    if (M < 0 || N < 0 || K < 0 || p < 3 || p >= (1u << 31) || !is_prime(p) || (sign != 1 && sign != -1))
+        return GBLA_E_INVAL;
+    if (M == 0 || N == 0 || K == 0) return GBLA_OK;
+    if (!A || !B || !C || lda < K || ldb < N || ldc < N) return GBLA_E_INVAL;
+    GBLA_TRY(check_device());
+    return modmatmul32(M, N, K, A, lda, B, ldb, C, ldc, p, sign, (cudaStream_t)stream);
+}
+
 int gbla_pipe_peak(int variant, double *tops, void *stream) {
     if (!tops || (variant != GBLA_GEMM_FP64 && variant != GBLA_GEMM_U8)) return GBLA_E_INVAL;
     GBLA_TRY(check_device());

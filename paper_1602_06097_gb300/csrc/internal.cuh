@@ -133,6 +133,12 @@ int modgemm_alt(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, 
                 uint16_t *C, int64_t ldc, int64_t M, int64_t N, int64_t K, int sign, const ModP &mp, int variant,
                 cudaStream_t s, const int32_t *c_rows, const int32_t *row_lead);
 
+// C <- (C + sign * A * B) mod p for residues of a prime p < 2^31 (uint32,
+// row-major, device): four balanced 8-bit digits per residue in bf16 and
+// seven fp32 TMEM accumulators (modgemm.cu); synchronises s.
+int modmatmul32(int64_t M, int64_t N, int64_t K, const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
+                uint32_t *C, int64_t ldc, uint32_t p, int sign, cudaStream_t s);
+
 // Issue-rate microbenchmark of the FP64 or U8 mma.sync pipe (ops of the
 // instruction per second, in units of 1e12), timed with events on s.
 int pipe_peak(int variant, double *tops, cudaStream_t s);

@@ -1263,6 +1263,250 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
+// ===================================================================
+// Wider limbs: residues of primes p < 2^31 (32-bit coefficients)
+// ===================================================================
+// A residue in balanced form s (|s| <= (p-1)/2 < 2^30) is split into four
+// balanced 8-bit digits s = d0 + 256 d1 + 65536 d2 + 2^24 d3, each exact in
+// bf16.  Then
+//     a * b = sum_{i,j} a_i b_j 256^(i+j),
+// and seven fp32 TMEM accumulators P_t collect the digit products with
+// i + j = t.  At most four products of magnitude <= 2^14 land in one P_t
+// per k, so over a k-block of 256 every partial sum stays below 2^24 and is
+// exact.  The drain forms x = sum_t (P_t + 2^24) * (256^t mod p), a
+// nonnegative integer below 2^59, reduces it with one Barrett step in 64-bit
+// integers and removes the constant sum_t 2^24 * (256^t mod p) mod p.
+// Tiles are 128 x 64 (7 x 64 = 448 TMEM columns, one buffer: the MMA issuer
+// waits for the drain between k-blocks); both operand sets hold 4 digit
+// planes, a 4-stage ring of 48 KB stages ([A01 | A23 | B01 | B23]).
+constexpr int W_BN = 64;
+constexpr int W_KSTEPS_PER_BLOCK = 256 / BK;
+constexpr int W_A_BOX = 128 * 128, W_B_BOX = W_BN * 128;
+constexpr int W_STAGE_BYTES = 2 * W_A_BOX + 2 * W_B_BOX;
+constexpr int W_SMEM_BYTES = STAGES * W_STAGE_BYTES + BAR_BYTES + 1024;
+constexpr uint32_t IDESC_W = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(W_BN >> 3) << 17) |
+                             ((uint32_t)(BM >> 4) << 24);
+
+struct WArgs {
+    int64_t M, N, K;
+    uint32_t *C;
+    int64_t ldc;
+    int sign;
+    uint32_t p;
+    uint64_t w[7];   // 256^t mod p
+    uint64_t mu;     // floor((2^64 - 1) / p)
+    uint32_t bias;   // (sum_t 2^24 * w[t]) mod p
+    uint32_t *err;
+};
+
+__device__ __forceinline__ void mma_w(uint32_t d, uint32_t a, uint32_t b, uint32_t hi, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p, e;\n\t.reg .b32 r;\n\t.reg .b64 x, y;\n\t"
+                 "elect.sync r|e, 0xffffffff;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "mov.b64 x, {%1, %3};\n\t"
+                 "mov.b64 y, {%2, %3};\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], x, y, %5, p;\n\t}" ::"r"(d),
+                 "r"(a), "r"(b), "r"(hi), "r"(acc), "r"(IDESC_W)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    modgemm32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const WArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + STAGES * W_STAGE_BYTES);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + STAGES;
+    uint64_t *accf = bars + 2 * STAGES;
+    uint64_t *acce = accf + 1;
+    uint64_t *done = acce + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(acce, EPI_WARPS);
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tcgen05_fence_before();
+    __syncthreads();
+    tcgen05_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t num_m = (g.M + BM - 1) / BM, num_n = (g.N + W_BN - 1) / W_BN, num_tiles = num_m * num_n;
+    const int ksteps = (int)(((g.K + BK - 1) / BK + 3) & ~int64_t(3));   // whole rounds of the 4-stage ring
+    const int kblocks = (ksteps + W_KSTEPS_PER_BLOCK - 1) / W_KSTEPS_PER_BLOCK;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[STAGES];
+            uint32_t issued_parity[STAGES];
+            for (int s = 0; s < STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                const int ay = (int)((t / num_n) * BM), by = (int)((t % num_n) * W_BN);
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                    uint8_t *st = tiles + stage * W_STAGE_BYTES;
+                    const int x = ks * 4 * BK;   // chunk ks of a 4-plane row
+                    mbar_expect_tx(&full[stage], W_STAGE_BYTES);
+                    tma_load_2d(st, &tmA, &full[stage], x, ay);
+                    tma_load_2d(st + W_A_BOX, &tmA, &full[stage], x + 2 * BK, ay);
+                    tma_load_2d(st + 2 * W_A_BOX, &tmB, &full[stage], x, by);
+                    tma_load_2d(st + 2 * W_A_BOX + W_B_BOX, &tmB, &full[stage], x + 2 * BK, by);
+                    issued[stage] = 1;
+                    issued_parity[stage] = phase;
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+            }
+            for (int s = 0; s < STAGES; ++s) {   // no copies left in flight
+                if (!issued[s]) continue;
+                const uint32_t addr = smem_u32(&full[s]);
+                const long long start = clock64();
+                while (!mbar_try_wait(addr, issued_parity[s])) {
+                    if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                        dev_fail(g.err, DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (whole warp, elected lane issues)
+        uint32_t phase = 0, kbc = 0;
+        bool ok = true;
+        const uint64_t d0 = make_sdesc(smem_u32(tiles));
+        const uint32_t dhi = (uint32_t)(d0 >> 32), lo0 = (uint32_t)d0;
+        constexpr uint32_t SB = W_STAGE_BYTES >> 4, AB = W_A_BOX >> 4, BB = W_B_BOX >> 4;
+        for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            for (int kb = 0; kb < kblocks && ok; ++kb, ++kbc) {
+                if (!mbar_wait_warp(acce, (kbc & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                tcgen05_fence_after();
+                const int ks_beg = kb * W_KSTEPS_PER_BLOCK, ks_end = min(ksteps, ks_beg + W_KSTEPS_PER_BLOCK);
+                bool first = true;
+                for (int ks = ks_beg; ks < ks_end && ok; ks += STAGES) {
+#pragma unroll
+                    for (int st = 0; st < STAGES; ++st) {
+                        if (!mbar_wait_warp(&full[st], phase, abort_flag, g.err)) { ok = false; break; }
+                        const uint32_t a = lo0 + st * SB, b = a + 2 * AB;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {   // the two 16-wide halves of the chunk
+                            bool seen[7] = {false, false, false, false, false, false, false};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    // plane q of a set: box q / 2, byte offset 64 (q % 2) + 32 h
+                                    const uint32_t ad = a + (i >> 1) * AB + (i & 1) * 4 + 2 * h;
+                                    const uint32_t bd = b + (j >> 1) * BB + (j & 1) * 4 + 2 * h;
+                                    const int tt = i + j;
+                                    mma_w(tmem + (uint32_t)(tt * W_BN), ad, bd, dhi,
+                                          (first && h == 0 && !seen[tt]) ? 0u : 1u);
+                                    seen[tt] = true;
+                                }
+                        }
+                        first = false;
+                        commit_elected<false, true>(&empty[st]);
+                    }
+                    phase ^= 1u;
+                }
+                if (ok) commit_elected<false, true>(accf);
+            }
+        }
+        commit_elected<false, false>(done);
+        const uint32_t addr = smem_u32(done);
+        const long long start = clock64();
+        while (!__any_sync(0xffffffffu, mbar_try_wait(addr, 0))) {
+            if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                if (lane == 0) dev_fail(g.err, DEV_ERR_TIMEOUT);
+                break;
+            }
+        }
+    } else {
+        // ---------------- drain: warps 2..9, lane quarter warp % 4, half of the 64 columns each
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const int row_in_tile = quarter * 32 + lane;
+        const int64_t P = g.p;
+        uint32_t kbc = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            uint32_t run[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) run[i] = 0;
+            for (int kb = 0; kb < kblocks; ++kb, ++kbc) {
+                if (!mbar_wait(accf, kbc & 1u, abort_flag, g.err)) { ok = false; break; }
+                tcgen05_fence_after();
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    uint64_t v[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = 0;
+#pragma unroll
+                    for (int tt = 0; tt < 7; ++tt) {
+                        float f[16];
+                        tmem_ld16(tb + (uint32_t)(tt * W_BN + c * 16), f);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            v[e] += (uint64_t)(__float2int_rn(f[e]) + (1 << 24)) * g.w[tt];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        // x mod p (Barrett: the quotient estimate is low by at most 2)
+                        const uint64_t x = v[e];
+                        uint64_t r = x - __umul64hi(x, g.mu) * (uint64_t)P;
+                        r -= r >= (uint64_t)P ? (uint64_t)P : 0;
+                        r -= r >= (uint64_t)P ? (uint64_t)P : 0;
+                        // remove the bias, add the running residue
+                        r += (uint64_t)run[c * 16 + e] + (uint64_t)P - g.bias;
+                        r -= r >= (uint64_t)P ? (uint64_t)P : 0;
+                        r -= r >= (uint64_t)P ? (uint64_t)P : 0;
+                        run[c * 16 + e] = (uint32_t)r;
+                    }
+                }
+                tcgen05_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce);
+            }
+            if (!ok) break;
+            const int64_t row = (t / num_n) * BM + row_in_tile;
+            const int64_t col0 = (t % num_n) * W_BN + half * 32;
+            if (row < g.M) {
+                uint32_t *crow = g.C + row * g.ldc + col0;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    if (col0 + e >= g.N) break;
+                    const uint64_t cur = crow[e], rv = run[e];
+                    const uint64_t o = g.sign > 0 ? cur + rv : cur + (uint64_t)P - rv;
+                    crow[e] = (uint32_t)(o % (uint64_t)P);
+                }
+            }
+        }
+    }
+    tcgen05_fence_before();
+    __syncthreads();
+    tcgen05_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
@@ -1653,6 +1897,80 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
     }
     if (ctr) ctr->tc_launches += 1;
     return GBLA_OK;
+}
+
+// ===================================================================
+// Wider limbs: host side of the product for primes p < 2^31
+// ===================================================================
+// dst(h, r, k) <- digit h of the balanced residue src[r][k] (transposed: of
+// src[k][r]) for r < R, k < Kc; zero elsewhere in the padded rectangle.
+__global__ void __launch_bounds__(256) to_planes32_kernel(Planes dst, int64_t R, int64_t Kc,
+                                                          const uint32_t *__restrict__ src, int64_t lds,
+                                                          int transposed, uint32_t p)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= dst.rows * dst.kp) return;
+    const int64_t r = idx / dst.kp, k = idx % dst.kp;
+    uint32_t a = 0;
+    if (r < R && k < Kc) a = transposed ? src[k * lds + r] : src[r * lds + k];
+    int64_t x = a > (p >> 1) ? (int64_t)a - (int64_t)p : (int64_t)a;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int d = h < 3 ? (int)((((x % 256) + 256 + 128) % 256) - 128) : (int)x;
+        *dst.at(h, r, k) = i2bf(d);
+        x = (x - d) / 256;
+    }
+}
+
+int modmatmul32(int64_t M, int64_t N, int64_t K, const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
+                uint32_t *C, int64_t ldc, uint32_t p, int sign, cudaStream_t s)
+{
+    if (!tc_supported()) return GBLA_E_UNSUPPORTED;
+    Planes Ap{}, Bp{};
+    uint32_t *err = nullptr;
+    int rc = dalloc_t(&err, 4, s);
+    if (rc == GBLA_OK) rc = planes_alloc(&Ap, M, K, 4, s);
+    if (rc == GBLA_OK) rc = planes_alloc(&Bp, N, K, 4, s);
+    if (rc == GBLA_OK && cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK) {
+        to_planes32_kernel<<<(unsigned)((Ap.rows * Ap.kp + 255) / 256), 256, 0, s>>>(Ap, M, K, A, lda, 0, p);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    if (rc == GBLA_OK) {
+        to_planes32_kernel<<<(unsigned)((Bp.rows * Bp.kp + 255) / 256), 256, 0, s>>>(Bp, N, K, B, ldb, 1, p);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    CUtensorMap ma, mb;
+    if (rc == GBLA_OK) rc = make_map(&ma, Ap, tc::BM);
+    if (rc == GBLA_OK) rc = make_map(&mb, Bp, tc::W_BN);
+    static const cudaError_t attr = cudaFuncSetAttribute(tc::modgemm32_kernel,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tc::W_SMEM_BYTES);
+    if (rc == GBLA_OK && attr != cudaSuccess) rc = GBLA_E_CUDA;
+    if (rc == GBLA_OK) {
+        tc::WArgs g{};
+        g.M = M; g.N = N; g.K = K;
+        g.C = C; g.ldc = ldc; g.sign = sign; g.p = p; g.err = err;
+        uint64_t w = 1, bias = 0;
+        for (int t = 0; t < 7; ++t) {
+            g.w[t] = w;
+            bias = (bias + ((uint64_t)1 << 24) % p * w) % p;
+            w = (w * 256u) % p;
+        }
+        g.mu = ~0ull / p;
+        g.bias = (uint32_t)bias;
+        const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::W_BN - 1) / tc::W_BN);
+        const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
+        tc::modgemm32_kernel<<<grid, tc::THREADS, tc::W_SMEM_BYTES, s>>>(ma, mb, g);
+        if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == GBLA_OK) rc = GBLA_E_CUDA;
+    uint32_t herr = 0;
+    if (rc == GBLA_OK && readback(&herr, err, 4, s) == GBLA_OK) rc = map_dev_err(herr);
+    planes_free(&Ap, s);
+    planes_free(&Bp, s);
+    dfree(err, s);
+    cudaStreamSynchronize(s);
+    return rc;
 }
 
 // Grouped product, SIMT variant: one launch of the reference kernel per

@@ -26,7 +26,7 @@ EXPORTS = ["gbla_reduce", "gbla_reduce_ex", "gbla_free", "gbla_strerror", "gbla_
            "gbla_selftest_wait_timeout", "gbla_reduce_batch", "gbla_server_create", "gbla_server_submit",
            "gbla_server_wait", "gbla_server_wait_ex", "gbla_server_poll", "gbla_server_cancel", "gbla_server_get_stats", "gbla_server_destroy",
            "gbla_decode_format2", "gbla_decode_format2_ex", "gbla_spmm", "gbla_pipe_peak",
-           "gbla_selftest_fail_alloc_after", "gbla_device_bytes_in_use"]
+           "gbla_selftest_fail_alloc_after", "gbla_device_bytes_in_use", "gbla_modmatmul32"]
 
 
 class CsrIn(ctypes.Structure):
@@ -130,6 +130,8 @@ def load():
         lib.gbla_version.restype = i32
         lib.gbla_modmatmul.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, u32, i32, i32, vp]
         lib.gbla_modmatmul.restype = i32
+        lib.gbla_modmatmul32.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, u32, i32, vp]
+        lib.gbla_modmatmul32.restype = i32
         lib.gbla_pivots.argtypes = [ctypes.POINTER(CsrIn), u32, vp, ctypes.POINTER(i64), vp]
         lib.gbla_spmm.restype = i32
         lib.gbla_selftest_fail_alloc_after.argtypes = [i64]
@@ -551,6 +553,18 @@ def pipe_peak(variant, stream=None):
     out = ctypes.c_double(0.0)
     _check(lib.gbla_pipe_peak(int(variant), ctypes.byref(out), _stream_ptr(stream)), "gbla_pipe_peak")
     return out.value
+
+
+def modmatmul32(A, B, C, p, sign=-1, stream=None):
+    """C <- (C + sign*A*B) mod p in place for a prime p < 2^31; A, B, C are 2-D
+    row-major CUDA tensors of 32-bit values (int32 views of uint32 residues)."""
+    lib = load()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K2 == K and tuple(C.shape) == (M, N)
+    rc = lib.gbla_modmatmul32(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                              C.data_ptr(), C.stride(0), int(p), int(sign), _stream_ptr(stream))
+    _check(rc, "gbla_modmatmul32")
 
 
 def spmm(X, S_row_ptr, S_col, S_val, N, C, p, sign=-1, x_lead=None, stream=None):
