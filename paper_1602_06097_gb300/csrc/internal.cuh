@@ -74,8 +74,8 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
 // sparse_build (sparse.cu): for 128-column tile t, the rows with a nonzero in
 // the tile are kidx[koff[t] .. koff[t+1]) (ascending, padded with KIDX_PAD to
 // a multiple of 128), and the tile restricted to them is stored as B-operand
-// digit planes, chunk-major (list entries 32 q .. 32 q + 31: 128 rows of 128
-// bf16 at planes + 128 * 128 * q).
+// digit planes, chunk-major (list entries 32 q .. 32 q + 31: 128 rows of 64
+// bf16, hi digits then lo, at planes + 128 * 64 * q).
 constexpr int32_t KIDX_PAD = 0x7F7F7F7F;
 struct Compact {
     int64_t ntiles = 0;        // column tiles

@@ -892,9 +892,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // C[r, c] <- (C[r, c] + sign * sum_j X[r, j] * S[j, c]) mod p for the output
 // column tiles nt0 .. of a compacted sparse operand S (sparse.cu): the rows j
 // of S with a nonzero in tile t are listed in kidx[koff[t] .. koff[t + 1])
-// (ascending, padded to whole ring rounds of 128 entries with KIDX_PAD), and S
+// (ascending, padded to a multiple of 128 entries with KIDX_PAD), and S
 // restricted to those rows and the tile's 128 columns is stored densely as
-// B-operand digit planes, 32 list entries per 128 x 128-bf16 chunk.  The
+// the two digit planes (hi, lo) of its residues, 32 list entries per
+// 128 x 64-bf16 chunk.  The
 // product's K is the list: K-compaction keeps the tensor cores on the
 // nonzero part of S.  X is read through its transpose: row j of the
 // A-operand plane set XT holds column j of X, so the 128 values of a row tile
@@ -903,17 +904,63 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // (cp.async), while one thread loads the compacted S chunk by TMA.  Rows of X
 // are ascending by lead (first nonzero column), so a tile skips the list
 // entries left of its first row's lead.
-// Warp roles: 0 TMA producer of the compacted operand, 1 MMA issuer, 2..5
-// drain (one per TMEM lane quarter, all 128 columns), 6..9 gather (warp
-// 6 + s fills ring slot s).
-constexpr int G_EPI_WARPS = 4;
-constexpr int G_GATHER_WARPS = STAGES;
+// The four digit products go to four fp32 accumulators,
+//     a*b = 65536*(ah*bh) + 256*(ah*bl + al*bh) + al*bl   (balanced digits),
+// H, M1 = sum ah*bl, M2 = sum al*bh and L (all 512 TMEM columns, one buffer:
+// the MMA issuer waits for the drain between k-blocks).  Each takes one
+// product of at most 2^14 per list entry, so a k-block of 1,024 entries
+// keeps every sum within 2^24 and exact: the drain runs once per 32 k-steps.
+// Without the 256*b mod p planes a stage is 32 KB (16 KB of gathered X^T,
+// 16 KB of S), so the ring holds six stages and six copies of X^T rows are in
+// flight.
+// Warp roles: 0 TMA producer of the compacted operand, 1 MMA issuer, 2..9
+// drain (two per TMEM lane quarter, 64 columns each), 10..15 gather (warp
+// 10 + s fills ring slot s).
+constexpr int G_STAGES = 6;
+constexpr int G_KSTEPS_PER_BLOCK = 1024 / BK;
+constexpr int G_A_BYTES = 128 * 128;                 // 32 entries x 128 rows x 2 planes
+constexpr int G_B_BYTES = 128 * 128;                 // 128 columns x 32 entries x 2 planes
+constexpr int G_STAGE_BYTES = G_A_BYTES + G_B_BYTES;
+constexpr int G_EPI_WARPS = 8;
+constexpr int G_GATHER_WARPS = G_STAGES;
 constexpr int G_THREADS = 64 + 32 * G_EPI_WARPS + 32 * G_GATHER_WARPS;
 // The drain's running residues (128 rows x 128 columns, two per word) live in
 // shared memory after the ring, column pair major so that the 32 lanes of a
 // warp (32 rows) touch 32 banks.
 constexpr int G_RUN_BYTES = BM * BN * 2;
-constexpr int G_SMEM_BYTES = SMEM_BYTES + G_RUN_BYTES;
+constexpr int G_SMEM_BYTES = G_STAGES * G_STAGE_BYTES + BAR_BYTES + 1024 + G_RUN_BYTES;
+
+// Ties registers written by tcgen05.ld to the point after tcgen05.wait::ld,
+// so that no use of them is scheduled before the wait.
+__device__ __forceinline__ void reg_fence16(float (&v)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(v[i]));
+}
+
+// (run + 65536 H + 256 (M1 + M2) + L) mod p for the four digit-product sums
+// of the gathered product (integers of magnitude at most 2^24 in fp32), in
+// full-rate float and integer operations only.  Each sum x is brought to
+// r = x - q p with q = x / p rounded (|x / p| < 2^22, so adding 1.5 * 2^23
+// rounds it to an integer); the fma forms r exactly, |r| <= p / 2 + 1, and
+// adding 1.5 * 2^23 again leaves r + 0x4B400000 as the word's bits.  Then
+// c16 * r_H + 256 (r_M1 + r_M2) + r_L (c16 = 65536 mod p, balanced) has
+// magnitude below 2^30 + 2^25; biasx is a multiple of p from 2^30 + 2^26 less
+// the four 0x4B400000 offsets (taken mod 2^32), so the 32-bit sum is the true
+// nonnegative value, below 2^31 + 2^27, and one Barrett step with a single
+// correction finishes it.
+__device__ __forceinline__ uint32_t reduce_to_word(float x, float pinv, float pf) {
+    const float q = fmaf(x, pinv, MAGIC) - MAGIC;
+    return __float_as_uint(fmaf(-q, pf, x) + MAGIC);
+}
+__device__ __forceinline__ uint32_t drain_step4(uint32_t run, float ha, float m1a, float m2a, float la, float pinv,
+                                                float pf, uint32_t c16, uint32_t biasx, uint32_t bm, uint32_t P) {
+    const uint32_t rh = reduce_to_word(ha, pinv, pf);
+    const uint32_t rm = reduce_to_word(m1a, pinv, pf) + reduce_to_word(m2a, pinv, pf);
+    const uint32_t rl = reduce_to_word(la, pinv, pf);
+    const uint32_t t = run + biasx + rl + 256u * rm + c16 * rh;
+    const uint32_t s = t - __umulhi(t, bm) * P;
+    return min(s, s - P);
+}
 
 struct GArgs {
     int64_t M, N;            // rows of X taking part; output columns (from column 0 of C)
@@ -959,7 +1006,7 @@ __global__ void gather_starts_kernel(int64_t num_m, int64_t num_n, int64_t nt0, 
     }
     kstart[i] = (int32_t)(lo - kb);
     if (exec) {
-        const int64_t s = ((lo - kb) / BK & ~(int64_t)(STAGES - 1)) * BK;   // as gtile rounds it
+        const int64_t s = (lo - kb) / BK * BK;   // as gtile rounds it
         atomicAdd(exec, (unsigned long long)(ke - kb - s));
     }
 }
@@ -976,7 +1023,7 @@ __device__ __forceinline__ GTile gtile(const GArgs &g, int64_t t, int64_t num_m,
     ti.chunk0 = kb / BK;
     ti.ksteps = (int)((ke - kb) / BK);
     const int64_t s = g.kstart ? (int64_t)g.kstart[ti.mt * num_n + ti.nt] : 0;
-    ti.ks0 = (int)(s / BK) & ~(STAGES - 1);   // whole rounds of the stage ring
+    ti.ks0 = (int)(s / BK);
     return ti;
 }
 
@@ -996,23 +1043,24 @@ __device__ __forceinline__ uint64_t make_sdesc_mn(uint32_t saddr) {
 // kind::f16 instruction descriptor with A MN-major (transposed), B K-major.
 constexpr uint32_t IDESC_G = IDESC | (1u << 15);
 
-// One K = 16 step: A planes ah (a) and al (a + 8 KB), B as in mma_step.
-__device__ __forceinline__ void mma_step_g(uint32_t dP, uint32_t dQ, uint32_t a, uint32_t b1, uint32_t b2,
-                                           uint32_t ahi, uint32_t bhi, uint32_t acc0) {
-    asm volatile("{\n\t.reg .pred p, e;\n\t.reg .b32 r;\n\t.reg .b64 a0, a1, x0, x1, y0, y1;\n\t"
+// One K = 16 step: A planes ah (a) and al (a + 8 KB), B planes bh (b) and bl
+// (b + 64 bytes);  H += ah*bh, M1 += ah*bl, M2 += al*bh, L += al*bl (TMEM
+// columns d, d + 128, d + 256, d + 384).
+__device__ __forceinline__ void mma_step_g4(uint32_t d, uint32_t a, uint32_t b, uint32_t ahi, uint32_t bhi,
+                                            uint32_t acc0) {
+    asm volatile("{\n\t.reg .pred p, e;\n\t.reg .b32 r, d1, d2, d3;\n\t.reg .b64 a0, a1, x0, x1;\n\t"
                  "elect.sync r|e, 0xffffffff;\n\t"
-                 "setp.ne.b32 p, %8, 0;\n\t"
-                 "mov.b64 a0, {%2, %5};\n\t"
-                 "add.u32 r, %2, 512;\n\tmov.b64 a1, {r, %5};\n\t"
-                 "mov.b64 x0, {%3, %6};\n\t"
-                 "add.u32 r, %3, 4;\n\tmov.b64 x1, {r, %6};\n\t"
-                 "mov.b64 y0, {%4, %6};\n\t"
-                 "add.u32 r, %4, 4;\n\tmov.b64 y1, {r, %6};\n\t"
-                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, y0, %7, p;\n\t"
-                 "@e tcgen05.mma.cta_group::1.kind::f16 [%1], a0, y1, %7, p;\n\t"
-                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a1, x0, %7, 1;\n\t"
-                 "@e tcgen05.mma.cta_group::1.kind::f16 [%1], a1, x1, %7, 1;\n\t}" ::"r"(dP),
-                 "r"(dQ), "r"(a), "r"(b1), "r"(b2), "r"(ahi), "r"(bhi), "r"(IDESC_G), "r"(acc0)
+                 "setp.ne.b32 p, %6, 0;\n\t"
+                 "add.u32 d1, %0, 128;\n\tadd.u32 d2, %0, 256;\n\tadd.u32 d3, %0, 384;\n\t"
+                 "mov.b64 a0, {%1, %3};\n\t"
+                 "add.u32 r, %1, 512;\n\tmov.b64 a1, {r, %3};\n\t"
+                 "mov.b64 x0, {%2, %4};\n\t"
+                 "add.u32 r, %2, 4;\n\tmov.b64 x1, {r, %4};\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, x0, %5, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [d1], a0, x1, %5, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [d2], a1, x0, %5, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [d3], a1, x1, %5, p;\n\t}" ::"r"(d),
+                 "r"(a), "r"(b), "r"(ahi), "r"(bhi), "r"(IDESC_G), "r"(acc0)
                  : "memory");
 }
 
@@ -1031,26 +1079,24 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + STAGES * STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + G_STAGES * G_STAGE_BYTES);
     uint64_t *full = bars;
-    uint64_t *empty = bars + STAGES;
-    uint64_t *accf = bars + 2 * STAGES;
-    uint64_t *acce = accf + 2;
-    uint64_t *done = acce + 2;
+    uint64_t *empty = bars + G_STAGES;
+    uint64_t *accf = bars + 2 * G_STAGES;
+    uint64_t *acce = accf + 1;
+    uint64_t *done = acce + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    uint32_t *run_s = reinterpret_cast<uint32_t *>(tiles + STAGES * STAGE_BYTES + BAR_BYTES);
+    uint32_t *run_s = reinterpret_cast<uint32_t *>(tiles + G_STAGES * G_STAGE_BYTES + BAR_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < G_STAGES; ++s) {
             mbar_init(&full[s], 1 + 32);   // the TMA thread and the slot's gather warp
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], G_EPI_WARPS);
-        }
+        mbar_init(accf, 1);
+        mbar_init(acce, G_EPI_WARPS);
         mbar_init(done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1072,32 +1118,30 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
     const int64_t num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
     const int64_t num_tiles = num_m * num_n;
     const int64_t tile0 = blockIdx.x, tstep = gridDim.x;
-    static_assert(STAGES == 4 && KSTEPS_PER_BLOCK % 4 == 0, "ring rounds");
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer of the compacted operand
             int stage = 0;
             uint32_t phase = 0;
-            int issued[STAGES];
-            uint32_t issued_parity[STAGES];
-            for (int s = 0; s < STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
+            int issued[G_STAGES];
+            uint32_t issued_parity[G_STAGES];
+            for (int s = 0; s < G_STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
             bool ok = true;
             for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
                 const GTile ti = gtile(g, t, num_m, num_n);
                 for (int ks = ti.ks0; ks < ti.ksteps; ++ks) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
-                    uint8_t *st = tiles + stage * STAGE_BYTES;
+                    uint8_t *st = tiles + stage * G_STAGE_BYTES;
                     const int y = (int)((ti.chunk0 + ks) * BN);
-                    mbar_expect_tx(&full[stage], 2 * BOX_BYTES);
-                    tma_load_2d(st + BOX_BYTES, &tmB, &full[stage], 0, y);
-                    tma_load_2d(st + 2 * BOX_BYTES, &tmB, &full[stage], 2 * BK, y);
+                    mbar_expect_tx(&full[stage], G_B_BYTES);
+                    tma_load_2d(st + G_A_BYTES, &tmB, &full[stage], 0, y);
                     issued[stage] = 1;
                     issued_parity[stage] = phase;
-                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                    if (++stage == G_STAGES) stage = 0, phase ^= 1u;
                 }
             }
-            for (int s = 0; s < STAGES; ++s) {   // never leave with copies in flight
+            for (int s = 0; s < G_STAGES; ++s) {   // never leave with copies in flight
                 if (!issued[s]) continue;
                 const uint32_t addr = smem_u32(&full[s]);
                 long long start = clock64();
@@ -1111,41 +1155,36 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (converged warp, elected lane)
-        uint32_t phase = 0;
-        uint32_t kbc = 0;
+        uint32_t phase = 0, kbc = 0;
+        int st = 0;
         bool ok = true;
         const uint32_t s0 = smem_u32(tiles);
         const uint64_t da = make_sdesc_mn(s0), db = make_sdesc(s0);
         const uint32_t ahi = (uint32_t)(da >> 32), alo = (uint32_t)da;
-        const uint32_t bhi = (uint32_t)(db >> 32), blo = (uint32_t)db;
-        constexpr uint32_t SB = STAGE_BYTES >> 4, B1 = BOX_BYTES >> 4, B2 = (2 * BOX_BYTES) >> 4;
+        const uint32_t bhi = (uint32_t)(db >> 32), blo = (uint32_t)db + (G_A_BYTES >> 4);
+        constexpr uint32_t SB = G_STAGE_BYTES >> 4;
         for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
             const GTile ti = gtile(g, t, num_m, num_n);
-            const int kbt = (ti.ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+            const int kbt = (ti.ksteps - ti.ks0 + G_KSTEPS_PER_BLOCK - 1) / G_KSTEPS_PER_BLOCK;
             for (int kb = 0; kb < kbt && ok; ++kb, ++kbc) {
-                const uint32_t buf = kbc & 1u, use = kbc >> 1;
-                if (!mbar_wait_warp(&acce[buf], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                if (!mbar_wait_warp(acce, (kbc & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
                 tcgen05_fence_after();
-                const uint32_t dP = tmem + buf * 256u, dQ = dP + 128u;
-                const int ks_beg = ti.ks0 + kb * KSTEPS_PER_BLOCK;
-                const int ks_end = min(ti.ksteps, ks_beg + KSTEPS_PER_BLOCK);
+                const int ks_beg = ti.ks0 + kb * G_KSTEPS_PER_BLOCK;
+                const int ks_end = min(ti.ksteps, ks_beg + G_KSTEPS_PER_BLOCK);
                 uint32_t acc0 = 0;
-                for (int ks = ks_beg; ks < ks_end && ok; ks += STAGES) {
-#pragma unroll
-                    for (int st = 0; st < STAGES; ++st) {
-                        if (!mbar_wait_warp(&full[st], phase, abort_flag, g.err)) { ok = false; break; }
-                        // the gather threads' copies are made visible to the
-                        // tensor core by their proxy fence before they arrive
-                        tcgen05_fence_after();
-                        const uint32_t a = alo + st * SB, b = blo + st * SB;
-                        mma_step_g(dP, dQ, a, b + B1, b + B2, ahi, bhi, acc0);
-                        mma_step_g(dP, dQ, a + 256, b + B1 + 2, b + B2 + 2, ahi, bhi, 1u);   // next 16 of K
-                        acc0 = 1u;
-                        commit_elected<false, true>(&empty[st]);
-                    }
-                    phase ^= 1u;
+                for (int ks = ks_beg; ks < ks_end; ++ks) {
+                    if (!mbar_wait_warp(&full[st], phase, abort_flag, g.err)) { ok = false; break; }
+                    // the gather threads' copies are made visible to the
+                    // tensor core by their proxy fence before they arrive
+                    tcgen05_fence_after();
+                    const uint32_t a = alo + (uint32_t)st * SB, b = blo + (uint32_t)st * SB;
+                    mma_step_g4(tmem, a, b, ahi, bhi, acc0);
+                    mma_step_g4(tmem, a + 256, b + 2, ahi, bhi, 1u);   // next 16 of K
+                    acc0 = 1u;
+                    commit_elected<false, true>(&empty[st]);
+                    if (++st == G_STAGES) st = 0, phase ^= 1u;
                 }
-                if (ok) commit_elected<false, true>(&accf[buf]);
+                if (ok) commit_elected<false, true>(accf);
             }
         }
         commit_elected<false, false>(done);
@@ -1158,63 +1197,72 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
             }
         }
     } else if (warp < 2 + G_EPI_WARPS) {
-        // ---------------- drain: one warp per TMEM lane quarter, all 128
-        // columns; otherwise as in modgemm_tc_kernel
+        // ---------------- drain: two warps per TMEM lane quarter, 64 columns
+        // each (column half `half`); otherwise as in modgemm_tc_kernel
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
-        const float pinv = g.pinv;
+        const float pinv = g.pinv, pf = (float)g.p;
         const int P = (int)g.p;
         const uint32_t bm = 0xFFFFFFFFu / g.p;
-        const int bias = 256 * P + (int)(((1u << 24) + g.p - 1) / g.p) * P;
+        uint32_t c16 = 65536u % g.p;
+        if (c16 > g.p / 2) c16 -= g.p;   // 65536 mod p, balanced (as a 32-bit word)
+        const uint32_t biasx = ((1u << 30) + (1u << 26) + g.p - 1) / g.p * g.p - 0x4B400000u * (513u + c16);
         constexpr int HC = BN / 2;
         uint32_t kbc = 0;
         bool ok = true;
         for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
             const GTile ti = gtile(g, t, num_m, num_n);
-            const int kbt = (ti.ksteps - ti.ks0 + KSTEPS_PER_BLOCK - 1) / KSTEPS_PER_BLOCK;
+            const int kbt = (ti.ksteps - ti.ks0 + G_KSTEPS_PER_BLOCK - 1) / G_KSTEPS_PER_BLOCK;
             if (kbt <= 0) continue;   // no list entry on this tile: C stays as it is
-            uint32_t *rs = run_s + row_in_tile;   // column pair i at rs[128 i]
+            // column pair i of this warp's half at rs[128 i]
+            uint32_t *rs = run_s + half * (HC / 2) * BM + row_in_tile;
 #pragma unroll 8
-            for (int i = 0; i < BN / 2; ++i) rs[BM * i] = 0;
+            for (int i = 0; i < HC / 2; ++i) rs[BM * i] = 0;
             for (int kb = 0; kb < kbt; ++kb, ++kbc) {
-                const uint32_t buf = kbc & 1u, use = kbc >> 1;
-                if (!mbar_wait(&accf[buf], use & 1u, abort_flag, g.err)) { ok = false; break; }
+                if (!mbar_wait(accf, kbc & 1u, abort_flag, g.err)) { ok = false; break; }
                 tcgen05_fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * 256u;
-#pragma unroll 2
-                for (int c = 0; c < BN / 16; ++c) {
-                    float pv[16], qv[16];
-                    tmem_ld16(tbase + c * 16, pv);
-                    tmem_ld16(tbase + 128 + c * 16, qv);
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + half * HC;
+#pragma unroll 1
+                for (int c = 0; c < HC / 16; ++c) {
+                    float hv[16], m1v[16], m2v[16], lv[16];
+                    tmem_ld16(tbase + c * 16, hv);
+                    tmem_ld16(tbase + 128 + c * 16, m1v);
+                    tmem_ld16(tbase + 256 + c * 16, m2v);
+                    tmem_ld16(tbase + 384 + c * 16, lv);
                     tmem_wait_ld();
+                    reg_fence16(hv);
+                    reg_fence16(m1v);
+                    reg_fence16(m2v);
+                    reg_fence16(lv);
+                    if (c + 1 == HC / 16) {   // every accumulator read: the MMA may go on
+                        tcgen05_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce);
+                    }
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         const uint32_t pair = rs[BM * (c * 8 + j / 2)];
-                        const int lo16 = drain_step((int)(pair & 0xFFFFu), pv[j], qv[j], pinv, P, bias, bm);
-                        const int hi16 = drain_step((int)(pair >> 16), pv[j + 1], qv[j + 1], pinv, P, bias, bm);
-                        rs[BM * (c * 8 + j / 2)] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
+                        const uint32_t lo16 = drain_step4(pair & 0xFFFFu, hv[j], m1v[j], m2v[j], lv[j], pinv, pf,
+                                                          c16, biasx, bm, g.p);
+                        const uint32_t hi16 = drain_step4(pair >> 16, hv[j + 1], m1v[j + 1], m2v[j + 1],
+                                                          lv[j + 1], pinv, pf, c16, biasx, bm, g.p);
+                        rs[BM * (c * 8 + j / 2)] = lo16 | (hi16 << 16);
                     }
                 }
-                tcgen05_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[buf]);
             }
             if (!ok) break;
             const int64_t row = ti.mt * BM + row_in_tile;
-            if (row < g.M) {
+            const int64_t col0 = ti.nt * BN + half * HC;
+            if (row < g.M && col0 < g.N) {
+                uint32_t part[HC / 2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int64_t col0 = ti.nt * BN + h * HC;
-                    if (col0 >= g.N) break;
-                    uint32_t part[HC / 2];
-#pragma unroll
-                    for (int i = 0; i < HC / 2; ++i) part[i] = rs[BM * (h * (HC / 2) + i)];
-                    rmw_segment(g.C + row * g.ldc + col0, col0, g.N, part, g.sign, P);
-                }
+                for (int i = 0; i < HC / 2; ++i) part[i] = rs[BM * i];
+                rmw_segment(g.C + row * g.ldc + col0, col0, g.N, part, g.sign, P);
             }
         }
     } else {
-        // ---------------- gather warps: warp 6 + s fills ring slot s with
+        // ---------------- gather warps: warp 10 + s fills ring slot s with
         // the X^T rows of the stage's 32 listed j (MN-major, 128-byte
         // swizzle), cp.async 16 bytes at a time.  Copy i: list entry kk =
         // i / 32 (one instruction moves an entry's 512 bytes), piece q = i % 32
@@ -1222,19 +1270,23 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
         // plane (q / 4) % 2.  The warp reads the stage's list entries with one
         // load (lane l: entry l) before its wait for the slot, waits for its
         // own copies, fences them to the tensor core's proxy and signals; the
-        // other slots' warps go on independently.
+        // other slots' warps go on independently.  (Vector loads through
+        // registers in place of cp.async measured 1.9x slower here.)
         const int slot = warp - 2 - G_EPI_WARPS;
-        const uint32_t abase = smem_u32(tiles) + slot * STAGE_BYTES;
+        const uint32_t abase = smem_u32(tiles) + slot * G_STAGE_BYTES;
         const int q = lane;
         const int rl = (q >> 3) * 32 + (q & 3) * 8;
         const uint32_t dst_lane = ((q >> 2) & 1) * 8192 + (rl >> 6) * 1024 + ((((rl & 63) >> 3)) << 4);
-        uint32_t seq = 0, use = 0;
+        int ring = 0;   // ring slot of the next k-step, as the producer and the MMA issuer count it
+        uint32_t use = 0;
         bool ok = true;
         for (int64_t t = tile0; t < num_tiles && ok; t += tstep) {
             const GTile ti = gtile(g, t, num_m, num_n);
             const __nv_bfloat16 *xseg = g.xt + (ti.mt * BM / 32) * 64 + q * 8;   // this lane's piece
-            for (int ks = ti.ks0; ks < ti.ksteps; ++ks, ++seq) {
-                if ((int)(seq & (STAGES - 1)) != slot) continue;
+            for (int ks = ti.ks0; ks < ti.ksteps; ++ks) {
+                const int mine = ring;
+                if (++ring == G_STAGES) ring = 0;
+                if (mine != slot) continue;
                 const int64_t kbase = (ti.chunk0 + ks) * BK;
                 const int32_t jl = g.kidx[kbase + lane];
                 if (!mbar_wait_warp(&empty[slot], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
@@ -1549,7 +1601,12 @@ struct KernelTimes {
     bool on = false;
     unsigned long long *tc_work = nullptr;   // device counter of the dense product's tile work
     std::vector<cudaEvent_t> pool;
-    std::vector<std::pair<int, size_t>> marks;   // (kind, index of the start event)
+    struct Mark {
+        int kind;
+        size_t ev;            // index of the start event
+        int64_t M, N, K;      // the launch's product shape (-1: not known on the host)
+    };
+    std::vector<Mark> marks;
     size_t used = 0;
     int dev = -1;
 };
@@ -1568,14 +1625,14 @@ cudaEvent_t kt_event() {
 }
 
 // kind 0: modgemm_tc_kernel, 1: modgemm_gather_kernel
-void kt_start(int kind, cudaStream_t s) {
+void kt_start(int kind, cudaStream_t s, int64_t M = -1, int64_t N = -1, int64_t K = -1) {
     if (!g_kt.on) return;
     const size_t i = g_kt.used;
     cudaEvent_t a = kt_event();
-    if (a && cudaEventRecord(a, s) == cudaSuccess) g_kt.marks.emplace_back(kind, i);
+    if (a && cudaEventRecord(a, s) == cudaSuccess) g_kt.marks.push_back({kind, i, M, N, K});
 }
 void kt_stop(cudaStream_t s) {
-    if (!g_kt.on || g_kt.marks.empty() || g_kt.marks.back().second + 1 != g_kt.used) return;
+    if (!g_kt.on || g_kt.marks.empty() || g_kt.marks.back().ev + 1 != g_kt.used) return;
     cudaEvent_t b = kt_event();
     if (b) cudaEventRecord(b, s);
 }
@@ -1595,18 +1652,30 @@ void kernel_times_begin(unsigned long long *tc_work_dev) {
     g_kt.used = 0;
 }
 
+// GBLA_LOG=2: also one stderr line per timed launch (kind, product shape, ms).
+static bool launch_trace() {
+    static const bool v = [] {
+        const char *e = getenv("GBLA_LOG");
+        return e && atoi(e) >= 2;
+    }();
+    return v;
+}
+
 void kernel_times_end(KernelTimeTotals *t) {
     *t = KernelTimeTotals{};
     if (g_kt.on)
         for (const auto &mk : g_kt.marks) {
-            if (mk.second + 1 >= g_kt.used) continue;
+            if (mk.ev + 1 >= g_kt.used) continue;
             float ms = 0;
-            if (cudaEventElapsedTime(&ms, g_kt.pool[mk.second], g_kt.pool[mk.second + 1]) != cudaSuccess) {
+            if (cudaEventElapsedTime(&ms, g_kt.pool[mk.ev], g_kt.pool[mk.ev + 1]) != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
-            t->ms[mk.first] += ms;
-            t->launches[mk.first] += 1;
+            t->ms[mk.kind] += ms;
+            t->launches[mk.kind] += 1;
+            if (launch_trace())
+                fprintf(stderr, "gbla-launch %s M=%lld N=%lld K=%lld ms=%.4f\n", mk.kind ? "gather" : "tc",
+                        (long long)mk.M, (long long)mk.N, (long long)mk.K, ms);
         }
     g_kt.on = false;
     g_kt.tc_work = nullptr;
@@ -1769,7 +1838,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
         cfg.attrs = at;
         cfg.numAttrs = 1;
         g.work = g_kt.tc_work;
-        kt_start(0, s);
+        kt_start(0, s, M, N, K);
         GBLA_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::modgemm_tc_kernel<true>, ma, mb, g));
         kt_stop(s);
         ++g_pair_launches;
@@ -1777,7 +1846,7 @@ int modgemm(const Planes &A, int64_t a_row0, int64_t a_k0, const Planes &B, int6
         const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
         const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
         g.work = g_kt.tc_work;
-        kt_start(0, s);
+        kt_start(0, s, M, N, K);
         tc::modgemm_tc_kernel<false><<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
         kt_stop(s);
     }
@@ -1819,7 +1888,7 @@ int modgemm_to_planes(const Planes &A, int64_t a_row0, const Planes &B, int64_t 
     g.work = g_kt.tc_work;
     const int64_t tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
-    kt_start(0, s);
+    kt_start(0, s, M, N, K);
     tc::modgemm_tc_kernel<false><<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, g);
     kt_stop(s);
     GBLA_CUDA_TRY(launch_check());
@@ -1840,8 +1909,8 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
     if (ctr) ctr->launches += 1;
     GBLA_TRY(get_encode());
     CUtensorMap mb;
-    cuuint64_t dims[2] = {128, (cuuint64_t)(S.total / tc::BK) * 128};
-    cuuint64_t strides[1] = {128 * 2};
+    cuuint64_t dims[2] = {2 * tc::BK, (cuuint64_t)(S.total / tc::BK) * 128};
+    cuuint64_t strides[1] = {2 * tc::BK * 2};
     cuuint32_t box[2] = {2 * tc::BK, 128};
     cuuint32_t estr[2] = {1, 1};
     if (g_encode(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)S.planes, dims, strides, box, estr,
@@ -1885,7 +1954,7 @@ int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_r
     g.kstart = kstart;
     const int64_t tiles = num_m * num_n;
     const int grid = (int)(tiles < device_sm_count() ? tiles : device_sm_count());
-    kt_start(1, s);
+    kt_start(1, s, M, N, -1);
     tc::modgemm_gather_kernel<<<grid, tc::G_THREADS, tc::G_SMEM_BYTES, s>>>(mb, g);
     kt_stop(s);
     const cudaError_t e = cudaGetLastError();

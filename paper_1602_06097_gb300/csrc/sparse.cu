@@ -16,7 +16,7 @@
 //     multiple of 128), and the tile restricted to those rows is stored as
 //     dense B-operand digit planes, chunk-major: list entries 32 q .. 32 q + 31
 //     of all tiles' lists form chunk q, 128 rows (the tile's columns) of
-//     128 bf16 (hi, lo of the values, hi, lo of 256 * value mod p, 32 each).
+//     64 bf16 (hi digits of the 32 values, then lo digits).
 //     F4 rows come in runs of consecutive columns with vertical repetition
 //     (Sec. 4.2), so a 128-column tile meets few rows and the compacted
 //     tiles are far denser than the block.
@@ -44,9 +44,6 @@ __device__ __forceinline__ void store_digit_planes(__nv_bfloat16 *rowp, int kin,
     digits(v, mp.p, h, l);
     rowp[kin] = i2bf(h);
     rowp[32 + kin] = i2bf(l);
-    digits(mod32(v * mp.r256, mp), mp.p, h, l);
-    rowp[64 + kin] = i2bf(h);
-    rowp[96 + kin] = i2bf(l);
 }
 
 // Step 1 (one warp per pivot row k).
@@ -159,7 +156,7 @@ __global__ void sp_values_kernel(int64_t npiv, int L, const int32_t *__restrict_
         }
         const int64_t t = cc / TILE;
         const int64_t kk = koff[t] + woff[t * wpr + w] + __popc(bits[t * wpr + w] & below);
-        __nv_bfloat16 *rowp = planes + ((kk >> 5) * TILE + (cc % TILE)) * 128;
+        __nv_bfloat16 *rowp = planes + ((kk >> 5) * TILE + (cc % TILE)) * 64;
         store_digit_planes(rowp, (int)(kk & 31), mulmod(val[i], inv, mp), mp);
     }
 }
@@ -225,9 +222,9 @@ int sparse_build(const DevCSR &in, const PivotInfo &pi, int L, uint16_t *Adiag, 
         cs[a]->total = totals[a];
         const size_t nk = (size_t)(totals[a] > 0 ? totals[a] : 1);
         if ((rc = dalloc_t(&cs[a]->kidx, nk, s)) != GBLA_OK) break;
-        // chunk q (list entries 32 q .. 32 q + 31) is 128 rows of 128 bf16:
-        // 512 plane elements per list entry
-        const size_t pe = (size_t)(totals[a] > 0 ? totals[a] : 32) * 512;
+        // chunk q (list entries 32 q .. 32 q + 31) is 128 rows of 64 bf16
+        // (hi digits of the 32 entries, then lo): 256 plane elements per entry
+        const size_t pe = (size_t)(totals[a] > 0 ? totals[a] : 32) * 256;
         if ((rc = dalloc(reinterpret_cast<void **>(&cs[a]->planes), pe * sizeof(__nv_bfloat16), s)) != GBLA_OK)
             break;
         if (cudaMemsetAsync(cs[a]->kidx, 0x7F, nk * sizeof(int32_t), s) != cudaSuccess ||

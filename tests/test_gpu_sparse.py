@@ -90,11 +90,12 @@ def test_spmm_staircase_leads(seed):
     assert np.array_equal(run_spmm(X, S, C, p, -1, lead), ref(X, S, C, p, -1))
 
 
-@pytest.mark.parametrize("K", [511, 512, 513, 1024, 2048 + 64])
+@pytest.mark.parametrize("K", [511, 512, 513, 1023, 1024, 1025, 2048 + 64, 3072 + 5])
 @pytest.mark.parametrize("fill", ["pm1", "half", "halfp1", "mixed"])
 def test_spmm_at_the_k_block_bound(K, fill):
     """A dense S makes every tile's list K long: all-extreme digits at and
-    around the 512-deep exact fp32 block."""
+    around the 1,024-deep exact fp32 block of the gathered product (each of
+    its four digit-product sums reaches 2^24 with the "half" fill)."""
     p = 65521
     M, N = 256, 200
     h = (p - 1) // 2
