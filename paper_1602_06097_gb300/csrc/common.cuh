@@ -147,8 +147,11 @@ __device__ __forceinline__ void dev_fail(uint32_t *err, uint32_t bit) {
 // 16-byte vectors.  The residues b' = 256 * b mod p of a 4-plane set use a
 // Barrett reduction.
 constexpr int TP_TILE = 64;
+// Transpose tile: row r (of the destination), k chunk c (8 residues) at
+// t[r][c ^ ((r >> 3) & 7)]: both the scattered writes and the 16-byte row
+// reads of the transpose are free of bank conflicts.
 struct TpSmem {
-    uint16_t t[TP_TILE][TP_TILE + 2];
+    uint4 t[TP_TILE][TP_TILE / 8];
 };
 
 // Two digits as a bf16 pair (lo_elem in the low half).
@@ -185,36 +188,61 @@ __device__ __forceinline__ void store_digits8(const Planes &dst, int64_t r, int6
     }
 }
 
+// 8 consecutive residues src[base .. base + 7] (positions at or past n read
+// as 0): one 16-byte load when all are in range and aligned.
+__device__ __forceinline__ void load8_u16(const uint16_t *__restrict__ p, int64_t avail, uint16_t (&w)[8]) {
+    if (avail >= 8 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t u[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) w[e] = (uint16_t)(u[e >> 1] >> ((e & 1) * 16));
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) w[e] = e < avail ? p[e] : (uint16_t)0;
+    }
+}
+
 __device__ __forceinline__ void tp_tile(const Planes &dst, int64_t row0, int64_t r0, int64_t k0, int64_t R, int64_t Kc,
                                         const uint16_t *__restrict__ src, int64_t lds, int64_t col0,
                                         const int32_t *__restrict__ rgather, const ModP &mp, TpSmem &sm,
                                         int64_t dcol0 = 0)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // all of this thread's loads are issued before any of them is used, so
-    // that 16 are in flight at once
-    uint16_t v[TP_TILE / 8][2];
+    static_assert(TP_TILE == 64, "256 threads: 8 column groups x 32 rows, twice");
+    const int tid = threadIdx.x;
+    const int cq = tid & 7, kr = tid >> 3;   // source columns r0 + 8 cq .., source row k0 + kr (+ 32)
+    uint16_t w[2][8];
 #pragma unroll
-    for (int j = 0; j < TP_TILE / 8; ++j) {
-        const int64_t k = k0 + warp + 8 * j;
+    for (int i = 0; i < 2; ++i) {
+        const int64_t k = k0 + kr + 32 * i;
         int64_t sr = -1;
         if (k < Kc) sr = rgather ? (int64_t)rgather[k] : k;
+        const int64_t r = r0 + cq * 8;
+        if (sr >= 0 && r < R) {
+            load8_u16(src + sr * lds + col0 + r, R - r, w[i]);
+        } else {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t r = r0 + lane + 32 * h;
-            v[j][h] = (sr >= 0 && r < R) ? src[sr * lds + col0 + r] : (uint16_t)0;
+            for (int e = 0; e < 8; ++e) w[i][e] = 0;
         }
     }
+    uint16_t *t16 = reinterpret_cast<uint16_t *>(&sm.t[0][0]);
 #pragma unroll
-    for (int j = 0; j < TP_TILE / 8; ++j)
+    for (int i = 0; i < 2; ++i) {
+        const int kl = kr + 32 * i;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) sm.t[warp + 8 * j][lane + 32 * h] = v[j][h];
+        for (int e = 0; e < 8; ++e) {
+            const int rl = cq * 8 + e;   // (rl >> 3) & 7 == cq
+            t16[rl * TP_TILE + ((((kl >> 3) ^ cq) << 3) | (kl & 7))] = w[i][e];
+        }
+    }
     __syncthreads();
+#pragma unroll
     for (int it = tid; it < TP_TILE * 8; it += 256) {
         const int c = it & 7, rr = it >> 3;
+        const uint4 x = sm.t[rr][c ^ ((rr >> 3) & 7)];
+        const uint32_t u[4] = {x.x, x.y, x.z, x.w};
         uint32_t a[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = sm.t[c * 8 + e][rr];
+        for (int e = 0; e < 8; ++e) a[e] = (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;
         store_digits8(dst, row0 + r0 + rr, dcol0 + k0 + c * 8, a, mp);
     }
 }

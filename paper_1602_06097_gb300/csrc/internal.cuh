@@ -89,7 +89,8 @@ void compact_free(Compact *c, cudaStream_t s);
 // Gathered product C[r, c] <- (C[r, c] + sign * sum_j X[r, j] * S[j, c]) mod p
 // for rows r < M and columns c < N of C, c in tile nt0 + c / 128 of S; X is
 // read from the A-operand plane set XT of its transpose (row j = column j of
-// X, K = r; rows xt_rows and beyond read as zero).  With row_lead (device,
+// X, K = r).  Every list entry j >= xt_rows must be padding (KIDX_PAD, whose
+// rows of S are zero): such entries read row 0 of XT.  With row_lead (device,
 // ascending absolute lead of each row of X) a row tile skips the list entries
 // left of its first row's lead.  Tensor-core variant only (p >= 8).
 // With exec (device, optional), adds the list entries times row tiles the

@@ -61,13 +61,25 @@ __global__ void __launch_bounds__(256) to_planes_kernel(Planes dst, int64_t R, i
         if (sr >= 0 && zero_if && zero_if[sr]) sr = -1;
     }
     uint32_t a[8];
+    if (!cgather) {
+        uint16_t w[8];
+        if (sr >= 0 && k0 < Kc) {
+            load8_u16(src + sr * lds + col_off + k0, Kc - k0, w);
+        } else {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int64_t k = k0 + e;
-        a[e] = 0;
-        if (sr >= 0 && k < Kc) {
-            const int64_t sc = cgather ? (int64_t)cgather[k] : k;
-            if (sc >= 0) a[e] = src[sr * lds + col_off + sc];
+            for (int e = 0; e < 8; ++e) w[e] = 0;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] = w[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t k = k0 + e;
+            a[e] = 0;
+            if (sr >= 0 && k < Kc) {
+                const int64_t sc = cgather[k];
+                if (sc >= 0) a[e] = src[sr * lds + col_off + sc];
+            }
         }
     }
     store_digits8(dst, r, k0, a, mp);
@@ -969,7 +981,7 @@ struct GArgs {
     const int64_t *koff;     // list offsets
     const __nv_bfloat16 *xt; // XT plane set (2 planes, rows = j, K = r)
     int64_t xt_row_elems;    // elements per XT row
-    int64_t xt_rows;         // list entries >= xt_rows (padding) read as zero
+    int64_t xt_rows;         // list entries >= xt_rows are padding (their rows of S are zero)
     const int32_t *kstart;   // [row tiles x output tiles]: first list entry of the tile's
                              // K range (0 without row leads), from gather_starts_kernel
     uint16_t *C;
@@ -1064,8 +1076,8 @@ __device__ __forceinline__ void mma_step_g4(uint32_t d, uint32_t a, uint32_t b, 
                  : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -1292,11 +1304,13 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
                 if (!mbar_wait_warp(&empty[slot], (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
 #pragma unroll 8
                 for (int kk = 0; kk < BK; ++kk) {
-                    const int64_t j = __shfl_sync(0xFFFFFFFFu, jl, kk);
-                    const bool valid = j < g.xt_rows;
+                    int64_t j = __shfl_sync(0xFFFFFFFFu, jl, kk);
+                    // a padding entry's row of S is zero: any row of X^T serves
+                    // (row 0; the zero-fill form of cp.async measured 9% slower)
+                    if (j >= g.xt_rows) j = 0;
                     // 16-byte chunk index XOR the row within the swizzle atom
                     const uint32_t dst = abase + (kk >> 3) * 2048 + (kk & 7) * 128 + (dst_lane ^ ((kk & 7) << 4));
-                    cp_async16(dst, valid ? xseg + j * g.xt_row_elems : g.xt, valid ? 16u : 0u);
+                    cp_async16(dst, xseg + j * g.xt_row_elems);
                 }
                 cp_async_commit();
                 cp_async_wait<0>();

@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(256) pair_planes_kernel(int mode, int w, int L
                                                           const uint16_t *__restrict__ ZN,
                                                           const uint16_t *__restrict__ U, Planes dst, ModP mp)
 {
-    __shared__ TpSmem sm;
+    __shared__ uint16_t t[TP_TILE][TP_TILE + 2];
     const int pairs_per_leaf = L / (2 * w);
     const int64_t b = blockIdx.z;
     const int64_t lo = (b / pairs_per_leaf) * L;
@@ -1045,14 +1045,14 @@ __global__ void __launch_bounds__(256) pair_planes_kernel(int mode, int w, int L
         } else {
             v = ZN[(lo + o2 + kk) * (int64_t)L + o2 + rr];
         }
-        sm.t[i][k] = v;
+        t[i][k] = v;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < TP_TILE * 8; it += 256) {
         const int c = it & 7, i = it >> 3;
         uint32_t a[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = sm.t[i][c * 8 + e];
+        for (int e = 0; e < 8; ++e) a[e] = t[i][c * 8 + e];
         store_digits8(dst, b * w + r0 + i, k0 + c * 8, a, mp);
     }
 }
