@@ -389,6 +389,65 @@ __global__ void bottom_fill_kernel(int64_t rank_d, const int32_t *__restrict__ p
     warp_compact(D + (prow ? (int64_t)prow[k] : k) * ldd, n_d, npcol_orig, ocol, oval, off, lane);
 }
 
+// Bottom rows from the reduced rows' non-pivot part Rnp (row k = RREF row k of
+// D'): the row is the pivot entry (pcol[k], 1) followed by the nonzeros of
+// Rnp[k] in column order (its entries left of the lead are zero).  A warp per
+// row; a lane loads 8 residues at a time (rows of Rnp are 128-byte aligned).
+__device__ __forceinline__ void load8_np(const uint16_t *row, int64_t i0, int64_t nnp, uint16_t (&v)[8]) {
+    if (i0 + 8 <= nnp) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(row + i0));
+        const uint32_t u[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (uint16_t)(u[e >> 1] >> ((e & 1) * 16));
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = i0 + e < nnp ? row[i0 + e] : (uint16_t)0;
+    }
+}
+
+__global__ void bottom_counts_np_kernel(int64_t rank_d, const int32_t *__restrict__ pcol,
+                                        const int32_t *__restrict__ npcol_orig, const uint16_t *__restrict__ Rnp,
+                                        int64_t ldnp, int64_t nnp, const int64_t *__restrict__ outpos, int64_t *cnt) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= rank_d) return;
+    const uint16_t *row = Rnp + k * ldnp;
+    int64_t c = 0;
+    for (int64_t i0 = (int64_t)lane * 8; i0 < nnp; i0 += 256) {
+        uint16_t v[8];
+        load8_np(row, i0, nnp, v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) c += v[e] != 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane == 0) cnt[outpos[npcol_orig[pcol[k]]]] = 1 + c;
+}
+
+// Input column of each non-pivot column of D': ocolmap[i] = npcol_orig[npc[i]].
+__global__ void np_colmap_kernel(int64_t nnp, const int32_t *__restrict__ npc, const int32_t *__restrict__ npcol_orig,
+                                 int32_t *__restrict__ ocolmap) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nnp) ocolmap[i] = npcol_orig[npc[i]];
+}
+
+__global__ void bottom_fill_np_kernel(int64_t rank_d, const int32_t *__restrict__ pcol,
+                                      const int32_t *__restrict__ npcol_orig, const uint16_t *__restrict__ Rnp,
+                                      int64_t ldnp, const int32_t *__restrict__ ocolmap, int64_t nnp,
+                                      const int64_t *__restrict__ outpos, const int64_t *__restrict__ orp,
+                                      int32_t *ocol, uint16_t *oval) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= rank_d) return;
+    const int32_t pc = npcol_orig[pcol[k]];
+    const int64_t off = orp[outpos[pc]];
+    if (lane == 0) {
+        ocol[off] = pc;
+        oval[off] = 1;
+    }
+    warp_compact(Rnp + k * ldnp, nnp, ocolmap, ocol, oval, off + 1, lane);
+}
+
 __global__ void transpose_u16_kernel(const uint16_t *__restrict__ src, int64_t lds, int64_t rows, int64_t cols,
                                      uint16_t *__restrict__ dst, int64_t ldd) {
     __shared__ uint16_t t[32][33];
@@ -688,6 +747,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
     Compact SA, SB;
     uint16_t *Adiag = nullptr;
     uint16_t *C16 = nullptr, *D16 = nullptr, *Bt16 = nullptr, *Y16 = nullptr, *R16 = nullptr;
+    EchelonD::NonPivot np_d;   // the reduced rows of D' at its non-pivot columns (output without R16)
+    int32_t *np_ocol = nullptr;   // input column of each of them
     uint16_t *A16 = nullptr, *B16 = nullptr;
     int32_t *is_piv_row = nullptr, *prow = nullptr, *pcol = nullptr;
     int64_t *outflag = nullptr, *outpos = nullptr, *cnt = nullptr, *orp = nullptr;
@@ -936,6 +997,8 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
                    tm.on ? tm.ev[7] : nullptr, back_leaf_width(),
                    echelon_opt == GBLA_ECHELON_SGE ? 1 : (echelon_opt == GBLA_ECHELON_AUTO ? 2 : 0),
                    &d_density, &sge_done};
+        // the second FL pass reads the dense rows; the output alone does not
+        if (!want_reduced) E.np_out = &np_d;
         NvtxRange r("gbla.echelon");
         STEP(echelon_d(E, &rank_d));
     }
@@ -991,9 +1054,13 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
                                                                             dc.row_ptr, Y16, ldd, n_d, outpos, cnt);
         CSTEP(launch_check());
     }
-    if (rank_d > 0) {
+    if (rank_d > 0 && R16) {
         bottom_counts_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(rank_d, nullptr, pcol, pi.npcol_orig,
                                                                                   R16, ldd, n_d, outpos, cnt);
+        CSTEP(launch_check());
+    } else if (rank_d > 0) {
+        bottom_counts_np_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(
+            rank_d, pcol, pi.npcol_orig, np_d.Rnp, np_d.ldnp, np_d.nnp, outpos, cnt);
         CSTEP(launch_check());
     }
     STEP(scan_i64(cnt, orp, rank, orp + rank, s));
@@ -1006,9 +1073,19 @@ int reduce_impl(const gbla_csr_in *in, uint32_t p, const gbla_options *opt, cuda
             outpos, orp, ocol, oval, mp);
         CSTEP(launch_check());
     }
-    if (rank_d > 0) {
+    if (rank_d > 0 && R16) {
         bottom_fill_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(
             rank_d, nullptr, pcol, pi.npcol_orig, R16, ldd, n_d, outpos, orp, ocol, oval);
+        CSTEP(launch_check());
+    } else if (rank_d > 0) {
+        STEP(dalloc_t(&np_ocol, (size_t)(np_d.nnp > 0 ? np_d.nnp : 1), s));
+        if (np_d.nnp > 0) {
+            np_colmap_kernel<<<(unsigned)((np_d.nnp + 255) / 256), 256, 0, s>>>(np_d.nnp, np_d.npc, pi.npcol_orig,
+                                                                               np_ocol);
+            CSTEP(launch_check());
+        }
+        bottom_fill_np_kernel<<<(unsigned)((rank_d * 32 + 255) / 256), 256, 0, s>>>(
+            rank_d, pcol, pi.npcol_orig, np_d.Rnp, np_d.ldnp, np_ocol, np_d.nnp, outpos, orp, ocol, oval);
         CSTEP(launch_check());
     }
     {
@@ -1166,6 +1243,9 @@ cleanup:
     dfree(Bt16, s);
     dfree(Y16, s);
     dfree(R16, s);
+    dfree(np_d.Rnp, s);
+    dfree(np_d.npc, s);
+    dfree(np_ocol, s);
     dfree(is_piv_row, s);
     dfree(prow, s);
     dfree(pcol, s);

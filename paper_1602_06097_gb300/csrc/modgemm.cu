@@ -1004,22 +1004,26 @@ __global__ void gather_starts_kernel(int64_t num_m, int64_t num_n, int64_t nt0, 
                                      int32_t *__restrict__ kstart, unsigned long long *exec)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= num_m * num_n) return;
-    const int64_t mt = i / num_n, nt = i % num_n;
-    const int64_t kb = koff[nt0 + nt], ke = koff[nt0 + nt + 1];
-    int64_t lo = kb, hi = ke;
-    if (row_lead) {
-        const int32_t L = row_lead[mt * BM];
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (kidx[mid] < L) lo = mid + 1;
-            else hi = mid;
+    unsigned long long run = 0;   // list entries this tile runs through
+    if (i < num_m * num_n) {
+        const int64_t mt = i / num_n, nt = i % num_n;
+        const int64_t kb = koff[nt0 + nt], ke = koff[nt0 + nt + 1];
+        int64_t lo = kb, hi = ke;
+        if (row_lead) {
+            const int32_t L = row_lead[mt * BM];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (kidx[mid] < L) lo = mid + 1;
+                else hi = mid;
+            }
         }
+        kstart[i] = (int32_t)(lo - kb);
+        run = (unsigned long long)(ke - kb - (lo - kb) / BK * BK);   // from the start gtile rounds to
     }
-    kstart[i] = (int32_t)(lo - kb);
-    if (exec) {
-        const int64_t s = (lo - kb) / BK * BK;   // as gtile rounds it
-        atomicAdd(exec, (unsigned long long)(ke - kb - s));
+    if (exec) {   // one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xFFFFFFFFu, run, o);
+        if ((threadIdx.x & 31) == 0 && run) atomicAdd(exec, run);
     }
 }
 

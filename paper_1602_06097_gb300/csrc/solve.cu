@@ -1587,7 +1587,7 @@ backward:
         uint16_t *Nm = nullptr, *Rnp = nullptr;
         int32_t *colmap = nullptr, *npc = nullptr;
         Planes Ap{}, Bp{};
-        rc = dalloc_t(&E.R[0], (size_t)rank * (size_t)ldr, s);
+        if (!E.np_out) rc = dalloc_t(&E.R[0], (size_t)rank * (size_t)ldr, s);
         if (rc == GBLA_OK) rc = dalloc_t(&colmap, (size_t)n, s);
         if (rc == GBLA_OK) rc = dalloc_t(&npc, (size_t)(nnp > 0 ? nnp : 1), s);
         if (rc == GBLA_OK) rc = dalloc_t(&Rnp, (size_t)rank * (size_t)ldnp, s);
@@ -1617,7 +1617,15 @@ backward:
         if (rc == GBLA_OK && nnp > 0) rc = planes_alloc(&Ap, rank, rank, 2, s);   // K up to a leaf or half the rows
         if (rc == GBLA_OK && nnp > 0) rc = planes_alloc(&Bp, nnp, rank, 4, s);   // Rnp^T
         if (rc == GBLA_OK && nnp > 0) rc = backsub_rec(E, Rnp, ldnp, nnp, E.pcol, pcol_h, 0, rank, Ap, Bp, Nm, BL);
-        if (rc == GBLA_OK) {
+        if (rc == GBLA_OK && E.np_out) {
+            // hand the non-pivot part over instead of the dense rows
+            E.np_out->Rnp = Rnp;
+            E.np_out->ldnp = ldnp;
+            E.np_out->npc = npc;
+            E.np_out->nnp = nnp;
+            Rnp = nullptr;
+            npc = nullptr;
+        } else if (rc == GBLA_OK) {
             expand_rref_kernel<<<rgrid, 256, 0, s>>>(Rnp, ldnp, colmap, rank, n, E.R[0], ldr);
             if (launch_check() != cudaSuccess) rc = GBLA_E_CUDA;
         }

@@ -120,6 +120,16 @@ struct EchelonD {
                                         // D' has at most SGE_MAX_DENSITY nonzeros, else panels
     double *density = nullptr;          // out (methods 1, 2): nonzero share of D' before the pass
     int *sge_completed = nullptr;       // out (methods 1, 2): 1 if SGE finished the forward pass
+    // With np_out set, *R is not formed: the caller receives the reduced rows
+    // at the non-pivot columns only (row k = RREF row k, whose pivot column is
+    // pcol[k] with value 1 and whose other pivot columns are 0), and owns the
+    // buffers (device, stream-ordered).
+    struct NonPivot {
+        uint16_t *Rnp = nullptr;   // rank x ldnp
+        int64_t ldnp = 0;
+        int32_t *npc = nullptr;    // [nnp] column of D of each non-pivot column, ascending
+        int64_t nnp = 0;
+    } *np_out = nullptr;
 };
 int echelon_d(const EchelonD &E, int64_t *rank_out);
 

@@ -182,7 +182,7 @@ def dense_case(dense, p):
 @pytest.mark.parametrize("want_reduced", [False, True])
 @pytest.mark.parametrize("case", ["empty_rows", "identity", "perm_identity", "zero", "duplicates",
                                   "rank_one", "all_pivots", "no_b_block", "p2", "p3", "p7", "wide",
-                                  "m0", "n1", "dependent_schur"])
+                                  "m0", "n1", "dependent_schur", "dense_square", "dense_tall"])
 def test_edge_cases(case, want_reduced):
     rng = np.random.default_rng(hash(case) % 2**32)
     p = 65521
@@ -222,6 +222,10 @@ def test_edge_cases(case, want_reduced):
         g = rng.integers(0, p, (60, 40))
         basis = np.where(rng.random((40, 300)) < 0.1, rng.integers(1, p, (40, 300)), 0)
         d = (g @ basis) % p
+    elif case in ("dense_square", "dense_tall"):
+        # one pivot row (column 0), then a Schur complement of full column
+        # rank: every column of D' is a pivot column of its echelon form
+        d = rng.integers(1, p, (70 if case == "dense_square" else 130, 70))
     (rp, c, v), m, n, p = dense_case(d, p)
     res = gbla.reduce(rp, c, v, (m, n), p, want_reduced=want_reduced)
     ref = oracle.rref(m, n, p, rp, c, v) if want_reduced else oracle.echelon(m, n, p, rp, c, v)[:4]
