@@ -98,6 +98,30 @@ void compact_free(Compact *c, cudaStream_t s);
 int modgemm_gather(const Compact &S, int64_t nt0, const Planes &XT, int64_t xt_rows, uint16_t *C, int64_t ldc,
                    int64_t M, int64_t N, int sign, const int32_t *row_lead, const ModP &mp, uint32_t *err,
                    cudaStream_t s, GemmCounters *ctr, unsigned long long *exec = nullptr);
+// Panel application of one echelon wave (solve.cu), fused: for every job q
+// (a panel with pivot rows S, t of them) and every 128-column block of D from
+// the job's first column, D[rows_q] += A_q * D[S]_old restricted to the block,
+// where A_q (M rows, K = 128, zero past t) is the job's stacked multipliers
+// (G - I for the new pivot rows, then -H G for the dependent candidates) as a
+// 2-plane A-operand set and rows_q = rowmap[a_row0 .. a_row0 + M) the rows of
+// D they update (the pivot rows S, then the candidates).  D[S] is read in its
+// u16 form, once per block, and turned into digit planes on chip; both updates
+// of a block read it before either writes (rows of different jobs are
+// disjoint).  jobs[q].item_off: prefix of the jobs' work items (column blocks
+// of jobs with M > 0); jobs[njobs].item_off = the total.
+struct PaJob {
+    int64_t a_row0;       // first row of the job's block of A (and of rowmap)
+    int64_t col0;         // first column of D the job updates
+    int64_t item_off;     // work items of the jobs before
+    const int32_t *srows; // the job's pivot rows of D (K of the product)
+    int32_t M;            // rows of the job's block
+    int32_t t;            // pivot rows (K used, <= 128)
+    int32_t nc;           // columns of D from col0
+    int32_t pad;
+};
+int panel_apply(const Planes &A, const PaJob *jobs, int njobs, const int32_t *rowmap, uint16_t *D, int64_t ldd,
+                int64_t n, const ModP &mp, uint32_t *err, cudaStream_t s);
+
 // Grouped product C[c_rows, c_col0:] += sign * A_p * B_p^T for every problem
 // p, one launch (see GroupProb).
 int modgemm_grouped(const Planes &A, const Planes &B, const GroupProb *probs, int nprob, int64_t K, uint16_t *C,

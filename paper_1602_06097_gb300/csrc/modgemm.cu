@@ -948,6 +948,19 @@ __device__ __forceinline__ void reg_fence16(float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(v[i]));
 }
+__device__ __forceinline__ void reg_fence8(float (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) asm volatile("" : "+f"(v[i]));
+}
+// 8 columns of a TMEM lane quarter (one 32-bit value per lane and column).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 // (run + 65536 H + 256 (M1 + M2) + L) mod p for the four digit-product sums
 // of the gathered product (integers of magnitude at most 2^24 in fp32), in
@@ -1324,6 +1337,399 @@ __global__ void __launch_bounds__(tc::G_THREADS, 1)
             }
         }
         cp_async_wait<0>();   // nothing in flight when the warp leaves
+    }
+
+    tcgen05_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tcgen05_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+// ===================================================================
+// Fused panel application of an echelon wave (see panel_apply)
+// ===================================================================
+// One work item = (job q, 128-column block cb of D from the job's first
+// column).  Per item: the loader copies the job's t pivot rows of D at the
+// block's columns (u16, one bulk copy per row) into a staging tile; four
+// converter warps turn the tile into the B operand's two digit planes
+// (B[col][k] = D[S_k][col], K-major, 128-byte swizzle, four 32-wide K steps);
+// the producer loads the job's A block (K = 128) by TMA, one 16 KB K step per
+// ring stage, for each of the item's 128-row tiles; the MMA warp accumulates
+// the four digit products H, M1, M2, L (512 TMEM columns; K = 128 keeps every
+// sum within 2^21) and eight drain warps add (65536 H + 256 (M1 + M2) + L)
+// mod p into the tile's rows of D, whose old values they fetch before the
+// products arrive.  B is double-buffered across items; TMEM is released as
+// soon as the drain has read it.
+// Warp roles: 0 A producer, 1 MMA issuer, 2..9 drain, 10 loader, 11..14
+// converters.
+constexpr int PA_STAGES = 4;                       // = K steps of one 128-row tile
+constexpr int PA_A_BYTES = 128 * 128;              // 128 rows x (32 K x 2 planes)
+constexpr int PA_B_BYTES = 4 * 128 * 128;          // 4 K steps x 128 columns x (32 K x 2 planes)
+constexpr int PA_STG_BYTES = 128 * 256;            // 128 rows x 128 u16
+constexpr int PA_EPI_WARPS = 8;
+constexpr int PA_CONV_WARPS = 4;
+constexpr int PA_THREADS = 64 + 32 * PA_EPI_WARPS + 32 + 32 * PA_CONV_WARPS;
+constexpr int PA_SMEM_BYTES = PA_STAGES * PA_A_BYTES + 2 * PA_B_BYTES + PA_STG_BYTES + BAR_BYTES + 1024;
+static_assert(PA_SMEM_BYTES <= 232448, "shared memory");
+
+struct PaArgs {
+    const PaJob *jobs;
+    int njobs;
+    const int32_t *rowmap;
+    uint16_t *D;
+    int64_t ldd, n;
+    uint32_t p;
+    float pinv;
+    uint32_t *err;
+};
+
+struct PaItem {
+    int q, cb, nmt;
+    int64_t a_row0, col0;   // col0: first column of the block
+    int t, M;
+    const int32_t *srows;
+};
+
+__device__ __forceinline__ PaItem pa_item(const PaArgs &g, int64_t it) {
+    int lo = 0, hi = g.njobs - 1;   // last job with item_off <= it
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.jobs[mid].item_off <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    const PaJob &J = g.jobs[lo];
+    PaItem x;
+    x.q = lo;
+    x.cb = (int)(it - J.item_off);
+    x.M = J.M;
+    x.t = J.t;
+    x.nmt = (J.M + BM - 1) / BM;
+    x.a_row0 = J.a_row0;
+    x.col0 = J.col0 + (int64_t)x.cb * BN;
+    x.srows = J.srows;
+    return x;
+}
+
+// One K = 16 step, both operands K-major with two planes per 128-byte row
+// (hi at the descriptor, lo 64 bytes on): H += ah*bh, M1 += ah*bl,
+// M2 += al*bh, L += al*bl (TMEM columns d, d + 128, d + 256, d + 384).
+__device__ __forceinline__ void mma_step_k4(uint32_t d, uint32_t a, uint32_t b, uint32_t hi, uint32_t acc0) {
+    asm volatile("{\n\t.reg .pred p, e;\n\t.reg .b32 r, d1, d2, d3;\n\t.reg .b64 a0, a1, x0, x1;\n\t"
+                 "elect.sync r|e, 0xffffffff;\n\t"
+                 "setp.ne.b32 p, %5, 0;\n\t"
+                 "add.u32 d1, %0, 128;\n\tadd.u32 d2, %0, 256;\n\tadd.u32 d3, %0, 384;\n\t"
+                 "mov.b64 a0, {%1, %3};\n\t"
+                 "add.u32 r, %1, 4;\n\tmov.b64 a1, {r, %3};\n\t"
+                 "mov.b64 x0, {%2, %3};\n\t"
+                 "add.u32 r, %2, 4;\n\tmov.b64 x1, {r, %3};\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, x0, %4, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [d1], a0, x1, %4, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [d2], a1, x0, %4, p;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [d3], a1, x1, %4, p;\n\t}" ::"r"(d),
+                 "r"(a), "r"(b), "r"(hi), "r"(IDESC), "r"(acc0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(tc::PA_THREADS, 1)
+    panel_apply_kernel(const __grid_constant__ CUtensorMap tmA, const PaArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sa = base;                                        // A ring
+    uint8_t *sb = base + PA_STAGES * PA_A_BYTES;               // B planes, two buffers
+    uint16_t *stg = reinterpret_cast<uint16_t *>(sb + 2 * PA_B_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sb + 2 * PA_B_BYTES + PA_STG_BYTES);
+    uint64_t *afull = bars;
+    uint64_t *aempty = bars + PA_STAGES;
+    uint64_t *bfull = bars + 2 * PA_STAGES;
+    uint64_t *bempty = bfull + 2;
+    uint64_t *sfull = bempty + 2;
+    uint64_t *sempty = sfull + 1;
+    uint64_t *accf = sempty + 1;
+    uint64_t *acce = accf + 1;
+    uint64_t *done = acce + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PA_STAGES; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bfull[b], 32 * PA_CONV_WARPS);
+            mbar_init(&bempty[b], 1);
+        }
+        mbar_init(sfull, 1);
+        mbar_init(sempty, 32 * PA_CONV_WARPS);
+        mbar_init(accf, 1);
+        mbar_init(acce, PA_EPI_WARPS);
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    tcgen05_fence_before();
+    __syncthreads();
+    tcgen05_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t total = g.jobs[g.njobs].item_off;
+    const int64_t it0 = blockIdx.x, itstep = gridDim.x;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- A producer: the item's row tiles, K step by K step
+            int st = 0;
+            uint32_t phase = 0;
+            int issued[PA_STAGES];
+            uint32_t issued_parity[PA_STAGES];
+            for (int s = 0; s < PA_STAGES; ++s) issued[s] = 0, issued_parity[s] = 0;
+            bool ok = true;
+            for (int64_t it = it0; it < total && ok; it += itstep) {
+                const PaItem x = pa_item(g, it);
+                for (int mt = 0; mt < x.nmt && ok; ++mt) {
+                    for (int ks = 0; ks < PA_STAGES; ++ks) {
+                        if (!mbar_wait(&aempty[st], phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                        mbar_expect_tx(&afull[st], PA_A_BYTES);
+                        tma_load_2d(sa + st * PA_A_BYTES, &tmA, &afull[st], ks * 2 * BK, (int)(x.a_row0 + mt * BM));
+                        issued[st] = 1;
+                        issued_parity[st] = phase;
+                        if (++st == PA_STAGES) st = 0, phase ^= 1u;
+                    }
+                }
+            }
+            for (int s = 0; s < PA_STAGES; ++s) {   // never leave with copies in flight
+                if (!issued[s]) continue;
+                const uint32_t addr = smem_u32(&afull[s]);
+                long long start = clock64();
+                while (!mbar_try_wait(addr, issued_parity[s])) {
+                    if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                        dev_fail(g.err, DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 2 + PA_EPI_WARPS) {
+        // ---------------- loader: the pivot rows' u16 values at the block's
+        // columns, one bulk copy per row (whole 16-byte chunks inside the
+        // row; the converters read a ragged tail directly)
+        uint32_t use = 0;
+        bool ok = true;
+        int pending = 0;
+        uint32_t pending_parity = 0;
+        for (int64_t it = it0; it < total && ok; it += itstep, ++use) {
+            const PaItem x = pa_item(g, it);
+            if (!mbar_wait_warp(sempty, (use & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+            const int64_t avail = g.n - x.col0;                      // >= 1
+            const int64_t wcols = (avail >= BN ? BN : avail) & ~int64_t(7);
+            const uint32_t rbytes = (uint32_t)(wcols * 2);
+            if (lane == 0) mbar_expect_tx(sfull, rbytes * (uint32_t)x.t);
+            __syncwarp();
+            if (rbytes > 0)
+                for (int k = lane; k < x.t; k += 32)
+                    bulk_copy_g2s(smem_u32(stg + k * BN), g.D + (int64_t)x.srows[k] * g.ldd + x.col0, rbytes,
+                                  smem_u32(sfull));
+            pending = 1;
+            pending_parity = use & 1u;
+        }
+        if (pending) {   // never leave with copies in flight
+            const uint32_t addr = smem_u32(sfull);
+            long long start = clock64();
+            while (!__any_sync(0xffffffffu, mbar_try_wait(addr, pending_parity))) {
+                if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                    if (lane == 0) dev_fail(g.err, DEV_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+    }
+    else if (warp > 2 + PA_EPI_WARPS) {
+        // ---------------- converters: thread j (0..127) owns column j of the
+        // block and writes the 16 chunks of 8 K values of its B row: hi and lo
+        // digits of D[S_k][col0 + j], k = 32 ks + 8 c .. + 7, at 16-byte chunk
+        // c (hi) and 4 + c (lo) of row j of K step ks, XOR j mod 8 (128-byte
+        // swizzle).
+        const int j = threadIdx.x - 32 * (3 + PA_EPI_WARPS);
+        const uint32_t P = g.p;
+        uint32_t use = 0;
+        bool ok = true;
+        for (int64_t it = it0; it < total && ok; it += itstep, ++use) {
+            const PaItem x = pa_item(g, it);
+            const uint32_t buf = use & 1u, bu = use >> 1;
+            if (!mbar_wait_warp(sfull, use & 1u, abort_flag, g.err)) { ok = false; break; }
+            if (!mbar_wait_warp(&bempty[buf], (bu & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+            const int64_t avail = g.n - x.col0;
+            const int64_t wcols = (avail >= BN ? BN : avail) & ~int64_t(7);
+            const bool live = j < avail;                 // column inside D
+            const bool staged = j < wcols;               // copied by the loader
+            uint8_t *brow = sb + buf * PA_B_BYTES + j * 128;
+#pragma unroll 1
+            for (int i = 0; i < 16; ++i) {
+                const int ks = i >> 2, c = i & 3, k0 = 32 * ks + 8 * c;
+                uint32_t vh[4], vl[4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    uint32_t a0 = 0, a1 = 0;
+                    if (live && k0 + e < x.t)
+                        a0 = staged ? stg[(k0 + e) * BN + j] : g.D[(int64_t)x.srows[k0 + e] * g.ldd + x.col0 + j];
+                    if (live && k0 + e + 1 < x.t)
+                        a1 = staged ? stg[(k0 + e + 1) * BN + j]
+                                    : g.D[(int64_t)x.srows[k0 + e + 1] * g.ldd + x.col0 + j];
+                    int h0, l0, h1, l1;
+                    digits(a0, P, h0, l0);
+                    digits(a1, P, h1, l1);
+                    vh[e / 2] = pack_bf2(h0, h1);
+                    vl[e / 2] = pack_bf2(l0, l1);
+                }
+                uint8_t *bk = brow + ks * (128 * 128);
+                *reinterpret_cast<uint4 *>(bk + ((c ^ (j & 7)) << 4)) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+                *reinterpret_cast<uint4 *>(bk + (((4 + c) ^ (j & 7)) << 4)) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
+            }
+            mbar_arrive(sempty);   // the staging tile is read
+            fence_proxy_async();   // the planes, to the tensor core's proxy
+            mbar_arrive(&bfull[buf]);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (converged warp, elected lane)
+        int st = 0;
+        uint32_t phase = 0, use = 0, mtc = 0;
+        bool ok = true;
+        const uint64_t d0 = make_sdesc(smem_u32(base));
+        const uint32_t hi = (uint32_t)(d0 >> 32), alo = (uint32_t)d0;
+        const uint32_t blo = alo + ((PA_STAGES * PA_A_BYTES) >> 4);
+        constexpr uint32_t SA = PA_A_BYTES >> 4, SKB = (128 * 128) >> 4, SBB = PA_B_BYTES >> 4;
+        for (int64_t it = it0; it < total && ok; it += itstep, ++use) {
+            const PaItem x = pa_item(g, it);
+            const uint32_t buf = use & 1u, bu = use >> 1;
+            if (!mbar_wait_warp(&bfull[buf], bu & 1u, abort_flag, g.err)) { ok = false; break; }
+            for (int mt = 0; mt < x.nmt && ok; ++mt, ++mtc) {
+                if (!mbar_wait_warp(acce, (mtc & 1u) ^ 1u, abort_flag, g.err)) { ok = false; break; }
+                tcgen05_fence_after();
+                for (int ks = 0; ks < PA_STAGES; ++ks) {
+                    if (!mbar_wait_warp(&afull[st], phase, abort_flag, g.err)) { ok = false; break; }
+                    tcgen05_fence_after();
+                    const uint32_t a = alo + (uint32_t)st * SA, b = blo + buf * SBB + (uint32_t)ks * SKB;
+                    mma_step_k4(tmem, a, b, hi, ks > 0 ? 1u : 0u);
+                    mma_step_k4(tmem, a + 2, b + 2, hi, 1u);   // next 16 of K
+                    commit_elected<false, false>(&aempty[st]);
+                    if (++st == PA_STAGES) st = 0, phase ^= 1u;
+                }
+                if (ok) commit_elected<false, false>(accf);
+            }
+            if (ok) commit_elected<false, false>(&bempty[buf]);
+        }
+        commit_elected<false, false>(done);
+        const uint32_t addr = smem_u32(done);
+        long long start = clock64();
+        while (!__any_sync(0xffffffffu, mbar_try_wait(addr, 0))) {
+            if (clock64() - start > WAIT_LIMIT_CYCLES) {
+                if (lane == 0) dev_fail(g.err, DEV_ERR_TIMEOUT);
+                break;
+            }
+        }
+    } else {
+        // ---------------- drain: warp 2 + 4 h + q reads TMEM lane quarter q,
+        // columns 64 h .. 64 h + 63, and updates row q * 32 + lane of the
+        // tile: D <- (D + (65536 H + 256 (M1 + M2) + L)) mod p
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        constexpr int HC = BN / 2;
+        const float pinv = g.pinv, pf = (float)g.p;
+        const uint32_t P = g.p;
+        const uint32_t bm = 0xFFFFFFFFu / g.p;
+        uint32_t c16 = 65536u % g.p;
+        if (c16 > g.p / 2) c16 -= g.p;
+        const uint32_t biasx = ((1u << 30) + (1u << 26) + g.p - 1) / g.p * g.p - 0x4B400000u * (513u + c16);
+        uint32_t mtc = 0;
+        bool ok = true;
+        for (int64_t it = it0; it < total && ok; it += itstep) {
+            const PaItem x = pa_item(g, it);
+            const int64_t col0 = x.col0 + half * HC;
+            for (int mt = 0; mt < x.nmt; ++mt, ++mtc) {
+                const int rl = mt * BM + quarter * 32 + lane;
+                const int64_t drow = rl < x.M ? (int64_t)g.rowmap[x.a_row0 + rl] : -1;
+                uint16_t *crow = drow >= 0 ? g.D + drow * g.ldd + col0 : nullptr;
+                const bool vec = crow && col0 + HC <= g.n && (reinterpret_cast<uintptr_t>(crow) & 15) == 0;
+                // old values first: their latency overlaps the products
+                uint32_t cw[HC / 2];
+                if (vec) {
+#pragma unroll
+                    for (int v = 0; v < HC / 8; ++v) {
+                        const uint4 q4 = reinterpret_cast<const uint4 *>(crow)[v];
+                        cw[4 * v] = q4.x, cw[4 * v + 1] = q4.y, cw[4 * v + 2] = q4.z, cw[4 * v + 3] = q4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < HC / 2; ++i) {
+                        uint32_t w = 0;
+                        if (crow && col0 + 2 * i < g.n) w = crow[2 * i];
+                        if (crow && col0 + 2 * i + 1 < g.n) w |= (uint32_t)crow[2 * i + 1] << 16;
+                        cw[i] = w;
+                    }
+                }
+                if (!mbar_wait(accf, mtc & 1u, abort_flag, g.err)) { ok = false; break; }
+                tcgen05_fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + half * HC;
+#pragma unroll
+                for (int c = 0; c < HC / 8; ++c) {   // unrolled: cw stays in registers
+                    float hv[8], m1v[8], m2v[8], lv[8];
+                    tmem_ld8(tbase + c * 8, hv);
+                    tmem_ld8(tbase + 128 + c * 8, m1v);
+                    tmem_ld8(tbase + 256 + c * 8, m2v);
+                    tmem_ld8(tbase + 384 + c * 8, lv);
+                    tmem_wait_ld();
+                    reg_fence8(hv);
+                    reg_fence8(m1v);
+                    reg_fence8(m2v);
+                    reg_fence8(lv);
+                    if (c + 1 == HC / 8) {   // every accumulator read: the MMA may go on
+                        tcgen05_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        const uint32_t v0 = drain_step4(0u, hv[e], m1v[e], m2v[e], lv[e], pinv, pf, c16, biasx, bm, P);
+                        const uint32_t v1 =
+                            drain_step4(0u, hv[e + 1], m1v[e + 1], m2v[e + 1], lv[e + 1], pinv, pf, c16, biasx, bm, P);
+                        const uint32_t w = cw[c * 4 + e / 2];
+                        uint32_t o0 = (w & 0xFFFFu) + v0, o1 = (w >> 16) + v1;
+                        o0 -= o0 >= P ? P : 0u;
+                        o1 -= o1 >= P ? P : 0u;
+                        cw[c * 4 + e / 2] = o0 | (o1 << 16);
+                    }
+                }
+                if (vec) {
+#pragma unroll
+                    for (int v = 0; v < HC / 8; ++v)
+                        reinterpret_cast<uint4 *>(crow)[v] =
+                            make_uint4(cw[4 * v], cw[4 * v + 1], cw[4 * v + 2], cw[4 * v + 3]);
+                } else if (crow) {
+#pragma unroll
+                    for (int i = 0; i < HC / 2; ++i) {
+                        if (col0 + 2 * i < g.n) crow[2 * i] = (uint16_t)(cw[i] & 0xFFFFu);
+                        if (col0 + 2 * i + 1 < g.n) crow[2 * i + 1] = (uint16_t)(cw[i] >> 16);
+                    }
+                }
+            }
+        }
     }
 
     tcgen05_fence_before();
@@ -2058,6 +2464,37 @@ int modmatmul32(int64_t M, int64_t N, int64_t K, const uint32_t *A, int64_t lda,
     dfree(err, s);
     cudaStreamSynchronize(s);
     return rc;
+}
+
+// Fused panel application (see tc::panel_apply_kernel).
+int panel_apply(const Planes &A, const PaJob *jobs, int njobs, const int32_t *rowmap, uint16_t *D, int64_t ldd,
+                int64_t n, const ModP &mp, uint32_t *err, cudaStream_t s)
+{
+    if (njobs <= 0 || n <= 0) return GBLA_OK;
+    if (!tc_supported() || mp.p < 8) return GBLA_E_UNSUPPORTED;
+    if (A.nplanes != 2 || A.kp != 128 || ldd % 8) return GBLA_E_INTERNAL;
+    CUtensorMap ma;
+    GBLA_TRY(make_map(&ma, A));
+    static std::once_flag attr_once;
+    static cudaError_t attr_rc = cudaSuccess;
+    static int attr_threads = 0;
+    std::call_once(attr_once, [] {
+        attr_rc = cudaFuncSetAttribute(tc::panel_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tc::PA_SMEM_BYTES);
+        cudaFuncAttributes fa;
+        if (attr_rc == cudaSuccess && (attr_rc = cudaFuncGetAttributes(&fa, tc::panel_apply_kernel)) == cudaSuccess)
+            attr_threads = fa.maxThreadsPerBlock;
+    });
+    GBLA_CUDA_TRY(attr_rc);
+    if (attr_threads < tc::PA_THREADS) return GBLA_E_INTERNAL;   // the block would not fit the SM's registers
+    tc::PaArgs g{};
+    g.jobs = jobs; g.njobs = njobs; g.rowmap = rowmap;
+    g.D = D; g.ldd = ldd; g.n = n;
+    g.p = mp.p; g.pinv = mp.pinv;
+    g.err = err;
+    tc::panel_apply_kernel<<<device_sm_count(), tc::PA_THREADS, tc::PA_SMEM_BYTES, s>>>(ma, g);
+    GBLA_CUDA_TRY(launch_check());
+    return GBLA_OK;
 }
 
 // Grouped product, SIMT variant: one launch of the reference kernel per

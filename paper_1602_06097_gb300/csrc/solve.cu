@@ -861,6 +861,94 @@ __global__ void make_probs_kernel(GroupProb *probs, int nprob, int mode, const P
     if (threadIdx.x == 0) probs[nprob].tile_off = off;
 }
 
+// Job table of the fused panel application (panel_apply) for the jobs of a
+// chunk: job q updates its new pivot rows (if the wave found new pivots on
+// its panel: D[S] <- G D[S]) and its dependent candidates (D[cand] -= H G
+// D[S]); its A block stacks G - I and -H G, rows a_row0 ..  One block.
+__global__ void pa_jobs_kernel(PaJob *jobs, int nj, const PanelPlan *__restrict__ plan,
+                               const int32_t *__restrict__ t_slot, const int32_t *__restrict__ S_slot,
+                               const int32_t *__restrict__ wave_slot, const int64_t *__restrict__ seg, int job0)
+{
+    int64_t arow = 0, items = 0;
+    for (int q0 = 0; q0 < nj; q0 += blockDim.x) {
+        const int q = q0 + (int)threadIdx.x;
+        PaJob J{};
+        int64_t m = 0, k = 0;
+        if (q < nj) {
+            const PanelPlan pl = plan[q];
+            const int t = t_slot[pl.slot];
+            const int64_t b = seg[job0 + q], e = seg[job0 + q + 1];
+            const int tn = wave_slot[2 * pl.slot] > 0 ? t : 0;                  // rows of G - I
+            const int64_t nd = wave_slot[2 * pl.slot + 1] > 0 ? e - b : 0;     // dependent candidates
+            J.t = t;
+            J.M = t > 0 ? (int32_t)(tn + nd) : 0;
+            J.pad = tn;
+            J.nc = pl.nc;
+            J.col0 = (int64_t)pl.slot * PANEL;
+            J.srows = S_slot + (int64_t)pl.slot * PANEL;
+            m = J.M;
+            k = J.M > 0 ? (pl.nc + 127) / 128 : 0;
+        }
+        int64_t tot_m = 0, tot_k = 0;
+        const int64_t em = block_exclusive_scan(m, &tot_m);
+        const int64_t ek = block_exclusive_scan(k, &tot_k);
+        if (q < nj) {
+            J.a_row0 = arow + em;
+            J.item_off = items + ek;
+            jobs[q] = J;
+        }
+        arow += tot_m;
+        items += tot_k;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        PaJob end{};
+        end.a_row0 = arow;
+        end.item_off = items;
+        jobs[nj] = end;
+    }
+}
+
+// A blocks and row maps of the jobs (blockIdx.y = job, rows strided over
+// blockIdx.x, thread k = K column): row m < tn is row m of G - I, row tn + r
+// is -(H G) of the job's r-th candidate (H G rows as in H16, from row_base);
+// K columns past t are 0.  A candidate that became a pivot in this wave is
+// also one of the rows G - I updates: its own row (zero multipliers) maps to
+// -1, so that the fused drain does not write its old values back.
+__global__ void pa_fill_kernel(Planes A, int32_t *__restrict__ rowmap, const PaJob *__restrict__ jobs,
+                               const PanelPlan *__restrict__ plan, const uint16_t *__restrict__ Gm_all,
+                               const uint16_t *__restrict__ HG, const int64_t *__restrict__ seg,
+                               const int32_t *__restrict__ cand, const int32_t *__restrict__ is_piv_row, int job0,
+                               int64_t row_base, uint32_t p)
+{
+    const int q = blockIdx.y, k = threadIdx.x;
+    const PaJob J = jobs[q];
+    const int tn = J.pad;
+    const int64_t b = seg[job0 + q];
+    const uint16_t *G = Gm_all + (int64_t)plan[q].slot * PANEL * PANEL;
+    for (int64_t m = blockIdx.x; m < J.M; m += gridDim.x) {
+        uint32_t a = 0;
+        if (k < J.t) {
+            if (m < tn) {
+                a = G[m * PANEL + k];
+            } else {
+                const uint32_t h = HG[(b - row_base + (m - tn)) * PANEL + k];
+                a = h ? p - h : 0u;
+            }
+        }
+        int hi, lo;
+        digits(a, p, hi, lo);
+        const int64_t row = J.a_row0 + m;
+        *A.at(0, row, k) = i2bf(hi);
+        *A.at(1, row, k) = i2bf(lo);
+        if (k == 0) {
+            int32_t r = m < tn ? J.srows[m] : cand[b + (m - tn)];
+            if (m >= tn && is_piv_row[r]) r = -1;
+            rowmap[row] = r;
+        }
+    }
+}
+
 // Pivot records in pivot-column order (slots ascending, columns ascending
 // inside a slot); *rank receives their number.  One block: a thread per slot,
 // record offsets by a block-wide prefix sum.
@@ -1401,6 +1489,11 @@ struct PanelWork {
     Planes Gp, Bs, H, GmT;
     uint16_t *H16;    // multipliers H = D[cand, pc], then H G (rows as in H)
     int32_t *iota;    // 0, 1, 2, .. (row maps of the H G products)
+    // fused application (tensor cores): job table, stacked A blocks, row maps
+    PaJob *pajobs;
+    Planes Apa;
+    int32_t *rowmap;
+    bool fused;
 };
 
 static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<PanelPlan> &plan, const int64_t *seg,
@@ -1413,6 +1506,27 @@ static int apply_panels(const EchelonD &E, PanelWork &W, const std::vector<Panel
     int64_t ncmax = 0;
     for (const auto &pl : plan) ncmax = pl.nc > ncmax ? pl.nc : ncmax;
     GBLA_CUDA_TRY(cudaMemcpyAsync(W.plan_dev, plan.data(), sizeof(PanelPlan) * (size_t)nj, cudaMemcpyHostToDevice, s));
+    if (W.fused) {
+        // H = D[cand, pc], then H G = H + H (G - I) (grouped product), then
+        // both updates of every job in one fused launch that reads D[S] once
+        const unsigned rb = (unsigned)(rows_max < 64 ? (rows_max > 0 ? rows_max : 1) : 64);
+        gather_h_planes_kernel<<<dim3(rb, (unsigned)nj), PANEL, 0, s>>>(
+            W.H, W.H16, E.D16, E.ldd, seg, cand, job_slot, job0, row_base, W.pc_slot, W.t_slot, E.is_piv_row, mp.p);
+        GBLA_CUDA_TRY(launch_check());
+        gather_gmt_planes_kernel<<<dim3(PANEL, (unsigned)nj), PANEL, 0, s>>>(W.GmT, W.Gm_all, W.plan_dev, mp);
+        GBLA_CUDA_TRY(launch_check());
+        make_probs_kernel<<<1, 256, 0, s>>>(W.probs, nj, 3, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, cand,
+                                           job0, row_base, W.iota);
+        GBLA_CUDA_TRY(launch_check());
+        GBLA_TRY(modgemm_grouped(W.H, W.GmT, W.probs, nj, PANEL, W.H16, PANEL, +1, mp, E.variant, E.err, s, E.ctr));
+        pa_jobs_kernel<<<1, 1024, 0, s>>>(W.pajobs, nj, W.plan_dev, W.t_slot, W.S_slot, W.wave_slot, seg, job0);
+        GBLA_CUDA_TRY(launch_check());
+        pa_fill_kernel<<<dim3(64, (unsigned)nj), PANEL, 0, s>>>(W.Apa, W.rowmap, W.pajobs, W.plan_dev, W.Gm_all,
+                                                              W.H16, seg, cand, E.is_piv_row, job0, row_base,
+                                                              mp.p);
+        GBLA_CUDA_TRY(launch_check());
+        return panel_apply(W.Apa, W.pajobs, nj, W.rowmap, E.D16, E.ldd, E.n, mp, E.err, s);
+    }
     // G - I of the jobs' slots as the A operand (rows q * 128 ..), and D[S]^T
     // as the B operand, converted once: both products below read D[S] as it
     // is before the first one updates it.
@@ -1504,12 +1618,24 @@ int echelon_d(const EchelonD &E, int64_t *rank_out)
         ESTEP(dalloc_t(&W.plan_dev, (size_t)npan + 1, s));
         ESTEP(dalloc_t(&W.probs, (size_t)npan + 2, s));
         ESTEP(dalloc_t(&inv_tab, 65536, s));
-        ESTEP(planes_alloc(&W.Bs, BS_ROWS + n, PANEL, 4, s));
-        ESTEP(planes_alloc(&W.Gp, npan * PANEL, PANEL, 2, s));
+        W.fused = E.variant != GBLA_GEMM_SIMT && mp.p >= 8 && tc_supported();
+        if (!W.fused) {   // the separate products' operands
+            ESTEP(planes_alloc(&W.Bs, BS_ROWS + n, PANEL, 4, s));
+            ESTEP(planes_alloc(&W.Gp, npan * PANEL, PANEL, 2, s));
+        }
         ESTEP(planes_alloc(&W.H, m + PANEL, PANEL, 2, s));
         ESTEP(planes_alloc(&W.GmT, npan * PANEL, PANEL, 4, s));
         ESTEP(dalloc_t(&W.H16, (size_t)W.H.rows * PANEL, s));
         ESTEP(dalloc_t(&W.iota, (size_t)W.H.rows, s));
+        if (W.fused) {
+            // a chunk's A blocks: at most PANEL rows of G - I per job plus its
+            // candidates; the last block's TMA box may read PANEL rows past it
+            const int64_t arows = m + (npan + 2) * PANEL;
+            ESTEP(dalloc_t(&W.pajobs, (size_t)npan + 2, s));
+            ESTEP(planes_alloc(&W.Apa, arows, PANEL, 2, s));
+            ECUDA(cudaMemsetAsync(W.Apa.ptr, 0, W.Apa.plane_elems() * (size_t)W.Apa.nplanes * sizeof(__nv_bfloat16), s));
+            ESTEP(dalloc_t(&W.rowmap, (size_t)arows, s));
+        }
         iota_kernel<<<(unsigned)((W.H.rows + 255) / 256), 256, 0, s>>>(W.iota, W.H.rows);
         ECUDA(launch_check());
         ECUDA(cudaMemsetAsync(E.is_piv_row, 0, sizeof(int32_t) * (size_t)m, s));
@@ -1661,6 +1787,9 @@ done:
     planes_free(&W.GmT, s);
     dfree(W.H16, s);
     dfree(W.iota, s);
+    dfree(W.pajobs, s);
+    planes_free(&W.Apa, s);
+    dfree(W.rowmap, s);
     *rank_out = rank;
     return rc;
 }
