@@ -1373,6 +1373,23 @@ constexpr int PA_THREADS = 64 + 32 * PA_EPI_WARPS + 32 + 32 * PA_CONV_WARPS;
 constexpr int PA_SMEM_BYTES = PA_STAGES * PA_A_BYTES + 2 * PA_B_BYTES + PA_STG_BYTES + BAR_BYTES + 1024;
 static_assert(PA_SMEM_BYTES <= 232448, "shared memory");
 
+// The four sums of a product with K <= 128 (each at most 2^21; M1 + M2 at
+// most 2^22 and exact in fp32), reduced to (65536 H + 256 (M1 + M2) + L)
+// mod p: H and M1 + M2 by a rounded quotient (as reduce_to_word), L read
+// straight through the 1.5 * 2^23 window.  c16 * r_H + 256 r_M + L has
+// magnitude below 2^30 + 2^24; biasy is a multiple of p from 2^30 + 2^24
+// less the three 0x4B400000 offsets (mod 2^32), so the 32-bit sum is the true
+// nonnegative value, below 2^31 + 2^25.
+__device__ __forceinline__ uint32_t drain_step4_k128(float ha, float m1a, float m2a, float la, float pinv, float pf,
+                                                     uint32_t c16, uint32_t biasy, uint32_t bm, uint32_t P) {
+    const uint32_t rh = reduce_to_word(ha, pinv, pf);
+    const uint32_t rm = reduce_to_word(m1a + m2a, pinv, pf);
+    const uint32_t lw = __float_as_uint(la + MAGIC);
+    const uint32_t t = biasy + lw + 256u * rm + c16 * rh;
+    const uint32_t s = t - __umulhi(t, bm) * P;
+    return min(s, s - P);
+}
+
 struct PaArgs {
     const PaJob *jobs;
     int njobs;
@@ -1656,7 +1673,7 @@ __global__ void __launch_bounds__(tc::PA_THREADS, 1)
         const uint32_t bm = 0xFFFFFFFFu / g.p;
         uint32_t c16 = 65536u % g.p;
         if (c16 > g.p / 2) c16 -= g.p;
-        const uint32_t biasx = ((1u << 30) + (1u << 26) + g.p - 1) / g.p * g.p - 0x4B400000u * (513u + c16);
+        const uint32_t biasy = ((1u << 30) + (1u << 24) + g.p - 1) / g.p * g.p - 0x4B400000u * (257u + c16);
         uint32_t mtc = 0;
         bool ok = true;
         for (int64_t it = it0; it < total && ok; it += itstep) {
@@ -1706,9 +1723,9 @@ __global__ void __launch_bounds__(tc::PA_THREADS, 1)
                     }
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
-                        const uint32_t v0 = drain_step4(0u, hv[e], m1v[e], m2v[e], lv[e], pinv, pf, c16, biasx, bm, P);
+                        const uint32_t v0 = drain_step4_k128(hv[e], m1v[e], m2v[e], lv[e], pinv, pf, c16, biasy, bm, P);
                         const uint32_t v1 =
-                            drain_step4(0u, hv[e + 1], m1v[e + 1], m2v[e + 1], lv[e + 1], pinv, pf, c16, biasx, bm, P);
+                            drain_step4_k128(hv[e + 1], m1v[e + 1], m2v[e + 1], lv[e + 1], pinv, pf, c16, biasy, bm, P);
                         const uint32_t w = cw[c * 4 + e / 2];
                         uint32_t o0 = (w & 0xFFFFu) + v0, o1 = (w >> 16) + v1;
                         o0 -= o0 >= P ? P : 0u;

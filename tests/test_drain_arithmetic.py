@@ -179,6 +179,46 @@ def test_drain4_over_k_blocks_equals_the_modular_dot_product(p):
     assert np.array_equal(run, (a * b).sum(axis=1) % p)
 
 
+def drain_step4_k128(ha, m1a, m2a, la, p):
+    """The fused panel product's drain (K <= 128: every sum within 2^21):
+    H and M1 + M2 by a rounded quotient, L straight through the 1.5 * 2^23
+    window, offsets folded into the bias mod 2^32."""
+    pinv, pf = np.float32(1.0 / p), np.float32(p)
+    bm = 0xFFFFFFFF // p
+    c16 = 65536 % p
+    if c16 > p // 2:
+        c16 -= p
+    bias = ((1 << 30) + (1 << 24) + p - 1) // p * p
+    biasy = (bias - MAGIC_BITS * (257 + c16)) % (1 << 32)
+    words = []
+    for x in (ha, m1a + m2a):
+        xf = x.astype(np.float32)
+        assert np.array_equal(xf.astype(np.int64), x)              # M1 + M2 exact in fp32
+        q = fmaf(xf, pinv, MAGIC) - MAGIC
+        r = fmaf(-q, pf, xf)
+        assert np.abs(r).max() <= p // 2 + 1
+        words.append((r + MAGIC).view(np.uint32).astype(np.int64))
+    rh, rm = words
+    lw = (la.astype(np.float32) + MAGIC).view(np.uint32).astype(np.int64)
+    assert np.array_equal(lw - MAGIC_BITS, la)                     # L read exactly
+    true = bias + (lw - MAGIC_BITS) + 256 * (rm - MAGIC_BITS) + c16 * (rh - MAGIC_BITS)
+    assert true.min() >= 0 and true.max() < (1 << 31) + (1 << 25)
+    t = (biasy + lw + 256 * rm + (c16 % (1 << 32)) * rh) % (1 << 32)
+    assert np.array_equal(t, true)
+    q = (t.astype(np.uint64) * np.uint64(bm)) >> np.uint64(32)
+    s = t - q.astype(np.int64) * p
+    assert s.min() >= 0 and s.max() < 2 * p
+    return np.minimum(s, np.where(s >= p, s - p, 1 << 40))
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_drain_step4_k128_is_exact(p):
+    rng = np.random.default_rng(11 * p)
+    n = 60000
+    ha, m1a, m2a, la = (sums(rng, n, 1 << 21) for _ in range(4))
+    assert np.array_equal(drain_step4_k128(ha, m1a, m2a, la, p), (65536 * ha + 256 * (m1a + m2a) + la) % p)
+
+
 def test_digit_bf16_patterns():
     """High half of the fp32 pattern built from 1.5 * 2^23 equals the bf16
     round-to-nearest-even of every digit value, and the low half is zero."""
