@@ -152,10 +152,11 @@ class ClockSampler:
 
 # ------------------------------------------------------ committed records
 def profiled_traffic(name="dram_traffic_fl_150000x200000.md",
-                     src=os.path.join("paper_1602_06097_gb300", "csrc", "modgemm.cu")):
+                     src=os.path.join("paper_1602_06097_gb300", "csrc", "modgemm.cu"), launches=None):
     """DRAM bytes per launch of the dense product from the committed ncu
     summary, if the kernel's source region (named in the summary) still
-    hashes as it did when the counters were taken (else None)."""
+    hashes as it did when the counters were taken and, given the launches
+    per reduction measured now, the summary counted as many (else None)."""
     import re
     try:
         txt = open(os.path.join(ROOT, "profiles", name)).read()
@@ -169,6 +170,9 @@ def profiled_traffic(name="dram_traffic_fl_150000x200000.md",
         return None
     a, b = code.find(m3.group(1)), code.find(m3.group(2))
     if a < 0 or b <= a or hashlib.sha256(code[a:b].encode()).hexdigest() != m2.group(1):
+        return None
+    m4 = re.search(r"launches_per_reduction:\s*(\d+)", txt)
+    if launches is not None and (not m4 or int(m4.group(1)) != int(round(launches))):
         return None
     return int(m1.group(1))
 
@@ -773,9 +777,9 @@ def main():
                     "algorithmic": "M x N x K of the dense products over each tile's K run, 8 flops per modular "
                                    "multiply-add (4 bf16 digit products)",
                     "avg_launch_ms": kernels["modgemm_tc_kernel"]["avg_launch_ms"],
-                    "traffic": profiled_traffic() if (a.workload == WORKLOAD and a.scale == 1.0) else None,
-                    "traffic_source": "profiles/dram_traffic_fl_150000x200000.md (ncu, mean over the 340 "
-                                      "launches of one reduction)"}
+                    "traffic": profiled_traffic(launches=tc_n) if (a.workload == WORKLOAD and a.scale == 1.0) else None,
+                    "traffic_source": "profiles/dram_traffic_fl_150000x200000.md (ncu, mean over the dense "
+                                      "product's launches of one reduction)"}
     else:
         roofline = dict(schur, peak_kind=f"bf16 dense sustained, {kind}", traffic=None)
         roofline["kernel"] = (f"modgemm_gather_kernel (dominant: {g_ms:.1f} ms per step over {g_n:.0f} launches); "

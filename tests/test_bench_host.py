@@ -52,10 +52,13 @@ def test_traffic_reported_only_for_the_measured_kernel_source(tmp_path, monkeypa
     a, b = code.index(begin), code.index(end)
     digest = hashlib.sha256(code[a:b].encode()).hexdigest()
     (tmp_path / rel_prof).write_text(f"traffic_bytes_per_launch: 739917251\n"
+                                     f"launches_per_reduction: 268\n"
                                      f'kernel_region: modgemm.cu "{begin}" .. "{end}"\n'
                                      f"kernel_source_sha256: {digest}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.profiled_traffic() == 739917251
+    assert bench.profiled_traffic(launches=268.0) == 739917251
+    assert bench.profiled_traffic(launches=340.0) is None       # another launch mix
     with open(tmp_path / rel_src, "a") as f:          # outside the region
         f.write("\n// edited\n")
     assert bench.profiled_traffic() == 739917251
