@@ -139,6 +139,9 @@ SMALL = [
     synth.FLSpec(m=520, n=700, npiv=500, density=0.04, run_len=(2, 8), seed=14),       # few C rows
     synth.FLSpec(m=900, n=600, npiv=200, density=0.08, run_len=(4, 16), seed=15),      # more rows than columns
     synth.FLSpec(m=640, n=900, npiv=400, density=0.02, seed=16, group=(2, 16), share=0.8, run_len=(20, 60)),
+    # small primes through the tensor-core path (p >= 8), ragged widths
+    synth.FLSpec(m=700, n=1003, npiv=300, density=0.03, run_len=(4, 16), seed=17, p=11),
+    synth.FLSpec(m=800, n=1201, npiv=350, density=0.03, run_len=(4, 16), seed=18, p=257),
 ]
 
 
@@ -148,6 +151,22 @@ def test_reduce_matches_oracle(idx, want_reduced):
     spec = SMALL[idx]
     rp, c, v = synth.fl_matrix(spec)
     res = gbla.reduce(rp, c, v, (spec.m, spec.n), spec.p, want_reduced=want_reduced)
+    ref = oracle.rref(spec.m, spec.n, spec.p, rp, c, v) if want_reduced else \
+        oracle.echelon(spec.m, spec.n, spec.p, rp, c, v)[:4]
+    same(res, ref)
+
+
+@pytest.mark.parametrize("p", [11, 257, 32003, 65521])
+@pytest.mark.parametrize("want_reduced", [False, True])
+def test_panel_path_matches_oracle(p, want_reduced):
+    """The column-panel forward pass (fused tensor-core application of each
+    wave) at small and large primes, on a D' the automatic choice would give
+    to the sparse SGE."""
+    spec = synth.FLSpec(m=900, n=1301, npiv=300, density=0.04, run_len=(4, 16), seed=19 + p, p=p)
+    rp, c, v = synth.fl_matrix(spec)
+    res = gbla.reduce(rp, c, v, (spec.m, spec.n), spec.p, want_reduced=want_reduced, echelon=gbla.ECHELON_PANELS,
+                      stats=True)
+    assert res[4]["echelon_method"] == gbla.ECHELON_PANELS
     ref = oracle.rref(spec.m, spec.n, spec.p, rp, c, v) if want_reduced else \
         oracle.echelon(spec.m, spec.n, spec.p, rp, c, v)[:4]
     same(res, ref)
