@@ -11,7 +11,8 @@
  * uint64 accumulators that are only reduced with the C `%` operator when a
  * value is read as a multiplier or stored (delayed reduction; every term
  * added is < p^2 < 2^32, and no entry receives more than 2^31 additions, so
- * no accumulator can overflow 2^64).
+ * no accumulator can overflow 2^64).  For a prime p >= 2^16 (oracle_rref32,
+ * p < 2^31) a term is < 2^62, so there every addition is reduced at once.
  *
  * Functions and the passages they follow (GBLA paper, arXiv 1602.06097):
  *   oracle_rref     -- textbook Gauss-Jordan on the WHOLE matrix, rows taken
@@ -26,6 +27,9 @@
  *                      the one keeping A sparsest is chosen.  The paper does
  *                      not fix the tie-break; this oracle reads it as
  *                      (fewest nonzeros, then smallest input row index).
+ *   oracle_rref32   -- oracle_rref for primes p < 2^31 with 32-bit values
+ *                      (the paper's uint32 coefficient type, Sec. 2):
+ *                      the same Gauss-Jordan, each addition reduced.
  *   oracle_echelon  -- the "new order of operations" (Alg. 2, Sec. 4.3) in
  *                      plain row form: every non-pivot row is reduced by the
  *                      normalised pivot rows in ascending pivot column order
@@ -76,13 +80,14 @@ static uint64_t ora_inv(uint64_t a, uint64_t p)
 }
 
 /* Validate a CSR matrix: row_ptr monotone from 0, columns strictly increasing
- * inside a row and in [0,n), values in [1,p).  p must be a prime < 2^16
- * (primality checked by trial division). */
-static int ora_validate(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
-                        const int32_t *col, const uint16_t *val)
+ * inside a row and in [0,n), values in [1,p).  p must be a prime below pmax
+ * (2^16, or 2^31 for the 32-bit entry point; primality checked by trial
+ * division).  Values come as uint16 (val) or uint32 (val32). */
+static int ora_validate_w(int64_t m, int64_t n, uint32_t p, uint32_t pmax, const int64_t *row_ptr,
+                          const int32_t *col, const uint16_t *val, const uint32_t *val32)
 {
-    if (m < 0 || n < 0 || p < 2 || p >= 65536u) return ORA_E_INVAL;
-    for (uint32_t d = 2; d * d <= p; ++d)
+    if (m < 0 || n < 0 || p < 2 || p >= pmax) return ORA_E_INVAL;
+    for (uint64_t d = 2; d * d <= p; ++d)
         if (p % d == 0) return ORA_E_INVAL;
     if (m > 0 && !row_ptr) return ORA_E_INVAL;
     if (m > 0 && row_ptr[0] != 0) return ORA_E_INVAL;
@@ -91,10 +96,17 @@ static int ora_validate(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
             if (col[e] < 0 || col[e] >= n) return ORA_E_INVAL;
             if (e > row_ptr[i] && col[e] <= col[e - 1]) return ORA_E_INVAL;
-            if (val[e] == 0 || val[e] >= p) return ORA_E_INVAL;
+            const uint32_t v = val32 ? val32[e] : val[e];
+            if (v == 0 || v >= p) return ORA_E_INVAL;
         }
     }
     return ORA_OK;
+}
+
+static int ora_validate(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr, const int32_t *col,
+                        const uint16_t *val)
+{
+    return ora_validate_w(m, n, p, 65536u, row_ptr, col, val, NULL);
 }
 
 /* A growing list of reduced dense rows (entries in [0,p)), each with the
@@ -180,7 +192,10 @@ static int ora_gauss_jordan(int64_t n, uint32_t p, int64_t m_in,
 #if ORACLE_MUTANT == 1
                 g = f;                          /* planted: wrong sign */
 #endif
-                for (int64_t k = j; k < n; ++k) w[k] += g * P[k];
+                for (int64_t k = j; k < n; ++k) {
+                    w[k] += g * P[k];
+                    if (p >= 65536u) w[k] %= p;   /* terms up to 2^62: reduce each addition */
+                }
             } else {
                 uint64_t inv = ora_inv(f, p);
                 for (int64_t k = 0; k < j; ++k) w[k] = 0;
@@ -214,7 +229,10 @@ static int ora_gauss_jordan(int64_t n, uint32_t p, int64_t m_in,
 #if ORACLE_MUTANT == 2
                 if (b == a + 1) continue;       /* planted: dropped term */
 #endif
-                for (int64_t k = c; k < n; ++k) w[k] += g * P[k];
+                for (int64_t k = c; k < n; ++k) {
+                    w[k] += g * P[k];
+                    if (p >= 65536u) w[k] %= p;
+                }
             }
             int64_t nz = 0;
             for (int64_t k = qc; k < n; ++k) {
@@ -286,6 +304,55 @@ int oracle_rref(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
     free(dense);
     if (rc == ORA_OK) rc = ora_rows_to_csr(&R, out_row_ptr, out_col, out_val);
     if (rc == ORA_OK) *rank = R.count;
+    free(R.rows);
+    free(R.pcol);
+    free(R.nz);
+    return rc;
+}
+
+/*
+ * RREF(M) over GF(p) for a prime p < 2^31, values as uint32 (the paper's
+ * 32-bit coefficient type, Sec. 2): the Gauss-Jordan of oracle_rref with
+ * every addition reduced.  Output as oracle_rref, values uint32.
+ */
+int oracle_rref32(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
+                  const int32_t *col, const uint32_t *val, int64_t *rank,
+                  int64_t **out_row_ptr, int32_t **out_col, uint32_t **out_val)
+{
+    int rc = ora_validate_w(m, n, p, 2147483648u, row_ptr, col, NULL, val);
+    if (rc) return rc;
+    uint32_t *dense = (uint32_t *)calloc((size_t)(m ? m : 1) * (size_t)(n ? n : 1), sizeof(uint32_t));
+    if (!dense) return ORA_E_NOMEM;
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            dense[(size_t)i * (size_t)n + (size_t)col[e]] = val[e];
+    ora_rows R = {n, 0, 0, NULL, NULL, NULL};
+    rc = ora_gauss_jordan(n, p, m, dense, &R, NULL);
+    free(dense);
+    if (rc == ORA_OK) {
+        int64_t nnz = 0;
+        for (int64_t i = 0; i < R.count; ++i) nnz += R.nz[i];
+        int64_t *rp = (int64_t *)malloc((size_t)(R.count + 1) * sizeof(int64_t));
+        int32_t *cl = (int32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t));
+        uint32_t *vl = (uint32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint32_t));
+        if (!rp || !cl || !vl) {
+            free(rp); free(cl); free(vl);
+            rc = ORA_E_NOMEM;
+        } else {
+            int64_t e = 0;
+            rp[0] = 0;
+            for (int64_t i = 0; i < R.count; ++i) {
+                const uint32_t *Q = R.rows + (size_t)i * (size_t)n;
+                for (int64_t k = 0; k < n; ++k)
+                    if (Q[k]) { cl[e] = (int32_t)k; vl[e] = Q[k]; ++e; }
+                rp[i + 1] = e;
+            }
+            *out_row_ptr = rp;
+            *out_col = cl;
+            *out_val = vl;
+            *rank = R.count;
+        }
+    }
     free(R.rows);
     free(R.pcol);
     free(R.nz);
