@@ -13,8 +13,9 @@ followed (GBLA paper, arXiv 1602.06097):
 
 * :func:`rref`     -- textbook Gauss-Jordan on the whole matrix: FL steps 4-5
   and the reduced-echelon pass (Sec. 4.1), Alg. 3's normalise/reduce rule.
-* :func:`rref32`   -- the same for primes p < 2^31 with uint32 values (the
-  paper's 32-bit coefficient type, Sec. 2), every addition reduced.
+* :func:`rref32`, :func:`echelon32` -- :func:`rref` and :func:`echelon` for
+  primes p < 2^31 with uint32 values (the paper's 32-bit coefficient type,
+  Sec. 2), every addition reduced.
 * :func:`echelon`  -- the new order of operations (Alg. 2, Sec. 4.3) in plain
   row form, then Gauss-Jordan of the Schur complement.
 * :func:`row_counts` -- the work counts of Alg. 2's row reduction alone.
@@ -27,8 +28,9 @@ Every function is pinned by ``tests/test_oracle.py`` against results fixed by
 the mathematics (brute-force row spaces, determinant ranks, closed forms,
 invariants) and, for :func:`multiline`, by the paper's Example 1; the file
 readers by ``tests/test_formats.py`` (files assembled by hand from Table 2);
-:func:`rref32` by ``tests/test_oracle32.py`` (sympy's RREF over GF(p), closed
-forms, invariants, agreement with :func:`rref` below 2^16).
+:func:`rref32` and :func:`echelon32` by ``tests/test_oracle32.py`` (sympy's
+RREF over GF(p) of the matrix and of its Schur complement, closed forms,
+invariants, agreement with the 16-bit functions below 2^16).
 """
 from __future__ import annotations
 
@@ -81,6 +83,10 @@ def _lib(mutant: int = 0):
         lib.oracle_rref32.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, vp, vp, vp,
                                       i64p, ctypes.POINTER(i64p), ctypes.POINTER(i32p),
                                       ctypes.POINTER(u32p)]
+        lib.oracle_echelon32.restype = ctypes.c_int
+        lib.oracle_echelon32.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, vp, vp, vp,
+                                         i64p, ctypes.POINTER(i64p), ctypes.POINTER(i32p),
+                                         ctypes.POINTER(u32p), i64p]
         lib.oracle_echelon.restype = ctypes.c_int
         lib.oracle_echelon.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, vp, vp, vp,
                                        i64p, ctypes.POINTER(i64p), ctypes.POINTER(i32p),
@@ -150,6 +156,25 @@ def rref32(m, n, p, row_ptr, col, val, mutant: int = 0):
     if rc != 0:
         raise OracleError(f"oracle_rref32 failed with code {rc}")
     return _take(lib, rank, rp, cl, vl)
+
+
+def echelon32(m, n, p, row_ptr, col, val, mutant: int = 0):
+    """The new-order echelon form for a prime p < 2^31 with uint32 values:
+    returns (rank, row_ptr, col, val, npiv)."""
+    lib = _lib(mutant)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.uint32)
+    rank = ctypes.c_int64(0)
+    npiv = ctypes.c_int64(0)
+    rp = ctypes.POINTER(ctypes.c_int64)()
+    cl = ctypes.POINTER(ctypes.c_int32)()
+    vl = ctypes.POINTER(ctypes.c_uint32)()
+    rc = lib.oracle_echelon32(m, n, p, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data, ctypes.byref(rank),
+                              ctypes.byref(rp), ctypes.byref(cl), ctypes.byref(vl), ctypes.byref(npiv))
+    if rc != 0:
+        raise OracleError(f"oracle_echelon32 failed with code {rc}")
+    return _take(lib, rank, rp, cl, vl) + (int(npiv.value),)
 
 
 def echelon(m, n, p, row_ptr, col, val, mutant: int = 0, phase_seconds=None, ops=None):

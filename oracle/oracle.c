@@ -27,9 +27,10 @@
  *                      the one keeping A sparsest is chosen.  The paper does
  *                      not fix the tie-break; this oracle reads it as
  *                      (fewest nonzeros, then smallest input row index).
- *   oracle_rref32   -- oracle_rref for primes p < 2^31 with 32-bit values
- *                      (the paper's uint32 coefficient type, Sec. 2):
- *                      the same Gauss-Jordan, each addition reduced.
+ *   oracle_rref32, oracle_echelon32
+ *                   -- oracle_rref and oracle_echelon for primes p < 2^31
+ *                      with 32-bit values (the paper's uint32 coefficient
+ *                      type, Sec. 2): the same steps, each addition reduced.
  *   oracle_echelon  -- the "new order of operations" (Alg. 2, Sec. 4.3) in
  *                      plain row form: every non-pivot row is reduced by the
  *                      normalised pivot rows in ascending pivot column order
@@ -391,10 +392,14 @@ int64_t oracle_pivots(int64_t m, int64_t n, const int64_t *row_ptr, const int32_
  * form.  Output rows: the chosen pivot rows normalised to a leading 1, plus
  * RREF of the Schur complement, merged by pivot column.
  */
-int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
-                   const int32_t *col, const uint16_t *val, int64_t *rank,
-                   int64_t **out_row_ptr, int32_t **out_col, uint16_t **out_val,
-                   int64_t *npiv_out, double *seconds, double *ops)
+/* The new-order echelon for either value width: values come as uint16
+ * (val16, p < 2^16, output out_val16) or uint32 (val32, p < 2^31, output
+ * out_val32).  For p >= 2^16 every addition is reduced (terms reach 2^62). */
+#define ORA_VAL(e) (val32 ? (uint64_t)val32[e] : (uint64_t)val16[e])
+static int ora_echelon_w(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
+                         const int32_t *col, const uint16_t *val16, const uint32_t *val32, int64_t *rank,
+                         int64_t **out_row_ptr, int32_t **out_col, uint16_t **out_val16, uint32_t **out_val32,
+                         int64_t *npiv_out, double *seconds, double *ops)
 {
     /* seconds (optional, 2 entries): wall time of the row reduction by the
      * pivot rows, and of the Gauss-Jordan pass on the Schur complement.
@@ -411,7 +416,7 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
      *       form keeps the pivot rows as they are). */
     double t0 = ora_now(), t1 = t0;
     double ops_b = 0, ops_c = 0, ops_d = 0;
-    int rc = ora_validate(m, n, p, row_ptr, col, val);
+    int rc = ora_validate_w(m, n, p, val32 ? 2147483648u : 65536u, row_ptr, col, val16, val32);
     if (rc) return rc;
     int64_t *piv_row = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
     uint64_t *inv_lead = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
@@ -421,7 +426,7 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
     for (int64_t c = 0; c < n; ++c)
         if (piv_row[c] >= 0) {
             is_piv_row[piv_row[c]] = 1;
-            inv_lead[c] = ora_inv(val[row_ptr[piv_row[c]]], p);
+            inv_lead[c] = ora_inv(ORA_VAL(row_ptr[piv_row[c]]), p);
         }
     /* entries of each pivot row at other pivot columns (na) and at the
      * non-pivot columns (nb), for the work counter */
@@ -463,7 +468,7 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
             if (!w) continue;
             int64_t i = cd_rows[t];
             memset(w, 0, (size_t)n * sizeof(uint64_t));
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) w[col[e]] = val[e];
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) w[col[e]] = ORA_VAL(e);
             for (int64_t j = 0; j < n; ++j) {
                 if (piv_row[j] < 0) continue;
                 uint64_t f = w[j] % p;
@@ -474,8 +479,10 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
                 ops_b += (double)na[j];
                 ops_c += (double)nb[j];
                 uint64_t g = (p - f) * inv_lead[j] % p;
-                for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
-                    w[col[e]] += g * val[e];
+                for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                    w[col[e]] += g * ORA_VAL(e);
+                    if (p >= 65536u) w[col[e]] %= p;   /* terms up to 2^62 */
+                }
             }
             uint32_t *dst = left + (size_t)t * (size_t)n;
             for (int64_t k = 0; k < n; ++k) dst[k] = (uint32_t)(w[k] % p);
@@ -505,10 +512,11 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
                 if (B.rows[(size_t)a * (size_t)n + (size_t)k]) nnz++;
         int64_t *rp = (int64_t *)malloc((size_t)(r + 1) * sizeof(int64_t));
         int32_t *cl = (int32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t));
-        uint16_t *vl = (uint16_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint16_t));
+        uint16_t *vl = val32 ? NULL : (uint16_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint16_t));
+        uint32_t *vl32 = val32 ? (uint32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint32_t)) : NULL;
         int64_t *bottom_of = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
-        if (!rp || !cl || !vl || !bottom_of) {
-            free(rp); free(cl); free(vl); free(bottom_of); free(B.rows); free(B.pcol); free(B.nz);
+        if (!rp || !cl || (!vl && !vl32) || !bottom_of) {
+            free(rp); free(cl); free(vl); free(vl32); free(bottom_of); free(B.rows); free(B.pcol); free(B.nz);
             rc = ORA_E_NOMEM; goto fail0;
         }
         for (int64_t c = 0; c < n; ++c) bottom_of[c] = -1;
@@ -520,14 +528,21 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
                 int64_t i = piv_row[c];
                 for (int64_t s = row_ptr[i]; s < row_ptr[i + 1]; ++s) {
                     cl[e] = col[s];
-                    vl[e] = (uint16_t)((uint64_t)val[s] * inv_lead[c] % p);
+                    const uint64_t v = ORA_VAL(s) * inv_lead[c] % p;
+                    if (vl32) vl32[e] = (uint32_t)v;
+                    else vl[e] = (uint16_t)v;
                     ++e;
                 }
                 rp[++a_out] = e;
             } else if (bottom_of[c] >= 0) {
                 const uint32_t *Q = B.rows + (size_t)bottom_of[c] * (size_t)n;
                 for (int64_t k = 0; k < n; ++k)
-                    if (Q[k]) { cl[e] = (int32_t)k; vl[e] = (uint16_t)Q[k]; ++e; }
+                    if (Q[k]) {
+                        cl[e] = (int32_t)k;
+                        if (vl32) vl32[e] = Q[k];
+                        else vl[e] = (uint16_t)Q[k];
+                        ++e;
+                    }
                 rp[++a_out] = e;
             }
         }
@@ -535,7 +550,9 @@ int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
         free(B.rows);
         free(B.pcol);
         free(B.nz);
-        *out_row_ptr = rp; *out_col = cl; *out_val = vl;
+        *out_row_ptr = rp; *out_col = cl;
+        if (vl32) *out_val32 = vl32;
+        else *out_val16 = vl;
         *rank = r;
         if (npiv_out) *npiv_out = npiv;
     }
@@ -544,6 +561,28 @@ fail0:
     free(inv_lead);
     free(is_piv_row);
     return rc;
+}
+#undef ORA_VAL
+
+int oracle_echelon(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
+                   const int32_t *col, const uint16_t *val, int64_t *rank,
+                   int64_t **out_row_ptr, int32_t **out_col, uint16_t **out_val,
+                   int64_t *npiv_out, double *seconds, double *ops)
+{
+    return ora_echelon_w(m, n, p, row_ptr, col, val, NULL, rank, out_row_ptr, out_col, out_val, NULL, npiv_out,
+                         seconds, ops);
+}
+
+/*
+ * The new-order echelon form (as oracle_echelon) for a prime p < 2^31 with
+ * uint32 values (the paper's 32-bit coefficient type, Sec. 2).
+ */
+int oracle_echelon32(int64_t m, int64_t n, uint32_t p, const int64_t *row_ptr,
+                     const int32_t *col, const uint32_t *val, int64_t *rank,
+                     int64_t **out_row_ptr, int32_t **out_col, uint32_t **out_val, int64_t *npiv_out)
+{
+    return ora_echelon_w(m, n, p, row_ptr, col, NULL, val, rank, out_row_ptr, out_col, NULL, out_val, npiv_out,
+                         NULL, NULL);
 }
 
 /*

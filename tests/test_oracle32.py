@@ -1,5 +1,5 @@
-"""Pins of the oracle's 32-bit RREF (oracle.rref32, primes p < 2^31, uint32
-values: the paper's 32-bit coefficient type, Sec. 2).
+"""Pins of the oracle's 32-bit functions (oracle.rref32, oracle.echelon32:
+primes p < 2^31, uint32 values, the paper's 32-bit coefficient type, Sec. 2).
 
 What fixes the expected results, independently of the oracle:
 1. sympy's reduced row echelon form over GF(p) (DomainMatrix over GF(p)), a
@@ -13,7 +13,11 @@ What fixes the expected results, independently of the oracle:
    tests/test_oracle.py);
 5. malformed input is rejected;
 6. the planted mistakes of the mutant builds (wrong sign, dropped term) fail
-   pin 1.
+   pin 1;
+7. the new-order echelon form: its top block is the FL step-1 pivot rows
+   normalised, its bottom block sympy's RREF of the Schur complement
+   D - C A^-1 B over GF(p) (inverse and RREF by sympy), and below 2^16 it
+   agrees with oracle.echelon.
 """
 import numpy as np
 import pytest
@@ -164,3 +168,85 @@ def test_planted_mistakes_fail_the_sympy_pin(mutant):
     rp, col, val, m, n = to_csr(d)
     got = dense_out(oracle.rref32(m, n, p, rp, col, val, mutant=mutant), n)
     assert not np.array_equal(got, sympy_rref(d, p))
+
+
+# ------------------------------------------------ new-order echelon, 32 bits
+def split_expected(d, p):
+    """The echelon form fixed by the mathematics: the FL step-1 pivot rows
+    (leftmost nonzero; fewest nonzeros, then smallest index) normalised to a
+    leading 1, and RREF(D - C A^-1 B) over GF(p) by sympy, placed at the
+    non-pivot columns; rows ordered by pivot column."""
+    m, n = d.shape
+    F = sympy.GF(p)
+    best = {}
+    for i in range(m):
+        nz = np.nonzero(d[i])[0]
+        if len(nz) == 0:
+            continue
+        c, w = int(nz[0]), len(nz)
+        if c not in best or w < best[c][1]:
+            best[c] = (i, w)
+    pcols = sorted(best)
+    prows = [best[c][0] for c in pcols]
+    others = [i for i in range(m) if i not in set(prows) and np.any(d[i])]
+    npc = [c for c in range(n) if c not in best]
+    rows = {}
+    for c, i in zip(pcols, prows):
+        inv = pow(int(d[i, c]), p - 2, p)
+        rows[c] = [int(x) * inv % p for x in d[i]]
+    if others and npc:
+        def dm(sub):
+            return DomainMatrix([[F(int(x)) for x in r] for r in sub], (len(sub), len(sub[0]) if sub else 0), F)
+        A = dm([[d[i, c] for c in pcols] for i in prows]) if pcols else None
+        Bm = dm([[d[i, c] for c in npc] for i in prows]) if pcols else None
+        Cm = dm([[d[i, c] for c in pcols] for i in others]) if pcols else None
+        Dm = dm([[d[i, c] for c in npc] for i in others])
+        S = Dm - Cm * A.inv() * Bm if pcols else Dm
+        R, piv = S.rref()
+        Rl = R.to_list()
+        for t, pc in enumerate(piv):
+            row = [0] * n
+            for j, c in enumerate(npc):
+                row[c] = int(F.to_sympy(Rl[t][j])) % p
+            rows[npc[pc]] = row
+    order = sorted(rows)
+    return np.array([rows[c] for c in order], dtype=np.int64).reshape(len(order), n), len(pcols)
+
+
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("seed", range(3))
+def test_echelon32_equals_the_split_through_sympy(p, seed):
+    rng = np.random.default_rng(seed * 7919 + p % 991)
+    # a nearly triangular matrix: staircase pivot rows plus dense-ish others
+    m, n = 16, 22
+    d = np.zeros((m, n), dtype=np.int64)
+    for i in range(8):
+        d[i, 2 * i] = rng.integers(1, p)
+        extra = rng.random(n) < 0.3
+        extra[:2 * i + 1] = False
+        d[i, extra] = rng.integers(1, p, size=int(extra.sum()))
+    d[8:] = random_matrix(rng, m - 8, n, p, 0.4)
+    d[14] = d[9]                                         # a dependent row
+    rp, col, val, mm, nn = to_csr(d)
+    r, orp, ocol, oval, npiv = oracle.echelon32(mm, nn, p, rp, col, val)
+    expect, enpiv = split_expected(d, p)
+    assert npiv == enpiv and r == len(expect)
+    assert np.array_equal(dense_out((r, orp, ocol, oval), nn), expect)
+
+
+def test_echelon32_agrees_with_the_16_bit_oracle():
+    p = 65521
+    rng = np.random.default_rng(17)
+    d = random_matrix(rng, 50, 80, p, 0.1)
+    rp, col, val, m, n = to_csr(d)
+    a = oracle.echelon32(m, n, p, rp, col, val)
+    b = oracle.echelon(m, n, p, rp, col, val.astype(np.uint16))
+    assert a[0] == b[0] and a[4] == b[4]
+    for x, y in zip(a[1:4], b[1:4]):
+        assert np.array_equal(np.asarray(x, np.int64), np.asarray(y, np.int64))
+
+
+def test_echelon32_rejects_a_composite_modulus():
+    rp, col, val, m, n = to_csr(np.eye(3, dtype=np.int64))
+    with pytest.raises(oracle.OracleError):
+        oracle.echelon32(m, n, 2**31 - 3, rp, col, val)
